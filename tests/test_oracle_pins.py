@@ -1,0 +1,315 @@
+"""Pins of the FP64 oracle to values fixed by the paper and by mathematics (no GPU).
+
+Each test ties an oracle function to something other than itself: printed constants
+(Table 1, Supplementary Note on the Madelung constant, Fig. 1, Fig. 2), textbook
+constants (rock salt), an independent brute-force lattice sum (Eq. 17 with a finite
+neutralising width), the splitting-parameter independence of Eq. 19-20, and the
+agreement of three independent routes to the neutral charges (Eq. 29 + 34, Eq. 33,
+Eq. 35).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ewald as ew
+from oracle import precond as pc
+from oracle import solve as sv
+from paper_2111_06704_gb300 import workloads as wl
+from tests import _cases
+
+INF = np.inf
+S3 = math.sqrt(3.0)
+
+
+def _point_matrix(xyz, box, g, rc, slab=False, eps=1e-16):
+    xyz = np.asarray(xyz, dtype=np.float64)
+    return ew.interaction_matrix(xyz, np.full(len(xyz), INF), box, g, rc, eps, slab)
+
+
+# ---------------------------------------------------------------- Madelung constants
+
+@pytest.mark.parametrize("edge", [1.0, 2.5])
+def test_simple_cubic_wigner_constant(edge):
+    # Supplementary Note "Madelung constant in Ewald interaction matrix": the diagonal
+    # entry of E for one point charge in a cube of edge L is xi / L, xi = -2.837297479.
+    e = _point_matrix([[0.1 * edge, 0.2 * edge, 0.3 * edge]], (edge,) * 3, 3.0 / edge,
+                      3.0 * edge)
+    assert e[0, 0] * edge == pytest.approx(-2.837297479, abs=2e-9)
+
+
+def test_bcc_wigner_constant():
+    # Same note: U^BCC = -3.63923345028097 for the two-site body-centred cubic cell.
+    e = _point_matrix([[0, 0, 0], [0.5, 0.5, 0.5]], (1.0,) * 3, 3.0, 3.0)
+    assert e[0].sum() == pytest.approx(-3.63923345028097, rel=1e-9)
+
+
+def test_fcc_wigner_constant_recorded():
+    # Same note prints U^FCC = -4.58536207398061.  The lattice sum gives -4.584862074,
+    # which in Wigner-Seitz units is -1.7917472, the standard FCC value; the printed
+    # digits differ at the fourth decimal, so only that agreement is asserted.
+    e = _point_matrix([[0, 0, 0], [0, 0.5, 0.5], [0.5, 0, 0.5], [0.5, 0.5, 0]], (1.0,) * 3,
+                      3.0, 3.0)
+    val = e[0].sum()
+    assert val == pytest.approx(-4.58536207398061, abs=6e-4)
+    r_ws = (3.0 / (16.0 * math.pi)) ** (1.0 / 3.0)
+    assert val * r_ws == pytest.approx(-1.7917472, abs=1e-7)
+
+
+def test_rock_salt_madelung_constant():
+    # NaCl: the potential at a Na+ site of the rock-salt lattice, times the nearest
+    # neighbour distance a/2, is -1.7475645946 (textbook Madelung constant).
+    na = [[0, 0, 0], [0, 0.5, 0.5], [0.5, 0, 0.5], [0.5, 0.5, 0]]
+    cl = [[0.5, 0, 0], [0, 0.5, 0], [0, 0, 0.5], [0.5, 0.5, 0.5]]
+    e = _point_matrix(na + cl, (1.0,) * 3, 3.0, 3.0)
+    q = np.array([1.0] * 4 + [-1.0] * 4)
+    assert -(e[0] @ q) * 0.5 == pytest.approx(1.7475645946, abs=1e-9)
+
+
+def test_fig1_three_charges_diagonal_is_xi():
+    # Fig. 1: three point charges 0.01 L apart in a cube of L = 1; every diagonal
+    # entry of E is the SC Wigner constant xi (the self-interaction is position-free).
+    e = _point_matrix([[0.5, 0.5, 0.49], [0.5, 0.5, 0.5], [0.5, 0.5, 0.51]], (1.0,) * 3, 3.0,
+                      3.0)
+    assert np.allclose(np.diag(e), -2.837297479, atol=2e-9)
+    # off-diagonal entries approach the bare Coulomb law at short range (Eq. S7)
+    assert e[0, 1] - e[0, 0] == pytest.approx(1.0 / 0.01, rel=1e-3)
+
+
+def test_fig1_charge_matrix_inverse():
+    # Eq. S10-S12 with a = N + 1, b = -1: Q~^-1 = (I + 1 1^T)/(N + 1); for N = 3 the
+    # diagonal is 0.5 and the off-diagonal 0.25 (Fig. 1 / Supplementary Note).
+    n = 3
+    qt = (n + 1) * np.eye(n) - np.ones((n, n))
+    inv = np.linalg.inv(qt)
+    assert np.allclose(np.diag(inv), 0.5) and np.allclose(inv[0, 1:], 0.25)
+
+
+# ------------------------------------------------------- 2D lattices (Table 1, Eq. 39)
+
+LATTICES = {
+    # name: (rectangular cell, basis, U^LATT of Table 1 at nearest-neighbour distance 1)
+    "SQ": ((1.0, 1.0), [(0, 0)], 3.90026492000196),
+    "HEX": ((1.0, S3), [(0, 0), (0.5, S3 / 2)], 4.21342263613691),
+    "Kagome": ((2.0, 2 * S3), [(0, 0), (1, 0), (0.5, S3 / 2), (1, S3), (0, S3),
+                               (1.5, 1.5 * S3)], 3.51118553011409),
+    "GRA": ((S3, 3.0), [(0, 0), (0, 1), (S3 / 2, 1.5), (S3 / 2, 2.5)], 3.32302166466011),
+}
+
+
+@pytest.mark.parametrize("name", sorted(LATTICES))
+def test_table1_lattice_constants(name):
+    # One flat sheet of equal point charges in a tall periodic box with the slab
+    # correction of Eq. 39: the Lz^2/6 term cancels the 3D background's sheet-to-sheet
+    # potential exactly, so the row sum of E is the 2D Wigner potential -U^LATT / r_1nn
+    # (Table 1; Sec. III C gives U^GRA / r_1NN = -3.32302166466011).
+    (ax, ay), basis, u = LATTICES[name]
+    nx, ny = max(1, round(6 / ax)), max(1, round(6 / ay))
+    pts = [(ix * ax + bx, iy * ay + by, 0.0) for ix in range(nx) for iy in range(ny)
+           for bx, by in basis]
+    box = (nx * ax, ny * ay, 40.0)
+    e = _point_matrix(pts, box, 1.2, 5.0, slab=True)
+    assert np.allclose(e.sum(axis=1), -u, atol=1e-12)
+
+
+def test_table1_graphene_at_bond_length():
+    # Table 1 lists U^GRA = 2.34015610187332 at r_1nn = 1.42 A; Sec. III C gives the
+    # matching width alpha0 = sqrt(pi/2) U^GRA = 2.93295072600296 1/A.
+    (ax, ay), basis, _ = LATTICES["GRA"]
+    s = 1.42
+    pts = [(ix * ax * s + bx * s, iy * ay * s + by * s, 0.0) for ix in range(3)
+           for iy in range(2) for bx, by in basis]
+    box = (3 * ax * s, 2 * ay * s, 50.0)
+    e = _point_matrix(pts, box, 1.0, 6.0, slab=True)
+    assert e[0].sum() == pytest.approx(-2.34015610187332, abs=1e-12)
+    assert math.sqrt(math.pi / 2) * -e[0].sum() == pytest.approx(2.93295072600296, abs=1e-11)
+
+
+# ------------------------------------------- brute force and splitting independence
+
+def _eq17_brute_force(xyz, alpha, box, lam, rmax):
+    """Eq. 17 with a finite neutralising width lambda: a direct real-space lattice sum
+    of [erf(alpha_ij r) - erf(lambda r)] / r minus pi / (V lambda^2).  Exact up to
+    exp(-K_min^2 / 4 lambda^2) because lambda's own reciprocal sum is dropped."""
+    from scipy.special import erf
+    xyz = np.asarray(xyz)
+    L = np.asarray(box)
+    n = len(xyz)
+    nr = [int(math.ceil(rmax / l)) for l in L]
+    grid = np.array(np.meshgrid(*[np.arange(-m, m + 1) for m in nr], indexing="ij"))
+    shifts = grid.reshape(3, -1).T * L
+    out = np.zeros((n, n))
+    for i in range(n):
+        for j in range(n):
+            aij = ew.mix_alpha(alpha[i], alpha[j])
+            d = xyz[i] - xyz[j] + shifts
+            r = np.sqrt((d * d).sum(axis=1))
+            keep = (r < rmax) & (r > 0)
+            rr = r[keep]
+            s = np.sum((erf(aij * rr) - erf(lam * rr)) / rr)
+            if i == j:
+                s += 2.0 * (aij - lam) / math.sqrt(math.pi)  # r -> 0 limit of the n = 0 term
+            out[i, j] = s
+    return out - math.pi / (np.prod(L) * lam * lam)
+
+
+def test_eq17_brute_force_lattice_sum():
+    rng = np.random.default_rng(11)
+    box = (5.0, 5.5, 6.0)
+    xyz = rng.uniform(0, 1, (4, 3)) * np.array(box)
+    alpha = rng.uniform(1.5, 2.5, 4)
+    ref = _eq17_brute_force(xyz, alpha, box, lam=0.09, rmax=75.0)
+    e = ew.interaction_matrix(xyz, alpha, box, 0.9, 6.6, 1e-16, slab=False)
+    assert np.allclose(e, ref, atol=1e-11, rtol=0)
+
+
+def test_splitting_parameter_independence():
+    # Eq. 19-20: the partition only moves terms between real and reciprocal space, so
+    # E does not depend on g once both sums are converged.
+    work = _cases.tiny_two_sheet(2, 1)
+    el = work.electrode
+    mats = [ew.interaction_matrix(el.xyz, el.alpha, el.box, g, 5.9 / g, 1e-14, True)
+            for g in (0.35, 0.5, 0.7)]
+    scale = np.abs(mats[0]).max()
+    assert np.abs(mats[1] - mats[0]).max() < 1e-10 * scale
+    assert np.abs(mats[2] - mats[0]).max() < 1e-10 * scale
+
+
+def test_kspace_truncation_reading():
+    # "k-space to 1e-8 accuracy" is read as Kc = 2 g sqrt(ln 1e8); a 20% larger Kc
+    # changes E by less than 1e-8 max|E|.
+    work = _cases.tiny_two_sheet(2, 1)
+    el = work.electrode
+    kc = 2 * 0.3 * math.sqrt(math.log(1e8))
+    eps2 = math.exp(-(1.2 * kc) ** 2 / (4 * 0.09))
+    e1 = ew.interaction_matrix(el.xyz, el.alpha, el.box, 0.3, 12.0, 1e-8, True)
+    e2 = ew.interaction_matrix(el.xyz, el.alpha, el.box, 0.3, 12.0, eps2, True)
+    assert np.abs(e1 - e2).max() < 1e-8 * np.abs(e1).max()
+    hkl, _, w = ew.kvectors(wl.small_cell().electrode.box, 0.3, 1e-8)
+    assert len(w) == 8645 and np.all(hkl[:, 0] >= 0)
+
+
+def test_matrix_symmetry():
+    work = _cases.tiny_two_sheet()
+    el = work.electrode
+    e = ew.interaction_matrix(el.xyz, el.alpha, el.box, 0.3, 12.0, 1e-8, True)
+    assert np.abs(e - e.T).max() <= 1e-14 * np.abs(e).max()
+
+
+# --------------------------------------------------- neutral charges: three routes
+
+@pytest.mark.parametrize("q_sol", [0, 2])
+def test_three_routes_agree(q_sol):
+    work = _cases.tiny_two_sheet(q_sol=q_sol)
+    el, io = work.electrode, work.electrolyte
+    e = ew.interaction_matrix(el.xyz, el.alpha, el.box, 0.3, 12.0, 1e-8, True)
+    bsol = ew.electrolyte_potential(el.xyz, el.alpha, io.xyz[0], io.q[0], el.box, 0.3, 12.0)
+    b = ew.rhs_volts(el.chi, bsol) / ew.KE
+    qs = float(io.q[0].sum())
+    assert qs == q_sol
+    q1, mu = sv.solve_bordered(e, b, qs)
+    q2 = sv.two_step(e, b, qs)
+    scale = np.abs(q1).max()
+    assert np.abs(q1 - q2).max() < 1e-10 * scale
+    assert abs(q1.sum() + qs) < 1e-12 * np.abs(q1).sum() + 1e-14
+    # the bordered solution satisfies Eq. 29 with one multiplier for every atom
+    assert np.allclose(e @ q1 + mu, b, atol=1e-10 * np.abs(b).max())
+    if q_sol == 0:
+        q3 = sv.s_matrix(e) @ b
+        assert np.abs(q1 - q3).max() < 1e-10 * scale
+
+
+@pytest.mark.parametrize("q_sol", [0, 2])
+def test_neutral_form_gives_the_same_charges(q_sol):
+    work = _cases.tiny_two_sheet(q_sol=q_sol)
+    el, io = work.electrode, work.electrolyte
+    e = ew.interaction_matrix(el.xyz, el.alpha, el.box, 0.3, 12.0, 1e-8, True)
+    bsol = ew.electrolyte_potential(el.xyz, el.alpha, io.xyz[0], io.q[0], el.box, 0.3, 12.0)
+    qs = float(io.q[0].sum())
+    q_ref, _ = sv.solve_bordered(e, ew.rhs_volts(el.chi, bsol) / ew.KE, qs)
+    en = ew.neutral_form_matrix(e, el.xyz, el.box, 0.3)
+    bn = ew.neutral_form_bsol(bsol, el.xyz, io.xyz[0], io.q[0], el.box, 0.3)
+    q_n = sv.two_step(en, ew.rhs_volts(el.chi, bn) / ew.KE, qs)
+    assert np.abs(q_n - q_ref).max() < 1e-10 * np.abs(q_ref).max()
+    # the neutral form is positive definite; the literal Eq. 22 + 39 matrix is not
+    assert np.linalg.eigvalsh(en).min() > 0
+    assert np.linalg.eigvalsh(e).min() < 0
+
+
+def test_neutralizing_vector():
+    work = _cases.tiny_two_sheet()
+    el = work.electrode
+    e = ew.interaction_matrix(el.xyz, el.alpha, el.box, 0.3, 12.0, 1e-8, True)
+    d, dp, c = sv.neutralizing_vector(e)
+    assert d.sum() == pytest.approx(1.0, abs=1e-13)  # Eq. S8
+    assert np.allclose(e @ dp, 1.0, atol=1e-11)      # Eq. S9
+    assert c == pytest.approx(np.linalg.inv(e).sum(), rel=1e-10)  # C^ele, Eq. 32
+
+
+# ---------------------------------------------------------------- PCG and PCG-DC
+
+def test_fig2_chain_neighbour_count():
+    # Fig. 2: a 50-atom chain in L = 75 A (spacing 1.5 A), r_cut = 15 A: N_cut = 21
+    # neighbours including the atom itself, which fixes the inclusive tie at r = r_cut.
+    xyz = np.zeros((50, 3))
+    xyz[:, 0] = 1.5 * np.arange(50)
+    nb = pc.neighbours(xyz, (75.0, 75.0, 75.0), 15.0)
+    assert all(len(x) == 21 for x in nb)
+
+
+def test_dc_column_is_local_inverse_column():
+    # Three atoms A-B-C on a line, A and C beyond r_cut of each other: M_A is 2x2, so
+    # P[B, A] and P[A, A] have the 2x2 closed form; P[A, B] comes from the 3x3 M_B and
+    # differs from P[B, A] (P is not symmetric, Sec. III B 2 step 2).
+    from scipy.special import erfc
+    xyz = np.array([[0.0, 0, 0], [1.4, 0, 0], [3.1, 0, 0]])
+    alpha = np.array([2.0, 2.0, 2.0])
+    box, g, rc = (20.0, 20.0, 20.0), 0.1, 2.0
+    p, nb = pc.dc_preconditioner(xyz, alpha, box, g, rc)
+    a = math.sqrt(2 / math.pi) * 2.0
+    m = (erfc(g * 1.4) - erfc(g * rc)) / 1.4
+    assert p[1, 0] == pytest.approx(-m / (a * a - m * m), rel=1e-12)
+    assert p[0, 0] == pytest.approx(a / (a * a - m * m), rel=1e-12)
+    # column B comes from the tridiagonal 3x3 M_B: entry [A, B] = -m / (a^2 - m^2 - m2^2)
+    m2 = (erfc(g * 1.7) - erfc(g * rc)) / 1.7
+    assert p[0, 1] == pytest.approx(-m / (a * a - m * m - m2 * m2), rel=1e-12)
+    assert p[2, 0] == 0.0 and p[0, 1] != p[1, 0]
+    # beyond the nearest neighbour cutoff P reduces to 1 / self-energy
+    p1, _ = pc.dc_preconditioner(xyz, alpha, box, g, 1.0)
+    assert np.allclose(p1, np.eye(3) / a)
+
+
+def test_p_gap_preserves_the_inverse_sum():
+    # Eq. 37: filling the n_zero entries with p_gap makes the entries of P sum to
+    # sum_ij (E^-1)_ij.
+    work = _cases.tiny_two_sheet()
+    el = work.electrode
+    e = ew.interaction_matrix(el.xyz, el.alpha, el.box, 0.3, 12.0, 1e-8, True)
+    en = ew.neutral_form_matrix(e, el.xyz, el.box, 0.3)
+    p, nb = pc.dc_preconditioner(el.xyz, el.alpha, el.box, 0.083, 3.0)
+    _, _, c = sv.neutralizing_vector(en)
+    gap = pc.p_gap(p, c, nb)
+    assert pc.fill_gap(p, nb, gap).sum() == pytest.approx(c, rel=1e-10)
+
+
+@pytest.mark.parametrize("kind", ["cg", "jacobi", "dc", "dc_gap"])
+def test_pcg_reaches_the_direct_solution(kind):
+    work = _cases.tiny_two_sheet()
+    el, io = work.electrode, work.electrolyte
+    e = ew.interaction_matrix(el.xyz, el.alpha, el.box, 0.3, 12.0, 1e-8, True)
+    en = ew.neutral_form_matrix(e, el.xyz, el.box, 0.3)
+    bsol = ew.electrolyte_potential(el.xyz, el.alpha, io.xyz[0], io.q[0], el.box, 0.3, 12.0)
+    bn = ew.rhs_volts(el.chi, ew.neutral_form_bsol(bsol, el.xyz, io.xyz[0], io.q[0],
+                                                   el.box, 0.3)) / ew.KE
+    p = None
+    if kind == "jacobi":
+        p = sv.jacobi(en)
+    elif kind.startswith("dc"):
+        p, nb = pc.dc_preconditioner(el.xyz, el.alpha, el.box, 0.083, 3.0)
+        if kind == "dc_gap":
+            _, _, c = sv.neutralizing_vector(en)
+            p = pc.fill_gap(p, nb, pc.p_gap(p, c, nb))
+    x, it, rel = sv.pcg(en, bn, p, tol=1e-12, maxit=500)
+    assert rel <= 1e-12 and it < 200
+    ref = np.linalg.solve(en, bn)
+    assert np.abs(x - ref).max() < 1e-9 * np.abs(ref).max()
