@@ -1,0 +1,181 @@
+/*
+ * cpm.h -- C ABI of the GB300 SR-CPM electrode-charge library (libcpm.so).
+ *
+ * The library computes the electrode charges of the Siepmann-Sprik / Reed constant
+ * potential method as reformulated by Li, Wang, Liu & Jiang (arXiv 2111.06704):
+ *
+ *   cpm_build_E     the Gaussian Ewald interaction matrix E of the electrode atoms
+ *                   (Sec. II C, Eq. 22-23; slab correction Eq. 39), the PCG-DC
+ *                   preconditioner (Sec. III B 2, Eq. 36-37) and the neutralising
+ *                   vector d (Eq. S8-S9);
+ *   cpm_potential   the extrinsic potential b = chi - b^sol on every electrode atom
+ *                   (Eq. 25) for one or many electrolyte frames;
+ *   cpm_solve       the first step of the two-step method, E q^b = b, by
+ *                   preconditioned conjugate gradient (Sec. III B 2);
+ *   cpm_neutralize  the second step q = q^b - (Q^b + Q^sol) d (Eq. 35).
+ *
+ * Units: positions in Angstrom, charges in e, chi and b in volts.  E is kept in
+ * Gaussian units (1/A); volts convert with k_e = 14.399645478 V A / e.
+ *
+ * Neutral-equivalent form.  Eq. 39 expands to -(2 pi/V)(z_i^2 + z_j^2) + (4 pi/V) z_i z_j
+ * - (2 pi/V) Lz^2/6 and the Ewald constant -pi/(V g^2) is the same for every pair.  The
+ * library stores E_n = E + pi/(V g^2) + (2 pi/V)(z_i^2 + z_j^2 + Lz^2/6), i.e. it keeps
+ * the dipole term (4 pi/V) z_i z_j and drops the rank-2 remainder u 1^T + 1 u^T + k0 1 1^T.
+ * For charges with 1^T q = -Q^sol that remainder only adds a multiple of 1 (absorbed by
+ * the multiplier mu_c of Eq. 29-30) and a -Q^sol u term that the matching Q^sol z_i^2
+ * term of b^sol cancels, so the neutral charges of Eq. 35 are unchanged.  E_n is
+ * symmetric positive definite; the literal E is indefinite along 1 for slabs, which
+ * conjugate gradient cannot handle.  cpm_potential returns b in the same form.
+ *
+ * Pointers: every array argument may be a host pointer or a CUDA device pointer of the
+ * context's device (detected with cudaPointerGetAttributes).  The caller owns them; the
+ * library never keeps them past the call.  Host arrays are staged through device
+ * buffers inside the call.  Layouts are row-major and contiguous.
+ *
+ * Synchronisation: every call is ordered on the context's stream and returns after its
+ * results are complete (the call synchronises that stream before returning).
+ *
+ * Errors: every call returns CPM_OK (0) or a negative status; cpm_last_error() gives a
+ * message.  No call aborts or exits the process.  A context is not thread safe.
+ */
+#ifndef CPM_H
+#define CPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------- */
+#define CPM_OK 0
+#define CPM_EINVAL (-1)      /* bad argument (size, pointer, parameter) */
+#define CPM_ENOMEM (-2)      /* device allocation failed */
+#define CPM_ECUDA (-3)       /* a CUDA runtime or driver call failed */
+#define CPM_ENOCONV (-4)     /* maxit reached: q holds the last iterate, relres is set */
+#define CPM_EBREAKDOWN (-5)  /* p^T E p <= 0 or a non-finite value in the iteration */
+#define CPM_ENOTBUILT (-7)   /* cpm_build_E has not succeeded on this context */
+
+/* ---- precision of the E build and of the solve ----------------------------------- */
+#define CPM_PREC_FP64 0    /* FP64 phases, FP64 structure-factor GEMM, FP64 E and matvec */
+#define CPM_PREC_FP32 1    /* exact fixed-point phases, FP32 SIMT GEMM with K-chunks
+                              summed in FP64, FP32 E, FP32 matvec with FP64 reductions */
+#define CPM_PREC_BF16X6 2  /* as FP32, but the GEMM runs on tcgen05 tensor cores with a
+                              three-way BF16 split of each operand (6 products) */
+
+/* ---- preconditioners (Sec. III B 2) ----------------------------------------------- */
+#define CPM_PRECOND_NONE 0    /* conventional CG */
+#define CPM_PRECOND_JACOBI 1  /* diag(E)^-1: the plain baseline */
+#define CPM_PRECOND_DC 2      /* PCG-DC: columns of local inverses M_tau^-1 (Eq. 36) */
+
+/* ---- forms for cpm_get_E ----------------------------------------------------------- */
+#define CPM_E_STORED 0  /* the stored neutral-equivalent E_n */
+#define CPM_E_PAPER 1   /* E of Eq. 22 with Eq. 39, rebuilt from E_n by adding the
+                           rank-2 remainder back */
+
+typedef struct cpm_params {
+  double box[3];       /* orthorhombic periodic cell edges Lx, Ly, Lz (A) */
+  double g_ewald;      /* Ewald splitting parameter (the paper's eta, Eq. 12), 1/A */
+  double rcut_real;    /* real-space cutoff (A); every image within it is summed */
+  double kspace_eps;   /* reciprocal cutoff Kc = 2 g sqrt(ln(1/eps)) */
+  int slab;            /* 1: Yeh-Ballenger slab correction of Eq. 39 */
+  int precision;       /* CPM_PREC_* */
+  int precond;         /* CPM_PRECOND_* */
+  double g_dc;         /* PCG-DC screening factor g of Eq. 36 (1/A) */
+  double rcut_dc;      /* PCG-DC neighbour cutoff r_cut (A), inclusive */
+  int p_gap;           /* 1: fill the zeros of P with p_gap (Eq. 37) */
+  void* stream;        /* cudaStream_t for every call; NULL = the legacy default stream */
+  /* Optional device allocator (e.g. the PyTorch caching allocator).  NULL = cudaMalloc.
+     alloc returns NULL on failure; free receives the pointers alloc returned. */
+  void* (*alloc)(size_t bytes, void* user);
+  void (*free)(void* ptr, void* user);
+  void* alloc_user;
+} cpm_params;
+
+typedef struct cpm_ctx cpm_ctx;
+
+/* Fills p with the defaults: g 0.3, rcut 12, eps 1e-8, slab 1, FP32, PCG-DC with
+ * g_dc 0.083 and r_cut 8 (Sec. IV A), p_gap 1, default stream, cudaMalloc.  The box
+ * is left zero and must be set. */
+void cpm_default_params(cpm_params* p);
+
+/* Creates a context on the current CUDA device.  *out receives the handle. */
+int cpm_create(cpm_ctx** out, const cpm_params* p);
+int cpm_destroy(cpm_ctx* c);
+
+/*
+ * Builds everything that depends only on the electrode geometry (done once per
+ * geometry; the electrode coefficients are invariant during MD, Sec. III A):
+ *  - the half-space k-vector table: K = 2 pi (h/Lx, k/Ly, l/Lz) != 0, |K| <= Kc,
+ *    weights W_K = 2 (4 pi/V) exp(-K^2/4g^2) / K^2 (Eq. 13, Eq. 20);
+ *  - the structure-factor operand A = [sqrt(W) cos(K.r_i) | sqrt(W) sin(K.r_i)] and
+ *    the reciprocal part of E as A A^T (Eq. 23 with cos(K.(r_i - r_j)) split by the
+ *    angle-addition formula);
+ *  - in the same pass, the real-space part, the diagonal self terms and the slab
+ *    dipole term of Eq. 22 / Eq. 39 (neutral-equivalent form, see above);
+ *  - the PCG-DC preconditioner (if selected) and d = d' / (1^T d'), E_n d' = 1.
+ * n: electrode atoms (1 <= n).  xyz[n*3]: positions (A).  alpha[n]: Gaussian inverse
+ * widths (1/A) of Eq. 4; INFINITY marks a point charge (no self-energy, Sec. II C).
+ * Replaces any earlier build on the context.
+ */
+int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha);
+
+/*
+ * b = chi - k_e * b^sol for `frames` electrolyte frames (Eq. 25), in the
+ * neutral-equivalent form: b^sol_i = sum_I q_I [real + reciprocal part of e_iI with
+ * the point-Gaussian coefficient alpha_i] + (4 pi/V) z_i sum_I q_I z_I (slab).
+ * ion_xyz[frames*n_ion*3] (A), ion_q[frames*n_ion] (e), chi[n] (V, shared by all
+ * frames).  b_out[frames*n] (V).  qsol_out[frames] (may be NULL) receives
+ * Q^sol = sum_I q_I of each frame.  n_ion may be 0.
+ */
+int cpm_potential(cpm_ctx* c, int frames, int n_ion, const double* ion_xyz,
+                  const double* ion_q, const double* chi, double* b_out, double* qsol_out);
+
+/*
+ * First step of Eq. 35: solves E_n q^b = b / k_e for nrhs right-hand sides by
+ * (preconditioned) conjugate gradient.  The PCG-DC preconditioner is not symmetric, so
+ * the flexible (Polak-Ribiere) beta is used with it.
+ * b[nrhs*n] (V).  q_inout[nrhs*n] (e): with use_guess != 0 it holds the initial guess
+ * (e.g. the previous MD step, Eq. 26), else the guess is zero; on return it holds q^b.
+ * Stops when ||b - E_n q||_2 / ||b||_2 <= tol for every column, or after maxit
+ * iterations (CPM_ENOCONV).  iters_out[nrhs] and relres_out[nrhs] may be NULL.
+ */
+int cpm_solve(cpm_ctx* c, int nrhs, const double* b, double* q_inout, int use_guess,
+              double tol, int maxit, int* iters_out, double* relres_out);
+
+/*
+ * Second step of Eq. 35 for nrhs columns: q <- q - (sum_i q_i + Q^sol) d, so that
+ * sum_i q_i = -Q^sol (Eq. 34).  qsol[nrhs] may be NULL (Q^sol = 0).
+ */
+int cpm_neutralize(cpm_ctx* c, int nrhs, double* q_inout, const double* qsol);
+
+/* Copies E (form CPM_E_STORED or CPM_E_PAPER) into out[n*ld] (row-major, ld >= n). */
+int cpm_get_E(cpm_ctx* c, int form, double* out, int64_t ld);
+
+typedef struct cpm_info_t {
+  int n;              /* electrode atoms */
+  int m;              /* half-space k-vectors */
+  int64_t nnz_p;      /* stored entries of the PCG-DC preconditioner */
+  double p_gap;       /* Eq. 37 value in use (0 if disabled) */
+  double c_ele;       /* 1^T E_n^-1 1 */
+  double t_kspace_ms; /* device time of the last build's k-space GEMM (fused epilogue) */
+  double t_phase_ms;  /* structure-factor operand generation */
+  double t_precond_ms;
+  double t_dsolve_ms;
+  int d_iters;        /* iterations of the E_n d' = 1 solve */
+  int64_t launches;   /* CUDA kernels launched by the library in this process so far */
+} cpm_info_t;
+
+int cpm_get_info(cpm_ctx* c, cpm_info_t* out);
+
+/* Copies the neutralising vector d (Eq. S8) into d_out[n]. */
+int cpm_get_d(cpm_ctx* c, double* d_out);
+
+const char* cpm_last_error(const cpm_ctx* c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CPM_H */

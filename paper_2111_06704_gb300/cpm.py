@@ -1,0 +1,276 @@
+"""Thin ctypes binding of libcpm.so (include/cpm.h): argument marshalling only.
+
+Arrays may be numpy arrays (host) or CUDA torch tensors (device, float64, contiguous);
+the library stages host arrays itself.  Every compute step runs in the CUDA library;
+there is no Python or CPU fallback, and loading fails loudly when the library is absent.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+CPM_OK = 0
+CPM_EINVAL = -1
+CPM_ENOMEM = -2
+CPM_ECUDA = -3
+CPM_ENOCONV = -4
+CPM_EBREAKDOWN = -5
+CPM_ENOTBUILT = -7
+
+CPM_PREC_FP64 = 0
+CPM_PREC_FP32 = 1
+CPM_PREC_BF16X6 = 2
+
+CPM_PRECOND_NONE = 0
+CPM_PRECOND_JACOBI = 1
+CPM_PRECOND_DC = 2
+
+CPM_E_STORED = 0
+CPM_E_PAPER = 1
+
+KE = 14.399645478  # V A / e
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class cpm_params(ctypes.Structure):
+    _fields_ = [
+        ("box", ctypes.c_double * 3),
+        ("g_ewald", ctypes.c_double),
+        ("rcut_real", ctypes.c_double),
+        ("kspace_eps", ctypes.c_double),
+        ("slab", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("precond", ctypes.c_int),
+        ("g_dc", ctypes.c_double),
+        ("rcut_dc", ctypes.c_double),
+        ("p_gap", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+        ("alloc", ALLOC_FN),
+        ("free", FREE_FN),
+        ("alloc_user", ctypes.c_void_p),
+    ]
+
+
+class cpm_info_t(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int),
+        ("m", ctypes.c_int),
+        ("nnz_p", ctypes.c_int64),
+        ("p_gap", ctypes.c_double),
+        ("c_ele", ctypes.c_double),
+        ("t_kspace_ms", ctypes.c_double),
+        ("t_phase_ms", ctypes.c_double),
+        ("t_precond_ms", ctypes.c_double),
+        ("t_dsolve_ms", ctypes.c_double),
+        ("d_iters", ctypes.c_int),
+        ("launches", ctypes.c_int64),
+    ]
+
+
+EXPORTS = ["cpm_default_params", "cpm_create", "cpm_destroy", "cpm_build_E", "cpm_potential",
+           "cpm_solve", "cpm_neutralize", "cpm_get_E", "cpm_get_info", "cpm_get_d",
+           "cpm_last_error"]
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Loads libcpm.so (building it first when asked and it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"libcpm.so is not built ({path})")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    vp, d, i, i64 = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int64
+    lib.cpm_default_params.argtypes = [P(cpm_params)]
+    lib.cpm_default_params.restype = None
+    lib.cpm_create.argtypes = [P(vp), P(cpm_params)]
+    lib.cpm_destroy.argtypes = [vp]
+    lib.cpm_build_E.argtypes = [vp, i, vp, vp]
+    lib.cpm_potential.argtypes = [vp, i, i, vp, vp, vp, vp, vp]
+    lib.cpm_solve.argtypes = [vp, i, vp, vp, i, d, i, vp, vp]
+    lib.cpm_neutralize.argtypes = [vp, i, vp, vp]
+    lib.cpm_get_E.argtypes = [vp, i, vp, i64]
+    lib.cpm_get_info.argtypes = [vp, P(cpm_info_t)]
+    lib.cpm_get_d.argtypes = [vp, vp]
+    lib.cpm_last_error.argtypes = [vp]
+    lib.cpm_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("cpm_default_params", "cpm_last_error"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+class CpmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"cpm status {status}: {msg}")
+        self.status = status
+
+
+def _ptr(a):
+    """(pointer, keep-alive) for a numpy array or a CUDA torch tensor (float64/int)."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        return a.ctypes.data_as(ctypes.c_void_p), a
+    # torch tensor
+    if not a.is_contiguous():
+        raise ValueError("tensors passed to libcpm must be contiguous")
+    return ctypes.c_void_p(a.data_ptr()), a
+
+
+def default_params(box, **kw) -> cpm_params:
+    lib = load()
+    p = cpm_params()
+    lib.cpm_default_params(ctypes.byref(p))
+    p.box[0], p.box[1], p.box[2] = (float(x) for x in box)
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Context:
+    """One libcpm context (one electrode geometry, one CUDA device and stream)."""
+
+    def __init__(self, box, stream=None, torch_allocator: bool = False, **params):
+        self.lib = load()
+        self.params = default_params(box, **params)
+        if stream is not None:
+            self.params.stream = ctypes.c_void_p(int(stream))
+        self._cb = None
+        if torch_allocator:
+            import torch
+            dev = torch.cuda.current_device()
+
+            def _alloc(nbytes, _user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream)
+                except Exception:  # noqa: BLE001 - reported to C as NULL
+                    return None
+
+            def _free(ptr, _user):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._cb = (ALLOC_FN(_alloc), FREE_FN(_free))
+            self.params.alloc, self.params.free = self._cb
+        h = ctypes.c_void_p()
+        self._check(self.lib.cpm_create(ctypes.byref(h), ctypes.byref(self.params)), None)
+        self.h = h
+        self.n = 0
+
+    def _check(self, st, h=-1):
+        if st != CPM_OK:
+            hh = self.h if h == -1 else h
+            msg = self.lib.cpm_last_error(hh).decode() if hh else "create failed"
+            raise CpmError(st, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.cpm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    # -- the four calls of the boundary ---------------------------------------------
+    def cpm_build_E(self, xyz, alpha):
+        n = int(xyz.shape[0])
+        px, kx = _ptr(xyz)
+        pa, ka = _ptr(alpha)
+        self._check(self.lib.cpm_build_E(self.h, n, px, pa))
+        self.n = n
+
+    def cpm_potential(self, ion_xyz, ion_q, chi, b_out=None, qsol_out=None):
+        frames, n_ion = int(ion_q.shape[0]), int(ion_q.shape[1])
+        if b_out is None:
+            b_out = np.empty((frames, self.n))
+        if qsol_out is None and isinstance(b_out, np.ndarray):
+            qsol_out = np.empty(frames)
+        p1, k1 = _ptr(ion_xyz)
+        p2, k2 = _ptr(ion_q)
+        p3, k3 = _ptr(chi)
+        p4, k4 = _ptr(b_out)
+        p5, k5 = _ptr(qsol_out)
+        self._check(self.lib.cpm_potential(self.h, frames, n_ion, p1, p2, p3, p4, p5))
+        if isinstance(b_out, np.ndarray) and k4 is not b_out:
+            b_out[...] = k4
+        if isinstance(qsol_out, np.ndarray) and k5 is not qsol_out:
+            qsol_out[...] = k5
+        return b_out, qsol_out
+
+    def cpm_solve(self, b, q=None, use_guess=False, tol=1e-6, maxit=1000, allow_noconv=False):
+        nrhs = int(b.shape[0]) if b.ndim == 2 else 1
+        if q is None:
+            q = np.zeros((nrhs, self.n))
+        pb, kb = _ptr(b)
+        pq, kq = _ptr(q)
+        iters = np.zeros(nrhs, dtype=np.int32)
+        rel = np.zeros(nrhs)
+        st = self.lib.cpm_solve(self.h, nrhs, pb, pq, 1 if use_guess else 0, float(tol),
+                                int(maxit), iters.ctypes.data_as(ctypes.c_void_p),
+                                rel.ctypes.data_as(ctypes.c_void_p))
+        if not (st == CPM_ENOCONV and allow_noconv):
+            self._check(st)
+        if isinstance(q, np.ndarray) and kq is not q:
+            q[...] = kq
+        return q, iters, rel
+
+    def cpm_neutralize(self, q, qsol=None):
+        nrhs = int(q.shape[0]) if q.ndim == 2 else 1
+        pq, kq = _ptr(q)
+        ps, ks = _ptr(qsol)
+        self._check(self.lib.cpm_neutralize(self.h, nrhs, pq, ps))
+        if isinstance(q, np.ndarray) and kq is not q:
+            q[...] = kq
+        return q
+
+    # -- inspection -----------------------------------------------------------------
+    def cpm_get_E(self, form=CPM_E_STORED):
+        out = np.empty((self.n, self.n))
+        self._check(self.lib.cpm_get_E(self.h, int(form), out.ctypes.data_as(ctypes.c_void_p),
+                                       self.n))
+        return out
+
+    def cpm_get_d(self):
+        out = np.empty(self.n)
+        self._check(self.lib.cpm_get_d(self.h, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def cpm_get_info(self) -> dict:
+        info = cpm_info_t()
+        self._check(self.lib.cpm_get_info(self.h, ctypes.byref(info)))
+        return {k: getattr(info, k) for k, _ in cpm_info_t._fields_}
+
+
+def charges(ctx: Context, ion_xyz, ion_q, chi, tol=1e-6, maxit=1000, q0=None):
+    """One charge solve per frame through the boundary: b, q^b, neutral q (Eq. 25, 35)."""
+    b, qsol = ctx.cpm_potential(ion_xyz, ion_q, chi)
+    q, iters, rel = ctx.cpm_solve(b, q0, use_guess=q0 is not None, tol=tol, maxit=maxit)
+    ctx.cpm_neutralize(q, qsol)
+    return q, iters, rel, b, qsol
+
+
+__all__ = ["Context", "CpmError", "load", "charges", "EXPORTS", "KE"] + [
+    n for n in dir() if n.startswith("CPM_")]

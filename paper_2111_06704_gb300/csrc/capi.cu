@@ -1,0 +1,586 @@
+// C ABI entry points (include/cpm.h): argument checks, staging of host arrays, the
+// k-vector table, and the order of the build / potential / solve / neutralise steps.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "cpm_internal.cuh"
+
+namespace cpm {
+
+namespace {
+std::atomic<long long> g_launches{0};
+}
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+int set_err(Ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_check(Ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return CPM_OK;
+  return set_err(c, CPM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int buf_alloc(Ctx* c, Buf* b, size_t bytes) {
+  buf_free(c, b);
+  if (bytes == 0) bytes = 256;
+  void* p = nullptr;
+  if (c->p.alloc) {
+    p = c->p.alloc(bytes, c->p.alloc_user);
+    if (!p) return set_err(c, CPM_ENOMEM, "allocator callback returned NULL");
+  } else {
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(c, CPM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+  }
+  b->ptr = p;
+  b->bytes = bytes;
+  return CPM_OK;
+}
+
+void buf_free(Ctx* c, Buf* b) {
+  if (!b->ptr) return;
+  if (c->p.free) c->p.free(b->ptr, c->p.alloc_user);
+  else cudaFree(b->ptr);
+  b->ptr = nullptr;
+  b->bytes = 0;
+}
+
+int buf_reserve(Ctx* c, Buf* b, size_t bytes) {
+  if (b->ptr && b->bytes >= bytes) return CPM_OK;
+  // the buffer may still be in use by queued work
+  if (b->ptr) {
+    int st = cuda_check(c, cudaStreamSynchronize(c->stream), "reserve sync");
+    if (st) return st;
+  }
+  return buf_alloc(c, b, bytes);
+}
+
+namespace {
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Returns a device pointer holding `bytes` of `src` (src itself if it is on the device).
+int stage_in(Ctx* c, Buf* tmp, const void* src, size_t bytes, const void** out) {
+  if (is_device_ptr(src)) {
+    *out = src;
+    return CPM_OK;
+  }
+  if (int st = buf_reserve(c, tmp, bytes)) return st;
+  if (int st = cuda_check(c, cudaMemcpyAsync(tmp->ptr, src, bytes, cudaMemcpyHostToDevice,
+                                             c->stream), "copy in"))
+    return st;
+  *out = tmp->ptr;
+  return CPM_OK;
+}
+
+// Device destination for `dst` (dst itself when on the device); copy_out finishes it.
+int stage_out(Ctx* c, Buf* tmp, void* dst, size_t bytes, void** out) {
+  if (is_device_ptr(dst)) {
+    *out = dst;
+    return CPM_OK;
+  }
+  if (int st = buf_reserve(c, tmp, bytes)) return st;
+  *out = tmp->ptr;
+  return CPM_OK;
+}
+
+int copy_out(Ctx* c, void* dst, const void* dev, size_t bytes) {
+  if (dst == dev) return CPM_OK;
+  return cuda_check(c, cudaMemcpyAsync(dst, dev, bytes, cudaMemcpyDeviceToHost, c->stream),
+                    "copy out");
+}
+
+Geometry geometry(const Ctx* c) {
+  Geometry g;
+  for (int d = 0; d < 3; ++d) g.L[d] = c->p.box[d];
+  g.vol = c->p.box[0] * c->p.box[1] * c->p.box[2];
+  g.g = c->p.g_ewald;
+  g.rc = c->p.rcut_real;
+  g.slab = c->p.slab;
+  return g;
+}
+
+// Half-space reciprocal vectors with |K| <= Kc (Eq. 13, Eq. 20): h > 0, or h = 0 and
+// k > 0, or h = k = 0 and l > 0; weights W = 2 (4 pi / V) exp(-K^2 / 4 g^2) / K^2,
+// sorted by decreasing weight.
+void kvector_table(const cpm_params& p, std::vector<int>& hkl, std::vector<double>& w) {
+  const double lx = p.box[0], ly = p.box[1], lz = p.box[2];
+  const double vol = lx * ly * lz;
+  const double kc = 2.0 * p.g_ewald * sqrt(log(1.0 / p.kspace_eps));
+  const int hmax = (int)floor(kc * lx / (2.0 * kPi));
+  const int kmax = (int)floor(kc * ly / (2.0 * kPi));
+  const int lmax = (int)floor(kc * lz / (2.0 * kPi));
+  const double kc2 = kc * kc;
+  hkl.clear();
+  w.clear();
+  for (int h = 0; h <= hmax; ++h)
+    for (int k = -kmax; k <= kmax; ++k)
+      for (int l = -lmax; l <= lmax; ++l) {
+        if (!(h > 0 || (h == 0 && k > 0) || (h == 0 && k == 0 && l > 0))) continue;
+        const double kx = 2.0 * kPi * h / lx, ky = 2.0 * kPi * k / ly, kz = 2.0 * kPi * l / lz;
+        const double k2 = kx * kx + ky * ky + kz * kz;
+        if (k2 > kc2) continue;
+        hkl.push_back(h);
+        hkl.push_back(k);
+        hkl.push_back(l);
+        w.push_back(2.0 * (4.0 * kPi / vol) * exp(-k2 / (4.0 * p.g_ewald * p.g_ewald)) / k2);
+      }
+  // heaviest weights first: the k-space accumulation handles the large terms first and
+  // in higher precision (see the GEMM kernels)
+  std::vector<size_t> order(w.size());
+  for (size_t t = 0; t < order.size(); ++t) order[t] = t;
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return w[a] > w[b]; });
+  std::vector<int> hkl2(hkl.size());
+  std::vector<double> w2(w.size());
+  for (size_t t = 0; t < order.size(); ++t) {
+    w2[t] = w[order[t]];
+    for (int d = 0; d < 3; ++d) hkl2[3 * t + d] = hkl[3 * order[t] + d];
+  }
+  hkl.swap(hkl2);
+  w.swap(w2);
+}
+
+void free_build(Ctx* c) {
+  Buf* all[] = {&c->xyz, &c->alpha, &c->sfix, &c->hkl, &c->sqw, &c->flush, &c->Ahead, &c->A,
+                &c->E, &c->diag,
+                &c->nbr_off, &c->nbr_idx, &c->prow, &c->d};
+  for (Buf* b : all) buf_free(c, b);
+  c->built = false;
+}
+
+__global__ void k_inverse_tail(double* diag, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) diag[n + i] = 1.0 / diag[i];
+}
+
+__global__ void k_fill(double* v, int64_t len, double x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = x;
+}
+
+__global__ void k_scale(double* v, int64_t len, double s) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x)
+    v[i] *= s;
+}
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+}  // namespace cpm
+
+using namespace cpm;
+
+struct cpm_ctx : public cpm::Ctx {};
+
+extern "C" {
+
+void cpm_default_params(cpm_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->g_ewald = 0.3;
+  p->rcut_real = 12.0;
+  p->kspace_eps = 1e-8;
+  p->slab = 1;
+  p->precision = CPM_PREC_FP32;
+  p->precond = CPM_PRECOND_DC;
+  p->g_dc = 0.083;
+  p->rcut_dc = 8.0;
+  p->p_gap = 1;
+}
+
+int cpm_create(cpm_ctx** out, const cpm_params* p) {
+  if (!out || !p) return CPM_EINVAL;
+  *out = nullptr;
+  if (!(p->box[0] > 0 && p->box[1] > 0 && p->box[2] > 0) || !(p->g_ewald > 0) ||
+      !(p->rcut_real > 0) || !(p->kspace_eps > 0 && p->kspace_eps < 1))
+    return CPM_EINVAL;
+  if (p->precision != CPM_PREC_FP64 && p->precision != CPM_PREC_FP32 &&
+      p->precision != CPM_PREC_BF16X6)
+    return CPM_EINVAL;
+  if (p->precond < CPM_PRECOND_NONE || p->precond > CPM_PRECOND_DC) return CPM_EINVAL;
+  if ((p->alloc == nullptr) != (p->free == nullptr)) return CPM_EINVAL;
+  cpm_ctx* c = new (std::nothrow) cpm_ctx();
+  if (!c) return CPM_ENOMEM;
+  c->p = *p;
+  c->stream = (cudaStream_t)p->stream;
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return CPM_ECUDA;
+  }
+  *out = c;
+  return CPM_OK;
+}
+
+int cpm_destroy(cpm_ctx* c) {
+  if (!c) return CPM_EINVAL;
+  cudaStreamSynchronize(c->stream);
+  free_build(c);
+  Buf* ws[] = {&c->ws_solve, &c->ws_in0, &c->ws_in1, &c->ws_in2, &c->ws_out0, &c->ws_out1,
+               &c->ws_pot};
+  for (Buf* b : ws) buf_free(c, b);
+  delete c;
+  return CPM_OK;
+}
+
+const char* cpm_last_error(const cpm_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
+  if (!c) return CPM_EINVAL;
+  if (n < 1 || !xyz || !alpha) return set_err(c, CPM_EINVAL, "cpm_build_E: n >= 1 and arrays required");
+  if (c->p.precision == CPM_PREC_BF16X6)
+    return set_err(c, CPM_EINVAL, "BF16X6 build is not available in this library build");
+  free_build(c);
+  cudaStream_t s = c->stream;
+  const bool f64 = c->fp64();
+  int st;
+  c->n = n;
+  c->npad = (int)round_up(n, 128);
+  c->ldE = round_up(n, 128);
+  c->vol = c->p.box[0] * c->p.box[1] * c->p.box[2];
+  std::vector<int> hkl;
+  std::vector<double> w;
+  kvector_table(c->p, hkl, w);
+  c->m = (int)w.size();
+  c->mpad = (int)round_up(std::max(c->m, 1), 64);
+  hkl.resize(3 * (size_t)c->mpad, 0);
+  std::vector<double> sqw(c->mpad, 0.0);
+  for (int k = 0; k < c->m; ++k) sqw[k] = sqrt(w[k]);
+  // Accumulation schedule of the float k-space GEMM.  k-step s covers 16 operand
+  // columns: block s / 8 holds 64 k-vectors as [cos | sin], so its steps 0-3 and 4-7
+  // carry the same weights.  Leading blocks whose steps carry more than 2e-3 of weight
+  // are summed exactly in FP64; later float partials are flushed into FP64 once a chunk
+  // has gathered about 1e-3 of weight or 32 steps.
+  const int nk = 2 * c->mpad / 16;
+  std::vector<uint32_t> fmask((nk + 31) / 32, 0u);
+  {
+    std::vector<double> ws(nk, 0.0);
+    for (int st = 0; st < nk; ++st) {
+      const int k0 = 64 * (st / 8) + 16 * (st % 4);
+      for (int t = 0; t < 16; ++t)
+        if (k0 + t < c->m) ws[st] += w[k0 + t];
+    }
+    int heavy = 0;
+    while (heavy < nk && ws[heavy] > 2e-3) ++heavy;
+    heavy = std::min(nk, (heavy + 7) / 8 * 8);
+    c->heavy_steps = heavy;
+    // head of the b^sol contraction kept in FP64: the heavy blocks, at least 256 and at
+    // most 1024 k-vectors
+    c->kh = f64 ? 0 : std::min(c->mpad, std::max(256, std::min(1024, heavy / 8 * 64)));
+    double cw = 0.0;
+    int len = 0;
+    for (int st = heavy; st < nk; ++st) {
+      cw += ws[st];
+      ++len;
+      if (cw >= 1e-3 || len >= 32 || st == nk - 1) {
+        fmask[st >> 5] |= 1u << (st & 31);
+        cw = 0.0;
+        len = 0;
+      }
+    }
+  }
+
+  const size_t a_bytes = (size_t)c->npad * 2 * c->mpad * c->esz();
+  const size_t e_bytes = (size_t)n * c->ldE * c->esz();
+  if ((st = buf_alloc(c, &c->xyz, (size_t)n * 3 * sizeof(double))) ||
+      (st = buf_alloc(c, &c->alpha, (size_t)n * sizeof(double))) ||
+      (st = buf_alloc(c, &c->sfix, (size_t)c->npad * 3 * sizeof(uint32_t))) ||
+      (st = buf_alloc(c, &c->hkl, hkl.size() * sizeof(int))) ||
+      (st = buf_alloc(c, &c->sqw, sqw.size() * sizeof(double))) ||
+      (st = buf_alloc(c, &c->flush, fmask.size() * sizeof(uint32_t))) ||
+      (st = buf_alloc(c, &c->Ahead, (size_t)c->npad * 2 * std::max(c->kh, 1) * sizeof(double))) ||
+      (st = buf_alloc(c, &c->A, a_bytes)) || (st = buf_alloc(c, &c->E, e_bytes)) ||
+      (st = buf_alloc(c, &c->diag, 2 * (size_t)n * sizeof(double))) ||
+      (st = buf_alloc(c, &c->d, (size_t)n * sizeof(double)))) {
+    free_build(c);
+    return st;
+  }
+  auto fail = [&](int code) {
+    free_build(c);
+    return code;
+  };
+  const cudaMemcpyKind h2d = cudaMemcpyHostToDevice;
+  const cudaMemcpyKind any = cudaMemcpyDefault;
+  if ((st = cuda_check(c, cudaMemcpyAsync(c->xyz.ptr, xyz, (size_t)n * 3 * sizeof(double), any, s), "xyz")) ||
+      (st = cuda_check(c, cudaMemcpyAsync(c->alpha.ptr, alpha, (size_t)n * sizeof(double), any, s), "alpha")) ||
+      (st = cuda_check(c, cudaMemcpyAsync(c->hkl.ptr, hkl.data(), hkl.size() * sizeof(int), h2d, s), "hkl")) ||
+      (st = cuda_check(c, cudaMemcpyAsync(c->sqw.ptr, sqw.data(), sqw.size() * sizeof(double), h2d, s), "sqw")) ||
+      (st = cuda_check(c, cudaMemcpyAsync(c->flush.ptr, fmask.data(), fmask.size() * sizeof(uint32_t), h2d, s), "flush")) ||
+      (st = cuda_check(c, cudaMemsetAsync(c->E.ptr, 0, e_bytes, s), "E memset")) ||
+      (st = cuda_check(c, cudaStreamSynchronize(s), "build upload")))
+    return fail(st);
+
+  cudaEvent_t ev[6];
+  for (auto& e : ev) cudaEventCreate(&e);
+  const Geometry geo = geometry(c);
+  cudaEventRecord(ev[0], s);
+  launch_fixed_point_coords((const double*)c->xyz.ptr, n, c->npad, c->p.box,
+                            (uint32_t*)c->sfix.ptr, s);
+  launch_structure_operand(f64, (const double*)c->xyz.ptr, (const uint32_t*)c->sfix.ptr,
+                           c->npad, n, (const int*)c->hkl.ptr, (const double*)c->sqw.ptr,
+                           c->mpad, c->p.box, c->A.ptr, s);
+  if (c->kh > 0)
+    launch_structure_operand_head((const double*)c->xyz.ptr, c->npad, n, (const int*)c->hkl.ptr,
+                                  (const double*)c->sqw.ptr, c->kh, c->p.box,
+                                  (double*)c->Ahead.ptr, s);
+  cudaEventRecord(ev[1], s);
+  st = launch_ek_simt(f64, c->A.ptr, c->npad, c->mpad, (const double*)c->xyz.ptr,
+                      (const double*)c->alpha.ptr, n, geo, c->E.ptr, c->ldE, c->heavy_steps,
+                      (const uint32_t*)c->flush.ptr, s);
+  if (st) {
+    for (auto& e : ev) cudaEventDestroy(e);
+    return fail(cuda_check(c, cudaGetLastError(), "k-space GEMM launch") ? CPM_ECUDA : st);
+  }
+  cudaEventRecord(ev[2], s);
+  launch_mirror_lower(f64, c->E.ptr, n, c->ldE, s);
+  launch_extract_diag(f64, c->E.ptr, n, c->ldE, (double*)c->diag.ptr, s);
+  (k_inverse_tail<<<(n + 255) / 256, 256, 0, s>>>((double*)c->diag.ptr, n), note_launch());
+  if ((st = cuda_check(c, cudaGetLastError(), "E build")) ||
+      (st = cuda_check(c, cudaStreamSynchronize(s), "E build sync"))) {
+    for (auto& e : ev) cudaEventDestroy(e);
+    return fail(st);
+  }
+  c->built = true;  // E is usable from here on (the solves below need it)
+
+  cudaEventRecord(ev[3], s);
+  if (c->p.precond == CPM_PRECOND_DC) {
+    if ((st = build_dc_preconditioner(c))) {
+      for (auto& e : ev) cudaEventDestroy(e);
+      return fail(st);
+    }
+  }
+  cudaEventRecord(ev[4], s);
+  // d' from E_n d' = 1 (Eq. S9), then d = d' / (1^T d') (Eq. S8)
+  {
+    double* ones = (double*)c->d.ptr;
+    (k_fill<<<64, 256, 0, s>>>(ones, n, 1.0), note_launch());
+    Buf dp;
+    if ((st = buf_alloc(c, &dp, (size_t)n * sizeof(double)))) {
+      for (auto& e : ev) cudaEventDestroy(e);
+      return fail(st);
+    }
+    int it = 0;
+    double rr = 0;
+    SolveArgs a{1, ones, 1.0, (double*)dp.ptr, false, 1e-10, 20000, &it, &rr};
+    const double saved_gap = c->pgap;
+    c->pgap = 0.0;
+    st = pcg_solve(c, a);
+    c->pgap = saved_gap;
+    c->d_iters = it;
+    double csum = 0.0;
+    if (!st) st = device_sum(c, (const double*)dp.ptr, n, &csum);
+    if (!st) {
+      c->c_ele = csum;
+      st = cuda_check(c, cudaMemcpyAsync(c->d.ptr, dp.ptr, (size_t)n * sizeof(double),
+                                         cudaMemcpyDeviceToDevice, s), "d copy");
+      (k_scale<<<64, 256, 0, s>>>((double*)c->d.ptr, n, 1.0 / csum), note_launch());
+    }
+    if (!st) st = cuda_check(c, cudaStreamSynchronize(s), "d sync");
+    buf_free(c, &dp);
+    if (st) {
+      for (auto& e : ev) cudaEventDestroy(e);
+      return fail(st);
+    }
+  }
+  cudaEventRecord(ev[5], s);
+  if (c->p.precond == CPM_PRECOND_DC && c->p.p_gap) {
+    if ((st = apply_p_gap(c))) {
+      for (auto& e : ev) cudaEventDestroy(e);
+      return fail(st);
+    }
+  }
+  cudaEventSynchronize(ev[5]);
+  cudaEventElapsedTime(&c->t_phase_ms, ev[0], ev[1]);
+  cudaEventElapsedTime(&c->t_kspace_ms, ev[1], ev[2]);
+  cudaEventElapsedTime(&c->t_precond_ms, ev[3], ev[4]);
+  cudaEventElapsedTime(&c->t_dsolve_ms, ev[4], ev[5]);
+  for (auto& e : ev) cudaEventDestroy(e);
+  return cuda_check(c, cudaStreamSynchronize(s), "build end");
+}
+
+int cpm_potential(cpm_ctx* c, int frames, int n_ion, const double* ion_xyz,
+                  const double* ion_q, const double* chi, double* b_out, double* qsol_out) {
+  if (!c) return CPM_EINVAL;
+  if (!c->built) return set_err(c, CPM_ENOTBUILT, "cpm_potential before cpm_build_E");
+  if (frames < 1 || n_ion < 0 || !chi || !b_out || (n_ion > 0 && (!ion_xyz || !ion_q)))
+    return set_err(c, CPM_EINVAL, "cpm_potential: bad arguments");
+  const int n = c->n;
+  cudaStream_t s = c->stream;
+  const bool f64 = c->fp64();
+  const double *dx = nullptr, *dq = nullptr, *dchi = nullptr;
+  static const double zero = 0.0;
+  int st;
+  if (n_ion > 0) {
+    if ((st = stage_in(c, &c->ws_in0, ion_xyz, (size_t)frames * n_ion * 3 * sizeof(double),
+                       (const void**)&dx)) ||
+        (st = stage_in(c, &c->ws_in1, ion_q, (size_t)frames * n_ion * sizeof(double),
+                       (const void**)&dq)))
+      return st;
+  } else {
+    dx = dq = &zero;  // never read
+  }
+  if ((st = stage_in(c, &c->ws_in2, chi, (size_t)n * sizeof(double), (const void**)&dchi)))
+    return st;
+  double *db = nullptr, *dqs = nullptr;
+  if ((st = stage_out(c, &c->ws_out0, b_out, (size_t)frames * n * sizeof(double), (void**)&db)))
+    return st;
+  if (qsol_out && (st = stage_out(c, &c->ws_out1, qsol_out, (size_t)frames * sizeof(double),
+                                  (void**)&dqs)))
+    return st;
+  // scratch: v [frames][2 mpad] (storage type) | v_head [frames][2 kh] | b^sol_k [frames][n]
+  const size_t vbytes = ((size_t)frames * 2 * c->mpad * c->esz() + 255) & ~size_t(255);
+  const size_t hbytes = ((size_t)frames * 2 * std::max(c->kh, 1) * sizeof(double) + 255) & ~size_t(255);
+  if ((st = buf_reserve(c, &c->ws_pot, vbytes + hbytes + (size_t)frames * n * sizeof(double))))
+    return st;
+  void* v = c->ws_pot.ptr;
+  double* vh = (double*)((char*)c->ws_pot.ptr + vbytes);
+  double* bk = (double*)((char*)c->ws_pot.ptr + vbytes + hbytes);
+  if (n_ion > 0) {
+    launch_ion_structure_factor(f64, dx, dq, frames, n_ion, (const int*)c->hkl.ptr,
+                                (const double*)c->sqw.ptr, c->mpad, c->kh, c->p.box, v, vh, s);
+  } else if ((st = cuda_check(c, cudaMemsetAsync(v, 0, vbytes + hbytes, s), "v zero"))) {
+    return st;
+  }
+  launch_bsol_kspace(f64, c->A.ptr, (const double*)c->Ahead.ptr, n, c->mpad, c->kh, v, vh,
+                     frames, bk, s);
+  launch_bsol_real_and_finish(f64, (const double*)c->xyz.ptr, (const double*)c->alpha.ptr, n,
+                              dx, dq, frames, n_ion, geometry(c), dchi, bk, db, dqs, s);
+  if ((st = cuda_check(c, cudaGetLastError(), "potential kernels"))) return st;
+  if (qsol_out && n_ion == 0 &&
+      (st = cuda_check(c, cudaMemsetAsync(dqs, 0, frames * sizeof(double), s), "qsol zero")))
+    return st;
+  if ((st = copy_out(c, b_out, db, (size_t)frames * n * sizeof(double)))) return st;
+  if (qsol_out && (st = copy_out(c, qsol_out, dqs, (size_t)frames * sizeof(double)))) return st;
+  return cuda_check(c, cudaStreamSynchronize(s), "potential sync");
+}
+
+int cpm_solve(cpm_ctx* c, int nrhs, const double* b, double* q_inout, int use_guess,
+              double tol, int maxit, int* iters_out, double* relres_out) {
+  if (!c) return CPM_EINVAL;
+  if (!c->built) return set_err(c, CPM_ENOTBUILT, "cpm_solve before cpm_build_E");
+  if (nrhs < 1 || !b || !q_inout || !(tol > 0) || maxit < 1)
+    return set_err(c, CPM_EINVAL, "cpm_solve: bad arguments");
+  const int n = c->n;
+  const size_t bytes = (size_t)nrhs * n * sizeof(double);
+  const double* db = nullptr;
+  double* dq = nullptr;
+  int st;
+  if ((st = stage_in(c, &c->ws_in0, b, bytes, (const void**)&db))) return st;
+  const bool q_dev = is_device_ptr(q_inout);
+  if (q_dev) {
+    dq = q_inout;
+  } else {
+    if ((st = buf_reserve(c, &c->ws_out0, bytes))) return st;
+    dq = (double*)c->ws_out0.ptr;
+    if (use_guess && (st = cuda_check(c, cudaMemcpyAsync(dq, q_inout, bytes,
+                                                         cudaMemcpyHostToDevice, c->stream),
+                                      "guess in")))
+      return st;
+  }
+  std::vector<int> it(nrhs);
+  std::vector<double> rr(nrhs);
+  SolveArgs a{nrhs, db, 1.0 / kKe, dq, use_guess != 0, tol, maxit, it.data(), rr.data()};
+  const int solve_st = pcg_solve(c, a);
+  if (solve_st != CPM_OK && solve_st != CPM_ENOCONV) return solve_st;
+  if (!q_dev && (st = copy_out(c, q_inout, dq, bytes))) return st;
+  if ((st = cuda_check(c, cudaStreamSynchronize(c->stream), "solve sync"))) return st;
+  if (iters_out) memcpy(iters_out, it.data(), nrhs * sizeof(int));
+  if (relres_out) memcpy(relres_out, rr.data(), nrhs * sizeof(double));
+  return solve_st;
+}
+
+int cpm_neutralize(cpm_ctx* c, int nrhs, double* q_inout, const double* qsol) {
+  if (!c) return CPM_EINVAL;
+  if (!c->built) return set_err(c, CPM_ENOTBUILT, "cpm_neutralize before cpm_build_E");
+  if (nrhs < 1 || !q_inout) return set_err(c, CPM_EINVAL, "cpm_neutralize: bad arguments");
+  const int n = c->n;
+  const size_t bytes = (size_t)nrhs * n * sizeof(double);
+  int st;
+  double* dq = nullptr;
+  const double* dqs = nullptr;
+  const bool q_dev = is_device_ptr(q_inout);
+  if (q_dev) {
+    dq = q_inout;
+  } else {
+    if ((st = buf_reserve(c, &c->ws_out0, bytes))) return st;
+    dq = (double*)c->ws_out0.ptr;
+    if ((st = cuda_check(c, cudaMemcpyAsync(dq, q_inout, bytes, cudaMemcpyHostToDevice,
+                                            c->stream), "q in")))
+      return st;
+  }
+  if (qsol && (st = stage_in(c, &c->ws_in1, qsol, nrhs * sizeof(double), (const void**)&dqs)))
+    return st;
+  launch_neutralize(dq, nrhs, n, (const double*)c->d.ptr, dqs, c->stream);
+  if ((st = cuda_check(c, cudaGetLastError(), "neutralize"))) return st;
+  if (!q_dev && (st = copy_out(c, q_inout, dq, bytes))) return st;
+  return cuda_check(c, cudaStreamSynchronize(c->stream), "neutralize sync");
+}
+
+int cpm_get_E(cpm_ctx* c, int form, double* out, int64_t ld) {
+  if (!c) return CPM_EINVAL;
+  if (!c->built) return set_err(c, CPM_ENOTBUILT, "cpm_get_E before cpm_build_E");
+  if (!out || ld < c->n || (form != CPM_E_STORED && form != CPM_E_PAPER))
+    return set_err(c, CPM_EINVAL, "cpm_get_E: bad arguments");
+  const size_t bytes = (size_t)c->n * ld * sizeof(double);
+  double* d = nullptr;
+  int st;
+  if ((st = stage_out(c, &c->ws_out0, out, bytes, (void**)&d))) return st;
+  launch_get_E(c->fp64(), c->E.ptr, c->n, c->ldE, (const double*)c->xyz.ptr, geometry(c),
+               form == CPM_E_PAPER, d, ld, c->stream);
+  if ((st = cuda_check(c, cudaGetLastError(), "get_E"))) return st;
+  if ((st = copy_out(c, out, d, bytes))) return st;
+  return cuda_check(c, cudaStreamSynchronize(c->stream), "get_E sync");
+}
+
+int cpm_get_d(cpm_ctx* c, double* d_out) {
+  if (!c) return CPM_EINVAL;
+  if (!c->built) return set_err(c, CPM_ENOTBUILT, "cpm_get_d before cpm_build_E");
+  if (!d_out) return set_err(c, CPM_EINVAL, "cpm_get_d: null output");
+  int st = cuda_check(c, cudaMemcpyAsync(d_out, c->d.ptr, (size_t)c->n * sizeof(double),
+                                         cudaMemcpyDefault, c->stream), "get_d");
+  if (st) return st;
+  return cuda_check(c, cudaStreamSynchronize(c->stream), "get_d sync");
+}
+
+int cpm_get_info(cpm_ctx* c, cpm_info_t* out) {
+  if (!c || !out) return CPM_EINVAL;
+  memset(out, 0, sizeof(*out));
+  out->n = c->n;
+  out->m = c->m;
+  out->nnz_p = c->nnz;
+  out->p_gap = c->pgap;
+  out->c_ele = c->c_ele;
+  out->t_kspace_ms = c->t_kspace_ms;
+  out->t_phase_ms = c->t_phase_ms;
+  out->t_precond_ms = c->t_precond_ms;
+  out->t_dsolve_ms = c->t_dsolve_ms;
+  out->d_iters = c->d_iters;
+  out->launches = launch_count();
+  return CPM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,151 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/cpm.h"
+
+namespace cpm {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kKe = 14.399645478;  // V A / e
+
+struct Status {
+  int code = CPM_OK;
+  std::string msg;
+};
+
+// Device buffer owned by a context (allocated through the context's allocator).
+struct Buf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+struct Geometry {
+  double L[3];
+  double vol;
+  double g;
+  double rc;
+  int slab;
+};
+
+struct Ctx {
+  cpm_params p;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::string err;
+
+  bool built = false;
+  int n = 0;        // electrode atoms
+  int npad = 0;     // rows of A (multiple of 128), zero beyond n
+  int m = 0;        // k-vectors
+  int mpad = 0;     // k-vectors padded to a multiple of 64 (zero weight)
+  int64_t ldE = 0;  // leading dimension of E (elements)
+  double vol = 0;
+
+  // geometry on device
+  Buf xyz;      // double [n*3]
+  Buf alpha;    // double [n]
+  Buf sfix;     // uint32 [npad*3]: fractional coordinates in 2^-32 fixed point
+  Buf hkl;      // int32 [mpad*3]
+  Buf sqw;      // double [mpad]  sqrt(W_K), zero in the padding
+  Buf flush;    // uint32 [(2*mpad/16 + 31)/32]: k-steps after which float partials flush
+  int heavy_steps = 0;  // leading k-steps accumulated exactly in FP64
+  int kh = 0;           // head k-vectors with an FP64 operand copy (float storage only)
+  Buf Ahead;            // double [npad][2*kh], same column layout as A
+  Buf A;        // float/double [npad][2*mpad]
+  Buf E;        // float/double [n][ldE]
+  Buf diag;     // double [2n]: diag(E_n), then its reciprocal
+
+  // PCG-DC preconditioner (row form: z_j = sum_tau P[j,tau] r_tau)
+  Buf nbr_off;  // int64 [n+1]
+  Buf nbr_idx;  // int32 [nnz]
+  Buf prow;     // double [nnz]  (P - p_gap on the pattern when p_gap is on)
+  int64_t nnz = 0;
+  double pgap = 0;
+
+  Buf d;        // double [n] neutralising vector
+  double c_ele = 0;
+  int d_iters = 0;
+
+  // scratch (grown on demand, never shrunk)
+  std::vector<Buf*> scratch;
+  Buf ws_solve, ws_in0, ws_in1, ws_in2, ws_out0, ws_out1, ws_pot;
+
+  float t_kspace_ms = 0, t_phase_ms = 0, t_precond_ms = 0, t_dsolve_ms = 0;
+
+  bool fp64() const { return p.precision == CPM_PREC_FP64; }
+  size_t esz() const { return fp64() ? 8 : 4; }
+};
+
+// ---- kernel launch count (every launch site calls note_launch) ---------------------
+void note_launch();
+long long launch_count();
+
+// ---- allocation (ctx.cu) -----------------------------------------------------------
+int buf_alloc(Ctx* c, Buf* b, size_t bytes);
+void buf_free(Ctx* c, Buf* b);
+int buf_reserve(Ctx* c, Buf* b, size_t bytes);  // grow-only
+int set_err(Ctx* c, int code, const std::string& msg);
+int cuda_check(Ctx* c, cudaError_t e, const char* what);
+
+// ---- kernels (launchers) -----------------------------------------------------------
+// kspace.cu
+void launch_fixed_point_coords(const double* xyz, int n, int npad, const double L[3],
+                               uint32_t* sfix, cudaStream_t s);
+void launch_structure_operand(bool fp64, const double* xyz, const uint32_t* sfix, int npad,
+                              int n, const int* hkl, const double* sqw, int mpad,
+                              const double L[3], void* A, cudaStream_t s);
+void launch_structure_operand_head(const double* xyz, int npad, int n, const int* hkl,
+                                   const double* sqw, int kh, const double L[3], double* Ahead,
+                                   cudaStream_t s);
+int launch_ek_simt(bool fp64, const void* A, int npad, int mpad, const double* xyz,
+                   const double* alpha, int n, const Geometry& geo, void* E, int64_t ldE,
+                   int heavy_steps, const uint32_t* flush_mask, cudaStream_t s);
+void launch_mirror_lower(bool fp64, void* E, int n, int64_t ldE, cudaStream_t s);
+void launch_extract_diag(bool fp64, const void* E, int n, int64_t ldE, double* diag,
+                         cudaStream_t s);
+void launch_get_E(bool fp64, const void* E, int n, int64_t ldE, const double* xyz,
+                  const Geometry& geo, int paper_form, double* out, int64_t ld,
+                  cudaStream_t s);
+
+// potential.cu
+void launch_ion_structure_factor(bool fp64, const double* ion_xyz, const double* ion_q,
+                                 int frames, int n_ion, const int* hkl, const double* sqw,
+                                 int mpad, int kh, const double L[3], void* v, double* vhead,
+                                 cudaStream_t s);
+void launch_bsol_kspace(bool fp64, const void* A, const double* Ahead, int n, int mpad, int kh,
+                        const void* v, const double* vhead, int frames, double* bsol,
+                        cudaStream_t s);
+void launch_bsol_real_and_finish(bool fp64, const double* xyz, const double* alpha, int n,
+                                 const double* ion_xyz, const double* ion_q, int frames,
+                                 int n_ion, const Geometry& geo, const double* chi,
+                                 const double* bsol_k, double* b_out, double* qsol,
+                                 cudaStream_t s);
+
+// pcg.cu
+struct SolveArgs {
+  int nrhs;
+  const double* b;   // [nrhs*n]; multiplied by bscale to give e/A
+  double bscale;
+  double* x;         // [nrhs*n]
+  bool use_guess;
+  double tol;
+  int maxit;
+  int* iters;        // host [nrhs]
+  double* relres;    // host [nrhs]
+};
+int pcg_solve(Ctx* c, const SolveArgs& a);
+void launch_neutralize(double* q, int nrhs, int n, const double* d, const double* qsol,
+                       cudaStream_t s);
+
+// dc.cu
+int build_dc_preconditioner(Ctx* c);
+int apply_p_gap(Ctx* c);
+int device_sum(Ctx* c, const double* v, int64_t len, double* out);
+
+}  // namespace cpm

@@ -1,0 +1,293 @@
+// PCG-DC preconditioner (Sec. III B 2, steps 1-3; Eq. 36).
+//
+// For every electrode atom tau: its neighbours j with |r_tau - r_j| <= r_cut (minimum
+// image, tau included, sorted by index); the local matrix M_tau of Eq. 36 over them;
+// column tau of M_tau^-1, i.e. the solution of M_tau x = e_tau, by Gaussian elimination
+// with partial pivoting in FP64 shared memory (one block per atom).  The column is
+// stored as P[j, tau] for the neighbours j; a transpose pass re-files it by row so the
+// apply z_j = sum_tau P[j, tau] r_tau is a gather.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "cpm_internal.cuh"
+
+namespace cpm {
+
+namespace {
+
+constexpr int kMaxLocal = 160;  // largest neighbourhood held in shared memory
+
+__device__ __forceinline__ double min_image(double d, double L) { return d - L * rint(d / L); }
+
+__device__ __forceinline__ double dist2(const double* a, const double* b, double lx, double ly,
+                                        double lz) {
+  double dx = min_image(a[0] - b[0], lx), dy = min_image(a[1] - b[1], ly),
+         dz = min_image(a[2] - b[2], lz);
+  return dx * dx + dy * dy + dz * dz;
+}
+
+// One warp per atom: count (fill == 0) or list (fill == 1) its neighbours in index order.
+__global__ void k_neighbours(const double* __restrict__ xyz, int n, double lx, double ly,
+                             double lz, double rc2, int* __restrict__ cnt,
+                             const int64_t* __restrict__ off, int* __restrict__ idx, int fill) {
+  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (t >= n) return;
+  const double* rt = xyz + 3 * t;
+  int c = 0;
+  for (int base = 0; base < n; base += 32) {
+    const int j = base + lane;
+    bool in = false;
+    if (j < n) in = dist2(rt, xyz + 3 * j, lx, ly, lz) <= rc2;
+    const unsigned m = __ballot_sync(0xffffffffu, in);
+    if (fill && in) idx[off[t] + c + __popc(m & ((1u << lane) - 1u))] = j;
+    c += __popc(m);
+  }
+  if (!fill && lane == 0) cnt[t] = c;
+}
+
+// Column tau of M_tau^-1 (Eq. 36), written to pcol[off[tau] .. off[tau+1]).
+__global__ void __launch_bounds__(128)
+k_dc_local(const double* __restrict__ xyz, const double* __restrict__ alpha, int n,
+           double lx, double ly, double lz, double g, double rcut,
+           const int64_t* __restrict__ off, const int* __restrict__ idx,
+           double* __restrict__ pcol, int* __restrict__ status) {
+  extern __shared__ double sm[];
+  const int tau = blockIdx.x;
+  const int64_t o = off[tau];
+  const int m = (int)(off[tau + 1] - o);
+  const int w = m + 1;  // augmented row width
+  double* M = sm;                  // [m][m + 1]
+  double* pos = sm + m * w;        // [m][3]
+  __shared__ int s_piv;
+  __shared__ double s_val;
+  for (int a = threadIdx.x; a < m; a += blockDim.x) {
+    const int j = idx[o + a];
+    pos[3 * a] = xyz[3 * j];
+    pos[3 * a + 1] = xyz[3 * j + 1];
+    pos[3 * a + 2] = xyz[3 * j + 2];
+  }
+  __syncthreads();
+  const double erfc_rc = erfc(g * rcut);
+  const double rc2 = rcut * rcut;
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int a = e / m, b = e % m;
+    double v;
+    if (a == b) {
+      const double al = alpha[idx[o + a]];
+      v = isinf(al) ? 0.0 : 0.7978845608028654 * al;  // sqrt(2/pi) alpha_i
+    } else {
+      const double r2 = dist2(pos + 3 * a, pos + 3 * b, lx, ly, lz);
+      if (r2 < rc2) {
+        const double r = sqrt(r2);
+        v = (erfc(g * r) - erfc_rc) / r;
+      } else {
+        v = 0.0;
+      }
+    }
+    M[a * w + b] = v;
+  }
+  for (int a = threadIdx.x; a < m; a += blockDim.x) M[a * w + m] = idx[o + a] == tau ? 1.0 : 0.0;
+  __syncthreads();
+  // Gaussian elimination with partial pivoting on [M | e_tau]
+  for (int k = 0; k < m; ++k) {
+    if (threadIdx.x < 32) {
+      double best = -1.0;
+      int bi = k;
+      for (int a = k + threadIdx.x; a < m; a += 32) {
+        const double v = fabs(M[a * w + k]);
+        if (v > best) {
+          best = v;
+          bi = a;
+        }
+      }
+      for (int s = 16; s; s >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, s);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, s);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      if (threadIdx.x == 0) {
+        s_piv = bi;
+        s_val = best;
+      }
+    }
+    __syncthreads();
+    if (!(s_val > 0.0)) {
+      if (threadIdx.x == 0) atomicExch(status, 1);
+      return;  // singular local matrix (whole block leaves together)
+    }
+    const int pv = s_piv;
+    if (pv != k)
+      for (int b = threadIdx.x; b < w; b += blockDim.x) {
+        const double t = M[k * w + b];
+        M[k * w + b] = M[pv * w + b];
+        M[pv * w + b] = t;
+      }
+    __syncthreads();
+    const double inv = 1.0 / M[k * w + k];
+    const int rows = m - k - 1, cols = w - k - 1;
+    for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
+      const int a = k + 1 + e / cols, b = k + 1 + e % cols;
+      M[a * w + b] -= M[a * w + k] * inv * M[k * w + b];
+    }
+    __syncthreads();
+  }
+  // back substitution (single warp; m is small)
+  if (threadIdx.x < 32) {
+    for (int k = m - 1; k >= 0; --k) {
+      double s = 0.0;
+      for (int b = k + 1 + threadIdx.x; b < m; b += 32) s += M[k * w + b] * M[b * w + m];
+      for (int o2 = 16; o2; o2 >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o2);
+      if (threadIdx.x == 0) M[k * w + m] = (M[k * w + m] - s) / M[k * w + k];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < m; a += blockDim.x) pcol[o + a] = M[a * w + m];
+}
+
+// prow[off[j] + position of tau in j's list] = pcol[off[tau] + a] - shift, j = idx[off[tau] + a]
+__global__ void k_dc_transpose(int n, const int64_t* __restrict__ off, const int* __restrict__ idx,
+                               const double* __restrict__ pcol, double shift,
+                               double* __restrict__ prow) {
+  const int tau = blockIdx.x;
+  for (int64_t e = off[tau] + threadIdx.x; e < off[tau + 1]; e += blockDim.x) {
+    const int j = idx[e];
+    int64_t lo = off[j], hi = off[j + 1];
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (idx[mid] < tau) lo = mid + 1;
+      else hi = mid;
+    }
+    if (lo < off[j + 1] && idx[lo] == tau) prow[lo] = pcol[e] - shift;
+  }
+}
+
+__global__ void k_sum_blocks(const double* __restrict__ v, int64_t len, double* __restrict__ part) {
+  __shared__ double sm[32];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x)
+    s += v[i];
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0;
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+  }
+}
+
+}  // namespace
+
+// Sum of a device vector, deterministic (fixed block partials, host sum in order).
+int device_sum(Ctx* c, const double* v, int64_t len, double* out) {
+  const int blocks = 256;
+  Buf tmp;
+  if (int rc = buf_alloc(c, &tmp, blocks * sizeof(double))) return rc;
+  (k_sum_blocks<<<blocks, 256, 0, c->stream>>>(v, len, (double*)tmp.ptr), note_launch());
+  std::vector<double> h(blocks);
+  int rc = cuda_check(c, cudaMemcpyAsync(h.data(), tmp.ptr, blocks * sizeof(double),
+                                         cudaMemcpyDeviceToHost, c->stream), "sum copy");
+  if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "sum sync");
+  buf_free(c, &tmp);
+  if (rc) return rc;
+  double s = 0.0;
+  for (double x : h) s += x;
+  *out = s;
+  return CPM_OK;
+}
+
+// Builds the neighbour pattern and the row form of P (without p_gap).
+int build_dc_preconditioner(Ctx* c) {
+  const int n = c->n;
+  const double* L = c->p.box;
+  const double rc = c->p.rcut_dc;
+  if (!(rc > 0.0) || 2.0 * rc >= std::min(L[0], std::min(L[1], L[2])))
+    return set_err(c, CPM_EINVAL, "rcut_dc must be positive and below half of every box edge");
+  cudaStream_t s = c->stream;
+  Buf cnt;
+  if (int rc2 = buf_alloc(c, &cnt, (size_t)n * sizeof(int))) return rc2;
+  const int blocks = (n * 32 + 255) / 256;
+  (k_neighbours<<<blocks, 256, 0, s>>>((const double*)c->xyz.ptr, n, L[0], L[1], L[2], rc * rc,
+                                      (int*)cnt.ptr, nullptr, nullptr, 0), note_launch());
+  std::vector<int> hc(n);
+  int st = cuda_check(c, cudaMemcpyAsync(hc.data(), cnt.ptr, n * sizeof(int),
+                                         cudaMemcpyDeviceToHost, s), "dc counts");
+  if (!st) st = cuda_check(c, cudaStreamSynchronize(s), "dc counts sync");
+  buf_free(c, &cnt);
+  if (st) return st;
+  std::vector<int64_t> off(n + 1, 0);
+  int mx = 0;
+  for (int i = 0; i < n; ++i) {
+    off[i + 1] = off[i] + hc[i];
+    mx = std::max(mx, hc[i]);
+  }
+  if (mx > kMaxLocal)
+    return set_err(c, CPM_EINVAL, "PCG-DC neighbourhood larger than 160 atoms; lower rcut_dc");
+  c->nnz = off[n];
+  if ((st = buf_alloc(c, &c->nbr_off, (n + 1) * sizeof(int64_t)))) return st;
+  if ((st = buf_alloc(c, &c->nbr_idx, c->nnz * sizeof(int)))) return st;
+  if ((st = buf_alloc(c, &c->prow, c->nnz * sizeof(double)))) return st;
+  Buf pcol, status;
+  if ((st = buf_alloc(c, &pcol, c->nnz * sizeof(double)))) return st;
+  if ((st = buf_alloc(c, &status, sizeof(int)))) {
+    buf_free(c, &pcol);
+    return st;
+  }
+  st = cuda_check(c, cudaMemcpyAsync(c->nbr_off.ptr, off.data(), (n + 1) * sizeof(int64_t),
+                                     cudaMemcpyHostToDevice, s), "dc offsets");
+  if (!st) st = cuda_check(c, cudaMemsetAsync(status.ptr, 0, sizeof(int), s), "dc status");
+  if (!st) {
+    (k_neighbours<<<blocks, 256, 0, s>>>((const double*)c->xyz.ptr, n, L[0], L[1], L[2], rc * rc,
+                                        nullptr, (const int64_t*)c->nbr_off.ptr,
+                                        (int*)c->nbr_idx.ptr, 1), note_launch());
+    const size_t smem = ((size_t)mx * (mx + 1) + 3 * (size_t)mx) * sizeof(double);
+    st = cuda_check(c, cudaFuncSetAttribute(k_dc_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem), "dc smem");
+    if (!st) {
+      (k_dc_local<<<n, 128, smem, s>>>((const double*)c->xyz.ptr, (const double*)c->alpha.ptr, n,
+                                      L[0], L[1], L[2], c->p.g_dc, rc,
+                                      (const int64_t*)c->nbr_off.ptr, (const int*)c->nbr_idx.ptr,
+                                      (double*)pcol.ptr, (int*)status.ptr), note_launch());
+      (k_dc_transpose<<<n, 128, 0, s>>>(n, (const int64_t*)c->nbr_off.ptr,
+                                       (const int*)c->nbr_idx.ptr, (const double*)pcol.ptr, 0.0,
+                                       (double*)c->prow.ptr), note_launch());
+      st = cuda_check(c, cudaGetLastError(), "dc kernels");
+    }
+  }
+  int hs = 0;
+  if (!st) st = cuda_check(c, cudaMemcpyAsync(&hs, status.ptr, sizeof(int),
+                                              cudaMemcpyDeviceToHost, s), "dc status copy");
+  if (!st) st = cuda_check(c, cudaStreamSynchronize(s), "dc sync");
+  buf_free(c, &pcol);
+  buf_free(c, &status);
+  if (st) return st;
+  if (hs) return set_err(c, CPM_EINVAL, "a PCG-DC local matrix is singular");
+  return CPM_OK;
+}
+
+__global__ void k_shift(double* __restrict__ v, int64_t len, double s) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x)
+    v[i] -= s;
+}
+
+// p_gap of Eq. 37 from C^ele = 1^T E^-1 1; stored as prow -= p_gap on the pattern.
+int apply_p_gap(Ctx* c) {
+  double sum_p = 0.0;
+  if (int st = device_sum(c, (const double*)c->prow.ptr, c->nnz, &sum_p)) return st;
+  const double n2 = (double)c->n * (double)c->n;
+  const double nzero = n2 - (double)c->nnz;
+  c->pgap = nzero > 0 ? (c->c_ele - sum_p) / nzero : 0.0;
+  if (c->pgap != 0.0) (k_shift<<<256, 256, 0, c->stream>>>((double*)c->prow.ptr, c->nnz, c->pgap), note_launch());
+  return cuda_check(c, cudaGetLastError(), "p_gap");
+}
+
+}  // namespace cpm

@@ -1,0 +1,555 @@
+// Preconditioned conjugate gradient on E_n q = b (Sec. III B 2) and the neutralisation
+// step of Eq. 35.
+//
+// Every scalar lives on the device: per-block partial sums are reduced by one warp per
+// right-hand side, so the host only polls a small status array every few iterations.
+// Vectors are FP64; the matvec streams E in its storage type (FP32: float products with
+// FP64 row sums).  The PCG-DC preconditioner is not symmetric, so beta is the flexible
+// Polak-Ribiere form r_{k+1}^T (z_{k+1} - z_k) / (r_k^T z_k).
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "cpm_internal.cuh"
+
+namespace cpm {
+
+namespace {
+
+struct ColState {
+  double rz;      // r^T z of the current iterate
+  double bb;      // b^T b
+  double alpha;
+  double beta;
+  double relres;  // ||r|| / ||b||
+  int iter;
+  int done;       // 0 running, 1 converged, 2 breakdown
+};
+
+constexpr int kThreads = 256;
+constexpr int kMvWarps = 8;
+
+__device__ __forceinline__ double warp_sum(double x) {
+  for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Block-wide sum of NV values per thread; result valid in thread 0.
+template <int NV>
+__device__ void block_sum(double (&v)[NV], double* sm /* [32*NV] */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t < NV; ++t) v[t] = warp_sum(v[t]);
+  if (lane == 0)
+#pragma unroll
+    for (int t = 0; t < NV; ++t) sm[warp * NV + t] = v[t];
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+      double x = lane < nw ? sm[lane * NV + t] : 0.0;
+      v[t] = warp_sum(x);
+    }
+  }
+  __syncthreads();
+}
+
+// q[r] = E p[r] for NR columns starting at column c0, one warp per row, plus the
+// per-block partial of p^T q.  FP32 E: float4 loads of E and of the float copy of p,
+// float products summed 32 at a time into FP64.
+template <typename T, int NR>
+__global__ void __launch_bounds__(kThreads)
+k_matvec(const T* __restrict__ E, int64_t ldE, int n, const T* __restrict__ pv,
+         const double* __restrict__ p64, int64_t ldv, int c0, int nrhs, double* __restrict__ q,
+         double* __restrict__ pq_part) {
+  __shared__ double sm[32 * NR];
+  constexpr int VEC = 16 / sizeof(T);
+  const int lane = threadIdx.x & 31;
+  const int wid = blockIdx.x * kMvWarps + (threadIdx.x >> 5);
+  const int nwarps = gridDim.x * kMvWarps;
+  double pq[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) pq[r] = 0.0;
+  for (int row = wid; row < n; row += nwarps) {
+    const T* e = E + (int64_t)row * ldE;
+    double acc[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] = 0.0;
+    for (int64_t c = lane * VEC; c < ldE; c += 8 * 32 * VEC) {
+      T part[NR];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) part[r] = T(0);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t cc = c + (int64_t)u * 32 * VEC;
+        if (cc < ldE) {
+          T ev[VEC];
+          *reinterpret_cast<float4*>(ev) = __ldg(reinterpret_cast<const float4*>(e + cc));
+#pragma unroll
+          for (int r = 0; r < NR; ++r) {
+            if (c0 + r < nrhs) {
+              T pvv[VEC];
+              *reinterpret_cast<float4*>(pvv) =
+                  *reinterpret_cast<const float4*>(pv + (int64_t)(c0 + r) * ldv + cc);
+#pragma unroll
+              for (int w = 0; w < VEC; ++w) part[r] = fma(ev[w], pvv[w], part[r]);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < NR; ++r) acc[r] += (double)part[r];
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      double s = warp_sum(acc[r]);
+      if (lane == 0 && c0 + r < nrhs) {
+        q[(int64_t)(c0 + r) * ldv + row] = s;
+        pq[r] += s * p64[(int64_t)(c0 + r) * ldv + row];
+      }
+    }
+  }
+  block_sum<NR>(pq, sm);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+      if (c0 + r < nrhs) pq_part[(int64_t)blockIdx.x * nrhs + c0 + r] = pq[r];
+}
+
+// alpha = r^T z / p^T q for every running column.
+__global__ void k_alpha(const double* __restrict__ pq_part, int nparts, int nrhs,
+                        ColState* __restrict__ st) {
+  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (col >= nrhs) return;
+  double s = 0.0;
+  for (int b = lane; b < nparts; b += 32) s += pq_part[(int64_t)b * nrhs + col];
+  s = warp_sum(s);
+  if (lane == 0) {
+    ColState& c = st[col];
+    if (c.done) {
+      c.alpha = 0.0;
+    } else if (!(s > 0.0) || !isfinite(s)) {
+      c.alpha = 0.0;
+      c.done = 2;
+    } else {
+      c.alpha = c.rz / s;
+    }
+  }
+}
+
+// x += alpha p, r -= alpha q; Jacobi/none also form z; partial dots
+// [r^T z_new, r^T z_old, r^T r, sum r].
+template <int PRE>
+__global__ void __launch_bounds__(kThreads)
+k_update(int n, int64_t ldv, int nrhs, const ColState* __restrict__ st,
+         double* __restrict__ x, double* __restrict__ r, double* __restrict__ z,
+         const double* __restrict__ p, const double* __restrict__ q,
+         const double* __restrict__ inv_diag, double* __restrict__ dots) {
+  __shared__ double sm[32 * 4];
+  for (int col = 0; col < nrhs; ++col) {
+    const double a = st[col].alpha;
+    const bool active = st[col].done == 0;
+    double v[4] = {0, 0, 0, 0};
+    const int64_t o = (int64_t)col * ldv;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      double ri = r[o + i];
+      if (active) {
+        x[o + i] += a * p[o + i];
+        ri -= a * q[o + i];
+        r[o + i] = ri;
+      }
+      if (PRE != CPM_PRECOND_DC) {
+        const double zo = z[o + i];
+        const double zn = PRE == CPM_PRECOND_JACOBI ? ri * inv_diag[i] : ri;
+        if (active) z[o + i] = zn;
+        v[0] += ri * zn;
+        v[1] += ri * zo;
+      }
+      v[2] += ri * ri;
+      v[3] += ri;
+    }
+    block_sum<4>(v, sm);
+    if (threadIdx.x == 0)
+      for (int t = 0; t < 4; ++t) dots[((int64_t)blockIdx.x * nrhs + col) * 4 + t] = v[t];
+  }
+}
+
+// z = P r (+ p_gap * sum r on the complement of the pattern) for PCG-DC, one thread per
+// row; partial dots [r^T z_new, r^T z_old] into slots 0, 1.
+__global__ void __launch_bounds__(kThreads)
+k_dc_apply(int n, int64_t ldv, int nrhs, const ColState* __restrict__ st,
+           const int64_t* __restrict__ off, const int* __restrict__ idx,
+           const double* __restrict__ prow, double pgap, const double* __restrict__ r,
+           double* __restrict__ z, const double* __restrict__ rsum_part, int nparts,
+           double* __restrict__ dots, int first) {
+  __shared__ double sm[32 * 2];
+  __shared__ double s_rsum;
+  for (int col = 0; col < nrhs; ++col) {
+    const bool active = first || st[col].done == 0;
+    if (threadIdx.x < 32) {
+      double s = 0.0;
+      if (pgap != 0.0)
+        for (int b = threadIdx.x; b < nparts; b += 32) s += rsum_part[((int64_t)b * nrhs + col) * 4 + 3];
+      s = warp_sum(s);
+      if (threadIdx.x == 0) s_rsum = s;
+    }
+    __syncthreads();
+    const double gsum = pgap * s_rsum;
+    const int64_t o = (int64_t)col * ldv;
+    double v[2] = {0, 0};
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+      double acc = gsum;
+      for (int64_t e = off[j]; e < off[j + 1]; ++e) acc += prow[e] * r[o + idx[e]];
+      const double rj = r[o + j];
+      const double zo = z[o + j];
+      if (active) z[o + j] = acc;
+      v[0] += rj * acc;
+      v[1] += rj * zo;
+    }
+    block_sum<2>(v, sm);
+    if (threadIdx.x == 0) {
+      dots[((int64_t)blockIdx.x * nrhs + col) * 4 + 0] = v[0];
+      dots[((int64_t)blockIdx.x * nrhs + col) * 4 + 1] = v[1];
+    }
+  }
+}
+
+// Reduce the dots, test convergence, form beta, and advance the column state.
+__global__ void k_beta(const double* __restrict__ dots, int nparts, int nrhs, double tol,
+                       int flexible, const ColState* __restrict__ cur,
+                       ColState* __restrict__ next) {
+  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (col >= nrhs) return;
+  double s[3] = {0, 0, 0};
+  for (int b = lane; b < nparts; b += 32)
+    for (int t = 0; t < 3; ++t) s[t] += dots[((int64_t)b * nrhs + col) * 4 + t];
+  for (int t = 0; t < 3; ++t) s[t] = warp_sum(s[t]);
+  if (lane == 0) {
+    ColState c = cur[col];
+    if (c.done == 0) {
+      c.iter += 1;
+      c.relres = sqrt(s[2] / c.bb);
+      if (!isfinite(c.relres)) {
+        c.done = 2;
+      } else if (c.relres <= tol) {
+        c.done = 1;
+      } else {
+        c.beta = flexible ? (s[0] - s[1]) / c.rz : s[0] / c.rz;
+        c.rz = s[0];
+        if (!isfinite(c.beta) || !(c.rz != 0.0)) c.done = 2;
+      }
+    }
+    next[col] = c;
+  }
+}
+
+// p = z + beta p (and the storage-type copy used by the matvec).
+template <typename T>
+__global__ void k_p_update(int n, int64_t ldv, int nrhs, const ColState* __restrict__ st,
+                           const double* __restrict__ z, double* __restrict__ p,
+                           T* __restrict__ pv, int first) {
+  for (int col = 0; col < nrhs; ++col) {
+    if (!first && st[col].done) continue;
+    const double bta = first ? 0.0 : st[col].beta;
+    const int64_t o = (int64_t)col * ldv;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      // the direction is rounded once to the matvec's type and used as rounded
+      // everywhere, so x and r stay consistent (r = b - E x up to the matvec error)
+      const T v = (T)(z[o + i] + bta * p[o + i]);
+      p[o + i] = (double)v;
+      pv[o + i] = v;
+    }
+  }
+}
+
+// part 0: p = fl(x); part 1: p = fl(x - fl(x)) (the low half of a float guess).
+template <typename T>
+__global__ void k_guess_part(int n, int64_t ldv, int nrhs, const double* __restrict__ x,
+                             double* __restrict__ p, T* __restrict__ pv, int low) {
+  for (int col = 0; col < nrhs; ++col) {
+    const int64_t o = (int64_t)col * ldv;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      const double xi = x[o + i];
+      const T hi = (T)xi;
+      const T v = low ? (T)(xi - (double)hi) : hi;
+      p[o + i] = (double)v;
+      pv[o + i] = v;
+    }
+  }
+}
+
+// r = b - E x0 (q [+ q2] holds E x0 when use_guess) or r = b; x = x0 or 0.
+__global__ void k_init_r(int n, int64_t ldv, int nrhs, const double* __restrict__ b,
+                         double bscale, const double* __restrict__ q,
+                         const double* __restrict__ q2, int use_guess, double* __restrict__ r,
+                         double* __restrict__ x, double* __restrict__ z,
+                         const double* __restrict__ inv_diag, int pre,
+                         double* __restrict__ dots) {
+  __shared__ double sm[32 * 4];
+  for (int col = 0; col < nrhs; ++col) {
+    const int64_t o = (int64_t)col * ldv;
+    double v[4] = {0, 0, 0, 0};  // r^T z, b^T b, r^T r, sum r
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      const double bi = b[(int64_t)col * n + i] * bscale;
+      const double ri = use_guess ? bi - q[o + i] - (q2 ? q2[o + i] : 0.0) : bi;
+      r[o + i] = ri;
+      if (!use_guess) x[o + i] = 0.0;
+      double zi = 0.0;
+      if (pre != CPM_PRECOND_DC) {
+        zi = pre == CPM_PRECOND_JACOBI ? ri * inv_diag[i] : ri;
+        z[o + i] = zi;
+      } else {
+        z[o + i] = 0.0;
+      }
+      v[0] += ri * zi;
+      v[1] += bi * bi;
+      v[2] += ri * ri;
+      v[3] += ri;
+    }
+    block_sum<4>(v, sm);
+    if (threadIdx.x == 0)
+      for (int t = 0; t < 4; ++t) dots[((int64_t)blockIdx.x * nrhs + col) * 4 + t] = v[t];
+  }
+}
+
+__global__ void k_init_state(const double* __restrict__ dots, int nparts, int nrhs,
+                             double tol, int pre, ColState* __restrict__ st) {
+  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (col >= nrhs) return;
+  double s[3] = {0, 0, 0};
+  for (int b = lane; b < nparts; b += 32)
+    for (int t = 0; t < 3; ++t) s[t] += dots[((int64_t)b * nrhs + col) * 4 + t];
+  for (int t = 0; t < 3; ++t) s[t] = warp_sum(s[t]);
+  (void)pre;
+  if (lane == 0) {
+    ColState c;
+    c.rz = s[0];
+    c.bb = s[1];
+    c.alpha = 0.0;
+    c.beta = 0.0;
+    c.iter = 0;
+    c.done = 0;
+    if (c.bb == 0.0) {
+      c.relres = 0.0;
+      c.done = 1;
+    } else {
+      c.relres = sqrt(s[2] / c.bb);
+      if (c.relres <= tol) c.done = 1;
+    }
+    st[col] = c;
+  }
+}
+
+// The DC apply in the init phase writes r^T z into slot 0 of its own dots array.
+__global__ void k_init_rz_dc(const double* __restrict__ dots_dc, int nparts, int nrhs,
+                             ColState* __restrict__ st) {
+  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (col >= nrhs) return;
+  double s = 0.0;
+  for (int b = lane; b < nparts; b += 32) s += dots_dc[((int64_t)b * nrhs + col) * 4];
+  s = warp_sum(s);
+  if (lane == 0) st[col].rz = s;
+}
+
+__global__ void k_neutralize(double* __restrict__ q, int n, const double* __restrict__ d,
+                             const double* __restrict__ qsol) {
+  __shared__ double sm[32];
+  __shared__ double s_tot;
+  const int col = blockIdx.x;
+  double* qc = q + (int64_t)col * n;
+  double v[1] = {0.0};
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v[0] += qc[i];
+  block_sum<1>(v, sm);
+  if (threadIdx.x == 0) s_tot = v[0] + (qsol ? qsol[col] : 0.0);
+  __syncthreads();
+  const double t = s_tot;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) qc[i] -= t * d[i];
+}
+
+int sm_count(int device) {
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+  return v > 0 ? v : 1;
+}
+
+template <typename T>
+void launch_matvec(const Ctx* c, const void* pv, const double* p64, int64_t ldv, int nrhs,
+                   double* q, double* pq_part, int gm) {
+  for (int c0 = 0; c0 < nrhs; c0 += 4) {
+    int left = nrhs - c0;
+    if (left >= 4)
+      (k_matvec<T, 4><<<gm, kThreads, 0, c->stream>>>((const T*)c->E.ptr, c->ldE, c->n,
+                                                     (const T*)pv, p64, ldv, c0, nrhs, q,
+                                                     pq_part), note_launch());
+    else if (left >= 2)
+      (k_matvec<T, 2><<<gm, kThreads, 0, c->stream>>>((const T*)c->E.ptr, c->ldE, c->n,
+                                                     (const T*)pv, p64, ldv, c0, nrhs, q,
+                                                     pq_part), note_launch());
+    else
+      (k_matvec<T, 1><<<gm, kThreads, 0, c->stream>>>((const T*)c->E.ptr, c->ldE, c->n,
+                                                     (const T*)pv, p64, ldv, c0, nrhs, q,
+                                                     pq_part), note_launch());
+    if (left == 3) {  // the NR=2 launch above covered two of three columns
+      (k_matvec<T, 1><<<gm, kThreads, 0, c->stream>>>((const T*)c->E.ptr, c->ldE, c->n,
+                                                     (const T*)pv, p64, ldv, c0 + 2, nrhs, q,
+                                                     pq_part), note_launch());
+    }
+  }
+}
+
+}  // namespace
+
+int pcg_solve(Ctx* c, const SolveArgs& a) {
+  const int n = c->n, nrhs = a.nrhs;
+  const int64_t ldv = c->ldE;
+  const int sms = sm_count(c->device);
+  const int ge = std::max(1, std::min((n + kThreads - 1) / kThreads, 2 * sms));
+  const int gm = std::max(1, std::min((n + kMvWarps - 1) / kMvWarps, 2 * sms));
+  const int pre = c->p.precond;
+  const bool f64 = c->fp64();
+  const size_t vbytes = (size_t)nrhs * ldv * sizeof(double);
+  // layout: x r z p q (double) | pv (storage type) | pq_part | dots | dots_dc | states
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) & ~size_t(255);
+    return o;
+  };
+  const size_t ox = take(vbytes), orr = take(vbytes), oz = take(vbytes), op = take(vbytes),
+               oq = take(vbytes), opv = take((size_t)nrhs * ldv * c->esz()),
+               opq = take((size_t)gm * nrhs * sizeof(double)),
+               odt = take((size_t)ge * nrhs * 4 * sizeof(double)),
+               odc = take((size_t)ge * nrhs * 4 * sizeof(double)),
+               ost = take(2 * (size_t)nrhs * sizeof(ColState));
+  int rc = buf_reserve(c, &c->ws_solve, off);
+  if (rc) return rc;
+  char* base = (char*)c->ws_solve.ptr;
+  double* x = (double*)(base + ox);
+  double* r = (double*)(base + orr);
+  double* z = (double*)(base + oz);
+  double* p = (double*)(base + op);
+  double* q = (double*)(base + oq);
+  void* pv = base + opv;
+  double* pq_part = (double*)(base + opq);
+  double* dots = (double*)(base + odt);
+  double* dots_dc = (double*)(base + odc);
+  ColState* st = (ColState*)(base + ost);
+  cudaStream_t s = c->stream;
+  // zero the padded vectors so the matvec can read whole padded rows
+  if (cuda_check(c, cudaMemsetAsync(base, 0, ost, s), "memset")) return CPM_ECUDA;
+
+  const double* inv_diag = c->diag.ptr ? (const double*)c->diag.ptr + n : nullptr;
+  // initial guess; in float storage E x0 = E hi + E lo with hi = fl(x0), lo = fl(x0 - hi),
+  // so the first residual is that of x0 itself, not of its rounding
+  const double* q2 = nullptr;
+  if (a.use_guess) {
+    for (int col = 0; col < nrhs; ++col)
+      if (cuda_check(c, cudaMemcpyAsync(x + (int64_t)col * ldv, a.x + (int64_t)col * n,
+                                        n * sizeof(double), cudaMemcpyDeviceToDevice, s),
+                     "copy guess"))
+        return CPM_ECUDA;
+    if (f64) {
+      (k_guess_part<double><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, x, p, (double*)pv, 0), note_launch());
+      launch_matvec<double>(c, pv, p, ldv, nrhs, q, pq_part, gm);
+    } else {
+      (k_guess_part<float><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, x, p, (float*)pv, 1), note_launch());
+      launch_matvec<float>(c, pv, p, ldv, nrhs, z, pq_part, gm);
+      (k_guess_part<float><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, x, p, (float*)pv, 0), note_launch());
+      launch_matvec<float>(c, pv, p, ldv, nrhs, q, pq_part, gm);
+      q2 = z;
+    }
+  }
+  (k_init_r<<<ge, kThreads, 0, s>>>(n, ldv, nrhs, a.b, a.bscale, q, q2, a.use_guess ? 1 : 0, r, x, z,
+                                   inv_diag, pre, dots), note_launch());
+  const int wb = 8;  // warps per block for the per-column reductions
+  const int gcol = (nrhs + wb - 1) / wb;
+  (k_init_state<<<gcol, wb * 32, 0, s>>>(dots, ge, nrhs, a.tol, pre, st), note_launch());
+  if (pre == CPM_PRECOND_DC) {
+    (k_dc_apply<<<ge, kThreads, 0, s>>>(n, ldv, nrhs, st, (const int64_t*)c->nbr_off.ptr,
+                                       (const int*)c->nbr_idx.ptr, (const double*)c->prow.ptr,
+                                       c->pgap, r, z, dots, ge, dots_dc, 1), note_launch());
+    (k_init_rz_dc<<<gcol, wb * 32, 0, s>>>(dots_dc, ge, nrhs, st), note_launch());
+  }
+  if (f64) (k_p_update<double><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, st, z, p, (double*)pv, 1), note_launch());
+  else (k_p_update<float><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, st, z, p, (float*)pv, 1), note_launch());
+  if (cuda_check(c, cudaGetLastError(), "pcg init")) return CPM_ECUDA;
+
+  std::vector<ColState> host(nrhs);
+  const int flexible = pre == CPM_PRECOND_DC ? 1 : 0;
+  int it = 0;
+  bool all_done = false;
+  const int check_every = 4;
+  // state at the start of iteration `it` lives in st[(it & 1) * nrhs]
+  auto poll = [&](int k) -> int {
+    ColState* cur = st + (size_t)(k & 1) * nrhs;
+    if (cuda_check(c, cudaMemcpyAsync(host.data(), cur, nrhs * sizeof(ColState),
+                                      cudaMemcpyDeviceToHost, s),
+                   "poll"))
+      return CPM_ECUDA;
+    if (cuda_check(c, cudaStreamSynchronize(s), "poll sync")) return CPM_ECUDA;
+    all_done = true;
+    for (auto& h : host) all_done &= h.done != 0;
+    return CPM_OK;
+  };
+  if ((rc = poll(0))) return rc;
+  while (!all_done && it < a.maxit) {
+    ColState* cur = st + (size_t)(it & 1) * nrhs;
+    ColState* nxt = st + (size_t)((it + 1) & 1) * nrhs;
+    if (f64) launch_matvec<double>(c, pv, p, ldv, nrhs, q, pq_part, gm);
+    else launch_matvec<float>(c, pv, p, ldv, nrhs, q, pq_part, gm);
+    (k_alpha<<<gcol, wb * 32, 0, s>>>(pq_part, gm, nrhs, cur), note_launch());
+    if (pre == CPM_PRECOND_DC) {
+      (k_update<CPM_PRECOND_DC><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, cur, x, r, z, p, q,
+                                                       inv_diag, dots), note_launch());
+      (k_dc_apply<<<ge, kThreads, 0, s>>>(n, ldv, nrhs, cur, (const int64_t*)c->nbr_off.ptr,
+                                         (const int*)c->nbr_idx.ptr,
+                                         (const double*)c->prow.ptr, c->pgap, r, z, dots, ge,
+                                         dots, 0), note_launch());
+    } else if (pre == CPM_PRECOND_JACOBI) {
+      (k_update<CPM_PRECOND_JACOBI><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, cur, x, r, z, p, q,
+                                                           inv_diag, dots), note_launch());
+    } else {
+      (k_update<CPM_PRECOND_NONE><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, cur, x, r, z, p, q,
+                                                         inv_diag, dots), note_launch());
+    }
+    (k_beta<<<gcol, wb * 32, 0, s>>>(dots, ge, nrhs, a.tol, flexible, cur, nxt), note_launch());
+    if (f64) (k_p_update<double><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, nxt, z, p, (double*)pv, 0), note_launch());
+    else (k_p_update<float><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, nxt, z, p, (float*)pv, 0), note_launch());
+    ++it;
+    if (it % check_every == 0 || it == a.maxit) {
+      if (cuda_check(c, cudaGetLastError(), "pcg iteration")) return CPM_ECUDA;
+      if ((rc = poll(it))) return rc;
+    }
+  }
+  if (!all_done && (rc = poll(it))) return rc;
+  for (int col = 0; col < nrhs; ++col)
+    if (cuda_check(c, cudaMemcpyAsync(a.x + (int64_t)col * n, x + (int64_t)col * ldv,
+                                      n * sizeof(double), cudaMemcpyDeviceToDevice, s),
+                   "copy x"))
+      return CPM_ECUDA;
+  if (cuda_check(c, cudaStreamSynchronize(s), "pcg end")) return CPM_ECUDA;
+  int status = CPM_OK;
+  for (int col = 0; col < nrhs; ++col) {
+    if (a.iters) a.iters[col] = host[col].iter;
+    if (a.relres) a.relres[col] = host[col].relres;
+    if (host[col].done == 2) status = CPM_EBREAKDOWN;
+    else if (host[col].done == 0 && status == CPM_OK) status = CPM_ENOCONV;
+  }
+  if (status == CPM_EBREAKDOWN) return set_err(c, status, "PCG breakdown (p^T E p <= 0 or non-finite)");
+  if (status == CPM_ENOCONV) return set_err(c, status, "PCG reached maxit before tol");
+  return CPM_OK;
+}
+
+void launch_neutralize(double* q, int nrhs, int n, const double* d, const double* qsol,
+                       cudaStream_t s) {
+  (k_neutralize<<<nrhs, 1024, 0, s>>>(q, n, d, qsol), note_launch());
+}
+
+}  // namespace cpm
