@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cells", type=int, default=40, help="cells per sheet edge (40: 12,800 atoms)")
     ap.add_argument("--ions", type=int, default=2000)
-    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--precision", choices=["bf16x6", "fp32", "fp64"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -232,7 +232,8 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream(device=dev)
     el, ions, q = make_workload(args.cells, args.ions, rank)
     n = el.n
-    prec = cpm.CPM_PREC_FP32 if args.precision == "fp32" else cpm.CPM_PREC_FP64
+    prec = {"fp32": cpm.CPM_PREC_FP32, "fp64": cpm.CPM_PREC_FP64,
+            "bf16x6": cpm.CPM_PREC_BF16X6}[args.precision]
     ctx = cpm.Context(el.box, stream=stream.cuda_stream, precision=prec,
                       precond=cpm.CPM_PRECOND_DC)
     t = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
@@ -240,7 +241,7 @@ def run_ours(args, rank, world, local_rank):
     b = torch.empty((1, n), dtype=torch.float64, device=dev)
     qs = torch.empty(1, dtype=torch.float64, device=dev)
     qq = torch.zeros((1, n), dtype=torch.float64, device=dev)
-    info = {"kspace_ms": [], "iters": [], "relres": []}
+    info = {"kspace_ms": [], "tc_ms": [], "iters": [], "relres": []}
 
     def step():
         ctx.cpm_build_E(xyz, alpha)
@@ -249,6 +250,8 @@ def run_ours(args, rank, world, local_rank):
         ctx.cpm_neutralize(qq, qs)
         inf = ctx.cpm_get_info()
         info["kspace_ms"].append(inf["t_kspace_ms"])
+        info["tc_ms"].append(inf["t_tc_ms"])
+        info["head_cols"] = inf["head_cols"]
         info["iters"].append(int(it[0]))
         info["relres"].append(float(rel[0]))
 
@@ -256,7 +259,7 @@ def run_ours(args, rank, world, local_rank):
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize()
-        info = {k: [] for k in info}
+        info = {k: ([] if isinstance(v, list) else v) for k, v in info.items()}
         if world > 1:
             dist.barrier()
         launches0 = ctx.cpm_get_info()["launches"]
@@ -319,7 +322,23 @@ def run_ours(args, rank, world, local_rank):
     flops = 2.0 * (n * (n + 1) / 2) * (2 * m)
     clk = clocks.summary()
     sm_mhz = clk.get("sm_max_mhz") or 2070.0
-    if args.precision == "fp32":
+    esz = 8 if args.precision == "fp64" else 4
+    if args.precision == "bf16x6":
+        # the tensor-core tail kernel alone: lower-triangle tiles, tail columns, six BF16
+        # products per term (the FP64 head kernel is timed apart in e_build_s)
+        tc_ms = statistics.mean(info["tc_ms"])
+        nt = (n + 127) // 128
+        tail_cols = 2 * ((m + 63) // 64 * 64) - info["head_cols"]
+        tc_flops = 6 * 2.0 * (nt * (nt + 1) / 2) * 128 * 128 * tail_cols
+        algo_flops = 6 * 2.0 * (n * (n + 1) / 2) * tail_cols
+        bf16_peak = peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"])
+        roof = {"bound": "tensor", "achieved": algo_flops / (tc_ms * 1e-3) / 1e12,
+                "peak": bf16_peak, "unit": "TFLOP/s",
+                "kernel": "k_ek_tc (tcgen05 BF16x6 k-space GEMM, TMEM two-sum accumulation)",
+                "peak_source": f"{src} bf16_tflops (burst)",
+                "issued_tflops": tc_flops / (tc_ms * 1e-3) / 1e12,
+                "fp32_accurate_tflops": algo_flops / 6 / (tc_ms * 1e-3) / 1e12}
+    elif args.precision == "fp32":
         peak = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": flops / (kspace_ms * 1e-3) / 1e12, "peak": peak,
                 "unit": "TFLOP/s", "kernel": "k_ek_simt<float> (k-space GEMM + fused epilogue)",
@@ -337,13 +356,13 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "dtype": {"fp32": "f32", "fp64": "f64", "bf16x6": "bf16x6 (f32-accurate)"}[args.precision], "data": "synthetic",
         "config": {"workload": f"two-sheet graphene N={n}, {args.ions} ions, one frame per "
                                f"step incl. full E/P/d build",
                    "electrode_atoms": n, "ions": args.ions, "kvectors": m,
                    "l2": "working set > L2 (E %.0f MB, A %.1f GB)" % (
-                       n * n * (4 if args.precision == "fp32" else 8) / 1e6,
-                       n * 2 * m * (4 if args.precision == "fp32" else 8) / 1e9),
+                       n * n * esz / 1e6,
+                       n * 2 * m * esz / 1e9),
                    "tol": TOL, "precond": "PCG-DC (g=0.083, r_cut=8)"},
         "e_build_s": kspace_ms / 1e3,
         "solve_only": {"value": 1000.0 / solve_ms, "unit": "solves/s",

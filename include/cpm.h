@@ -165,6 +165,8 @@ typedef struct cpm_info_t {
   double t_dsolve_ms;
   int d_iters;        /* iterations of the E_n d' = 1 solve */
   int64_t launches;   /* CUDA kernels launched by the library in this process so far */
+  double t_tc_ms;     /* BF16X6 builds: device time of the tensor-core tail kernel alone */
+  int head_cols;      /* leading k-space operand columns summed in FP64 (heaviest weights) */
 } cpm_info_t;
 
 int cpm_get_info(cpm_ctx* c, cpm_info_t* out);

@@ -70,6 +70,8 @@ class cpm_info_t(ctypes.Structure):
         ("t_dsolve_ms", ctypes.c_double),
         ("d_iters", ctypes.c_int),
         ("launches", ctypes.c_int64),
+        ("t_tc_ms", ctypes.c_double),
+        ("head_cols", ctypes.c_int),
     ]
 
 

@@ -163,7 +163,8 @@ void kvector_table(const cpm_params& p, std::vector<int>& hkl, std::vector<doubl
 }
 
 void free_build(Ctx* c) {
-  Buf* all[] = {&c->xyz, &c->alpha, &c->sfix, &c->hkl, &c->sqw, &c->flush, &c->Ahead, &c->A,
+  Buf* all[] = {&c->xyz, &c->alpha, &c->sfix, &c->hkl, &c->sqw, &c->flush, &c->chunk_end,
+                &c->Ahead, &c->A,
                 &c->E, &c->diag,
                 &c->nbr_off, &c->nbr_idx, &c->prow, &c->d};
   for (Buf* b : all) buf_free(c, b);
@@ -227,6 +228,8 @@ int cpm_create(cpm_ctx** out, const cpm_params* p) {
   if (!c) return CPM_ENOMEM;
   c->p = *p;
   c->stream = (cudaStream_t)p->stream;
+  cudaEventCreate(&c->ev_tc[0]);
+  cudaEventCreate(&c->ev_tc[1]);
   if (cudaGetDevice(&c->device) != cudaSuccess) {
     cudaGetLastError();
     delete c;
@@ -240,6 +243,8 @@ int cpm_destroy(cpm_ctx* c) {
   if (!c) return CPM_EINVAL;
   cudaStreamSynchronize(c->stream);
   free_build(c);
+  cudaEventDestroy(c->ev_tc[0]);
+  cudaEventDestroy(c->ev_tc[1]);
   Buf* ws[] = {&c->ws_solve, &c->ws_in0, &c->ws_in1, &c->ws_in2, &c->ws_out0, &c->ws_out1,
                &c->ws_pot};
   for (Buf* b : ws) buf_free(c, b);
@@ -252,8 +257,6 @@ const char* cpm_last_error(const cpm_ctx* c) { return c ? c->err.c_str() : "null
 int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
   if (!c) return CPM_EINVAL;
   if (n < 1 || !xyz || !alpha) return set_err(c, CPM_EINVAL, "cpm_build_E: n >= 1 and arrays required");
-  if (c->p.precision == CPM_PREC_BF16X6)
-    return set_err(c, CPM_EINVAL, "BF16X6 build is not available in this library build");
   free_build(c);
   cudaStream_t s = c->stream;
   const bool f64 = c->fp64();
@@ -286,7 +289,7 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
     }
     int heavy = 0;
     while (heavy < nk && ws[heavy] > 2e-3) ++heavy;
-    heavy = std::min(nk, (heavy + 7) / 8 * 8);
+    heavy = std::min(std::min(nk, 128), (heavy + 7) / 8 * 8);  // at most 1024 k-vectors
     c->heavy_steps = heavy;
     // head of the b^sol contraction kept in FP64: the heavy blocks, at least 256 and at
     // most 1024 k-vectors
@@ -304,6 +307,25 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
     }
   }
 
+  // tensor-core build: accumulation chunks of 64-column K-blocks after the head, ending
+  // once a chunk has gathered 5e-4 of weight or 8 blocks
+  const bool tc = c->p.precision == CPM_PREC_BF16X6;
+  const int nkb = 2 * c->mpad / 64;
+  std::vector<uint32_t> cmask((nkb + 31) / 32, 0u);
+  {
+    double cw = 0.0;
+    int len = 0;
+    for (int b = c->heavy_steps / 4; b < nkb; ++b) {
+      for (int t = 0; t < 64; ++t) cw += (64 * (b / 2) + t < c->m) ? w[64 * (b / 2) + t] : 0.0;
+      ++len;
+      if (cw >= 5e-4 || len >= 8 || b == nkb - 1) {
+        cmask[b >> 5] |= 1u << (b & 31);
+        cw = 0.0;
+        len = 0;
+      }
+    }
+  }
+
   const size_t a_bytes = (size_t)c->npad * 2 * c->mpad * c->esz();
   const size_t e_bytes = (size_t)n * c->ldE * c->esz();
   if ((st = buf_alloc(c, &c->xyz, (size_t)n * 3 * sizeof(double))) ||
@@ -312,6 +334,7 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
       (st = buf_alloc(c, &c->hkl, hkl.size() * sizeof(int))) ||
       (st = buf_alloc(c, &c->sqw, sqw.size() * sizeof(double))) ||
       (st = buf_alloc(c, &c->flush, fmask.size() * sizeof(uint32_t))) ||
+      (st = buf_alloc(c, &c->chunk_end, cmask.size() * sizeof(uint32_t))) ||
       (st = buf_alloc(c, &c->Ahead, (size_t)c->npad * 2 * std::max(c->kh, 1) * sizeof(double))) ||
       (st = buf_alloc(c, &c->A, a_bytes)) || (st = buf_alloc(c, &c->E, e_bytes)) ||
       (st = buf_alloc(c, &c->diag, 2 * (size_t)n * sizeof(double))) ||
@@ -330,6 +353,7 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
       (st = cuda_check(c, cudaMemcpyAsync(c->hkl.ptr, hkl.data(), hkl.size() * sizeof(int), h2d, s), "hkl")) ||
       (st = cuda_check(c, cudaMemcpyAsync(c->sqw.ptr, sqw.data(), sqw.size() * sizeof(double), h2d, s), "sqw")) ||
       (st = cuda_check(c, cudaMemcpyAsync(c->flush.ptr, fmask.data(), fmask.size() * sizeof(uint32_t), h2d, s), "flush")) ||
+      (st = cuda_check(c, cudaMemcpyAsync(c->chunk_end.ptr, cmask.data(), cmask.size() * sizeof(uint32_t), h2d, s), "chunks")) ||
       (st = cuda_check(c, cudaMemsetAsync(c->E.ptr, 0, e_bytes, s), "E memset")) ||
       (st = cuda_check(c, cudaStreamSynchronize(s), "build upload")))
     return fail(st);
@@ -347,13 +371,55 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
     launch_structure_operand_head((const double*)c->xyz.ptr, c->npad, n, (const int*)c->hkl.ptr,
                                   (const double*)c->sqw.ptr, c->kh, c->p.box,
                                   (double*)c->Ahead.ptr, s);
+  Buf planes[3], ehead, errbuf;
+  auto free_tc = [&]() {
+    for (Buf& b : planes) buf_free(c, &b);
+    buf_free(c, &ehead);
+    buf_free(c, &errbuf);
+  };
+  if (tc) {
+    const size_t pbytes = (size_t)c->npad * 2 * c->mpad * 2;
+    if ((st = buf_alloc(c, &planes[0], pbytes)) || (st = buf_alloc(c, &planes[1], pbytes)) ||
+        (st = buf_alloc(c, &planes[2], pbytes)) ||
+        (st = buf_alloc(c, &ehead, (size_t)n * c->ldE * sizeof(double))) ||
+        (st = buf_alloc(c, &errbuf, sizeof(int))) ||
+        (st = cuda_check(c, cudaMemsetAsync(errbuf.ptr, 0, sizeof(int), s), "err flag"))) {
+      free_tc();
+      for (auto& e : ev) cudaEventDestroy(e);
+      return fail(st);
+    }
+    launch_split_bf16((const float*)c->A.ptr, (int64_t)c->npad * 2 * c->mpad, planes[0].ptr,
+                      planes[1].ptr, planes[2].ptr, s);
+  }
   cudaEventRecord(ev[1], s);
-  st = launch_ek_simt(f64, c->A.ptr, c->npad, c->mpad, (const double*)c->xyz.ptr,
-                      (const double*)c->alpha.ptr, n, geo, c->E.ptr, c->ldE, c->heavy_steps,
-                      (const uint32_t*)c->flush.ptr, s);
+  if (tc) {
+    // FP64 head (heaviest k-vectors) with the real-space, self and dipole terms, then the
+    // tensor-core tail, which adds the head in its epilogue
+    st = launch_ek_head_f64((const double*)c->Ahead.ptr, c->kh, 16 * c->heavy_steps,
+                            (const double*)c->xyz.ptr, (const double*)c->alpha.ptr, n, geo,
+                            (double*)ehead.ptr, c->ldE, s);
+    cudaEventRecord(c->ev_tc[0], s);
+    if (!st)
+      st = launch_ek_tc(planes[0].ptr, planes[1].ptr, planes[2].ptr, c->npad, c->mpad, n,
+                        c->heavy_steps / 4, (const uint32_t*)c->chunk_end.ptr,
+                        (const double*)ehead.ptr, c->ldE, (float*)c->E.ptr, c->ldE,
+                        (int*)errbuf.ptr, s);
+    cudaEventRecord(c->ev_tc[1], s);
+    int herr = 0;
+    if (!st) st = cuda_check(c, cudaMemcpyAsync(&herr, errbuf.ptr, sizeof(int),
+                                                cudaMemcpyDeviceToHost, s), "tc err");
+    if (!st) st = cuda_check(c, cudaStreamSynchronize(s), "tc sync");
+    if (!st && herr) st = set_err(c, CPM_ECUDA, "tensor-core k-space kernel: a pipeline wait timed out");
+    if (!st) cudaEventElapsedTime(&c->t_tc_ms, c->ev_tc[0], c->ev_tc[1]);
+    free_tc();
+  } else {
+    st = launch_ek_simt(f64, c->A.ptr, c->npad, c->mpad, (const double*)c->xyz.ptr,
+                        (const double*)c->alpha.ptr, n, geo, c->E.ptr, c->ldE, c->heavy_steps,
+                        (const uint32_t*)c->flush.ptr, s);
+  }
   if (st) {
     for (auto& e : ev) cudaEventDestroy(e);
-    return fail(cuda_check(c, cudaGetLastError(), "k-space GEMM launch") ? CPM_ECUDA : st);
+    return fail(st == CPM_ECUDA && c->err.empty() ? cuda_check(c, cudaGetLastError(), "k-space GEMM") : st);
   }
   cudaEventRecord(ev[2], s);
   launch_mirror_lower(f64, c->E.ptr, n, c->ldE, s);
@@ -578,6 +644,8 @@ int cpm_get_info(cpm_ctx* c, cpm_info_t* out) {
   out->t_phase_ms = c->t_phase_ms;
   out->t_precond_ms = c->t_precond_ms;
   out->t_dsolve_ms = c->t_dsolve_ms;
+  out->t_tc_ms = c->t_tc_ms;
+  out->head_cols = 16 * c->heavy_steps;
   out->d_iters = c->d_iters;
   out->launches = launch_count();
   return CPM_OK;

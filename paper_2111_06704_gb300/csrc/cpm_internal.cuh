@@ -57,6 +57,7 @@ struct Ctx {
   int heavy_steps = 0;  // leading k-steps accumulated exactly in FP64
   int kh = 0;           // head k-vectors with an FP64 operand copy (float storage only)
   Buf Ahead;            // double [npad][2*kh], same column layout as A
+  Buf chunk_end;        // uint32 bit per K-block of 64 columns (tensor-core build)
   Buf A;        // float/double [npad][2*mpad]
   Buf E;        // float/double [n][ldE]
   Buf diag;     // double [2n]: diag(E_n), then its reciprocal
@@ -76,7 +77,8 @@ struct Ctx {
   std::vector<Buf*> scratch;
   Buf ws_solve, ws_in0, ws_in1, ws_in2, ws_out0, ws_out1, ws_pot;
 
-  float t_kspace_ms = 0, t_phase_ms = 0, t_precond_ms = 0, t_dsolve_ms = 0;
+  float t_kspace_ms = 0, t_phase_ms = 0, t_precond_ms = 0, t_dsolve_ms = 0, t_tc_ms = 0;
+  cudaEvent_t ev_tc[2] = {nullptr, nullptr};
 
   bool fp64() const { return p.precision == CPM_PREC_FP64; }
   size_t esz() const { return fp64() ? 8 : 4; }
@@ -107,6 +109,17 @@ int launch_ek_simt(bool fp64, const void* A, int npad, int mpad, const double* x
                    const double* alpha, int n, const Geometry& geo, void* E, int64_t ldE,
                    int heavy_steps, const uint32_t* flush_mask, cudaStream_t s);
 void launch_mirror_lower(bool fp64, void* E, int n, int64_t ldE, cudaStream_t s);
+
+int launch_ek_head_f64(const double* Ahead, int kh, int ktot, const double* xyz,
+                       const double* alpha, int n, const Geometry& geo, double* Ehead,
+                       int64_t ldE, cudaStream_t s);
+
+// tc_syrk.cu
+void launch_split_bf16(const float* A, int64_t len, void* p0, void* p1, void* p2,
+                       cudaStream_t s);
+int launch_ek_tc(const void* p0, const void* p1, const void* p2, int npad, int mpad, int n,
+                 int kb_begin, const uint32_t* chunk_end, const double* head, int64_t ldh,
+                 float* E, int64_t ldE, int* err, cudaStream_t s);
 void launch_extract_diag(bool fp64, const void* E, int n, int64_t ldE, double* diag,
                          cudaStream_t s);
 void launch_get_E(bool fp64, const void* E, int n, int64_t ldE, const double* xyz,

@@ -408,6 +408,29 @@ int launch_ek_simt(bool fp64, const void* A, int npad, int mpad, const double* x
   return cudaGetLastError() == cudaSuccess ? CPM_OK : CPM_ECUDA;
 }
 
+// FP64 head of the k-space sum (the first ktot columns of the FP64 head operand, row
+// stride 2 kh) plus the real-space, self and dipole terms, lower triangle, into Ehead.
+int launch_ek_head_f64(const double* Ahead, int kh, int ktot, const double* xyz,
+                       const double* alpha, int n, const Geometry& geo, double* Ehead,
+                       int64_t ldE, cudaStream_t s) {
+  Epi ep;
+  ep.xyz = xyz;
+  ep.alpha = alpha;
+  ep.n = n;
+  for (int d = 0; d < 3; ++d) ep.L[d] = geo.L[d];
+  ep.rc = geo.rc;
+  ep.rc2 = geo.rc * geo.rc;
+  ep.g = geo.g;
+  ep.self_g = -2.0 * geo.g / sqrt(kPi);
+  ep.dip = geo.slab ? 4.0 * kPi / geo.vol : 0.0;
+  constexpr int BM = 64;
+  const int nt = (n + BM - 1) / BM;
+  const int tiles = nt * (nt + 1) / 2;
+  (k_ek_simt<double, BM, 4, false><<<tiles, 256, 0, s>>>(Ahead, 2 * (int64_t)kh, ktot, Ehead,
+                                                          ldE, ep, 0, nullptr), note_launch());
+  return cudaGetLastError() == cudaSuccess ? CPM_OK : CPM_ECUDA;
+}
+
 void launch_mirror_lower(bool fp64, void* E, int n, int64_t ldE, cudaStream_t s) {
   int nb = (n + 31) / 32;
   dim3 grid(nb, nb), block(32, 8);

@@ -58,13 +58,17 @@ __device__ void block_sum(double (&v)[NV], double* sm /* [32*NV] */) {
 }
 
 // q[r] = E p[r] for NR columns starting at column c0, one warp per row, plus the
-// per-block partial of p^T q.  FP32 E: float4 loads of E and of the float copy of p,
-// float products summed 32 at a time into FP64.
+// per-block partial of p^T q.
+// FP32 E: p is held as a float pair p = hi + lo (to ~1e-14).  Each product e * hi is
+// split exactly into its float value and rounding error (fma(e, hi, -e*hi)); values
+// and errors (plus e * lo) are summed over 8 elements in float and then in FP64, so the
+// matvec is accurate to ~1e-8 of |E||p| instead of float rounding of every product,
+// while E is still streamed once in 4-byte words.
 template <typename T, int NR>
 __global__ void __launch_bounds__(kThreads)
 k_matvec(const T* __restrict__ E, int64_t ldE, int n, const T* __restrict__ pv,
-         const double* __restrict__ p64, int64_t ldv, int c0, int nrhs, double* __restrict__ q,
-         double* __restrict__ pq_part) {
+         const T* __restrict__ plo, const double* __restrict__ p64, int64_t ldv, int c0,
+         int nrhs, double* __restrict__ q, double* __restrict__ pq_part) {
   __shared__ double sm[32 * NR];
   constexpr int VEC = 16 / sizeof(T);
   const int lane = threadIdx.x & 31;
@@ -79,29 +83,43 @@ k_matvec(const T* __restrict__ E, int64_t ldE, int n, const T* __restrict__ pv,
 #pragma unroll
     for (int r = 0; r < NR; ++r) acc[r] = 0.0;
     for (int64_t c = lane * VEC; c < ldE; c += 8 * 32 * VEC) {
-      T part[NR];
 #pragma unroll
-      for (int r = 0; r < NR; ++r) part[r] = T(0);
+      for (int u2 = 0; u2 < 4; ++u2) {
+        T part[NR], perr[NR];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int64_t cc = c + (int64_t)u * 32 * VEC;
-        if (cc < ldE) {
-          T ev[VEC];
-          *reinterpret_cast<float4*>(ev) = __ldg(reinterpret_cast<const float4*>(e + cc));
+        for (int r = 0; r < NR; ++r) part[r] = perr[r] = T(0);
 #pragma unroll
-          for (int r = 0; r < NR; ++r) {
-            if (c0 + r < nrhs) {
-              T pvv[VEC];
-              *reinterpret_cast<float4*>(pvv) =
-                  *reinterpret_cast<const float4*>(pv + (int64_t)(c0 + r) * ldv + cc);
+        for (int u = 2 * u2; u < 2 * u2 + 2; ++u) {
+          const int64_t cc = c + (int64_t)u * 32 * VEC;
+          if (cc < ldE) {
+            T ev[VEC];
+            *reinterpret_cast<float4*>(ev) = __ldg(reinterpret_cast<const float4*>(e + cc));
 #pragma unroll
-              for (int w = 0; w < VEC; ++w) part[r] = fma(ev[w], pvv[w], part[r]);
+            for (int r = 0; r < NR; ++r) {
+              if (c0 + r < nrhs) {
+                T hv[VEC];
+                const int64_t o = (int64_t)(c0 + r) * ldv + cc;
+                *reinterpret_cast<float4*>(hv) = *reinterpret_cast<const float4*>(pv + o);
+                if (plo) {
+                  T lv[VEC];
+                  *reinterpret_cast<float4*>(lv) = *reinterpret_cast<const float4*>(plo + o);
+#pragma unroll
+                  for (int w = 0; w < VEC; ++w) {
+                    const T pr = ev[w] * hv[w];
+                    perr[r] = fma(ev[w], lv[w], perr[r] + fma(ev[w], hv[w], -pr));
+                    part[r] += pr;
+                  }
+                } else {
+#pragma unroll
+                  for (int w = 0; w < VEC; ++w) part[r] = fma(ev[w], hv[w], part[r]);
+                }
+              }
             }
           }
         }
-      }
 #pragma unroll
-      for (int r = 0; r < NR; ++r) acc[r] += (double)part[r];
+        for (int r = 0; r < NR; ++r) acc[r] += (double)part[r] + (double)perr[r];
+      }
     }
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
@@ -248,37 +266,22 @@ __global__ void k_beta(const double* __restrict__ dots, int nparts, int nrhs, do
   }
 }
 
-// p = z + beta p (and the storage-type copy used by the matvec).
+// p = z + beta p, and the matvec's copy: the value itself in FP64 storage, a float
+// pair hi + lo (plo != nullptr) in float storage.
 template <typename T>
 __global__ void k_p_update(int n, int64_t ldv, int nrhs, const ColState* __restrict__ st,
                            const double* __restrict__ z, double* __restrict__ p,
-                           T* __restrict__ pv, int first) {
+                           T* __restrict__ pv, T* __restrict__ plo, int first) {
   for (int col = 0; col < nrhs; ++col) {
     if (!first && st[col].done) continue;
     const double bta = first ? 0.0 : st[col].beta;
     const int64_t o = (int64_t)col * ldv;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-      // the direction is rounded once to the matvec's type and used as rounded
-      // everywhere, so x and r stay consistent (r = b - E x up to the matvec error)
-      const T v = (T)(z[o + i] + bta * p[o + i]);
-      p[o + i] = (double)v;
-      pv[o + i] = v;
-    }
-  }
-}
-
-// part 0: p = fl(x); part 1: p = fl(x - fl(x)) (the low half of a float guess).
-template <typename T>
-__global__ void k_guess_part(int n, int64_t ldv, int nrhs, const double* __restrict__ x,
-                             double* __restrict__ p, T* __restrict__ pv, int low) {
-  for (int col = 0; col < nrhs; ++col) {
-    const int64_t o = (int64_t)col * ldv;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-      const double xi = x[o + i];
-      const T hi = (T)xi;
-      const T v = low ? (T)(xi - (double)hi) : hi;
-      p[o + i] = (double)v;
-      pv[o + i] = v;
+      const double v = z[o + i] + bta * p[o + i];
+      p[o + i] = v;
+      const T hi = (T)v;
+      pv[o + i] = hi;
+      if (plo) plo[o + i] = (T)(v - (double)hi);
     }
   }
 }
@@ -380,27 +383,25 @@ int sm_count(int device) {
 }
 
 template <typename T>
-void launch_matvec(const Ctx* c, const void* pv, const double* p64, int64_t ldv, int nrhs,
-                   double* q, double* pq_part, int gm) {
+void launch_matvec(const Ctx* c, const void* pv, const void* plo, const double* p64,
+                   int64_t ldv, int nrhs, double* q, double* pq_part, int gm) {
+  const T* E = (const T*)c->E.ptr;
+  const T* hi = (const T*)pv;
+  const T* lo = (const T*)plo;
   for (int c0 = 0; c0 < nrhs; c0 += 4) {
     int left = nrhs - c0;
     if (left >= 4)
-      (k_matvec<T, 4><<<gm, kThreads, 0, c->stream>>>((const T*)c->E.ptr, c->ldE, c->n,
-                                                     (const T*)pv, p64, ldv, c0, nrhs, q,
-                                                     pq_part), note_launch());
+      (k_matvec<T, 4><<<gm, kThreads, 0, c->stream>>>(E, c->ldE, c->n, hi, lo, p64, ldv, c0,
+                                                     nrhs, q, pq_part), note_launch());
     else if (left >= 2)
-      (k_matvec<T, 2><<<gm, kThreads, 0, c->stream>>>((const T*)c->E.ptr, c->ldE, c->n,
-                                                     (const T*)pv, p64, ldv, c0, nrhs, q,
-                                                     pq_part), note_launch());
+      (k_matvec<T, 2><<<gm, kThreads, 0, c->stream>>>(E, c->ldE, c->n, hi, lo, p64, ldv, c0,
+                                                     nrhs, q, pq_part), note_launch());
     else
-      (k_matvec<T, 1><<<gm, kThreads, 0, c->stream>>>((const T*)c->E.ptr, c->ldE, c->n,
-                                                     (const T*)pv, p64, ldv, c0, nrhs, q,
-                                                     pq_part), note_launch());
-    if (left == 3) {  // the NR=2 launch above covered two of three columns
-      (k_matvec<T, 1><<<gm, kThreads, 0, c->stream>>>((const T*)c->E.ptr, c->ldE, c->n,
-                                                     (const T*)pv, p64, ldv, c0 + 2, nrhs, q,
-                                                     pq_part), note_launch());
-    }
+      (k_matvec<T, 1><<<gm, kThreads, 0, c->stream>>>(E, c->ldE, c->n, hi, lo, p64, ldv, c0,
+                                                     nrhs, q, pq_part), note_launch());
+    if (left == 3)  // the NR=2 launch above covered two of three columns
+      (k_matvec<T, 1><<<gm, kThreads, 0, c->stream>>>(E, c->ldE, c->n, hi, lo, p64, ldv,
+                                                     c0 + 2, nrhs, q, pq_part), note_launch());
   }
 }
 
@@ -423,7 +424,7 @@ int pcg_solve(Ctx* c, const SolveArgs& a) {
     return o;
   };
   const size_t ox = take(vbytes), orr = take(vbytes), oz = take(vbytes), op = take(vbytes),
-               oq = take(vbytes), opv = take((size_t)nrhs * ldv * c->esz()),
+               oq = take(vbytes), opv = take((f64 ? 1 : 2) * (size_t)nrhs * ldv * c->esz()),
                opq = take((size_t)gm * nrhs * sizeof(double)),
                odt = take((size_t)ge * nrhs * 4 * sizeof(double)),
                odc = take((size_t)ge * nrhs * 4 * sizeof(double)),
@@ -437,6 +438,8 @@ int pcg_solve(Ctx* c, const SolveArgs& a) {
   double* p = (double*)(base + op);
   double* q = (double*)(base + oq);
   void* pv = base + opv;
+  // float storage: the low halves of the direction follow the high halves
+  float* plo = f64 ? nullptr : (float*)pv + (size_t)nrhs * ldv;
   double* pq_part = (double*)(base + opq);
   double* dots = (double*)(base + odt);
   double* dots_dc = (double*)(base + odc);
@@ -446,8 +449,7 @@ int pcg_solve(Ctx* c, const SolveArgs& a) {
   if (cuda_check(c, cudaMemsetAsync(base, 0, ost, s), "memset")) return CPM_ECUDA;
 
   const double* inv_diag = c->diag.ptr ? (const double*)c->diag.ptr + n : nullptr;
-  // initial guess; in float storage E x0 = E hi + E lo with hi = fl(x0), lo = fl(x0 - hi),
-  // so the first residual is that of x0 itself, not of its rounding
+  // initial guess: q = E x0 through the same (hi + lo) matvec
   const double* q2 = nullptr;
   if (a.use_guess) {
     for (int col = 0; col < nrhs; ++col)
@@ -456,14 +458,11 @@ int pcg_solve(Ctx* c, const SolveArgs& a) {
                      "copy guess"))
         return CPM_ECUDA;
     if (f64) {
-      (k_guess_part<double><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, x, p, (double*)pv, 0), note_launch());
-      launch_matvec<double>(c, pv, p, ldv, nrhs, q, pq_part, gm);
+      (k_p_update<double><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, st, x, p, (double*)pv, nullptr, 1), note_launch());
+      launch_matvec<double>(c, pv, nullptr, p, ldv, nrhs, q, pq_part, gm);
     } else {
-      (k_guess_part<float><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, x, p, (float*)pv, 1), note_launch());
-      launch_matvec<float>(c, pv, p, ldv, nrhs, z, pq_part, gm);
-      (k_guess_part<float><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, x, p, (float*)pv, 0), note_launch());
-      launch_matvec<float>(c, pv, p, ldv, nrhs, q, pq_part, gm);
-      q2 = z;
+      (k_p_update<float><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, st, x, p, (float*)pv, plo, 1), note_launch());
+      launch_matvec<float>(c, pv, plo, p, ldv, nrhs, q, pq_part, gm);
     }
   }
   (k_init_r<<<ge, kThreads, 0, s>>>(n, ldv, nrhs, a.b, a.bscale, q, q2, a.use_guess ? 1 : 0, r, x, z,
@@ -477,8 +476,8 @@ int pcg_solve(Ctx* c, const SolveArgs& a) {
                                        c->pgap, r, z, dots, ge, dots_dc, 1), note_launch());
     (k_init_rz_dc<<<gcol, wb * 32, 0, s>>>(dots_dc, ge, nrhs, st), note_launch());
   }
-  if (f64) (k_p_update<double><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, st, z, p, (double*)pv, 1), note_launch());
-  else (k_p_update<float><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, st, z, p, (float*)pv, 1), note_launch());
+  if (f64) (k_p_update<double><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, st, z, p, (double*)pv, nullptr, 1), note_launch());
+  else (k_p_update<float><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, st, z, p, (float*)pv, plo, 1), note_launch());
   if (cuda_check(c, cudaGetLastError(), "pcg init")) return CPM_ECUDA;
 
   std::vector<ColState> host(nrhs);
@@ -502,8 +501,8 @@ int pcg_solve(Ctx* c, const SolveArgs& a) {
   while (!all_done && it < a.maxit) {
     ColState* cur = st + (size_t)(it & 1) * nrhs;
     ColState* nxt = st + (size_t)((it + 1) & 1) * nrhs;
-    if (f64) launch_matvec<double>(c, pv, p, ldv, nrhs, q, pq_part, gm);
-    else launch_matvec<float>(c, pv, p, ldv, nrhs, q, pq_part, gm);
+    if (f64) launch_matvec<double>(c, pv, nullptr, p, ldv, nrhs, q, pq_part, gm);
+    else launch_matvec<float>(c, pv, plo, p, ldv, nrhs, q, pq_part, gm);
     (k_alpha<<<gcol, wb * 32, 0, s>>>(pq_part, gm, nrhs, cur), note_launch());
     if (pre == CPM_PRECOND_DC) {
       (k_update<CPM_PRECOND_DC><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, cur, x, r, z, p, q,
@@ -520,8 +519,8 @@ int pcg_solve(Ctx* c, const SolveArgs& a) {
                                                          inv_diag, dots), note_launch());
     }
     (k_beta<<<gcol, wb * 32, 0, s>>>(dots, ge, nrhs, a.tol, flexible, cur, nxt), note_launch());
-    if (f64) (k_p_update<double><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, nxt, z, p, (double*)pv, 0), note_launch());
-    else (k_p_update<float><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, nxt, z, p, (float*)pv, 0), note_launch());
+    if (f64) (k_p_update<double><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, nxt, z, p, (double*)pv, nullptr, 0), note_launch());
+    else (k_p_update<float><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, nxt, z, p, (float*)pv, plo, 0), note_launch());
     ++it;
     if (it % check_every == 0 || it == a.maxit) {
       if (cuda_check(c, cudaGetLastError(), "pcg iteration")) return CPM_ECUDA;

@@ -1,0 +1,436 @@
+// k-space part of E on the tcgen05 tensor cores (sm_103a): E_k = A A^T over the light
+// tail of the k-vector table, with a three-way BF16 split of each operand.
+//
+// Each FP32 operand value a = a0 + a1 + a2 (BF16 planes, a1 and a2 the successive
+// rounding remainders), and
+//   a b^T ~= a0 b0 + a0 b1 + a1 b0 + a0 b2 + a1 b1 + a2 b0      (six BF16 products),
+// which keeps ~24 bits of each product; BF16 x BF16 products are exact in the FP32
+// accumulator.  The heaviest k-vectors (the head) are summed in FP64 by the SIMT kernel
+// beforehand; this kernel adds the tail.
+//
+// Tile: 128 x 128 outputs of the lower triangle per CTA (cta_group::1, M = N = 128).
+// Warp roles: warp 0 issues TMA loads of the six 128 x 64 BF16 tiles of a K-block
+// (128-byte swizzle) into a 2-stage shared-memory ring; warp 1 issues the MMAs (one
+// thread); warps 2-5 drain the accumulator.  TMEM (512 columns): two FP32 accumulators
+// (ping-pong) and a hi/lo float pair per output.  After each accumulation chunk (one or
+// more K-blocks, schedule from the host) the epilogue adds the chunk into hi/lo with an
+// error-free two-sum, so FP32 rounding only touches chunk sums of light terms.  The final
+// drain adds the FP64 head and writes the float E tile.
+//
+// Every wait is bounded: on timeout the kernel records an error code and leaves; the
+// host reports CPM_ECUDA-class failure instead of hanging.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+#include <stdint.h>
+
+#include "cpm_internal.cuh"
+
+namespace cpm {
+
+namespace {
+
+constexpr int kTile = 128;           // output tile edge
+constexpr int kBlockK = 64;          // operand columns per K-block (128 B of BF16)
+constexpr int kStages = 2;
+constexpr int kPlaneTileBytes = kTile * kBlockK * 2;  // 16 KB
+constexpr int kStageBytes = 6 * kPlaneTileBytes;      // A0 A1 A2 (rows i) + B0 B1 B2 (rows j)
+constexpr int kThreads = 192;                         // 6 warps
+constexpr long long kWaitCycles = 20000000000ll;      // ~10 s at 2 GHz: wait limit
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: gives up after kWaitCycles SM clocks (~10 s) or once another thread has
+// recorded an error; on its own timeout it records `code` in *err.  Returns true when the
+// phase completed.
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
+  const long long t0 = clock64();
+  for (unsigned it = 0;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 255u) {
+      if (*(volatile int*)err) return false;
+      if (clock64() - t0 > kWaitCycles) break;
+    }
+  }
+  atomicCAS(err, 0, code);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_addr(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile, 128-byte swizzle, rows of 128 B,
+// 8-row groups 1024 B apart (SBO), version 1, layout type 2 (SWIZZLE_128B).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused for SW128 K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset
+  d |= (uint64_t)1 << 46;                   // descriptor version
+  d |= (uint64_t)2 << 61;                   // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = N = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTile >> 3) << 17) |
+                            ((uint32_t)(kTile >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+#define TMEM_LD32(taddr, r)                                                                  \
+  asm volatile(                                                                              \
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"   \
+      "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];" \
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),  \
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),           \
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),        \
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),        \
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),        \
+        "=r"(r[31])                                                                          \
+      : "r"(taddr))
+
+#define TMEM_ST32(taddr, r)                                                                  \
+  asm volatile(                                                                              \
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12," \
+      "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"     \
+      ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]),        \
+      "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]),        \
+      "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]),    \
+      "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]),    \
+      "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31]))
+
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tri_tile(int t, int& I, int& J) {
+  int r = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while ((r + 1) * (r + 2) / 2 <= t) ++r;
+  while (r * (r + 1) / 2 > t) --r;
+  I = r;
+  J = t - r * (r + 1) / 2;
+}
+
+struct TcArgs {
+  int n;
+  int kb_begin;   // first K-block of the tail
+  int kb_end;     // one past the last K-block
+  const uint32_t* chunk_end;  // bit per K-block: an accumulation chunk ends after it
+  const double* head;         // [n][ldh] FP64 head + real-space terms (lower triangle)
+  int64_t ldh;
+  float* E;
+  int64_t ldE;
+  int* err;
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_ek_tc(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1,
+        const __grid_constant__ CUtensorMap map2, TcArgs args) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  // 1024-byte aligned ring of kStages x 6 tiles
+  uint8_t* ring = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages];
+  __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
+  __shared__ uint32_t tmem_base_s;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int I, J;
+  tri_tile(blockIdx.x, I, J);
+  const int i0 = I * kTile, j0 = J * kTile;
+  const int nkb = args.kb_end - args.kb_begin;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                     smem_addr(&tmem_base_s))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_s;
+
+  if (warp == 0) {
+    // ---- TMA producer ------------------------------------------------------------
+    if (lane == 0) {
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % kStages;
+        if (!mbar_wait(&empty_bar[s], ((kb / kStages) & 1) ^ 1, args.err, 1)) break;
+        uint8_t* st = ring + s * kStageBytes;
+        mbar_expect_tx(&full_bar[s], kStageBytes);
+        const int x = (args.kb_begin + kb) * kBlockK;
+        tma_load_2d(st + 0 * kPlaneTileBytes, &map0, &full_bar[s], x, i0);
+        tma_load_2d(st + 1 * kPlaneTileBytes, &map1, &full_bar[s], x, i0);
+        tma_load_2d(st + 2 * kPlaneTileBytes, &map2, &full_bar[s], x, i0);
+        tma_load_2d(st + 3 * kPlaneTileBytes, &map0, &full_bar[s], x, j0);
+        tma_load_2d(st + 4 * kPlaneTileBytes, &map1, &full_bar[s], x, j0);
+        tma_load_2d(st + 5 * kPlaneTileBytes, &map2, &full_bar[s], x, j0);
+      }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer ----------------------------------------------------------------
+    if (lane == 0) {
+      int chunk = 0;
+      bool first_in_chunk = true;
+      bool ok = true;
+      for (int kb = 0; kb < nkb && ok; ++kb) {
+        const int s = kb % kStages;
+        const int buf = chunk & 1;
+        if (first_in_chunk) {
+          ok = mbar_wait(&acc_empty[buf], ((chunk >> 1) & 1) ^ 1, args.err, 2);
+          if (!ok) break;
+          tc_fence_after();
+        }
+        ok = mbar_wait(&full_bar[s], (kb / kStages) & 1, args.err, 3);
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t a0 = smem_addr(ring + s * kStageBytes);
+        const uint32_t d = tmem + (uint32_t)(buf * kTile);
+        // products (p, q) with p + q <= 2: A plane p (rows i), B plane q (rows j)
+        const int pa[6] = {0, 0, 1, 0, 1, 2};
+        const int pb[6] = {0, 1, 0, 2, 1, 0};
+#pragma unroll
+        for (int ks = 0; ks < kBlockK / 16; ++ks) {
+#pragma unroll
+          for (int t = 0; t < 6; ++t) {
+            const uint64_t da = smem_desc(a0 + pa[t] * kPlaneTileBytes + ks * 32);
+            const uint64_t db = smem_desc(a0 + (3 + pb[t]) * kPlaneTileBytes + ks * 32);
+            mma_bf16(d, da, db, (first_in_chunk && ks == 0 && t == 0) ? 0u : 1u);
+          }
+        }
+        mma_commit(&empty_bar[s]);  // frees the stage once these MMAs have read it
+        first_in_chunk = false;
+        const int g = args.kb_begin + kb;
+        const bool last = (kb + 1 == nkb) || ((args.chunk_end[g >> 5] >> (g & 31)) & 1u);
+        if (last) {
+          mma_commit(&acc_full[buf]);
+          ++chunk;
+          first_in_chunk = true;
+        }
+      }
+    }
+  } else {
+    // ---- epilogue: warps 2-5, TMEM lane quarter q = warp % 4 ------------------------
+    const int q = warp & 3;
+    const int row = i0 + 32 * q + lane;
+    const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+    int chunk = 0;
+    int kb = 0;
+    bool ok = true;
+    while (kb < nkb && ok) {
+      // find the end of this chunk (same rule as the MMA warp)
+      int kb_last = kb;
+      while (true) {
+        const int g = args.kb_begin + kb_last;
+        if (kb_last + 1 == nkb || ((args.chunk_end[g >> 5] >> (g & 31)) & 1u)) break;
+        ++kb_last;
+      }
+      const bool final_chunk = kb_last + 1 == nkb;
+      const int buf = chunk & 1;
+      ok = mbar_wait(&acc_full[buf], (chunk >> 1) & 1, args.err, 4);
+      if (!ok) break;
+      tc_fence_after();
+#pragma unroll 1
+      for (int cg = 0; cg < kTile / 32; ++cg) {
+        uint32_t acc[32], hi[32], lo[32];
+        const uint32_t col = (uint32_t)(cg * 32);
+        TMEM_LD32(tmem + lane_base + buf * kTile + col, acc);
+        if (chunk > 0) {
+          TMEM_LD32(tmem + lane_base + 2 * kTile + col, hi);
+          TMEM_LD32(tmem + lane_base + 3 * kTile + col, lo);
+        }
+        tmem_wait_ld();
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+          const float a = __uint_as_float(acc[t]);
+          float h = 0.f, l = 0.f;
+          if (chunk > 0) {
+            h = __uint_as_float(hi[t]);
+            l = __uint_as_float(lo[t]);
+          }
+          // two-sum: h + a = s + e exactly
+          const float s = __fadd_rn(h, a);
+          const float bb = __fsub_rn(s, h);
+          const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(a, bb));
+          hi[t] = __float_as_uint(s);
+          lo[t] = __float_as_uint(__fadd_rn(l, e));
+        }
+        if (final_chunk) {
+          if (row < args.n) {
+#pragma unroll
+            for (int t = 0; t < 32; ++t) {
+              const int j = j0 + cg * 32 + t;
+              if (j < args.n && j <= row) {
+                const double v = (double)__uint_as_float(hi[t]) + (double)__uint_as_float(lo[t]) +
+                                 args.head[(int64_t)row * args.ldh + j];
+                args.E[(int64_t)row * args.ldE + j] = (float)v;
+              }
+            }
+          }
+        } else {
+          TMEM_ST32(tmem + lane_base + 2 * kTile + col, hi);
+          TMEM_ST32(tmem + lane_base + 3 * kTile + col, lo);
+        }
+      }
+      tmem_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[buf]);
+      ++chunk;
+      kb = kb_last + 1;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem)
+                 : "memory");
+  }
+}
+
+// a = a0 + a1 + a2 in BF16 (each plane the rounding of the remainder of the previous).
+__global__ void k_split_bf16(const float* __restrict__ A, int64_t len, __nv_bfloat16* __restrict__ p0,
+                             __nv_bfloat16* __restrict__ p1, __nv_bfloat16* __restrict__ p2) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float a = A[i];
+    const __nv_bfloat16 b0 = __float2bfloat16_rn(a);
+    const float r1 = a - __bfloat162float(b0);
+    const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(b1);
+    p0[i] = b0;
+    p1[i] = b1;
+    p2[i] = __float2bfloat16_rn(r2);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, const void* base, int rows, int64_t cols) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  cuuint32_t box[2] = {(cuuint32_t)kBlockK, (cuuint32_t)kTile};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+void launch_split_bf16(const float* A, int64_t len, void* p0, void* p1, void* p2,
+                       cudaStream_t s) {
+  (k_split_bf16<<<2048, 256, 0, s>>>(A, len, (__nv_bfloat16*)p0, (__nv_bfloat16*)p1,
+                                     (__nv_bfloat16*)p2), note_launch());
+}
+
+int launch_ek_tc(const void* p0, const void* p1, const void* p2, int npad, int mpad, int n,
+                 int kb_begin, const uint32_t* chunk_end, const double* head, int64_t ldh,
+                 float* E, int64_t ldE, int* err, cudaStream_t s) {
+  CUtensorMap m0, m1, m2;
+  const int64_t cols = 2 * (int64_t)mpad;
+  if (!make_map(&m0, p0, npad, cols) || !make_map(&m1, p1, npad, cols) ||
+      !make_map(&m2, p2, npad, cols))
+    return CPM_ECUDA;
+  TcArgs a;
+  a.n = n;
+  a.kb_begin = kb_begin;
+  a.kb_end = (int)(cols / kBlockK);
+  a.chunk_end = chunk_end;
+  a.head = head;
+  a.ldh = ldh;
+  a.E = E;
+  a.ldE = ldE;
+  a.err = err;
+  const int nt = (n + kTile - 1) / kTile;
+  const int tiles = nt * (nt + 1) / 2;
+  const int smem = kStages * kStageBytes + 1024;
+  if (cudaFuncSetAttribute(k_ek_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+      cudaSuccess)
+    return CPM_ECUDA;
+  if (a.kb_begin >= a.kb_end) return CPM_OK;  // everything is in the head
+  (k_ek_tc<<<tiles, kThreads, smem, s>>>(m0, m1, m2, a), note_launch());
+  return cudaGetLastError() == cudaSuccess ? CPM_OK : CPM_ECUDA;
+}
+
+}  // namespace cpm
