@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cells", type=int, default=40, help="cells per sheet edge (40: 12,800 atoms)")
     ap.add_argument("--ions", type=int, default=2000)
-    ap.add_argument("--precision", choices=["bf16x6", "fp32", "fp64"], default="fp32")
+    ap.add_argument("--precision", choices=["bf16x6", "fp32", "fp64"], default="bf16x6")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()

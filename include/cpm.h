@@ -95,7 +95,7 @@ typedef struct cpm_params {
 
 typedef struct cpm_ctx cpm_ctx;
 
-/* Fills p with the defaults: g 0.3, rcut 12, eps 1e-8, slab 1, FP32, PCG-DC with
+/* Fills p with the defaults: g 0.3, rcut 12, eps 1e-8, slab 1, BF16X6, PCG-DC with
  * g_dc 0.083 and r_cut 8 (Sec. IV A), p_gap 1, default stream, cudaMalloc.  The box
  * is left zero and must be set. */
 void cpm_default_params(cpm_params* p);

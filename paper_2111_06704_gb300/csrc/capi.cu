@@ -206,7 +206,7 @@ void cpm_default_params(cpm_params* p) {
   p->rcut_real = 12.0;
   p->kspace_eps = 1e-8;
   p->slab = 1;
-  p->precision = CPM_PREC_FP32;
+  p->precision = CPM_PREC_BF16X6;
   p->precond = CPM_PRECOND_DC;
   p->g_dc = 0.083;
   p->rcut_dc = 8.0;

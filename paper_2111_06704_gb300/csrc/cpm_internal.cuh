@@ -151,6 +151,8 @@ struct SolveArgs {
   int maxit;
   int* iters;        // host [nrhs]
   double* relres;    // host [nrhs]
+  void* ws = nullptr;    // optional fixed device workspace (else the context's, grown)
+  size_t ws_bytes = 0;
 };
 int pcg_solve(Ctx* c, const SolveArgs& a);
 void launch_neutralize(double* q, int nrhs, int n, const double* d, const double* qsol,

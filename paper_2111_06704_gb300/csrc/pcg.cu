@@ -60,10 +60,12 @@ __device__ void block_sum(double (&v)[NV], double* sm /* [32*NV] */) {
 // q[r] = E p[r] for NR columns starting at column c0, one warp per row, plus the
 // per-block partial of p^T q.
 // FP32 E: p is held as a float pair p = hi + lo (to ~1e-14).  Each product e * hi is
-// split exactly into its float value and rounding error (fma(e, hi, -e*hi)); values
-// and errors (plus e * lo) are summed over 8 elements in float and then in FP64, so the
-// matvec is accurate to ~1e-8 of |E||p| instead of float rounding of every product,
-// while E is still streamed once in 4-byte words.
+// split exactly into its float value and rounding error (fma(e, hi, -e*hi)) and the
+// running float sum is an error-free two-sum, so over each 8-element stretch the float
+// value plus the float error term carry the exact sum; both go to FP64.  The stored
+// float E is thus applied to ~1e-14, not to float rounding of every product and sum --
+// otherwise PCG converges to the solution of a slightly different matrix (1e-6 of q at
+// the 512-atom cell) -- while E is still streamed once in 4-byte words.
 template <typename T, int NR>
 __global__ void __launch_bounds__(kThreads)
 k_matvec(const T* __restrict__ E, int64_t ldE, int n, const T* __restrict__ pv,
@@ -105,9 +107,14 @@ k_matvec(const T* __restrict__ E, int64_t ldE, int n, const T* __restrict__ pv,
                   *reinterpret_cast<float4*>(lv) = *reinterpret_cast<const float4*>(plo + o);
 #pragma unroll
                   for (int w = 0; w < VEC; ++w) {
+                    // exact product (two-product) and exact running sum (two-sum):
+                    // every float rounding error lands in perr
                     const T pr = ev[w] * hv[w];
-                    perr[r] = fma(ev[w], lv[w], perr[r] + fma(ev[w], hv[w], -pr));
-                    part[r] += pr;
+                    const T s = part[r] + pr;
+                    const T bb = s - part[r];
+                    const T e2 = (part[r] - (s - bb)) + (pr - bb);
+                    perr[r] = fma(ev[w], lv[w], perr[r] + fma(ev[w], hv[w], -pr) + e2);
+                    part[r] = s;
                   }
                 } else {
 #pragma unroll
@@ -168,7 +175,8 @@ k_update(int n, int64_t ldv, int nrhs, const ColState* __restrict__ st,
          const double* __restrict__ p, const double* __restrict__ q,
          const double* __restrict__ inv_diag, double* __restrict__ dots) {
   __shared__ double sm[32 * 4];
-  for (int col = 0; col < nrhs; ++col) {
+  {
+    const int col = blockIdx.y;  // one right-hand side per grid row
     const double a = st[col].alpha;
     const bool active = st[col].done == 0;
     double v[4] = {0, 0, 0, 0};
@@ -206,7 +214,8 @@ k_dc_apply(int n, int64_t ldv, int nrhs, const ColState* __restrict__ st,
            double* __restrict__ dots, int first) {
   __shared__ double sm[32 * 2];
   __shared__ double s_rsum;
-  for (int col = 0; col < nrhs; ++col) {
+  {
+    const int col = blockIdx.y;
     const bool active = first || st[col].done == 0;
     if (threadIdx.x < 32) {
       double s = 0.0;
@@ -272,8 +281,9 @@ template <typename T>
 __global__ void k_p_update(int n, int64_t ldv, int nrhs, const ColState* __restrict__ st,
                            const double* __restrict__ z, double* __restrict__ p,
                            T* __restrict__ pv, T* __restrict__ plo, int first) {
-  for (int col = 0; col < nrhs; ++col) {
-    if (!first && st[col].done) continue;
+  {
+    const int col = blockIdx.y;
+    if (!first && st[col].done) return;
     const double bta = first ? 0.0 : st[col].beta;
     const int64_t o = (int64_t)col * ldv;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -294,7 +304,8 @@ __global__ void k_init_r(int n, int64_t ldv, int nrhs, const double* __restrict_
                          const double* __restrict__ inv_diag, int pre,
                          double* __restrict__ dots) {
   __shared__ double sm[32 * 4];
-  for (int col = 0; col < nrhs; ++col) {
+  {
+    const int col = blockIdx.y;
     const int64_t o = (int64_t)col * ldv;
     double v[4] = {0, 0, 0, 0};  // r^T z, b^T b, r^T r, sum r
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -390,6 +401,12 @@ void launch_matvec(const Ctx* c, const void* pv, const void* plo, const double* 
   const T* lo = (const T*)plo;
   for (int c0 = 0; c0 < nrhs; c0 += 4) {
     int left = nrhs - c0;
+    if (left >= 8) {  // eight columns per pass over E
+      (k_matvec<T, 8><<<gm, kThreads, 0, c->stream>>>(E, c->ldE, c->n, hi, lo, p64, ldv, c0,
+                                                     nrhs, q, pq_part), note_launch());
+      c0 += 4;
+      continue;
+    }
     if (left >= 4)
       (k_matvec<T, 4><<<gm, kThreads, 0, c->stream>>>(E, c->ldE, c->n, hi, lo, p64, ldv, c0,
                                                      nrhs, q, pq_part), note_launch());
@@ -411,7 +428,9 @@ int pcg_solve(Ctx* c, const SolveArgs& a) {
   const int n = c->n, nrhs = a.nrhs;
   const int64_t ldv = c->ldE;
   const int sms = sm_count(c->device);
+  // elementwise kernels: ge blocks per right-hand side, one grid row per right-hand side
   const int ge = std::max(1, std::min((n + kThreads - 1) / kThreads, 2 * sms));
+  const dim3 g2(ge, nrhs);
   const int gm = std::max(1, std::min((n + kMvWarps - 1) / kMvWarps, 2 * sms));
   const int pre = c->p.precond;
   const bool f64 = c->fp64();
@@ -429,9 +448,18 @@ int pcg_solve(Ctx* c, const SolveArgs& a) {
                odt = take((size_t)ge * nrhs * 4 * sizeof(double)),
                odc = take((size_t)ge * nrhs * 4 * sizeof(double)),
                ost = take(2 * (size_t)nrhs * sizeof(ColState));
-  int rc = buf_reserve(c, &c->ws_solve, off);
-  if (rc) return rc;
-  char* base = (char*)c->ws_solve.ptr;
+  int rc;
+  char* base;
+  if (a.ws) {  // caller-provided workspace (never grown)
+    if (off > a.ws_bytes)
+      return set_err(c, CPM_EINVAL, "solve workspace needs " + std::to_string(off) +
+                                        " bytes; the fixed workspace holds " +
+                                        std::to_string(a.ws_bytes));
+    base = (char*)a.ws;
+  } else {
+    if ((rc = buf_reserve(c, &c->ws_solve, off))) return rc;
+    base = (char*)c->ws_solve.ptr;
+  }
   double* x = (double*)(base + ox);
   double* r = (double*)(base + orr);
   double* z = (double*)(base + oz);
@@ -458,26 +486,26 @@ int pcg_solve(Ctx* c, const SolveArgs& a) {
                      "copy guess"))
         return CPM_ECUDA;
     if (f64) {
-      (k_p_update<double><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, st, x, p, (double*)pv, nullptr, 1), note_launch());
+      (k_p_update<double><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, st, x, p, (double*)pv, nullptr, 1), note_launch());
       launch_matvec<double>(c, pv, nullptr, p, ldv, nrhs, q, pq_part, gm);
     } else {
-      (k_p_update<float><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, st, x, p, (float*)pv, plo, 1), note_launch());
+      (k_p_update<float><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, st, x, p, (float*)pv, plo, 1), note_launch());
       launch_matvec<float>(c, pv, plo, p, ldv, nrhs, q, pq_part, gm);
     }
   }
-  (k_init_r<<<ge, kThreads, 0, s>>>(n, ldv, nrhs, a.b, a.bscale, q, q2, a.use_guess ? 1 : 0, r, x, z,
+  (k_init_r<<<g2, kThreads, 0, s>>>(n, ldv, nrhs, a.b, a.bscale, q, q2, a.use_guess ? 1 : 0, r, x, z,
                                    inv_diag, pre, dots), note_launch());
   const int wb = 8;  // warps per block for the per-column reductions
   const int gcol = (nrhs + wb - 1) / wb;
   (k_init_state<<<gcol, wb * 32, 0, s>>>(dots, ge, nrhs, a.tol, pre, st), note_launch());
   if (pre == CPM_PRECOND_DC) {
-    (k_dc_apply<<<ge, kThreads, 0, s>>>(n, ldv, nrhs, st, (const int64_t*)c->nbr_off.ptr,
+    (k_dc_apply<<<g2, kThreads, 0, s>>>(n, ldv, nrhs, st, (const int64_t*)c->nbr_off.ptr,
                                        (const int*)c->nbr_idx.ptr, (const double*)c->prow.ptr,
                                        c->pgap, r, z, dots, ge, dots_dc, 1), note_launch());
     (k_init_rz_dc<<<gcol, wb * 32, 0, s>>>(dots_dc, ge, nrhs, st), note_launch());
   }
-  if (f64) (k_p_update<double><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, st, z, p, (double*)pv, nullptr, 1), note_launch());
-  else (k_p_update<float><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, st, z, p, (float*)pv, plo, 1), note_launch());
+  if (f64) (k_p_update<double><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, st, z, p, (double*)pv, nullptr, 1), note_launch());
+  else (k_p_update<float><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, st, z, p, (float*)pv, plo, 1), note_launch());
   if (cuda_check(c, cudaGetLastError(), "pcg init")) return CPM_ECUDA;
 
   std::vector<ColState> host(nrhs);
@@ -505,22 +533,22 @@ int pcg_solve(Ctx* c, const SolveArgs& a) {
     else launch_matvec<float>(c, pv, plo, p, ldv, nrhs, q, pq_part, gm);
     (k_alpha<<<gcol, wb * 32, 0, s>>>(pq_part, gm, nrhs, cur), note_launch());
     if (pre == CPM_PRECOND_DC) {
-      (k_update<CPM_PRECOND_DC><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, cur, x, r, z, p, q,
+      (k_update<CPM_PRECOND_DC><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, cur, x, r, z, p, q,
                                                        inv_diag, dots), note_launch());
-      (k_dc_apply<<<ge, kThreads, 0, s>>>(n, ldv, nrhs, cur, (const int64_t*)c->nbr_off.ptr,
+      (k_dc_apply<<<g2, kThreads, 0, s>>>(n, ldv, nrhs, cur, (const int64_t*)c->nbr_off.ptr,
                                          (const int*)c->nbr_idx.ptr,
                                          (const double*)c->prow.ptr, c->pgap, r, z, dots, ge,
                                          dots, 0), note_launch());
     } else if (pre == CPM_PRECOND_JACOBI) {
-      (k_update<CPM_PRECOND_JACOBI><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, cur, x, r, z, p, q,
+      (k_update<CPM_PRECOND_JACOBI><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, cur, x, r, z, p, q,
                                                            inv_diag, dots), note_launch());
     } else {
-      (k_update<CPM_PRECOND_NONE><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, cur, x, r, z, p, q,
+      (k_update<CPM_PRECOND_NONE><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, cur, x, r, z, p, q,
                                                          inv_diag, dots), note_launch());
     }
     (k_beta<<<gcol, wb * 32, 0, s>>>(dots, ge, nrhs, a.tol, flexible, cur, nxt), note_launch());
-    if (f64) (k_p_update<double><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, nxt, z, p, (double*)pv, nullptr, 0), note_launch());
-    else (k_p_update<float><<<ge, kThreads, 0, s>>>(n, ldv, nrhs, nxt, z, p, (float*)pv, plo, 0), note_launch());
+    if (f64) (k_p_update<double><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, nxt, z, p, (double*)pv, nullptr, 0), note_launch());
+    else (k_p_update<float><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, nxt, z, p, (float*)pv, plo, 0), note_launch());
     ++it;
     if (it % check_every == 0 || it == a.maxit) {
       if (cuda_check(c, cudaGetLastError(), "pcg iteration")) return CPM_ECUDA;

@@ -167,6 +167,8 @@ k_bsol_real(const double* __restrict__ xyz, const double* __restrict__ alpha, in
   }
   const double L[3] = {lx, ly, lz};
   const double rc2 = rc * rc;
+  const double invL[3] = {1.0 / lx, 1.0 / ly, 1.0 / lz};
+  const bool single[3] = {2.0 * rc < lx, 2.0 * rc < ly, 2.0 * rc < lz};
   double acc = 0.0, qz = 0.0, qs = 0.0;
   for (int base = 0; base < n_ion; base += kIonChunk) {
     const int cnt = min(kIonChunk, n_ion - base);
@@ -186,8 +188,13 @@ k_bsol_real(const double* __restrict__ xyz, const double* __restrict__ alpha, in
       double d[3] = {ri[0] - sx[t][0], ri[1] - sx[t][1], ri[2] - sx[t][2]};
       int lo[3], hi[3];
       for (int u = 0; u < 3; ++u) {
-        lo[u] = (int)ceil((-rc - d[u]) / L[u]);
-        hi[u] = (int)floor((rc - d[u]) / L[u]);
+        if (single[u]) {  // box edge above 2 rc: only the minimum image can be in range
+          d[u] -= L[u] * rint(d[u] * invL[u]);
+          lo[u] = hi[u] = 0;
+        } else {
+          lo[u] = (int)ceil((-rc - d[u]) * invL[u]);
+          hi[u] = (int)floor((rc - d[u]) * invL[u]);
+        }
       }
       for (int a = lo[0]; a <= hi[0]; ++a) {
         double x = d[0] + a * L[0];
@@ -201,7 +208,9 @@ k_bsol_real(const double* __restrict__ xyz, const double* __restrict__ alpha, in
             if (r2 >= rc2 || r2 == 0.0) continue;
             double r = sqrt(r2);
             double e = erfc(g * r);
-            if (!isinf(ai)) e -= erfc(ai * r);
+            // erfc(6) < 3e-17: beyond alpha r = 6 the Gaussian term is below double
+            // rounding of the erfc(g r) term
+            if (ai * r < 6.0) e -= erfc(ai * r);
             acc += qI * e / r;
           }
         }
