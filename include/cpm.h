@@ -145,6 +145,27 @@ int cpm_solve(cpm_ctx* c, int nrhs, const double* b, double* q_inout, int use_gu
               double tol, int maxit, int* iters_out, double* relres_out);
 
 /*
+ * cpm_solve_static: the same first-step solve as cpm_solve, but it allocates no device
+ * memory.  The paper has no counterpart; this variant is for callers that cannot call
+ * cudaMalloc at solve time -- an MD engine that has reserved the device for its own
+ * memory pool, a host program that forbids allocation after start-up, or a time step
+ * that must not stall on an allocation.  cpm_solve grows a per-context workspace on
+ * demand; this call instead runs the same kernels on a fixed workspace of
+ * CPM_STATIC_SCRATCH_BYTES held in a file-scope device array, which every device that
+ * loads the library keeps until the process exits.
+ * b[nrhs*n] and q_inout[nrhs*n] must be device pointers (staging host arrays would
+ * allocate); other arguments as for cpm_solve.  Returns CPM_EINVAL when the problem
+ * (n rounded up to 128, times nrhs) needs more workspace than the array holds, or when a
+ * pointer is on the host.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current, so make that first call
+ * before any stream capture.  All calls share the array and each call clears what must
+ * start at zero; calls whose work overlaps on the GPU race, so serialise them.
+ */
+#define CPM_STATIC_SCRATCH_BYTES (8u * 1024u * 1024u)
+int cpm_solve_static(cpm_ctx* c, int nrhs, const double* b, double* q_inout, int use_guess,
+                     double tol, int maxit, int* iters_out, double* relres_out);
+
+/*
  * Second step of Eq. 35 for nrhs columns: q <- q - (sum_i q_i + Q^sol) d, so that
  * sum_i q_i = -Q^sol (Eq. 34).  qsol[nrhs] may be NULL (Q^sol = 0).
  */

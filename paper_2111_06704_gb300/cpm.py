@@ -76,8 +76,8 @@ class cpm_info_t(ctypes.Structure):
 
 
 EXPORTS = ["cpm_default_params", "cpm_create", "cpm_destroy", "cpm_build_E", "cpm_potential",
-           "cpm_solve", "cpm_neutralize", "cpm_get_E", "cpm_get_info", "cpm_get_d",
-           "cpm_last_error"]
+           "cpm_solve", "cpm_solve_static", "cpm_neutralize", "cpm_get_E", "cpm_get_info",
+           "cpm_get_d", "cpm_last_error"]
 
 _lib = None
 
@@ -106,6 +106,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.cpm_build_E.argtypes = [vp, i, vp, vp]
     lib.cpm_potential.argtypes = [vp, i, i, vp, vp, vp, vp, vp]
     lib.cpm_solve.argtypes = [vp, i, vp, vp, i, d, i, vp, vp]
+    lib.cpm_solve_static.argtypes = [vp, i, vp, vp, i, d, i, vp, vp]
     lib.cpm_neutralize.argtypes = [vp, i, vp, vp]
     lib.cpm_get_E.argtypes = [vp, i, vp, i64]
     lib.cpm_get_info.argtypes = [vp, P(cpm_info_t)]
@@ -238,6 +239,20 @@ class Context:
         if isinstance(q, np.ndarray) and kq is not q:
             q[...] = kq
         return q, iters, rel
+
+    def cpm_solve_static(self, b, q, use_guess=False, tol=1e-6, maxit=1000):
+        """cpm_solve on the library's fixed device workspace: no allocation.  b and q
+        must be CUDA tensors (device pointers); returns (iterations, relative residual)."""
+        nrhs = int(b.shape[0]) if b.ndim == 2 else 1
+        pb, kb = _ptr(b)
+        pq, kq = _ptr(q)
+        iters = np.zeros(nrhs, dtype=np.int32)
+        rel = np.zeros(nrhs)
+        self._check(self.lib.cpm_solve_static(self.h, nrhs, pb, pq, 1 if use_guess else 0,
+                                              float(tol), int(maxit),
+                                              iters.ctypes.data_as(ctypes.c_void_p),
+                                              rel.ctypes.data_as(ctypes.c_void_p)))
+        return iters, rel
 
     def cpm_neutralize(self, q, qsol=None):
         nrhs = int(q.shape[0]) if q.ndim == 2 else 1
