@@ -50,6 +50,13 @@ def parse():
     ap.add_argument("--precision", choices=["bf16x6", "fp32", "fp64"], default="bf16x6")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=["precision", "batch", "learned"], default="precision")
+    ap.add_argument("--train-frames", type=int, default=20000)
+    ap.add_argument("--heldout-frames", type=int, default=2000)
+    ap.add_argument("--epochs", type=int, default=3)
+    ap.add_argument("--frames", type=int, default=256, help="frames per batch (batch workload)")
+    ap.add_argument("--baseline-frames", type=int, default=16,
+                    help="frames timed for the per-frame FP64 baseline (batch workload)")
     return ap.parse_args()
 
 
@@ -241,7 +248,7 @@ def run_ours(args, rank, world, local_rank):
     b = torch.empty((1, n), dtype=torch.float64, device=dev)
     qs = torch.empty(1, dtype=torch.float64, device=dev)
     qq = torch.zeros((1, n), dtype=torch.float64, device=dev)
-    info = {"kspace_ms": [], "tc_ms": [], "iters": [], "relres": []}
+    info = {"kspace_ms": [], "tc_ms": [], "head_ms": [], "iters": [], "relres": []}
 
     def step():
         ctx.cpm_build_E(xyz, alpha)
@@ -252,6 +259,8 @@ def run_ours(args, rank, world, local_rank):
         info["kspace_ms"].append(inf["t_kspace_ms"])
         info["tc_ms"].append(inf["t_tc_ms"])
         info["head_cols"] = inf["head_cols"]
+        info["tc_blocks"] = list(inf["tc_blocks"])
+        info["head_ms"].append(inf["t_head_ms"])
         info["iters"].append(int(it[0]))
         info["relres"].append(float(rel[0]))
 
@@ -287,6 +296,12 @@ def run_ours(args, rank, world, local_rank):
         ev1.record(stream)
         torch.cuda.synchronize()
         solve_ms = ev0.elapsed_time(ev1) / reps
+        # the PCG matvec alone (one column; events inside the library around its launch)
+        mv_ms = []
+        for _ in range(6):
+            ctx.cpm_apply_E(qq, b)
+            mv_ms.append(ctx.cpm_get_info()["t_matvec_ms"])
+        matvec_ms = statistics.median(mv_ms[1:])
 
     # end to end through the public API with host buffers
     e2e = None
@@ -324,20 +339,25 @@ def run_ours(args, rank, world, local_rank):
     sm_mhz = clk.get("sm_max_mhz") or 2070.0
     esz = 8 if args.precision == "fp64" else 4
     if args.precision == "bf16x6":
-        # the tensor-core tail kernel alone: lower-triangle tiles, tail columns, six BF16
-        # products per term (the FP64 head kernel is timed apart in e_build_s)
+        # the tensor-core tail kernel alone: lower-triangle tiles over the tail columns,
+        # each 64-column K-block with six, three or one BF16 products (weight-bounded
+        # schedule); the FP64-accurate head kernel is timed apart and sits in e_build_s
         tc_ms = statistics.mean(info["tc_ms"])
         nt = (n + 127) // 128
-        tail_cols = 2 * ((m + 63) // 64 * 64) - info["head_cols"]
-        tc_flops = 6 * 2.0 * (nt * (nt + 1) / 2) * 128 * 128 * tail_cols
-        algo_flops = 6 * 2.0 * (n * (n + 1) / 2) * tail_cols
+        n6, n3, n1 = info["tc_blocks"]
+        prod_cols = 64 * (6 * n6 + 3 * n3 + n1)
+        tail_cols = 64 * (n6 + n3 + n1)
+        tc_flops = 2.0 * (nt * (nt + 1) / 2) * 128 * 128 * prod_cols
+        algo_flops = 2.0 * (n * (n + 1) / 2) * prod_cols
         bf16_peak = peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"])
         roof = {"bound": "tensor", "achieved": algo_flops / (tc_ms * 1e-3) / 1e12,
                 "peak": bf16_peak, "unit": "TFLOP/s",
-                "kernel": "k_ek_tc (tcgen05 BF16x6 k-space GEMM, TMEM two-sum accumulation)",
+                "kernel": "k_ek_tc (tcgen05 split-BF16 k-space GEMM, TMEM two-sum accumulation)",
                 "peak_source": f"{src} bf16_tflops (burst)",
                 "issued_tflops": tc_flops / (tc_ms * 1e-3) / 1e12,
-                "fp32_accurate_tflops": algo_flops / 6 / (tc_ms * 1e-3) / 1e12}
+                "fp32_accurate_tflops": 2.0 * (n * (n + 1) / 2) * tail_cols / (tc_ms * 1e-3) / 1e12,
+                "k_blocks_6_3_1_products": [n6, n3, n1],
+                "tc_ms": tc_ms, "head_ms": statistics.mean(info["head_ms"])}
     elif args.precision == "fp32":
         peak = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": flops / (kspace_ms * 1e-3) / 1e12, "peak": peak,
@@ -369,6 +389,13 @@ def run_ours(args, rank, world, local_rank):
                        "iters": statistics.median(info["iters"])},
         "relres": max(info["relres"]),
         "roofline": roof,
+        "matvec_roofline": {
+            "bound": "hbm", "kernel": "k_matvec (PCG matvec, E streamed once)",
+            "achieved": n * ((n + 127) // 128 * 128) * esz / (matvec_ms * 1e-3) / 1e9,
+            "peak": peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]), "unit": "GB/s",
+            "frac": n * ((n + 127) // 128 * 128) * esz / (matvec_ms * 1e-3) / 1e9
+            / peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]),
+            "ms": matvec_ms, "bytes_per_launch": n * ((n + 127) // 128 * 128) * esz},
         "peaks": {"source": src},
         "clocks": clk,
         "gpu_launches": launches,
@@ -378,6 +405,233 @@ def run_ours(args, rank, world, local_rank):
         est, desc = oracle_sample(el, ions, q)
         line["cpu_baseline"] = {"value": 1.0 / est, "unit": "solves/s", "cores": os.cpu_count(),
                                 "kind": "oracle", "sample": desc}
+    print(json.dumps(line), flush=True)
+
+
+def run_batch(args, rank, world, local_rank):
+    """Batching form: the 512-atom electrode, `--frames` frames of 2,000 ions (Gaussian
+    perturbations of one base frame) solved as one multi-right-hand-side PCG, against the
+    plain per-frame path on the same GPU (FP64 E, FP64 Jacobi PCG, one frame per call)."""
+    import torch
+
+    from paper_2111_06704_gb300 import cpm
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    work = wl.frame_batch(frames=args.frames, seed=wl.seed_for(3, rank))
+    el, io = work.electrode, work.electrolyte
+    n, F = el.n, io.frames
+    t = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    xyz, alpha, chi, ion_xyz, ion_q = t(el.xyz), t(el.alpha), t(el.chi), t(io.xyz), t(io.q)
+    ctx = cpm.Context(el.box, stream=stream.cuda_stream, precision=cpm.CPM_PREC_BF16X6,
+                      precond=cpm.CPM_PRECOND_DC)
+    base = cpm.Context(el.box, stream=stream.cuda_stream, precision=cpm.CPM_PREC_FP64,
+                       precond=cpm.CPM_PRECOND_JACOBI)
+    b = torch.empty((F, n), dtype=torch.float64, device=dev)
+    qs = torch.empty(F, dtype=torch.float64, device=dev)
+    q = torch.zeros((F, n), dtype=torch.float64, device=dev)
+    iters = []
+
+    def step():
+        ctx.cpm_build_E(xyz, alpha)
+        ctx.cpm_potential(ion_xyz, ion_q, chi, b, qs)
+        _, it, _ = ctx.cpm_solve(b, q, tol=TOL, maxit=2000)
+        ctx.cpm_neutralize(q, qs)
+        iters.append(float(np.mean(it)))
+
+    def timed(fn, reps):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(reps):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / reps
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        launches0 = ctx.cpm_get_info()["launches"]
+        with ClockSampler(local_rank) as clocks:
+            ms = max_over_ranks(timed(step, args.steps), world)
+        launches = ctx.cpm_get_info()["launches"] - launches0
+        solve_ms = timed(lambda: (ctx.cpm_solve(b, q, tol=TOL, maxit=2000),
+                                  ctx.cpm_neutralize(q, qs)), 3)
+        pot_ms = timed(lambda: ctx.cpm_potential(ion_xyz, ion_q, chi, b, qs), 3)
+
+        # plain per-frame FP64 Jacobi PCG on the same GPU, zero and previous-step guesses
+        base.cpm_build_E(xyz, alpha)
+        nb = min(F, args.baseline_frames)
+        b1 = torch.empty((1, n), dtype=torch.float64, device=dev)
+        q1 = torch.zeros((1, n), dtype=torch.float64, device=dev)
+        qs1 = torch.empty(1, dtype=torch.float64, device=dev)
+        it_base = []
+
+        def base_frames(guess):
+            for f in range(nb):
+                base.cpm_potential(ion_xyz[f:f + 1], ion_q[f:f + 1], chi, b1, qs1)
+                if not guess:
+                    q1.zero_()
+                _, it, _ = base.cpm_solve(b1, q1, use_guess=guess, tol=TOL, maxit=5000)
+                base.cpm_neutralize(q1, qs1)
+                it_base.append(int(it[0]))
+
+        base_ms = timed(lambda: base_frames(False), 1) / nb
+        base_it = float(np.mean(it_base))
+        it_base.clear()
+        base_prev_ms = timed(lambda: base_frames(True), 1) / nb
+        base_solve_ms = timed(lambda: [(base.cpm_solve(b1, q1, tol=TOL, maxit=5000),
+                                        base.cpm_neutralize(q1, qs1)) for _ in range(nb)], 1) / nb
+    if rank != 0:
+        return
+    value = world * F * 1000.0 / ms
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x6 (f32-accurate)", "data": "synthetic",
+        "config": {"workload": f"batching form: two-sheet graphene N={n}, {F} frames x "
+                               f"{io.n_ion} ions per step incl. E/P/d build",
+                   "frames": F, "ions": io.n_ion, "tol": TOL,
+                   "l2": "E (1 MB) is L2-resident; batched frames share each pass over it"},
+        "solve_only": {"value": F * 1000.0 / solve_ms, "unit": "solves/s",
+                       "mean_iters": statistics.mean(iters)},
+        "potential_ms_per_batch": pot_ms,
+        "baseline_fp64_per_frame": {
+            "value": 1000.0 / base_ms, "unit": "solves/s", "mean_iters": base_it,
+            "prev_step_guess_value": 1000.0 / base_prev_ms,
+            "solve_only_value": 1000.0 / base_solve_ms, "frames_timed": nb,
+            "what": "FP64 E, FP64 Jacobi PCG, cpm_potential + cpm_solve + cpm_neutralize "
+                    "one frame per call"},
+        "speedup_vs_fp64_per_frame": {"with_b": (F * 1000.0 / ms) / (1000.0 / base_ms),
+                                      "solve_only": (F / solve_ms) / (1.0 / base_solve_ms)},
+        "clocks": clocks.summary(),
+        "gpu_launches": launches,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_learned(args, rank, world, local_rank):
+    """Learned-guess form: the 512-atom electrode with the 200-ion set random-walked in
+    0.1 A steps; the guess network is trained on `--train-frames` solver-generated frames
+    and compared with the previous-step guess (Eq. 26) on `--heldout-frames` frames, all
+    to 1e-6 relative residual.  Held-out frames are solved as one multi-RHS batch."""
+    import torch
+
+    from paper_2111_06704_gb300 import cpm
+    from paper_2111_06704_gb300.guess import LearnedGuess
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    T, H = args.train_frames, args.heldout_frames
+    t_gen = time.perf_counter()
+    work = wl.walk_frames(T + H + 1, step=0.1, seed=wl.seed_for(4, rank))
+    el, io = work.electrode, work.electrolyte
+    n, F = el.n, io.frames
+    tt = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    ctx = cpm.Context(el.box)
+    ctx.cpm_build_E(tt(el.xyz), tt(el.alpha))
+    chi = tt(el.chi)
+    b = torch.empty((F, n), dtype=torch.float64, device=dev)
+    qs = torch.empty(F, dtype=torch.float64, device=dev)
+    qb = torch.zeros((F, n), dtype=torch.float64, device=dev)
+    for f0 in range(0, F, 1024):
+        f1 = min(F, f0 + 1024)
+        ctx.cpm_potential(tt(io.xyz[f0:f1]), tt(io.q[f0:f1]), chi, b[f0:f1], qs[f0:f1])
+    for f0 in range(0, F, 512):
+        f1 = min(F, f0 + 512)
+        ctx.cpm_solve(b[f0:f1], qb[f0:f1], tol=1e-9, maxit=2000)
+    gen_s = time.perf_counter() - t_gen
+
+    g = LearnedGuess(ctx, seed=rank)
+    t_train = time.perf_counter()
+    feat = g.features(b[1:T + 1], b[0:T], chi).reshape(-1, 32)
+    target = (qb[1:T + 1] - qb[0:T]).reshape(-1).to(torch.float32).contiguous()
+    k = min(T, 500) * n
+    g.set_normalisation(feat[:k].cpu().numpy(), target[:k].cpu().numpy())
+    losses = g.train(feat, target, epochs=args.epochs, batch=65536, lr=2e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t_train
+    del feat, target
+
+    test = slice(T + 1, T + H + 1)
+    bt = b[test].contiguous()
+    prev = qb[T:T + H].contiguous()
+
+    def solve_prev():
+        q = prev.clone()
+        _, it, _ = ctx.cpm_solve(bt, q, use_guess=True, tol=TOL, maxit=2000)
+        ctx.cpm_neutralize(q, qs[test].contiguous())
+        return it
+
+    def solve_learned():
+        q0 = g.guess(g.features(bt, b[T:T + H].contiguous(), chi), prev).reshape(prev.shape)
+        q0 = q0.contiguous()
+        _, it, _ = ctx.cpm_solve(bt, q0, use_guess=True, tol=TOL, maxit=2000)
+        ctx.cpm_neutralize(q0, qs[test].contiguous())
+        return it
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        it = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, it
+
+    def guess_only():
+        q0 = g.guess(g.features(bt, b[T:T + H].contiguous(), chi), prev)
+        return q0
+
+    for _ in range(max(1, args.warmup)):
+        solve_prev()
+        solve_learned()
+        guess_only()
+    with ClockSampler(local_rank) as clocks:
+        s_prev, it_prev = timed(solve_prev)
+        s_learn, it_learn = timed(solve_learned)
+        s_guess, _ = timed(guess_only)
+    # plain per-frame FP64 Jacobi PCG from the previous-step guess, same GPU
+    base = cpm.Context(el.box, precision=cpm.CPM_PREC_FP64, precond=cpm.CPM_PRECOND_JACOBI)
+    base.cpm_build_E(tt(el.xyz), tt(el.alpha))
+    nb = min(H, args.baseline_frames)
+    q1 = torch.empty((1, n), dtype=torch.float64, device=dev)
+    it_base = []
+
+    def base_frames():
+        for f in range(nb):
+            q1.copy_(prev[f:f + 1])
+            _, it, _ = base.cpm_solve(bt[f:f + 1], q1, use_guess=True, tol=TOL, maxit=5000)
+            base.cpm_neutralize(q1, qs[T + 1 + f:T + 2 + f])
+            it_base.append(int(it[0]))
+
+    s_base, _ = timed(base_frames)
+    if rank != 0:
+        return
+    value = H / s_learn
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": 1, "warmup": args.warmup, "ms_per_step": 1e3 * s_learn,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x6 (f32-accurate); guess network bf16 weights, f32 accumulation",
+        "data": "synthetic",
+        "config": {"workload": f"learned-guess form: two-sheet graphene N={n}, 200 ions "
+                               f"random-walked 0.1 A/frame, {T} training frames, {H} held-out "
+                               f"frames solved as one batch", "tol": TOL, "epochs": args.epochs},
+        "learned": {"mean_iters": float(np.mean(it_learn)), "solves_per_s": H / s_learn,
+                    "guess_ms": 1e3 * s_guess},
+        "previous_step": {"mean_iters": float(np.mean(it_prev)), "solves_per_s": H / s_prev},
+        "iteration_gain": float(np.mean(it_prev) - np.mean(it_learn)),
+        "baseline_fp64_per_frame_prev_guess": {"solves_per_s": nb / s_base,
+                                               "mean_iters": float(np.mean(it_base)),
+                                               "frames_timed": nb},
+        "speedup_vs_fp64_per_frame": (H / s_learn) / (nb / s_base),
+        "train": {"seconds": train_s, "first_loss": float(losses[0]),
+                  "last_loss": float(losses[-1]), "steps": len(losses)},
+        "generate_seconds": gen_s,
+        "clocks": clocks.summary(),
+    }
     print(json.dumps(line), flush=True)
 
 
@@ -392,7 +646,12 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    run_ours(args, rank, world, local_rank)
+    if args.workload == "batch":
+        run_batch(args, rank, world, local_rank)
+    elif args.workload == "learned":
+        run_learned(args, rank, world, local_rank)
+    else:
+        run_ours(args, rank, world, local_rank)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

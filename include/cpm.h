@@ -171,6 +171,50 @@ int cpm_solve_static(cpm_ctx* c, int nrhs, const double* b, double* q_inout, int
  */
 int cpm_neutralize(cpm_ctx* c, int nrhs, double* q_inout, const double* qsol);
 
+/* ---- learned initial guess ------------------------------------------------------------
+ * The paper has no learned component; the warm start it describes is the previous MD
+ * step's charges (Eq. 26).  These calls add a small per-atom network that predicts the
+ * change of the first-step charges q^b between consecutive frames from local features of
+ * the potential, so PCG can start from q_prev + scale * net(features).  The converged
+ * residual judges every guess, so accuracy is never traded.  All arrays are device
+ * pointers.  Network: 32 -> 64 -> 64 -> 64 -> 1 with SiLU on the hidden layers;
+ * parameters as one FP32 vector [W1 (64x32), b1, W2 (64x64), b2, W3 (64x64), b3, W4 (64),
+ * b4]; with bf16 != 0 the weights are used rounded to BF16, accumulation in FP32.
+ * norm[64] holds a per-feature mean then inverse standard deviation. */
+#define CPM_MLP_FEATURES 32
+#define CPM_MLP_PARAMS 10497
+
+/* Features of every atom of `frames` frames from their potentials b[frames*n] (V) and
+ * the previous frames' b_prev[frames*n]: Delta b_i, the means of Delta b over the
+ * neighbour shells k - 1/2 <= r < k + 1/2 (k = 1..8), b_i and its shell means, chi_i,
+ * the side of the electrode (+1 above the mean height) and 12 zeros.
+ * feat[frames*n*32] (float).  Needs a PCG-DC build (its neighbour lists, r <= rcut_dc). */
+int cpm_guess_features(cpm_ctx* c, int frames, const double* b, const double* b_prev,
+                       const double* chi, float* feat);
+
+/* out[s] = net((feat[s] - mean) * inv_std) for s < samples. */
+int cpm_mlp_forward(cpm_ctx* c, const float* params, const float* norm, int bf16,
+                    int64_t samples, const float* feat, float* out);
+
+/* grad[CPM_MLP_PARAMS] = gradient of (1/samples) sum_s (net(x_s) - target_s)^2 and
+ * *loss = sum_s (net(x_s) - target_s)^2 (both overwritten). */
+int cpm_mlp_grad(cpm_ctx* c, const float* params, const float* norm, int bf16,
+                 int64_t samples, const float* feat, const float* target, float* grad,
+                 double* loss);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected for `step` >= 1). */
+int cpm_mlp_adam(cpm_ctx* c, float* params, float* m, float* v, const float* grad, int step,
+                 float lr);
+
+/* q0[k] = q_prev[k] + scale * y[k] for k < len. */
+int cpm_guess_apply(cpm_ctx* c, int64_t len, const float* y, float scale, const double* q_prev,
+                    double* q0);
+
+/* q = E_n p for nrhs charge vectors p[nrhs*n] (e): the electrostatic potentials (1/A per e)
+ * on the electrode atoms, through the same matvec as the solver (E streamed once per pass
+ * of up to eight columns). */
+int cpm_apply_E(cpm_ctx* c, int nrhs, const double* p, double* q);
+
 /* Copies E (form CPM_E_STORED or CPM_E_PAPER) into out[n*ld] (row-major, ld >= n). */
 int cpm_get_E(cpm_ctx* c, int form, double* out, int64_t ld);
 
@@ -188,9 +232,21 @@ typedef struct cpm_info_t {
   int64_t launches;   /* CUDA kernels launched by the library in this process so far */
   double t_tc_ms;     /* BF16X6 builds: device time of the tensor-core tail kernel alone */
   int head_cols;      /* leading k-space operand columns summed in FP64 (heaviest weights) */
+  double t_matvec_ms; /* last cpm_apply_E: device time of its matvec launches alone */
+  int tc_blocks[3];   /* BF16X6 builds: 64-column K-blocks of the tensor-core tail taking
+                         six, three and one BF16 products (weight-bounded schedule) */
+  double t_head_ms;   /* BF16X6 builds: device time of the FP64-accurate head kernel */
 } cpm_info_t;
 
 int cpm_get_info(cpm_ctx* c, cpm_info_t* out);
+
+/* Copies the PCG-DC preconditioner P (Sec. III B 2, Eq. 36) in row form: row j holds
+ * P[j, tau] for the neighbours tau of j (r <= rcut_dc, tau = j included, ascending), so
+ * z_j = sum_tau P[j, tau] r_tau.  off[n+1] (int64) row offsets, idx[nnz] (int32) columns
+ * tau, val[nnz] the entries as Eq. 36 gives them (column tau of M_tau^-1); the Eq. 37
+ * fill p_gap (cpm_info_t.p_gap) is not added.  nnz is cpm_info_t.nnz_p.  Host or device
+ * pointers, caller-owned.  CPM_EINVAL if the context was built without PCG-DC. */
+int cpm_get_precond(cpm_ctx* c, int64_t* off, int* idx, double* val);
 
 /* Copies the neutralising vector d (Eq. S8) into d_out[n]. */
 int cpm_get_d(cpm_ctx* c, double* d_out);

@@ -72,12 +72,17 @@ class cpm_info_t(ctypes.Structure):
         ("launches", ctypes.c_int64),
         ("t_tc_ms", ctypes.c_double),
         ("head_cols", ctypes.c_int),
+        ("t_matvec_ms", ctypes.c_double),
+        ("tc_blocks", ctypes.c_int * 3),
+        ("t_head_ms", ctypes.c_double),
     ]
 
 
 EXPORTS = ["cpm_default_params", "cpm_create", "cpm_destroy", "cpm_build_E", "cpm_potential",
            "cpm_solve", "cpm_solve_static", "cpm_neutralize", "cpm_get_E", "cpm_get_info",
-           "cpm_get_d", "cpm_last_error"]
+           "cpm_get_d", "cpm_guess_features", "cpm_mlp_forward", "cpm_mlp_grad",
+           "cpm_mlp_adam", "cpm_guess_apply", "cpm_apply_E", "cpm_get_precond",
+           "cpm_last_error"]
 
 _lib = None
 
@@ -111,6 +116,13 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.cpm_get_E.argtypes = [vp, i, vp, i64]
     lib.cpm_get_info.argtypes = [vp, P(cpm_info_t)]
     lib.cpm_get_d.argtypes = [vp, vp]
+    lib.cpm_get_precond.argtypes = [vp, vp, vp, vp]
+    lib.cpm_guess_features.argtypes = [vp, i, vp, vp, vp, vp]
+    lib.cpm_mlp_forward.argtypes = [vp, vp, vp, i, i64, vp, vp]
+    lib.cpm_mlp_grad.argtypes = [vp, vp, vp, i, i64, vp, vp, vp, vp]
+    lib.cpm_mlp_adam.argtypes = [vp, vp, vp, vp, vp, i, ctypes.c_float]
+    lib.cpm_guess_apply.argtypes = [vp, i64, vp, ctypes.c_float, vp, vp]
+    lib.cpm_apply_E.argtypes = [vp, i, vp, vp]
     lib.cpm_last_error.argtypes = [vp]
     lib.cpm_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -270,10 +282,33 @@ class Context:
                                        self.n))
         return out
 
+    def cpm_apply_E(self, p, q=None):
+        """q = E_n p (stored neutral-equivalent form) through the solver's matvec."""
+        nrhs = int(p.shape[0]) if p.ndim == 2 else 1
+        if q is None:
+            q = np.empty((nrhs, self.n))
+        pp, kp = _ptr(p)
+        pq, kq = _ptr(q)
+        self._check(self.lib.cpm_apply_E(self.h, nrhs, pp, pq))
+        if isinstance(q, np.ndarray) and kq is not q:
+            q[...] = kq
+        return q
+
     def cpm_get_d(self):
         out = np.empty(self.n)
         self._check(self.lib.cpm_get_d(self.h, out.ctypes.data_as(ctypes.c_void_p)))
         return out
+
+    def cpm_get_precond(self):
+        """PCG-DC P in row form (Eq. 36): (off int64[n+1], idx int32[nnz], val f64[nnz])."""
+        nnz = int(self.cpm_get_info()["nnz_p"])
+        off = np.empty(self.n + 1, dtype=np.int64)
+        idx = np.empty(max(nnz, 1), dtype=np.int32)
+        val = np.empty(max(nnz, 1))
+        vp = ctypes.c_void_p
+        self._check(self.lib.cpm_get_precond(self.h, off.ctypes.data_as(vp),
+                                             idx.ctypes.data_as(vp), val.ctypes.data_as(vp)))
+        return off, idx[:nnz], val[:nnz]
 
     def cpm_get_info(self) -> dict:
         info = cpm_info_t()

@@ -166,9 +166,11 @@ void free_build(Ctx* c) {
   Buf* all[] = {&c->xyz, &c->alpha, &c->sfix, &c->hkl, &c->sqw, &c->flush, &c->chunk_end,
                 &c->Ahead, &c->A,
                 &c->E, &c->diag,
-                &c->nbr_off, &c->nbr_idx, &c->prow, &c->d};
+                &c->nbr_off, &c->nbr_idx, &c->prow, &c->d, &c->shell_k, &c->shell_inv,
+                &c->turn};
   for (Buf* b : all) buf_free(c, b);
   c->built = false;
+  c->shells_ready = false;
 }
 
 __global__ void k_inverse_tail(double* diag, int n) {
@@ -326,6 +328,28 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
     }
   }
 
+  // Product count of each tensor-core K-block (weights decrease along the table, and a
+  // K-block's products are bounded by its summed weight): the trailing blocks whose
+  // weight times 2^-7 (one BF16 product) stays within 1e-8 take one product, the blocks
+  // before them whose weight times 3 * 2^-16 (three products) stays within another 1e-8
+  // take three, the rest six.
+  {
+    std::vector<double> bw(nkb, 0.0);
+    for (int b = 0; b < nkb; ++b)
+      for (int t = 0; t < 64; ++t)
+        if (64 * (b / 2) + t < c->m) bw[b] += w[64 * (b / 2) + t];
+    const int kb0 = c->heavy_steps / 4;
+    const double budget = 1e-8;
+    int kb3 = nkb;
+    double tw = 0.0;
+    while (kb3 > kb0 && (tw + bw[kb3 - 1]) * 0x1p-7 <= budget) tw += bw[--kb3];
+    int kb6 = kb3;
+    tw = 0.0;
+    while (kb6 > kb0 && (tw + bw[kb6 - 1]) * 3 * 0x1p-16 <= budget) tw += bw[--kb6];
+    c->kb6_end = kb6;
+    c->kb3_end = kb3;
+  }
+
   const size_t a_bytes = (size_t)c->npad * 2 * c->mpad * c->esz();
   const size_t e_bytes = (size_t)n * c->ldE * c->esz();
   if ((st = buf_alloc(c, &c->xyz, (size_t)n * 3 * sizeof(double))) ||
@@ -395,13 +419,17 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
   if (tc) {
     // FP64 head (heaviest k-vectors) with the real-space, self and dipole terms, then the
     // tensor-core tail, which adds the head in its epilogue
+    cudaEvent_t ev_head;
+    cudaEventCreate(&ev_head);
+    cudaEventRecord(ev_head, s);
     st = launch_ek_head_f64((const double*)c->Ahead.ptr, c->kh, 16 * c->heavy_steps,
                             (const double*)c->xyz.ptr, (const double*)c->alpha.ptr, n, geo,
                             (double*)ehead.ptr, c->ldE, s);
     cudaEventRecord(c->ev_tc[0], s);
     if (!st)
       st = launch_ek_tc(planes[0].ptr, planes[1].ptr, planes[2].ptr, c->npad, c->mpad, n,
-                        c->heavy_steps / 4, (const uint32_t*)c->chunk_end.ptr,
+                        c->heavy_steps / 4, c->kb6_end, c->kb3_end,
+                        (const uint32_t*)c->chunk_end.ptr,
                         (const double*)ehead.ptr, c->ldE, (float*)c->E.ptr, c->ldE,
                         (int*)errbuf.ptr, s);
     cudaEventRecord(c->ev_tc[1], s);
@@ -411,6 +439,8 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
     if (!st) st = cuda_check(c, cudaStreamSynchronize(s), "tc sync");
     if (!st && herr) st = set_err(c, CPM_ECUDA, "tensor-core k-space kernel: a pipeline wait timed out");
     if (!st) cudaEventElapsedTime(&c->t_tc_ms, c->ev_tc[0], c->ev_tc[1]);
+    if (!st) cudaEventElapsedTime(&c->t_head_ms, ev_head, c->ev_tc[0]);
+    cudaEventDestroy(ev_head);
     free_tc();
   } else {
     st = launch_ek_simt(f64, c->A.ptr, c->npad, c->mpad, (const double*)c->xyz.ptr,
@@ -518,23 +548,34 @@ int cpm_potential(cpm_ctx* c, int frames, int n_ion, const double* ion_xyz,
                                   (void**)&dqs)))
     return st;
   // scratch: v [frames][2 mpad] (storage type) | v_head [frames][2 kh] | b^sol_k [frames][n]
-  const size_t vbytes = ((size_t)frames * 2 * c->mpad * c->esz() + 255) & ~size_t(255);
-  const size_t hbytes = ((size_t)frames * 2 * std::max(c->kh, 1) * sizeof(double) + 255) & ~size_t(255);
-  if ((st = buf_reserve(c, &c->ws_pot, vbytes + hbytes + (size_t)frames * n * sizeof(double))))
-    return st;
+  //          | fixed-point ion coordinates [frames][n_ion][3]
+  auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t vbytes = up((size_t)frames * 2 * c->mpad * c->esz());
+  const size_t hbytes = up((size_t)frames * 2 * std::max(c->kh, 1) * sizeof(double));
+  const size_t kbytes = up((size_t)frames * n * sizeof(double));
+  const size_t ubytes = up((size_t)frames * std::max(n_ion, 1) * 3 * sizeof(uint32_t));
+  if ((st = buf_reserve(c, &c->ws_pot, vbytes + hbytes + kbytes + ubytes))) return st;
+  if (!f64 && !c->turn.ptr) {
+    if ((st = buf_alloc(c, &c->turn, 4096 * 4 * sizeof(float)))) return st;
+    launch_turn_table(c->turn.ptr, s);
+  }
   void* v = c->ws_pot.ptr;
   double* vh = (double*)((char*)c->ws_pot.ptr + vbytes);
   double* bk = (double*)((char*)c->ws_pot.ptr + vbytes + hbytes);
+  uint32_t* sion = (uint32_t*)((char*)c->ws_pot.ptr + vbytes + hbytes + kbytes);
   if (n_ion > 0) {
-    launch_ion_structure_factor(f64, dx, dq, frames, n_ion, (const int*)c->hkl.ptr,
-                                (const double*)c->sqw.ptr, c->mpad, c->kh, c->p.box, v, vh, s);
+    launch_ion_fixed(dx, frames, n_ion, c->p.box, sion, s);
+    launch_ion_structure_factor(f64, dx, sion, dq, frames, n_ion, (const int*)c->hkl.ptr,
+                                (const double*)c->sqw.ptr, c->mpad, c->kh, c->p.box,
+                                c->turn.ptr, v, vh, s);
   } else if ((st = cuda_check(c, cudaMemsetAsync(v, 0, vbytes + hbytes, s), "v zero"))) {
     return st;
   }
   launch_bsol_kspace(f64, c->A.ptr, (const double*)c->Ahead.ptr, n, c->mpad, c->kh, v, vh,
                      frames, bk, s);
-  launch_bsol_real_and_finish(f64, (const double*)c->xyz.ptr, (const double*)c->alpha.ptr, n,
-                              dx, dq, frames, n_ion, geometry(c), dchi, bk, db, dqs, s);
+  launch_bsol_real_and_finish((const double*)c->xyz.ptr, (const double*)c->alpha.ptr,
+                              (const uint32_t*)c->sfix.ptr, n, dx, dq, sion, frames, n_ion,
+                              geometry(c), dchi, bk, db, dqs, s);
   if ((st = cuda_check(c, cudaGetLastError(), "potential kernels"))) return st;
   if (qsol_out && n_ion == 0 &&
       (st = cuda_check(c, cudaMemsetAsync(dqs, 0, frames * sizeof(double), s), "qsol zero")))
@@ -622,6 +663,21 @@ int cpm_get_E(cpm_ctx* c, int form, double* out, int64_t ld) {
   return cuda_check(c, cudaStreamSynchronize(c->stream), "get_E sync");
 }
 
+int cpm_apply_E(cpm_ctx* c, int nrhs, const double* p, double* q) {
+  if (!c) return CPM_EINVAL;
+  if (!c->built) return set_err(c, CPM_ENOTBUILT, "cpm_apply_E before cpm_build_E");
+  if (nrhs < 1 || !p || !q) return set_err(c, CPM_EINVAL, "cpm_apply_E: bad arguments");
+  const size_t bytes = (size_t)nrhs * c->n * sizeof(double);
+  const double* dp = nullptr;
+  double* dq = nullptr;
+  int st;
+  if ((st = stage_in(c, &c->ws_in0, p, bytes, (const void**)&dp))) return st;
+  if ((st = stage_out(c, &c->ws_out0, q, bytes, (void**)&dq))) return st;
+  if ((st = apply_E(c, nrhs, dp, dq))) return st;
+  if ((st = copy_out(c, q, dq, bytes))) return st;
+  return cuda_check(c, cudaStreamSynchronize(c->stream), "apply_E sync");
+}
+
 int cpm_get_d(cpm_ctx* c, double* d_out) {
   if (!c) return CPM_EINVAL;
   if (!c->built) return set_err(c, CPM_ENOTBUILT, "cpm_get_d before cpm_build_E");
@@ -630,6 +686,15 @@ int cpm_get_d(cpm_ctx* c, double* d_out) {
                                          cudaMemcpyDefault, c->stream), "get_d");
   if (st) return st;
   return cuda_check(c, cudaStreamSynchronize(c->stream), "get_d sync");
+}
+
+int cpm_get_precond(cpm_ctx* c, int64_t* off, int* idx, double* val) {
+  if (!c) return CPM_EINVAL;
+  if (!c->built) return set_err(c, CPM_ENOTBUILT, "cpm_get_precond before cpm_build_E");
+  if (c->p.precond != CPM_PRECOND_DC || !c->nbr_off.ptr)
+    return set_err(c, CPM_EINVAL, "cpm_get_precond: the context was built without PCG-DC");
+  if (!off || !idx || !val) return set_err(c, CPM_EINVAL, "cpm_get_precond: null output");
+  return copy_precond(c, off, idx, val);
 }
 
 int cpm_get_info(cpm_ctx* c, cpm_info_t* out) {
@@ -646,6 +711,13 @@ int cpm_get_info(cpm_ctx* c, cpm_info_t* out) {
   out->t_dsolve_ms = c->t_dsolve_ms;
   out->t_tc_ms = c->t_tc_ms;
   out->head_cols = 16 * c->heavy_steps;
+  out->t_matvec_ms = c->t_matvec_ms;
+  const int kb0 = c->heavy_steps / 4, kbn = 2 * c->mpad / 64;
+  const bool tc = c->built && c->p.precision == CPM_PREC_BF16X6;
+  out->tc_blocks[0] = tc ? c->kb6_end - kb0 : 0;
+  out->tc_blocks[1] = tc ? c->kb3_end - c->kb6_end : 0;
+  out->tc_blocks[2] = tc ? kbn - c->kb3_end : 0;
+  out->t_head_ms = c->t_head_ms;
   out->d_iters = c->d_iters;
   out->launches = launch_count();
   return CPM_OK;

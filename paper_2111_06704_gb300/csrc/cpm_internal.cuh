@@ -14,6 +14,34 @@ namespace cpm {
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kKe = 14.399645478;  // V A / e
 
+// sin and cos of 2 pi x for a fixed-point phase x = ph * 2^-32 (mod 1) to about one float
+// ulp.  Converting the whole 32-bit phase to float would round it by up to 2^-25 of a
+// turn (2e-7 rad); instead its top 24 bits, exact in float, go through sincospif and
+// the low 8 bits (below 2^-24 of a turn, t <= 4e-7 rad) through first order, whose
+// neglected t^2 / 2 is below 1e-13.
+__device__ __forceinline__ void sincos_turns(uint32_t ph, float* s, float* c) {
+  const int32_t p = (int32_t)ph;
+  const float hi = (float)(p >> 8) * 5.9604644775390625e-08f;  // 2^-24, in [-1/2, 1/2)
+  const float t = (float)(p & 255) * 1.4629180792671596e-09f;  // 2 pi 2^-32
+  float s0, c0;
+  sincospif(2.0f * hi, &s0, &c0);
+  *c = fmaf(-s0, t, c0);
+  *s = fmaf(c0, t, s0);
+}
+
+// (h, l) += q x for a float pair (h, l) and q = qh + ql: the product qh x is split
+// exactly (two-product) and added by an error-free two-sum, so the pair carries the sum
+// to ~1e-14 relative however many terms are added.
+__device__ __forceinline__ void pair_fma(float& h, float& l, float qh, float ql, float x) {
+  const float p = qh * x;
+  const float pe = fmaf(qh, x, -p);
+  const float s = h + p;
+  const float bb = s - h;
+  const float e = (h - (s - bb)) + (p - bb);
+  l += e + fmaf(ql, x, pe);
+  h = s;
+}
+
 struct Status {
   int code = CPM_OK;
   std::string msg;
@@ -58,6 +86,8 @@ struct Ctx {
   int kh = 0;           // head k-vectors with an FP64 operand copy (float storage only)
   Buf Ahead;            // double [npad][2*kh], same column layout as A
   Buf chunk_end;        // uint32 bit per K-block of 64 columns (tensor-core build)
+  int kb6_end = 0, kb3_end = 0;  // tensor-core K-blocks: six products before kb6_end,
+                                 // three before kb3_end, one after
   Buf A;        // float/double [npad][2*mpad]
   Buf E;        // float/double [n][ldE]
   Buf diag;     // double [2n]: diag(E_n), then its reciprocal
@@ -69,6 +99,13 @@ struct Ctx {
   int64_t nnz = 0;
   double pgap = 0;
 
+  // learned-guess feature geometry (frame independent, made on first use)
+  Buf turn;       // float4 [4096]: exp(2 pi i j / 4096) as float pairs (ion phasors)
+  Buf shell_k;    // uint8 [nnz]: neighbour shell 1..8 of each PCG-DC pattern entry, 0 = none
+  Buf shell_inv;  // float [n][8]: 1 / (atoms in shell k of atom i), 0 for an empty shell
+  double zmean = 0;
+  bool shells_ready = false;
+
   Buf d;        // double [n] neutralising vector
   double c_ele = 0;
   int d_iters = 0;
@@ -78,6 +115,8 @@ struct Ctx {
   Buf ws_solve, ws_in0, ws_in1, ws_in2, ws_out0, ws_out1, ws_pot;
 
   float t_kspace_ms = 0, t_phase_ms = 0, t_precond_ms = 0, t_dsolve_ms = 0, t_tc_ms = 0;
+  float t_matvec_ms = 0;  // last cpm_apply_E: the matvec launches alone
+  float t_head_ms = 0;    // FP64-accurate head of the tensor-core build
   cudaEvent_t ev_tc[2] = {nullptr, nullptr};
 
   bool fp64() const { return p.precision == CPM_PREC_FP64; }
@@ -118,7 +157,8 @@ int launch_ek_head_f64(const double* Ahead, int kh, int ktot, const double* xyz,
 void launch_split_bf16(const float* A, int64_t len, void* p0, void* p1, void* p2,
                        cudaStream_t s);
 int launch_ek_tc(const void* p0, const void* p1, const void* p2, int npad, int mpad, int n,
-                 int kb_begin, const uint32_t* chunk_end, const double* head, int64_t ldh,
+                 int kb_begin, int kb6_end, int kb3_end, const uint32_t* chunk_end,
+                 const double* head, int64_t ldh,
                  float* E, int64_t ldE, int* err, cudaStream_t s);
 void launch_extract_diag(bool fp64, const void* E, int n, int64_t ldE, double* diag,
                          cudaStream_t s);
@@ -127,18 +167,21 @@ void launch_get_E(bool fp64, const void* E, int n, int64_t ldE, const double* xy
                   cudaStream_t s);
 
 // potential.cu
-void launch_ion_structure_factor(bool fp64, const double* ion_xyz, const double* ion_q,
-                                 int frames, int n_ion, const int* hkl, const double* sqw,
-                                 int mpad, int kh, const double L[3], void* v, double* vhead,
-                                 cudaStream_t s);
+void launch_ion_fixed(const double* ion_xyz, int frames, int n_ion, const double L[3],
+                      uint32_t* sion, cudaStream_t s);
+void launch_turn_table(void* T, cudaStream_t s);
+void launch_ion_structure_factor(bool fp64, const double* ion_xyz, const uint32_t* sion,
+                                 const double* ion_q, int frames, int n_ion, const int* hkl,
+                                 const double* sqw, int mpad, int kh, const double L[3],
+                                 const void* turn, void* v, double* vhead, cudaStream_t s);
 void launch_bsol_kspace(bool fp64, const void* A, const double* Ahead, int n, int mpad, int kh,
                         const void* v, const double* vhead, int frames, double* bsol,
                         cudaStream_t s);
-void launch_bsol_real_and_finish(bool fp64, const double* xyz, const double* alpha, int n,
-                                 const double* ion_xyz, const double* ion_q, int frames,
-                                 int n_ion, const Geometry& geo, const double* chi,
-                                 const double* bsol_k, double* b_out, double* qsol,
-                                 cudaStream_t s);
+void launch_bsol_real_and_finish(const double* xyz, const double* alpha, const uint32_t* sfix,
+                                 int n, const double* ion_xyz, const double* ion_q,
+                                 const uint32_t* sion, int frames, int n_ion,
+                                 const Geometry& geo, const double* chi, const double* bsol_k,
+                                 double* b_out, double* qsol, cudaStream_t s);
 
 // pcg.cu
 struct SolveArgs {
@@ -155,11 +198,13 @@ struct SolveArgs {
   size_t ws_bytes = 0;
 };
 int pcg_solve(Ctx* c, const SolveArgs& a);
+int apply_E(Ctx* c, int nrhs, const double* p, double* q);  // device arrays [nrhs][n]
 void launch_neutralize(double* q, int nrhs, int n, const double* d, const double* qsol,
                        cudaStream_t s);
 
 // dc.cu
 int build_dc_preconditioner(Ctx* c);
+int copy_precond(Ctx* c, int64_t* off, int* idx, double* val);
 int apply_p_gap(Ctx* c);
 int device_sum(Ctx* c, const double* v, int64_t len, double* out);
 

@@ -29,91 +29,129 @@ __device__ __forceinline__ double dist2(const double* a, const double* b, double
 }
 
 // One warp per atom: count (fill == 0) or list (fill == 1) its neighbours in index order.
-__global__ void k_neighbours(const double* __restrict__ xyz, int n, double lx, double ly,
-                             double lz, double rc2, int* __restrict__ cnt,
-                             const int64_t* __restrict__ off, int* __restrict__ idx, int fill) {
-  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (t >= n) return;
-  const double* rt = xyz + 3 * t;
-  int c = 0;
-  for (int base = 0; base < n; base += 32) {
-    const int j = base + lane;
-    bool in = false;
-    if (j < n) in = dist2(rt, xyz + 3 * j, lx, ly, lz) <= rc2;
-    const unsigned m = __ballot_sync(0xffffffffu, in);
-    if (fill && in) idx[off[t] + c + __popc(m & ((1u << lane) - 1u))] = j;
-    c += __popc(m);
+// The candidates of a block are staged as float positions; the float minimum-image
+// distance decides every pair outside a band of +-0.01 A^2 around r_cut^2 (float
+// positions of a box below 1e4 A are off by < 1e-3 A, so the band is ample), and the
+// pairs inside it are decided by the FP64 distance, as the definition asks.
+constexpr int kNbrWarps = 8;
+constexpr int kNbrStage = 1024;
+
+__global__ void __launch_bounds__(kNbrWarps * 32)
+k_neighbours(const double* __restrict__ xyz, int n, double lx, double ly, double lz,
+             double rc2, int* __restrict__ cnt, const int64_t* __restrict__ off,
+             int* __restrict__ idx, int fill) {
+  __shared__ float4 sp[kNbrStage];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * kNbrWarps + warp;
+  const bool live = t < n;
+  const float Lx = (float)lx, Ly = (float)ly, Lz = (float)lz;
+  const float ix = (float)(1.0 / lx), iy = (float)(1.0 / ly), iz = (float)(1.0 / lz);
+  const float lo2 = (float)rc2 - 0.01f, hi2 = (float)rc2 + 0.01f;
+  float tx = 0.f, ty = 0.f, tz = 0.f;
+  if (live) {
+    tx = (float)xyz[3 * t];
+    ty = (float)xyz[3 * t + 1];
+    tz = (float)xyz[3 * t + 2];
   }
-  if (!fill && lane == 0) cnt[t] = c;
+  int c = 0;
+  for (int base = 0; base < n; base += kNbrStage) {
+    const int cj = min(kNbrStage, n - base);
+    __syncthreads();
+    for (int e = threadIdx.x; e < cj; e += blockDim.x)
+      sp[e] = make_float4((float)xyz[3 * (base + e)], (float)xyz[3 * (base + e) + 1],
+                          (float)xyz[3 * (base + e) + 2], 0.f);
+    __syncthreads();
+    if (!live) continue;
+    for (int jj = 0; jj < cj; jj += 32) {
+      const int j = base + jj + lane;
+      bool in = false;
+      if (jj + lane < cj) {
+        const float4 pj = sp[jj + lane];
+        float dx = pj.x - tx, dy = pj.y - ty, dz = pj.z - tz;
+        dx -= Lx * rintf(dx * ix);
+        dy -= Ly * rintf(dy * iy);
+        dz -= Lz * rintf(dz * iz);
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 < lo2) in = true;
+        else if (r2 <= hi2) in = dist2(xyz + 3 * t, xyz + 3 * j, lx, ly, lz) <= rc2;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, in);
+      if (fill && in) idx[off[t] + c + __popc(m & ((1u << lane) - 1u))] = j;
+      c += __popc(m);
+    }
+  }
+  if (!fill && live && lane == 0) cnt[t] = c;
 }
 
-// Column tau of M_tau^-1 (Eq. 36), written to pcol[off[tau] .. off[tau+1]).
-__global__ void __launch_bounds__(128)
+// Column tau of M_tau^-1 (Eq. 36), written to pcol[off[tau] .. off[tau+1]).  One block
+// per atom: the symmetric local matrix is filled once per pair, then Gaussian
+// elimination with partial pivoting on [M | e_tau] with one warp per row of the update,
+// then back substitution.
+constexpr int kDcThreads = 128;
+
+__global__ void __launch_bounds__(kDcThreads)
 k_dc_local(const double* __restrict__ xyz, const double* __restrict__ alpha, int n,
            double lx, double ly, double lz, double g, double rcut,
            const int64_t* __restrict__ off, const int* __restrict__ idx,
            double* __restrict__ pcol, int* __restrict__ status) {
   extern __shared__ double sm[];
+  constexpr int kWarps = kDcThreads / 32;
   const int tau = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t o = off[tau];
   const int m = (int)(off[tau + 1] - o);
   const int w = m + 1;  // augmented row width
   double* M = sm;                  // [m][m + 1]
   double* pos = sm + m * w;        // [m][3]
   __shared__ int s_piv;
-  __shared__ double s_val;
+  __shared__ double s_val, s_inv;
   for (int a = threadIdx.x; a < m; a += blockDim.x) {
     const int j = idx[o + a];
     pos[3 * a] = xyz[3 * j];
     pos[3 * a + 1] = xyz[3 * j + 1];
     pos[3 * a + 2] = xyz[3 * j + 2];
+    const double al = alpha[j];
+    M[a * w + a] = isinf(al) ? 0.0 : 0.7978845608028654 * al;  // sqrt(2/pi) alpha_i
+    M[a * w + m] = j == tau ? 1.0 : 0.0;
   }
   __syncthreads();
   const double erfc_rc = erfc(g * rcut);
   const double rc2 = rcut * rcut;
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    const int a = e / m, b = e % m;
-    double v;
-    if (a == b) {
-      const double al = alpha[idx[o + a]];
-      v = isinf(al) ? 0.0 : 0.7978845608028654 * al;  // sqrt(2/pi) alpha_i
-    } else {
+  for (int a = warp; a < m; a += kWarps)
+    for (int b = a + 1 + lane; b < m; b += 32) {
       const double r2 = dist2(pos + 3 * a, pos + 3 * b, lx, ly, lz);
+      double v = 0.0;
       if (r2 < rc2) {
         const double r = sqrt(r2);
         v = (erfc(g * r) - erfc_rc) / r;
-      } else {
-        v = 0.0;
       }
+      M[a * w + b] = v;
+      M[b * w + a] = v;
     }
-    M[a * w + b] = v;
-  }
-  for (int a = threadIdx.x; a < m; a += blockDim.x) M[a * w + m] = idx[o + a] == tau ? 1.0 : 0.0;
   __syncthreads();
-  // Gaussian elimination with partial pivoting on [M | e_tau]
   for (int k = 0; k < m; ++k) {
-    if (threadIdx.x < 32) {
+    if (warp == 0) {
       double best = -1.0;
       int bi = k;
-      for (int a = k + threadIdx.x; a < m; a += 32) {
+      for (int a = k + lane; a < m; a += 32) {
         const double v = fabs(M[a * w + k]);
         if (v > best) {
           best = v;
           bi = a;
         }
       }
-      for (int s = 16; s; s >>= 1) {
-        const double ob = __shfl_xor_sync(0xffffffffu, best, s);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, s);
+      for (int sh = 16; sh; sh >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, sh);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, sh);
         if (ob > best || (ob == best && oi < bi)) {
           best = ob;
           bi = oi;
         }
       }
-      if (threadIdx.x == 0) {
+      if (lane == 0) {
         s_piv = bi;
         s_val = best;
+        s_inv = best > 0.0 ? 1.0 / M[bi * w + k] : 0.0;
       }
     }
     __syncthreads();
@@ -122,28 +160,27 @@ k_dc_local(const double* __restrict__ xyz, const double* __restrict__ alpha, int
       return;  // singular local matrix (whole block leaves together)
     }
     const int pv = s_piv;
-    if (pv != k)
-      for (int b = threadIdx.x; b < w; b += blockDim.x) {
+    if (pv != k)  // columns left of k are already eliminated in both rows
+      for (int b = k + threadIdx.x; b < w; b += blockDim.x) {
         const double t = M[k * w + b];
         M[k * w + b] = M[pv * w + b];
         M[pv * w + b] = t;
       }
     __syncthreads();
-    const double inv = 1.0 / M[k * w + k];
-    const int rows = m - k - 1, cols = w - k - 1;
-    for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
-      const int a = k + 1 + e / cols, b = k + 1 + e % cols;
-      M[a * w + b] -= M[a * w + k] * inv * M[k * w + b];
+    const double inv = s_inv;
+    for (int a = k + 1 + warp; a < m; a += kWarps) {
+      const double f = M[a * w + k] * inv;
+      for (int b = k + 1 + lane; b < w; b += 32) M[a * w + b] -= f * M[k * w + b];
     }
     __syncthreads();
   }
   // back substitution (single warp; m is small)
-  if (threadIdx.x < 32) {
+  if (warp == 0) {
     for (int k = m - 1; k >= 0; --k) {
       double s = 0.0;
-      for (int b = k + 1 + threadIdx.x; b < m; b += 32) s += M[k * w + b] * M[b * w + m];
+      for (int b = k + 1 + lane; b < m; b += 32) s += M[k * w + b] * M[b * w + m];
       for (int o2 = 16; o2; o2 >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o2);
-      if (threadIdx.x == 0) M[k * w + m] = (M[k * w + m] - s) / M[k * w + k];
+      if (lane == 0) M[k * w + m] = (M[k * w + m] - s) / M[k * w + k];
       __syncwarp();
     }
   }
@@ -214,9 +251,10 @@ int build_dc_preconditioner(Ctx* c) {
   cudaStream_t s = c->stream;
   Buf cnt;
   if (int rc2 = buf_alloc(c, &cnt, (size_t)n * sizeof(int))) return rc2;
-  const int blocks = (n * 32 + 255) / 256;
-  (k_neighbours<<<blocks, 256, 0, s>>>((const double*)c->xyz.ptr, n, L[0], L[1], L[2], rc * rc,
-                                      (int*)cnt.ptr, nullptr, nullptr, 0), note_launch());
+  const int blocks = (n + kNbrWarps - 1) / kNbrWarps;
+  (k_neighbours<<<blocks, kNbrWarps * 32, 0, s>>>((const double*)c->xyz.ptr, n, L[0], L[1],
+                                                   L[2], rc * rc, (int*)cnt.ptr, nullptr,
+                                                   nullptr, 0), note_launch());
   std::vector<int> hc(n);
   int st = cuda_check(c, cudaMemcpyAsync(hc.data(), cnt.ptr, n * sizeof(int),
                                          cudaMemcpyDeviceToHost, s), "dc counts");
@@ -245,17 +283,19 @@ int build_dc_preconditioner(Ctx* c) {
                                      cudaMemcpyHostToDevice, s), "dc offsets");
   if (!st) st = cuda_check(c, cudaMemsetAsync(status.ptr, 0, sizeof(int), s), "dc status");
   if (!st) {
-    (k_neighbours<<<blocks, 256, 0, s>>>((const double*)c->xyz.ptr, n, L[0], L[1], L[2], rc * rc,
-                                        nullptr, (const int64_t*)c->nbr_off.ptr,
-                                        (int*)c->nbr_idx.ptr, 1), note_launch());
+    (k_neighbours<<<blocks, kNbrWarps * 32, 0, s>>>((const double*)c->xyz.ptr, n, L[0], L[1],
+                                                   L[2], rc * rc, nullptr,
+                                                   (const int64_t*)c->nbr_off.ptr,
+                                                   (int*)c->nbr_idx.ptr, 1), note_launch());
     const size_t smem = ((size_t)mx * (mx + 1) + 3 * (size_t)mx) * sizeof(double);
     st = cuda_check(c, cudaFuncSetAttribute(k_dc_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)smem), "dc smem");
     if (!st) {
-      (k_dc_local<<<n, 128, smem, s>>>((const double*)c->xyz.ptr, (const double*)c->alpha.ptr, n,
-                                      L[0], L[1], L[2], c->p.g_dc, rc,
-                                      (const int64_t*)c->nbr_off.ptr, (const int*)c->nbr_idx.ptr,
-                                      (double*)pcol.ptr, (int*)status.ptr), note_launch());
+      (k_dc_local<<<n, kDcThreads, smem, s>>>((const double*)c->xyz.ptr,
+                                              (const double*)c->alpha.ptr, n, L[0], L[1], L[2],
+                                              c->p.g_dc, rc, (const int64_t*)c->nbr_off.ptr,
+                                              (const int*)c->nbr_idx.ptr, (double*)pcol.ptr,
+                                              (int*)status.ptr), note_launch());
       (k_dc_transpose<<<n, 128, 0, s>>>(n, (const int64_t*)c->nbr_off.ptr,
                                        (const int*)c->nbr_idx.ptr, (const double*)pcol.ptr, 0.0,
                                        (double*)c->prow.ptr), note_launch());
@@ -277,6 +317,27 @@ __global__ void k_shift(double* __restrict__ v, int64_t len, double s) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
        i += (int64_t)gridDim.x * blockDim.x)
     v[i] -= s;
+}
+
+// The row form of P on its pattern, as Eq. 36 defines it (the p_gap shift taken back out).
+int copy_precond(Ctx* c, int64_t* off, int* idx, double* val) {
+  cudaStream_t s = c->stream;
+  Buf tmp;
+  int st = buf_alloc(c, &tmp, std::max<int64_t>(c->nnz, 1) * sizeof(double));
+  if (st) return st;
+  st = cuda_check(c, cudaMemcpyAsync(tmp.ptr, c->prow.ptr, c->nnz * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, s), "P copy");
+  if (!st && c->pgap != 0.0)
+    (k_shift<<<256, 256, 0, s>>>((double*)tmp.ptr, c->nnz, -c->pgap), note_launch());
+  if (!st) st = cuda_check(c, cudaMemcpyAsync(off, c->nbr_off.ptr, (c->n + 1) * sizeof(int64_t),
+                                              cudaMemcpyDefault, s), "P offsets");
+  if (!st) st = cuda_check(c, cudaMemcpyAsync(idx, c->nbr_idx.ptr, c->nnz * sizeof(int),
+                                              cudaMemcpyDefault, s), "P columns");
+  if (!st) st = cuda_check(c, cudaMemcpyAsync(val, tmp.ptr, c->nnz * sizeof(double),
+                                              cudaMemcpyDefault, s), "P values");
+  if (!st) st = cuda_check(c, cudaStreamSynchronize(s), "P sync");
+  buf_free(c, &tmp);
+  return st;
 }
 
 // p_gap of Eq. 37 from C^ele = 1^T E^-1 1; stored as prow -= p_gap on the pattern.

@@ -1,0 +1,490 @@
+// Learned initial guess: per-atom features, a 32 -> 64 -> 64 -> 64 -> 1 SiLU network
+// (forward, gradient, Adam), and the guess q0 = q_prev + scale * net(features).
+//
+// The paper has no learned component; the network and its features are the project's
+// definition (see the FP64 oracle for the same definition written out).  Parameters are
+// FP32 master values; with `bf16` set the forward and gradient use them rounded to BF16
+// (FP32 accumulation throughout).
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include "cpm_internal.cuh"
+
+namespace cpm {
+
+namespace {
+
+constexpr int kF = CPM_MLP_FEATURES;  // 32
+constexpr int kH = 64;
+constexpr int kP = CPM_MLP_PARAMS;    // 10,497
+// parameter offsets: W1 [64][32], b1, W2 [64][64], b2, W3 [64][64], b3, W4 [64], b4
+constexpr int oW1 = 0, ob1 = oW1 + kH * kF, oW2 = ob1 + kH, ob2 = oW2 + kH * kH,
+              oW3 = ob2 + kH, ob3 = oW3 + kH * kH, oW4 = ob3 + kH, ob4 = oW4 + kH;
+static_assert(ob4 + 1 == kP, "parameter layout");
+
+__device__ __forceinline__ float silu(float z) { return z / (1.0f + expf(-z)); }
+__device__ __forceinline__ float silu_grad(float z) {
+  const float s = 1.0f / (1.0f + expf(-z));
+  return s * (1.0f + z * (1.0f - s));
+}
+
+// Shell of every PCG-DC pattern entry (k - 1/2 <= r < k + 1/2, k = 1..8; 0 outside or
+// for the atom itself) and the inverse shell populations; the electrode is fixed, so this
+// geometry is made once and every frame only sums potentials.
+__global__ void k_shell_table(int n, const double* __restrict__ xyz, double lx, double ly,
+                              double lz, const int64_t* __restrict__ off,
+                              const int* __restrict__ idx, uint8_t* __restrict__ shell,
+                              float* __restrict__ inv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int cnt[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) cnt[k] = 0;
+  const double xi = xyz[3 * i], yi = xyz[3 * i + 1], zi = xyz[3 * i + 2];
+  for (int64_t e = off[i]; e < off[i + 1]; ++e) {
+    const int j = idx[e];
+    int k = 0;
+    if (j != i) {
+      double dx = xyz[3 * j] - xi, dy = xyz[3 * j + 1] - yi, dz = xyz[3 * j + 2] - zi;
+      dx -= lx * rint(dx / lx);
+      dy -= ly * rint(dy / ly);
+      dz -= lz * rint(dz / lz);
+      k = (int)floor(sqrt(dx * dx + dy * dy + dz * dz) + 0.5);
+      if (k < 1 || k > 8) k = 0;
+    }
+    shell[e] = (uint8_t)k;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) cnt[q] += k == q + 1;
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) inv[(int64_t)i * 8 + k] = cnt[k] ? 1.0f / (float)cnt[k] : 0.f;
+}
+
+// Features of atom i in frame f (unscaled): 0 the potential change b - b_prev, 1-8 its
+// shell means, 9 b, 10-17 the shell means of b, 18 chi, 19 the side of the electrode
+// (+1 above the mean height), 20-31 zero.
+__global__ void k_guess_features(int n, int frames, const double* __restrict__ b,
+                                 const double* __restrict__ b_prev,
+                                 const double* __restrict__ chi,
+                                 const double* __restrict__ xyz, double zmean,
+                                 const int64_t* __restrict__ off, const int* __restrict__ idx,
+                                 const uint8_t* __restrict__ shell,
+                                 const float* __restrict__ inv, float* __restrict__ feat) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int f = blockIdx.y;
+  if (i >= n || f >= frames) return;
+  const double* bf = b + (int64_t)f * n;
+  const double* pf = b_prev + (int64_t)f * n;
+  double sd[8], sb[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) sd[k] = sb[k] = 0.0;
+  for (int64_t e = off[i]; e < off[i + 1]; ++e) {
+    const int k = shell[e];
+    if (!k) continue;
+    const int j = idx[e];
+    const double bj = bf[j], dj = bj - pf[j];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (k == q + 1) {
+        sd[q] += dj;
+        sb[q] += bj;
+      }
+  }
+  float* out = feat + ((int64_t)f * n + i) * kF;
+  const float* w = inv + (int64_t)i * 8;
+  out[0] = (float)(bf[i] - pf[i]);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    out[1 + k] = (float)(sd[k] * (double)w[k]);
+    out[10 + k] = (float)(sb[k] * (double)w[k]);
+  }
+  out[9] = (float)bf[i];
+  out[18] = (float)chi[i];
+  out[19] = xyz[3 * i + 2] > zmean ? 1.f : -1.f;
+#pragma unroll
+  for (int c = 20; c < kF; ++c) out[c] = 0.f;
+}
+
+__device__ void load_params(const float* __restrict__ params, float* w, int bf16) {
+  for (int k = threadIdx.x; k < kP; k += blockDim.x) {
+    const float v = params[k];
+    w[k] = bf16 ? __bfloat162float(__float2bfloat16_rn(v)) : v;
+  }
+}
+
+// y[s] = net((feat[s] - mean) * inv_std), 128 samples per tile.  Weights (transposed,
+// unit index fastest) and the activations of a tile (feature-major) sit in shared memory;
+// each thread owns 8 samples x 4 units of a layer, so every float4 of weights and of
+// activations it loads feeds 32 (or 16) FMAs.  The float4 slot of an activation row is
+// XOR-swizzled with the row's unit group, which keeps the transposed stores of a layer's
+// output free of bank conflicts.
+constexpr int kTs = 128;          // samples per tile
+constexpr int kFwdThreads = 256;  // 16 unit groups x 16 sample groups
+constexpr int kWT = kP + 3;       // transposed weights, padded to a float4 boundary
+constexpr size_t kFwdSmem = sizeof(float) * (kWT + 2 * kH * kTs);
+
+__device__ __forceinline__ int act_at(int row, int s) {
+  return row * kTs + 4 * ((s >> 2) ^ ((row >> 2) & 7)) + (s & 3);
+}
+
+// out[a][s] = silu(bias[a] + sum_c WT[c][a] in[c][s]) for this thread's 8 x 4 block.
+template <int NIN>
+__device__ __forceinline__ void fwd_layer(const float* __restrict__ WT,
+                                          const float* __restrict__ bias,
+                                          const float* __restrict__ in, float (&acc)[8][4],
+                                          int ug, int sg) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[k][j] = bias[4 * ug + j];
+#pragma unroll 8
+  for (int c = 0; c < NIN; ++c) {
+    const float4 w = *reinterpret_cast<const float4*>(WT + c * kH + 4 * ug);
+    const float4 x0 = *reinterpret_cast<const float4*>(in + act_at(c, 8 * sg));
+    const float4 x1 = *reinterpret_cast<const float4*>(in + act_at(c, 8 * sg + 4));
+    const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+    const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[k][j] = fmaf(xv[k], wv[j], acc[k][j]);
+  }
+}
+
+__device__ __forceinline__ void fwd_store(float* __restrict__ out, const float (&acc)[8][4],
+                                          int ug, int sg) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int row = 4 * ug + j;
+    *reinterpret_cast<float4*>(out + act_at(row, 8 * sg)) =
+        make_float4(silu(acc[0][j]), silu(acc[1][j]), silu(acc[2][j]), silu(acc[3][j]));
+    *reinterpret_cast<float4*>(out + act_at(row, 8 * sg + 4)) =
+        make_float4(silu(acc[4][j]), silu(acc[5][j]), silu(acc[6][j]), silu(acc[7][j]));
+  }
+}
+
+__global__ void __launch_bounds__(kFwdThreads, 2)
+k_mlp_forward(const float* __restrict__ params, const float* __restrict__ norm, int bf16,
+              int64_t samples, const float* __restrict__ feat, float* __restrict__ out) {
+  extern __shared__ __align__(16) float fsm[];
+  float* WT1 = fsm;               // [kF][kH]
+  float* WT2 = WT1 + kF * kH;     // [kH][kH]
+  float* WT3 = WT2 + kH * kH;     // [kH][kH]
+  float* bv = WT3 + kH * kH;      // b1, b2, b3, W4 [kH each], b4
+  float* act0 = fsm + kWT;        // [kH][kTs]
+  float* act1 = act0 + kH * kTs;  // [kH][kTs]
+  const int t = threadIdx.x;
+  for (int e = t; e < kP; e += kFwdThreads) {
+    float v = params[e];
+    if (bf16) v = __bfloat162float(__float2bfloat16_rn(v));
+    int d;
+    if (e < ob1) d = (e % kF) * kH + e / kF;                                  // W1[a][c]
+    else if (e < oW2) d = kF * kH + 2 * kH * kH + (e - ob1);                 // b1
+    else if (e < ob2) d = kF * kH + ((e - oW2) % kH) * kH + (e - oW2) / kH;  // W2
+    else if (e < oW3) d = kF * kH + 2 * kH * kH + kH + (e - ob2);            // b2
+    else if (e < ob3) d = kF * kH + kH * kH + ((e - oW3) % kH) * kH + (e - oW3) / kH;
+    else if (e < oW4) d = kF * kH + 2 * kH * kH + 2 * kH + (e - ob3);        // b3
+    else d = kF * kH + 2 * kH * kH + 3 * kH + (e - oW4);                     // W4, b4
+    fsm[d] = v;
+  }
+  const int ug = t & 15, sg = t >> 4;
+  const int64_t tiles = (samples + kTs - 1) / kTs;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t s0 = tile * kTs;
+    __syncthreads();  // weights written / the previous tile's reads of act0 done
+    for (int e = t; e < kTs * kF; e += kFwdThreads) {
+      const int s = e / kF, c = e % kF;
+      const int64_t gs = s0 + s;
+      act0[act_at(c, s)] = gs < samples ? (feat[gs * kF + c] - norm[c]) * norm[kF + c] : 0.f;
+    }
+    __syncthreads();
+    float acc[8][4];
+    fwd_layer<kF>(WT1, bv, act0, acc, ug, sg);
+    fwd_store(act1, acc, ug, sg);
+    __syncthreads();
+    fwd_layer<kH>(WT2, bv + kH, act1, acc, ug, sg);
+    __syncthreads();  // all reads of act0 (the features) are done
+    fwd_store(act0, acc, ug, sg);
+    __syncthreads();
+    fwd_layer<kH>(WT3, bv + 2 * kH, act0, acc, ug, sg);
+    // output unit: y = b4 + sum_a W4[a] silu(z3[a]), summed over the 16 unit groups
+    float y[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      float v = 0.f;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v = fmaf(bv[3 * kH + 4 * ug + j], silu(acc[k][j]), v);
+#pragma unroll
+      for (int o = 1; o < 16; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      y[k] = v + bv[4 * kH];
+    }
+    if (ug == 0)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int64_t gs = s0 + 8 * sg + k;
+        if (gs < samples) out[gs] = y[k];
+      }
+  }
+}
+
+// Gradient of the mean squared error (1/S) sum_s (y_s - t_s)^2 over this call's samples,
+// accumulated into grad (zeroed by the caller); loss_sum accumulates sum (y - t)^2.
+// One block = 128 samples; activations of the block in shared memory; the parameter
+// gradients are reductions over the block's samples, then one atomic add per parameter.
+constexpr int kB = 128;
+constexpr int kLd = kH + 1;  // padded row of a [sample][unit] array
+
+__global__ void __launch_bounds__(kB, 1)
+k_mlp_grad(const float* __restrict__ params, const float* __restrict__ norm, int bf16,
+           int64_t samples, double inv_s, const float* __restrict__ feat,
+           const float* __restrict__ target, float* __restrict__ grad,
+           double* __restrict__ loss_sum) {
+  extern __shared__ float sm[];
+  float* w = sm;                       // kP
+  float* X = w + kP;                   // [kB][kF + 1]
+  float* Z1 = X + kB * (kF + 1);       // pre-activations, later dL/dz
+  float* Z2 = Z1 + kB * kLd;
+  float* Z3 = Z2 + kB * kLd;
+  float* H1 = Z3 + kB * kLd;           // silu(Z1)
+  float* H2 = H1 + kB * kLd;           // silu(Z2)
+  float* DY = H2 + kB * kLd;           // [kB]
+  load_params(params, w, bf16);
+  __syncthreads();
+  const int t = threadIdx.x;
+  const int64_t s = blockIdx.x * (int64_t)kB + t;
+  const bool valid = s < samples;
+  // ---- forward, one sample per thread
+  {
+    float* x = X + t * (kF + 1);
+    for (int c = 0; c < kF; ++c)
+      x[c] = valid ? (feat[s * kF + c] - norm[c]) * norm[kF + c] : 0.f;
+    for (int a = 0; a < kH; ++a) {
+      float z = w[ob1 + a];
+      for (int c = 0; c < kF; ++c) z = fmaf(w[oW1 + a * kF + c], x[c], z);
+      Z1[t * kLd + a] = z;
+      H1[t * kLd + a] = silu(z);
+    }
+    for (int a = 0; a < kH; ++a) {
+      float z = w[ob2 + a];
+      for (int c = 0; c < kH; ++c) z = fmaf(w[oW2 + a * kH + c], H1[t * kLd + c], z);
+      Z2[t * kLd + a] = z;
+      H2[t * kLd + a] = silu(z);
+    }
+    float y = w[ob4];
+    for (int a = 0; a < kH; ++a) {
+      float z = w[ob3 + a];
+      for (int c = 0; c < kH; ++c) z = fmaf(w[oW3 + a * kH + c], H2[t * kLd + c], z);
+      Z3[t * kLd + a] = z;
+      y = fmaf(w[oW4 + a], silu(z), y);
+    }
+    const float diff = valid ? y - target[s] : 0.f;
+    DY[t] = (float)(2.0 * inv_s) * diff;
+    double l = (double)diff * (double)diff;
+    for (int o = 16; o; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    if ((t & 31) == 0) atomicAdd(loss_sum, l);
+  }
+  __syncthreads();
+  // ---- output layer: dW4[a] = sum_s dy_s h3[s][a]; db4 = sum_s dy_s
+  if (t < kH) {
+    float acc = 0.f;
+    for (int q = 0; q < kB; ++q) acc = fmaf(DY[q], silu(Z3[q * kLd + t]), acc);
+    atomicAdd(&grad[oW4 + t], acc);
+  } else if (t == kH) {
+    float acc = 0.f;
+    for (int q = 0; q < kB; ++q) acc += DY[q];
+    atomicAdd(&grad[ob4], acc);
+  }
+  __syncthreads();
+  // g3 = dy W4 * silu'(z3), in place of Z3
+  for (int a = 0; a < kH; ++a) Z3[t * kLd + a] = DY[t] * w[oW4 + a] * silu_grad(Z3[t * kLd + a]);
+  __syncthreads();
+  // ---- hidden layers: dW = sum_s g_s h_in_s^T, db = sum_s g_s, then g_in = W^T g * silu'
+  auto layer = [&](float* G, const float* Hin, int nin, int ow, int ob) {
+    // 64 x nin outputs over kB threads
+    const int per = kH * nin / kB;
+    for (int u = 0; u < per; ++u) {
+      const int e = t * per + u;
+      const int a = e / nin, c = e % nin;
+      float acc = 0.f;
+      for (int q = 0; q < kB; ++q) {
+        const float hv = nin == kF ? Hin[q * (kF + 1) + c] : Hin[q * kLd + c];
+        acc = fmaf(G[q * kLd + a], hv, acc);
+      }
+      atomicAdd(&grad[ow + a * nin + c], acc);
+    }
+    if (t < kH) {
+      float acc = 0.f;
+      for (int q = 0; q < kB; ++q) acc += G[q * kLd + t];
+      atomicAdd(&grad[ob + t], acc);
+    }
+  };
+  layer(Z3, H2, kH, oW3, ob3);
+  // g2 = W3^T g3 * silu'(z2), in place of Z2
+  {
+    float g[kH];
+    for (int c = 0; c < kH; ++c) {
+      float acc = 0.f;
+      for (int a = 0; a < kH; ++a) acc = fmaf(w[oW3 + a * kH + c], Z3[t * kLd + a], acc);
+      g[c] = acc * silu_grad(Z2[t * kLd + c]);
+    }
+    __syncthreads();  // every thread has finished reading Z2 through `layer`
+    for (int c = 0; c < kH; ++c) Z2[t * kLd + c] = g[c];
+  }
+  __syncthreads();
+  layer(Z2, H1, kH, oW2, ob2);
+  {
+    float g[kH];
+    for (int c = 0; c < kH; ++c) {
+      float acc = 0.f;
+      for (int a = 0; a < kH; ++a) acc = fmaf(w[oW2 + a * kH + c], Z2[t * kLd + a], acc);
+      g[c] = acc * silu_grad(Z1[t * kLd + c]);
+    }
+    __syncthreads();
+    for (int c = 0; c < kH; ++c) Z1[t * kLd + c] = g[c];
+  }
+  __syncthreads();
+  layer(Z1, X, kF, oW1, ob1);
+}
+
+__global__ void k_adam(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                       const float* __restrict__ g, int n, float lr, float c1, float c2) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const float gk = g[k];
+  const float mk = 0.9f * m[k] + 0.1f * gk;
+  const float vk = 0.999f * v[k] + 0.001f * gk * gk;
+  m[k] = mk;
+  v[k] = vk;
+  p[k] -= lr * (mk * c1) / (sqrtf(vk * c2) + 1e-8f);
+}
+
+__global__ void k_guess_apply(int64_t len, const float* __restrict__ y, float scale,
+                              const double* __restrict__ q_prev, double* __restrict__ q0) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < len;
+       k += (int64_t)gridDim.x * blockDim.x)
+    q0[k] = q_prev[k] + (double)scale * (double)y[k];
+}
+
+bool on_device(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+constexpr size_t kGradSmem =
+    sizeof(float) * (kP + kB * (kF + 1) + 5 * kB * kLd + kB);
+
+}  // namespace
+}  // namespace cpm
+
+using namespace cpm;
+
+struct cpm_ctx : public cpm::Ctx {};
+
+extern "C" {
+
+int cpm_guess_features(cpm_ctx* c, int frames, const double* b, const double* b_prev,
+                       const double* chi, float* feat) {
+  if (!c) return CPM_EINVAL;
+  if (!c->built) return set_err(c, CPM_ENOTBUILT, "cpm_guess_features before cpm_build_E");
+  if (c->p.precond != CPM_PRECOND_DC || !c->nbr_off.ptr)
+    return set_err(c, CPM_EINVAL, "cpm_guess_features needs the PCG-DC neighbour lists");
+  if (frames < 1 || !on_device(b) || !on_device(b_prev) || !on_device(chi) || !on_device(feat))
+    return set_err(c, CPM_EINVAL, "cpm_guess_features: frames >= 1 and device arrays");
+  int st = CPM_OK;
+  if (!c->shells_ready) {  // frame-independent geometry, once per electrode
+    std::vector<double> hx(3 * (size_t)c->n);
+    st = cuda_check(c, cudaMemcpyAsync(hx.data(), c->xyz.ptr, hx.size() * sizeof(double),
+                                       cudaMemcpyDeviceToHost, c->stream), "xyz");
+    if (!st) st = cuda_check(c, cudaStreamSynchronize(c->stream), "xyz sync");
+    if (!st) st = buf_alloc(c, &c->shell_k, std::max<int64_t>(c->nnz, 1));
+    if (!st) st = buf_alloc(c, &c->shell_inv, 8 * sizeof(float) * (size_t)c->n);
+    if (st) return st;
+    double zm = 0.0;
+    for (int i = 0; i < c->n; ++i) zm += hx[3 * i + 2];
+    c->zmean = zm / c->n;
+    (k_shell_table<<<(c->n + 127) / 128, 128, 0, c->stream>>>(
+         c->n, (const double*)c->xyz.ptr, c->p.box[0], c->p.box[1], c->p.box[2],
+         (const int64_t*)c->nbr_off.ptr, (const int*)c->nbr_idx.ptr, (uint8_t*)c->shell_k.ptr,
+         (float*)c->shell_inv.ptr), note_launch());
+    if ((st = cuda_check(c, cudaGetLastError(), "shell table"))) return st;
+    c->shells_ready = true;
+  }
+  dim3 grid((c->n + 127) / 128, frames);
+  (k_guess_features<<<grid, 128, 0, c->stream>>>(
+      c->n, frames, b, b_prev, chi, (const double*)c->xyz.ptr, c->zmean,
+      (const int64_t*)c->nbr_off.ptr, (const int*)c->nbr_idx.ptr,
+      (const uint8_t*)c->shell_k.ptr, (const float*)c->shell_inv.ptr, feat), note_launch());
+  if ((st = cuda_check(c, cudaGetLastError(), "features"))) return st;
+  return cuda_check(c, cudaStreamSynchronize(c->stream), "features sync");
+}
+
+int cpm_mlp_forward(cpm_ctx* c, const float* params, const float* norm, int bf16,
+                    int64_t samples, const float* feat, float* out) {
+  if (!c) return CPM_EINVAL;
+  if (samples < 1 || !on_device(params) || !on_device(norm) || !on_device(feat) ||
+      !on_device(out))
+    return set_err(c, CPM_EINVAL, "cpm_mlp_forward: samples >= 1 and device arrays");
+  int st = cuda_check(c, cudaFuncSetAttribute(k_mlp_forward,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)kFwdSmem), "forward smem");
+  if (st) return st;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  const int64_t tiles = (samples + kTs - 1) / kTs;
+  const int blocks = (int)std::min<int64_t>(tiles, 2 * (int64_t)std::max(sms, 1));
+  (k_mlp_forward<<<blocks, kFwdThreads, kFwdSmem, c->stream>>>(params, norm, bf16, samples,
+                                                               feat, out), note_launch());
+  if ((st = cuda_check(c, cudaGetLastError(), "forward"))) return st;
+  return cuda_check(c, cudaStreamSynchronize(c->stream), "forward sync");
+}
+
+int cpm_mlp_grad(cpm_ctx* c, const float* params, const float* norm, int bf16,
+                 int64_t samples, const float* feat, const float* target, float* grad,
+                 double* loss) {
+  if (!c) return CPM_EINVAL;
+  if (samples < 1 || !on_device(params) || !on_device(norm) || !on_device(feat) ||
+      !on_device(target) || !on_device(grad) || !on_device(loss))
+    return set_err(c, CPM_EINVAL, "cpm_mlp_grad: samples >= 1 and device arrays");
+  int st = cuda_check(c, cudaMemsetAsync(grad, 0, kP * sizeof(float), c->stream), "grad zero");
+  if (!st) st = cuda_check(c, cudaMemsetAsync(loss, 0, sizeof(double), c->stream), "loss zero");
+  if (!st) st = cuda_check(c, cudaFuncSetAttribute(k_mlp_grad,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)kGradSmem), "grad smem");
+  if (st) return st;
+  const int64_t blocks = (samples + kB - 1) / kB;
+  (k_mlp_grad<<<(unsigned)blocks, kB, kGradSmem, c->stream>>>(
+      params, norm, bf16, samples, 1.0 / (double)samples, feat, target, grad, loss), note_launch());
+  if ((st = cuda_check(c, cudaGetLastError(), "grad"))) return st;
+  return cuda_check(c, cudaStreamSynchronize(c->stream), "grad sync");
+}
+
+int cpm_mlp_adam(cpm_ctx* c, float* params, float* m, float* v, const float* grad, int step,
+                 float lr) {
+  if (!c) return CPM_EINVAL;
+  if (step < 1 || !on_device(params) || !on_device(m) || !on_device(v) || !on_device(grad))
+    return set_err(c, CPM_EINVAL, "cpm_mlp_adam: step >= 1 and device arrays");
+  const float c1 = 1.0f / (1.0f - powf(0.9f, (float)step));
+  const float c2 = 1.0f / (1.0f - powf(0.999f, (float)step));
+  (k_adam<<<(kP + 255) / 256, 256, 0, c->stream>>>(params, m, v, grad, kP, lr, c1, c2), note_launch());
+  return cuda_check(c, cudaGetLastError(), "adam");
+}
+
+int cpm_guess_apply(cpm_ctx* c, int64_t len, const float* y, float scale, const double* q_prev,
+                    double* q0) {
+  if (!c) return CPM_EINVAL;
+  if (len < 1 || !on_device(y) || !on_device(q_prev) || !on_device(q0))
+    return set_err(c, CPM_EINVAL, "cpm_guess_apply: len >= 1 and device arrays");
+  (k_guess_apply<<<256, 256, 0, c->stream>>>(len, y, scale, q_prev, q0), note_launch());
+  int st = cuda_check(c, cudaGetLastError(), "guess apply");
+  if (st) return st;
+  return cuda_check(c, cudaStreamSynchronize(c->stream), "guess sync");
+}
+
+}  // extern "C"

@@ -59,9 +59,8 @@ __global__ void k_structure_operand_f32(const uint32_t* __restrict__ sfix, int n
   for (int i = blockIdx.y; i < npad; i += gridDim.y) {
     float c = 0.f, s = 0.f;
     if (i < n) {
-      uint32_t ph = h * sfix[3 * i] + kk * sfix[3 * i + 1] + l * sfix[3 * i + 2];
-      float f = (float)(int32_t)ph * 2.3283064365386963e-10f;  // 2^-32, f in [-1/2, 1/2)
-      sincospif(2.0f * f, &s, &c);
+      const uint32_t ph = h * sfix[3 * i] + kk * sfix[3 * i + 1] + l * sfix[3 * i + 2];
+      sincos_turns(ph, &s, &c);
       c *= w;
       s *= w;
     }
@@ -302,6 +301,80 @@ k_ek_simt(const T* __restrict__ A, int64_t lda, int ktot, T* __restrict__ E, int
   }
 }
 
+// Head of the k-space sum in float-float arithmetic (lower-triangle 64 x 64 tiles, 4 x 4
+// outputs per thread): each FP64 operand value is split into a float pair a = ah + al,
+// and each term
+//   a_i a_j = ah*bh (exact: rounded product plus its fma remainder) + ah*bl + al*bh
+// (al*bl is below 2^-48 of the product) is added to a float pair (hi, lo) per output
+// with an error-free two-sum.  About 11 float operations per term instead of one FP64
+// FMA, which runs at 1/64 of the float rate on this GPU.  The epilogue adds the
+// real-space, self and dipole terms in FP64 and writes the FP64 head matrix.
+__global__ void __launch_bounds__(256)
+k_ek_head_ff(const double* __restrict__ A, int64_t lda, int ktot, double* __restrict__ Eh,
+             int64_t ldE, Epi ep) {
+  constexpr int BM = 64, BK = 16, TM = 4, LD = BM + 4;
+  __shared__ __align__(16) float Ah[BK][LD], Al[BK][LD], Bh[BK][LD], Bl[BK][LD];
+  int I, J;
+  tri_tile(blockIdx.x, I, J);
+  const int i0 = I * BM, j0 = J * BM;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int lrow = tid >> 2, lk = (tid & 3) * 4;
+  float sh[TM][TM], sl[TM][TM];
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+#pragma unroll
+    for (int b = 0; b < TM; ++b) sh[a][b] = sl[a][b] = 0.f;
+  const double* pa = A + (int64_t)(i0 + lrow) * lda + lk;
+  const double* pb = A + (int64_t)(j0 + lrow) * lda + lk;
+  for (int k0 = 0; k0 < ktot; k0 += BK) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const double x = pa[k0 + v], y = pb[k0 + v];
+      const float xh = (float)x, yh = (float)y;
+      Ah[lk + v][lrow] = xh;
+      Al[lk + v][lrow] = (float)(x - (double)xh);
+      Bh[lk + v][lrow] = yh;
+      Bl[lk + v][lrow] = (float)(y - (double)yh);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < BK; ++kk) {
+      float ah[TM], al[TM], bh[TM], bl[TM];
+#pragma unroll
+      for (int u = 0; u < TM; ++u) {
+        ah[u] = Ah[kk][ty * 4 + u];
+        al[u] = Al[kk][ty * 4 + u];
+        bh[u] = Bh[kk][tx * 4 + u];
+        bl[u] = Bl[kk][tx * 4 + u];
+      }
+#pragma unroll
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < TM; ++b) {
+          const float p = ah[a] * bh[b];
+          const float pe = fmaf(ah[a], bh[b], -p);
+          const float s = sh[a][b] + p;
+          const float bb = s - sh[a][b];
+          const float e2 = (sh[a][b] - (s - bb)) + (p - bb);
+          sl[a][b] = fmaf(al[a], bh[b], fmaf(ah[a], bl[b], sl[a][b] + (e2 + pe)));
+          sh[a][b] = s;
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < TM; ++a) {
+    const int i = i0 + ty * 4 + a;
+#pragma unroll
+    for (int b = 0; b < TM; ++b) {
+      const int j = j0 + tx * 4 + b;
+      if (i >= ep.n || j >= ep.n || j > i) continue;
+      Eh[(int64_t)i * ldE + j] =
+          (double)sh[a][b] + (double)sl[a][b] + epilogue_terms(ep, i, j);
+    }
+  }
+}
+
 template <typename T>
 __global__ void k_mirror_lower(T* __restrict__ E, int n, int64_t ldE) {
   __shared__ T tile[32][33];
@@ -426,8 +499,8 @@ int launch_ek_head_f64(const double* Ahead, int kh, int ktot, const double* xyz,
   constexpr int BM = 64;
   const int nt = (n + BM - 1) / BM;
   const int tiles = nt * (nt + 1) / 2;
-  (k_ek_simt<double, BM, 4, false><<<tiles, 256, 0, s>>>(Ahead, 2 * (int64_t)kh, ktot, Ehead,
-                                                          ldE, ep, 0, nullptr), note_launch());
+  (k_ek_head_ff<<<tiles, 256, 0, s>>>(Ahead, 2 * (int64_t)kh, ktot, Ehead, ldE, ep),
+   note_launch());
   return cudaGetLastError() == cudaSuccess ? CPM_OK : CPM_ECUDA;
 }
 

@@ -10,6 +10,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "cpm_internal.cuh"
@@ -57,22 +58,15 @@ __device__ void block_sum(double (&v)[NV], double* sm /* [32*NV] */) {
   __syncthreads();
 }
 
-// q[r] = E p[r] for NR columns starting at column c0, one warp per row, plus the
-// per-block partial of p^T q.
-// FP32 E: p is held as a float pair p = hi + lo (to ~1e-14).  Each product e * hi is
-// split exactly into its float value and rounding error (fma(e, hi, -e*hi)) and the
-// running float sum is an error-free two-sum, so over each 8-element stretch the float
-// value plus the float error term carry the exact sum; both go to FP64.  The stored
-// float E is thus applied to ~1e-14, not to float rounding of every product and sum --
-// otherwise PCG converges to the solution of a slightly different matrix (1e-6 of q at
-// the 512-atom cell) -- while E is still streamed once in 4-byte words.
-template <typename T, int NR>
+// FP64 E (the plain baseline build): q[r] = E p[r] for NR columns from c0, one warp per
+// row with FP64 products and sums, plus the per-block partial of p^T q.
+template <int NR>
 __global__ void __launch_bounds__(kThreads)
-k_matvec(const T* __restrict__ E, int64_t ldE, int n, const T* __restrict__ pv,
-         const T* __restrict__ plo, const double* __restrict__ p64, int64_t ldv, int c0,
-         int nrhs, double* __restrict__ q, double* __restrict__ pq_part) {
+k_matvec_f64(const double* __restrict__ E, int64_t ldE, int n, const double* __restrict__ pv,
+             int64_t ldv, int c0, int nrhs, double* __restrict__ q,
+             double* __restrict__ pq_part) {
   __shared__ double sm[32 * NR];
-  constexpr int VEC = 16 / sizeof(T);
+  c0 += blockIdx.y * NR;  // one column group per grid row
   const int lane = threadIdx.x & 31;
   const int wid = blockIdx.x * kMvWarps + (threadIdx.x >> 5);
   const int nwarps = gridDim.x * kMvWarps;
@@ -80,68 +74,137 @@ k_matvec(const T* __restrict__ E, int64_t ldE, int n, const T* __restrict__ pv,
 #pragma unroll
   for (int r = 0; r < NR; ++r) pq[r] = 0.0;
   for (int row = wid; row < n; row += nwarps) {
-    const T* e = E + (int64_t)row * ldE;
-    double acc[NR];
+    const double* e = E + (int64_t)row * ldE;
+    double acc[NR][2];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) acc[r] = 0.0;
-    for (int64_t c = lane * VEC; c < ldE; c += 8 * 32 * VEC) {
+    for (int r = 0; r < NR; ++r) acc[r][0] = acc[r][1] = 0.0;
+    for (int64_t c = lane * 2; c < ldE; c += 64) {
+      const double2 ev = __ldg(reinterpret_cast<const double2*>(e + c));
 #pragma unroll
-      for (int u2 = 0; u2 < 4; ++u2) {
-        T part[NR], perr[NR];
-#pragma unroll
-        for (int r = 0; r < NR; ++r) part[r] = perr[r] = T(0);
-#pragma unroll
-        for (int u = 2 * u2; u < 2 * u2 + 2; ++u) {
-          const int64_t cc = c + (int64_t)u * 32 * VEC;
-          if (cc < ldE) {
-            T ev[VEC];
-            *reinterpret_cast<float4*>(ev) = __ldg(reinterpret_cast<const float4*>(e + cc));
-#pragma unroll
-            for (int r = 0; r < NR; ++r) {
-              if (c0 + r < nrhs) {
-                T hv[VEC];
-                const int64_t o = (int64_t)(c0 + r) * ldv + cc;
-                *reinterpret_cast<float4*>(hv) = *reinterpret_cast<const float4*>(pv + o);
-                if (plo) {
-                  T lv[VEC];
-                  *reinterpret_cast<float4*>(lv) = *reinterpret_cast<const float4*>(plo + o);
-#pragma unroll
-                  for (int w = 0; w < VEC; ++w) {
-                    // exact product (two-product) and exact running sum (two-sum):
-                    // every float rounding error lands in perr
-                    const T pr = ev[w] * hv[w];
-                    const T s = part[r] + pr;
-                    const T bb = s - part[r];
-                    const T e2 = (part[r] - (s - bb)) + (pr - bb);
-                    perr[r] = fma(ev[w], lv[w], perr[r] + fma(ev[w], hv[w], -pr) + e2);
-                    part[r] = s;
-                  }
-                } else {
-#pragma unroll
-                  for (int w = 0; w < VEC; ++w) part[r] = fma(ev[w], hv[w], part[r]);
-                }
-              }
-            }
-          }
-        }
-#pragma unroll
-        for (int r = 0; r < NR; ++r) acc[r] += (double)part[r] + (double)perr[r];
+      for (int r = 0; r < NR; ++r) {
+        const double2 hv = *reinterpret_cast<const double2*>(pv + (int64_t)(c0 + r) * ldv + c);
+        acc[r][0] = fma(ev.x, hv.x, acc[r][0]);
+        acc[r][1] = fma(ev.y, hv.y, acc[r][1]);
       }
     }
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-      double s = warp_sum(acc[r]);
-      if (lane == 0 && c0 + r < nrhs) {
-        q[(int64_t)(c0 + r) * ldv + row] = s;
-        pq[r] += s * p64[(int64_t)(c0 + r) * ldv + row];
+      const double s = warp_sum(acc[r][0] + acc[r][1]);
+      if (lane == 0) {
+        const int64_t o = (int64_t)(c0 + r) * ldv + row;
+        q[o] = s;
+        pq[r] += s * pv[o];
       }
     }
   }
   block_sum<NR>(pq, sm);
   if (threadIdx.x == 0)
 #pragma unroll
-    for (int r = 0; r < NR; ++r)
-      if (c0 + r < nrhs) pq_part[(int64_t)blockIdx.x * nrhs + c0 + r] = pq[r];
+    for (int r = 0; r < NR; ++r) pq_part[(int64_t)blockIdx.x * nrhs + c0 + r] = pq[r];
+}
+
+// Float pair (hi, lo) += (bh, bl): the high parts meet in an error-free two-sum, the low
+// parts (already ~2^-24 of the high ones) in one rounded add.
+__device__ __forceinline__ void pair_add(float& hi, float& lo, float bh, float bl) {
+  const float s = hi + bh;
+  const float bb = s - hi;
+  const float e = (hi - (s - bb)) + (bh - bb);
+  lo = lo + bl + e;
+  hi = s;
+}
+
+// FP32 E, the path every float build takes: q[r] = E p[r] for NR columns from c0 and the
+// per-block partial of p^T q.  A block owns kMvRows rows; its eight warps split the
+// padded row into 128-column groups (one float4 per lane), so each float4 of the
+// direction pair (hi, lo) is loaded once per group and used for all kMvRows rows, and
+// the grid has n / kMvRows blocks of equal work for the scheduler to balance.  Products
+// and the running sum are error-free (two-product, two-sum, one chain per row and column
+// per lane), so the stored float E is applied to ~1e-14 rather than to float rounding of
+// every product and sum -- otherwise PCG converges to the solution of a slightly
+// different matrix (1e-6 of q at the 512-atom cell); lanes and warps combine float pairs, and only the final
+// per-row value goes to FP64 -- FP64 runs at 1/64 of the FP32 rate here.  E is read
+// with the streaming hint so the direction stays resident in L2.
+constexpr int kMvRows = 4;
+
+template <int NR>
+__global__ void __launch_bounds__(kThreads)
+k_matvec_f32(const float* __restrict__ E, int64_t ldE, int n, const float* __restrict__ pv,
+             const float* __restrict__ plo, const double* __restrict__ p64, int64_t ldv,
+             int c0, int nrhs, double* __restrict__ q, double* __restrict__ pq_part) {
+  constexpr int RB = kMvRows;
+  c0 += blockIdx.y * NR;  // one column group per grid row
+  __shared__ float2 sm[kMvWarps][RB * NR];
+  __shared__ double spq[RB * NR];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int row0 = blockIdx.x * RB;
+  const int ngroups = (int)(ldE >> 7);
+  const float* erow[RB];
+#pragma unroll
+  for (int i = 0; i < RB; ++i) erow[i] = E + (int64_t)min(row0 + i, n - 1) * ldE;
+  float part[RB][NR], perr[RB][NR];
+#pragma unroll
+  for (int i = 0; i < RB; ++i)
+#pragma unroll
+    for (int r = 0; r < NR; ++r) part[i][r] = perr[i][r] = 0.f;
+  for (int g = warp; g < ngroups; g += kMvWarps) {
+    const int64_t cc = (int64_t)g * 128 + lane * 4;
+    float ev[RB][4];
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+      *reinterpret_cast<float4*>(ev[i]) = __ldcs(reinterpret_cast<const float4*>(erow[i] + cc));
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const int64_t o = (int64_t)(c0 + r) * ldv + cc;
+      float hv[4], lv[4];
+      *reinterpret_cast<float4*>(hv) = __ldg(reinterpret_cast<const float4*>(pv + o));
+      *reinterpret_cast<float4*>(lv) = __ldg(reinterpret_cast<const float4*>(plo + o));
+#pragma unroll
+      for (int i = 0; i < RB; ++i)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          const float e = ev[i][w];
+          const float pr = e * hv[w];
+          const float s = part[i][r] + pr;
+          const float bb = s - part[i][r];
+          const float e2 = (part[i][r] - (s - bb)) + (pr - bb);
+          perr[i][r] = fmaf(e, lv[w], perr[i][r] + (fmaf(e, hv[w], -pr) + e2));
+          part[i][r] = s;
+        }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < RB; ++i)
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      float h = part[i][r], l = perr[i][r];
+#pragma unroll
+      for (int o = 16; o; o >>= 1)
+        pair_add(h, l, __shfl_xor_sync(0xffffffffu, h, o), __shfl_xor_sync(0xffffffffu, l, o));
+      if (lane == 0) sm[warp][i * NR + r] = make_float2(h, l);
+    }
+  __syncthreads();
+  const int t = threadIdx.x;
+  if (t < RB * NR) {
+    float h = sm[0][t].x, l = sm[0][t].y;
+#pragma unroll
+    for (int w = 1; w < kMvWarps; ++w) pair_add(h, l, sm[w][t].x, sm[w][t].y);
+    const int i = t / NR, r = t % NR, row = row0 + i;
+    double pq = 0.0;
+    if (row < n) {
+      const int64_t o = (int64_t)(c0 + r) * ldv + row;
+      const double v = (double)h + (double)l;
+      q[o] = v;
+      pq = v * p64[o];
+    }
+    spq[t] = pq;
+  }
+  __syncthreads();
+  if (t < NR) {
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < RB; ++i) s += spq[i * NR + t];
+    pq_part[(int64_t)blockIdx.x * nrhs + c0 + t] = s;
+  }
 }
 
 // alpha = r^T z / p^T q for every running column.
@@ -393,33 +456,54 @@ int sm_count(int device) {
   return v > 0 ? v : 1;
 }
 
+// Number of per-block p^T q partials a matvec writes (the block count of its launches).
+int matvec_parts(const Ctx* c) {
+  if (c->fp64()) return std::max(1, std::min((c->n + kMvWarps - 1) / kMvWarps, 4 * sm_count(c->device)));
+  return (c->n + kMvRows - 1) / kMvRows;
+}
+
 template <typename T>
 void launch_matvec(const Ctx* c, const void* pv, const void* plo, const double* p64,
-                   int64_t ldv, int nrhs, double* q, double* pq_part, int gm) {
-  const T* E = (const T*)c->E.ptr;
-  const T* hi = (const T*)pv;
-  const T* lo = (const T*)plo;
-  for (int c0 = 0; c0 < nrhs; c0 += 4) {
-    int left = nrhs - c0;
-    if (left >= 8) {  // eight columns per pass over E
-      (k_matvec<T, 8><<<gm, kThreads, 0, c->stream>>>(E, c->ldE, c->n, hi, lo, p64, ldv, c0,
-                                                     nrhs, q, pq_part), note_launch());
-      c0 += 4;
-      continue;
-    }
-    if (left >= 4)
-      (k_matvec<T, 4><<<gm, kThreads, 0, c->stream>>>(E, c->ldE, c->n, hi, lo, p64, ldv, c0,
-                                                     nrhs, q, pq_part), note_launch());
-    else if (left >= 2)
-      (k_matvec<T, 2><<<gm, kThreads, 0, c->stream>>>(E, c->ldE, c->n, hi, lo, p64, ldv, c0,
-                                                     nrhs, q, pq_part), note_launch());
-    else
-      (k_matvec<T, 1><<<gm, kThreads, 0, c->stream>>>(E, c->ldE, c->n, hi, lo, p64, ldv, c0,
-                                                     nrhs, q, pq_part), note_launch());
-    if (left == 3)  // the NR=2 launch above covered two of three columns
-      (k_matvec<T, 1><<<gm, kThreads, 0, c->stream>>>(E, c->ldE, c->n, hi, lo, p64, ldv,
-                                                     c0 + 2, nrhs, q, pq_part), note_launch());
+                   int64_t ldv, int nrhs, double* q, double* pq_part, int gm);
+
+// Launches KERNEL<NR> over all nrhs columns: full groups of four columns as grid rows of
+// one launch, then a pair and a single column for the remainder.
+template <typename Launch>
+void for_column_groups(int nrhs, Launch&& launch) {
+  const int groups = nrhs / 4;
+  for (int g0 = 0; g0 < groups; g0 += 65535)
+    launch(std::integral_constant<int, 4>(), 4 * g0, std::min(groups - g0, 65535));
+  int c0 = 4 * groups;
+  if (nrhs - c0 >= 2) {
+    launch(std::integral_constant<int, 2>(), c0, 1);
+    c0 += 2;
   }
+  if (nrhs - c0 == 1) launch(std::integral_constant<int, 1>(), c0, 1);
+}
+
+// FP64 storage (the plain baseline build): one warp per row, FP64 products and sums.
+template <>
+void launch_matvec<double>(const Ctx* c, const void* pv, const void*, const double*,
+                           int64_t ldv, int nrhs, double* q, double* pq_part, int gm) {
+  const double* E = (const double*)c->E.ptr;
+  const double* hi = (const double*)pv;
+  for_column_groups(nrhs, [&](auto nr, int c0, int ny) {
+    (k_matvec_f64<decltype(nr)::value><<<dim3(gm, ny), kThreads, 0, c->stream>>>(
+         E, c->ldE, c->n, hi, ldv, c0, nrhs, q, pq_part), note_launch());
+  });
+}
+
+// FP32 storage: k_matvec_f32, four columns per pass over E.
+template <>
+void launch_matvec<float>(const Ctx* c, const void* pv, const void* plo, const double* p64,
+                          int64_t ldv, int nrhs, double* q, double* pq_part, int gm) {
+  const float* E = (const float*)c->E.ptr;
+  const float* hi = (const float*)pv;
+  const float* lo = (const float*)plo;
+  for_column_groups(nrhs, [&](auto nr, int c0, int ny) {
+    (k_matvec_f32<decltype(nr)::value><<<dim3(gm, ny), kThreads, 0, c->stream>>>(
+         E, c->ldE, c->n, hi, lo, p64, ldv, c0, nrhs, q, pq_part), note_launch());
+  });
 }
 
 }  // namespace
@@ -431,7 +515,7 @@ int pcg_solve(Ctx* c, const SolveArgs& a) {
   // elementwise kernels: ge blocks per right-hand side, one grid row per right-hand side
   const int ge = std::max(1, std::min((n + kThreads - 1) / kThreads, 2 * sms));
   const dim3 g2(ge, nrhs);
-  const int gm = std::max(1, std::min((n + kMvWarps - 1) / kMvWarps, 2 * sms));
+  const int gm = matvec_parts(c);  // p^T q partials per column
   const int pre = c->p.precond;
   const bool f64 = c->fp64();
   const size_t vbytes = (size_t)nrhs * ldv * sizeof(double);
@@ -571,6 +655,53 @@ int pcg_solve(Ctx* c, const SolveArgs& a) {
   }
   if (status == CPM_EBREAKDOWN) return set_err(c, status, "PCG breakdown (p^T E p <= 0 or non-finite)");
   if (status == CPM_ENOCONV) return set_err(c, status, "PCG reached maxit before tol");
+  return CPM_OK;
+}
+
+// q = E_n p for nrhs columns (device arrays [nrhs][n]) through the solver's matvec; the
+// matvec launches alone are timed with events on the context's stream (t_matvec_ms).
+int apply_E(Ctx* c, int nrhs, const double* p_in, double* q_out) {
+  const int n = c->n;
+  const int64_t ldv = c->ldE;
+  const bool f64 = c->fp64();
+  const int sms = sm_count(c->device);
+  const int ge = std::max(1, std::min((n + kThreads - 1) / kThreads, 2 * sms));
+  const int gm = matvec_parts(c);  // p^T q partials per column
+  const size_t vbytes = ((size_t)nrhs * ldv * sizeof(double) + 255) & ~size_t(255);
+  const size_t hbytes = ((f64 ? 1 : 2) * (size_t)nrhs * ldv * c->esz() + 255) & ~size_t(255);
+  const size_t pqbytes = (size_t)gm * nrhs * sizeof(double);
+  const size_t need = 3 * vbytes + hbytes + pqbytes + 2 * nrhs * sizeof(ColState);
+  int rc = buf_reserve(c, &c->ws_solve, need);
+  if (rc) return rc;
+  char* base = (char*)c->ws_solve.ptr;
+  double* p = (double*)base;
+  double* q = (double*)(base + vbytes);
+  double* zin = (double*)(base + 2 * vbytes);
+  void* pv = base + 3 * vbytes;
+  float* plo = f64 ? nullptr : (float*)pv + (size_t)nrhs * ldv;
+  double* pq_part = (double*)(base + 3 * vbytes + hbytes);
+  ColState* st = (ColState*)(base + 3 * vbytes + hbytes + pqbytes);
+  cudaStream_t s = c->stream;
+  if (cuda_check(c, cudaMemsetAsync(base, 0, 3 * vbytes + hbytes, s), "memset")) return CPM_ECUDA;
+  for (int col = 0; col < nrhs; ++col)
+    if (cuda_check(c, cudaMemcpyAsync(zin + (int64_t)col * ldv, p_in + (int64_t)col * n,
+                                      n * sizeof(double), cudaMemcpyDeviceToDevice, s), "p in"))
+      return CPM_ECUDA;
+  const dim3 g2(ge, nrhs);
+  // first = 1: p = zin, and its float pair
+  if (f64) (k_p_update<double><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, st, zin, p, (double*)pv, nullptr, 1), note_launch());
+  else (k_p_update<float><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, st, zin, p, (float*)pv, plo, 1), note_launch());
+  cudaEventRecord(c->ev_tc[0], s);
+  if (f64) launch_matvec<double>(c, pv, nullptr, p, ldv, nrhs, q, pq_part, gm);
+  else launch_matvec<float>(c, pv, plo, p, ldv, nrhs, q, pq_part, gm);
+  cudaEventRecord(c->ev_tc[1], s);
+  if (cuda_check(c, cudaGetLastError(), "apply_E")) return CPM_ECUDA;
+  for (int col = 0; col < nrhs; ++col)
+    if (cuda_check(c, cudaMemcpyAsync(q_out + (int64_t)col * n, q + (int64_t)col * ldv,
+                                      n * sizeof(double), cudaMemcpyDeviceToDevice, s), "q out"))
+      return CPM_ECUDA;
+  if (cuda_check(c, cudaStreamSynchronize(s), "apply_E sync")) return CPM_ECUDA;
+  cudaEventElapsedTime(&c->t_matvec_ms, c->ev_tc[0], c->ev_tc[1]);
   return CPM_OK;
 }
 

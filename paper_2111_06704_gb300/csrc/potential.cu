@@ -9,6 +9,8 @@
 // over the images within the cutoff.
 #include <math.h>
 
+#include <algorithm>
+
 #include "cpm_internal.cuh"
 
 namespace cpm {
@@ -18,16 +20,159 @@ namespace {
 constexpr int kSfThreads = 128;
 constexpr int kIonChunk = 256;
 
+// Fractional ion coordinates in 2^-32 fixed point, once per ion and frame: the phases of
+// every k-vector and the real-space screening use them.
+__global__ void k_ion_fixed(const double* __restrict__ ion_xyz, int64_t count, double lx,
+                            double ly, double lz, uint32_t* __restrict__ sion) {
+  const double L[3] = {lx, ly, lz};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 3 * count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double s = ion_xyz[e] / L[e % 3];
+    s -= floor(s);
+    sion[e] = (uint32_t)((unsigned long long)llrint(s * 4294967296.0) & 0xffffffffull);
+  }
+}
+
+// exp(2 pi i j / 4096), j < 4096, as float pairs (cos hi, cos lo, sin hi, sin lo).
+__global__ void k_turn_table(float4* __restrict__ T) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= 4096) return;
+  double s, c;
+  sincospi(j / 2048.0, &s, &c);
+  const float ch = (float)c, sh = (float)s;
+  T[j] = make_float4(ch, (float)(c - ch), sh, (float)(s - sh));
+}
+
+// a * b for float pairs, to ~2^-44 relative (the lo * lo term dropped).
+__device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, float& ph,
+                                       float& pl) {
+  ph = ah * bh;
+  pl = fmaf(ah, bh, -ph) + fmaf(ah, bl, al * bh);
+}
+
+// a + b for float pairs (two-sum of the high parts).
+__device__ __forceinline__ void ff_add(float ah, float al, float bh, float bl, float& sh,
+                                       float& sl) {
+  const float s = ah + bh;
+  const float bb = s - ah;
+  sl = ((ah - (s - bb)) + (bh - bb)) + (al + bl);
+  sh = s;
+}
+
+// exp(2 pi i ph 2^-32) as float pairs, to ~1e-13: the top 12 bits of the phase index the
+// exact table, the low 20 bits give an angle t < 2 pi 2^-12 whose sine and cosine follow
+// from their Taylor series (t - t^3/6, 1 - t^2/2 + t^4/24; the next terms are below
+// 1e-16), and the two rotations are multiplied in float pairs.
+__device__ __forceinline__ void phasor_ff(uint32_t ph, const float4* __restrict__ T, float& ch,
+                                          float& cl, float& sh, float& sl) {
+  const float4 t4 = __ldg(T + (ph >> 20));
+  const float low = (float)(ph & 0xFFFFFu);
+  constexpr float kCh = 1.462918119976564e-09f;   // 2 pi 2^-32, high part
+  constexpr float kCl = -4.070940267922164e-17f;  // and the rest
+  const float th = low * kCh;
+  const float tl = fmaf(low, kCh, -th) + low * kCl;
+  const float p = th * th;
+  const float pe = fmaf(th, th, -p) + 2.0f * th * tl;
+  // cos t = 1 - t^2/2 + t^4/24
+  const float half = 0.5f * p;
+  const float c0 = 1.0f - half;
+  const float c0l = ((1.0f - c0) - half) - 0.5f * pe + p * p * (1.0f / 24.0f);
+  // sin t = t - t^3/6
+  const float t3 = th * p * (1.0f / 6.0f);
+  const float s0 = th - t3;
+  const float s0l = ((th - s0) - t3) + tl;
+  // (Tc + i Ts)(c0 + i s0)
+  float ah, al, bh, bl;
+  ff_mul(t4.x, t4.y, c0, c0l, ah, al);
+  ff_mul(t4.z, t4.w, s0, s0l, bh, bl);
+  ff_add(ah, al, -bh, -bl, ch, cl);
+  ff_mul(t4.z, t4.w, c0, c0l, ah, al);
+  ff_mul(t4.x, t4.y, s0, s0l, bh, bl);
+  ff_add(ah, al, bh, bl, sh, sl);
+}
+
 // v[f][c(k)] = sqrt(W_k) sum_I q_I cos(theta_Ik), v[f][c(k) + 64] = sqrt(W_k) sum_I q_I sin,
-// in the column layout of the electrode operand, c(k) = 128 (k / 64) + k % 64.
-// FP32 path: exact fixed-point phases, sincospif, charge-weighted sums in FP64.
-template <bool FP64>
+// in the column layout of the electrode operand, c(k) = 128 (k / 64) + k % 64, from the
+// exact fixed-point phases.  Sums over the ions run in error-free float pairs (S_K is a
+// sum of O(n_ion) unit phasors whose float partial sums would lose bits; FP64 runs at
+// 1/64 of the float rate here).  The tail k-vectors take float sin/cos (sincos_turns,
+// about one ulp); the head (k < kh, the heaviest weights) takes float-pair phasors and
+// goes out in FP64 to vhead for the FP64 head contraction.
 __global__ void __launch_bounds__(kSfThreads)
-k_ion_sf(const double* __restrict__ ion_xyz, const double* __restrict__ ion_q, int n_ion,
-         const int* __restrict__ hkl, const double* __restrict__ sqw, int mpad, int kh,
-         double lx, double ly, double lz, void* __restrict__ vout,
-         double* __restrict__ vhead) {
+k_ion_sf_f32(const uint32_t* __restrict__ sion, const double* __restrict__ ion_q, int n_ion,
+             const int* __restrict__ hkl, const double* __restrict__ sqw, int mpad, int kh,
+             const float4* __restrict__ turn, float* __restrict__ vout,
+             double* __restrict__ vhead) {
   __shared__ uint32_t sf[kIonChunk][3];
+  __shared__ float sqh[kIonChunk], sql[kIonChunk];
+  const int f = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t* fx = sion + (size_t)f * n_ion * 3;
+  const double* q = ion_q + (size_t)f * n_ion;
+  uint32_t h = 0, kk = 0, l = 0;
+  if (k < mpad) {
+    h = (uint32_t)hkl[3 * k];
+    kk = (uint32_t)hkl[3 * k + 1];
+    l = (uint32_t)hkl[3 * k + 2];
+  }
+  const bool head = k < kh;  // whole blocks take one branch unless they straddle kh
+  float reh = 0.f, rel = 0.f, imh = 0.f, iml = 0.f;
+  for (int base = 0; base < n_ion; base += kIonChunk) {
+    const int cnt = min(kIonChunk, n_ion - base);
+    __syncthreads();
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+      sf[t][0] = fx[3 * (base + t)];
+      sf[t][1] = fx[3 * (base + t) + 1];
+      sf[t][2] = fx[3 * (base + t) + 2];
+      const double qv = q[base + t];
+      sqh[t] = (float)qv;
+      sql[t] = (float)(qv - (double)sqh[t]);
+    }
+    __syncthreads();
+    if (k >= mpad) continue;
+    if (head) {
+      for (int t = 0; t < cnt; ++t) {
+        const uint32_t ph = h * sf[t][0] + kk * sf[t][1] + l * sf[t][2];
+        float ch, cl, sh, sl, ph_, pl_;
+        phasor_ff(ph, turn, ch, cl, sh, sl);
+        ff_mul(sqh[t], sql[t], ch, cl, ph_, pl_);
+        ff_add(reh, rel, ph_, pl_, reh, rel);
+        ff_mul(sqh[t], sql[t], sh, sl, ph_, pl_);
+        ff_add(imh, iml, ph_, pl_, imh, iml);
+      }
+    } else {
+      for (int t = 0; t < cnt; ++t) {
+        const uint32_t ph = h * sf[t][0] + kk * sf[t][1] + l * sf[t][2];
+        float s, c;
+        sincos_turns(ph, &s, &c);
+        pair_fma(reh, rel, sqh[t], sql[t], c);
+        pair_fma(imh, iml, sqh[t], sql[t], s);
+      }
+    }
+  }
+  if (k >= mpad) return;
+  const double re = (double)reh + (double)rel, im = (double)imh + (double)iml;
+  const double w = sqw[k];
+  const size_t kcol = 128 * (size_t)(k >> 6) + (k & 63);  // operand column layout
+  float* v = vout + (size_t)f * 2 * mpad;
+  if (head) {  // FP64 values for the FP64 head contraction; zero float columns
+    double* vh = vhead + (size_t)f * 2 * kh;
+    vh[kcol] = w * re;
+    vh[kcol + 64] = w * im;
+    v[kcol] = 0.f;
+    v[kcol + 64] = 0.f;
+  } else {
+    v[kcol] = (float)(w * re);
+    v[kcol + 64] = (float)(w * im);
+  }
+}
+
+// FP64 storage (the plain baseline build): the same sums with FP64 phases, sincospi and
+// FP64 accumulation.
+__global__ void __launch_bounds__(kSfThreads)
+k_ion_sf_f64(const double* __restrict__ ion_xyz, const double* __restrict__ ion_q, int n_ion,
+             const int* __restrict__ hkl, const double* __restrict__ sqw, int mpad, double lx,
+             double ly, double lz, double* __restrict__ vout) {
   __shared__ double sd[kIonChunk][3];
   __shared__ double sq[kIonChunk];
   const int f = blockIdx.y;
@@ -48,95 +193,70 @@ k_ion_sf(const double* __restrict__ ion_xyz, const double* __restrict__ ion_q, i
       const double L[3] = {lx, ly, lz};
       for (int d = 0; d < 3; ++d) {
         double s = xyz[3 * (base + t) + d] / L[d];
-        s -= floor(s);
-        sd[t][d] = s;
-        unsigned long long u = (unsigned long long)llrint(s * 4294967296.0);
-        sf[t][d] = (uint32_t)(u & 0xffffffffull);
+        sd[t][d] = s - floor(s);
       }
       sq[t] = q[base + t];
     }
     __syncthreads();
-    if (k < mpad) {
-      if (FP64 || k < kh) {
-        for (int t = 0; t < cnt; ++t) {
-          double fr = h * sd[t][0] + kk * sd[t][1] + l * sd[t][2];
-          fr -= rint(fr);
-          double s, c;
-          sincospi(2.0 * fr, &s, &c);
-          re += sq[t] * c;
-          im += sq[t] * s;
-        }
-      } else {
-        for (int t = 0; t < cnt; ++t) {
-          uint32_t ph = (uint32_t)h * sf[t][0] + (uint32_t)kk * sf[t][1] +
-                        (uint32_t)l * sf[t][2];
-          float fr = (float)(int32_t)ph * 2.3283064365386963e-10f;
-          float s, c;
-          sincospif(2.0f * fr, &s, &c);
-          // float cos/sin, summed over the ions in double: S_K is a sum of O(n_ion)
-          // unit phasors whose partial sums would otherwise lose float bits
-          re = fma(sq[t], (double)c, re);
-          im = fma(sq[t], (double)s, im);
-        }
-      }
+    if (k >= mpad) continue;
+    for (int t = 0; t < cnt; ++t) {
+      double fr = h * sd[t][0] + kk * sd[t][1] + l * sd[t][2];
+      fr -= rint(fr);
+      double s, c;
+      sincospi(2.0 * fr, &s, &c);
+      re += sq[t] * c;
+      im += sq[t] * s;
     }
   }
-  if (k < mpad) {
-    const double w = sqw[k];
-    const size_t kcol = 128 * (size_t)(k >> 6) + (k & 63);  // operand column layout
-    if (!FP64 && k < kh) {
-      // head k-vectors: FP64 values for the FP64 head contraction; zero float columns
-      double* vh = vhead + (size_t)f * 2 * kh;
-      vh[kcol] = w * re;
-      vh[kcol + 64] = w * im;
-      float* v = (float*)vout + (size_t)f * 2 * mpad;
-      v[kcol] = 0.f;
-      v[kcol + 64] = 0.f;
-    } else if (FP64) {
-      double* v = (double*)vout + (size_t)f * 2 * mpad;
-      v[kcol] = w * re;
-      v[kcol + 64] = w * im;
-    } else {
-      float* v = (float*)vout + (size_t)f * 2 * mpad;
-      v[kcol] = (float)(w * re);
-      v[kcol + 64] = (float)(w * im);
-    }
-  }
+  if (k >= mpad) return;
+  const double w = sqw[k];
+  const size_t kcol = 128 * (size_t)(k >> 6) + (k & 63);
+  double* v = vout + (size_t)f * 2 * mpad;
+  v[kcol] = w * re;
+  v[kcol + 64] = w * im;
 }
 
-// b^sol_k[f][i] = sum_c A[i][c] v[f][c]: one warp per electrode row, up to 4 frames per
-// pass (A row read once per pass).  FP32: float products, 8-term float partials
-// summed in FP64.
+// b^sol_k[f][i] = sum_c A[i][c] v[f][c]: one warp per electrode row and NF frames per
+// grid row (the A row is read once per NF frames).  Float storage: 4-term float partials
+// summed in error-free float pairs; FP64 storage: FP64 throughout.
 template <typename T, int NF>
 __global__ void __launch_bounds__(256)
 k_bsol_kspace(const T* __restrict__ A, int n, int64_t lda, const T* __restrict__ v,
-              int frames, int f0, double* __restrict__ bsol, int accumulate) {
+              int frames, double* __restrict__ bsol, int accumulate) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
+  const int f0 = blockIdx.y * NF;
   if (warp >= n) return;
   const T* a = A + (int64_t)warp * lda;
   constexpr int VEC = 16 / sizeof(T);
-  double acc[NF];
+  T hi[NF], lo[NF];
 #pragma unroll
-  for (int r = 0; r < NF; ++r) acc[r] = 0.0;
+  for (int r = 0; r < NF; ++r) hi[r] = lo[r] = T(0);
   for (int64_t c = lane * VEC; c < lda; c += 32 * VEC) {
     T av[VEC];
-    *reinterpret_cast<float4*>(av) = *reinterpret_cast<const float4*>(a + c);
+    *reinterpret_cast<float4*>(av) = __ldg(reinterpret_cast<const float4*>(a + c));
 #pragma unroll
     for (int r = 0; r < NF; ++r) {
       if (f0 + r >= frames) break;
       T vv[VEC];
       *reinterpret_cast<float4*>(vv) =
-          *reinterpret_cast<const float4*>(v + (int64_t)(f0 + r) * lda + c);
+          __ldg(reinterpret_cast<const float4*>(v + (int64_t)(f0 + r) * lda + c));
       T s = T(0);
 #pragma unroll
       for (int u = 0; u < VEC; ++u) s = fma(av[u], vv[u], s);
-      acc[r] += (double)s;
+      if constexpr (sizeof(T) == 4) {
+        const float t = hi[r] + s;
+        const float bb = t - hi[r];
+        lo[r] += (hi[r] - (t - bb)) + (s - bb);
+        hi[r] = t;
+      } else {
+        hi[r] += s;
+      }
     }
   }
 #pragma unroll
   for (int r = 0; r < NF; ++r) {
-    double x = acc[r];
+    double x = (double)hi[r] + (double)lo[r];
     for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     if (lane == 0 && f0 + r < frames) {
       double* dst = bsol + (int64_t)(f0 + r) * n + warp;
@@ -146,29 +266,43 @@ k_bsol_kspace(const T* __restrict__ A, int n, int64_t lda, const T* __restrict__
 }
 
 // Real-space electrode-ion sums, slab dipole term, and b = chi - k_e b^sol.
-// One thread per electrode atom; ions staged through shared memory.
+// One thread per electrode atom; ions staged through shared memory.  Every image of a
+// pair is at least as far as its nearest one, so a pair whose nearest-image distance is
+// beyond r_cut contributes nothing: that distance is screened in float from the exact
+// fixed-point coordinate difference (off by < 1e-3 A^2 in r^2, against a band of
+// 0.01 A^2), and only the pairs that pass are summed in FP64 over their images.
 __global__ void __launch_bounds__(128)
-k_bsol_real(const double* __restrict__ xyz, const double* __restrict__ alpha, int n,
-            const double* __restrict__ ion_xyz, const double* __restrict__ ion_q, int n_ion,
+k_bsol_real(const double* __restrict__ xyz, const double* __restrict__ alpha,
+            const uint32_t* __restrict__ sfix, int n, const double* __restrict__ ion_xyz,
+            const double* __restrict__ ion_q, const uint32_t* __restrict__ sion, int n_ion,
             double lx, double ly, double lz, double g, double rc, double dip,
             const double* __restrict__ chi, const double* __restrict__ bsol_k,
             double* __restrict__ b_out, double* __restrict__ qsol) {
   __shared__ double sx[kIonChunk][4];
+  __shared__ uint32_t su[kIonChunk][3];
   const int f = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const double* ix = ion_xyz + (size_t)f * n_ion * 3;
   const double* iq = ion_q + (size_t)f * n_ion;
+  const uint32_t* iu = sion + (size_t)f * n_ion * 3;
   double ri[3] = {0, 0, 0}, ai = INFINITY;
+  uint32_t ui[3] = {0, 0, 0};
   if (i < n) {
     ri[0] = xyz[3 * i];
     ri[1] = xyz[3 * i + 1];
     ri[2] = xyz[3 * i + 2];
+    ui[0] = sfix[3 * i];
+    ui[1] = sfix[3 * i + 1];
+    ui[2] = sfix[3 * i + 2];
     ai = alpha[i];
   }
   const double L[3] = {lx, ly, lz};
   const double rc2 = rc * rc;
   const double invL[3] = {1.0 / lx, 1.0 / ly, 1.0 / lz};
   const bool single[3] = {2.0 * rc < lx, 2.0 * rc < ly, 2.0 * rc < lz};
+  const float fs[3] = {(float)(lx * 0x1p-32), (float)(ly * 0x1p-32), (float)(lz * 0x1p-32)};
+  const float screen2 = (float)rc2 + 0.01f;
+  // sum q_I z_I and sum q_I over the frame: each thread takes the ions it stages
   double acc = 0.0, qz = 0.0, qs = 0.0;
   for (int base = 0; base < n_ion; base += kIonChunk) {
     const int cnt = min(kIonChunk, n_ion - base);
@@ -178,13 +312,23 @@ k_bsol_real(const double* __restrict__ xyz, const double* __restrict__ alpha, in
       sx[t][1] = ix[3 * (base + t) + 1];
       sx[t][2] = ix[3 * (base + t) + 2];
       sx[t][3] = iq[base + t];
+      su[t][0] = iu[3 * (base + t)];
+      su[t][1] = iu[3 * (base + t) + 1];
+      su[t][2] = iu[3 * (base + t) + 2];
+      qz += sx[t][3] * sx[t][2];
+      qs += sx[t][3];
     }
     __syncthreads();
+    if (i >= n) continue;
     for (int t = 0; t < cnt; ++t) {
+      float m2 = 0.f;
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const float du = (float)(int32_t)(ui[u] - su[t][u]) * fs[u];  // nearest image
+        m2 = fmaf(du, du, m2);
+      }
+      if (m2 >= screen2) continue;
       const double qI = sx[t][3];
-      qz += qI * sx[t][2];
-      qs += qI;
-      if (i >= n) continue;
       double d[3] = {ri[0] - sx[t][0], ri[1] - sx[t][1], ri[2] - sx[t][2]};
       int lo[3], hi[3];
       for (int u = 0; u < 3; ++u) {
@@ -217,6 +361,18 @@ k_bsol_real(const double* __restrict__ xyz, const double* __restrict__ alpha, in
       }
     }
   }
+  __shared__ double red[2][4];
+  for (int o = 16; o; o >>= 1) {
+    qz += __shfl_xor_sync(0xffffffffu, qz, o);
+    qs += __shfl_xor_sync(0xffffffffu, qs, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = qz;
+    red[1][threadIdx.x >> 5] = qs;
+  }
+  __syncthreads();
+  qz = red[0][0] + red[0][1] + red[0][2] + red[0][3];
+  qs = red[1][0] + red[1][1] + red[1][2] + red[1][3];
   if (i < n) {
     double bs = bsol_k[(size_t)f * n + i] + acc + dip * ri[2] * qz;
     b_out[(size_t)f * n + i] = chi[i] - kKe * bs;
@@ -226,17 +382,28 @@ k_bsol_real(const double* __restrict__ xyz, const double* __restrict__ alpha, in
 
 }  // namespace
 
-void launch_ion_structure_factor(bool fp64, const double* ion_xyz, const double* ion_q,
-                                 int frames, int n_ion, const int* hkl, const double* sqw,
-                                 int mpad, int kh, const double L[3], void* v, double* vhead,
-                                 cudaStream_t s) {
+void launch_ion_fixed(const double* ion_xyz, int frames, int n_ion, const double L[3],
+                      uint32_t* sion, cudaStream_t s) {
+  const int64_t count = (int64_t)frames * n_ion;
+  const int blocks = (int)std::min<int64_t>((3 * count + 255) / 256, 4096);
+  (k_ion_fixed<<<blocks, 256, 0, s>>>(ion_xyz, count, L[0], L[1], L[2], sion), note_launch());
+}
+
+void launch_turn_table(void* T, cudaStream_t s) {
+  (k_turn_table<<<16, 256, 0, s>>>((float4*)T), note_launch());
+}
+
+void launch_ion_structure_factor(bool fp64, const double* ion_xyz, const uint32_t* sion,
+                                 const double* ion_q, int frames, int n_ion, const int* hkl,
+                                 const double* sqw, int mpad, int kh, const double L[3],
+                                 const void* turn, void* v, double* vhead, cudaStream_t s) {
   dim3 grid((mpad + kSfThreads - 1) / kSfThreads, frames);
   if (fp64)
-    (k_ion_sf<true><<<grid, kSfThreads, 0, s>>>(ion_xyz, ion_q, n_ion, hkl, sqw, mpad, 0, L[0],
-                                                L[1], L[2], v, vhead), note_launch());
+    (k_ion_sf_f64<<<grid, kSfThreads, 0, s>>>(ion_xyz, ion_q, n_ion, hkl, sqw, mpad, L[0], L[1],
+                                              L[2], (double*)v), note_launch());
   else
-    (k_ion_sf<false><<<grid, kSfThreads, 0, s>>>(ion_xyz, ion_q, n_ion, hkl, sqw, mpad, kh,
-                                                 L[0], L[1], L[2], v, vhead), note_launch());
+    (k_ion_sf_f32<<<grid, kSfThreads, 0, s>>>(sion, ion_q, n_ion, hkl, sqw, mpad, kh,
+                                              (const float4*)turn, (float*)v, vhead), note_launch());
 }
 
 // b^sol_k = A v: in float storage the head k-vectors (the heaviest weights) are
@@ -244,32 +411,36 @@ void launch_ion_structure_factor(bool fp64, const double* ion_xyz, const double*
 void launch_bsol_kspace(bool fp64, const void* A, const double* Ahead, int n, int mpad, int kh,
                         const void* v, const double* vhead, int frames, double* bsol,
                         cudaStream_t s) {
-  const int blocks = (n * 32 + 255) / 256;
   const int64_t lda = 2 * (int64_t)mpad;
-  for (int f0 = 0; f0 < frames; f0 += 4) {
+  for (int g0 = 0; g0 < (frames + 3) / 4; g0 += 65535) {
+    const int f0 = 4 * g0;
+    const dim3 grid((n * 32 + 255) / 256, std::min((frames - f0 + 3) / 4, 65535));
     if (fp64) {
-      (k_bsol_kspace<double, 4><<<blocks, 256, 0, s>>>((const double*)A, n, lda,
-                                                       (const double*)v, frames, f0, bsol, 0), note_launch());
+      (k_bsol_kspace<double, 4><<<grid, 256, 0, s>>>((const double*)A, n, lda,
+                                                     (const double*)v + f0 * lda, frames - f0,
+                                                     bsol + (int64_t)f0 * n, 0), note_launch());
     } else {
-      (k_bsol_kspace<float, 4><<<blocks, 256, 0, s>>>((const float*)A, n, lda,
-                                                      (const float*)v, frames, f0, bsol, 0), note_launch());
+      (k_bsol_kspace<float, 4><<<grid, 256, 0, s>>>((const float*)A, n, lda,
+                                                    (const float*)v + f0 * lda, frames - f0,
+                                                    bsol + (int64_t)f0 * n, 0), note_launch());
       if (kh > 0)
-        (k_bsol_kspace<double, 4><<<blocks, 256, 0, s>>>(Ahead, n, 2 * (int64_t)kh, vhead,
-                                                         frames, f0, bsol, 1), note_launch());
+        (k_bsol_kspace<double, 4><<<grid, 256, 0, s>>>(Ahead, n, 2 * (int64_t)kh,
+                                                       vhead + f0 * 2 * (int64_t)kh, frames - f0,
+                                                       bsol + (int64_t)f0 * n, 1), note_launch());
     }
   }
 }
 
-void launch_bsol_real_and_finish(bool fp64, const double* xyz, const double* alpha, int n,
-                                 const double* ion_xyz, const double* ion_q, int frames,
-                                 int n_ion, const Geometry& geo, const double* chi,
-                                 const double* bsol_k, double* b_out, double* qsol,
-                                 cudaStream_t s) {
-  (void)fp64;
+void launch_bsol_real_and_finish(const double* xyz, const double* alpha, const uint32_t* sfix,
+                                 int n, const double* ion_xyz, const double* ion_q,
+                                 const uint32_t* sion, int frames, int n_ion,
+                                 const Geometry& geo, const double* chi, const double* bsol_k,
+                                 double* b_out, double* qsol, cudaStream_t s) {
   dim3 grid((n + 127) / 128, frames);
   double dip = geo.slab ? 4.0 * kPi / geo.vol : 0.0;
-  (k_bsol_real<<<grid, 128, 0, s>>>(xyz, alpha, n, ion_xyz, ion_q, n_ion, geo.L[0], geo.L[1],
-                                   geo.L[2], geo.g, geo.rc, dip, chi, bsol_k, b_out, qsol), note_launch());
+  (k_bsol_real<<<grid, 128, 0, s>>>(xyz, alpha, sfix, n, ion_xyz, ion_q, sion, n_ion, geo.L[0],
+                                   geo.L[1], geo.L[2], geo.g, geo.rc, dip, chi, bsol_k, b_out,
+                                   qsol), note_launch());
 }
 
 }  // namespace cpm

@@ -1,21 +1,27 @@
 // k-space part of E on the tcgen05 tensor cores (sm_103a): E_k = A A^T over the light
-// tail of the k-vector table, with a three-way BF16 split of each operand.
+// tail of the k-vector table, with a BF16 split of each operand.
 //
 // Each FP32 operand value a = a0 + a1 + a2 (BF16 planes, a1 and a2 the successive
 // rounding remainders), and
 //   a b^T ~= a0 b0 + a0 b1 + a1 b0 + a0 b2 + a1 b1 + a2 b0      (six BF16 products),
 // which keeps ~24 bits of each product; BF16 x BF16 products are exact in the FP32
-// accumulator.  The heaviest k-vectors (the head) are summed in FP64 by the SIMT kernel
-// beforehand; this kernel adds the tail.
+// accumulator.  The heaviest k-vectors (the head) are summed in FP64 by a SIMT kernel
+// beforehand; this kernel adds the tail.  The k-vectors are sorted by decreasing weight
+// W_K and every product of a column is bounded by its W_K, so the far tail needs fewer
+// bits: the host picks, per 64-column K-block, six products, three (a0 b0 + a0 b1 +
+// a1 b0, within 3 * 2^-16 of |ab|) or one (a0 b0, within 2^-7), such that the summed
+// weight of each reduced group times its bound stays below 1e-8 (E entries are O(1)).
 //
 // Tile: 128 x 128 outputs of the lower triangle per CTA (cta_group::1, M = N = 128).
-// Warp roles: warp 0 issues TMA loads of the six 128 x 64 BF16 tiles of a K-block
-// (128-byte swizzle) into a 2-stage shared-memory ring; warp 1 issues the MMAs (one
-// thread); warps 2-5 drain the accumulator.  TMEM (512 columns): two FP32 accumulators
-// (ping-pong) and a hi/lo float pair per output.  After each accumulation chunk (one or
-// more K-blocks, schedule from the host) the epilogue adds the chunk into hi/lo with an
-// error-free two-sum, so FP32 rounding only touches chunk sums of light terms.  The final
-// drain adds the FP64 head and writes the float E tile.
+// Warp roles: warp 0 issues TMA loads of the 128 x 64 BF16 tiles (128-byte swizzle) into
+// a 2-stage shared-memory ring of six tile slots per stage: one six-product K-block (A0
+// A1 A2 B0 B1 B2), one three-product block (A0 A1 B0 B1) or up to three one-product
+// blocks (A0 B0 each); warp 1 issues the MMAs (one thread); warps 2-5 drain the
+// accumulator.  TMEM (512 columns): two FP32 accumulators (ping-pong) and a hi/lo float
+// pair per output.  After each accumulation chunk (one or more K-blocks, schedule from
+// the host) the epilogue adds the chunk into hi/lo with an error-free two-sum, so FP32
+// rounding only touches chunk sums of light terms.  The final drain adds the FP64 head
+// and writes the float E tile.
 //
 // Every wait is bounded: on timeout the kernel records an error code and leaves; the
 // host reports CPM_ECUDA-class failure instead of hanging.
@@ -170,6 +176,8 @@ struct TcArgs {
   int n;
   int kb_begin;   // first K-block of the tail
   int kb_end;     // one past the last K-block
+  int kb6_end;    // K-blocks before this take six products,
+  int kb3_end;    // then three up to this one, then one
   const uint32_t* chunk_end;  // bit per K-block: an accumulation chunk ends after it
   const double* head;         // [n][ldh] FP64 head + real-space terms (lower triangle)
   int64_t ldh;
@@ -177,6 +185,22 @@ struct TcArgs {
   int64_t ldE;
   int* err;
 };
+
+// K-blocks held by the ring stage that starts at relative block kb, and their product
+// count: one six- or three-product block, or up to three one-product blocks.
+__device__ __forceinline__ int stage_blocks(const TcArgs& a, int kb, int nkb, int& prods) {
+  const int g = a.kb_begin + kb;
+  if (g < a.kb6_end) {
+    prods = 6;
+    return 1;
+  }
+  if (g < a.kb3_end) {
+    prods = 3;
+    return 1;
+  }
+  prods = 1;
+  return min(3, nkb - kb);
+}
 
 __global__ void __launch_bounds__(kThreads, 1)
 k_ek_tc(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1,
@@ -219,60 +243,90 @@ k_ek_tc(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtens
   if (warp == 0) {
     // ---- TMA producer ------------------------------------------------------------
     if (lane == 0) {
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % kStages;
-        if (!mbar_wait(&empty_bar[s], ((kb / kStages) & 1) ^ 1, args.err, 1)) break;
+      int stage = 0;
+      for (int kb = 0; kb < nkb; ++stage) {
+        const int s = stage % kStages;
+        if (!mbar_wait(&empty_bar[s], ((stage / kStages) & 1) ^ 1, args.err, 1)) break;
         uint8_t* st = ring + s * kStageBytes;
-        mbar_expect_tx(&full_bar[s], kStageBytes);
+        int prods;
+        const int cnt = stage_blocks(args, kb, nkb, prods);
         const int x = (args.kb_begin + kb) * kBlockK;
-        tma_load_2d(st + 0 * kPlaneTileBytes, &map0, &full_bar[s], x, i0);
-        tma_load_2d(st + 1 * kPlaneTileBytes, &map1, &full_bar[s], x, i0);
-        tma_load_2d(st + 2 * kPlaneTileBytes, &map2, &full_bar[s], x, i0);
-        tma_load_2d(st + 3 * kPlaneTileBytes, &map0, &full_bar[s], x, j0);
-        tma_load_2d(st + 4 * kPlaneTileBytes, &map1, &full_bar[s], x, j0);
-        tma_load_2d(st + 5 * kPlaneTileBytes, &map2, &full_bar[s], x, j0);
+        if (prods == 6) {
+          mbar_expect_tx(&full_bar[s], 6 * kPlaneTileBytes);
+          tma_load_2d(st + 0 * kPlaneTileBytes, &map0, &full_bar[s], x, i0);
+          tma_load_2d(st + 1 * kPlaneTileBytes, &map1, &full_bar[s], x, i0);
+          tma_load_2d(st + 2 * kPlaneTileBytes, &map2, &full_bar[s], x, i0);
+          tma_load_2d(st + 3 * kPlaneTileBytes, &map0, &full_bar[s], x, j0);
+          tma_load_2d(st + 4 * kPlaneTileBytes, &map1, &full_bar[s], x, j0);
+          tma_load_2d(st + 5 * kPlaneTileBytes, &map2, &full_bar[s], x, j0);
+        } else if (prods == 3) {
+          mbar_expect_tx(&full_bar[s], 4 * kPlaneTileBytes);
+          tma_load_2d(st + 0 * kPlaneTileBytes, &map0, &full_bar[s], x, i0);
+          tma_load_2d(st + 1 * kPlaneTileBytes, &map1, &full_bar[s], x, i0);
+          tma_load_2d(st + 2 * kPlaneTileBytes, &map0, &full_bar[s], x, j0);
+          tma_load_2d(st + 3 * kPlaneTileBytes, &map1, &full_bar[s], x, j0);
+        } else {
+          mbar_expect_tx(&full_bar[s], 2 * cnt * kPlaneTileBytes);
+          for (int u = 0; u < cnt; ++u) {
+            tma_load_2d(st + (2 * u) * kPlaneTileBytes, &map0, &full_bar[s], x + u * kBlockK, i0);
+            tma_load_2d(st + (2 * u + 1) * kPlaneTileBytes, &map0, &full_bar[s], x + u * kBlockK,
+                        j0);
+          }
+        }
+        kb += cnt;
       }
     }
   } else if (warp == 1) {
     // ---- MMA issuer ----------------------------------------------------------------
     if (lane == 0) {
+      // products (p, q) with p + q <= 2, in the order (0,0) (0,1) (1,0) (0,2) (1,1) (2,0):
+      // A plane p (rows i), B plane q (rows j); the three- and one-product forms are the
+      // first three and the first one
+      constexpr uint32_t kPa = 0x210100u, kPb = 0x012010u;  // nibble t: plane of product t
       int chunk = 0;
       bool first_in_chunk = true;
       bool ok = true;
-      for (int kb = 0; kb < nkb && ok; ++kb) {
-        const int s = kb % kStages;
-        const int buf = chunk & 1;
-        if (first_in_chunk) {
-          ok = mbar_wait(&acc_empty[buf], ((chunk >> 1) & 1) ^ 1, args.err, 2);
-          if (!ok) break;
-          tc_fence_after();
-        }
-        ok = mbar_wait(&full_bar[s], (kb / kStages) & 1, args.err, 3);
+      int stage = 0;
+      for (int kb = 0; kb < nkb && ok; ++stage) {
+        const int s = stage % kStages;
+        int prods;
+        const int cnt = stage_blocks(args, kb, nkb, prods);
+        ok = mbar_wait(&full_bar[s], (stage / kStages) & 1, args.err, 3);
         if (!ok) break;
         tc_fence_after();
-        const uint32_t a0 = smem_addr(ring + s * kStageBytes);
-        const uint32_t d = tmem + (uint32_t)(buf * kTile);
-        // products (p, q) with p + q <= 2: A plane p (rows i), B plane q (rows j)
-        const int pa[6] = {0, 0, 1, 0, 1, 2};
-        const int pb[6] = {0, 1, 0, 2, 1, 0};
+        const uint32_t st = smem_addr(ring + s * kStageBytes);
+        for (int u = 0; u < cnt; ++u) {
+          const int buf = chunk & 1;
+          if (first_in_chunk) {
+            ok = mbar_wait(&acc_empty[buf], ((chunk >> 1) & 1) ^ 1, args.err, 2);
+            if (!ok) break;
+            tc_fence_after();
+          }
+          // tile slots of this block: A planes from slot sa, B planes from slot sb
+          const int sa = prods == 1 ? 2 * u : 0;
+          const int sb = prods == 6 ? 3 : prods == 3 ? 2 : 2 * u + 1;
+          const uint32_t d = tmem + (uint32_t)(buf * kTile);
 #pragma unroll
-        for (int ks = 0; ks < kBlockK / 16; ++ks) {
-#pragma unroll
-          for (int t = 0; t < 6; ++t) {
-            const uint64_t da = smem_desc(a0 + pa[t] * kPlaneTileBytes + ks * 32);
-            const uint64_t db = smem_desc(a0 + (3 + pb[t]) * kPlaneTileBytes + ks * 32);
-            mma_bf16(d, da, db, (first_in_chunk && ks == 0 && t == 0) ? 0u : 1u);
+          for (int ks = 0; ks < kBlockK / 16; ++ks) {
+            for (int t = 0; t < prods; ++t) {
+              const int pa = (kPa >> (4 * t)) & 15, pb = (kPb >> (4 * t)) & 15;
+              const uint64_t da = smem_desc(st + (sa + pa) * kPlaneTileBytes + ks * 32);
+              const uint64_t db = smem_desc(st + (sb + pb) * kPlaneTileBytes + ks * 32);
+              mma_bf16(d, da, db, (first_in_chunk && ks == 0 && t == 0) ? 0u : 1u);
+            }
+          }
+          first_in_chunk = false;
+          const int g = args.kb_begin + kb + u;
+          const bool last = (kb + u + 1 == nkb) || ((args.chunk_end[g >> 5] >> (g & 31)) & 1u);
+          if (last) {
+            mma_commit(&acc_full[buf]);
+            ++chunk;
+            first_in_chunk = true;
           }
         }
+        if (!ok) break;
         mma_commit(&empty_bar[s]);  // frees the stage once these MMAs have read it
-        first_in_chunk = false;
-        const int g = args.kb_begin + kb;
-        const bool last = (kb + 1 == nkb) || ((args.chunk_end[g >> 5] >> (g & 31)) & 1u);
-        if (last) {
-          mma_commit(&acc_full[buf]);
-          ++chunk;
-          first_in_chunk = true;
-        }
+        kb += cnt;
       }
     }
   } else {
@@ -405,7 +459,7 @@ void launch_split_bf16(const float* A, int64_t len, void* p0, void* p1, void* p2
 }
 
 int launch_ek_tc(const void* p0, const void* p1, const void* p2, int npad, int mpad, int n,
-                 int kb_begin, const uint32_t* chunk_end, const double* head, int64_t ldh,
+                 int kb_begin, int kb6_end, int kb3_end, const uint32_t* chunk_end, const double* head, int64_t ldh,
                  float* E, int64_t ldE, int* err, cudaStream_t s) {
   CUtensorMap m0, m1, m2;
   const int64_t cols = 2 * (int64_t)mpad;
@@ -416,6 +470,8 @@ int launch_ek_tc(const void* p0, const void* p1, const void* p2, int npad, int m
   a.n = n;
   a.kb_begin = kb_begin;
   a.kb_end = (int)(cols / kBlockK);
+  a.kb6_end = kb6_end;
+  a.kb3_end = kb3_end;
   a.chunk_end = chunk_end;
   a.head = head;
   a.ldh = ldh;

@@ -1,0 +1,120 @@
+"""Learned initial guess for consecutive frames (driver over the C ABI).
+
+The network predicts the change of the first-step charges q^b between consecutive MD
+frames from per-atom features of the potential; PCG then starts from
+q_prev + scale * net(features) instead of the previous step's charges (Eq. 26).  Every
+numerical step runs in libcpm.so kernels (features, forward, gradient, Adam, guess);
+this module only orders the calls and keeps the device buffers.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import cpm
+
+N_FEATURES = 32
+N_PARAMS = 10497
+
+
+def _vp(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class LearnedGuess:
+    """Parameters, Adam state and feature normalisation of one guess network."""
+
+    def __init__(self, ctx: cpm.Context, seed: int = 0, bf16: bool = True):
+        import torch
+        self.ctx = ctx
+        self.lib = ctx.lib
+        self.bf16 = 1 if bf16 else 0
+        self.dev = torch.device("cuda", torch.cuda.current_device())
+        rng = np.random.default_rng(seed)
+        parts = []
+        for o, i in [(64, 32), (64, 64), (64, 64), (1, 64)]:
+            lim = np.sqrt(6.0 / i)
+            parts.append(rng.uniform(-lim, lim, size=o * i))
+            parts.append(np.zeros(o))
+        p = np.concatenate(parts).astype(np.float32)
+        p[-65:-1] *= 0.1  # small output layer: start close to the previous-step guess
+        self.params = torch.tensor(p, device=self.dev)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.grad = torch.zeros_like(self.params)
+        self.loss = torch.zeros(1, dtype=torch.float64, device=self.dev)
+        self.norm = torch.cat([torch.zeros(N_FEATURES), torch.ones(N_FEATURES)]).to(self.dev)
+        self.target_scale = 1.0
+        self.step = 0
+
+    # -- kernels --------------------------------------------------------------------
+    def features(self, b, b_prev, chi):
+        import torch
+        frames, n = int(b.shape[0]), int(b.shape[1])
+        feat = torch.empty((frames, n, N_FEATURES), dtype=torch.float32, device=self.dev)
+        self.ctx._check(self.lib.cpm_guess_features(self.ctx.h, frames, _vp(b), _vp(b_prev),
+                                                    _vp(chi), _vp(feat)))
+        return feat
+
+    def forward(self, feat):
+        import torch
+        s = feat.numel() // N_FEATURES
+        out = torch.empty(s, dtype=torch.float32, device=self.dev)
+        self.ctx._check(self.lib.cpm_mlp_forward(self.ctx.h, _vp(self.params), _vp(self.norm),
+                                                 self.bf16, ctypes.c_int64(s), _vp(feat),
+                                                 _vp(out)))
+        return out
+
+    def gradient(self, feat, target):
+        s = feat.numel() // N_FEATURES
+        self.ctx._check(self.lib.cpm_mlp_grad(self.ctx.h, _vp(self.params), _vp(self.norm),
+                                              self.bf16, ctypes.c_int64(s), _vp(feat),
+                                              _vp(target), _vp(self.grad), _vp(self.loss)))
+        return float(self.loss.item()) / s
+
+    def adam(self, lr):
+        self.step += 1
+        self.ctx._check(self.lib.cpm_mlp_adam(self.ctx.h, _vp(self.params), _vp(self.m),
+                                              _vp(self.v), _vp(self.grad), self.step,
+                                              ctypes.c_float(lr)))
+
+    def guess(self, feat, q_prev):
+        import torch
+        y = self.forward(feat)
+        q0 = torch.empty_like(q_prev)
+        self.ctx._check(self.lib.cpm_guess_apply(self.ctx.h, ctypes.c_int64(q_prev.numel()),
+                                                 _vp(y), ctypes.c_float(self.target_scale),
+                                                 _vp(q_prev), _vp(q0)))
+        return q0
+
+    # -- training -------------------------------------------------------------------
+    def set_normalisation(self, feat_sample: np.ndarray, target_sample: np.ndarray):
+        """Per-feature mean / inverse deviation and the target scale from a host sample."""
+        import torch
+        f = feat_sample.reshape(-1, N_FEATURES).astype(np.float64)
+        mu = f.mean(axis=0)
+        sd = f.std(axis=0)
+        inv = np.where(sd > 1e-12, 1.0 / np.where(sd > 1e-12, sd, 1.0), 0.0)
+        self.norm = torch.tensor(np.concatenate([mu, inv]).astype(np.float32), device=self.dev)
+        ts = float(np.std(target_sample))
+        self.target_scale = ts if ts > 0 else 1.0
+
+    def train(self, feat, target_q, epochs=3, batch=32768, lr=2e-3, seed=0, log=None):
+        """Adam on the mean squared error of net(features) vs Delta q^b / target_scale.
+        feat [S, 32] and target_q [S] are device tensors (float32); samples are visited in
+        a seeded random order of contiguous blocks."""
+        import torch
+        s = feat.shape[0]
+        target = (target_q / self.target_scale).to(torch.float32).contiguous()
+        rng = np.random.default_rng(seed)
+        starts = np.arange(0, s, batch)
+        losses = []
+        for ep in range(epochs):
+            for b0 in rng.permutation(starts):
+                b1 = min(s, b0 + batch)
+                losses.append(self.gradient(feat[b0:b1], target[b0:b1]))
+                self.adam(lr)
+            if log:
+                log(f"epoch {ep}: loss {np.mean(losses[-len(starts):]):.4e}")
+        return losses

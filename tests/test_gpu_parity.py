@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 from oracle import ewald as ew
+from oracle import precond as pc
 from paper_2111_06704_gb300 import cpm
 from paper_2111_06704_gb300 import workloads as wl
 from tests import _cases
@@ -67,6 +68,19 @@ def test_interaction_matrix_matches_oracle(built, oc):
     assert np.array_equal(e_n, e_n.T)  # mirrored: exactly symmetric
 
 
+def test_apply_E_is_the_stored_matrix_times_p(built, oc):
+    # the solver's matvec applies the stored matrix exactly up to FP64 summation: the
+    # float path keeps every product and partial-sum rounding error
+    prec, ctx = built
+    rng = np.random.default_rng(2)
+    p = rng.standard_normal((3, oc.work.electrode.n))
+    q = ctx.cpm_apply_E(p)
+    e_n = ctx.cpm_get_E(cpm.CPM_E_STORED)
+    ref = p @ e_n.T
+    assert np.abs(q - ref).max() <= 1e-12 * np.abs(ref).max()
+    assert np.abs(q - p @ oc.e_neutral.T).max() <= E_TOL[prec] * 50 * np.abs(ref).max()
+
+
 def test_potential_matches_oracle(built, oc):
     prec, ctx = built
     io, el = oc.work.electrolyte, oc.work.electrode
@@ -114,6 +128,27 @@ def test_dc_preconditioner_needs_fewer_iterations(oc):
         its[pre] = int(it[0])
         ctx.close()
     assert its[cpm.CPM_PRECOND_DC] < its[cpm.CPM_PRECOND_JACOBI]
+
+
+def test_dc_preconditioner_matches_oracle(oc):
+    # P of Eq. 36 entry by entry (pattern exact, values to FP64 rounding of the local
+    # eliminations) and p_gap of Eq. 37 from the library's own 1^T E_n^-1 1
+    el = oc.work.electrode
+    ctx = make_ctx(oc.work, "fp32")
+    off, idx, val = ctx.cpm_get_precond()
+    p_ref, nb = pc.dc_preconditioner(el.xyz, el.alpha, el.box, wl.G_DC, wl.RCUT_DC)
+    assert off[-1] == sum(len(x) for x in nb)
+    for j in range(el.n):
+        cols = idx[off[j]:off[j + 1]]
+        assert np.array_equal(cols, nb[j])  # the pattern is symmetric: j's row = j's list
+        np.testing.assert_allclose(val[off[j]:off[j + 1]], p_ref[j, cols], rtol=0,
+                                   atol=1e-11 * np.abs(p_ref).max())
+    info = ctx.cpm_get_info()
+    if info["p_gap"] != 0.0:
+        gap = pc.p_gap(p_ref, info["c_ele"], nb)
+        n_zero = el.n ** 2 - off[-1]
+        assert abs(info["p_gap"] - gap) <= 1e-10 * (abs(info["c_ele"]) + np.abs(p_ref).sum()) / n_zero
+    ctx.close()
 
 
 def test_device_pointers_give_the_same_answer(oc):

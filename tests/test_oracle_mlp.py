@@ -1,0 +1,79 @@
+"""Pins of the FP64 learned-guess oracle (no GPU): hand-written backpropagation against
+central finite differences of the forward pass, SiLU against its closed-form limits,
+and the shell features on lattices whose answer is known by symmetry."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp
+from paper_2111_06704_gb300 import workloads as wl
+from oracle import precond as pc
+
+
+def test_parameter_count():
+    assert mlp.N_PARAMS == 64 * 32 + 64 + 2 * (64 * 64 + 64) + 64 + 1
+
+
+def test_silu_limits_and_derivative():
+    z = np.array([-30.0, -1.0, 0.0, 1.0, 30.0])
+    s = mlp.silu(z)
+    assert s[2] == 0.0 and s[4] == pytest.approx(30.0) and abs(s[0]) < 1e-11
+    assert s[3] == pytest.approx(1.0 / (1.0 + math.exp(-1.0)))
+    h = 1e-6
+    fd = (mlp.silu(z + h) - mlp.silu(z - h)) / (2 * h)
+    assert np.allclose(mlp.silu_grad(z), fd, atol=1e-8)
+    assert mlp.silu_grad(np.array([0.0]))[0] == pytest.approx(0.5)
+
+
+def test_backprop_matches_finite_differences():
+    rng = np.random.default_rng(3)
+    params = mlp.init_params(rng, scale=0.7)
+    params += 0.05 * rng.standard_normal(params.shape)  # non-zero biases too
+    x = rng.standard_normal((9, mlp.N_FEATURES))
+    t = rng.standard_normal(9)
+    loss, grad = mlp.loss_and_grad(params, x, t)
+    idx = rng.choice(mlp.N_PARAMS, size=60, replace=False)
+    idx = np.concatenate([idx, [mlp.N_PARAMS - 1, 64 * 32, 64 * 32 + 64]])  # biases
+    h = 1e-6
+    for k in idx:
+        e = np.zeros_like(params)
+        e[k] = h
+        lp, _ = mlp.loss_and_grad(params + e, x, t)
+        lm, _ = mlp.loss_and_grad(params - e, x, t)
+        fd = (lp - lm) / (2 * h)
+        assert grad[k] == pytest.approx(fd, rel=1e-5, abs=1e-9)
+    # the loss is zero at the network's own output
+    y, _ = mlp.forward(params, x)
+    assert mlp.loss_and_grad(params, x, y)[0] == 0.0
+
+
+def test_shell_features_on_a_uniform_sheet():
+    # every site of a perfect sheet is equivalent: uniform b gives uniform shell means,
+    # and a change of b on one atom shows up only in its neighbours' matching shell
+    el = wl.two_sheet_electrode(7, 4)  # box edges above 2 x 8 A
+    nb = pc.neighbours(el.xyz, el.box, 8.0)
+    b = np.full(el.n, 0.25)
+    f = mlp.features(b, b, el.chi, el.xyz, el.box, nb)
+    assert np.allclose(f[:, 0], 0.0) and np.allclose(f[:, 1:9], 0.0)
+    assert np.allclose(f[:, 9], 0.25)
+    filled = f[:, 10:18] != 0.0
+    assert np.allclose(f[:, 10:18][filled], 0.25)
+    assert set(np.unique(f[:, 19])) == {-1.0, 1.0}
+    b2 = b.copy()
+    b2[0] += 1.0
+    g = mlp.features(b2, b, el.chi, el.xyz, el.box, nb)
+    assert g[0, 0] == 1.0 and np.all(g[0, 1:9] == 0.0)
+    # nearest neighbours of atom 0 (1.42 A: shell k = 1) see it in their first shell
+    d = el.xyz - el.xyz[0]
+    d -= np.asarray(el.box) * np.round(d / np.asarray(el.box))
+    r = np.sqrt((d * d).sum(axis=1))
+    nn = np.nonzero((r > 0.5) & (r < 1.5))[0]
+    assert len(nn) == 3
+    for j in nn:
+        shell = [k for k in nb[j] if k != j]
+        dj = el.xyz[shell] - el.xyz[j]
+        dj -= np.asarray(el.box) * np.round(dj / np.asarray(el.box))
+        rj = np.sqrt((dj * dj).sum(axis=1))
+        members = np.count_nonzero((rj >= 0.5) & (rj < 1.5))
+        assert g[j, 1] == pytest.approx(1.0 / members)
