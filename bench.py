@@ -50,7 +50,11 @@ def parse():
     ap.add_argument("--precision", choices=["bf16x6", "fp32", "fp64"], default="bf16x6")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["precision", "batch", "learned"], default="precision")
+    ap.add_argument("--workload", choices=["precision", "batch", "learned", "matvec"],
+                    default="precision")
+    ap.add_argument("--rhs", type=int, default=1, help="directions per matvec (matvec workload)")
+    ap.add_argument("--ragged", type=int, default=32,
+                    help="ragged systems in the batch workload (0: skip that part)")
     ap.add_argument("--train-frames", type=int, default=20000)
     ap.add_argument("--heldout-frames", type=int, default=2000)
     ap.add_argument("--epochs", type=int, default=3)
@@ -408,6 +412,51 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_matvec(args, rank, world, local_rank):
+    """The PCG matvec alone: E of the `--cells` two-sheet electrode (FP32 storage) applied
+    to `--rhs` directions per call through cpm_apply_E, timed by CUDA events inside the
+    library around its matvec launches.  The matvec streams E whatever its entries are,
+    so the k-space cutoff is loosened to 1e-3 to keep the build (and the device memory
+    a counter capture saves and restores) small."""
+    import torch
+
+    from paper_2111_06704_gb300 import cpm
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    el = wl.two_sheet_electrode(args.cells, args.cells)
+    n = el.n
+    ctx = cpm.Context(el.box, precision=cpm.CPM_PREC_FP32, kspace_eps=1e-3)
+    ctx.cpm_build_E(el.xyz, el.alpha)
+    rng = np.random.default_rng(wl.seed_for(2, rank))
+    p = torch.tensor(rng.standard_normal((args.rhs, n)), device=dev)
+    q = torch.empty_like(p)
+    for _ in range(args.warmup):
+        ctx.cpm_apply_E(p, q)
+    ms = []
+    with ClockSampler(local_rank) as clocks:
+        for _ in range(args.steps):
+            ctx.cpm_apply_E(p, q)
+            ms.append(ctx.cpm_get_info()["t_matvec_ms"])
+    ms = max_over_ranks(statistics.median(ms), world)
+    if rank != 0:
+        return
+    e_bytes = n * ((n + 127) // 128 * 128) * 4
+    peak = measured_peaks()[0].get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"])
+    gbs = world * e_bytes / (ms * 1e-3) / 1e9
+    line = {"metric": "PCG matvec E-streaming rate", "value": gbs, "unit": "GB/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"matvec: two-sheet graphene N={n}, {args.rhs} right-hand "
+                                   f"side(s) per pass, E {e_bytes / 1e6:.0f} MB",
+                       "l2": "E larger than L2" if e_bytes > 129e6 else "E fits in L2"},
+            "roofline": {"bound": "hbm", "achieved": gbs / world, "peak": peak, "unit": "GB/s",
+                         "frac": gbs / world / peak, "traffic": None},
+            "clocks": clocks.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def run_batch(args, rank, world, local_rank):
     """Batching form: the 512-atom electrode, `--frames` frames of 2,000 ions (Gaussian
     perturbations of one base frame) solved as one multi-right-hand-side PCG, against the
@@ -484,6 +533,7 @@ def run_batch(args, rank, world, local_rank):
         base_prev_ms = timed(lambda: base_frames(True), 1) / nb
         base_solve_ms = timed(lambda: [(base.cpm_solve(b1, q1, tol=TOL, maxit=5000),
                                         base.cpm_neutralize(q1, qs1)) for _ in range(nb)], 1) / nb
+        ragged = run_ragged(args, rank, dev, stream, timed) if args.ragged > 0 else None
     if rank != 0:
         return
     value = world * F * 1000.0 / ms
@@ -510,7 +560,81 @@ def run_batch(args, rank, world, local_rank):
         "clocks": clocks.summary(),
         "gpu_launches": launches,
     }
+    if ragged is not None:
+        line["ragged"] = ragged
     print(json.dumps(line), flush=True)
+
+
+def run_ragged(args, rank, dev, stream, timed):
+    """The ragged part of the batching form: `--ragged` independent two-sheet systems with
+    electrode counts drawn uniformly in [500, 8000] (one frame each), built once; timed: the
+    potentials, then one batched PCG over all systems plus the batched neutralisation,
+    against the same systems solved one context at a time."""
+    import torch
+
+    from paper_2111_06704_gb300 import cpm
+
+    works = wl.ragged_systems(count=args.ragged, n_lo=500, n_hi=8000,
+                              seed=wl.seed_for(3, 100 + rank))
+    t = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    t0 = time.perf_counter()
+    ctxs, ins = [], []
+    for w in works:
+        el, io = w.electrode, w.electrolyte
+        c = cpm.Context(el.box, stream=stream.cuda_stream, precision=cpm.CPM_PREC_BF16X6,
+                        precond=cpm.CPM_PRECOND_DC)
+        c.cpm_build_E(t(el.xyz), t(el.alpha))
+        ctxs.append(c)
+        ins.append((t(io.xyz), t(io.q), t(el.chi)))
+    build_s = time.perf_counter() - t0
+    sizes = [c.n for c in ctxs]
+    tot = sum(sizes)
+    b = torch.empty(tot, dtype=torch.float64, device=dev)
+    q = torch.zeros(tot, dtype=torch.float64, device=dev)
+    qs = torch.empty(len(ctxs), dtype=torch.float64, device=dev)
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    batch = cpm.Batch(ctxs)
+    its = {}
+
+    def potentials():
+        for k, (c, (x, qi, chi)) in enumerate(zip(ctxs, ins)):
+            c.cpm_potential(x, qi, chi, b[offs[k]:offs[k + 1]].view(1, -1), qs[k:k + 1])
+
+    def batched():
+        potentials()
+        q.zero_()
+        _, it, _ = batch.solve(b, q, tol=TOL, maxit=2000)
+        batch.neutralize(q, qs)
+        its["batch"] = float(np.mean(it))
+
+    def one_by_one():
+        potentials()
+        q.zero_()
+        it_all = []
+        for k, c in enumerate(ctxs):
+            qk = q[offs[k]:offs[k + 1]].view(1, -1)
+            _, it, _ = c.cpm_solve(b[offs[k]:offs[k + 1]].view(1, -1), qk, tol=TOL, maxit=2000)
+            c.cpm_neutralize(qk, qs[k:k + 1])
+            it_all.append(int(it[0]))
+        its["single"] = float(np.mean(it_all))
+
+    batched()
+    one_by_one()
+    ms_batch = timed(batched, 2)
+    ms_single = timed(one_by_one, 2)
+    pot_ms = timed(potentials, 2)
+    out = {"systems": len(ctxs), "atoms_min": min(sizes), "atoms_max": max(sizes),
+           "atoms_total": tot, "build_s_all": build_s,
+           "batched": {"value": len(ctxs) * 1000.0 / ms_batch, "unit": "solves/s",
+                       "ms": ms_batch, "mean_iters": its["batch"]},
+           "one_context_at_a_time": {"value": len(ctxs) * 1000.0 / ms_single,
+                                     "unit": "solves/s", "ms": ms_single,
+                                     "mean_iters": its["single"]},
+           "potential_ms_all": pot_ms}
+    batch.close()
+    for c in ctxs:
+        c.close()
+    return out
 
 
 def run_learned(args, rank, world, local_rank):
@@ -650,6 +774,8 @@ def main():
         run_batch(args, rank, world, local_rank)
     elif args.workload == "learned":
         run_learned(args, rank, world, local_rank)
+    elif args.workload == "matvec":
+        run_matvec(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
     if world > 1:

@@ -253,6 +253,32 @@ int cpm_get_d(cpm_ctx* c, double* d_out);
 
 const char* cpm_last_error(const cpm_ctx* c);
 
+/* ---- ragged batches (no counterpart in the paper) --------------------------------------
+ * Several independent electrodes of any sizes, each its own built context (float storage
+ * of E: CPM_PREC_FP32 or CPM_PREC_BF16X6; same preconditioner; same device), solved by
+ * one PCG over all of them: every system is a right-hand-side column with its own E,
+ * preconditioner and d, so an iteration is one launch per step for the whole batch.  The
+ * batch reads the systems' builds at every call (a rebuilt system is picked up) and runs
+ * on the first system's stream.  It does not own the contexts; destroy the batch first. */
+typedef struct cpm_batch cpm_batch;
+
+int cpm_batch_create(cpm_batch** out, int count, cpm_ctx* const* systems);
+int cpm_batch_destroy(cpm_batch* b);
+
+/* Eq. 25 first step for every system: E_k q_k = b_k (b in V as cpm_potential gives it).
+ * rhs and q_inout are the systems' vectors concatenated in batch order
+ * ([n_0 + n_1 + ...], host or device); q_inout holds the guess when use_guess != 0.
+ * iters_out / relres_out: host [count] or NULL.  Returns CPM_ENOCONV if any system
+ * missed tol within maxit (q holds the last iterates). */
+int cpm_batch_solve(cpm_batch* b, const double* rhs, double* q_inout, int use_guess,
+                    double tol, int maxit, int* iters_out, double* relres_out);
+
+/* Eq. 35 for every system with its own d: q_k -= (sum q_k + qsol[k]) d_k.  q_inout
+ * concatenated as above; qsol [count] or NULL (all zero). */
+int cpm_batch_neutralize(cpm_batch* b, double* q_inout, const double* qsol);
+
+const char* cpm_batch_last_error(const cpm_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,13 +17,18 @@ this frame and the previous one, Delta b = b_t - b_{t-1}):
   10-17  the same shell means of b
   18     chi_i
   19     +1 above the mean electrode height (z_i > mean z), -1 otherwise
-  20-31  zero
+  20     (P Delta b)_i / k_e with P the PCG-DC preconditioner of Eq. 36 (its pattern
+         entries, no p_gap fill): the local inverses applied to the potential change, a
+         local estimate of Delta q^b itself
+  21-31  zero
 The network predicts the change of the first-step charges, Delta q^b_i, in units of
 `target_scale`; features are divided by `feature_scale` beforehand.
 """
 from __future__ import annotations
 
 import numpy as np
+
+from oracle.ewald import KE
 
 LAYERS = [(64, 32), (64, 64), (64, 64), (1, 64)]
 N_FEATURES = 32
@@ -111,8 +116,9 @@ def shell_means(values, xyz, box, nbrs):
     return out
 
 
-def features(b, b_prev, chi, xyz, box, nbrs):
-    """The 32 per-atom features of one frame (unscaled)."""
+def features(b, b_prev, chi, xyz, box, nbrs, p_dc):
+    """The 32 per-atom features of one frame (unscaled); p_dc is the dense PCG-DC
+    preconditioner (zero outside its neighbour pattern)."""
     b = np.asarray(b, dtype=np.float64)
     db = b - np.asarray(b_prev, dtype=np.float64)
     n = b.shape[0]
@@ -124,4 +130,5 @@ def features(b, b_prev, chi, xyz, box, nbrs):
     f[:, 18] = chi
     z = np.asarray(xyz)[:, 2]
     f[:, 19] = np.where(z > z.mean(), 1.0, -1.0)
+    f[:, 20] = (np.asarray(p_dc, dtype=np.float64) @ db) / KE
     return f

@@ -82,7 +82,8 @@ EXPORTS = ["cpm_default_params", "cpm_create", "cpm_destroy", "cpm_build_E", "cp
            "cpm_solve", "cpm_solve_static", "cpm_neutralize", "cpm_get_E", "cpm_get_info",
            "cpm_get_d", "cpm_guess_features", "cpm_mlp_forward", "cpm_mlp_grad",
            "cpm_mlp_adam", "cpm_guess_apply", "cpm_apply_E", "cpm_get_precond",
-           "cpm_last_error"]
+           "cpm_last_error", "cpm_batch_create", "cpm_batch_destroy", "cpm_batch_solve",
+           "cpm_batch_neutralize", "cpm_batch_last_error"]
 
 _lib = None
 
@@ -117,6 +118,12 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.cpm_get_info.argtypes = [vp, P(cpm_info_t)]
     lib.cpm_get_d.argtypes = [vp, vp]
     lib.cpm_get_precond.argtypes = [vp, vp, vp, vp]
+    lib.cpm_batch_create.argtypes = [P(vp), i, P(vp)]
+    lib.cpm_batch_destroy.argtypes = [vp]
+    lib.cpm_batch_solve.argtypes = [vp, vp, vp, i, d, i, vp, vp]
+    lib.cpm_batch_neutralize.argtypes = [vp, vp, vp]
+    lib.cpm_batch_last_error.argtypes = [vp]
+    lib.cpm_batch_last_error.restype = ctypes.c_char_p
     lib.cpm_guess_features.argtypes = [vp, i, vp, vp, vp, vp]
     lib.cpm_mlp_forward.argtypes = [vp, vp, vp, i, i64, vp, vp]
     lib.cpm_mlp_grad.argtypes = [vp, vp, vp, i, i64, vp, vp, vp, vp]
@@ -126,7 +133,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.cpm_last_error.argtypes = [vp]
     lib.cpm_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("cpm_default_params", "cpm_last_error"):
+        if name not in ("cpm_default_params", "cpm_last_error", "cpm_batch_last_error"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -314,6 +321,60 @@ class Context:
         info = cpm_info_t()
         self._check(self.lib.cpm_get_info(self.h, ctypes.byref(info)))
         return {k: getattr(info, k) for k, _ in cpm_info_t._fields_}
+
+
+class Batch:
+    """A ragged batch over built contexts (cpm_batch_*): one PCG over all systems.
+    Vectors are the systems' vectors concatenated in batch order."""
+
+    def __init__(self, contexts):
+        self.lib = load()
+        self.contexts = list(contexts)  # kept alive: the batch refers to their builds
+        arr = (ctypes.c_void_p * len(self.contexts))(*[c.h.value for c in self.contexts])
+        h = ctypes.c_void_p()
+        st = self.lib.cpm_batch_create(ctypes.byref(h), len(self.contexts), arr)
+        if st != CPM_OK:
+            raise CpmError(st, "cpm_batch_create failed")
+        self.h = h
+        self.sizes = [c.n for c in self.contexts]
+
+    def _check(self, st):
+        if st != CPM_OK:
+            raise CpmError(st, self.lib.cpm_batch_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.cpm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def solve(self, b, q=None, use_guess=False, tol=1e-6, maxit=1000):
+        count = len(self.contexts)
+        if q is None:
+            q = np.zeros(sum(self.sizes))
+        pb, kb = _ptr(b)
+        pq, kq = _ptr(q)
+        iters = np.zeros(count, dtype=np.int32)
+        rel = np.zeros(count)
+        self._check(self.lib.cpm_batch_solve(self.h, pb, pq, 1 if use_guess else 0, float(tol),
+                                             int(maxit), iters.ctypes.data_as(ctypes.c_void_p),
+                                             rel.ctypes.data_as(ctypes.c_void_p)))
+        if isinstance(q, np.ndarray) and kq is not q:
+            q[...] = kq
+        return q, iters, rel
+
+    def neutralize(self, q, qsol=None):
+        pq, kq = _ptr(q)
+        ps, ks = _ptr(qsol)
+        self._check(self.lib.cpm_batch_neutralize(self.h, pq, ps))
+        if isinstance(q, np.ndarray) and kq is not q:
+            q[...] = kq
+        return q
 
 
 def charges(ctx: Context, ion_xyz, ion_q, chi, tol=1e-6, maxit=1000, q0=None):

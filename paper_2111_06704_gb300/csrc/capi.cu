@@ -166,7 +166,7 @@ void free_build(Ctx* c) {
   Buf* all[] = {&c->xyz, &c->alpha, &c->sfix, &c->hkl, &c->sqw, &c->flush, &c->chunk_end,
                 &c->Ahead, &c->A,
                 &c->E, &c->diag,
-                &c->nbr_off, &c->nbr_idx, &c->prow, &c->d, &c->shell_k, &c->shell_inv,
+                &c->nbr_off, &c->nbr_idx, &c->prow, &c->d, &c->shell_off, &c->shell_members,
                 &c->turn};
   for (Buf* b : all) buf_free(c, b);
   c->built = false;
@@ -248,7 +248,7 @@ int cpm_destroy(cpm_ctx* c) {
   cudaEventDestroy(c->ev_tc[0]);
   cudaEventDestroy(c->ev_tc[1]);
   Buf* ws[] = {&c->ws_solve, &c->ws_in0, &c->ws_in1, &c->ws_in2, &c->ws_out0, &c->ws_out1,
-               &c->ws_pot};
+               &c->ws_pot, &c->ws_guess};
   for (Buf* b : ws) buf_free(c, b);
   delete c;
   return CPM_OK;

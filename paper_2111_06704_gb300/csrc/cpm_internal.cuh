@@ -101,8 +101,8 @@ struct Ctx {
 
   // learned-guess feature geometry (frame independent, made on first use)
   Buf turn;       // float4 [4096]: exp(2 pi i j / 4096) as float pairs (ion phasors)
-  Buf shell_k;    // uint8 [nnz]: neighbour shell 1..8 of each PCG-DC pattern entry, 0 = none
-  Buf shell_inv;  // float [n][8]: 1 / (atoms in shell k of atom i), 0 for an empty shell
+  Buf shell_off;    // int64 [8n+1]: offsets of the (atom, shell 1..8) buckets in shell_members
+  Buf shell_members;  // int32: members of the buckets (neighbours filed by shell)
   double zmean = 0;
   bool shells_ready = false;
 
@@ -112,7 +112,7 @@ struct Ctx {
 
   // scratch (grown on demand, never shrunk)
   std::vector<Buf*> scratch;
-  Buf ws_solve, ws_in0, ws_in1, ws_in2, ws_out0, ws_out1, ws_pot;
+  Buf ws_solve, ws_in0, ws_in1, ws_in2, ws_out0, ws_out1, ws_pot, ws_guess;
 
   float t_kspace_ms = 0, t_phase_ms = 0, t_precond_ms = 0, t_dsolve_ms = 0, t_tc_ms = 0;
   float t_matvec_ms = 0;  // last cpm_apply_E: the matvec launches alone
@@ -158,8 +158,8 @@ void launch_split_bf16(const float* A, int64_t len, void* p0, void* p1, void* p2
                        cudaStream_t s);
 int launch_ek_tc(const void* p0, const void* p1, const void* p2, int npad, int mpad, int n,
                  int kb_begin, int kb6_end, int kb3_end, const uint32_t* chunk_end,
-                 const double* head, int64_t ldh,
-                 float* E, int64_t ldE, int* err, cudaStream_t s);
+                 const double* head, int64_t ldh, float* E, int64_t ldE, int* err,
+                 cudaStream_t s);
 void launch_extract_diag(bool fp64, const void* E, int n, int64_t ldE, double* diag,
                          cudaStream_t s);
 void launch_get_E(bool fp64, const void* E, int n, int64_t ldE, const double* xyz,
@@ -184,6 +184,20 @@ void launch_bsol_real_and_finish(const double* xyz, const double* alpha, const u
                                  double* b_out, double* qsol, cudaStream_t s);
 
 // pcg.cu
+// One system of a ragged batch: a right-hand side with its own (float) matrix, size and
+// preconditioner.  Vectors of the batch are laid out [system][ld], zero past n.
+struct SysCol {
+  const float* E;
+  int64_t ldE;
+  int n;
+  const int64_t* nbr_off;  // PCG-DC pattern (row form) and values, p_gap
+  const int* nbr_idx;
+  const double* prow;
+  double pgap;
+  const double* inv_diag;  // Jacobi
+  const double* d;         // neutralising vector
+};
+
 struct SolveArgs {
   int nrhs;
   const double* b;   // [nrhs*n]; multiplied by bscale to give e/A
@@ -196,11 +210,15 @@ struct SolveArgs {
   double* relres;    // host [nrhs]
   void* ws = nullptr;    // optional fixed device workspace (else the context's, grown)
   size_t ws_bytes = 0;
+  const SysCol* sys = nullptr;  // ragged batch: device array [nrhs], one system per column
 };
 int pcg_solve(Ctx* c, const SolveArgs& a);
 int apply_E(Ctx* c, int nrhs, const double* p, double* q);  // device arrays [nrhs][n]
 void launch_neutralize(double* q, int nrhs, int n, const double* d, const double* qsol,
                        cudaStream_t s);
+// ragged batch: q [count][ld], system c neutralised with its own d over its n
+void launch_neutralize_ragged(double* q, int count, int64_t ld, const SysCol* sys,
+                              const double* qsol, cudaStream_t s);
 
 // dc.cu
 int build_dc_preconditioner(Ctx* c);

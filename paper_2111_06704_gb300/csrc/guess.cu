@@ -9,6 +9,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "cpm_internal.cuh"
 
@@ -31,17 +32,13 @@ __device__ __forceinline__ float silu_grad(float z) {
 }
 
 // Shell of every PCG-DC pattern entry (k - 1/2 <= r < k + 1/2, k = 1..8; 0 outside or
-// for the atom itself) and the inverse shell populations; the electrode is fixed, so this
-// geometry is made once and every frame only sums potentials.
-__global__ void k_shell_table(int n, const double* __restrict__ xyz, double lx, double ly,
+// for the atom itself).  The electrode is fixed, so this geometry is found once; the host
+// then files the entries of each atom by shell.
+__global__ void k_shell_codes(int n, const double* __restrict__ xyz, double lx, double ly,
                               double lz, const int64_t* __restrict__ off,
-                              const int* __restrict__ idx, uint8_t* __restrict__ shell,
-                              float* __restrict__ inv) {
+                              const int* __restrict__ idx, uint8_t* __restrict__ shell) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  int cnt[8];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) cnt[k] = 0;
   const double xi = xyz[3 * i], yi = xyz[3 * i + 1], zi = xyz[3 * i + 2];
   for (int64_t e = off[i]; e < off[i + 1]; ++e) {
     const int j = idx[e];
@@ -55,56 +52,58 @@ __global__ void k_shell_table(int n, const double* __restrict__ xyz, double lx, 
       if (k < 1 || k > 8) k = 0;
     }
     shell[e] = (uint8_t)k;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) cnt[q] += k == q + 1;
   }
-#pragma unroll
-  for (int k = 0; k < 8; ++k) inv[(int64_t)i * 8 + k] = cnt[k] ? 1.0f / (float)cnt[k] : 0.f;
 }
 
-// Features of atom i in frame f (unscaled): 0 the potential change b - b_prev, 1-8 its
-// shell means, 9 b, 10-17 the shell means of b, 18 chi, 19 the side of the electrode
-// (+1 above the mean height), 20-31 zero.
-__global__ void k_guess_features(int n, int frames, const double* __restrict__ b,
-                                 const double* __restrict__ b_prev,
+// The potentials of a frame as floats: (b - b_prev, b) per atom.
+__global__ void k_guess_prep(int64_t len, const double* __restrict__ b,
+                             const double* __restrict__ b_prev, float2* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = make_float2((float)(b[e] - b_prev[e]), (float)b[e]);
+}
+
+// Features of atom i in frame f (unscaled): 0 the potential change Delta b = b - b_prev,
+// 1-8 its means over the neighbour shells k = 1..8, 9 b, 10-17 the shell means of b,
+// 18 chi, 19 the side of the electrode (+1 above the mean height), 20 (P Delta b) / k_e
+// with the PCG-DC preconditioner's pattern entries, 21-31 zero.
+__global__ void k_guess_features(int n, int frames, const float2* __restrict__ pot,
                                  const double* __restrict__ chi,
                                  const double* __restrict__ xyz, double zmean,
+                                 const int64_t* __restrict__ sh_off,
+                                 const int* __restrict__ sh_idx,
                                  const int64_t* __restrict__ off, const int* __restrict__ idx,
-                                 const uint8_t* __restrict__ shell,
-                                 const float* __restrict__ inv, float* __restrict__ feat) {
+                                 const double* __restrict__ prow, double pgap,
+                                 float* __restrict__ feat) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int f = blockIdx.y;
   if (i >= n || f >= frames) return;
-  const double* bf = b + (int64_t)f * n;
-  const double* pf = b_prev + (int64_t)f * n;
-  double sd[8], sb[8];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) sd[k] = sb[k] = 0.0;
-  for (int64_t e = off[i]; e < off[i + 1]; ++e) {
-    const int k = shell[e];
-    if (!k) continue;
-    const int j = idx[e];
-    const double bj = bf[j], dj = bj - pf[j];
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-      if (k == q + 1) {
-        sd[q] += dj;
-        sb[q] += bj;
-      }
-  }
+  const float2* pf = pot + (int64_t)f * n;
   float* out = feat + ((int64_t)f * n + i) * kF;
-  const float* w = inv + (int64_t)i * 8;
-  out[0] = (float)(bf[i] - pf[i]);
+  const float2 self = pf[i];
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    out[1 + k] = (float)(sd[k] * (double)w[k]);
-    out[10 + k] = (float)(sb[k] * (double)w[k]);
+    const int64_t e0 = sh_off[(int64_t)i * 8 + k], e1 = sh_off[(int64_t)i * 8 + k + 1];
+    float sd = 0.f, sb = 0.f;
+    for (int64_t e = e0; e < e1; ++e) {
+      const float2 v = pf[sh_idx[e]];
+      sd += v.x;
+      sb += v.y;
+    }
+    const float inv = e1 > e0 ? 1.0f / (float)(e1 - e0) : 0.f;
+    out[1 + k] = sd * inv;
+    out[10 + k] = sb * inv;
   }
-  out[9] = (float)bf[i];
+  float pz = 0.f;
+  for (int64_t e = off[i]; e < off[i + 1]; ++e)
+    pz = fmaf((float)(prow[e] + pgap), pf[idx[e]].x, pz);
+  out[0] = self.x;
+  out[9] = self.y;
   out[18] = (float)chi[i];
   out[19] = xyz[3 * i + 2] > zmean ? 1.f : -1.f;
+  out[20] = pz * (float)(1.0 / kKe);
 #pragma unroll
-  for (int c = 20; c < kF; ++c) out[c] = 0.f;
+  for (int c = 21; c < kF; ++c) out[c] = 0.f;
 }
 
 __device__ void load_params(const float* __restrict__ params, float* w, int bf16) {
@@ -398,29 +397,65 @@ int cpm_guess_features(cpm_ctx* c, int frames, const double* b, const double* b_
   if (frames < 1 || !on_device(b) || !on_device(b_prev) || !on_device(chi) || !on_device(feat))
     return set_err(c, CPM_EINVAL, "cpm_guess_features: frames >= 1 and device arrays");
   int st = CPM_OK;
+  const int n = c->n;
   if (!c->shells_ready) {  // frame-independent geometry, once per electrode
-    std::vector<double> hx(3 * (size_t)c->n);
+    Buf codes;
+    if ((st = buf_alloc(c, &codes, std::max<int64_t>(c->nnz, 1)))) return st;
+    (k_shell_codes<<<(n + 127) / 128, 128, 0, c->stream>>>(
+         n, (const double*)c->xyz.ptr, c->p.box[0], c->p.box[1], c->p.box[2],
+         (const int64_t*)c->nbr_off.ptr, (const int*)c->nbr_idx.ptr, (uint8_t*)codes.ptr),
+     note_launch());
+    std::vector<double> hx(3 * (size_t)n);
+    std::vector<int64_t> hoff(n + 1);
+    std::vector<int> hidx(c->nnz);
+    std::vector<uint8_t> hk(c->nnz);
     st = cuda_check(c, cudaMemcpyAsync(hx.data(), c->xyz.ptr, hx.size() * sizeof(double),
                                        cudaMemcpyDeviceToHost, c->stream), "xyz");
-    if (!st) st = cuda_check(c, cudaStreamSynchronize(c->stream), "xyz sync");
-    if (!st) st = buf_alloc(c, &c->shell_k, std::max<int64_t>(c->nnz, 1));
-    if (!st) st = buf_alloc(c, &c->shell_inv, 8 * sizeof(float) * (size_t)c->n);
+    if (!st) st = cuda_check(c, cudaMemcpyAsync(hoff.data(), c->nbr_off.ptr,
+                                                hoff.size() * sizeof(int64_t),
+                                                cudaMemcpyDeviceToHost, c->stream), "off");
+    if (!st) st = cuda_check(c, cudaMemcpyAsync(hidx.data(), c->nbr_idx.ptr,
+                                                hidx.size() * sizeof(int),
+                                                cudaMemcpyDeviceToHost, c->stream), "idx");
+    if (!st) st = cuda_check(c, cudaMemcpyAsync(hk.data(), codes.ptr, hk.size(),
+                                                cudaMemcpyDeviceToHost, c->stream), "codes");
+    if (!st) st = cuda_check(c, cudaStreamSynchronize(c->stream), "shell sync");
+    buf_free(c, &codes);
     if (st) return st;
+    // entries of atom i filed by shell: bucket (i, k) = sh_off[8 i + k] .. sh_off[8 i + k + 1]
+    std::vector<int64_t> so(8 * (size_t)n + 1, 0);
+    for (int i = 0; i < n; ++i)
+      for (int64_t e = hoff[i]; e < hoff[i + 1]; ++e)
+        if (hk[e]) ++so[8 * (size_t)i + hk[e]];
+    for (size_t t = 1; t < so.size(); ++t) so[t] += so[t - 1];
+    std::vector<int> sj(std::max<int64_t>(so.back(), 1));
+    std::vector<int64_t> fill(so.begin(), so.end() - 1);
+    for (int i = 0; i < n; ++i)
+      for (int64_t e = hoff[i]; e < hoff[i + 1]; ++e)
+        if (hk[e]) sj[fill[8 * (size_t)i + hk[e] - 1]++] = hidx[e];
     double zm = 0.0;
-    for (int i = 0; i < c->n; ++i) zm += hx[3 * i + 2];
-    c->zmean = zm / c->n;
-    (k_shell_table<<<(c->n + 127) / 128, 128, 0, c->stream>>>(
-         c->n, (const double*)c->xyz.ptr, c->p.box[0], c->p.box[1], c->p.box[2],
-         (const int64_t*)c->nbr_off.ptr, (const int*)c->nbr_idx.ptr, (uint8_t*)c->shell_k.ptr,
-         (float*)c->shell_inv.ptr), note_launch());
-    if ((st = cuda_check(c, cudaGetLastError(), "shell table"))) return st;
+    for (int i = 0; i < n; ++i) zm += hx[3 * i + 2];
+    c->zmean = zm / n;
+    if ((st = buf_alloc(c, &c->shell_off, so.size() * sizeof(int64_t))) ||
+        (st = buf_alloc(c, &c->shell_members, sj.size() * sizeof(int))))
+      return st;
+    st = cuda_check(c, cudaMemcpy(c->shell_off.ptr, so.data(), so.size() * sizeof(int64_t),
+                                  cudaMemcpyHostToDevice), "shell offsets");
+    if (!st) st = cuda_check(c, cudaMemcpy(c->shell_members.ptr, sj.data(), sj.size() * sizeof(int),
+                                           cudaMemcpyHostToDevice), "shell members");
+    if (st) return st;
     c->shells_ready = true;
   }
-  dim3 grid((c->n + 127) / 128, frames);
+  const int64_t len = (int64_t)frames * n;
+  if ((st = buf_reserve(c, &c->ws_guess, len * sizeof(float2)))) return st;
+  (k_guess_prep<<<(int)std::min<int64_t>((len + 255) / 256, 8192), 256, 0, c->stream>>>(
+       len, b, b_prev, (float2*)c->ws_guess.ptr), note_launch());
+  dim3 grid((n + 127) / 128, frames);
   (k_guess_features<<<grid, 128, 0, c->stream>>>(
-      c->n, frames, b, b_prev, chi, (const double*)c->xyz.ptr, c->zmean,
-      (const int64_t*)c->nbr_off.ptr, (const int*)c->nbr_idx.ptr,
-      (const uint8_t*)c->shell_k.ptr, (const float*)c->shell_inv.ptr, feat), note_launch());
+       n, frames, (const float2*)c->ws_guess.ptr, chi, (const double*)c->xyz.ptr, c->zmean,
+       (const int64_t*)c->shell_off.ptr, (const int*)c->shell_members.ptr,
+       (const int64_t*)c->nbr_off.ptr, (const int*)c->nbr_idx.ptr,
+       (const double*)c->prow.ptr, c->pgap, feat), note_launch());
   if ((st = cuda_check(c, cudaGetLastError(), "features"))) return st;
   return cuda_check(c, cudaStreamSynchronize(c->stream), "features sync");
 }

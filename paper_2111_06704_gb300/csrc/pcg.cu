@@ -64,9 +64,18 @@ template <int NR>
 __global__ void __launch_bounds__(kThreads)
 k_matvec_f64(const double* __restrict__ E, int64_t ldE, int n, const double* __restrict__ pv,
              int64_t ldv, int c0, int nrhs, double* __restrict__ q,
-             double* __restrict__ pq_part) {
+             double* __restrict__ pq_part, const ColState* __restrict__ st) {
   __shared__ double sm[32 * NR];
   c0 += blockIdx.y * NR;  // one column group per grid row
+  if (st) {  // converged columns are not multiplied again (uniform per block)
+    bool live = false;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) live |= st[c0 + r].done == 0;
+    if (!live) {
+      if (threadIdx.x < NR) pq_part[(int64_t)blockIdx.x * nrhs + c0 + threadIdx.x] = 0.0;
+      return;
+    }
+  }
   const int lane = threadIdx.x & 31;
   const int wid = blockIdx.x * kMvWarps + (threadIdx.x >> 5);
   const int nwarps = gridDim.x * kMvWarps;
@@ -130,9 +139,19 @@ template <int NR>
 __global__ void __launch_bounds__(kThreads)
 k_matvec_f32(const float* __restrict__ E, int64_t ldE, int n, const float* __restrict__ pv,
              const float* __restrict__ plo, const double* __restrict__ p64, int64_t ldv,
-             int c0, int nrhs, double* __restrict__ q, double* __restrict__ pq_part) {
+             int c0, int nrhs, double* __restrict__ q, double* __restrict__ pq_part,
+             const ColState* __restrict__ st) {
   constexpr int RB = kMvRows;
   c0 += blockIdx.y * NR;  // one column group per grid row
+  if (st) {  // converged columns are not multiplied again (uniform per block)
+    bool live = false;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) live |= st[c0 + r].done == 0;
+    if (!live) {
+      if (threadIdx.x < NR) pq_part[(int64_t)blockIdx.x * nrhs + c0 + threadIdx.x] = 0.0;
+      return;
+    }
+  }
   __shared__ float2 sm[kMvWarps][RB * NR];
   __shared__ double spq[RB * NR];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -207,6 +226,91 @@ k_matvec_f32(const float* __restrict__ E, int64_t ldE, int n, const float* __res
   }
 }
 
+// Ragged batch: column c is system c with its own float E (ld, n); one column per grid
+// row, the same arithmetic as k_matvec_f32<1>.  Row blocks past the system's n write a
+// zero partial.
+__global__ void __launch_bounds__(kThreads)
+k_matvec_ragged(const SysCol* __restrict__ sys, const float* __restrict__ pv,
+                const float* __restrict__ plo, const double* __restrict__ p64, int64_t ldv,
+                int nrhs, double* __restrict__ q, double* __restrict__ pq_part,
+                const ColState* __restrict__ st) {
+  constexpr int RB = kMvRows;
+  __shared__ float2 sm[kMvWarps][RB];
+  __shared__ double spq[RB];
+  const int c = blockIdx.y;
+  const int n = (st && st[c].done) ? 0 : sys[c].n;  // converged: only the zero partial
+  const int64_t ldE = sys[c].ldE;
+  const float* E = sys[c].E;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int row0 = blockIdx.x * RB;
+  if (row0 >= n) {  // uniform per block
+    if (threadIdx.x == 0) pq_part[(int64_t)blockIdx.x * nrhs + c] = 0.0;
+    return;
+  }
+  const int ngroups = (int)(ldE >> 7);
+  const float* erow[RB];
+#pragma unroll
+  for (int i = 0; i < RB; ++i) erow[i] = E + (int64_t)min(row0 + i, n - 1) * ldE;
+  float part[RB], perr[RB];
+#pragma unroll
+  for (int i = 0; i < RB; ++i) part[i] = perr[i] = 0.f;
+  const float* ph = pv + (int64_t)c * ldv;
+  const float* pl = plo + (int64_t)c * ldv;
+  for (int g = warp; g < ngroups; g += kMvWarps) {
+    const int64_t cc = (int64_t)g * 128 + lane * 4;
+    float ev[RB][4];
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+      *reinterpret_cast<float4*>(ev[i]) = __ldcs(reinterpret_cast<const float4*>(erow[i] + cc));
+    float hv[4], lv[4];
+    *reinterpret_cast<float4*>(hv) = __ldg(reinterpret_cast<const float4*>(ph + cc));
+    *reinterpret_cast<float4*>(lv) = __ldg(reinterpret_cast<const float4*>(pl + cc));
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const float e = ev[i][w];
+        const float pr = e * hv[w];
+        const float s = part[i] + pr;
+        const float bb = s - part[i];
+        const float e2 = (part[i] - (s - bb)) + (pr - bb);
+        perr[i] = fmaf(e, lv[w], perr[i] + (fmaf(e, hv[w], -pr) + e2));
+        part[i] = s;
+      }
+  }
+#pragma unroll
+  for (int i = 0; i < RB; ++i) {
+    float h = part[i], l = perr[i];
+#pragma unroll
+    for (int o = 16; o; o >>= 1)
+      pair_add(h, l, __shfl_xor_sync(0xffffffffu, h, o), __shfl_xor_sync(0xffffffffu, l, o));
+    if (lane == 0) sm[warp][i] = make_float2(h, l);
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  if (t < RB) {
+    float h = sm[0][t].x, l = sm[0][t].y;
+#pragma unroll
+    for (int w = 1; w < kMvWarps; ++w) pair_add(h, l, sm[w][t].x, sm[w][t].y);
+    const int row = row0 + t;
+    double pq = 0.0;
+    if (row < n) {
+      const int64_t o = (int64_t)c * ldv + row;
+      const double v = (double)h + (double)l;
+      q[o] = v;
+      pq = v * p64[o];
+    }
+    spq[t] = pq;
+  }
+  __syncthreads();
+  if (t == 0) {
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < RB; ++i) s += spq[i];
+    pq_part[(int64_t)blockIdx.x * nrhs + c] = s;
+  }
+}
+
 // alpha = r^T z / p^T q for every running column.
 __global__ void k_alpha(const double* __restrict__ pq_part, int nparts, int nrhs,
                         ColState* __restrict__ st) {
@@ -236,12 +340,18 @@ __global__ void __launch_bounds__(kThreads)
 k_update(int n, int64_t ldv, int nrhs, const ColState* __restrict__ st,
          double* __restrict__ x, double* __restrict__ r, double* __restrict__ z,
          const double* __restrict__ p, const double* __restrict__ q,
-         const double* __restrict__ inv_diag, double* __restrict__ dots) {
+         const double* __restrict__ inv_diag, double* __restrict__ dots,
+         const SysCol* __restrict__ sys) {
   __shared__ double sm[32 * 4];
   {
     const int col = blockIdx.y;  // one right-hand side per grid row
+    if (sys) {  // ragged batch: this column's system
+      n = sys[col].n;
+      inv_diag = sys[col].inv_diag;
+    }
     const double a = st[col].alpha;
     const bool active = st[col].done == 0;
+    if (!active) return;  // converged column: its dots are not read (uniform per block)
     double v[4] = {0, 0, 0, 0};
     const int64_t o = (int64_t)col * ldv;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -274,12 +384,20 @@ k_dc_apply(int n, int64_t ldv, int nrhs, const ColState* __restrict__ st,
            const int64_t* __restrict__ off, const int* __restrict__ idx,
            const double* __restrict__ prow, double pgap, const double* __restrict__ r,
            double* __restrict__ z, const double* __restrict__ rsum_part, int nparts,
-           double* __restrict__ dots, int first) {
+           double* __restrict__ dots, int first, const SysCol* __restrict__ sys) {
   __shared__ double sm[32 * 2];
   __shared__ double s_rsum;
   {
     const int col = blockIdx.y;
+    if (sys) {  // ragged batch: this column's system
+      n = sys[col].n;
+      off = sys[col].nbr_off;
+      idx = sys[col].nbr_idx;
+      prow = sys[col].prow;
+      pgap = sys[col].pgap;
+    }
     const bool active = first || st[col].done == 0;
+    if (!active) return;  // converged column (uniform per block)
     if (threadIdx.x < 32) {
       double s = 0.0;
       if (pgap != 0.0)
@@ -365,13 +483,18 @@ __global__ void k_init_r(int n, int64_t ldv, int nrhs, const double* __restrict_
                          const double* __restrict__ q2, int use_guess, double* __restrict__ r,
                          double* __restrict__ x, double* __restrict__ z,
                          const double* __restrict__ inv_diag, int pre,
-                         double* __restrict__ dots) {
+                         double* __restrict__ dots, const SysCol* __restrict__ sys) {
   __shared__ double sm[32 * 4];
   {
     const int col = blockIdx.y;
     const int64_t o = (int64_t)col * ldv;
+    int nc = n;  // rows of this column's system (b rows are n apart)
+    if (sys) {
+      nc = sys[col].n;
+      inv_diag = sys[col].inv_diag;
+    }
     double v[4] = {0, 0, 0, 0};  // r^T z, b^T b, r^T r, sum r
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
       const double bi = b[(int64_t)col * n + i] * bscale;
       const double ri = use_guess ? bi - q[o + i] - (q2 ? q2[o + i] : 0.0) : bi;
       r[o + i] = ri;
@@ -450,6 +573,24 @@ __global__ void k_neutralize(double* __restrict__ q, int n, const double* __rest
   for (int i = threadIdx.x; i < n; i += blockDim.x) qc[i] -= t * d[i];
 }
 
+__global__ void k_neutralize_ragged(double* __restrict__ q, int64_t ld,
+                                    const SysCol* __restrict__ sys,
+                                    const double* __restrict__ qsol) {
+  __shared__ double sm[32];
+  __shared__ double s_tot;
+  const int col = blockIdx.x;
+  const int n = sys[col].n;
+  const double* d = sys[col].d;
+  double* qc = q + (int64_t)col * ld;
+  double v[1] = {0.0};
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v[0] += qc[i];
+  block_sum<1>(v, sm);
+  if (threadIdx.x == 0) s_tot = v[0] + (qsol ? qsol[col] : 0.0);
+  __syncthreads();
+  const double t = s_tot;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) qc[i] -= t * d[i];
+}
+
 int sm_count(int device) {
   int v = 0;
   cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
@@ -464,7 +605,8 @@ int matvec_parts(const Ctx* c) {
 
 template <typename T>
 void launch_matvec(const Ctx* c, const void* pv, const void* plo, const double* p64,
-                   int64_t ldv, int nrhs, double* q, double* pq_part, int gm);
+                   int64_t ldv, int nrhs, double* q, double* pq_part, int gm,
+                   const ColState* st);
 
 // Launches KERNEL<NR> over all nrhs columns: full groups of four columns as grid rows of
 // one launch, then a pair and a single column for the remainder.
@@ -484,25 +626,27 @@ void for_column_groups(int nrhs, Launch&& launch) {
 // FP64 storage (the plain baseline build): one warp per row, FP64 products and sums.
 template <>
 void launch_matvec<double>(const Ctx* c, const void* pv, const void*, const double*,
-                           int64_t ldv, int nrhs, double* q, double* pq_part, int gm) {
+                           int64_t ldv, int nrhs, double* q, double* pq_part, int gm,
+                           const ColState* st) {
   const double* E = (const double*)c->E.ptr;
   const double* hi = (const double*)pv;
   for_column_groups(nrhs, [&](auto nr, int c0, int ny) {
     (k_matvec_f64<decltype(nr)::value><<<dim3(gm, ny), kThreads, 0, c->stream>>>(
-         E, c->ldE, c->n, hi, ldv, c0, nrhs, q, pq_part), note_launch());
+         E, c->ldE, c->n, hi, ldv, c0, nrhs, q, pq_part, st), note_launch());
   });
 }
 
 // FP32 storage: k_matvec_f32, four columns per pass over E.
 template <>
 void launch_matvec<float>(const Ctx* c, const void* pv, const void* plo, const double* p64,
-                          int64_t ldv, int nrhs, double* q, double* pq_part, int gm) {
+                          int64_t ldv, int nrhs, double* q, double* pq_part, int gm,
+                          const ColState* st) {
   const float* E = (const float*)c->E.ptr;
   const float* hi = (const float*)pv;
   const float* lo = (const float*)plo;
   for_column_groups(nrhs, [&](auto nr, int c0, int ny) {
     (k_matvec_f32<decltype(nr)::value><<<dim3(gm, ny), kThreads, 0, c->stream>>>(
-         E, c->ldE, c->n, hi, lo, p64, ldv, c0, nrhs, q, pq_part), note_launch());
+         E, c->ldE, c->n, hi, lo, p64, ldv, c0, nrhs, q, pq_part, st), note_launch());
   });
 }
 
@@ -557,6 +701,17 @@ int pcg_solve(Ctx* c, const SolveArgs& a) {
   double* dots_dc = (double*)(base + odc);
   ColState* st = (ColState*)(base + ost);
   cudaStream_t s = c->stream;
+  // cur: the column states (converged columns are skipped), nullptr before they exist
+  auto matvec = [&](const ColState* cur) {
+    if (f64) {
+      launch_matvec<double>(c, pv, nullptr, p, ldv, nrhs, q, pq_part, gm, cur);
+    } else if (a.sys) {  // ragged batch: one system per column
+      (k_matvec_ragged<<<dim3(gm, nrhs), kThreads, 0, s>>>(a.sys, (const float*)pv, plo, p, ldv,
+                                                           nrhs, q, pq_part, cur), note_launch());
+    } else {
+      launch_matvec<float>(c, pv, plo, p, ldv, nrhs, q, pq_part, gm, cur);
+    }
+  };
   // zero the padded vectors so the matvec can read whole padded rows
   if (cuda_check(c, cudaMemsetAsync(base, 0, ost, s), "memset")) return CPM_ECUDA;
 
@@ -569,23 +724,19 @@ int pcg_solve(Ctx* c, const SolveArgs& a) {
                                         n * sizeof(double), cudaMemcpyDeviceToDevice, s),
                      "copy guess"))
         return CPM_ECUDA;
-    if (f64) {
-      (k_p_update<double><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, st, x, p, (double*)pv, nullptr, 1), note_launch());
-      launch_matvec<double>(c, pv, nullptr, p, ldv, nrhs, q, pq_part, gm);
-    } else {
-      (k_p_update<float><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, st, x, p, (float*)pv, plo, 1), note_launch());
-      launch_matvec<float>(c, pv, plo, p, ldv, nrhs, q, pq_part, gm);
-    }
+    if (f64) (k_p_update<double><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, st, x, p, (double*)pv, nullptr, 1), note_launch());
+    else (k_p_update<float><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, st, x, p, (float*)pv, plo, 1), note_launch());
+    matvec(nullptr);
   }
   (k_init_r<<<g2, kThreads, 0, s>>>(n, ldv, nrhs, a.b, a.bscale, q, q2, a.use_guess ? 1 : 0, r, x, z,
-                                   inv_diag, pre, dots), note_launch());
+                                   inv_diag, pre, dots, a.sys), note_launch());
   const int wb = 8;  // warps per block for the per-column reductions
   const int gcol = (nrhs + wb - 1) / wb;
   (k_init_state<<<gcol, wb * 32, 0, s>>>(dots, ge, nrhs, a.tol, pre, st), note_launch());
   if (pre == CPM_PRECOND_DC) {
     (k_dc_apply<<<g2, kThreads, 0, s>>>(n, ldv, nrhs, st, (const int64_t*)c->nbr_off.ptr,
                                        (const int*)c->nbr_idx.ptr, (const double*)c->prow.ptr,
-                                       c->pgap, r, z, dots, ge, dots_dc, 1), note_launch());
+                                       c->pgap, r, z, dots, ge, dots_dc, 1, a.sys), note_launch());
     (k_init_rz_dc<<<gcol, wb * 32, 0, s>>>(dots_dc, ge, nrhs, st), note_launch());
   }
   if (f64) (k_p_update<double><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, st, z, p, (double*)pv, nullptr, 1), note_launch());
@@ -613,22 +764,21 @@ int pcg_solve(Ctx* c, const SolveArgs& a) {
   while (!all_done && it < a.maxit) {
     ColState* cur = st + (size_t)(it & 1) * nrhs;
     ColState* nxt = st + (size_t)((it + 1) & 1) * nrhs;
-    if (f64) launch_matvec<double>(c, pv, nullptr, p, ldv, nrhs, q, pq_part, gm);
-    else launch_matvec<float>(c, pv, plo, p, ldv, nrhs, q, pq_part, gm);
+    matvec(cur);
     (k_alpha<<<gcol, wb * 32, 0, s>>>(pq_part, gm, nrhs, cur), note_launch());
     if (pre == CPM_PRECOND_DC) {
       (k_update<CPM_PRECOND_DC><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, cur, x, r, z, p, q,
-                                                       inv_diag, dots), note_launch());
+                                                       inv_diag, dots, a.sys), note_launch());
       (k_dc_apply<<<g2, kThreads, 0, s>>>(n, ldv, nrhs, cur, (const int64_t*)c->nbr_off.ptr,
                                          (const int*)c->nbr_idx.ptr,
                                          (const double*)c->prow.ptr, c->pgap, r, z, dots, ge,
-                                         dots, 0), note_launch());
+                                         dots, 0, a.sys), note_launch());
     } else if (pre == CPM_PRECOND_JACOBI) {
       (k_update<CPM_PRECOND_JACOBI><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, cur, x, r, z, p, q,
-                                                           inv_diag, dots), note_launch());
+                                                           inv_diag, dots, a.sys), note_launch());
     } else {
       (k_update<CPM_PRECOND_NONE><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, cur, x, r, z, p, q,
-                                                         inv_diag, dots), note_launch());
+                                                         inv_diag, dots, a.sys), note_launch());
     }
     (k_beta<<<gcol, wb * 32, 0, s>>>(dots, ge, nrhs, a.tol, flexible, cur, nxt), note_launch());
     if (f64) (k_p_update<double><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, nxt, z, p, (double*)pv, nullptr, 0), note_launch());
@@ -692,8 +842,8 @@ int apply_E(Ctx* c, int nrhs, const double* p_in, double* q_out) {
   if (f64) (k_p_update<double><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, st, zin, p, (double*)pv, nullptr, 1), note_launch());
   else (k_p_update<float><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, st, zin, p, (float*)pv, plo, 1), note_launch());
   cudaEventRecord(c->ev_tc[0], s);
-  if (f64) launch_matvec<double>(c, pv, nullptr, p, ldv, nrhs, q, pq_part, gm);
-  else launch_matvec<float>(c, pv, plo, p, ldv, nrhs, q, pq_part, gm);
+  if (f64) launch_matvec<double>(c, pv, nullptr, p, ldv, nrhs, q, pq_part, gm, nullptr);
+  else launch_matvec<float>(c, pv, plo, p, ldv, nrhs, q, pq_part, gm, nullptr);
   cudaEventRecord(c->ev_tc[1], s);
   if (cuda_check(c, cudaGetLastError(), "apply_E")) return CPM_ECUDA;
   for (int col = 0; col < nrhs; ++col)
@@ -703,6 +853,11 @@ int apply_E(Ctx* c, int nrhs, const double* p_in, double* q_out) {
   if (cuda_check(c, cudaStreamSynchronize(s), "apply_E sync")) return CPM_ECUDA;
   cudaEventElapsedTime(&c->t_matvec_ms, c->ev_tc[0], c->ev_tc[1]);
   return CPM_OK;
+}
+
+void launch_neutralize_ragged(double* q, int count, int64_t ld, const SysCol* sys,
+                              const double* qsol, cudaStream_t s) {
+  (k_neutralize_ragged<<<count, 1024, 0, s>>>(q, ld, sys, qsol), note_launch());
 }
 
 void launch_neutralize(double* q, int nrhs, int n, const double* d, const double* qsol,

@@ -1,9 +1,9 @@
 """Learned initial guess on the GPU against the FP64 oracle (features, forward pass,
 gradient), and what the trained network gains over the previous-step guess.
 
-Tolerances: features are FP64 sums stored as float (1e-6 of each column's scale); the
-forward pass and gradient accumulate in FP32 over 32-64-term dot products and over the
-samples, so FP32-weight results match the FP64 oracle to 1e-5 (relative); with BF16
+Tolerances: features are float sums of float-rounded potentials (1e-6 of each column's
+scale); the forward pass and gradient accumulate in FP32 over 32-64-term dot products and
+over the samples, so FP32-weight results match the FP64 oracle to 1e-5 (relative); with BF16
 weights the oracle is evaluated at the same BF16-rounded weights and the gap to the FP32
 oracle is held to 1e-3, as the BF16 rounding of the weights (2^-9) allows.
 """
@@ -52,10 +52,10 @@ def test_features_match_the_oracle(walk):
     g = LearnedGuess(ctx)
     chi = _dev(el.chi)
     feat = g.features(b[1:4], b[0:3], chi).cpu().numpy()
-    nb = pc.neighbours(el.xyz, el.box, wl.RCUT_DC)
+    p_dc, nb = pc.dc_preconditioner(el.xyz, el.alpha, el.box, wl.G_DC, wl.RCUT_DC)
     bh = b.cpu().numpy()
     for k in range(3):
-        ref = mlp.features(bh[k + 1], bh[k], el.chi, el.xyz, el.box, nb)
+        ref = mlp.features(bh[k + 1], bh[k], el.chi, el.xyz, el.box, nb, p_dc)
         scale = np.maximum(np.abs(ref).max(axis=0), 1e-30)
         assert np.all(np.abs(feat[k] - ref) <= 1e-6 * scale + 1e-12)
 

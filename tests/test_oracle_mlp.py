@@ -6,6 +6,7 @@ import math
 import numpy as np
 import pytest
 
+from oracle import ewald as ew
 from oracle import mlp
 from paper_2111_06704_gb300 import workloads as wl
 from oracle import precond as pc
@@ -54,7 +55,8 @@ def test_shell_features_on_a_uniform_sheet():
     el = wl.two_sheet_electrode(7, 4)  # box edges above 2 x 8 A
     nb = pc.neighbours(el.xyz, el.box, 8.0)
     b = np.full(el.n, 0.25)
-    f = mlp.features(b, b, el.chi, el.xyz, el.box, nb)
+    p0 = np.zeros((el.n, el.n))  # the P feature is pinned separately below
+    f = mlp.features(b, b, el.chi, el.xyz, el.box, nb, p0)
     assert np.allclose(f[:, 0], 0.0) and np.allclose(f[:, 1:9], 0.0)
     assert np.allclose(f[:, 9], 0.25)
     filled = f[:, 10:18] != 0.0
@@ -62,7 +64,7 @@ def test_shell_features_on_a_uniform_sheet():
     assert set(np.unique(f[:, 19])) == {-1.0, 1.0}
     b2 = b.copy()
     b2[0] += 1.0
-    g = mlp.features(b2, b, el.chi, el.xyz, el.box, nb)
+    g = mlp.features(b2, b, el.chi, el.xyz, el.box, nb, p0)
     assert g[0, 0] == 1.0 and np.all(g[0, 1:9] == 0.0)
     # nearest neighbours of atom 0 (1.42 A: shell k = 1) see it in their first shell
     d = el.xyz - el.xyz[0]
@@ -77,3 +79,20 @@ def test_shell_features_on_a_uniform_sheet():
         rj = np.sqrt((dj * dj).sum(axis=1))
         members = np.count_nonzero((rj >= 0.5) & (rj < 1.5))
         assert g[j, 1] == pytest.approx(1.0 / members)
+
+
+def test_dc_feature_is_the_local_inverse_applied_to_the_change():
+    # when every neighbourhood holds the whole system, column tau of M_tau^-1 is column
+    # tau of the inverse of one global matrix M (Eq. 36 with all atoms), so feature 20,
+    # (P Delta b) / k_e, solves M x = Delta b / k_e: check by multiplying back
+    rng = np.random.default_rng(4)
+    box = (30.0, 30.0, 30.0)
+    xyz = rng.uniform(0, 4.0, (9, 3)) + 10.0
+    alpha = np.full(9, 1.979)
+    p, nb = pc.dc_preconditioner(xyz, alpha, box, 0.083, 14.0)
+    assert all(len(x) == 9 for x in nb)
+    m = pc.local_matrix(np.arange(9), xyz, alpha, box, 0.083, 14.0)
+    b0 = rng.standard_normal(9)
+    db = rng.standard_normal(9)
+    f = mlp.features(b0 + db, b0, np.zeros(9), xyz, box, nb, p)
+    assert np.allclose(m @ f[:, 20], db / ew.KE, rtol=0, atol=1e-12)
