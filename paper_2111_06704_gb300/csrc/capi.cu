@@ -395,18 +395,21 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
     launch_structure_operand_head((const double*)c->xyz.ptr, c->npad, n, (const int*)c->hkl.ptr,
                                   (const double*)c->sqw.ptr, c->kh, c->p.box,
                                   (double*)c->Ahead.ptr, s);
-  Buf planes[3], ehead, errbuf;
+  Buf planes[3], ehead, errbuf, hsplit;
   auto free_tc = [&]() {
     for (Buf& b : planes) buf_free(c, &b);
     buf_free(c, &ehead);
     buf_free(c, &errbuf);
+    buf_free(c, &hsplit);
   };
+  const int head_cols = 16 * c->heavy_steps;
   if (tc) {
     const size_t pbytes = (size_t)c->npad * 2 * c->mpad * 2;
     if ((st = buf_alloc(c, &planes[0], pbytes)) || (st = buf_alloc(c, &planes[1], pbytes)) ||
         (st = buf_alloc(c, &planes[2], pbytes)) ||
         (st = buf_alloc(c, &ehead, (size_t)n * c->ldE * sizeof(double))) ||
         (st = buf_alloc(c, &errbuf, sizeof(int))) ||
+        (st = buf_alloc(c, &hsplit, 2 * (size_t)c->npad * std::max(head_cols, 16) * sizeof(float))) ||
         (st = cuda_check(c, cudaMemsetAsync(errbuf.ptr, 0, sizeof(int), s), "err flag"))) {
       free_tc();
       for (auto& e : ev) cudaEventDestroy(e);
@@ -422,7 +425,9 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
     cudaEvent_t ev_head;
     cudaEventCreate(&ev_head);
     cudaEventRecord(ev_head, s);
-    st = launch_ek_head_f64((const double*)c->Ahead.ptr, c->kh, 16 * c->heavy_steps,
+    float* hhi = (float*)hsplit.ptr;
+    st = launch_ek_head_f64((const double*)c->Ahead.ptr, c->kh, head_cols, c->npad, hhi,
+                            hhi + (size_t)c->npad * std::max(head_cols, 16),
                             (const double*)c->xyz.ptr, (const double*)c->alpha.ptr, n, geo,
                             (double*)ehead.ptr, c->ldE, s);
     cudaEventRecord(c->ev_tc[0], s);

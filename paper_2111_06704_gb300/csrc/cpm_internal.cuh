@@ -149,9 +149,9 @@ int launch_ek_simt(bool fp64, const void* A, int npad, int mpad, const double* x
                    int heavy_steps, const uint32_t* flush_mask, cudaStream_t s);
 void launch_mirror_lower(bool fp64, void* E, int n, int64_t ldE, cudaStream_t s);
 
-int launch_ek_head_f64(const double* Ahead, int kh, int ktot, const double* xyz,
-                       const double* alpha, int n, const Geometry& geo, double* Ehead,
-                       int64_t ldE, cudaStream_t s);
+int launch_ek_head_f64(const double* Ahead, int kh, int ktot, int npad, float* hi, float* lo,
+                       const double* xyz, const double* alpha, int n, const Geometry& geo,
+                       double* Ehead, int64_t ldE, cudaStream_t s);
 
 // tc_syrk.cu
 void launch_split_bf16(const float* A, int64_t len, void* p0, void* p1, void* p2,

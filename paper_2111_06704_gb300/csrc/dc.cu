@@ -83,17 +83,43 @@ k_neighbours(const double* __restrict__ xyz, int n, double lx, double ly, double
   if (!fill && live && lane == 0) cnt[t] = c;
 }
 
+// The off-diagonal value of Eq. 36 for every pattern entry (j, j'): (erfc(g r) -
+// erfc(g r_cut)) / r, zero for the atom itself and at r = r_cut.  Every local matrix
+// M_tau only holds pairs within r_cut of each other, i.e. pattern entries, so the FP64
+// erfc runs once per entry instead of once per entry of every local matrix.
+__global__ void k_dc_pairs(const double* __restrict__ xyz, int n, double lx, double ly,
+                           double lz, double g, double rcut, const int64_t* __restrict__ off,
+                           const int* __restrict__ idx, double* __restrict__ val) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double erfc_rc = erfc(g * rcut);
+  const double rc2 = rcut * rcut;
+  for (int64_t e = off[j]; e < off[j + 1]; ++e) {
+    const int k = idx[e];
+    double v = 0.0;
+    if (k != j) {
+      const double r2 = dist2(xyz + 3 * j, xyz + 3 * k, lx, ly, lz);
+      if (r2 < rc2) {
+        const double r = sqrt(r2);
+        v = (erfc(g * r) - erfc_rc) / r;
+      }
+    }
+    val[e] = v;
+  }
+}
+
 // Column tau of M_tau^-1 (Eq. 36), written to pcol[off[tau] .. off[tau+1]).  One block
-// per atom: the symmetric local matrix is filled once per pair, then Gaussian
-// elimination with partial pivoting on [M | e_tau] with one warp per row of the update,
-// then back substitution.
+// per atom: the symmetric local matrix is filled from the pattern's pair values (a pair
+// of tau's neighbours closer than r_cut is an entry of the first one's pattern row,
+// found by binary search), then Gaussian elimination with partial pivoting on
+// [M | e_tau] with one warp per row of the update, then back substitution.
 constexpr int kDcThreads = 128;
 
 __global__ void __launch_bounds__(kDcThreads)
-k_dc_local(const double* __restrict__ xyz, const double* __restrict__ alpha, int n,
-           double lx, double ly, double lz, double g, double rcut,
-           const int64_t* __restrict__ off, const int* __restrict__ idx,
-           double* __restrict__ pcol, int* __restrict__ status) {
+k_dc_local(const double* __restrict__ alpha, const int64_t* __restrict__ off,
+           const int* __restrict__ idx,
+           const double* __restrict__ pval, double* __restrict__ pcol,
+           int* __restrict__ status) {
   extern __shared__ double sm[];
   constexpr int kWarps = kDcThreads / 32;
   const int tau = blockIdx.x;
@@ -102,32 +128,30 @@ k_dc_local(const double* __restrict__ xyz, const double* __restrict__ alpha, int
   const int m = (int)(off[tau + 1] - o);
   const int w = m + 1;  // augmented row width
   double* M = sm;                  // [m][m + 1]
-  double* pos = sm + m * w;        // [m][3]
   __shared__ int s_piv;
   __shared__ double s_val, s_inv;
   for (int a = threadIdx.x; a < m; a += blockDim.x) {
     const int j = idx[o + a];
-    pos[3 * a] = xyz[3 * j];
-    pos[3 * a + 1] = xyz[3 * j + 1];
-    pos[3 * a + 2] = xyz[3 * j + 2];
     const double al = alpha[j];
     M[a * w + a] = isinf(al) ? 0.0 : 0.7978845608028654 * al;  // sqrt(2/pi) alpha_i
     M[a * w + m] = j == tau ? 1.0 : 0.0;
   }
-  __syncthreads();
-  const double erfc_rc = erfc(g * rcut);
-  const double rc2 = rcut * rcut;
-  for (int a = warp; a < m; a += kWarps)
+  for (int a = warp; a < m; a += kWarps) {
+    const int ja = idx[o + a];
+    const int64_t lo0 = off[ja], hi0 = off[ja + 1];
     for (int b = a + 1 + lane; b < m; b += 32) {
-      const double r2 = dist2(pos + 3 * a, pos + 3 * b, lx, ly, lz);
-      double v = 0.0;
-      if (r2 < rc2) {
-        const double r = sqrt(r2);
-        v = (erfc(g * r) - erfc_rc) / r;
+      const int jb = idx[o + b];
+      int64_t lo = lo0, hi = hi0;  // jb in ja's (ascending) pattern row?
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (idx[mid] < jb) lo = mid + 1;
+        else hi = mid;
       }
+      const double v = (lo < hi0 && idx[lo] == jb) ? pval[lo] : 0.0;
       M[a * w + b] = v;
       M[b * w + a] = v;
     }
+  }
   __syncthreads();
   for (int k = 0; k < m; ++k) {
     if (warp == 0) {
@@ -287,14 +311,20 @@ int build_dc_preconditioner(Ctx* c) {
                                                    L[2], rc * rc, nullptr,
                                                    (const int64_t*)c->nbr_off.ptr,
                                                    (int*)c->nbr_idx.ptr, 1), note_launch());
-    const size_t smem = ((size_t)mx * (mx + 1) + 3 * (size_t)mx) * sizeof(double);
+    const size_t smem = (size_t)mx * (mx + 1) * sizeof(double);
     st = cuda_check(c, cudaFuncSetAttribute(k_dc_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)smem), "dc smem");
     if (!st) {
-      (k_dc_local<<<n, kDcThreads, smem, s>>>((const double*)c->xyz.ptr,
-                                              (const double*)c->alpha.ptr, n, L[0], L[1], L[2],
-                                              c->p.g_dc, rc, (const int64_t*)c->nbr_off.ptr,
-                                              (const int*)c->nbr_idx.ptr, (double*)pcol.ptr,
+      // pair values of the pattern, held in prow until the transpose overwrites it
+      (k_dc_pairs<<<(n + 127) / 128, 128, 0, s>>>((const double*)c->xyz.ptr, n, L[0], L[1],
+                                                  L[2], c->p.g_dc, rc,
+                                                  (const int64_t*)c->nbr_off.ptr,
+                                                  (const int*)c->nbr_idx.ptr,
+                                                  (double*)c->prow.ptr), note_launch());
+      (k_dc_local<<<n, kDcThreads, smem, s>>>((const double*)c->alpha.ptr,
+                                              (const int64_t*)c->nbr_off.ptr,
+                                              (const int*)c->nbr_idx.ptr,
+                                              (const double*)c->prow.ptr, (double*)pcol.ptr,
                                               (int*)status.ptr), note_launch());
       (k_dc_transpose<<<n, 128, 0, s>>>(n, (const int64_t*)c->nbr_off.ptr,
                                        (const int*)c->nbr_idx.ptr, (const double*)pcol.ptr, 0.0,

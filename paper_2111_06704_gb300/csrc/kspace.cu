@@ -310,8 +310,8 @@ k_ek_simt(const T* __restrict__ A, int64_t lda, int ktot, T* __restrict__ E, int
 // FMA, which runs at 1/64 of the float rate on this GPU.  The epilogue adds the
 // real-space, self and dipole terms in FP64 and writes the FP64 head matrix.
 __global__ void __launch_bounds__(256)
-k_ek_head_ff(const double* __restrict__ A, int64_t lda, int ktot, double* __restrict__ Eh,
-             int64_t ldE, Epi ep) {
+k_ek_head_ff(const float* __restrict__ Ah_g, const float* __restrict__ Al_g, int64_t lda,
+             int ktot, double* __restrict__ Eh, int64_t ldE, Epi ep) {
   constexpr int BM = 64, BK = 16, TM = 4, LD = BM + 4;
   __shared__ __align__(16) float Ah[BK][LD], Al[BK][LD], Bh[BK][LD], Bl[BK][LD];
   int I, J;
@@ -324,29 +324,24 @@ k_ek_head_ff(const double* __restrict__ A, int64_t lda, int ktot, double* __rest
   for (int a = 0; a < TM; ++a)
 #pragma unroll
     for (int b = 0; b < TM; ++b) sh[a][b] = sl[a][b] = 0.f;
-  const double* pa = A + (int64_t)(i0 + lrow) * lda + lk;
-  const double* pb = A + (int64_t)(j0 + lrow) * lda + lk;
+  const int64_t oa = (int64_t)(i0 + lrow) * lda + lk, ob = (int64_t)(j0 + lrow) * lda + lk;
   for (int k0 = 0; k0 < ktot; k0 += BK) {
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const double x = pa[k0 + v], y = pb[k0 + v];
-      const float xh = (float)x, yh = (float)y;
-      Ah[lk + v][lrow] = xh;
-      Al[lk + v][lrow] = (float)(x - (double)xh);
-      Bh[lk + v][lrow] = yh;
-      Bl[lk + v][lrow] = (float)(y - (double)yh);
-    }
+    const float4 xh = __ldg(reinterpret_cast<const float4*>(Ah_g + oa + k0));
+    const float4 xl = __ldg(reinterpret_cast<const float4*>(Al_g + oa + k0));
+    const float4 yh = __ldg(reinterpret_cast<const float4*>(Ah_g + ob + k0));
+    const float4 yl = __ldg(reinterpret_cast<const float4*>(Al_g + ob + k0));
+    Ah[lk][lrow] = xh.x; Ah[lk + 1][lrow] = xh.y; Ah[lk + 2][lrow] = xh.z; Ah[lk + 3][lrow] = xh.w;
+    Al[lk][lrow] = xl.x; Al[lk + 1][lrow] = xl.y; Al[lk + 2][lrow] = xl.z; Al[lk + 3][lrow] = xl.w;
+    Bh[lk][lrow] = yh.x; Bh[lk + 1][lrow] = yh.y; Bh[lk + 2][lrow] = yh.z; Bh[lk + 3][lrow] = yh.w;
+    Bl[lk][lrow] = yl.x; Bl[lk + 1][lrow] = yl.y; Bl[lk + 2][lrow] = yl.z; Bl[lk + 3][lrow] = yl.w;
     __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < BK; ++kk) {
       float ah[TM], al[TM], bh[TM], bl[TM];
-#pragma unroll
-      for (int u = 0; u < TM; ++u) {
-        ah[u] = Ah[kk][ty * 4 + u];
-        al[u] = Al[kk][ty * 4 + u];
-        bh[u] = Bh[kk][tx * 4 + u];
-        bl[u] = Bl[kk][tx * 4 + u];
-      }
+      *reinterpret_cast<float4*>(ah) = *reinterpret_cast<const float4*>(&Ah[kk][ty * 4]);
+      *reinterpret_cast<float4*>(al) = *reinterpret_cast<const float4*>(&Al[kk][ty * 4]);
+      *reinterpret_cast<float4*>(bh) = *reinterpret_cast<const float4*>(&Bh[kk][tx * 4]);
+      *reinterpret_cast<float4*>(bl) = *reinterpret_cast<const float4*>(&Bl[kk][tx * 4]);
 #pragma unroll
       for (int a = 0; a < TM; ++a)
 #pragma unroll
@@ -372,6 +367,21 @@ k_ek_head_ff(const double* __restrict__ A, int64_t lda, int ktot, double* __rest
       Eh[(int64_t)i * ldE + j] =
           (double)sh[a][b] + (double)sl[a][b] + epilogue_terms(ep, i, j);
     }
+  }
+}
+
+// The head operand columns [0, ktot) of every row as float pairs x = hi + lo (exact to
+// ~2^-48), split once so the head GEMM loads floats only.
+__global__ void k_split_head(const double* __restrict__ A, int64_t lda, int rows, int ktot,
+                             float* __restrict__ hi, float* __restrict__ lo) {
+  const int64_t total = (int64_t)rows * ktot;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / ktot, c = e % ktot;
+    const double x = A[r * lda + c];
+    const float h = (float)x;
+    hi[e] = h;
+    lo[e] = (float)(x - (double)h);
   }
 }
 
@@ -481,11 +491,12 @@ int launch_ek_simt(bool fp64, const void* A, int npad, int mpad, const double* x
   return cudaGetLastError() == cudaSuccess ? CPM_OK : CPM_ECUDA;
 }
 
-// FP64 head of the k-space sum (the first ktot columns of the FP64 head operand, row
-// stride 2 kh) plus the real-space, self and dipole terms, lower triangle, into Ehead.
-int launch_ek_head_f64(const double* Ahead, int kh, int ktot, const double* xyz,
-                       const double* alpha, int n, const Geometry& geo, double* Ehead,
-                       int64_t ldE, cudaStream_t s) {
+// FP64-accurate head of the k-space sum (the first ktot columns of the FP64 head operand,
+// row stride 2 kh, split into float pairs in hi/lo [npad][ktot]) plus the real-space,
+// self and dipole terms, lower triangle, into Ehead.
+int launch_ek_head_f64(const double* Ahead, int kh, int ktot, int npad, float* hi, float* lo,
+                       const double* xyz, const double* alpha, int n, const Geometry& geo,
+                       double* Ehead, int64_t ldE, cudaStream_t s) {
   Epi ep;
   ep.xyz = xyz;
   ep.alpha = alpha;
@@ -499,8 +510,8 @@ int launch_ek_head_f64(const double* Ahead, int kh, int ktot, const double* xyz,
   constexpr int BM = 64;
   const int nt = (n + BM - 1) / BM;
   const int tiles = nt * (nt + 1) / 2;
-  (k_ek_head_ff<<<tiles, 256, 0, s>>>(Ahead, 2 * (int64_t)kh, ktot, Ehead, ldE, ep),
-   note_launch());
+  (k_split_head<<<2048, 256, 0, s>>>(Ahead, 2 * (int64_t)kh, npad, ktot, hi, lo), note_launch());
+  (k_ek_head_ff<<<tiles, 256, 0, s>>>(hi, lo, ktot, ktot, Ehead, ldE, ep), note_launch());
   return cudaGetLastError() == cudaSuccess ? CPM_OK : CPM_ECUDA;
 }
 
