@@ -265,13 +265,57 @@ k_bsol_kspace(const T* __restrict__ A, int n, int64_t lda, const T* __restrict__
   }
 }
 
+// FP64 real-space sum of one electrode-ion pair over every image within r_c:
+// sum q_I [erfc(g r) - erfc(alpha_i r)] / r.
+__device__ __forceinline__ double pair_images(const double* ri, double ai, const double* ion,
+                                              const double* L, const double* invL,
+                                              const bool* single, double rc, double rc2,
+                                              double g) {
+  double d[3] = {ri[0] - ion[0], ri[1] - ion[1], ri[2] - ion[2]};
+  int lo[3], hi[3];
+  for (int u = 0; u < 3; ++u) {
+    if (single[u]) {  // box edge above 2 rc: only the minimum image can be in range
+      d[u] -= L[u] * rint(d[u] * invL[u]);
+      lo[u] = hi[u] = 0;
+    } else {
+      lo[u] = (int)ceil((-rc - d[u]) * invL[u]);
+      hi[u] = (int)floor((rc - d[u]) * invL[u]);
+    }
+  }
+  double acc = 0.0;
+  for (int a = lo[0]; a <= hi[0]; ++a) {
+    const double x = d[0] + a * L[0];
+    for (int b = lo[1]; b <= hi[1]; ++b) {
+      const double y = d[1] + b * L[1];
+      const double xy = x * x + y * y;
+      if (xy >= rc2) continue;
+      for (int c = lo[2]; c <= hi[2]; ++c) {
+        const double z = d[2] + c * L[2];
+        const double r2 = xy + z * z;
+        if (r2 >= rc2 || r2 == 0.0) continue;
+        const double r = sqrt(r2);
+        double e = erfc(g * r);
+        // erfc(6) < 3e-17: beyond alpha r = 6 the Gaussian term is below double rounding
+        // of the erfc(g r) term
+        if (ai * r < 6.0) e -= erfc(ai * r);
+        acc += ion[3] * e / r;
+      }
+    }
+  }
+  return acc;
+}
+
 // Real-space electrode-ion sums, slab dipole term, and b = chi - k_e b^sol.
-// One thread per electrode atom; ions staged through shared memory.  Every image of a
-// pair is at least as far as its nearest one, so a pair whose nearest-image distance is
-// beyond r_cut contributes nothing: that distance is screened in float from the exact
-// fixed-point coordinate difference (off by < 1e-3 A^2 in r^2, against a band of
-// 0.01 A^2), and only the pairs that pass are summed in FP64 over their images.
-__global__ void __launch_bounds__(128)
+// Four warps, 32 electrode atoms each; ions staged through shared memory.  Every image
+// of a pair is at least as far as its nearest one, so a pair whose nearest-image distance
+// is beyond r_cut contributes nothing: each lane screens its atom against every ion in
+// float from the exact fixed-point coordinate difference (off by < 1e-3 A^2 in r^2,
+// against a band of 0.01 A^2).  The pairs that pass are queued per warp and summed in
+// FP64 over their images 32 at a time, all lanes busy; each atom then adds its queued
+// pairs in ion order, so the sums are those of a plain per-atom loop.
+constexpr int kRealWarps = 4;
+
+__global__ void __launch_bounds__(kRealWarps * 32)
 k_bsol_real(const double* __restrict__ xyz, const double* __restrict__ alpha,
             const uint32_t* __restrict__ sfix, int n, const double* __restrict__ ion_xyz,
             const double* __restrict__ ion_q, const uint32_t* __restrict__ sion, int n_ion,
@@ -280,21 +324,25 @@ k_bsol_real(const double* __restrict__ xyz, const double* __restrict__ alpha,
             double* __restrict__ b_out, double* __restrict__ qsol) {
   __shared__ double sx[kIonChunk][4];
   __shared__ uint32_t su[kIonChunk][3];
+  __shared__ double sa[kRealWarps * 32][4];        // the block's atoms: x, y, z, alpha
+  __shared__ uint32_t queue[kRealWarps][64];       // (atom lane << 16) | ion in chunk
+  __shared__ double qval[kRealWarps][32];
+  __shared__ uint32_t qkey[kRealWarps][32];
   const int f = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const double* ix = ion_xyz + (size_t)f * n_ion * 3;
   const double* iq = ion_q + (size_t)f * n_ion;
   const uint32_t* iu = sion + (size_t)f * n_ion * 3;
-  double ri[3] = {0, 0, 0}, ai = INFINITY;
   uint32_t ui[3] = {0, 0, 0};
   if (i < n) {
-    ri[0] = xyz[3 * i];
-    ri[1] = xyz[3 * i + 1];
-    ri[2] = xyz[3 * i + 2];
     ui[0] = sfix[3 * i];
     ui[1] = sfix[3 * i + 1];
     ui[2] = sfix[3 * i + 2];
-    ai = alpha[i];
+    sa[threadIdx.x][0] = xyz[3 * i];
+    sa[threadIdx.x][1] = xyz[3 * i + 1];
+    sa[threadIdx.x][2] = xyz[3 * i + 2];
+    sa[threadIdx.x][3] = alpha[i];
   }
   const double L[3] = {lx, ly, lz};
   const double rc2 = rc * rc;
@@ -302,6 +350,22 @@ k_bsol_real(const double* __restrict__ xyz, const double* __restrict__ alpha,
   const bool single[3] = {2.0 * rc < lx, 2.0 * rc < ly, 2.0 * rc < lz};
   const float fs[3] = {(float)(lx * 0x1p-32), (float)(ly * 0x1p-32), (float)(lz * 0x1p-32)};
   const float screen2 = (float)rc2 + 0.01f;
+  // evaluates the first `cnt` queued pairs (one per lane) and adds each atom's values in
+  // queue order
+  auto drain = [&](int cnt, double& acc) {
+    __syncwarp();
+    if (lane < cnt) {
+      const uint32_t e = queue[warp][lane];
+      const int a = (int)(e >> 16), t = (int)(e & 0xffffu);
+      qval[warp][lane] = pair_images(sa[warp * 32 + a], sa[warp * 32 + a][3], sx[t], L, invL,
+                                     single, rc, rc2, g);
+      qkey[warp][lane] = (uint32_t)a;
+    }
+    __syncwarp();
+    for (int k = 0; k < cnt; ++k)
+      if (qkey[warp][k] == (uint32_t)lane) acc += qval[warp][k];
+    __syncwarp();
+  };
   // sum q_I z_I and sum q_I over the frame: each thread takes the ions it stages
   double acc = 0.0, qz = 0.0, qs = 0.0;
   for (int base = 0; base < n_ion; base += kIonChunk) {
@@ -319,62 +383,43 @@ k_bsol_real(const double* __restrict__ xyz, const double* __restrict__ alpha,
       qs += sx[t][3];
     }
     __syncthreads();
-    if (i >= n) continue;
+    int qn = 0;  // queued pairs of this warp (warp-uniform)
     for (int t = 0; t < cnt; ++t) {
-      float m2 = 0.f;
+      bool cand = false;
+      if (i < n) {
+        float m2 = 0.f;
 #pragma unroll
-      for (int u = 0; u < 3; ++u) {
-        const float du = (float)(int32_t)(ui[u] - su[t][u]) * fs[u];  // nearest image
-        m2 = fmaf(du, du, m2);
-      }
-      if (m2 >= screen2) continue;
-      const double qI = sx[t][3];
-      double d[3] = {ri[0] - sx[t][0], ri[1] - sx[t][1], ri[2] - sx[t][2]};
-      int lo[3], hi[3];
-      for (int u = 0; u < 3; ++u) {
-        if (single[u]) {  // box edge above 2 rc: only the minimum image can be in range
-          d[u] -= L[u] * rint(d[u] * invL[u]);
-          lo[u] = hi[u] = 0;
-        } else {
-          lo[u] = (int)ceil((-rc - d[u]) * invL[u]);
-          hi[u] = (int)floor((rc - d[u]) * invL[u]);
+        for (int u = 0; u < 3; ++u) {
+          const float du = (float)(int32_t)(ui[u] - su[t][u]) * fs[u];  // nearest image
+          m2 = fmaf(du, du, m2);
         }
+        cand = m2 < screen2;
       }
-      for (int a = lo[0]; a <= hi[0]; ++a) {
-        double x = d[0] + a * L[0];
-        for (int b = lo[1]; b <= hi[1]; ++b) {
-          double y = d[1] + b * L[1];
-          double xy = x * x + y * y;
-          if (xy >= rc2) continue;
-          for (int c = lo[2]; c <= hi[2]; ++c) {
-            double z = d[2] + c * L[2];
-            double r2 = xy + z * z;
-            if (r2 >= rc2 || r2 == 0.0) continue;
-            double r = sqrt(r2);
-            double e = erfc(g * r);
-            // erfc(6) < 3e-17: beyond alpha r = 6 the Gaussian term is below double
-            // rounding of the erfc(g r) term
-            if (ai * r < 6.0) e -= erfc(ai * r);
-            acc += qI * e / r;
-          }
-        }
+      const unsigned m = __ballot_sync(0xffffffffu, cand);
+      if (cand) queue[warp][qn + __popc(m & ((1u << lane) - 1u))] = ((uint32_t)lane << 16) | t;
+      qn += __popc(m);
+      if (qn >= 32) {
+        drain(32, acc);
+        if (lane < qn - 32) queue[warp][lane] = queue[warp][32 + lane];
+        qn -= 32;
       }
     }
+    if (qn > 0) drain(qn, acc);
   }
-  __shared__ double red[2][4];
+  __shared__ double red[2][kRealWarps];
   for (int o = 16; o; o >>= 1) {
     qz += __shfl_xor_sync(0xffffffffu, qz, o);
     qs += __shfl_xor_sync(0xffffffffu, qs, o);
   }
-  if ((threadIdx.x & 31) == 0) {
-    red[0][threadIdx.x >> 5] = qz;
-    red[1][threadIdx.x >> 5] = qs;
+  if (lane == 0) {
+    red[0][warp] = qz;
+    red[1][warp] = qs;
   }
   __syncthreads();
   qz = red[0][0] + red[0][1] + red[0][2] + red[0][3];
   qs = red[1][0] + red[1][1] + red[1][2] + red[1][3];
   if (i < n) {
-    double bs = bsol_k[(size_t)f * n + i] + acc + dip * ri[2] * qz;
+    double bs = bsol_k[(size_t)f * n + i] + acc + dip * sa[threadIdx.x][2] * qz;
     b_out[(size_t)f * n + i] = chi[i] - kKe * bs;
   }
   if (i == 0 && qsol) qsol[f] = qs;
@@ -436,9 +481,9 @@ void launch_bsol_real_and_finish(const double* xyz, const double* alpha, const u
                                  const uint32_t* sion, int frames, int n_ion,
                                  const Geometry& geo, const double* chi, const double* bsol_k,
                                  double* b_out, double* qsol, cudaStream_t s) {
-  dim3 grid((n + 127) / 128, frames);
+  dim3 grid((n + kRealWarps * 32 - 1) / (kRealWarps * 32), frames);
   double dip = geo.slab ? 4.0 * kPi / geo.vol : 0.0;
-  (k_bsol_real<<<grid, 128, 0, s>>>(xyz, alpha, sfix, n, ion_xyz, ion_q, sion, n_ion, geo.L[0],
+  (k_bsol_real<<<grid, kRealWarps * 32, 0, s>>>(xyz, alpha, sfix, n, ion_xyz, ion_q, sion, n_ion, geo.L[0],
                                    geo.L[1], geo.L[2], geo.g, geo.rc, dip, chi, bsol_k, b_out,
                                    qsol), note_launch());
 }
