@@ -91,6 +91,13 @@ typedef struct cpm_params {
   void* (*alloc)(size_t bytes, void* user);
   void (*free)(void* ptr, void* user);
   void* alloc_user;
+  /* Operand streaming (BF16X6 builds): the structure-factor operand A is kept resident
+     when it fits 32 GiB, otherwise the build makes its BF16 planes k-window by k-window
+     (about 12 GB of planes at a time) and cpm_potential sums the k-space part directly
+     from the electrode phases.  stream_operand: 0 automatic, 1 always.  k_window:
+     k-vectors per window (rounded down to a multiple of 64), 0 automatic. */
+  int stream_operand;
+  int k_window;
 } cpm_params;
 
 typedef struct cpm_ctx cpm_ctx;
@@ -217,6 +224,10 @@ int cpm_apply_E(cpm_ctx* c, int nrhs, const double* p, double* q);
 
 /* Copies E (form CPM_E_STORED or CPM_E_PAPER) into out[n*ld] (row-major, ld >= n). */
 int cpm_get_E(cpm_ctx* c, int form, double* out, int64_t ld);
+
+/* Copies rows rows[0..nrows) of E (form as above) into out[nrows*ld]; rows host or
+ * device, each in [0, n). */
+int cpm_get_E_rows(cpm_ctx* c, int form, int nrows, const int* rows, double* out, int64_t ld);
 
 typedef struct cpm_info_t {
   int n;              /* electrode atoms */

@@ -112,17 +112,22 @@ def kspace_pairs(ra, rb, box, g: float, eps: float = 1e-8):
     _, kvec, w = kvectors(box, g, eps)
     ra = np.asarray(ra, dtype=np.float64)
     rb = np.asarray(rb, dtype=np.float64)
-    out = np.empty((ra.shape[0], rb.shape[0]))
-    chunk = max(1, 4_000_000 // max(1, rb.shape[0] * kvec.shape[0]))
+    na, nb, m = ra.shape[0], rb.shape[0], kvec.shape[0]
+    out = np.empty((na, nb))
+    # tiles of (a rows) x (b columns) x M phases of about 4e6 elements each, so the
+    # memory stays bounded however large the sets are
+    cb = max(1, min(nb, 4_000_000 // max(1, m)))
+    ca = max(1, 4_000_000 // max(1, cb * m))
 
-    def rows(a0):
-        d = ra[a0:a0 + chunk, None, :] - rb[None, :, :]  # [c, nb, 3]
-        ph = d @ kvec.T  # [c, nb, M]
-        out[a0:a0 + chunk] = np.cos(ph) @ w
+    def tile(t):
+        a0, b0 = t
+        d = ra[a0:a0 + ca, None, :] - rb[None, b0:b0 + cb, :]  # [ca, cb, 3]
+        out[a0:a0 + ca, b0:b0 + cb] = np.cos(d @ kvec.T) @ w    # phases [ca, cb, M]
 
-    # numpy releases the GIL inside cos/matmul, so row blocks run on all host cores.
+    # numpy releases the GIL inside cos/matmul, so tiles run on all host cores.
+    tiles = [(a0, b0) for a0 in range(0, na, ca) for b0 in range(0, nb, cb)]
     with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as pool:
-        list(pool.map(rows, range(0, ra.shape[0], chunk)))
+        list(pool.map(tile, tiles))
     return out
 
 

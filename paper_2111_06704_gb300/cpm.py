@@ -54,6 +54,8 @@ class cpm_params(ctypes.Structure):
         ("alloc", ALLOC_FN),
         ("free", FREE_FN),
         ("alloc_user", ctypes.c_void_p),
+        ("stream_operand", ctypes.c_int),
+        ("k_window", ctypes.c_int),
     ]
 
 
@@ -83,7 +85,7 @@ EXPORTS = ["cpm_default_params", "cpm_create", "cpm_destroy", "cpm_build_E", "cp
            "cpm_get_d", "cpm_guess_features", "cpm_mlp_forward", "cpm_mlp_grad",
            "cpm_mlp_adam", "cpm_guess_apply", "cpm_apply_E", "cpm_get_precond",
            "cpm_last_error", "cpm_batch_create", "cpm_batch_destroy", "cpm_batch_solve",
-           "cpm_batch_neutralize", "cpm_batch_last_error"]
+           "cpm_batch_neutralize", "cpm_batch_last_error", "cpm_get_E_rows"]
 
 _lib = None
 
@@ -115,6 +117,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.cpm_solve_static.argtypes = [vp, i, vp, vp, i, d, i, vp, vp]
     lib.cpm_neutralize.argtypes = [vp, i, vp, vp]
     lib.cpm_get_E.argtypes = [vp, i, vp, i64]
+    lib.cpm_get_E_rows.argtypes = [vp, i, i, vp, vp, i64]
     lib.cpm_get_info.argtypes = [vp, P(cpm_info_t)]
     lib.cpm_get_d.argtypes = [vp, vp]
     lib.cpm_get_precond.argtypes = [vp, vp, vp, vp]
@@ -287,6 +290,14 @@ class Context:
         out = np.empty((self.n, self.n))
         self._check(self.lib.cpm_get_E(self.h, int(form), out.ctypes.data_as(ctypes.c_void_p),
                                        self.n))
+        return out
+
+    def cpm_get_E_rows(self, rows, form=CPM_E_STORED):
+        rows = np.ascontiguousarray(rows, dtype=np.int32)
+        out = np.empty((len(rows), self.n))
+        self._check(self.lib.cpm_get_E_rows(self.h, int(form), len(rows),
+                                            rows.ctypes.data_as(ctypes.c_void_p),
+                                            out.ctypes.data_as(ctypes.c_void_p), self.n))
         return out
 
     def cpm_apply_E(self, p, q=None):

@@ -225,6 +225,7 @@ int cpm_create(cpm_ctx** out, const cpm_params* p) {
       p->precision != CPM_PREC_BF16X6)
     return CPM_EINVAL;
   if (p->precond < CPM_PRECOND_NONE || p->precond > CPM_PRECOND_DC) return CPM_EINVAL;
+  if (p->stream_operand < 0 || p->stream_operand > 1 || p->k_window < 0) return CPM_EINVAL;
   if ((p->alloc == nullptr) != (p->free == nullptr)) return CPM_EINVAL;
   cpm_ctx* c = new (std::nothrow) cpm_ctx();
   if (!c) return CPM_ENOMEM;
@@ -351,6 +352,10 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
   }
 
   const size_t a_bytes = (size_t)c->npad * 2 * c->mpad * c->esz();
+  // A larger than this is not kept: the tensor-core build streams it in k-windows and the
+  // potential sums its k-space part directly (a streamed build)
+  constexpr size_t kResidentOperandBytes = 32ull << 30;
+  c->streamed = tc && (c->p.stream_operand == 1 || a_bytes > kResidentOperandBytes);
   const size_t e_bytes = (size_t)n * c->ldE * c->esz();
   if ((st = buf_alloc(c, &c->xyz, (size_t)n * 3 * sizeof(double))) ||
       (st = buf_alloc(c, &c->alpha, (size_t)n * sizeof(double))) ||
@@ -360,7 +365,8 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
       (st = buf_alloc(c, &c->flush, fmask.size() * sizeof(uint32_t))) ||
       (st = buf_alloc(c, &c->chunk_end, cmask.size() * sizeof(uint32_t))) ||
       (st = buf_alloc(c, &c->Ahead, (size_t)c->npad * 2 * std::max(c->kh, 1) * sizeof(double))) ||
-      (st = buf_alloc(c, &c->A, a_bytes)) || (st = buf_alloc(c, &c->E, e_bytes)) ||
+      (!c->streamed && (st = buf_alloc(c, &c->A, a_bytes))) ||
+      (st = buf_alloc(c, &c->E, e_bytes)) ||
       (st = buf_alloc(c, &c->diag, 2 * (size_t)n * sizeof(double))) ||
       (st = buf_alloc(c, &c->d, (size_t)n * sizeof(double)))) {
     free_build(c);
@@ -388,13 +394,6 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
   cudaEventRecord(ev[0], s);
   launch_fixed_point_coords((const double*)c->xyz.ptr, n, c->npad, c->p.box,
                             (uint32_t*)c->sfix.ptr, s);
-  launch_structure_operand(f64, (const double*)c->xyz.ptr, (const uint32_t*)c->sfix.ptr,
-                           c->npad, n, (const int*)c->hkl.ptr, (const double*)c->sqw.ptr,
-                           c->mpad, c->p.box, c->A.ptr, s);
-  if (c->kh > 0)
-    launch_structure_operand_head((const double*)c->xyz.ptr, c->npad, n, (const int*)c->hkl.ptr,
-                                  (const double*)c->sqw.ptr, c->kh, c->p.box,
-                                  (double*)c->Ahead.ptr, s);
   Buf planes[3], ehead, errbuf, hsplit;
   auto free_tc = [&]() {
     for (Buf& b : planes) buf_free(c, &b);
@@ -403,8 +402,16 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
     buf_free(c, &hsplit);
   };
   const int head_cols = 16 * c->heavy_steps;
+  // k-vectors whose BF16 planes are held at once: all of them, or in a streamed build a
+  // window of ~12 GB of planes (12 bytes per row and k-vector)
+  int kwin = c->mpad;
+  if (c->streamed)
+    kwin = c->p.k_window > 0
+               ? std::max(64, std::min(c->mpad, c->p.k_window / 64 * 64))
+               : std::max(64, (int)std::min<int64_t>(c->mpad, (int64_t)(12ull << 30) /
+                                                               (12ll * c->npad) / 64 * 64));
   if (tc) {
-    const size_t pbytes = (size_t)c->npad * 2 * c->mpad * 2;
+    const size_t pbytes = (size_t)c->npad * 2 * kwin * 2;
     if ((st = buf_alloc(c, &planes[0], pbytes)) || (st = buf_alloc(c, &planes[1], pbytes)) ||
         (st = buf_alloc(c, &planes[2], pbytes)) ||
         (st = buf_alloc(c, &ehead, (size_t)n * c->ldE * sizeof(double))) ||
@@ -415,9 +422,19 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
       for (auto& e : ev) cudaEventDestroy(e);
       return fail(st);
     }
-    launch_split_bf16((const float*)c->A.ptr, (int64_t)c->npad * 2 * c->mpad, planes[0].ptr,
-                      planes[1].ptr, planes[2].ptr, s);
   }
+  // A (and, for the tensor-core build, its BF16 planes where the schedule reads them);
+  // a streamed build makes the planes window by window below
+  void* plane_ptrs[3] = {planes[0].ptr, planes[1].ptr, planes[2].ptr};
+  if (!c->streamed)
+    launch_structure_operand(f64, (const double*)c->xyz.ptr, (const uint32_t*)c->sfix.ptr,
+                             c->npad, n, (const int*)c->hkl.ptr, (const double*)c->sqw.ptr,
+                             c->mpad, c->p.box, c->A.ptr, tc ? plane_ptrs : nullptr,
+                             c->heavy_steps / 4, c->kb6_end, c->kb3_end, 0, c->mpad, s);
+  if (c->kh > 0)
+    launch_structure_operand_head((const double*)c->xyz.ptr, c->npad, n, (const int*)c->hkl.ptr,
+                                  (const double*)c->sqw.ptr, c->kh, c->p.box,
+                                  (double*)c->Ahead.ptr, s);
   cudaEventRecord(ev[1], s);
   if (tc) {
     // FP64 head (heaviest k-vectors) with the real-space, self and dipole terms, then the
@@ -431,12 +448,22 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
                             (const double*)c->xyz.ptr, (const double*)c->alpha.ptr, n, geo,
                             (double*)ehead.ptr, c->ldE, s);
     cudaEventRecord(c->ev_tc[0], s);
-    if (!st)
-      st = launch_ek_tc(planes[0].ptr, planes[1].ptr, planes[2].ptr, c->npad, c->mpad, n,
-                        c->heavy_steps / 4, c->kb6_end, c->kb3_end,
-                        (const uint32_t*)c->chunk_end.ptr,
-                        (const double*)ehead.ptr, c->ldE, (float*)c->E.ptr, c->ldE,
-                        (int*)errbuf.ptr, s);
+    // the tail, one k-window at a time: every window but the last carries the sum in the
+    // FP64 head matrix, the last writes float E
+    for (int kbeg = 0; kbeg < c->mpad && !st; kbeg += kwin) {
+      const int kend = std::min(c->mpad, kbeg + kwin);
+      const bool last = kend == c->mpad;
+      if (c->streamed)
+        launch_structure_operand(false, (const double*)c->xyz.ptr, (const uint32_t*)c->sfix.ptr,
+                                 c->npad, n, (const int*)c->hkl.ptr, (const double*)c->sqw.ptr,
+                                 c->mpad, c->p.box, nullptr, plane_ptrs, c->heavy_steps / 4,
+                                 c->kb6_end, c->kb3_end, kbeg, kend, s);
+      st = launch_ek_tc(planes[0].ptr, planes[1].ptr, planes[2].ptr, c->npad,
+                        2 * (int64_t)(kend - kbeg), kbeg / 32, n,
+                        std::max(c->heavy_steps / 4, kbeg / 32), kend / 32, c->kb6_end,
+                        c->kb3_end, (const uint32_t*)c->chunk_end.ptr, (double*)ehead.ptr,
+                        c->ldE, last ? (float*)c->E.ptr : nullptr, c->ldE, (int*)errbuf.ptr, s);
+    }
     cudaEventRecord(c->ev_tc[1], s);
     int herr = 0;
     if (!st) st = cuda_check(c, cudaMemcpyAsync(&herr, errbuf.ptr, sizeof(int),
@@ -577,7 +604,8 @@ int cpm_potential(cpm_ctx* c, int frames, int n_ion, const double* ion_xyz,
     return st;
   }
   launch_bsol_kspace(f64, c->A.ptr, (const double*)c->Ahead.ptr, n, c->mpad, c->kh, v, vh,
-                     frames, bk, s);
+                     frames, bk, (const uint32_t*)c->sfix.ptr, (const int*)c->hkl.ptr,
+                     (const double*)c->sqw.ptr, s);
   launch_bsol_real_and_finish((const double*)c->xyz.ptr, (const double*)c->alpha.ptr,
                               (const uint32_t*)c->sfix.ptr, n, dx, dq, sion, frames, n_ion,
                               geometry(c), dchi, bk, db, dqs, s);
@@ -662,10 +690,35 @@ int cpm_get_E(cpm_ctx* c, int form, double* out, int64_t ld) {
   int st;
   if ((st = stage_out(c, &c->ws_out0, out, bytes, (void**)&d))) return st;
   launch_get_E(c->fp64(), c->E.ptr, c->n, c->ldE, (const double*)c->xyz.ptr, geometry(c),
-               form == CPM_E_PAPER, d, ld, c->stream);
+               form == CPM_E_PAPER, nullptr, c->n, d, ld, c->stream);
   if ((st = cuda_check(c, cudaGetLastError(), "get_E"))) return st;
   if ((st = copy_out(c, out, d, bytes))) return st;
   return cuda_check(c, cudaStreamSynchronize(c->stream), "get_E sync");
+}
+
+int cpm_get_E_rows(cpm_ctx* c, int form, int nrows, const int* rows, double* out, int64_t ld) {
+  if (!c) return CPM_EINVAL;
+  if (!c->built) return set_err(c, CPM_ENOTBUILT, "cpm_get_E_rows before cpm_build_E");
+  if (nrows < 1 || !rows || !out || ld < c->n || (form != CPM_E_STORED && form != CPM_E_PAPER))
+    return set_err(c, CPM_EINVAL, "cpm_get_E_rows: bad arguments");
+  std::vector<int> hr(nrows);
+  int st = cuda_check(c, cudaMemcpyAsync(hr.data(), rows, nrows * sizeof(int), cudaMemcpyDefault,
+                                         c->stream), "rows");
+  if (!st) st = cuda_check(c, cudaStreamSynchronize(c->stream), "rows sync");
+  if (st) return st;
+  for (int r : hr)
+    if (r < 0 || r >= c->n) return set_err(c, CPM_EINVAL, "cpm_get_E_rows: row out of range");
+  const size_t bytes = (size_t)nrows * ld * sizeof(double);
+  double* d = nullptr;
+  const int* dr = nullptr;
+  if ((st = stage_in(c, &c->ws_in0, hr.data(), nrows * sizeof(int), (const void**)&dr)) ||
+      (st = stage_out(c, &c->ws_out0, out, bytes, (void**)&d)))
+    return st;
+  launch_get_E(c->fp64(), c->E.ptr, c->n, c->ldE, (const double*)c->xyz.ptr, geometry(c),
+               form == CPM_E_PAPER, dr, nrows, d, ld, c->stream);
+  if ((st = cuda_check(c, cudaGetLastError(), "get_E_rows"))) return st;
+  if ((st = copy_out(c, out, d, bytes))) return st;
+  return cuda_check(c, cudaStreamSynchronize(c->stream), "get_E_rows sync");
 }
 
 int cpm_apply_E(cpm_ctx* c, int nrhs, const double* p, double* q) {

@@ -86,6 +86,7 @@ struct Ctx {
   int kh = 0;           // head k-vectors with an FP64 operand copy (float storage only)
   Buf Ahead;            // double [npad][2*kh], same column layout as A
   Buf chunk_end;        // uint32 bit per K-block of 64 columns (tensor-core build)
+  bool streamed = false;  // A too large to keep: built in k-windows, potential direct
   int kb6_end = 0, kb3_end = 0;  // tensor-core K-blocks: six products before kb6_end,
                                  // three before kb3_end, one after
   Buf A;        // float/double [npad][2*mpad]
@@ -138,9 +139,12 @@ int cuda_check(Ctx* c, cudaError_t e, const char* what);
 // kspace.cu
 void launch_fixed_point_coords(const double* xyz, int n, int npad, const double L[3],
                                uint32_t* sfix, cudaStream_t s);
+// k-vectors [kbeg, kend) (multiples of 64): A (if not null) and the BF16 planes (if not
+// null) over that window
 void launch_structure_operand(bool fp64, const double* xyz, const uint32_t* sfix, int npad,
                               int n, const int* hkl, const double* sqw, int mpad,
-                              const double L[3], void* A, cudaStream_t s);
+                              const double L[3], void* A, void* const* planes, int kb0,
+                              int kb6, int kb3, int kbeg, int kend, cudaStream_t s);
 void launch_structure_operand_head(const double* xyz, int npad, int n, const int* hkl,
                                    const double* sqw, int kh, const double L[3], double* Ahead,
                                    cudaStream_t s);
@@ -154,17 +158,15 @@ int launch_ek_head_f64(const double* Ahead, int kh, int ktot, int npad, float* h
                        double* Ehead, int64_t ldE, cudaStream_t s);
 
 // tc_syrk.cu
-void launch_split_bf16(const float* A, int64_t len, void* p0, void* p1, void* p2,
-                       cudaStream_t s);
-int launch_ek_tc(const void* p0, const void* p1, const void* p2, int npad, int mpad, int n,
-                 int kb_begin, int kb6_end, int kb3_end, const uint32_t* chunk_end,
-                 const double* head, int64_t ldh, float* E, int64_t ldE, int* err,
-                 cudaStream_t s);
+int launch_ek_tc(const void* p0, const void* p1, const void* p2, int npad, int64_t plane_cols,
+                 int kb_col0, int n, int kb_begin, int kb_end, int kb6_end, int kb3_end,
+                 const uint32_t* chunk_end, double* head, int64_t ldh, float* E, int64_t ldE,
+                 int* err, cudaStream_t s);
 void launch_extract_diag(bool fp64, const void* E, int n, int64_t ldE, double* diag,
                          cudaStream_t s);
 void launch_get_E(bool fp64, const void* E, int n, int64_t ldE, const double* xyz,
-                  const Geometry& geo, int paper_form, double* out, int64_t ld,
-                  cudaStream_t s);
+                  const Geometry& geo, int paper_form, const int* rows, int nrows, double* out,
+                  int64_t ld, cudaStream_t s);
 
 // potential.cu
 void launch_ion_fixed(const double* ion_xyz, int frames, int n_ion, const double L[3],
@@ -176,6 +178,7 @@ void launch_ion_structure_factor(bool fp64, const double* ion_xyz, const uint32_
                                  const void* turn, void* v, double* vhead, cudaStream_t s);
 void launch_bsol_kspace(bool fp64, const void* A, const double* Ahead, int n, int mpad, int kh,
                         const void* v, const double* vhead, int frames, double* bsol,
+                        const uint32_t* sfix, const int* hkl, const double* sqw,
                         cudaStream_t s);
 void launch_bsol_real_and_finish(const double* xyz, const double* alpha, const uint32_t* sfix,
                                  int n, const double* ion_xyz, const double* ion_q,

@@ -8,6 +8,7 @@
 //
 // The reciprocal sum is split by cos(a - b) = cos a cos b + sin a sin b into A A^T with
 // A[i] = [sqrt(W) cos(K.r_i) | sqrt(W) sin(K.r_i)]: a dense contraction over 2M terms.
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include "cpm_internal.cuh"
@@ -45,17 +46,44 @@ __global__ void k_fixed_point_coords(const double* __restrict__ xyz, int n, int 
 // h, k, l times 2^-32-quantised fractional coordinates, wrapping mod 1), then one
 // rounding to float and sincospif.  FP64 operand: fractional coordinates in double,
 // reduced to [-1/2, 1/2] by rint, then sincospi.
+// BF16 planes of the tensor-core build, written with A: a = a0 + a1 + a2, each plane the
+// rounding of the remainder of the previous; K-block b (64 columns) needs plane 0 from
+// kb0 on, plane 1 below kb3 and plane 2 below kb6 (the weight-bounded product schedule).
+struct PlaneOut {
+  __nv_bfloat16* p[3];
+  int kb0, kb6, kb3;
+};
+
+__device__ __forceinline__ void write_planes(const PlaneOut& po, size_t e, int b, float a) {
+  if (b < po.kb0) return;
+  const __nv_bfloat16 b0 = __float2bfloat16_rn(a);
+  po.p[0][e] = b0;
+  if (b >= po.kb3) return;
+  const float r1 = a - __bfloat162float(b0);
+  const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
+  po.p[1][e] = b1;
+  if (b >= po.kb6) return;
+  po.p[2][e] = __float2bfloat16_rn(r1 - __bfloat162float(b1));
+}
+
+// A (lda = 2 mpad) and, with PLANES, the BF16 planes for the k-vectors [kbeg, kend)
+// (multiples of 64), the planes laid out over that window only: row stride
+// 2 (kend - kbeg), column kcol - 2 kbeg.  A may be null (a streamed build keeps no A).
+template <bool PLANES>
 __global__ void k_structure_operand_f32(const uint32_t* __restrict__ sfix, int npad, int n,
                                         const int* __restrict__ hkl,
-                                        const double* __restrict__ sqw, int mpad,
-                                        float* __restrict__ A) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= mpad) return;
+                                        const double* __restrict__ sqw, int mpad, int kbeg,
+                                        int kend, float* __restrict__ A, PlaneOut po) {
+  int k = kbeg + blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= kend) return;
   const uint32_t h = (uint32_t)hkl[3 * k], kk = (uint32_t)hkl[3 * k + 1],
                  l = (uint32_t)hkl[3 * k + 2];
   const float w = (float)sqw[k];
   const size_t lda = 2 * (size_t)mpad;
+  const size_t ldp = 2 * (size_t)(kend - kbeg);
   const size_t kcol = 128 * (size_t)(k >> 6) + (k & 63);
+  const size_t pcol = kcol - 2 * (size_t)kbeg;
+  const int bc = (int)(kcol >> 6);  // K-block of the cos column; the sin column is bc + 1
   for (int i = blockIdx.y; i < npad; i += gridDim.y) {
     float c = 0.f, s = 0.f;
     if (i < n) {
@@ -64,8 +92,14 @@ __global__ void k_structure_operand_f32(const uint32_t* __restrict__ sfix, int n
       c *= w;
       s *= w;
     }
-    A[i * lda + kcol] = c;
-    A[i * lda + kcol + 64] = s;
+    if (A) {
+      A[i * lda + kcol] = c;
+      A[i * lda + kcol + 64] = s;
+    }
+    if (PLANES) {
+      write_planes(po, i * ldp + pcol, bc, c);
+      write_planes(po, i * ldp + pcol + 64, bc + 1, s);
+    }
   }
 }
 
@@ -413,17 +447,19 @@ __global__ void k_extract_diag(const T* __restrict__ E, int n, int64_t ldE,
 template <typename T>
 __global__ void k_get_E(const T* __restrict__ E, int n, int64_t ldE,
                         const double* __restrict__ xyz, double c0, double cz, double lz2_6,
-                        int slab, double* __restrict__ out, int64_t ld) {
+                        int slab, const int* __restrict__ rows, int nrows,
+                        double* __restrict__ out, int64_t ld) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
-  for (int i = blockIdx.y; i < n; i += gridDim.y) {
+  for (int r = blockIdx.y; r < nrows; r += gridDim.y) {
+    const int i = rows ? rows[r] : r;
     double v = (double)E[(int64_t)i * ldE + j];
     v += c0;
     if (slab) {
       double zi = xyz[3 * i + 2], zj = xyz[3 * j + 2];
       v += cz * (zi * zi + zj * zj + lz2_6);
     }
-    out[(int64_t)i * ld + j] = v;
+    out[(int64_t)r * ld + j] = v;
   }
 }
 
@@ -445,13 +481,25 @@ void launch_structure_operand_head(const double* xyz, int npad, int n, const int
 
 void launch_structure_operand(bool fp64, const double* xyz, const uint32_t* sfix, int npad,
                               int n, const int* hkl, const double* sqw, int mpad,
-                              const double L[3], void* A, cudaStream_t s) {
-  dim3 grid((mpad + 127) / 128, npad < 1024 ? npad : 1024);
-  if (fp64)
-    (k_structure_operand_f64<<<grid, 128, 0, s>>>(xyz, npad, n, hkl, sqw, mpad, L[0], L[1],
-                                                 L[2], (double*)A), note_launch());
-  else
-    (k_structure_operand_f32<<<grid, 128, 0, s>>>(sfix, npad, n, hkl, sqw, mpad, (float*)A), note_launch());
+                              const double L[3], void* A, void* const* planes, int kb0,
+                              int kb6, int kb3, int kbeg, int kend, cudaStream_t s) {
+  dim3 grid((kend - kbeg + 127) / 128, npad < 1024 ? npad : 1024);
+  PlaneOut po{};
+  if (fp64) {
+    dim3 g64((mpad + 127) / 128, npad < 1024 ? npad : 1024);
+    (k_structure_operand_f64<<<g64, 128, 0, s>>>(xyz, npad, n, hkl, sqw, mpad, L[0], L[1],
+                                                L[2], (double*)A), note_launch());
+  } else if (planes) {
+    for (int t = 0; t < 3; ++t) po.p[t] = (__nv_bfloat16*)planes[t];
+    po.kb0 = kb0;
+    po.kb6 = kb6;
+    po.kb3 = kb3;
+    (k_structure_operand_f32<true><<<grid, 128, 0, s>>>(sfix, npad, n, hkl, sqw, mpad, kbeg,
+                                                        kend, (float*)A, po), note_launch());
+  } else {
+    (k_structure_operand_f32<false><<<grid, 128, 0, s>>>(sfix, npad, n, hkl, sqw, mpad, kbeg,
+                                                         kend, (float*)A, po), note_launch());
+  }
 }
 
 int launch_ek_simt(bool fp64, const void* A, int npad, int mpad, const double* xyz,
@@ -532,20 +580,23 @@ void launch_extract_diag(bool fp64, const void* E, int n, int64_t ldE, double* d
     (k_extract_diag<float><<<(n + 255) / 256, 256, 0, s>>>((const float*)E, n, ldE, diag), note_launch());
 }
 
+// Rows of E (all n when rows is null, else rows[0..nrows)) into out[nrows][ld].
 void launch_get_E(bool fp64, const void* E, int n, int64_t ldE, const double* xyz,
-                  const Geometry& geo, int paper_form, double* out, int64_t ld,
-                  cudaStream_t s) {
+                  const Geometry& geo, int paper_form, const int* rows, int nrows, double* out,
+                  int64_t ld, cudaStream_t s) {
   // Paper form (Eq. 22 + Eq. 39) = stored form - pi/(V g^2) - (2 pi/V)(z_i^2 + z_j^2 + Lz^2/6)
   double c0 = paper_form ? -kPi / (geo.vol * geo.g * geo.g) : 0.0;
   double cz = -2.0 * kPi / geo.vol;
   int slab = paper_form && geo.slab;
-  dim3 grid((n + 255) / 256, n < 65535 ? n : 65535);
+  dim3 grid((n + 255) / 256, nrows < 65535 ? nrows : 65535);
   if (fp64)
     (k_get_E<double><<<grid, 256, 0, s>>>((const double*)E, n, ldE, xyz, c0, cz,
-                                         geo.L[2] * geo.L[2] / 6.0, slab, out, ld), note_launch());
+                                         geo.L[2] * geo.L[2] / 6.0, slab, rows, nrows, out,
+                                         ld), note_launch());
   else
     (k_get_E<float><<<grid, 256, 0, s>>>((const float*)E, n, ldE, xyz, c0, cz,
-                                        geo.L[2] * geo.L[2] / 6.0, slab, out, ld), note_launch());
+                                        geo.L[2] * geo.L[2] / 6.0, slab, rows, nrows, out,
+                                        ld), note_launch());
 }
 
 }  // namespace cpm

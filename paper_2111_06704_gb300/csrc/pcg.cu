@@ -130,18 +130,21 @@ __device__ __forceinline__ void pair_add(float& hi, float& lo, float bh, float b
 // and the running sum are error-free (two-product, two-sum, one chain per row and column
 // per lane), so the stored float E is applied to ~1e-14 rather than to float rounding of
 // every product and sum -- otherwise PCG converges to the solution of a slightly
-// different matrix (1e-6 of q at the 512-atom cell); lanes and warps combine float pairs, and only the final
-// per-row value goes to FP64 -- FP64 runs at 1/64 of the FP32 rate here.  E is read
-// with the streaming hint so the direction stays resident in L2.
+// different matrix (1e-6 of q at the 512-atom cell); lanes and warps combine float
+// pairs, and only the final per-row value goes to FP64 -- FP64 runs at 1/64 of the FP32
+// rate here.  E is read with the streaming hint so the direction stays resident in L2.
 constexpr int kMvRows = 4;
 
-template <int NR>
+// WS warps share a group of kMvRows rows (8: the column split above, for long rows;
+// 1: every warp owns its rows, for short rows where eight warps would idle).
+template <int NR, int WS>
 __global__ void __launch_bounds__(kThreads)
 k_matvec_f32(const float* __restrict__ E, int64_t ldE, int n, const float* __restrict__ pv,
              const float* __restrict__ plo, const double* __restrict__ p64, int64_t ldv,
              int c0, int nrhs, double* __restrict__ q, double* __restrict__ pq_part,
              const ColState* __restrict__ st) {
   constexpr int RB = kMvRows;
+  constexpr int RBB = RB * (kMvWarps / WS);  // rows per block
   c0 += blockIdx.y * NR;  // one column group per grid row
   if (st) {  // converged columns are not multiplied again (uniform per block)
     bool live = false;
@@ -153,9 +156,10 @@ k_matvec_f32(const float* __restrict__ E, int64_t ldE, int n, const float* __res
     }
   }
   __shared__ float2 sm[kMvWarps][RB * NR];
-  __shared__ double spq[RB * NR];
+  __shared__ double spq[RBB * NR];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int row0 = blockIdx.x * RB;
+  const int gi = warp / WS, sub = warp % WS;  // row group of this warp, its column share
+  const int row0 = blockIdx.x * RBB + gi * RB;
   const int ngroups = (int)(ldE >> 7);
   const float* erow[RB];
 #pragma unroll
@@ -165,7 +169,7 @@ k_matvec_f32(const float* __restrict__ E, int64_t ldE, int n, const float* __res
   for (int i = 0; i < RB; ++i)
 #pragma unroll
     for (int r = 0; r < NR; ++r) part[i][r] = perr[i][r] = 0.f;
-  for (int g = warp; g < ngroups; g += kMvWarps) {
+  for (int g = sub; g < ngroups; g += WS) {
     const int64_t cc = (int64_t)g * 128 + lane * 4;
     float ev[RB][4];
 #pragma unroll
@@ -203,11 +207,12 @@ k_matvec_f32(const float* __restrict__ E, int64_t ldE, int n, const float* __res
     }
   __syncthreads();
   const int t = threadIdx.x;
-  if (t < RB * NR) {
-    float h = sm[0][t].x, l = sm[0][t].y;
+  if (t < RBB * NR) {  // t = (row group, row, column)
+    const int tg = t / (RB * NR), ti = t % (RB * NR);
+    float h = sm[tg * WS][ti].x, l = sm[tg * WS][ti].y;
 #pragma unroll
-    for (int w = 1; w < kMvWarps; ++w) pair_add(h, l, sm[w][t].x, sm[w][t].y);
-    const int i = t / NR, r = t % NR, row = row0 + i;
+    for (int w = 1; w < WS; ++w) pair_add(h, l, sm[tg * WS + w][ti].x, sm[tg * WS + w][ti].y);
+    const int i = ti / NR, r = ti % NR, row = blockIdx.x * RBB + tg * RB + i;
     double pq = 0.0;
     if (row < n) {
       const int64_t o = (int64_t)(c0 + r) * ldv + row;
@@ -221,7 +226,7 @@ k_matvec_f32(const float* __restrict__ E, int64_t ldE, int n, const float* __res
   if (t < NR) {
     double s = 0.0;
 #pragma unroll
-    for (int i = 0; i < RB; ++i) s += spq[i * NR + t];
+    for (int i = 0; i < RBB; ++i) s += spq[i * NR + t];
     pq_part[(int64_t)blockIdx.x * nrhs + c0 + t] = s;
   }
 }
@@ -598,9 +603,14 @@ int sm_count(int device) {
 }
 
 // Number of per-block p^T q partials a matvec writes (the block count of its launches).
+// Float matvec shape: eight warps split long rows (at least 16 groups of 128 columns),
+// otherwise every warp owns its rows.
+bool mv_split_rows(const Ctx* c) { return (c->ldE >> 7) >= 16; }
+
 int matvec_parts(const Ctx* c) {
   if (c->fp64()) return std::max(1, std::min((c->n + kMvWarps - 1) / kMvWarps, 4 * sm_count(c->device)));
-  return (c->n + kMvRows - 1) / kMvRows;
+  const int rbb = mv_split_rows(c) ? kMvRows : kMvRows * kMvWarps;
+  return (c->n + rbb - 1) / rbb;
 }
 
 template <typename T>
@@ -644,9 +654,15 @@ void launch_matvec<float>(const Ctx* c, const void* pv, const void* plo, const d
   const float* E = (const float*)c->E.ptr;
   const float* hi = (const float*)pv;
   const float* lo = (const float*)plo;
+  const bool split = mv_split_rows(c);
   for_column_groups(nrhs, [&](auto nr, int c0, int ny) {
-    (k_matvec_f32<decltype(nr)::value><<<dim3(gm, ny), kThreads, 0, c->stream>>>(
-         E, c->ldE, c->n, hi, lo, p64, ldv, c0, nrhs, q, pq_part, st), note_launch());
+    constexpr int NR = decltype(nr)::value;
+    if (split)
+      (k_matvec_f32<NR, kMvWarps><<<dim3(gm, ny), kThreads, 0, c->stream>>>(
+           E, c->ldE, c->n, hi, lo, p64, ldv, c0, nrhs, q, pq_part, st), note_launch());
+    else
+      (k_matvec_f32<NR, 1><<<dim3(gm, ny), kThreads, 0, c->stream>>>(
+           E, c->ldE, c->n, hi, lo, p64, ldv, c0, nrhs, q, pq_part, st), note_launch());
   });
 }
 
@@ -659,7 +675,9 @@ int pcg_solve(Ctx* c, const SolveArgs& a) {
   // elementwise kernels: ge blocks per right-hand side, one grid row per right-hand side
   const int ge = std::max(1, std::min((n + kThreads - 1) / kThreads, 2 * sms));
   const dim3 g2(ge, nrhs);
-  const int gm = matvec_parts(c);  // p^T q partials per column
+  // p^T q partials per column: one per matvec block (the ragged kernel takes kMvRows rows
+  // per block)
+  const int gm = a.sys ? (n + kMvRows - 1) / kMvRows : matvec_parts(c);
   const int pre = c->p.precond;
   const bool f64 = c->fp64();
   const size_t vbytes = (size_t)nrhs * ldv * sizeof(double);

@@ -265,6 +265,56 @@ k_bsol_kspace(const T* __restrict__ A, int n, int64_t lda, const T* __restrict__
   }
 }
 
+// Streamed builds keep no A: b^sol_k[f][i] = sum_{k >= kh} sqrt(W_k) [cos(K.r_i) v_c +
+// sin(K.r_i) v_s] with the electrode phases formed on the fly (fixed point, sincos_turns)
+// and the terms summed in error-free float pairs; one thread per electrode atom, the
+// k-vectors of a chunk and their structure factors staged in shared memory.
+constexpr int kDirectChunk = 256;
+
+__global__ void __launch_bounds__(128)
+k_bsol_kspace_direct(const uint32_t* __restrict__ sfix, int n, const int* __restrict__ hkl,
+                     const double* __restrict__ sqw, int mpad, int kh,
+                     const float* __restrict__ v, double* __restrict__ bsol) {
+  __shared__ uint32_t sh[kDirectChunk][3];
+  __shared__ float sv[kDirectChunk][3];  // sqrt(W), v_cos, v_sin
+  const int f = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const float* vf = v + (size_t)f * 2 * mpad;
+  uint32_t u0 = 0, u1 = 0, u2 = 0;
+  if (i < n) {
+    u0 = sfix[3 * i];
+    u1 = sfix[3 * i + 1];
+    u2 = sfix[3 * i + 2];
+  }
+  float hi = 0.f, lo = 0.f;
+  for (int k0 = kh; k0 < mpad; k0 += kDirectChunk) {
+    const int cnt = min(kDirectChunk, mpad - k0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+      const int k = k0 + t;
+      sh[t][0] = (uint32_t)hkl[3 * k];
+      sh[t][1] = (uint32_t)hkl[3 * k + 1];
+      sh[t][2] = (uint32_t)hkl[3 * k + 2];
+      const size_t kcol = 128 * (size_t)(k >> 6) + (k & 63);
+      sv[t][0] = (float)sqw[k];
+      sv[t][1] = vf[kcol];
+      sv[t][2] = vf[kcol + 64];
+    }
+    __syncthreads();
+    if (i >= n) continue;
+    for (int t = 0; t < cnt; ++t) {
+      float sn, cs;
+      sincos_turns(sh[t][0] * u0 + sh[t][1] * u1 + sh[t][2] * u2, &sn, &cs);
+      const float term = sv[t][0] * fmaf(sn, sv[t][2], cs * sv[t][1]);
+      const float s2 = hi + term;
+      const float bb = s2 - hi;
+      lo += (hi - (s2 - bb)) + (term - bb);
+      hi = s2;
+    }
+  }
+  if (i < n) bsol[(size_t)f * n + i] = (double)hi + (double)lo;
+}
+
 // FP64 real-space sum of one electrode-ion pair over every image within r_c:
 // sum q_I [erfc(g r) - erfc(alpha_i r)] / r.
 __device__ __forceinline__ double pair_images(const double* ri, double ai, const double* ion,
@@ -452,11 +502,29 @@ void launch_ion_structure_factor(bool fp64, const double* ion_xyz, const uint32_
 }
 
 // b^sol_k = A v: in float storage the head k-vectors (the heaviest weights) are
-// contracted in FP64 against an FP64 copy of their operand columns.
+// contracted in FP64 against an FP64 copy of their operand columns.  Without A (a streamed
+// build) the float part is the direct sum over the tail k-vectors.
 void launch_bsol_kspace(bool fp64, const void* A, const double* Ahead, int n, int mpad, int kh,
                         const void* v, const double* vhead, int frames, double* bsol,
+                        const uint32_t* sfix, const int* hkl, const double* sqw,
                         cudaStream_t s) {
   const int64_t lda = 2 * (int64_t)mpad;
+  if (!A && !fp64) {
+    for (int f0 = 0; f0 < frames; f0 += 65535) {
+      const int nf = std::min(frames - f0, 65535);
+      (k_bsol_kspace_direct<<<dim3((n + 127) / 128, nf), 128, 0, s>>>(
+           sfix, n, hkl, sqw, mpad, kh, (const float*)v + f0 * lda, bsol + (int64_t)f0 * n),
+       note_launch());
+    }
+    for (int g0 = 0; kh > 0 && g0 < (frames + 3) / 4; g0 += 65535) {
+      const int f0 = 4 * g0;
+      const dim3 grid((n * 32 + 255) / 256, std::min((frames - f0 + 3) / 4, 65535));
+      (k_bsol_kspace<double, 4><<<grid, 256, 0, s>>>(Ahead, n, 2 * (int64_t)kh,
+                                                     vhead + f0 * 2 * (int64_t)kh, frames - f0,
+                                                     bsol + (int64_t)f0 * n, 1), note_launch());
+    }
+    return;
+  }
   for (int g0 = 0; g0 < (frames + 3) / 4; g0 += 65535) {
     const int f0 = 4 * g0;
     const dim3 grid((n * 32 + 255) / 256, std::min((frames - f0 + 3) / 4, 65535));

@@ -179,7 +179,8 @@ struct TcArgs {
   int kb6_end;    // K-blocks before this take six products,
   int kb3_end;    // then three up to this one, then one
   const uint32_t* chunk_end;  // bit per K-block: an accumulation chunk ends after it
-  const double* head;         // [n][ldh] FP64 head + real-space terms (lower triangle)
+  int kb_col0;                // the operand planes start at this K-block
+  double* head;               // [n][ldh] FP64 head + real-space terms (lower triangle)
   int64_t ldh;
   float* E;
   int64_t ldE;
@@ -250,7 +251,7 @@ k_ek_tc(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtens
         uint8_t* st = ring + s * kStageBytes;
         int prods;
         const int cnt = stage_blocks(args, kb, nkb, prods);
-        const int x = (args.kb_begin + kb) * kBlockK;
+        const int x = (args.kb_begin + kb - args.kb_col0) * kBlockK;
         if (prods == 6) {
           mbar_expect_tx(&full_bar[s], 6 * kPlaneTileBytes);
           tma_load_2d(st + 0 * kPlaneTileBytes, &map0, &full_bar[s], x, i0);
@@ -381,9 +382,10 @@ k_ek_tc(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtens
             for (int t = 0; t < 32; ++t) {
               const int j = j0 + cg * 32 + t;
               if (j < args.n && j <= row) {
-                const double v = (double)__uint_as_float(hi[t]) + (double)__uint_as_float(lo[t]) +
-                                 args.head[(int64_t)row * args.ldh + j];
-                args.E[(int64_t)row * args.ldE + j] = (float)v;
+                double* hp = args.head + (int64_t)row * args.ldh + j;
+                const double v = (double)__uint_as_float(hi[t]) + (double)__uint_as_float(lo[t]) + *hp;
+                if (args.E) args.E[(int64_t)row * args.ldE + j] = (float)v;
+                else *hp = v;  // a K-window of a streamed build: carry the sum in FP64
               }
             }
           }
@@ -409,20 +411,12 @@ k_ek_tc(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtens
   }
 }
 
-// a = a0 + a1 + a2 in BF16 (each plane the rounding of the remainder of the previous).
-__global__ void k_split_bf16(const float* __restrict__ A, int64_t len, __nv_bfloat16* __restrict__ p0,
-                             __nv_bfloat16* __restrict__ p1, __nv_bfloat16* __restrict__ p2) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const float a = A[i];
-    const __nv_bfloat16 b0 = __float2bfloat16_rn(a);
-    const float r1 = a - __bfloat162float(b0);
-    const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
-    const float r2 = r1 - __bfloat162float(b1);
-    p0[i] = b0;
-    p1[i] = b1;
-    p2[i] = __float2bfloat16_rn(r2);
-  }
+// E = head (lower triangle) when the tail contributes nothing to the last window.
+__global__ void k_head_to_float(const double* __restrict__ head, int64_t ldh,
+                                float* __restrict__ E, int64_t ldE, int n) {
+  const int j = blockIdx.x * 32 + threadIdx.x;
+  for (int i = blockIdx.y * 32 + threadIdx.y; i < min(n, (int)(blockIdx.y + 1) * 32); i += 8)
+    if (j < n && j <= i) E[(int64_t)i * ldE + j] = (float)head[(int64_t)i * ldh + j];
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -452,26 +446,24 @@ bool make_map(CUtensorMap* m, const void* base, int rows, int64_t cols) {
 
 }  // namespace
 
-void launch_split_bf16(const float* A, int64_t len, void* p0, void* p1, void* p2,
-                       cudaStream_t s) {
-  (k_split_bf16<<<2048, 256, 0, s>>>(A, len, (__nv_bfloat16*)p0, (__nv_bfloat16*)p1,
-                                     (__nv_bfloat16*)p2), note_launch());
-}
-
-int launch_ek_tc(const void* p0, const void* p1, const void* p2, int npad, int mpad, int n,
-                 int kb_begin, int kb6_end, int kb3_end, const uint32_t* chunk_end, const double* head, int64_t ldh,
-                 float* E, int64_t ldE, int* err, cudaStream_t s) {
+// K-blocks [kb_begin, kb_end) of the lower triangle from BF16 planes holding the K-blocks
+// kb_col0 .. kb_col0 + plane_cols / 64; the result plus head goes to float E, or back into
+// head (FP64) when E is null.
+int launch_ek_tc(const void* p0, const void* p1, const void* p2, int npad, int64_t plane_cols,
+                 int kb_col0, int n, int kb_begin, int kb_end, int kb6_end, int kb3_end,
+                 const uint32_t* chunk_end, double* head, int64_t ldh, float* E, int64_t ldE,
+                 int* err, cudaStream_t s) {
   CUtensorMap m0, m1, m2;
-  const int64_t cols = 2 * (int64_t)mpad;
-  if (!make_map(&m0, p0, npad, cols) || !make_map(&m1, p1, npad, cols) ||
-      !make_map(&m2, p2, npad, cols))
+  if (!make_map(&m0, p0, npad, plane_cols) || !make_map(&m1, p1, npad, plane_cols) ||
+      !make_map(&m2, p2, npad, plane_cols))
     return CPM_ECUDA;
   TcArgs a;
   a.n = n;
   a.kb_begin = kb_begin;
-  a.kb_end = (int)(cols / kBlockK);
+  a.kb_end = kb_end;
   a.kb6_end = kb6_end;
   a.kb3_end = kb3_end;
+  a.kb_col0 = kb_col0;
   a.chunk_end = chunk_end;
   a.head = head;
   a.ldh = ldh;
@@ -484,7 +476,13 @@ int launch_ek_tc(const void* p0, const void* p1, const void* p2, int npad, int m
   if (cudaFuncSetAttribute(k_ek_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
       cudaSuccess)
     return CPM_ECUDA;
-  if (a.kb_begin >= a.kb_end) return CPM_OK;  // everything is in the head
+  if (a.kb_begin >= a.kb_end) {  // nothing of the tail in this window
+    if (E)
+      (k_head_to_float<<<dim3((n + 31) / 32, (n + 31) / 32), dim3(32, 8), 0, s>>>(head, ldh, E,
+                                                                              ldE, n),
+       note_launch());
+    return cudaGetLastError() == cudaSuccess ? CPM_OK : CPM_ECUDA;
+  }
   (k_ek_tc<<<tiles, kThreads, smem, s>>>(m0, m1, m2, a), note_launch());
   return cudaGetLastError() == cudaSuccess ? CPM_OK : CPM_ECUDA;
 }

@@ -246,3 +246,58 @@ def ragged_systems(count: int = 32, n_lo: int = 500, n_hi: int = 8000, seed: int
         out.append(Workload(f"two-sheet graphene N={el.n}, {n_ion} ions", el,
                             Electrolyte(ions[None], q[None])))
     return out
+
+
+def stacked_electrode(rng: np.random.Generator, nx: int = 90, ny: int = 52, sheets: int = 6,
+                      spacing: float = 7.0, lz: float = 105.0, hole_frac: float = 0.05,
+                      r_lo: float = 3.0, r_hi: float = 8.0, alpha: float = 1.979,
+                      chi: float = 0.5) -> Electrode:
+    """`sheets` graphene sheets of nx x ny cells, `spacing` apart from z = 0, each with
+    seeded circular pinholes (radius uniform in [r_lo, r_hi], minimum image in x, y) cut
+    until at least `hole_frac` of its atoms are removed; sheet potentials alternate
+    -chi, +chi."""
+    lx, ly = nx * CELL_A, ny * CELL_B
+    parts, chis = [], []
+    for s in range(sheets):
+        pts = graphene_sheet(nx, ny, s * spacing)
+        keep = np.ones(pts.shape[0], dtype=bool)
+        while np.count_nonzero(~keep) < hole_frac * pts.shape[0]:
+            c = np.array([rng.uniform(0.0, lx), rng.uniform(0.0, ly), s * spacing])
+            r = rng.uniform(r_lo, r_hi)
+            keep &= _min_image_dist2(c, pts, lx, ly) >= r * r
+        parts.append(pts[keep])
+        chis.append(np.full(int(keep.sum()), chi if s % 2 else -chi))
+    xyz = np.concatenate(parts, axis=0)
+    return Electrode(xyz=xyz, alpha=np.full(xyz.shape[0], alpha), chi=np.concatenate(chis),
+                     box=(lx, ly, lz))
+
+
+def scale_point(seed: int | None = None, n_ion: int = 20000, rhs: int = 1) -> Workload:
+    """Six stacked 90 x 52-cell sheets 7 A apart with 5% pinholes (~106,700 atoms) in a
+    221.4 x 221.52 x 105 A box; n_ion ions (half +1, half -1) spread evenly over the five
+    gaps, each at least 2 A from both sheets and 2.5 A from the other ions of its gap;
+    `rhs` frames, Gaussian perturbations (0.5 A) of the first, z reflected into the band."""
+    rng = np.random.default_rng(seed_for(5) if seed is None else seed)
+    el = stacked_electrode(rng)
+    gaps = 5
+    per = n_ion // gaps
+    xyz, q = [], []
+    for g_ in range(gaps):
+        zlo, zhi = 7.0 * g_ + 2.0, 7.0 * (g_ + 1) - 2.0
+        pts, qq = random_ions(rng, per // 2, per - per // 2, el.box, zlo=zlo, zhi=zhi,
+                              min_sep=2.5)
+        xyz.append(pts)
+        q.append(qq)
+    base = np.concatenate(xyz, axis=0)
+    qv = np.concatenate(q)
+    frames = [base]
+    for _ in range(rhs - 1):
+        f = base + rng.normal(0.0, 0.5, size=base.shape)
+        f[:, 0] %= el.box[0]
+        f[:, 1] %= el.box[1]
+        for g_ in range(gaps):  # reflect each ion back into its own band
+            sel = (base[:, 2] >= 7.0 * g_) & (base[:, 2] < 7.0 * (g_ + 1))
+            f[sel, 2] = _reflect(f[sel, 2], 7.0 * g_ + 2.0, 7.0 * (g_ + 1) - 2.0)
+        frames.append(f)
+    return Workload(f"six stacked graphene sheets with pinholes N={el.n}, {len(qv)} ions",
+                    el, Electrolyte(np.stack(frames), np.broadcast_to(qv, (rhs, len(qv))).copy()))
