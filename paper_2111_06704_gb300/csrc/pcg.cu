@@ -596,6 +596,17 @@ __global__ void k_neutralize_ragged(double* __restrict__ q, int64_t ld,
   for (int i = threadIdx.x; i < n; i += blockDim.x) qc[i] -= t * d[i];
 }
 
+// nrhs columns of n doubles between layouts with leading dimensions ldd and lds (device
+// to device): one strided copy instead of one call per column.
+cudaError_t copy_cols(double* dst, int64_t ldd, const double* src, int64_t lds, int n,
+                      int nrhs, cudaStream_t s) {
+  if (ldd == n && lds == n)
+    return cudaMemcpyAsync(dst, src, (size_t)nrhs * n * sizeof(double), cudaMemcpyDeviceToDevice,
+                           s);
+  return cudaMemcpy2DAsync(dst, ldd * sizeof(double), src, lds * sizeof(double),
+                           n * sizeof(double), nrhs, cudaMemcpyDeviceToDevice, s);
+}
+
 int sm_count(int device) {
   int v = 0;
   cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
@@ -737,11 +748,7 @@ int pcg_solve(Ctx* c, const SolveArgs& a) {
   // initial guess: q = E x0 through the same (hi + lo) matvec
   const double* q2 = nullptr;
   if (a.use_guess) {
-    for (int col = 0; col < nrhs; ++col)
-      if (cuda_check(c, cudaMemcpyAsync(x + (int64_t)col * ldv, a.x + (int64_t)col * n,
-                                        n * sizeof(double), cudaMemcpyDeviceToDevice, s),
-                     "copy guess"))
-        return CPM_ECUDA;
+    if (cuda_check(c, copy_cols(x, ldv, a.x, n, n, nrhs, s), "copy guess")) return CPM_ECUDA;
     if (f64) (k_p_update<double><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, st, x, p, (double*)pv, nullptr, 1), note_launch());
     else (k_p_update<float><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, st, x, p, (float*)pv, plo, 1), note_launch());
     matvec(nullptr);
@@ -808,11 +815,7 @@ int pcg_solve(Ctx* c, const SolveArgs& a) {
     }
   }
   if (!all_done && (rc = poll(it))) return rc;
-  for (int col = 0; col < nrhs; ++col)
-    if (cuda_check(c, cudaMemcpyAsync(a.x + (int64_t)col * n, x + (int64_t)col * ldv,
-                                      n * sizeof(double), cudaMemcpyDeviceToDevice, s),
-                   "copy x"))
-      return CPM_ECUDA;
+  if (cuda_check(c, copy_cols(a.x, n, x, ldv, n, nrhs, s), "copy x")) return CPM_ECUDA;
   if (cuda_check(c, cudaStreamSynchronize(s), "pcg end")) return CPM_ECUDA;
   int status = CPM_OK;
   for (int col = 0; col < nrhs; ++col) {
@@ -851,10 +854,7 @@ int apply_E(Ctx* c, int nrhs, const double* p_in, double* q_out) {
   ColState* st = (ColState*)(base + 3 * vbytes + hbytes + pqbytes);
   cudaStream_t s = c->stream;
   if (cuda_check(c, cudaMemsetAsync(base, 0, 3 * vbytes + hbytes, s), "memset")) return CPM_ECUDA;
-  for (int col = 0; col < nrhs; ++col)
-    if (cuda_check(c, cudaMemcpyAsync(zin + (int64_t)col * ldv, p_in + (int64_t)col * n,
-                                      n * sizeof(double), cudaMemcpyDeviceToDevice, s), "p in"))
-      return CPM_ECUDA;
+  if (cuda_check(c, copy_cols(zin, ldv, p_in, n, n, nrhs, s), "p in")) return CPM_ECUDA;
   const dim3 g2(ge, nrhs);
   // first = 1: p = zin, and its float pair
   if (f64) (k_p_update<double><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, st, zin, p, (double*)pv, nullptr, 1), note_launch());
@@ -864,10 +864,7 @@ int apply_E(Ctx* c, int nrhs, const double* p_in, double* q_out) {
   else launch_matvec<float>(c, pv, plo, p, ldv, nrhs, q, pq_part, gm, nullptr);
   cudaEventRecord(c->ev_tc[1], s);
   if (cuda_check(c, cudaGetLastError(), "apply_E")) return CPM_ECUDA;
-  for (int col = 0; col < nrhs; ++col)
-    if (cuda_check(c, cudaMemcpyAsync(q_out + (int64_t)col * n, q + (int64_t)col * ldv,
-                                      n * sizeof(double), cudaMemcpyDeviceToDevice, s), "q out"))
-      return CPM_ECUDA;
+  if (cuda_check(c, copy_cols(q_out, n, q, ldv, n, nrhs, s), "q out")) return CPM_ECUDA;
   if (cuda_check(c, cudaStreamSynchronize(s), "apply_E sync")) return CPM_ECUDA;
   cudaEventElapsedTime(&c->t_matvec_ms, c->ev_tc[0], c->ev_tc[1]);
   return CPM_OK;
