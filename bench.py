@@ -773,9 +773,10 @@ def run_learned(args, rank, world, local_rank):
         ctx.cpm_neutralize(q, qs[test].contiguous())
         return it
 
+    bp = b[T:T + H].contiguous()
+
     def solve_learned():
-        q0 = g.guess(g.features(bt, b[T:T + H].contiguous(), chi), prev).reshape(prev.shape)
-        q0 = q0.contiguous()
+        q0 = g.guess_frames(bt, bp, chi, prev)
         _, it, _ = ctx.cpm_solve(bt, q0, use_guess=True, tol=TOL, maxit=2000)
         ctx.cpm_neutralize(q0, qs[test].contiguous())
         return it
@@ -788,8 +789,7 @@ def run_learned(args, rank, world, local_rank):
         return time.perf_counter() - t0, it
 
     def guess_only():
-        q0 = g.guess(g.features(bt, b[T:T + H].contiguous(), chi), prev)
-        return q0
+        return g.guess_frames(bt, bp, chi, prev)
 
     for _ in range(max(1, args.warmup)):
         solve_prev()

@@ -217,6 +217,13 @@ int cpm_mlp_adam(cpm_ctx* c, float* params, float* m, float* v, const float* gra
 int cpm_guess_apply(cpm_ctx* c, int64_t len, const float* y, float scale, const double* q_prev,
                     double* q0);
 
+/* The whole guess in one call: features of `frames` frames (as cpm_guess_features, into
+ * a context workspace), the network, and q0 = q_prev + scale * y, with one
+ * synchronisation.  Device arrays; b, b_prev, q_prev, q0 [frames*n]. */
+int cpm_guess(cpm_ctx* c, const float* params, const float* norm, int bf16, int frames,
+              const double* b, const double* b_prev, const double* chi, float scale,
+              const double* q_prev, double* q0);
+
 /* q = E_n p for nrhs charge vectors p[nrhs*n] (e): the electrostatic potentials (1/A per e)
  * on the electrode atoms, through the same matvec as the solver (E streamed once per pass
  * of up to eight columns). */

@@ -85,7 +85,8 @@ EXPORTS = ["cpm_default_params", "cpm_create", "cpm_destroy", "cpm_build_E", "cp
            "cpm_get_d", "cpm_guess_features", "cpm_mlp_forward", "cpm_mlp_grad",
            "cpm_mlp_adam", "cpm_guess_apply", "cpm_apply_E", "cpm_get_precond",
            "cpm_last_error", "cpm_batch_create", "cpm_batch_destroy", "cpm_batch_solve",
-           "cpm_batch_neutralize", "cpm_batch_last_error", "cpm_get_E_rows"]
+           "cpm_batch_neutralize", "cpm_batch_last_error", "cpm_get_E_rows",
+           "cpm_guess"]
 
 _lib = None
 
@@ -132,6 +133,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.cpm_mlp_grad.argtypes = [vp, vp, vp, i, i64, vp, vp, vp, vp]
     lib.cpm_mlp_adam.argtypes = [vp, vp, vp, vp, vp, i, ctypes.c_float]
     lib.cpm_guess_apply.argtypes = [vp, i64, vp, ctypes.c_float, vp, vp]
+    lib.cpm_guess.argtypes = [vp, vp, vp, i, i, vp, vp, vp, ctypes.c_float, vp, vp]
     lib.cpm_apply_E.argtypes = [vp, i, vp, vp]
     lib.cpm_last_error.argtypes = [vp]
     lib.cpm_last_error.restype = ctypes.c_char_p

@@ -249,7 +249,7 @@ int cpm_destroy(cpm_ctx* c) {
   cudaEventDestroy(c->ev_tc[0]);
   cudaEventDestroy(c->ev_tc[1]);
   Buf* ws[] = {&c->ws_solve, &c->ws_in0, &c->ws_in1, &c->ws_in2, &c->ws_out0, &c->ws_out1,
-               &c->ws_pot, &c->ws_guess};
+               &c->ws_pot, &c->ws_guess, &c->ws_feat};
   for (Buf* b : ws) buf_free(c, b);
   delete c;
   return CPM_OK;

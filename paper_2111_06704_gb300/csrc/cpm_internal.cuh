@@ -113,7 +113,7 @@ struct Ctx {
 
   // scratch (grown on demand, never shrunk)
   std::vector<Buf*> scratch;
-  Buf ws_solve, ws_in0, ws_in1, ws_in2, ws_out0, ws_out1, ws_pot, ws_guess;
+  Buf ws_solve, ws_in0, ws_in1, ws_in2, ws_out0, ws_out1, ws_pot, ws_guess, ws_feat;
 
   float t_kspace_ms = 0, t_phase_ms = 0, t_precond_ms = 0, t_dsolve_ms = 0, t_tc_ms = 0;
   float t_matvec_ms = 0;  // last cpm_apply_E: the matvec launches alone

@@ -166,7 +166,8 @@ __device__ __forceinline__ void fwd_store(float* __restrict__ out, const float (
 
 __global__ void __launch_bounds__(kFwdThreads, 2)
 k_mlp_forward(const float* __restrict__ params, const float* __restrict__ norm, int bf16,
-              int64_t samples, const float* __restrict__ feat, float* __restrict__ out) {
+              int64_t samples, const float* __restrict__ feat, float* __restrict__ out,
+              float scale, const double* __restrict__ q_prev, double* __restrict__ q0) {
   extern __shared__ __align__(16) float fsm[];
   float* WT1 = fsm;               // [kF][kH]
   float* WT2 = WT1 + kF * kH;     // [kH][kH]
@@ -223,7 +224,10 @@ k_mlp_forward(const float* __restrict__ params, const float* __restrict__ norm, 
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const int64_t gs = s0 + 8 * sg + k;
-        if (gs < samples) out[gs] = y[k];
+        if (gs < samples) {
+          if (out) out[gs] = y[k];
+          if (q0) q0[gs] = q_prev[gs] + (double)scale * (double)y[k];  // the guess, fused
+        }
       }
   }
 }
@@ -386,10 +390,10 @@ using namespace cpm;
 
 struct cpm_ctx : public cpm::Ctx {};
 
-extern "C" {
+namespace {
 
-int cpm_guess_features(cpm_ctx* c, int frames, const double* b, const double* b_prev,
-                       const double* chi, float* feat) {
+int features_async(cpm_ctx* c, int frames, const double* b, const double* b_prev,
+                   const double* chi, float* feat) {
   if (!c) return CPM_EINVAL;
   if (!c->built) return set_err(c, CPM_ENOTBUILT, "cpm_guess_features before cpm_build_E");
   if (c->p.precond != CPM_PRECOND_DC || !c->nbr_off.ptr)
@@ -456,8 +460,46 @@ int cpm_guess_features(cpm_ctx* c, int frames, const double* b, const double* b_
        (const int64_t*)c->shell_off.ptr, (const int*)c->shell_members.ptr,
        (const int64_t*)c->nbr_off.ptr, (const int*)c->nbr_idx.ptr,
        (const double*)c->prow.ptr, c->pgap, feat), note_launch());
-  if ((st = cuda_check(c, cudaGetLastError(), "features"))) return st;
+  return cuda_check(c, cudaGetLastError(), "features");
+}
+
+}  // namespace
+
+extern "C" {
+
+int cpm_guess_features(cpm_ctx* c, int frames, const double* b, const double* b_prev,
+                       const double* chi, float* feat) {
+  int st = features_async(c, frames, b, b_prev, chi, feat);
+  if (st) return st;
   return cuda_check(c, cudaStreamSynchronize(c->stream), "features sync");
+}
+
+int cpm_guess(cpm_ctx* c, const float* params, const float* norm, int bf16, int frames,
+              const double* b, const double* b_prev, const double* chi, float scale,
+              const double* q_prev, double* q0) {
+  if (!c) return CPM_EINVAL;
+  if (!c->built) return set_err(c, CPM_ENOTBUILT, "cpm_guess before cpm_build_E");
+  if (frames < 1 || !on_device(params) || !on_device(norm) || !on_device(q_prev) ||
+      !on_device(q0))
+    return set_err(c, CPM_EINVAL, "cpm_guess: frames >= 1 and device arrays");
+  const int64_t samples = (int64_t)frames * c->n;
+  int st = buf_reserve(c, &c->ws_feat, samples * kF * sizeof(float));
+  if (st) return st;
+  float* feat = (float*)c->ws_feat.ptr;
+  if ((st = features_async(c, frames, b, b_prev, chi, feat))) return st;
+  if ((st = cuda_check(c, cudaFuncSetAttribute(k_mlp_forward,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)kFwdSmem), "forward smem")))
+    return st;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  const int64_t tiles = (samples + kTs - 1) / kTs;
+  const int blocks = (int)std::min<int64_t>(tiles, 2 * (int64_t)std::max(sms, 1));
+  (k_mlp_forward<<<blocks, kFwdThreads, kFwdSmem, c->stream>>>(params, norm, bf16, samples,
+                                                               feat, nullptr, scale, q_prev,
+                                                               q0), note_launch());
+  if ((st = cuda_check(c, cudaGetLastError(), "guess"))) return st;
+  return cuda_check(c, cudaStreamSynchronize(c->stream), "guess sync");
 }
 
 int cpm_mlp_forward(cpm_ctx* c, const float* params, const float* norm, int bf16,
@@ -475,7 +517,8 @@ int cpm_mlp_forward(cpm_ctx* c, const float* params, const float* norm, int bf16
   const int64_t tiles = (samples + kTs - 1) / kTs;
   const int blocks = (int)std::min<int64_t>(tiles, 2 * (int64_t)std::max(sms, 1));
   (k_mlp_forward<<<blocks, kFwdThreads, kFwdSmem, c->stream>>>(params, norm, bf16, samples,
-                                                               feat, out), note_launch());
+                                                               feat, out, 0.f, nullptr,
+                                                               nullptr), note_launch());
   if ((st = cuda_check(c, cudaGetLastError(), "forward"))) return st;
   return cuda_check(c, cudaStreamSynchronize(c->stream), "forward sync");
 }

@@ -29,6 +29,7 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include "cpm_internal.cuh"
 
@@ -37,10 +38,19 @@ namespace cpm {
 namespace {
 
 constexpr int kTile = 128;           // output tile edge
-constexpr int kBlockK = 64;          // operand columns per K-block (128 B of BF16)
-constexpr int kStages = 2;
-constexpr int kPlaneTileBytes = kTile * kBlockK * 2;  // 16 KB
-constexpr int kStageBytes = 6 * kPlaneTileBytes;      // A0 A1 A2 (rows i) + B0 B1 B2 (rows j)
+constexpr int kBlockK = 64;          // operand columns per K-block of the schedule
+constexpr int kRingBytes = 192 * 1024;
+
+// Loads and MMAs go by sub-blocks of BK columns: BK = 64 (128-byte swizzle, two 96 KB
+// stages) or BK = 32 (64-byte swizzle, four 48 KB stages: the same bytes in flight,
+// refilled at half the granularity).
+template <int BK>
+struct TcCfg {
+  static constexpr int kSub = kBlockK / BK;            // sub-blocks per K-block
+  static constexpr int kTileBytes = kTile * BK * 2;    // one 128 x BK BF16 tile
+  static constexpr int kStageBytes = 6 * kTileBytes;   // six tile slots
+  static constexpr int kStages = kRingBytes / kStageBytes;
+};
 constexpr int kThreads = 192;                         // 6 warps
 constexpr long long kWaitCycles = 20000000000ll;      // ~10 s at 2 GHz: wait limit
 
@@ -100,13 +110,16 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
 
 // Shared-memory matrix descriptor: K-major tile, 128-byte swizzle, rows of 128 B,
 // 8-row groups 1024 B apart (SBO), version 1, layout type 2 (SWIZZLE_128B).
+template <int BK>
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  // K-major tile, rows of BK * 2 bytes, 8-row groups SBO apart, version 1, swizzle
+  // 128 B (layout type 2) for BK = 64 or 64 B (layout type 4) for BK = 32
   uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);  // start address
-  d |= (uint64_t)1 << 16;                   // leading byte offset (unused for SW128 K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset
-  d |= (uint64_t)1 << 46;                   // descriptor version
-  d |= (uint64_t)2 << 61;                   // SWIZZLE_128B
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);     // start address
+  d |= (uint64_t)1 << 16;                      // leading byte offset (unused when swizzled)
+  d |= (uint64_t)((8 * BK * 2) >> 4) << 32;    // stride byte offset: 8 rows
+  d |= (uint64_t)1 << 46;                      // descriptor version
+  d |= (uint64_t)(BK == 64 ? 2 : 4) << 61;     // swizzle mode
   return d;
 }
 
@@ -187,10 +200,12 @@ struct TcArgs {
   int* err;
 };
 
-// K-blocks held by the ring stage that starts at relative block kb, and their product
-// count: one six- or three-product block, or up to three one-product blocks.
-__device__ __forceinline__ int stage_blocks(const TcArgs& a, int kb, int nkb, int& prods) {
-  const int g = a.kb_begin + kb;
+// Sub-blocks (of BK columns) held by the ring stage that starts at relative sub-block sb,
+// and their product count (from the schedule block they belong to): one six- or
+// three-product sub-block, or up to three one-product sub-blocks.
+template <int BK>
+__device__ __forceinline__ int stage_blocks(const TcArgs& a, int sb, int nsb, int& prods) {
+  const int g = (a.kb_begin * TcCfg<BK>::kSub + sb) / TcCfg<BK>::kSub;
   if (g < a.kb6_end) {
     prods = 6;
     return 1;
@@ -200,12 +215,15 @@ __device__ __forceinline__ int stage_blocks(const TcArgs& a, int kb, int nkb, in
     return 1;
   }
   prods = 1;
-  return min(3, nkb - kb);
+  return min(3, nsb - sb);
 }
 
+template <int BK>
 __global__ void __launch_bounds__(kThreads, 1)
 k_ek_tc(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1,
         const __grid_constant__ CUtensorMap map2, TcArgs args) {
+  constexpr int kSub = TcCfg<BK>::kSub, kStages = TcCfg<BK>::kStages;
+  constexpr int kPlaneTileBytes = TcCfg<BK>::kTileBytes, kStageBytes = TcCfg<BK>::kStageBytes;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // 1024-byte aligned ring of kStages x 6 tiles
   uint8_t* ring = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -217,7 +235,8 @@ k_ek_tc(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtens
   int I, J;
   tri_tile(blockIdx.x, I, J);
   const int i0 = I * kTile, j0 = J * kTile;
-  const int nkb = args.kb_end - args.kb_begin;
+  const int nkb = args.kb_end - args.kb_begin;       // schedule blocks (epilogue chunks)
+  const int nsb = nkb * kSub;                         // sub-blocks (loads and MMAs)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -245,13 +264,13 @@ k_ek_tc(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtens
     // ---- TMA producer ------------------------------------------------------------
     if (lane == 0) {
       int stage = 0;
-      for (int kb = 0; kb < nkb; ++stage) {
+      for (int kb = 0; kb < nsb; ++stage) {  // kb: relative sub-block
         const int s = stage % kStages;
         if (!mbar_wait(&empty_bar[s], ((stage / kStages) & 1) ^ 1, args.err, 1)) break;
         uint8_t* st = ring + s * kStageBytes;
         int prods;
-        const int cnt = stage_blocks(args, kb, nkb, prods);
-        const int x = (args.kb_begin + kb - args.kb_col0) * kBlockK;
+        const int cnt = stage_blocks<BK>(args, kb, nsb, prods);
+        const int x = ((args.kb_begin - args.kb_col0) * kSub + kb) * BK;
         if (prods == 6) {
           mbar_expect_tx(&full_bar[s], 6 * kPlaneTileBytes);
           tma_load_2d(st + 0 * kPlaneTileBytes, &map0, &full_bar[s], x, i0);
@@ -269,9 +288,8 @@ k_ek_tc(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtens
         } else {
           mbar_expect_tx(&full_bar[s], 2 * cnt * kPlaneTileBytes);
           for (int u = 0; u < cnt; ++u) {
-            tma_load_2d(st + (2 * u) * kPlaneTileBytes, &map0, &full_bar[s], x + u * kBlockK, i0);
-            tma_load_2d(st + (2 * u + 1) * kPlaneTileBytes, &map0, &full_bar[s], x + u * kBlockK,
-                        j0);
+            tma_load_2d(st + (2 * u) * kPlaneTileBytes, &map0, &full_bar[s], x + u * BK, i0);
+            tma_load_2d(st + (2 * u + 1) * kPlaneTileBytes, &map0, &full_bar[s], x + u * BK, j0);
           }
         }
         kb += cnt;
@@ -288,10 +306,10 @@ k_ek_tc(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtens
       bool first_in_chunk = true;
       bool ok = true;
       int stage = 0;
-      for (int kb = 0; kb < nkb && ok; ++stage) {
+      for (int kb = 0; kb < nsb && ok; ++stage) {  // kb: relative sub-block
         const int s = stage % kStages;
         int prods;
-        const int cnt = stage_blocks(args, kb, nkb, prods);
+        const int cnt = stage_blocks<BK>(args, kb, nsb, prods);
         ok = mbar_wait(&full_bar[s], (stage / kStages) & 1, args.err, 3);
         if (!ok) break;
         tc_fence_after();
@@ -308,17 +326,21 @@ k_ek_tc(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtens
           const int sb = prods == 6 ? 3 : prods == 3 ? 2 : 2 * u + 1;
           const uint32_t d = tmem + (uint32_t)(buf * kTile);
 #pragma unroll
-          for (int ks = 0; ks < kBlockK / 16; ++ks) {
+          for (int ks = 0; ks < BK / 16; ++ks) {
             for (int t = 0; t < prods; ++t) {
               const int pa = (kPa >> (4 * t)) & 15, pb = (kPb >> (4 * t)) & 15;
-              const uint64_t da = smem_desc(st + (sa + pa) * kPlaneTileBytes + ks * 32);
-              const uint64_t db = smem_desc(st + (sb + pb) * kPlaneTileBytes + ks * 32);
+              const uint64_t da = smem_desc<BK>(st + (sa + pa) * kPlaneTileBytes + ks * 32);
+              const uint64_t db = smem_desc<BK>(st + (sb + pb) * kPlaneTileBytes + ks * 32);
               mma_bf16(d, da, db, (first_in_chunk && ks == 0 && t == 0) ? 0u : 1u);
             }
           }
           first_in_chunk = false;
-          const int g = args.kb_begin + kb + u;
-          const bool last = (kb + u + 1 == nkb) || ((args.chunk_end[g >> 5] >> (g & 31)) & 1u);
+          // an accumulation chunk ends with the last sub-block of a schedule block whose
+          // chunk bit is set, or with the launch's last sub-block
+          const int gs = args.kb_begin * kSub + kb + u;
+          const int g = gs / kSub;
+          const bool last = (kb + u + 1 == nsb) ||
+                            (gs % kSub == kSub - 1 && ((args.chunk_end[g >> 5] >> (g & 31)) & 1u));
           if (last) {
             mma_commit(&acc_full[buf]);
             ++chunk;
@@ -432,15 +454,16 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-bool make_map(CUtensorMap* m, const void* base, int rows, int64_t cols) {
+bool make_map(CUtensorMap* m, const void* base, int rows, int64_t cols, int bk) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-  cuuint32_t box[2] = {(cuuint32_t)kBlockK, (cuuint32_t)kTile};
+  cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)kTile};
   cuuint32_t estr[2] = {1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
-            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -453,9 +476,11 @@ int launch_ek_tc(const void* p0, const void* p1, const void* p2, int npad, int64
                  int kb_col0, int n, int kb_begin, int kb_end, int kb6_end, int kb3_end,
                  const uint32_t* chunk_end, double* head, int64_t ldh, float* E, int64_t ldE,
                  int* err, cudaStream_t s) {
+  const char* env = getenv("CPM_TC_BK");
+  const int bk = env && atoi(env) == 32 ? 32 : 64;
   CUtensorMap m0, m1, m2;
-  if (!make_map(&m0, p0, npad, plane_cols) || !make_map(&m1, p1, npad, plane_cols) ||
-      !make_map(&m2, p2, npad, plane_cols))
+  if (!make_map(&m0, p0, npad, plane_cols, bk) || !make_map(&m1, p1, npad, plane_cols, bk) ||
+      !make_map(&m2, p2, npad, plane_cols, bk))
     return CPM_ECUDA;
   TcArgs a;
   a.n = n;
@@ -472,9 +497,11 @@ int launch_ek_tc(const void* p0, const void* p1, const void* p2, int npad, int64
   a.err = err;
   const int nt = (n + kTile - 1) / kTile;
   const int tiles = nt * (nt + 1) / 2;
-  const int smem = kStages * kStageBytes + 1024;
-  if (cudaFuncSetAttribute(k_ek_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-      cudaSuccess)
+  const int smem = kRingBytes + 1024;
+  if (cudaFuncSetAttribute(k_ek_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_ek_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+          cudaSuccess)
     return CPM_ECUDA;
   if (a.kb_begin >= a.kb_end) {  // nothing of the tail in this window
     if (E)
@@ -483,7 +510,8 @@ int launch_ek_tc(const void* p0, const void* p1, const void* p2, int npad, int64
        note_launch());
     return cudaGetLastError() == cudaSuccess ? CPM_OK : CPM_ECUDA;
   }
-  (k_ek_tc<<<tiles, kThreads, smem, s>>>(m0, m1, m2, a), note_launch());
+  if (bk == 32) (k_ek_tc<32><<<tiles, kThreads, smem, s>>>(m0, m1, m2, a), note_launch());
+  else (k_ek_tc<64><<<tiles, kThreads, smem, s>>>(m0, m1, m2, a), note_launch());
   return cudaGetLastError() == cudaSuccess ? CPM_OK : CPM_ECUDA;
 }
 

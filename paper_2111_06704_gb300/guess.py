@@ -88,6 +88,17 @@ class LearnedGuess:
                                                  _vp(q_prev), _vp(q0)))
         return q0
 
+    def guess_frames(self, b, b_prev, chi, q_prev):
+        """Features, network and q0 = q_prev + scale * net in one library call."""
+        import torch
+        frames = int(b.shape[0])
+        q0 = torch.empty_like(q_prev)
+        self.ctx._check(self.lib.cpm_guess(self.ctx.h, _vp(self.params), _vp(self.norm),
+                                           self.bf16, frames, _vp(b), _vp(b_prev), _vp(chi),
+                                           ctypes.c_float(self.target_scale), _vp(q_prev),
+                                           _vp(q0)))
+        return q0
+
     # -- training -------------------------------------------------------------------
     def set_normalisation(self, feat_sample: np.ndarray, target_sample: np.ndarray):
         """Per-feature mean / inverse deviation and the target scale from a host sample."""

@@ -109,3 +109,16 @@ def test_trained_guess_beats_the_previous_step(walk):
     _, it_prev, _ = ctx.cpm_solve(b[test].contiguous(), prev.clone(), use_guess=True, tol=1e-6)
     _, it_mlp, _ = ctx.cpm_solve(b[test].contiguous(), q0.clone(), use_guess=True, tol=1e-6)
     assert it_mlp.mean() < it_prev.mean()
+
+
+def test_one_call_guess_equals_the_three_calls(walk):
+    ctx, work, b, qb = walk
+    chi = _dev(work.electrode.chi)
+    g = LearnedGuess(ctx, seed=5)
+    feat = g.features(b[1:9], b[0:8], chi)
+    g.set_normalisation(feat.reshape(-1, mlp.N_FEATURES).cpu().numpy(),
+                        (qb[1:9] - qb[0:8]).reshape(-1).cpu().numpy())
+    prev = qb[0:8].contiguous()
+    three = g.guess(feat, prev).reshape(prev.shape)
+    one = g.guess_frames(b[1:9].contiguous(), b[0:8].contiguous(), chi, prev)
+    assert torch.equal(one, three)
