@@ -104,6 +104,7 @@ struct Ctx {
   Buf turn;       // float4 [4096]: exp(2 pi i j / 4096) as float pairs (ion phasors)
   Buf shell_off;    // int64 [8n+1]: offsets of the (atom, shell 1..8) buckets in shell_members
   Buf shell_members;  // int32: members of the buckets (neighbours filed by shell)
+  Buf p_f32;          // float [nnz]: PCG-DC pattern values (Eq. 36) for the guess feature
   double zmean = 0;
   bool shells_ready = false;
 

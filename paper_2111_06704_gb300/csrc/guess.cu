@@ -25,9 +25,14 @@ constexpr int oW1 = 0, ob1 = oW1 + kH * kF, oW2 = ob1 + kH, ob2 = oW2 + kH * kH,
               oW3 = ob2 + kH, ob3 = oW3 + kH * kH, oW4 = ob3 + kH, ob4 = oW4 + kH;
 static_assert(ob4 + 1 == kP, "parameter layout");
 
-__device__ __forceinline__ float silu(float z) { return z / (1.0f + expf(-z)); }
+// SiLU and its derivative through the fast exponential and reciprocal (relative error
+// ~1e-6, far inside what a guess needs and what the oracle comparison allows): the
+// forward pass spends as many instructions on 192 activations per sample as on its
+// 10,497 multiply-adds otherwise.
+__device__ __forceinline__ float sigmoid(float z) { return __frcp_rn(1.0f + __expf(-z)); }
+__device__ __forceinline__ float silu(float z) { return z * sigmoid(z); }
 __device__ __forceinline__ float silu_grad(float z) {
-  const float s = 1.0f / (1.0f + expf(-z));
+  const float s = sigmoid(z);
   return s * (1.0f + z * (1.0f - s));
 }
 
@@ -55,6 +60,13 @@ __global__ void k_shell_codes(int n, const double* __restrict__ xyz, double lx, 
   }
 }
 
+__global__ void k_to_float(const double* __restrict__ v, int64_t len, double add,
+                           float* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = (float)(v[e] + add);
+}
+
 // The potentials of a frame as floats: (b - b_prev, b) per atom.
 __global__ void k_guess_prep(int64_t len, const double* __restrict__ b,
                              const double* __restrict__ b_prev, float2* __restrict__ out) {
@@ -67,43 +79,87 @@ __global__ void k_guess_prep(int64_t len, const double* __restrict__ b,
 // 1-8 its means over the neighbour shells k = 1..8, 9 b, 10-17 the shell means of b,
 // 18 chi, 19 the side of the electrode (+1 above the mean height), 20 (P Delta b) / k_e
 // with the PCG-DC preconditioner's pattern entries, 21-31 zero.
-__global__ void k_guess_features(int n, int frames, const float2* __restrict__ pot,
-                                 const double* __restrict__ chi,
-                                 const double* __restrict__ xyz, double zmean,
-                                 const int64_t* __restrict__ sh_off,
-                                 const int* __restrict__ sh_idx,
-                                 const int64_t* __restrict__ off, const int* __restrict__ idx,
-                                 const double* __restrict__ prow, double pgap,
-                                 float* __restrict__ feat) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int f = blockIdx.y;
-  if (i >= n || f >= frames) return;
-  const float2* pf = pot + (int64_t)f * n;
-  float* out = feat + ((int64_t)f * n + i) * kF;
-  const float2 self = pf[i];
+constexpr int kFeatFrames = 4;     // frames per thread: index loads shared by them
+constexpr int kFeatThreads = 128;  // atoms per block
+
+__global__ void __launch_bounds__(kFeatThreads)
+k_guess_features(int n, int frames, const float2* __restrict__ pot,
+                 const double* __restrict__ chi, const double* __restrict__ xyz, double zmean,
+                 const int64_t* __restrict__ sh_off, const int* __restrict__ sh_idx,
+                 const int64_t* __restrict__ off, const int* __restrict__ idx,
+                 const float* __restrict__ pf32, float* __restrict__ feat) {
+  constexpr int FB = kFeatFrames;
+  __shared__ float stage[kFeatThreads * (kF + 1)];
+  const int i0 = blockIdx.x * kFeatThreads;
+  const int i = i0 + threadIdx.x;
+  const int f0 = blockIdx.y * FB;
+  const bool live = i < n;
+  float sd[FB][8], sb[FB][8], pz[FB];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const int64_t e0 = sh_off[(int64_t)i * 8 + k], e1 = sh_off[(int64_t)i * 8 + k + 1];
-    float sd = 0.f, sb = 0.f;
-    for (int64_t e = e0; e < e1; ++e) {
-      const float2 v = pf[sh_idx[e]];
-      sd += v.x;
-      sb += v.y;
-    }
-    const float inv = e1 > e0 ? 1.0f / (float)(e1 - e0) : 0.f;
-    out[1 + k] = sd * inv;
-    out[10 + k] = sb * inv;
+  for (int u = 0; u < FB; ++u) {
+    pz[u] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sd[u][k] = sb[u][k] = 0.f;
   }
-  float pz = 0.f;
-  for (int64_t e = off[i]; e < off[i + 1]; ++e)
-    pz = fmaf((float)(prow[e] + pgap), pf[idx[e]].x, pz);
-  out[0] = self.x;
-  out[9] = self.y;
-  out[18] = (float)chi[i];
-  out[19] = xyz[3 * i + 2] > zmean ? 1.f : -1.f;
-  out[20] = pz * (float)(1.0 / kKe);
+  // a frame past the last reads frame 0 and is not written
+  const float2* pf[FB];
 #pragma unroll
-  for (int c = 21; c < kF; ++c) out[c] = 0.f;
+  for (int u = 0; u < FB; ++u) pf[u] = pot + (int64_t)(f0 + u < frames ? f0 + u : 0) * n;
+  int cnt[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) cnt[k] = 0;
+  if (live) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int64_t e0 = sh_off[(int64_t)i * 8 + k], e1 = sh_off[(int64_t)i * 8 + k + 1];
+      cnt[k] = (int)(e1 - e0);
+      for (int64_t e = e0; e < e1; ++e) {
+        const int j = sh_idx[e];
+#pragma unroll
+        for (int u = 0; u < FB; ++u) {
+          const float2 v = pf[u][j];
+          sd[u][k] += v.x;
+          sb[u][k] += v.y;
+        }
+      }
+    }
+    for (int64_t e = off[i]; e < off[i + 1]; ++e) {
+      const int j = idx[e];
+      const float w = pf32[e];
+#pragma unroll
+      for (int u = 0; u < FB; ++u) pz[u] = fmaf(w, pf[u][j].x, pz[u]);
+    }
+  }
+  const float chi_i = live ? (float)chi[i] : 0.f;
+  const float side = live && xyz[3 * i + 2] > zmean ? 1.f : -1.f;
+  const int na = min(kFeatThreads, n - i0);
+#pragma unroll
+  for (int u = 0; u < FB; ++u) {
+    if (f0 + u >= frames) break;  // uniform per block
+    float* row = stage + threadIdx.x * (kF + 1);
+    if (live) {
+      const float2 self = pf[u][i];
+      row[0] = self.x;
+      row[9] = self.y;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float inv = cnt[k] ? 1.0f / (float)cnt[k] : 0.f;
+        row[1 + k] = sd[u][k] * inv;
+        row[10 + k] = sb[u][k] * inv;
+      }
+      row[18] = chi_i;
+      row[19] = side;
+      row[20] = pz[u] * (float)(1.0 / kKe);
+#pragma unroll
+      for (int c = 21; c < kF; ++c) row[c] = 0.f;
+    }
+    __syncthreads();
+    // the block's atoms are consecutive: one contiguous, coalesced write per frame
+    float* dst = feat + ((int64_t)(f0 + u) * n + i0) * kF;
+    for (int e = threadIdx.x; e < na * kF; e += kFeatThreads)
+      dst[e] = stage[(e / kF) * (kF + 1) + e % kF];
+    __syncthreads();
+  }
 }
 
 __device__ void load_params(const float* __restrict__ params, float* w, int bf16) {
@@ -448,18 +504,23 @@ int features_async(cpm_ctx* c, int frames, const double* b, const double* b_prev
     if (!st) st = cuda_check(c, cudaMemcpy(c->shell_members.ptr, sj.data(), sj.size() * sizeof(int),
                                            cudaMemcpyHostToDevice), "shell members");
     if (st) return st;
+    // the preconditioner's pattern values (Eq. 36, p_gap taken back out) as floats
+    if ((st = buf_alloc(c, &c->p_f32, std::max<int64_t>(c->nnz, 1) * sizeof(float)))) return st;
+    (k_to_float<<<256, 256, 0, c->stream>>>((const double*)c->prow.ptr, c->nnz, c->pgap,
+                                           (float*)c->p_f32.ptr), note_launch());
+    if ((st = cuda_check(c, cudaGetLastError(), "P float"))) return st;
     c->shells_ready = true;
   }
   const int64_t len = (int64_t)frames * n;
   if ((st = buf_reserve(c, &c->ws_guess, len * sizeof(float2)))) return st;
   (k_guess_prep<<<(int)std::min<int64_t>((len + 255) / 256, 8192), 256, 0, c->stream>>>(
        len, b, b_prev, (float2*)c->ws_guess.ptr), note_launch());
-  dim3 grid((n + 127) / 128, frames);
-  (k_guess_features<<<grid, 128, 0, c->stream>>>(
+  dim3 grid((n + kFeatThreads - 1) / kFeatThreads, (frames + kFeatFrames - 1) / kFeatFrames);
+  (k_guess_features<<<grid, kFeatThreads, 0, c->stream>>>(
        n, frames, (const float2*)c->ws_guess.ptr, chi, (const double*)c->xyz.ptr, c->zmean,
        (const int64_t*)c->shell_off.ptr, (const int*)c->shell_members.ptr,
        (const int64_t*)c->nbr_off.ptr, (const int*)c->nbr_idx.ptr,
-       (const double*)c->prow.ptr, c->pgap, feat), note_launch());
+       (const float*)c->p_f32.ptr, feat), note_launch());
   return cuda_check(c, cudaGetLastError(), "features");
 }
 
