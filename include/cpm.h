@@ -254,6 +254,8 @@ typedef struct cpm_info_t {
   int tc_blocks[3];   /* BF16X6 builds: 64-column K-blocks of the tensor-core tail taking
                          six, three and one BF16 products (weight-bounded schedule) */
   double t_head_ms;   /* BF16X6 builds: device time of the FP64-accurate head kernel */
+  double t_tc_light_ms; /* BF16X6 builds with a resident operand: the part of t_tc_ms spent
+                           on the three- and one-product K-blocks */
 } cpm_info_t;
 
 int cpm_get_info(cpm_ctx* c, cpm_info_t* out);

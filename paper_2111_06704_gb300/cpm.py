@@ -77,6 +77,7 @@ class cpm_info_t(ctypes.Structure):
         ("t_matvec_ms", ctypes.c_double),
         ("tc_blocks", ctypes.c_int * 3),
         ("t_head_ms", ctypes.c_double),
+        ("t_tc_light_ms", ctypes.c_double),
     ]
 
 

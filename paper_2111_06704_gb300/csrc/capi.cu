@@ -234,6 +234,7 @@ int cpm_create(cpm_ctx** out, const cpm_params* p) {
   c->stream = (cudaStream_t)p->stream;
   cudaEventCreate(&c->ev_tc[0]);
   cudaEventCreate(&c->ev_tc[1]);
+  cudaEventCreate(&c->ev_tc[2]);
   if (cudaGetDevice(&c->device) != cudaSuccess) {
     cudaGetLastError();
     delete c;
@@ -249,6 +250,7 @@ int cpm_destroy(cpm_ctx* c) {
   free_build(c);
   cudaEventDestroy(c->ev_tc[0]);
   cudaEventDestroy(c->ev_tc[1]);
+  cudaEventDestroy(c->ev_tc[2]);
   Buf* ws[] = {&c->ws_solve, &c->ws_in0, &c->ws_in1, &c->ws_in2, &c->ws_out0, &c->ws_out1,
                &c->ws_pot, &c->ws_guess, &c->ws_feat};
   for (Buf* b : ws) buf_free(c, b);
@@ -277,6 +279,8 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
   hkl.resize(3 * (size_t)c->mpad, 0);
   std::vector<double> sqw(c->mpad, 0.0);
   for (int k = 0; k < c->m; ++k) sqw[k] = sqrt(w[k]);
+  c->kw.assign(c->mpad, 0.0);
+  std::copy(w.begin(), w.end(), c->kw.begin());
   // Accumulation schedule of the float k-space GEMM.  k-step s covers 16 operand
   // columns: block s / 8 holds 64 k-vectors as [cos | sin], so its steps 0-3 and 4-7
   // carry the same weights.  Leading blocks whose steps carry more than 2e-3 of weight
@@ -349,9 +353,14 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
     int kb3 = nkb;
     double tw = 0.0;
     while (kb3 > kb0 && (tw + bw[kb3 - 1]) * 0x1p-7 <= budget) tw += bw[--kb3];
+    kb3 = std::min(nkb, (kb3 + 1) & ~1);  // even: see below
     int kb6 = kb3;
     tw = 0.0;
     while (kb6 > kb0 && (tw + bw[kb6 - 1]) * 3 * 0x1p-16 <= budget) tw += bw[--kb6];
+    // both ends even (whole [cos | sin] pairs in each region, one more block with more
+    // products at most): the 256 x 256 tile kernels take their launch ranges at even
+    // K-blocks and read plane 2 over the whole six-product range
+    kb6 = std::min(kb3, (kb6 + 1) & ~1);
     c->kb6_end = kb6;
     c->kb3_end = kb3;
   }
@@ -467,7 +476,8 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
                         2 * (int64_t)(kend - kbeg), kbeg / 32, n,
                         std::max(c->heavy_steps / 4, kbeg / 32), kend / 32, c->kb6_end,
                         c->kb3_end, (const uint32_t*)c->chunk_end.ptr, (double*)ehead.ptr,
-                        c->ldE, last ? (float*)c->E.ptr : nullptr, c->ldE, (int*)errbuf.ptr, s);
+                        c->ldE, last ? (float*)c->E.ptr : nullptr, c->ldE, (int*)errbuf.ptr,
+                        c->kw.data(), c->streamed ? nullptr : c->ev_tc[2], s);
     }
     cudaEventRecord(c->ev_tc[1], s);
     int herr = 0;
@@ -477,6 +487,8 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
     if (!st && herr) st = set_err(c, CPM_ECUDA, "tensor-core k-space kernel: a pipeline wait timed out");
     if (!st) cudaEventElapsedTime(&c->t_tc_ms, c->ev_tc[0], c->ev_tc[1]);
     if (!st) cudaEventElapsedTime(&c->t_head_ms, ev_head, c->ev_tc[0]);
+    c->t_light_ms = 0;
+    if (!st && !c->streamed) cudaEventElapsedTime(&c->t_light_ms, c->ev_tc[2], c->ev_tc[1]);
     cudaEventDestroy(ev_head);
     free_tc();
   } else {
@@ -781,6 +793,7 @@ int cpm_get_info(cpm_ctx* c, cpm_info_t* out) {
   out->tc_blocks[1] = tc ? c->kb3_end - c->kb6_end : 0;
   out->tc_blocks[2] = tc ? kbn - c->kb3_end : 0;
   out->t_head_ms = c->t_head_ms;
+  out->t_tc_light_ms = c->t_light_ms;
   out->d_iters = c->d_iters;
   out->launches = launch_count();
   return CPM_OK;

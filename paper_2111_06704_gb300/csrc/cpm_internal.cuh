@@ -114,12 +114,14 @@ struct Ctx {
 
   // scratch (grown on demand, never shrunk)
   std::vector<Buf*> scratch;
+  std::vector<double> kw;  // k-vector weights W_K of the sorted table, mpad entries (0 past m)
   Buf ws_solve, ws_in0, ws_in1, ws_in2, ws_out0, ws_out1, ws_pot, ws_guess, ws_feat;
 
   float t_kspace_ms = 0, t_phase_ms = 0, t_precond_ms = 0, t_dsolve_ms = 0, t_tc_ms = 0;
   float t_matvec_ms = 0;  // last cpm_apply_E: the matvec launches alone
   float t_head_ms = 0;    // FP64-accurate head of the tensor-core build
-  cudaEvent_t ev_tc[2] = {nullptr, nullptr};
+  float t_light_ms = 0;   // tensor-core tail: the three- and one-product K-blocks
+  cudaEvent_t ev_tc[3] = {nullptr, nullptr, nullptr};
 
   bool fp64() const { return p.precision == CPM_PREC_FP64; }
   size_t esz() const { return fp64() ? 8 : 4; }
@@ -162,7 +164,7 @@ int launch_ek_head_f64(const double* Ahead, int kh, int ktot, int npad, float* h
 int launch_ek_tc(const void* p0, const void* p1, const void* p2, int npad, int64_t plane_cols,
                  int kb_col0, int n, int kb_begin, int kb_end, int kb6_end, int kb3_end,
                  const uint32_t* chunk_end, double* head, int64_t ldh, float* E, int64_t ldE,
-                 int* err, cudaStream_t s);
+                 int* err, const double* kw, cudaEvent_t mid, cudaStream_t s);
 void launch_extract_diag(bool fp64, const void* E, int n, int64_t ldE, double* diag,
                          cudaStream_t s);
 void launch_get_E(bool fp64, const void* E, int n, int64_t ldE, const double* xyz,

@@ -29,6 +29,9 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 #include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
 #include <stdlib.h>
 
 #include "cpm_internal.cuh"
@@ -198,6 +201,8 @@ struct TcArgs {
   float* E;
   int64_t ldE;
   int* err;
+  int diag_exact;  // the diagonal takes w_diag in place of its accumulated sum
+  double w_diag;   // sum of W_K over the launch's k-vectors (cos^2 + sin^2 = 1)
 };
 
 // Sub-blocks (of BK columns) held by the ring stage that starts at relative sub-block sb,
@@ -405,7 +410,10 @@ k_ek_tc(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtens
               const int j = j0 + cg * 32 + t;
               if (j < args.n && j <= row) {
                 double* hp = args.head + (int64_t)row * args.ldh + j;
-                const double v = (double)__uint_as_float(hi[t]) + (double)__uint_as_float(lo[t]) + *hp;
+                const double tail = args.diag_exact && j == row
+                                        ? args.w_diag
+                                        : (double)__uint_as_float(hi[t]) + (double)__uint_as_float(lo[t]);
+                const double v = tail + *hp;
                 if (args.E) args.E[(int64_t)row * args.ldE + j] = (float)v;
                 else *hp = v;  // a K-window of a streamed build: carry the sum in FP64
               }
@@ -422,6 +430,296 @@ k_ek_tc(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtens
       if (lane == 0) mbar_arrive(&acc_empty[buf]);
       ++chunk;
       kb = kb_last + 1;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem)
+                 : "memory");
+  }
+}
+
+// ---- 256 x 256 tiles, FP32 accumulation ----------------------------------------------
+//
+// The whole of TMEM holds one 256 x 256 output tile: two M = 128, N = 256 accumulators
+// (rows i0 .. i0 + 127 and i0 + 128 .. i0 + 255).  Twice the tile edge of k_ek_tc halves
+// the operand bytes per MMA, which is what limits these stages; the price is that no TMEM
+// is left for a second accumulator or hi/lo pairs.
+//   SIX = false: three-product stages (32 columns of planes 0 and 1 for 256 rows and 256
+//     columns, 64 KB, 12 MMAs of 128 x 256 x 16) then one-product stages (64 columns of
+//     plane 0, 64 KB, 8 MMAs); three 64 KB stages in flight.  The summed weight of these
+//     K-blocks is small (each reduced group's weight times its product bound stays below
+//     1e-8): one FP32 accumulation over the launch.
+//   SIX = true: six-product stages (32 columns of planes 0-2, 96 KB, 24 MMAs); two stages.
+//     FP32 accumulation error grows with the terms added and their size (the tensor-core
+//     adds lose ~0.1 ulp on average, not centred), so after each accumulation chunk of
+//     the host's schedule the MMAs pause while the epilogue adds the accumulator into the
+//     FP64 head in global memory.
+// Off the diagonal the k-space terms oscillate in sign; the diagonal, where every term is
+// positive, takes the exact FP64 weight sum instead (range_weight).  Eight epilogue
+// warps: TMEM lane quarter warp % 4, column half (warp - 2) / 4.
+constexpr int kStripTile = 256;
+constexpr int kStripThreads = 320;  // 10 warps: TMA, MMA, 8 epilogue
+constexpr uint32_t kIdescN256 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(256 >> 3) << 17) |
+                                ((uint32_t)(kTile >> 4) << 24);
+
+template <bool SIX>
+struct StripCfg {
+  static constexpr int kStages = SIX ? 2 : 3;
+  static constexpr int kStageBytes = (SIX ? 96 : 64) * 1024;
+  static constexpr int kPlanes = SIX ? 3 : 2;   // planes of a narrow (32-column) stage
+  static constexpr int kProds = SIX ? 6 : 3;    // BF16 products of a narrow stage
+};
+
+__device__ __forceinline__ void mma_bf16_id(uint32_t d_tmem, uint64_t a, uint64_t b,
+                                            uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+struct StripArgs {
+  int n, npad;
+  int kb_begin;   // first K-block
+  int kb_end;     // one past the last K-block
+  int kb3_end;    // SIX = false: K-blocks before this take three products, the rest one
+  int kb_col0;    // the operand planes start at this K-block
+  const uint32_t* chunk_end;  // SIX: bit per K-block, an accumulation chunk ends after it
+  double* head;   // [n][ldh] FP64 head + everything before kb_begin (lower triangle)
+  int64_t ldh;
+  float* E;       // float E, or null: the sum goes back into head (FP64)
+  int64_t ldE;
+  int* err;
+  int diag_exact;  // the diagonal takes w_diag in place of its accumulated sum
+  double w_diag;   // sum of W_K over the launch's k-vectors
+};
+
+// One epilogue thread's 32 accumulator values (row `row`, columns jb .. jb + 31) into the
+// FP64 head: the head segment is loaded whole before any store (16-byte vectors where
+// the segment lies below the diagonal and inside n), then either head += acc (a chunk
+// before the last) or tail + head goes to float E, or back to head without E.  The
+// diagonal entry takes the exact weight sum (nothing on intermediate chunks).
+__device__ __forceinline__ void strip_group(const StripArgs& a, const uint32_t (&acc)[32], int row,
+                                            int jb, bool final_chunk) {
+  const int jmax = min(a.n - 1, row);
+  if (jb > jmax) return;
+  double* hp = a.head + (int64_t)row * a.ldh + jb;
+  const bool full = jb + 31 <= jmax;
+  double hv[32];
+  if (full) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const double2 x = reinterpret_cast<const double2*>(hp)[u];
+      hv[2 * u] = x.x;
+      hv[2 * u + 1] = x.y;
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < 32; ++t) hv[t] = jb + t <= jmax ? hp[t] : 0.0;
+  }
+#pragma unroll
+  for (int t = 0; t < 32; ++t) {
+    const bool exact = a.diag_exact && jb + t == row;
+    if (exact) hv[t] += final_chunk ? a.w_diag : 0.0;
+    else hv[t] += (double)__uint_as_float(acc[t]);
+  }
+  if (final_chunk && a.E) {
+    float* ep = a.E + (int64_t)row * a.ldE + jb;
+    if (full) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        reinterpret_cast<float4*>(ep)[u] = make_float4((float)hv[4 * u], (float)hv[4 * u + 1],
+                                                       (float)hv[4 * u + 2], (float)hv[4 * u + 3]);
+    } else {
+#pragma unroll
+      for (int t = 0; t < 32; ++t)
+        if (jb + t <= jmax) ep[t] = (float)hv[t];
+    }
+  } else if (full) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+      reinterpret_cast<double2*>(hp)[u] = make_double2(hv[2 * u], hv[2 * u + 1]);
+  } else {
+#pragma unroll
+    for (int t = 0; t < 32; ++t)
+      if (jb + t <= jmax) hp[t] = hv[t];
+  }
+}
+
+template <bool SIX>
+__global__ void __launch_bounds__(kStripThreads, 1)
+k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CUtensorMap map0n,
+           const __grid_constant__ CUtensorMap map1n, const __grid_constant__ CUtensorMap map2n,
+           StripArgs args) {
+  // map0w: plane 0 in 128 x 64 boxes (128-byte swizzle); map0n / map1n / map2n: planes
+  // 0-2 in 128 x 32 boxes (64-byte swizzle)
+  using Cfg = StripCfg<SIX>;
+  constexpr int kStages = Cfg::kStages, kStageBytes = Cfg::kStageBytes;
+  constexpr int P = Cfg::kPlanes;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* ring = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages];
+  __shared__ __align__(8) uint64_t acc_full, acc_empty;
+  __shared__ uint32_t tmem_base_s;
+  constexpr int kNarrow = kTile * 32 * 2, kWide = kTile * 64 * 2;  // 8 KB and 16 KB tiles
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int I, J;
+  tri_tile(blockIdx.x, I, J);
+  const int i0 = I * kStripTile, j0 = J * kStripTile;
+  const bool diag = I == J;
+  // row and column halves inside the padded operand (npad is a multiple of 128)
+  const int rb = i0 + kTile < args.npad ? 2 : 1, cb = j0 + kTile < args.npad ? 2 : 1;
+  // narrow stages (two per K-block) then wide ones (one per one-product K-block)
+  const int nnarrow =
+      2 * (SIX ? args.kb_end - args.kb_begin
+               : max(0, min(args.kb_end, args.kb3_end) - args.kb_begin));
+  const int kb1 = max(args.kb_begin, args.kb3_end);
+  const int nst = nnarrow + (SIX ? 0 : max(0, args.kb_end - kb1));
+  // an accumulation chunk ends with stage t: the last stage, or (SIX) the second half of a
+  // K-block whose chunk bit is set
+  auto chunk_ends = [&](int t) {
+    if (t + 1 == nst) return true;
+    if (!SIX || !(t & 1)) return false;
+    const int g = args.kb_begin + t / 2;
+    return ((args.chunk_end[g >> 5] >> (g & 31)) & 1u) != 0u;
+  };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&acc_full, 1);
+    mbar_init(&acc_empty, 8);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                     smem_addr(&tmem_base_s))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_s;
+
+  if (warp == 0) {
+    // ---- TMA producer ------------------------------------------------------------
+    if (lane == 0) {
+      for (int t = 0; t < nst; ++t) {
+        const int s = t % kStages;
+        if (!mbar_wait(&empty_bar[s], ((t / kStages) & 1) ^ 1, args.err, 11)) break;
+        uint8_t* st = ring + s * kStageBytes;
+        if (t < nnarrow) {
+          // 32 columns of planes 0 .. P-1: A plane p half r at slot 2p + r, B plane p half
+          // c at slot 2P + 2p + c (the two B halves adjacent: one N = 256 operand)
+          const int x = (args.kb_begin - args.kb_col0) * kBlockK + t * 32;
+          mbar_expect_tx(&full_bar[s], P * (rb + cb) * kNarrow);
+#pragma unroll
+          for (int p = 0; p < P; ++p) {
+            const CUtensorMap* mp = p == 0 ? &map0n : p == 1 ? &map1n : &map2n;
+            for (int r = 0; r < rb; ++r)
+              tma_load_2d(st + (2 * p + r) * kNarrow, mp, &full_bar[s], x, i0 + r * kTile);
+            for (int c = 0; c < cb; ++c)
+              tma_load_2d(st + (2 * P + 2 * p + c) * kNarrow, mp, &full_bar[s], x,
+                          j0 + c * kTile);
+          }
+        } else {
+          // 64 columns of plane 0: A half r at r x 16 KB, B halves at 32 KB and 48 KB
+          const int x = (kb1 - args.kb_col0 + (t - nnarrow)) * kBlockK;
+          mbar_expect_tx(&full_bar[s], (rb + cb) * kWide);
+          for (int r = 0; r < rb; ++r)
+            tma_load_2d(st + r * kWide, &map0w, &full_bar[s], x, i0 + r * kTile);
+          for (int c = 0; c < cb; ++c)
+            tma_load_2d(st + 2 * kWide + c * kWide, &map0w, &full_bar[s], x, j0 + c * kTile);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer ----------------------------------------------------------------
+    if (lane == 0) {
+      // products (p, q) with p + q <= 2 in the order (0,0) (0,1) (1,0) (0,2) (1,1) (2,0):
+      // A plane p, B plane q; the three-product form is the first three
+      constexpr uint32_t kPa = 0x210100u, kPb = 0x012010u;
+      // on a diagonal tile the first row half needs only the first 128 columns
+      const uint32_t id0 = diag ? kIdesc : kIdescN256;
+      bool ok = true;
+      bool first = true;  // first stage of an accumulation chunk
+      int chunk = 0;
+      for (int t = 0; t < nst && ok; ++t) {
+        const int s = t % kStages;
+        ok = mbar_wait(&full_bar[s], (t / kStages) & 1, args.err, 13);
+        if (!ok) break;
+        if (first && chunk > 0) {  // the epilogue has read the previous chunk
+          ok = mbar_wait(&acc_empty, (chunk - 1) & 1, args.err, 12);
+          if (!ok) break;
+        }
+        tc_fence_after();
+        const uint32_t st = smem_addr(ring + s * kStageBytes);
+        if (t < nnarrow) {
+#pragma unroll
+          for (int ks = 0; ks < 2; ++ks)
+            for (int r = 0; r < rb; ++r)
+#pragma unroll
+              for (int p = 0; p < Cfg::kProds; ++p) {
+                const int pa = (kPa >> (4 * p)) & 15, pb = (kPb >> (4 * p)) & 15;
+                const uint64_t da = smem_desc<32>(st + (2 * pa + r) * kNarrow + ks * 32);
+                const uint64_t db = smem_desc<32>(st + (2 * P + 2 * pb) * kNarrow + ks * 32);
+                mma_bf16_id(tmem + (uint32_t)(r * 256), da, db, r == 0 ? id0 : kIdescN256,
+                            (first && ks == 0 && p == 0) ? 0u : 1u);
+              }
+        } else {
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks)
+            for (int r = 0; r < rb; ++r) {
+              const uint64_t da = smem_desc<64>(st + r * kWide + ks * 32);
+              const uint64_t db = smem_desc<64>(st + 2 * kWide + ks * 32);
+              mma_bf16_id(tmem + (uint32_t)(r * 256), da, db, r == 0 ? id0 : kIdescN256,
+                          (first && ks == 0) ? 0u : 1u);
+            }
+        }
+        first = false;
+        mma_commit(&empty_bar[s]);  // frees the stage once these MMAs have read it
+        if (chunk_ends(t)) {
+          mma_commit(&acc_full);
+          ++chunk;
+          first = true;
+        }
+      }
+    }
+  } else {
+    // ---- epilogue: warps 2-9, TMEM lane quarter q = warp % 4, column half h ---------
+    const int q = warp & 3, h = (warp - 2) >> 2;
+    const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+    int chunk = 0;
+    for (int t0 = 0; t0 < nst;) {
+      int t1 = t0;
+      while (!chunk_ends(t1)) ++t1;
+      const bool final_chunk = t1 + 1 == nst;
+      if (!mbar_wait(&acc_full, chunk & 1, args.err, 14)) break;
+      tc_fence_after();
+      for (int r = 0; r < rb; ++r) {
+        const int row = i0 + r * kTile + 32 * q + lane;
+#pragma unroll 1
+        for (int cg = 4 * h; cg < 4 * h + 4; ++cg) {
+          if (diag && r == 0 && cg >= kTile / 32) break;  // above the diagonal
+          if (j0 + cg * 32 >= args.n) break;
+          uint32_t acc[32];
+          TMEM_LD32(tmem + lane_base + (uint32_t)(r * 256 + cg * 32), acc);
+          tmem_wait_ld();
+          if (row < args.n) strip_group(args, acc, row, j0 + cg * 32, final_chunk);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty);
+      ++chunk;
+      t0 = t1 + 1;
     }
   }
   tc_fence_before();
@@ -467,51 +765,122 @@ bool make_map(CUtensorMap* m, const void* base, int rows, int64_t cols, int bk) 
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Diagonal of the K-blocks [kb0, kb1): every k-vector adds W_K (cos^2 + sin^2) to E_ii,
+// so where the range holds whole [cos | sin] pairs (both ends even: K-block b is the cos
+// or sin half of k-vectors 64 (b / 2) ..) the diagonal is their summed weight, exact in
+// FP64, instead of an FP32 tensor-core sum of same-sign terms, whose rounding errors add
+// up (measured ~1e-7 too low at 12,800 atoms).  Returns 0 where an end is odd.
+int range_weight(const double* kw, int kb0, int kb1, double* w) {
+  *w = 0.0;
+  if (!kw || (kb0 & 1) || (kb1 & 1)) return 0;
+  double s = 0.0, comp = 0.0;  // Neumaier-compensated sum
+  for (int k = 32 * kb0; k < 32 * kb1; ++k) {
+    const double t = s + kw[k];
+    comp += std::fabs(s) >= std::fabs(kw[k]) ? (s - t) + kw[k] : (kw[k] - t) + s;
+    s = t;
+  }
+  *w = s + comp;
+  return 1;
+}
+
 }  // namespace
 
 // K-blocks [kb_begin, kb_end) of the lower triangle from BF16 planes holding the K-blocks
 // kb_col0 .. kb_col0 + plane_cols / 64; the result plus head goes to float E, or back into
-// head (FP64) when E is null.
+// head (FP64) when E is null.  Two launches, the first adding its K-range to head and the
+// second writing E: the six-product K-blocks, then the three- and one-product ones, both
+// on 256 x 256 tiles (k_ek_strip).  CPM_TC_STRIP=0 in the environment runs the whole range
+// on 128 x 128 tiles with TMEM two-sum drains instead (k_ek_tc).  `mid`, when given, is
+// recorded before the light launch.
 int launch_ek_tc(const void* p0, const void* p1, const void* p2, int npad, int64_t plane_cols,
                  int kb_col0, int n, int kb_begin, int kb_end, int kb6_end, int kb3_end,
                  const uint32_t* chunk_end, double* head, int64_t ldh, float* E, int64_t ldE,
-                 int* err, cudaStream_t s) {
+                 int* err, const double* kw, cudaEvent_t mid, cudaStream_t s) {
   const char* env = getenv("CPM_TC_BK");
   const int bk = env && atoi(env) == 32 ? 32 : 64;
-  CUtensorMap m0, m1, m2;
+  const char* env_strip = getenv("CPM_TC_STRIP");
+  const bool strip = !(env_strip && atoi(env_strip) == 0);
+  CUtensorMap m0, m1, m2, m0n, m1n, m2n;
   if (!make_map(&m0, p0, npad, plane_cols, bk) || !make_map(&m1, p1, npad, plane_cols, bk) ||
-      !make_map(&m2, p2, npad, plane_cols, bk))
+      !make_map(&m2, p2, npad, plane_cols, bk) || !make_map(&m0n, p0, npad, plane_cols, 32) ||
+      !make_map(&m1n, p1, npad, plane_cols, 32) || !make_map(&m2n, p2, npad, plane_cols, 32))
     return CPM_ECUDA;
-  TcArgs a;
-  a.n = n;
-  a.kb_begin = kb_begin;
-  a.kb_end = kb_end;
-  a.kb6_end = kb6_end;
-  a.kb3_end = kb3_end;
-  a.kb_col0 = kb_col0;
-  a.chunk_end = chunk_end;
-  a.head = head;
-  a.ldh = ldh;
-  a.E = E;
-  a.ldE = ldE;
-  a.err = err;
-  const int nt = (n + kTile - 1) / kTile;
-  const int tiles = nt * (nt + 1) / 2;
   const int smem = kRingBytes + 1024;
+  const int smem6 = StripCfg<true>::kStages * StripCfg<true>::kStageBytes + 1024;
+  const int smem31 = StripCfg<false>::kStages * StripCfg<false>::kStageBytes + 1024;
   if (cudaFuncSetAttribute(k_ek_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
           cudaSuccess ||
       cudaFuncSetAttribute(k_ek_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-          cudaSuccess)
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_ek_strip<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           smem6) != cudaSuccess ||
+      cudaFuncSetAttribute(k_ek_strip<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           smem31) != cudaSuccess)
     return CPM_ECUDA;
-  if (a.kb_begin >= a.kb_end) {  // nothing of the tail in this window
-    if (E)
-      (k_head_to_float<<<dim3((n + 31) / 32, (n + 31) / 32), dim3(32, 8), 0, s>>>(head, ldh, E,
-                                                                              ldE, n),
-       note_launch());
-    return cudaGetLastError() == cudaSuccess ? CPM_OK : CPM_ECUDA;
+  // segments: kind 0 = k_ek_tc, 1 = six-product 256-tiles, 2 = light 256-tiles; the
+  // boundary is kept even so that each segment holds whole [cos | sin] block pairs
+  struct Seg {
+    int kind, b, e;
+  };
+  Seg seg[2];
+  int nseg = 0;
+  const int x6_end = strip ? std::min(kb_end, (kb6_end + 1) & ~1) : kb_end;
+  if (kb_begin < x6_end) seg[nseg++] = {strip ? 1 : 0, kb_begin, x6_end};
+  const int s_begin = std::max(kb_begin, x6_end);
+  const int first_light = nseg;
+  if (s_begin < kb_end) seg[nseg++] = {2, s_begin, kb_end};
+  for (int q = 0; q < nseg; ++q) {
+    float* Eq = q + 1 == nseg ? E : nullptr;
+    if (q == first_light && mid) cudaEventRecord(mid, s);
+    if (seg[q].kind == 0) {
+      TcArgs a;
+      a.n = n;
+      a.kb_begin = seg[q].b;
+      a.kb_end = seg[q].e;
+      a.kb6_end = kb6_end;
+      a.kb3_end = kb3_end;
+      a.kb_col0 = kb_col0;
+      a.chunk_end = chunk_end;
+      a.head = head;
+      a.ldh = ldh;
+      a.E = Eq;
+      a.ldE = ldE;
+      a.err = err;
+      a.diag_exact = range_weight(kw, seg[q].b, seg[q].e, &a.w_diag);
+      const int nt = (n + kTile - 1) / kTile;
+      const int tiles = nt * (nt + 1) / 2;
+      if (bk == 32) (k_ek_tc<32><<<tiles, kThreads, smem, s>>>(m0, m1, m2, a), note_launch());
+      else (k_ek_tc<64><<<tiles, kThreads, smem, s>>>(m0, m1, m2, a), note_launch());
+    } else {
+      StripArgs a;
+      a.n = n;
+      a.npad = npad;
+      a.kb_begin = seg[q].b;
+      a.kb_end = seg[q].e;
+      a.kb3_end = kb3_end;
+      a.kb_col0 = kb_col0;
+      a.chunk_end = chunk_end;
+      a.head = head;
+      a.ldh = ldh;
+      a.E = Eq;
+      a.ldE = ldE;
+      a.err = err;
+      a.diag_exact = range_weight(kw, seg[q].b, seg[q].e, &a.w_diag);
+      const int nt = (n + kStripTile - 1) / kStripTile;
+      const int tiles = nt * (nt + 1) / 2;
+      if (seg[q].kind == 1)
+        (k_ek_strip<true><<<tiles, kStripThreads, smem6, s>>>(m0, m0n, m1n, m2n, a),
+         note_launch());
+      else
+        (k_ek_strip<false><<<tiles, kStripThreads, smem31, s>>>(m0, m0n, m1n, m2n, a),
+         note_launch());
+    }
   }
-  if (bk == 32) (k_ek_tc<32><<<tiles, kThreads, smem, s>>>(m0, m1, m2, a), note_launch());
-  else (k_ek_tc<64><<<tiles, kThreads, smem, s>>>(m0, m1, m2, a), note_launch());
+  if (first_light == nseg && mid) cudaEventRecord(mid, s);
+  if (nseg == 0 && E)  // nothing of the tail in this window
+    (k_head_to_float<<<dim3((n + 31) / 32, (n + 31) / 32), dim3(32, 8), 0, s>>>(head, ldh, E,
+                                                                              ldE, n),
+     note_launch());
   return cudaGetLastError() == cudaSuccess ? CPM_OK : CPM_ECUDA;
 }
 
