@@ -361,8 +361,8 @@ def run_ours(args, rank, world, local_rank):
         roof = {"bound": "tensor", "achieved": algo_flops / (tc_ms * 1e-3) / 1e12,
                 "peak": bf16_peak, "unit": "TFLOP/s",
                 "kernel": "k_ek_strip<true> + k_ek_strip<false> (tcgen05 split-BF16 k-space "
-                          "GEMM on 256 x 256 tiles: six-product K-blocks with FP64 chunk drains, "
-                          "then three- and one-product K-blocks)",
+                          "GEMM on 256 x 256 tiles: six-product K-blocks with two-sum chunk drains "
+                          "into per-SM hi/lo scratch, then three- and one-product K-blocks)",
                 "peak_source": f"{src} bf16_tflops (burst)",
                 "issued_tflops": tc_flops / (tc_ms * 1e-3) / 1e12,
                 "fp32_accurate_tflops": 2.0 * (n * (n + 1) / 2) * tail_cols / (tc_ms * 1e-3) / 1e12,

@@ -324,7 +324,8 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
     int len = 0;
     // chunks of up to 5e-3 of weight or 32 K-blocks: the FP32 accumulation error of a
     // chunk stays near 6e-8 x 5e-3 x sqrt(768 terms) ~ 1e-8 (measured: E unchanged at the
-    // 512-atom cell against 5e-4 / 8, 6% faster at 12,800 atoms; at 1e-2 / 64 E degrades)
+    // 512-atom cell against 5e-4 / 8, 6% faster at 12,800 atoms; at 1e-2 / 64 E degrades;
+    // at 3,200 atoms 2e-2 / 32 already doubles the off-diagonal RMS error, 3.9e-9 -> 9.7e-9)
     const double wmax = 5e-3;
     const int bmax = 32;
     for (int b = c->heavy_steps / 4; b < nkb; ++b) {
@@ -408,8 +409,10 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
   cudaEventRecord(ev[0], s);
   launch_fixed_point_coords((const double*)c->xyz.ptr, n, c->npad, c->p.box,
                             (uint32_t*)c->sfix.ptr, s);
-  Buf planes[3], ehead, errbuf, hsplit;
+  Buf planes[3], ehead, errbuf, hsplit, tcscratch;
+  int sms = 0;  // SM slots of the tensor-core scratch (%nsmid)
   auto free_tc = [&]() {
+    buf_free(c, &tcscratch);
     for (Buf& b : planes) buf_free(c, &b);
     buf_free(c, &ehead);
     buf_free(c, &errbuf);
@@ -430,6 +433,12 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
         (st = buf_alloc(c, &planes[2], pbytes)) ||
         (st = buf_alloc(c, &ehead, (size_t)n * c->ldE * sizeof(double))) ||
         (st = buf_alloc(c, &errbuf, sizeof(int))) ||
+        (launch_nsmid((int*)errbuf.ptr, s),
+         st = cuda_check(c, cudaMemcpyAsync(&sms, errbuf.ptr, sizeof(int), cudaMemcpyDeviceToHost, s),
+                         "nsmid")) ||
+        (st = cuda_check(c, cudaStreamSynchronize(s), "nsmid sync")) ||
+        (sms = std::max(1, std::min(sms, 4096)),
+         st = buf_alloc(c, &tcscratch, (size_t)sms * ek_strip_scratch_floats() * sizeof(float))) ||
         (st = buf_alloc(c, &hsplit, 2 * (size_t)c->npad * std::max(head_cols, 16) * sizeof(float))) ||
         (st = cuda_check(c, cudaMemsetAsync(errbuf.ptr, 0, sizeof(int), s), "err flag"))) {
       free_tc();
@@ -477,7 +486,8 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
                         std::max(c->heavy_steps / 4, kbeg / 32), kend / 32, c->kb6_end,
                         c->kb3_end, (const uint32_t*)c->chunk_end.ptr, (double*)ehead.ptr,
                         c->ldE, last ? (float*)c->E.ptr : nullptr, c->ldE, (int*)errbuf.ptr,
-                        c->kw.data(), c->streamed ? nullptr : c->ev_tc[2], s);
+                        c->kw.data(), (float*)tcscratch.ptr, sms,
+                        c->streamed ? nullptr : c->ev_tc[2], s);
     }
     cudaEventRecord(c->ev_tc[1], s);
     int herr = 0;

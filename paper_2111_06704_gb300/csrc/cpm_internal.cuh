@@ -164,7 +164,10 @@ int launch_ek_head_f64(const double* Ahead, int kh, int ktot, int npad, float* h
 int launch_ek_tc(const void* p0, const void* p1, const void* p2, int npad, int64_t plane_cols,
                  int kb_col0, int n, int kb_begin, int kb_end, int kb6_end, int kb3_end,
                  const uint32_t* chunk_end, double* head, int64_t ldh, float* E, int64_t ldE,
-                 int* err, const double* kw, cudaEvent_t mid, cudaStream_t s);
+                 int* err, const double* kw, float* scratch, int scratch_slots, cudaEvent_t mid,
+                 cudaStream_t s);
+int64_t ek_strip_scratch_floats();  // per SM slot of the 256 x 256 tile kernels
+void launch_nsmid(int* d_out, cudaStream_t s);
 void launch_extract_diag(bool fp64, const void* E, int n, int64_t ldE, double* diag,
                          cudaStream_t s);
 void launch_get_E(bool fp64, const void* E, int n, int64_t ldE, const double* xyz,

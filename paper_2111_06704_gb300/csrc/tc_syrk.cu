@@ -455,8 +455,10 @@ k_ek_tc(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtens
 //   SIX = true: six-product stages (32 columns of planes 0-2, 96 KB, 24 MMAs); two stages.
 //     FP32 accumulation error grows with the terms added and their size (the tensor-core
 //     adds lose ~0.1 ulp on average, not centred), so after each accumulation chunk of
-//     the host's schedule the MMAs pause while the epilogue adds the accumulator into the
-//     FP64 head in global memory.
+//     the host's schedule the MMAs pause while the epilogue adds the accumulator, by an
+//     error-free two-sum, into the tile's running hi / lo floats: 512 KB per CTA of global
+//     scratch, each thread's entries laid out for whole-warp 512-byte accesses, small
+//     enough for the whole grid's to stay in L2.  The FP64 head is touched once per tile.
 // Off the diagonal the k-space terms oscillate in sign; the diagonal, where every term is
 // positive, takes the exact FP64 weight sum instead (range_weight).  Eight epilogue
 // warps: TMEM lane quarter warp % 4, column half (warp - 2) / 4.
@@ -483,11 +485,14 @@ __device__ __forceinline__ void mma_bf16_id(uint32_t d_tmem, uint64_t a, uint64_
 
 struct StripArgs {
   int n, npad;
+  int tiles;      // lower-triangle 256 x 256 tiles
   int kb_begin;   // first K-block
   int kb_end;     // one past the last K-block
   int kb3_end;    // SIX = false: K-blocks before this take three products, the rest one
   int kb_col0;    // the operand planes start at this K-block
   const uint32_t* chunk_end;  // SIX: bit per K-block, an accumulation chunk ends after it
+  float* scratch; // SIX: per SM 2 x 65,536 floats (the tile's running hi / lo sums)
+  int scratch_slots;  // SM slots in scratch (%nsmid)
   double* head;   // [n][ldh] FP64 head + everything before kb_begin (lower triangle)
   int64_t ldh;
   float* E;       // float E, or null: the sum goes back into head (FP64)
@@ -497,13 +502,12 @@ struct StripArgs {
   double w_diag;   // sum of W_K over the launch's k-vectors
 };
 
-// One epilogue thread's 32 accumulator values (row `row`, columns jb .. jb + 31) into the
-// FP64 head: the head segment is loaded whole before any store (16-byte vectors where
-// the segment lies below the diagonal and inside n), then either head += acc (a chunk
-// before the last) or tail + head goes to float E, or back to head without E.  The
-// diagonal entry takes the exact weight sum (nothing on intermediate chunks).
-__device__ __forceinline__ void strip_group(const StripArgs& a, const uint32_t (&acc)[32], int row,
-                                            int jb, bool final_chunk) {
+// One epilogue thread's 32 final tail values (row `row`, columns jb .. jb + 31) plus the
+// FP64 head: the head segment is loaded whole before any store (16-byte vectors where the
+// segment lies below the diagonal and inside n); the sum goes to float E, or back to head
+// without E.  The diagonal entry takes the exact weight sum.
+__device__ __forceinline__ void strip_final(const StripArgs& a, const double (&tail)[32], int row,
+                                            int jb) {
   const int jmax = min(a.n - 1, row);
   if (jb > jmax) return;
   double* hp = a.head + (int64_t)row * a.ldh + jb;
@@ -521,12 +525,8 @@ __device__ __forceinline__ void strip_group(const StripArgs& a, const uint32_t (
     for (int t = 0; t < 32; ++t) hv[t] = jb + t <= jmax ? hp[t] : 0.0;
   }
 #pragma unroll
-  for (int t = 0; t < 32; ++t) {
-    const bool exact = a.diag_exact && jb + t == row;
-    if (exact) hv[t] += final_chunk ? a.w_diag : 0.0;
-    else hv[t] += (double)__uint_as_float(acc[t]);
-  }
-  if (final_chunk && a.E) {
+  for (int t = 0; t < 32; ++t) hv[t] += a.diag_exact && jb + t == row ? a.w_diag : tail[t];
+  if (a.E) {
     float* ep = a.E + (int64_t)row * a.ldE + jb;
     if (full) {
 #pragma unroll
@@ -549,6 +549,26 @@ __device__ __forceinline__ void strip_group(const StripArgs& a, const uint32_t (
   }
 }
 
+// Tile geometry of lower-triangle tile `tile`.
+struct StripTile {
+  int i0, j0, rb, cb;
+  bool diag;
+  __device__ StripTile(int tile, int npad) {
+    int I, J;
+    tri_tile(tile, I, J);
+    i0 = I * kStripTile;
+    j0 = J * kStripTile;
+    diag = I == J;
+    // row and column halves inside the padded operand (npad is a multiple of 128)
+    rb = i0 + kTile < npad ? 2 : 1;
+    cb = j0 + kTile < npad ? 2 : 1;
+  }
+};
+
+// Each CTA takes tiles blockIdx.x, blockIdx.x + gridDim.x, ... (one, when the grid covers
+// the tiles); the ring's stage count and the accumulator's chunk count run on across
+// tiles.  The scratch slot is the SM's: its shared memory and TMEM admit one CTA of this
+// kernel per SM at a time.
 template <bool SIX>
 __global__ void __launch_bounds__(kStripThreads, 1)
 k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CUtensorMap map0n,
@@ -567,20 +587,15 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
   constexpr int kNarrow = kTile * 32 * 2, kWide = kTile * 64 * 2;  // 8 KB and 16 KB tiles
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int I, J;
-  tri_tile(blockIdx.x, I, J);
-  const int i0 = I * kStripTile, j0 = J * kStripTile;
-  const bool diag = I == J;
-  // row and column halves inside the padded operand (npad is a multiple of 128)
-  const int rb = i0 + kTile < args.npad ? 2 : 1, cb = j0 + kTile < args.npad ? 2 : 1;
-  // narrow stages (two per K-block) then wide ones (one per one-product K-block)
+  // narrow stages (two per K-block) then wide ones (one per one-product K-block); the
+  // same for every tile
   const int nnarrow =
       2 * (SIX ? args.kb_end - args.kb_begin
                : max(0, min(args.kb_end, args.kb3_end) - args.kb_begin));
   const int kb1 = max(args.kb_begin, args.kb3_end);
   const int nst = nnarrow + (SIX ? 0 : max(0, args.kb_end - kb1));
-  // an accumulation chunk ends with stage t: the last stage, or (SIX) the second half of a
-  // K-block whose chunk bit is set
+  // an accumulation chunk ends with stage t: the tile's last stage, or (SIX) the second
+  // half of a K-block whose chunk bit is set
   auto chunk_ends = [&](int t) {
     if (t + 1 == nst) return true;
     if (!SIX || !(t & 1)) return false;
@@ -611,32 +626,39 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
   if (warp == 0) {
     // ---- TMA producer ------------------------------------------------------------
     if (lane == 0) {
-      for (int t = 0; t < nst; ++t) {
-        const int s = t % kStages;
-        if (!mbar_wait(&empty_bar[s], ((t / kStages) & 1) ^ 1, args.err, 11)) break;
-        uint8_t* st = ring + s * kStageBytes;
-        if (t < nnarrow) {
-          // 32 columns of planes 0 .. P-1: A plane p half r at slot 2p + r, B plane p half
-          // c at slot 2P + 2p + c (the two B halves adjacent: one N = 256 operand)
-          const int x = (args.kb_begin - args.kb_col0) * kBlockK + t * 32;
-          mbar_expect_tx(&full_bar[s], P * (rb + cb) * kNarrow);
+      uint32_t g = 0;  // stages issued by this CTA
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < args.tiles && ok; tile += gridDim.x) {
+        const StripTile tg(tile, args.npad);
+        for (int t = 0; t < nst; ++t, ++g) {
+          const int s = g % kStages;
+          ok = mbar_wait(&empty_bar[s], ((g / kStages) & 1) ^ 1, args.err, 11);
+          if (!ok) break;
+          uint8_t* st = ring + s * kStageBytes;
+          if (t < nnarrow) {
+            // 32 columns of planes 0 .. P-1: A plane p half r at slot 2p + r, B plane p
+            // half c at slot 2P + 2p + c (the two B halves adjacent: one N = 256 operand)
+            const int x = (args.kb_begin - args.kb_col0) * kBlockK + t * 32;
+            mbar_expect_tx(&full_bar[s], P * (tg.rb + tg.cb) * kNarrow);
 #pragma unroll
-          for (int p = 0; p < P; ++p) {
-            const CUtensorMap* mp = p == 0 ? &map0n : p == 1 ? &map1n : &map2n;
-            for (int r = 0; r < rb; ++r)
-              tma_load_2d(st + (2 * p + r) * kNarrow, mp, &full_bar[s], x, i0 + r * kTile);
-            for (int c = 0; c < cb; ++c)
-              tma_load_2d(st + (2 * P + 2 * p + c) * kNarrow, mp, &full_bar[s], x,
-                          j0 + c * kTile);
+            for (int p = 0; p < P; ++p) {
+              const CUtensorMap* mp = p == 0 ? &map0n : p == 1 ? &map1n : &map2n;
+              for (int r = 0; r < tg.rb; ++r)
+                tma_load_2d(st + (2 * p + r) * kNarrow, mp, &full_bar[s], x, tg.i0 + r * kTile);
+              for (int c = 0; c < tg.cb; ++c)
+                tma_load_2d(st + (2 * P + 2 * p + c) * kNarrow, mp, &full_bar[s], x,
+                            tg.j0 + c * kTile);
+            }
+          } else {
+            // 64 columns of plane 0: A half r at r x 16 KB, B halves at 32 KB and 48 KB
+            const int x = (kb1 - args.kb_col0 + (t - nnarrow)) * kBlockK;
+            mbar_expect_tx(&full_bar[s], (tg.rb + tg.cb) * kWide);
+            for (int r = 0; r < tg.rb; ++r)
+              tma_load_2d(st + r * kWide, &map0w, &full_bar[s], x, tg.i0 + r * kTile);
+            for (int c = 0; c < tg.cb; ++c)
+              tma_load_2d(st + 2 * kWide + c * kWide, &map0w, &full_bar[s], x,
+                          tg.j0 + c * kTile);
           }
-        } else {
-          // 64 columns of plane 0: A half r at r x 16 KB, B halves at 32 KB and 48 KB
-          const int x = (kb1 - args.kb_col0 + (t - nnarrow)) * kBlockK;
-          mbar_expect_tx(&full_bar[s], (rb + cb) * kWide);
-          for (int r = 0; r < rb; ++r)
-            tma_load_2d(st + r * kWide, &map0w, &full_bar[s], x, i0 + r * kTile);
-          for (int c = 0; c < cb; ++c)
-            tma_load_2d(st + 2 * kWide + c * kWide, &map0w, &full_bar[s], x, j0 + c * kTile);
         }
       }
     }
@@ -646,80 +668,154 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
       // products (p, q) with p + q <= 2 in the order (0,0) (0,1) (1,0) (0,2) (1,1) (2,0):
       // A plane p, B plane q; the three-product form is the first three
       constexpr uint32_t kPa = 0x210100u, kPb = 0x012010u;
-      // on a diagonal tile the first row half needs only the first 128 columns
-      const uint32_t id0 = diag ? kIdesc : kIdescN256;
+      uint32_t g = 0, chunk = 0;  // stages consumed, chunks committed by this CTA
       bool ok = true;
-      bool first = true;  // first stage of an accumulation chunk
-      int chunk = 0;
-      for (int t = 0; t < nst && ok; ++t) {
-        const int s = t % kStages;
-        ok = mbar_wait(&full_bar[s], (t / kStages) & 1, args.err, 13);
-        if (!ok) break;
-        if (first && chunk > 0) {  // the epilogue has read the previous chunk
-          ok = mbar_wait(&acc_empty, (chunk - 1) & 1, args.err, 12);
+      for (int tile = blockIdx.x; tile < args.tiles && ok; tile += gridDim.x) {
+        const StripTile tg(tile, args.npad);
+        // on a diagonal tile the first row half needs only the first 128 columns
+        const uint32_t id0 = tg.diag ? kIdesc : kIdescN256;
+        bool first = true;  // first stage of an accumulation chunk
+        for (int t = 0; t < nst; ++t, ++g) {
+          const int s = g % kStages;
+          ok = mbar_wait(&full_bar[s], (g / kStages) & 1, args.err, 13);
           if (!ok) break;
-        }
-        tc_fence_after();
-        const uint32_t st = smem_addr(ring + s * kStageBytes);
-        if (t < nnarrow) {
+          if (first && chunk > 0) {  // the epilogue has read the previous chunk
+            ok = mbar_wait(&acc_empty, (chunk - 1) & 1, args.err, 12);
+            if (!ok) break;
+          }
+          tc_fence_after();
+          const uint32_t st = smem_addr(ring + s * kStageBytes);
+          if (t < nnarrow) {
 #pragma unroll
-          for (int ks = 0; ks < 2; ++ks)
-            for (int r = 0; r < rb; ++r)
+            for (int ks = 0; ks < 2; ++ks)
+              for (int r = 0; r < tg.rb; ++r)
 #pragma unroll
-              for (int p = 0; p < Cfg::kProds; ++p) {
-                const int pa = (kPa >> (4 * p)) & 15, pb = (kPb >> (4 * p)) & 15;
-                const uint64_t da = smem_desc<32>(st + (2 * pa + r) * kNarrow + ks * 32);
-                const uint64_t db = smem_desc<32>(st + (2 * P + 2 * pb) * kNarrow + ks * 32);
+                for (int p = 0; p < Cfg::kProds; ++p) {
+                  const int pa = (kPa >> (4 * p)) & 15, pb = (kPb >> (4 * p)) & 15;
+                  const uint64_t da = smem_desc<32>(st + (2 * pa + r) * kNarrow + ks * 32);
+                  const uint64_t db = smem_desc<32>(st + (2 * P + 2 * pb) * kNarrow + ks * 32);
+                  mma_bf16_id(tmem + (uint32_t)(r * 256), da, db, r == 0 ? id0 : kIdescN256,
+                              (first && ks == 0 && p == 0) ? 0u : 1u);
+                }
+          } else {
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+              for (int r = 0; r < tg.rb; ++r) {
+                const uint64_t da = smem_desc<64>(st + r * kWide + ks * 32);
+                const uint64_t db = smem_desc<64>(st + 2 * kWide + ks * 32);
                 mma_bf16_id(tmem + (uint32_t)(r * 256), da, db, r == 0 ? id0 : kIdescN256,
-                            (first && ks == 0 && p == 0) ? 0u : 1u);
+                            (first && ks == 0) ? 0u : 1u);
               }
-        } else {
-#pragma unroll
-          for (int ks = 0; ks < 4; ++ks)
-            for (int r = 0; r < rb; ++r) {
-              const uint64_t da = smem_desc<64>(st + r * kWide + ks * 32);
-              const uint64_t db = smem_desc<64>(st + 2 * kWide + ks * 32);
-              mma_bf16_id(tmem + (uint32_t)(r * 256), da, db, r == 0 ? id0 : kIdescN256,
-                          (first && ks == 0) ? 0u : 1u);
-            }
-        }
-        first = false;
-        mma_commit(&empty_bar[s]);  // frees the stage once these MMAs have read it
-        if (chunk_ends(t)) {
-          mma_commit(&acc_full);
-          ++chunk;
-          first = true;
+          }
+          first = false;
+          mma_commit(&empty_bar[s]);  // frees the stage once these MMAs have read it
+          if (chunk_ends(t)) {
+            mma_commit(&acc_full);
+            ++chunk;
+            first = true;
+          }
         }
       }
     }
   } else {
     // ---- epilogue: warps 2-9, TMEM lane quarter q = warp % 4, column half h ---------
-    const int q = warp & 3, h = (warp - 2) >> 2;
+    // A chunk before a tile's last goes, by an error-free two-sum, into the tile's running
+    // hi / lo floats in this CTA's scratch (each thread its own 8 x 32 entries, laid out so
+    // that a warp's accesses are contiguous); the last chunk adds hi + lo + acc to head.
+    const int q = warp & 3, h = (warp - 2) >> 2, ew = warp - 2;
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-    int chunk = 0;
-    for (int t0 = 0; t0 < nst;) {
-      int t1 = t0;
-      while (!chunk_ends(t1)) ++t1;
-      const bool final_chunk = t1 + 1 == nst;
-      if (!mbar_wait(&acc_full, chunk & 1, args.err, 14)) break;
-      tc_fence_after();
-      for (int r = 0; r < rb; ++r) {
-        const int row = i0 + r * kTile + 32 * q + lane;
-#pragma unroll 1
-        for (int cg = 4 * h; cg < 4 * h + 4; ++cg) {
-          if (diag && r == 0 && cg >= kTile / 32) break;  // above the diagonal
-          if (j0 + cg * 32 >= args.n) break;
-          uint32_t acc[32];
-          TMEM_LD32(tmem + lane_base + (uint32_t)(r * 256 + cg * 32), acc);
-          tmem_wait_ld();
-          if (row < args.n) strip_group(args, acc, row, j0 + cg * 32, final_chunk);
-        }
+    float4* hi4 = nullptr;
+    float4* lo4 = nullptr;
+    bool ok = true;
+    if (SIX) {
+      uint32_t smid;
+      asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+      if ((int)smid < args.scratch_slots) {
+        hi4 = reinterpret_cast<float4*>(args.scratch + (size_t)smid * 2 * 65536) +
+              (size_t)ew * 8 * 8 * 32 + lane;
+        lo4 = hi4 + 65536 / 4;
+      } else {
+        atomicCAS(args.err, 0, 15);  // no slot: give up (the other roles' waits see it)
+        ok = false;
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty);
-      ++chunk;
-      t0 = t1 + 1;
+    }
+    uint32_t chunk = 0;
+    for (int tile = blockIdx.x; tile < args.tiles && ok; tile += gridDim.x) {
+      const StripTile tg(tile, args.npad);
+      int ci = 0;  // chunk index within the tile
+      for (int t0 = 0; t0 < nst; ++ci) {
+        int t1 = t0;
+        while (!chunk_ends(t1)) ++t1;
+        const bool final_chunk = t1 + 1 == nst;
+        ok = mbar_wait(&acc_full, chunk & 1, args.err, 14);
+        if (!ok) break;
+        tc_fence_after();
+        for (int r = 0; r < tg.rb; ++r) {
+          const int row = tg.i0 + r * kTile + 32 * q + lane;
+#pragma unroll 1
+          for (int cl = 0; cl < 4; ++cl) {
+            const int cg = 4 * h + cl;
+            if (tg.diag && r == 0 && cg >= kTile / 32) break;  // above the diagonal
+            if (tg.j0 + cg * 32 >= args.n) break;
+            uint32_t acc[32];
+            TMEM_LD32(tmem + lane_base + (uint32_t)(r * 256 + cg * 32), acc);
+            tmem_wait_ld();
+            const int grp = (r * 4 + cl) * 8 * 32;  // float4 offset of this group
+            if (final_chunk) {
+              double tail[32];
+              if (SIX && ci > 0) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                  const float4 hv = hi4[grp + u * 32], lv = lo4[grp + u * 32];
+                  tail[4 * u] = (double)hv.x + (double)lv.x;
+                  tail[4 * u + 1] = (double)hv.y + (double)lv.y;
+                  tail[4 * u + 2] = (double)hv.z + (double)lv.z;
+                  tail[4 * u + 3] = (double)hv.w + (double)lv.w;
+                }
+#pragma unroll
+                for (int t = 0; t < 32; ++t) tail[t] += (double)__uint_as_float(acc[t]);
+              } else {
+#pragma unroll
+                for (int t = 0; t < 32; ++t) tail[t] = (double)__uint_as_float(acc[t]);
+              }
+              if (row < args.n) strip_final(args, tail, row, tg.j0 + cg * 32);
+            } else {
+              float hv[32], lv[32];
+              if (ci > 0) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                  const float4 a4 = hi4[grp + u * 32], b4 = lo4[grp + u * 32];
+                  hv[4 * u] = a4.x, hv[4 * u + 1] = a4.y, hv[4 * u + 2] = a4.z, hv[4 * u + 3] = a4.w;
+                  lv[4 * u] = b4.x, lv[4 * u + 1] = b4.y, lv[4 * u + 2] = b4.z, lv[4 * u + 3] = b4.w;
+                }
+              } else {
+#pragma unroll
+                for (int t = 0; t < 32; ++t) hv[t] = lv[t] = 0.f;
+              }
+#pragma unroll
+              for (int t = 0; t < 32; ++t) {
+                // two-sum: hv + a = s + e exactly
+                const float a = __uint_as_float(acc[t]);
+                const float s = __fadd_rn(hv[t], a);
+                const float bb = __fsub_rn(s, hv[t]);
+                const float e = __fadd_rn(__fsub_rn(hv[t], __fsub_rn(s, bb)), __fsub_rn(a, bb));
+                hv[t] = s;
+                lv[t] = __fadd_rn(lv[t], e);
+              }
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                hi4[grp + u * 32] = make_float4(hv[4 * u], hv[4 * u + 1], hv[4 * u + 2], hv[4 * u + 3]);
+                lo4[grp + u * 32] = make_float4(lv[4 * u], lv[4 * u + 1], lv[4 * u + 2], lv[4 * u + 3]);
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty);
+        ++chunk;
+        t0 = t1 + 1;
+      }
     }
   }
   tc_fence_before();
@@ -785,6 +881,22 @@ int range_weight(const double* kw, int kb0, int kb1, double* w) {
 
 }  // namespace
 
+__global__ void k_nsmid(int* out) {
+  uint32_t v;
+  asm volatile("mov.u32 %0, %%nsmid;" : "=r"(v));
+  *out = (int)v;
+}
+
+// Floats of k_ek_strip scratch per SM slot.
+int64_t ek_strip_scratch_floats() { return 2 * 65536; }
+
+// SM identifiers of the current device (%nsmid: the largest %smid + 1, which may exceed the
+// SM count), written to the device int *d_out.
+void launch_nsmid(int* d_out, cudaStream_t s) {
+  k_nsmid<<<1, 1, 0, s>>>(d_out);
+  note_launch();
+}
+
 // K-blocks [kb_begin, kb_end) of the lower triangle from BF16 planes holding the K-blocks
 // kb_col0 .. kb_col0 + plane_cols / 64; the result plus head goes to float E, or back into
 // head (FP64) when E is null.  Two launches, the first adding its K-range to head and the
@@ -795,7 +907,8 @@ int range_weight(const double* kw, int kb0, int kb1, double* w) {
 int launch_ek_tc(const void* p0, const void* p1, const void* p2, int npad, int64_t plane_cols,
                  int kb_col0, int n, int kb_begin, int kb_end, int kb6_end, int kb3_end,
                  const uint32_t* chunk_end, double* head, int64_t ldh, float* E, int64_t ldE,
-                 int* err, const double* kw, cudaEvent_t mid, cudaStream_t s) {
+                 int* err, const double* kw, float* scratch, int scratch_slots, cudaEvent_t mid,
+                 cudaStream_t s) {
   const char* env = getenv("CPM_TC_BK");
   const int bk = env && atoi(env) == 32 ? 32 : 64;
   const char* env_strip = getenv("CPM_TC_STRIP");
@@ -855,6 +968,8 @@ int launch_ek_tc(const void* p0, const void* p1, const void* p2, int npad, int64
       StripArgs a;
       a.n = n;
       a.npad = npad;
+      a.scratch = scratch;
+      a.scratch_slots = scratch_slots;
       a.kb_begin = seg[q].b;
       a.kb_end = seg[q].e;
       a.kb3_end = kb3_end;
@@ -867,12 +982,15 @@ int launch_ek_tc(const void* p0, const void* p1, const void* p2, int npad, int64
       a.err = err;
       a.diag_exact = range_weight(kw, seg[q].b, seg[q].e, &a.w_diag);
       const int nt = (n + kStripTile - 1) / kStripTile;
-      const int tiles = nt * (nt + 1) / 2;
+      a.tiles = nt * (nt + 1) / 2;
+      // one CTA per tile; the hardware hands each SM its next tile as it frees up
+      const int grid = a.tiles;
+      if (seg[q].kind == 1 && (!scratch || scratch_slots < 1)) return CPM_EINVAL;
       if (seg[q].kind == 1)
-        (k_ek_strip<true><<<tiles, kStripThreads, smem6, s>>>(m0, m0n, m1n, m2n, a),
+        (k_ek_strip<true><<<grid, kStripThreads, smem6, s>>>(m0, m0n, m1n, m2n, a),
          note_launch());
       else
-        (k_ek_strip<false><<<tiles, kStripThreads, smem31, s>>>(m0, m0n, m1n, m2n, a),
+        (k_ek_strip<false><<<grid, kStripThreads, smem31, s>>>(m0, m0n, m1n, m2n, a),
          note_launch());
     }
   }
