@@ -109,11 +109,26 @@ __global__ void k_dc_pairs(const double* __restrict__ xyz, int n, double lx, dou
 }
 
 // Column tau of M_tau^-1 (Eq. 36), written to pcol[off[tau] .. off[tau+1]).  One block
-// per atom: the symmetric local matrix is filled from the pattern's pair values (a pair
-// of tau's neighbours closer than r_cut is an entry of the first one's pattern row,
-// found by binary search), then Gaussian elimination with partial pivoting on
-// [M | e_tau] with one warp per row of the update, then back substitution.
+// per atom.  The symmetric local matrix is filled in FP64 from the pattern's pair values
+// (a pair of tau's neighbours closer than r_cut is an entry of the first one's pattern
+// row, found by binary search) and kept as its packed upper triangle.  A float copy is
+// factored P M = L U with partial pivoting (FP64 runs at 1/64 of the float rate here, and
+// the factorisation is m^3 / 3 multiply-adds), and the solution is refined against the
+// FP64 matrix: x += (LU)^-1 P (e_tau - M x), residuals in FP64, until the correction is
+// below FP64 rounding of x (each step gains the ~1e-5 that kappa(M) x 2^-24 leaves).
 constexpr int kDcThreads = 128;
+constexpr int kDcMaxRefine = 6;
+
+__device__ __forceinline__ int sym_index(int a, int b, int m) {  // packed upper, a <= b
+  return a * m - (a * (a - 1)) / 2 + (b - a);
+}
+
+// shared memory of k_dc_local for a neighbourhood of m atoms
+size_t dc_local_smem(int m) {
+  return (size_t)m * (m + 1) / 2 * sizeof(double) + 2 * (size_t)m * sizeof(double) +
+         (size_t)m * (m + 1) * sizeof(float) + (size_t)m * sizeof(float) +
+         (size_t)m * sizeof(int) + 16;
+}
 
 __global__ void __launch_bounds__(kDcThreads)
 k_dc_local(const double* __restrict__ alpha, const int64_t* __restrict__ off,
@@ -126,15 +141,20 @@ k_dc_local(const double* __restrict__ alpha, const int64_t* __restrict__ off,
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t o = off[tau];
   const int m = (int)(off[tau + 1] - o);
-  const int w = m + 1;  // augmented row width
-  double* M = sm;                  // [m][m + 1]
-  __shared__ int s_piv;
-  __shared__ double s_val, s_inv;
+  const int ld = m + 1;                        // float row stride
+  double* S = sm;                              // packed upper triangle of M (FP64)
+  double* x = S + (size_t)m * (m + 1) / 2;     // solution (FP64)
+  double* r = x + m;                           // residual (FP64)
+  float* F = reinterpret_cast<float*>(r + m);  // [m][ld]: L (unit, below) and U
+  float* y = F + (size_t)m * ld;               // correction (float)
+  int* piv = reinterpret_cast<int*>(y + m);    // row exchanged with row k at step k
+  __shared__ int s_piv, s_pos, s_done;
+  __shared__ float s_val;
   for (int a = threadIdx.x; a < m; a += blockDim.x) {
     const int j = idx[o + a];
     const double al = alpha[j];
-    M[a * w + a] = isinf(al) ? 0.0 : 0.7978845608028654 * al;  // sqrt(2/pi) alpha_i
-    M[a * w + m] = j == tau ? 1.0 : 0.0;
+    S[sym_index(a, a, m)] = isinf(al) ? 0.0 : 0.7978845608028654 * al;  // sqrt(2/pi) alpha_i
+    if (j == tau) s_pos = a;
   }
   for (int a = warp; a < m; a += kWarps) {
     const int ja = idx[o + a];
@@ -147,25 +167,29 @@ k_dc_local(const double* __restrict__ alpha, const int64_t* __restrict__ off,
         if (idx[mid] < jb) lo = mid + 1;
         else hi = mid;
       }
-      const double v = (lo < hi0 && idx[lo] == jb) ? pval[lo] : 0.0;
-      M[a * w + b] = v;
-      M[b * w + a] = v;
+      S[sym_index(a, b, m)] = (lo < hi0 && idx[lo] == jb) ? pval[lo] : 0.0;
     }
   }
   __syncthreads();
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int a = e / m, b = e - a * m;
+    F[a * ld + b] = (float)S[a <= b ? sym_index(a, b, m) : sym_index(b, a, m)];
+  }
+  __syncthreads();
+  // ---- P M = L U in float, partial pivoting, whole rows exchanged ---------------------
   for (int k = 0; k < m; ++k) {
     if (warp == 0) {
-      double best = -1.0;
+      float best = -1.f;
       int bi = k;
       for (int a = k + lane; a < m; a += 32) {
-        const double v = fabs(M[a * w + k]);
+        const float v = fabsf(F[a * ld + k]);
         if (v > best) {
           best = v;
           bi = a;
         }
       }
       for (int sh = 16; sh; sh >>= 1) {
-        const double ob = __shfl_xor_sync(0xffffffffu, best, sh);
+        const float ob = __shfl_xor_sync(0xffffffffu, best, sh);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, sh);
         if (ob > best || (ob == best && oi < bi)) {
           best = ob;
@@ -175,41 +199,86 @@ k_dc_local(const double* __restrict__ alpha, const int64_t* __restrict__ off,
       if (lane == 0) {
         s_piv = bi;
         s_val = best;
-        s_inv = best > 0.0 ? 1.0 / M[bi * w + k] : 0.0;
+        piv[k] = bi;
       }
     }
     __syncthreads();
-    if (!(s_val > 0.0)) {
+    if (!(s_val > 0.f)) {
       if (threadIdx.x == 0) atomicExch(status, 1);
       return;  // singular local matrix (whole block leaves together)
     }
     const int pv = s_piv;
-    if (pv != k)  // columns left of k are already eliminated in both rows
-      for (int b = k + threadIdx.x; b < w; b += blockDim.x) {
-        const double t = M[k * w + b];
-        M[k * w + b] = M[pv * w + b];
-        M[pv * w + b] = t;
+    if (pv != k)
+      for (int b = threadIdx.x; b < m; b += blockDim.x) {
+        const float t = F[k * ld + b];
+        F[k * ld + b] = F[pv * ld + b];
+        F[pv * ld + b] = t;
       }
     __syncthreads();
-    const double inv = s_inv;
+    const float inv = 1.f / F[k * ld + k];
     for (int a = k + 1 + warp; a < m; a += kWarps) {
-      const double f = M[a * w + k] * inv;
-      for (int b = k + 1 + lane; b < w; b += 32) M[a * w + b] -= f * M[k * w + b];
+      const float f = F[a * ld + k] * inv;
+      for (int b = k + 1 + lane; b < m; b += 32) F[a * ld + b] -= f * F[k * ld + b];
+      __syncwarp();
+      if (lane == 0) F[a * ld + k] = f;
     }
     __syncthreads();
   }
-  // back substitution (single warp; m is small)
-  if (warp == 0) {
-    for (int k = m - 1; k >= 0; --k) {
-      double s = 0.0;
-      for (int b = k + 1 + lane; b < m; b += 32) s += M[k * w + b] * M[b * w + m];
-      for (int o2 = 16; o2; o2 >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o2);
-      if (lane == 0) M[k * w + m] = (M[k * w + m] - s) / M[k * w + k];
-      __syncwarp();
-    }
+  // ---- x = 0, r = e_tau; x += (LU)^-1 P r; r = e_tau - M x (FP64) ------------------------
+  for (int a = threadIdx.x; a < m; a += blockDim.x) {
+    x[a] = 0.0;
+    r[a] = a == s_pos ? 1.0 : 0.0;
   }
+  if (threadIdx.x == 0) s_done = 0;
   __syncthreads();
-  for (int a = threadIdx.x; a < m; a += blockDim.x) pcol[o + a] = M[a * w + m];
+  for (int it = 0; it < kDcMaxRefine && !s_done; ++it) {
+    if (warp == 0) {
+      for (int a = lane; a < m; a += 32) y[a] = (float)r[a];
+      __syncwarp();
+      if (lane == 0)
+        for (int k = 0; k < m; ++k)
+          if (piv[k] != k) {
+            const float t = y[k];
+            y[k] = y[piv[k]];
+            y[piv[k]] = t;
+          }
+      __syncwarp();
+      for (int k = 0; k < m; ++k) {  // forward: unit lower L
+        const float yk = y[k];
+        for (int a = k + 1 + lane; a < m; a += 32) y[a] -= F[a * ld + k] * yk;
+        __syncwarp();
+      }
+      for (int k = m - 1; k >= 0; --k) {  // back: U
+        const float yk = y[k] / F[k * ld + k];
+        __syncwarp();
+        if (lane == 0) y[k] = yk;
+        for (int a = lane; a < k; a += 32) y[a] -= F[a * ld + k] * yk;
+        __syncwarp();
+      }
+      double dmax = 0.0, xmax = 0.0;
+      for (int a = lane; a < m; a += 32) {
+        x[a] += (double)y[a];
+        dmax = fmax(dmax, fabs((double)y[a]));
+        xmax = fmax(xmax, fabs(x[a]));
+      }
+      for (int sh = 16; sh; sh >>= 1) {
+        dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, sh));
+        xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, sh));
+      }
+      if (lane == 0 && dmax <= 1e-16 * xmax) s_done = 1;
+    }
+    __syncthreads();
+    if (s_done) break;
+    for (int a = warp; a < m; a += kWarps) {  // r = e_tau - M x, one warp per row
+      double s = 0.0;
+      for (int b = lane; b < m; b += 32)
+        s += S[a <= b ? sym_index(a, b, m) : sym_index(b, a, m)] * x[b];
+      for (int sh = 16; sh; sh >>= 1) s += __shfl_xor_sync(0xffffffffu, s, sh);
+      if (lane == 0) r[a] = (a == s_pos ? 1.0 : 0.0) - s;
+    }
+    __syncthreads();
+  }
+  for (int a = threadIdx.x; a < m; a += blockDim.x) pcol[o + a] = x[a];
 }
 
 // prow[off[j] + position of tau in j's list] = pcol[off[tau] + a] - shift, j = idx[off[tau] + a]
@@ -311,7 +380,7 @@ int build_dc_preconditioner(Ctx* c) {
                                                    L[2], rc * rc, nullptr,
                                                    (const int64_t*)c->nbr_off.ptr,
                                                    (int*)c->nbr_idx.ptr, 1), note_launch());
-    const size_t smem = (size_t)mx * (mx + 1) * sizeof(double);
+    const size_t smem = dc_local_smem(mx);
     st = cuda_check(c, cudaFuncSetAttribute(k_dc_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)smem), "dc smem");
     if (!st) {
