@@ -360,9 +360,10 @@ def run_ours(args, rank, world, local_rank):
         bf16_peak = peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"])
         roof = {"bound": "tensor", "achieved": algo_flops / (tc_ms * 1e-3) / 1e12,
                 "peak": bf16_peak, "unit": "TFLOP/s",
-                "kernel": "k_ek_strip<true> + k_ek_strip<false> (tcgen05 split-BF16 k-space "
-                          "GEMM on 256 x 256 tiles: six-product K-blocks with two-sum chunk drains "
-                          "into per-SM hi/lo scratch, then three- and one-product K-blocks)",
+                "kernel": "k_ek_strip<true> + k_ek_strip<false> (tcgen05 k-space GEMM on "
+                          "256 x 256 tiles: six BF16 products per heavy K-block, then three or "
+                          "one FP16 products of per-block scaled values; two-sum chunk drains "
+                          "into per-SM hi/lo scratch)",
                 "peak_source": f"{src} bf16_tflops (burst)",
                 "issued_tflops": tc_flops / (tc_ms * 1e-3) / 1e12,
                 "fp32_accurate_tflops": 2.0 * (n * (n + 1) / 2) * tail_cols / (tc_ms * 1e-3) / 1e12,
@@ -387,7 +388,7 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32": "f32", "fp64": "f64", "bf16x6": "bf16x6 (f32-accurate)"}[args.precision], "data": "synthetic",
+        "dtype": {"fp32": "f32", "fp64": "f64", "bf16x6": "bf16x6+fp16x3 (f32-accurate)"}[args.precision], "data": "synthetic",
         "config": {"workload": f"two-sheet graphene N={n}, {args.ions} ions, one frame per "
                                f"step incl. full E/P/d build",
                    "electrode_atoms": n, "ions": args.ions, "kvectors": m,

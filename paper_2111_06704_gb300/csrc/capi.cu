@@ -165,6 +165,7 @@ void kvector_table(const cpm_params& p, std::vector<int>& hkl, std::vector<doubl
 
 void free_build(Ctx* c) {
   Buf* all[] = {&c->xyz, &c->alpha, &c->sfix, &c->hkl, &c->sqw, &c->flush, &c->chunk_end,
+                &c->kexp,
                 &c->Ahead, &c->A,
                 &c->E, &c->diag,
                 &c->nbr_off, &c->nbr_idx, &c->prow, &c->d, &c->shell_off, &c->shell_members, &c->p_f32,
@@ -315,55 +316,63 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
     }
   }
 
-  // tensor-core build: accumulation chunks of 64-column K-blocks after the head
+  // Tensor-core build: product schedule, per-block FP16 scales and accumulation chunks of
+  // the 64-column K-blocks after the head (K-block b holds the cos or sin columns of
+  // k-vectors 64 (b / 2) ..; a pair shares its weights).
   const bool tc = c->p.precision == CPM_PREC_BF16X6;
   const int nkb = 2 * c->mpad / 64;
   std::vector<uint32_t> cmask((nkb + 31) / 32, 0u);
+  std::vector<int> kexp(nkb, 0);
   {
+    // bwm[b]: 64 x the block's largest weight, which bounds the block's |a_i a_j| sums
+    std::vector<double> bw(nkb, 0.0), bwm(nkb, 0.0);
+    for (int b = 0; b < nkb; ++b)
+      for (int t = 0; t < 64; ++t)
+        if (64 * (b / 2) + t < c->m) {
+          bw[b] += w[64 * (b / 2) + t];
+          bwm[b] = std::max(bwm[b], 64.0 * w[64 * (b / 2) + t]);
+        }
+    // Product count (weights decrease along the table): trailing blocks whose summed
+    // bound times the one-FP16-product error (2^-10 + 2^-23, the second for subnormal
+    // remainders) stays within 1e-8 take one product; the blocks before them up to
+    // another 1e-8 at the three-FP16-product error (5 x 2^-22) take three; the rest the
+    // six BF16 products (~2^-24).  Both ends even: whole [cos | sin] pairs per region,
+    // one more block with more products at most.
+    const int kb0 = c->heavy_steps / 4;
+    const double budget = 1e-8;
+    int kb3 = nkb;
+    double tw = 0.0;
+    while (kb3 > kb0 && (tw + bwm[kb3 - 1]) * (0x1p-10 + 0x1p-23) <= budget) tw += bwm[--kb3];
+    kb3 = std::min(nkb, (kb3 + 1) & ~1);
+    int kb6 = kb3;
+    tw = 0.0;
+    while (kb6 > kb0 && (tw + bwm[kb6 - 1]) * 5 * 0x1p-22 <= budget) tw += bwm[--kb6];
+    kb6 = std::min(kb3, (kb6 + 1) & ~1);
+    c->kb6_end = kb6;
+    c->kb3_end = kb3;
+    // FP16 blocks: x = 2^e a with 2^e sqrt(max W) in [1/2, 1), so |x| < 1
+    for (int b = kb6; b < nkb; ++b)
+      if (bwm[b] > 0.0) kexp[b] = -ilogb(sqrt(bwm[b] / 64.0)) - 1;
+    // Accumulation chunks.  Six-product blocks: up to 5e-3 of weight or 32 blocks (the
+    // FP32 accumulation error of a chunk stays near 6e-8 x 5e-3 x sqrt(768 terms) ~ 1e-8;
+    // measured: E unchanged at the 512-atom cell against 5e-4 / 8; at 3,200 atoms 2e-2 / 32
+    // doubles the off-diagonal RMS error, 3.9e-9 -> 9.7e-9).  FP16 blocks: one scale per
+    // chunk (a chunk ends where the next block's scale differs), at most 512 blocks; their
+    // summed weight is below 1e-2.
     double cw = 0.0;
     int len = 0;
-    // chunks of up to 5e-3 of weight or 32 K-blocks: the FP32 accumulation error of a
-    // chunk stays near 6e-8 x 5e-3 x sqrt(768 terms) ~ 1e-8 (measured: E unchanged at the
-    // 512-atom cell against 5e-4 / 8, 6% faster at 12,800 atoms; at 1e-2 / 64 E degrades;
-    // at 3,200 atoms 2e-2 / 32 already doubles the off-diagonal RMS error, 3.9e-9 -> 9.7e-9)
-    const double wmax = 5e-3;
-    const int bmax = 32;
-    for (int b = c->heavy_steps / 4; b < nkb; ++b) {
-      for (int t = 0; t < 64; ++t) cw += (64 * (b / 2) + t < c->m) ? w[64 * (b / 2) + t] : 0.0;
+    for (int b = kb0; b < nkb; ++b) {
+      cw += bw[b];
       ++len;
-      if (cw >= wmax || len >= bmax || b == nkb - 1) {
+      const bool end = b == nkb - 1 || b + 1 == kb6 ||
+                       (b < kb6 ? (cw >= 5e-3 || len >= 32)
+                                : (kexp[b + 1] != kexp[b] || len >= 512));
+      if (end) {
         cmask[b >> 5] |= 1u << (b & 31);
         cw = 0.0;
         len = 0;
       }
     }
-  }
-
-  // Product count of each tensor-core K-block (weights decrease along the table, and a
-  // K-block's products are bounded by its summed weight): the trailing blocks whose
-  // weight times 2^-7 (one BF16 product) stays within 1e-8 take one product, the blocks
-  // before them whose weight times 3 * 2^-16 (three products) stays within another 1e-8
-  // take three, the rest six.
-  {
-    std::vector<double> bw(nkb, 0.0);
-    for (int b = 0; b < nkb; ++b)
-      for (int t = 0; t < 64; ++t)
-        if (64 * (b / 2) + t < c->m) bw[b] += w[64 * (b / 2) + t];
-    const int kb0 = c->heavy_steps / 4;
-    const double budget = 1e-8;
-    int kb3 = nkb;
-    double tw = 0.0;
-    while (kb3 > kb0 && (tw + bw[kb3 - 1]) * 0x1p-7 <= budget) tw += bw[--kb3];
-    kb3 = std::min(nkb, (kb3 + 1) & ~1);  // even: see below
-    int kb6 = kb3;
-    tw = 0.0;
-    while (kb6 > kb0 && (tw + bw[kb6 - 1]) * 3 * 0x1p-16 <= budget) tw += bw[--kb6];
-    // both ends even (whole [cos | sin] pairs in each region, one more block with more
-    // products at most): the 256 x 256 tile kernels take their launch ranges at even
-    // K-blocks and read plane 2 over the whole six-product range
-    kb6 = std::min(kb3, (kb6 + 1) & ~1);
-    c->kb6_end = kb6;
-    c->kb3_end = kb3;
   }
 
   const size_t a_bytes = (size_t)c->npad * 2 * c->mpad * c->esz();
@@ -379,6 +388,7 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
       (st = buf_alloc(c, &c->sqw, sqw.size() * sizeof(double))) ||
       (st = buf_alloc(c, &c->flush, fmask.size() * sizeof(uint32_t))) ||
       (st = buf_alloc(c, &c->chunk_end, cmask.size() * sizeof(uint32_t))) ||
+      (st = buf_alloc(c, &c->kexp, kexp.size() * sizeof(int))) ||
       (st = buf_alloc(c, &c->Ahead, (size_t)c->npad * 2 * std::max(c->kh, 1) * sizeof(double))) ||
       (!c->streamed && (st = buf_alloc(c, &c->A, a_bytes))) ||
       (st = buf_alloc(c, &c->E, e_bytes)) ||
@@ -399,6 +409,7 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
       (st = cuda_check(c, cudaMemcpyAsync(c->sqw.ptr, sqw.data(), sqw.size() * sizeof(double), h2d, s), "sqw")) ||
       (st = cuda_check(c, cudaMemcpyAsync(c->flush.ptr, fmask.data(), fmask.size() * sizeof(uint32_t), h2d, s), "flush")) ||
       (st = cuda_check(c, cudaMemcpyAsync(c->chunk_end.ptr, cmask.data(), cmask.size() * sizeof(uint32_t), h2d, s), "chunks")) ||
+      (st = cuda_check(c, cudaMemcpyAsync(c->kexp.ptr, kexp.data(), kexp.size() * sizeof(int), h2d, s), "scales")) ||
       (st = cuda_check(c, cudaMemsetAsync(c->E.ptr, 0, e_bytes, s), "E memset")) ||
       (st = cuda_check(c, cudaStreamSynchronize(s), "build upload")))
     return fail(st);
@@ -453,7 +464,8 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
     launch_structure_operand(f64, (const double*)c->xyz.ptr, (const uint32_t*)c->sfix.ptr,
                              c->npad, n, (const int*)c->hkl.ptr, (const double*)c->sqw.ptr,
                              c->mpad, c->p.box, c->A.ptr, tc ? plane_ptrs : nullptr,
-                             c->heavy_steps / 4, c->kb6_end, c->kb3_end, 0, c->mpad, s);
+                             c->heavy_steps / 4, c->kb6_end, c->kb3_end,
+                             (const int*)c->kexp.ptr, 0, c->mpad, s);
   if (c->kh > 0)
     launch_structure_operand_head((const double*)c->xyz.ptr, c->npad, n, (const int*)c->hkl.ptr,
                                   (const double*)c->sqw.ptr, c->kh, c->p.box,
@@ -480,11 +492,12 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
         launch_structure_operand(false, (const double*)c->xyz.ptr, (const uint32_t*)c->sfix.ptr,
                                  c->npad, n, (const int*)c->hkl.ptr, (const double*)c->sqw.ptr,
                                  c->mpad, c->p.box, nullptr, plane_ptrs, c->heavy_steps / 4,
-                                 c->kb6_end, c->kb3_end, kbeg, kend, s);
+                                 c->kb6_end, c->kb3_end, (const int*)c->kexp.ptr, kbeg, kend, s);
       st = launch_ek_tc(planes[0].ptr, planes[1].ptr, planes[2].ptr, c->npad,
                         2 * (int64_t)(kend - kbeg), kbeg / 32, n,
                         std::max(c->heavy_steps / 4, kbeg / 32), kend / 32, c->kb6_end,
-                        c->kb3_end, (const uint32_t*)c->chunk_end.ptr, (double*)ehead.ptr,
+                        c->kb3_end, (const uint32_t*)c->chunk_end.ptr, (const int*)c->kexp.ptr,
+                        (double*)ehead.ptr,
                         c->ldE, last ? (float*)c->E.ptr : nullptr, c->ldE, (int*)errbuf.ptr,
                         c->kw.data(), (float*)tcscratch.ptr, sms,
                         c->streamed ? nullptr : c->ev_tc[2], s);

@@ -86,6 +86,7 @@ struct Ctx {
   int kh = 0;           // head k-vectors with an FP64 operand copy (float storage only)
   Buf Ahead;            // double [npad][2*kh], same column layout as A
   Buf chunk_end;        // uint32 bit per K-block of 64 columns (tensor-core build)
+  Buf kexp;             // int per K-block: FP16 plane scale exponent (tensor-core build)
   bool streamed = false;  // A too large to keep: built in k-windows, potential direct
   int kb6_end = 0, kb3_end = 0;  // tensor-core K-blocks: six products before kb6_end,
                                  // three before kb3_end, one after
@@ -147,7 +148,8 @@ void launch_fixed_point_coords(const double* xyz, int n, int npad, const double 
 void launch_structure_operand(bool fp64, const double* xyz, const uint32_t* sfix, int npad,
                               int n, const int* hkl, const double* sqw, int mpad,
                               const double L[3], void* A, void* const* planes, int kb0,
-                              int kb6, int kb3, int kbeg, int kend, cudaStream_t s);
+                              int kb6, int kb3, const int* kexp, int kbeg, int kend,
+                              cudaStream_t s);
 void launch_structure_operand_head(const double* xyz, int npad, int n, const int* hkl,
                                    const double* sqw, int kh, const double L[3], double* Ahead,
                                    cudaStream_t s);
@@ -163,9 +165,9 @@ int launch_ek_head_f64(const double* Ahead, int kh, int ktot, int npad, float* h
 // tc_syrk.cu
 int launch_ek_tc(const void* p0, const void* p1, const void* p2, int npad, int64_t plane_cols,
                  int kb_col0, int n, int kb_begin, int kb_end, int kb6_end, int kb3_end,
-                 const uint32_t* chunk_end, double* head, int64_t ldh, float* E, int64_t ldE,
-                 int* err, const double* kw, float* scratch, int scratch_slots, cudaEvent_t mid,
-                 cudaStream_t s);
+                 const uint32_t* chunk_end, const int* kexp, double* head, int64_t ldh,
+                 float* E, int64_t ldE, int* err, const double* kw, float* scratch,
+                 int scratch_slots, cudaEvent_t mid, cudaStream_t s);
 int64_t ek_strip_scratch_floats();  // per SM slot of the 256 x 256 tile kernels
 void launch_nsmid(int* d_out, cudaStream_t s);
 void launch_extract_diag(bool fp64, const void* E, int n, int64_t ldE, double* diag,

@@ -9,6 +9,7 @@
 // The reciprocal sum is split by cos(a - b) = cos a cos b + sin a sin b into A A^T with
 // A[i] = [sqrt(W) cos(K.r_i) | sqrt(W) sin(K.r_i)]: a dense contraction over 2M terms.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include "cpm_internal.cuh"
@@ -46,24 +47,36 @@ __global__ void k_fixed_point_coords(const double* __restrict__ xyz, int n, int 
 // h, k, l times 2^-32-quantised fractional coordinates, wrapping mod 1), then one
 // rounding to float and sincospif.  FP64 operand: fractional coordinates in double,
 // reduced to [-1/2, 1/2] by rint, then sincospi.
-// BF16 planes of the tensor-core build, written with A: a = a0 + a1 + a2, each plane the
-// rounding of the remainder of the previous; K-block b (64 columns) needs plane 0 from
-// kb0 on, plane 1 below kb3 and plane 2 below kb6 (the weight-bounded product schedule).
+// 16-bit planes of the tensor-core build, written with A (the weight-bounded product
+// schedule of K-block b, 64 columns):
+//   kb0 <= b < kb6: BF16, a = a0 + a1 + a2, each plane the rounding of the remainder of
+//     the previous (six products);
+//   kb6 <= b: FP16 of the block's power-of-two scaled value x = 2^kexp[b] a (|x| < 1),
+//     x = h0 + h1 below kb3 (three products), h0 alone from kb3 on (one product).
+// FP16 keeps 11 bits a plane against BF16's 8, so two planes and three products hold
+// ~2^-21 of each product where BF16 needs six; its narrow exponent range is what the
+// per-block scale is for.
 struct PlaneOut {
-  __nv_bfloat16* p[3];
+  uint16_t* p[3];
+  const int* kexp;  // per K-block
   int kb0, kb6, kb3;
 };
 
 __device__ __forceinline__ void write_planes(const PlaneOut& po, size_t e, int b, float a) {
   if (b < po.kb0) return;
+  if (b >= po.kb6) {
+    const float x = ldexpf(a, po.kexp[b]);  // exact: a power of two
+    const __half h0 = __float2half_rn(x);
+    po.p[0][e] = __half_as_ushort(h0);
+    if (b < po.kb3) po.p[1][e] = __half_as_ushort(__float2half_rn(x - __half2float(h0)));
+    return;
+  }
   const __nv_bfloat16 b0 = __float2bfloat16_rn(a);
-  po.p[0][e] = b0;
-  if (b >= po.kb3) return;
+  po.p[0][e] = __bfloat16_as_ushort(b0);
   const float r1 = a - __bfloat162float(b0);
   const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
-  po.p[1][e] = b1;
-  if (b >= po.kb6) return;
-  po.p[2][e] = __float2bfloat16_rn(r1 - __bfloat162float(b1));
+  po.p[1][e] = __bfloat16_as_ushort(b1);
+  po.p[2][e] = __bfloat16_as_ushort(__float2bfloat16_rn(r1 - __bfloat162float(b1)));
 }
 
 // A (lda = 2 mpad) and, with PLANES, the BF16 planes for the k-vectors [kbeg, kend)
@@ -482,7 +495,8 @@ void launch_structure_operand_head(const double* xyz, int npad, int n, const int
 void launch_structure_operand(bool fp64, const double* xyz, const uint32_t* sfix, int npad,
                               int n, const int* hkl, const double* sqw, int mpad,
                               const double L[3], void* A, void* const* planes, int kb0,
-                              int kb6, int kb3, int kbeg, int kend, cudaStream_t s) {
+                              int kb6, int kb3, const int* kexp, int kbeg, int kend,
+                              cudaStream_t s) {
   dim3 grid((kend - kbeg + 127) / 128, npad < 1024 ? npad : 1024);
   PlaneOut po{};
   if (fp64) {
@@ -490,7 +504,8 @@ void launch_structure_operand(bool fp64, const double* xyz, const uint32_t* sfix
     (k_structure_operand_f64<<<g64, 128, 0, s>>>(xyz, npad, n, hkl, sqw, mpad, L[0], L[1],
                                                 L[2], (double*)A), note_launch());
   } else if (planes) {
-    for (int t = 0; t < 3; ++t) po.p[t] = (__nv_bfloat16*)planes[t];
+    for (int t = 0; t < 3; ++t) po.p[t] = (uint16_t*)planes[t];
+    po.kexp = kexp;
     po.kb0 = kb0;
     po.kb6 = kb6;
     po.kb3 = kb3;

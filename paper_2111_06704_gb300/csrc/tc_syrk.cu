@@ -1,30 +1,27 @@
 // k-space part of E on the tcgen05 tensor cores (sm_103a): E_k = A A^T over the light
-// tail of the k-vector table, with a BF16 split of each operand.
+// tail of the k-vector table, from 16-bit planes of each FP32 operand value.
 //
-// Each FP32 operand value a = a0 + a1 + a2 (BF16 planes, a1 and a2 the successive
-// rounding remainders), and
-//   a b^T ~= a0 b0 + a0 b1 + a1 b0 + a0 b2 + a1 b1 + a2 b0      (six BF16 products),
-// which keeps ~24 bits of each product; BF16 x BF16 products are exact in the FP32
-// accumulator.  The heaviest k-vectors (the head) are summed in FP64 by a SIMT kernel
-// beforehand; this kernel adds the tail.  The k-vectors are sorted by decreasing weight
-// W_K and every product of a column is bounded by its W_K, so the far tail needs fewer
-// bits: the host picks, per 64-column K-block, six products, three (a0 b0 + a0 b1 +
-// a1 b0, within 3 * 2^-16 of |ab|) or one (a0 b0, within 2^-7), such that the summed
-// weight of each reduced group times its bound stays below 1e-8 (E entries are O(1)).
+// The heaviest k-vectors (the head) are summed in FP64 by a SIMT kernel beforehand; these
+// kernels add the tail.  The k-vectors are sorted by decreasing weight W_K and every
+// product of a column is bounded by its W_K, so the tail needs fewer bits as it goes; the
+// host picks per 64-column K-block (a cos or sin half of 64 k-vectors):
+//   six BF16 products a0 b0 + a0 b1 + a1 b0 + a0 b2 + a1 b1 + a2 b0 (a = a0 + a1 + a2,
+//     ~2^-24 of each product), for the heavier part;
+//   three FP16 products h0 g0 + h0 g1 + h1 g0 of the block's power-of-two scaled values
+//     (x = h0 + h1, within 5 x 2^-22), or one, h0 g0 (within 2^-10 + 2^-23),
+// such that each reduced group's summed weight times its bound stays below 1e-8 (E
+// entries are O(1)).  BF16 x BF16 and FP16 x FP16 products are exact in the FP32
+// accumulator.
 //
-// Tile: 128 x 128 outputs of the lower triangle per CTA (cta_group::1, M = N = 128).
-// Warp roles: warp 0 issues TMA loads of the 128 x 64 BF16 tiles (128-byte swizzle) into
-// a 2-stage shared-memory ring of six tile slots per stage: one six-product K-block (A0
-// A1 A2 B0 B1 B2), one three-product block (A0 A1 B0 B1) or up to three one-product
-// blocks (A0 B0 each); warp 1 issues the MMAs (one thread); warps 2-5 drain the
-// accumulator.  TMEM (512 columns): two FP32 accumulators (ping-pong) and a hi/lo float
-// pair per output.  After each accumulation chunk (one or more K-blocks, schedule from
-// the host) the epilogue adds the chunk into hi/lo with an error-free two-sum, so FP32
-// rounding only touches chunk sums of light terms.  The final drain adds the FP64 head
-// and writes the float E tile.
+// Tiles of 256 x 256 outputs of the lower triangle, one CTA each; warp roles: TMA
+// producer, single-thread MMA issuer, eight epilogue warps.  All 512 TMEM columns hold
+// two M = 128, N = 256 FP32 accumulators.  After each accumulation chunk of the host's
+// schedule the MMAs pause while the epilogue adds the accumulator (times the chunk's
+// scale) into the tile's running hi / lo floats by an error-free two-sum; the last chunk
+// adds hi + lo + the accumulator to the FP64 head and writes float E (or FP64 head).
 //
 // Every wait is bounded: on timeout the kernel records an error code and leaves; the
-// host reports CPM_ECUDA-class failure instead of hanging.
+// host reports a CPM_ECUDA-class failure instead of hanging.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -42,19 +39,6 @@ namespace {
 
 constexpr int kTile = 128;           // output tile edge
 constexpr int kBlockK = 64;          // operand columns per K-block of the schedule
-constexpr int kRingBytes = 192 * 1024;
-
-// Loads and MMAs go by sub-blocks of BK columns: BK = 64 (128-byte swizzle, two 96 KB
-// stages) or BK = 32 (64-byte swizzle, four 48 KB stages: the same bytes in flight,
-// refilled at half the granularity).
-template <int BK>
-struct TcCfg {
-  static constexpr int kSub = kBlockK / BK;            // sub-blocks per K-block
-  static constexpr int kTileBytes = kTile * BK * 2;    // one 128 x BK BF16 tile
-  static constexpr int kStageBytes = 6 * kTileBytes;   // six tile slots
-  static constexpr int kStages = kRingBytes / kStageBytes;
-};
-constexpr int kThreads = 192;                         // 6 warps
 constexpr long long kWaitCycles = 20000000000ll;      // ~10 s at 2 GHz: wait limit
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -126,15 +110,19 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = N = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTile >> 3) << 17) |
-                            ((uint32_t)(kTile >> 4) << 24);
+// Instruction descriptor, kind::f16: D = F32, A and B both K-major, M = 128, N = n;
+// operand type BF16 (bf16 = true) or FP16.
+__host__ __device__ constexpr uint32_t idesc_f16(bool bf16, int n) {
+  return (1u << 4) | (bf16 ? (1u << 7) | (1u << 10) : 0u) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(kTile >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -163,23 +151,9 @@ __device__ __forceinline__ void tc_fence_after() {
         "=r"(r[31])                                                                          \
       : "r"(taddr))
 
-#define TMEM_ST32(taddr, r)                                                                  \
-  asm volatile(                                                                              \
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12," \
-      "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"     \
-      ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]),        \
-      "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]),        \
-      "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]),    \
-      "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]),    \
-      "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31]))
-
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
-__device__ __forceinline__ void tmem_wait_st() {
-  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-}
-
 __device__ __forceinline__ void tri_tile(int t, int& I, int& J) {
   int r = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
   while ((r + 1) * (r + 2) / 2 <= t) ++r;
@@ -188,300 +162,33 @@ __device__ __forceinline__ void tri_tile(int t, int& I, int& J) {
   J = t - r * (r + 1) / 2;
 }
 
-struct TcArgs {
-  int n;
-  int kb_begin;   // first K-block of the tail
-  int kb_end;     // one past the last K-block
-  int kb6_end;    // K-blocks before this take six products,
-  int kb3_end;    // then three up to this one, then one
-  const uint32_t* chunk_end;  // bit per K-block: an accumulation chunk ends after it
-  int kb_col0;                // the operand planes start at this K-block
-  double* head;               // [n][ldh] FP64 head + real-space terms (lower triangle)
-  int64_t ldh;
-  float* E;
-  int64_t ldE;
-  int* err;
-  int diag_exact;  // the diagonal takes w_diag in place of its accumulated sum
-  double w_diag;   // sum of W_K over the launch's k-vectors (cos^2 + sin^2 = 1)
-};
-
-// Sub-blocks (of BK columns) held by the ring stage that starts at relative sub-block sb,
-// and their product count (from the schedule block they belong to): one six- or
-// three-product sub-block, or up to three one-product sub-blocks.
-template <int BK>
-__device__ __forceinline__ int stage_blocks(const TcArgs& a, int sb, int nsb, int& prods) {
-  const int g = (a.kb_begin * TcCfg<BK>::kSub + sb) / TcCfg<BK>::kSub;
-  if (g < a.kb6_end) {
-    prods = 6;
-    return 1;
-  }
-  if (g < a.kb3_end) {
-    prods = 3;
-    return 1;
-  }
-  prods = 1;
-  return min(3, nsb - sb);
-}
-
-template <int BK>
-__global__ void __launch_bounds__(kThreads, 1)
-k_ek_tc(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1,
-        const __grid_constant__ CUtensorMap map2, TcArgs args) {
-  constexpr int kSub = TcCfg<BK>::kSub, kStages = TcCfg<BK>::kStages;
-  constexpr int kPlaneTileBytes = TcCfg<BK>::kTileBytes, kStageBytes = TcCfg<BK>::kStageBytes;
-  extern __shared__ __align__(1024) uint8_t smem_raw[];
-  // 1024-byte aligned ring of kStages x 6 tiles
-  uint8_t* ring = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages];
-  __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
-  __shared__ uint32_t tmem_base_s;
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int I, J;
-  tri_tile(blockIdx.x, I, J);
-  const int i0 = I * kTile, j0 = J * kTile;
-  const int nkb = args.kb_end - args.kb_begin;       // schedule blocks (epilogue chunks)
-  const int nsb = nkb * kSub;                         // sub-blocks (loads and MMAs)
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(&full_bar[s], 1);
-      mbar_init(&empty_bar[s], 1);
-    }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 4);
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
-                     smem_addr(&tmem_base_s))
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = tmem_base_s;
-
-  if (warp == 0) {
-    // ---- TMA producer ------------------------------------------------------------
-    if (lane == 0) {
-      int stage = 0;
-      for (int kb = 0; kb < nsb; ++stage) {  // kb: relative sub-block
-        const int s = stage % kStages;
-        if (!mbar_wait(&empty_bar[s], ((stage / kStages) & 1) ^ 1, args.err, 1)) break;
-        uint8_t* st = ring + s * kStageBytes;
-        int prods;
-        const int cnt = stage_blocks<BK>(args, kb, nsb, prods);
-        const int x = ((args.kb_begin - args.kb_col0) * kSub + kb) * BK;
-        if (prods == 6) {
-          mbar_expect_tx(&full_bar[s], 6 * kPlaneTileBytes);
-          tma_load_2d(st + 0 * kPlaneTileBytes, &map0, &full_bar[s], x, i0);
-          tma_load_2d(st + 1 * kPlaneTileBytes, &map1, &full_bar[s], x, i0);
-          tma_load_2d(st + 2 * kPlaneTileBytes, &map2, &full_bar[s], x, i0);
-          tma_load_2d(st + 3 * kPlaneTileBytes, &map0, &full_bar[s], x, j0);
-          tma_load_2d(st + 4 * kPlaneTileBytes, &map1, &full_bar[s], x, j0);
-          tma_load_2d(st + 5 * kPlaneTileBytes, &map2, &full_bar[s], x, j0);
-        } else if (prods == 3) {
-          mbar_expect_tx(&full_bar[s], 4 * kPlaneTileBytes);
-          tma_load_2d(st + 0 * kPlaneTileBytes, &map0, &full_bar[s], x, i0);
-          tma_load_2d(st + 1 * kPlaneTileBytes, &map1, &full_bar[s], x, i0);
-          tma_load_2d(st + 2 * kPlaneTileBytes, &map0, &full_bar[s], x, j0);
-          tma_load_2d(st + 3 * kPlaneTileBytes, &map1, &full_bar[s], x, j0);
-        } else {
-          mbar_expect_tx(&full_bar[s], 2 * cnt * kPlaneTileBytes);
-          for (int u = 0; u < cnt; ++u) {
-            tma_load_2d(st + (2 * u) * kPlaneTileBytes, &map0, &full_bar[s], x + u * BK, i0);
-            tma_load_2d(st + (2 * u + 1) * kPlaneTileBytes, &map0, &full_bar[s], x + u * BK, j0);
-          }
-        }
-        kb += cnt;
-      }
-    }
-  } else if (warp == 1) {
-    // ---- MMA issuer ----------------------------------------------------------------
-    if (lane == 0) {
-      // products (p, q) with p + q <= 2, in the order (0,0) (0,1) (1,0) (0,2) (1,1) (2,0):
-      // A plane p (rows i), B plane q (rows j); the three- and one-product forms are the
-      // first three and the first one
-      constexpr uint32_t kPa = 0x210100u, kPb = 0x012010u;  // nibble t: plane of product t
-      int chunk = 0;
-      bool first_in_chunk = true;
-      bool ok = true;
-      int stage = 0;
-      for (int kb = 0; kb < nsb && ok; ++stage) {  // kb: relative sub-block
-        const int s = stage % kStages;
-        int prods;
-        const int cnt = stage_blocks<BK>(args, kb, nsb, prods);
-        ok = mbar_wait(&full_bar[s], (stage / kStages) & 1, args.err, 3);
-        if (!ok) break;
-        tc_fence_after();
-        const uint32_t st = smem_addr(ring + s * kStageBytes);
-        for (int u = 0; u < cnt; ++u) {
-          const int buf = chunk & 1;
-          if (first_in_chunk) {
-            ok = mbar_wait(&acc_empty[buf], ((chunk >> 1) & 1) ^ 1, args.err, 2);
-            if (!ok) break;
-            tc_fence_after();
-          }
-          // tile slots of this block: A planes from slot sa, B planes from slot sb
-          const int sa = prods == 1 ? 2 * u : 0;
-          const int sb = prods == 6 ? 3 : prods == 3 ? 2 : 2 * u + 1;
-          const uint32_t d = tmem + (uint32_t)(buf * kTile);
-#pragma unroll
-          for (int ks = 0; ks < BK / 16; ++ks) {
-            for (int t = 0; t < prods; ++t) {
-              const int pa = (kPa >> (4 * t)) & 15, pb = (kPb >> (4 * t)) & 15;
-              const uint64_t da = smem_desc<BK>(st + (sa + pa) * kPlaneTileBytes + ks * 32);
-              const uint64_t db = smem_desc<BK>(st + (sb + pb) * kPlaneTileBytes + ks * 32);
-              mma_bf16(d, da, db, (first_in_chunk && ks == 0 && t == 0) ? 0u : 1u);
-            }
-          }
-          first_in_chunk = false;
-          // an accumulation chunk ends with the last sub-block of a schedule block whose
-          // chunk bit is set, or with the launch's last sub-block
-          const int gs = args.kb_begin * kSub + kb + u;
-          const int g = gs / kSub;
-          const bool last = (kb + u + 1 == nsb) ||
-                            (gs % kSub == kSub - 1 && ((args.chunk_end[g >> 5] >> (g & 31)) & 1u));
-          if (last) {
-            mma_commit(&acc_full[buf]);
-            ++chunk;
-            first_in_chunk = true;
-          }
-        }
-        if (!ok) break;
-        mma_commit(&empty_bar[s]);  // frees the stage once these MMAs have read it
-        kb += cnt;
-      }
-    }
-  } else {
-    // ---- epilogue: warps 2-5, TMEM lane quarter q = warp % 4 ------------------------
-    const int q = warp & 3;
-    const int row = i0 + 32 * q + lane;
-    const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-    int chunk = 0;
-    int kb = 0;
-    bool ok = true;
-    while (kb < nkb && ok) {
-      // find the end of this chunk (same rule as the MMA warp)
-      int kb_last = kb;
-      while (true) {
-        const int g = args.kb_begin + kb_last;
-        if (kb_last + 1 == nkb || ((args.chunk_end[g >> 5] >> (g & 31)) & 1u)) break;
-        ++kb_last;
-      }
-      const bool final_chunk = kb_last + 1 == nkb;
-      const int buf = chunk & 1;
-      ok = mbar_wait(&acc_full[buf], (chunk >> 1) & 1, args.err, 4);
-      if (!ok) break;
-      tc_fence_after();
-#pragma unroll 1
-      for (int cg = 0; cg < kTile / 32; ++cg) {
-        uint32_t acc[32], hi[32], lo[32];
-        const uint32_t col = (uint32_t)(cg * 32);
-        TMEM_LD32(tmem + lane_base + buf * kTile + col, acc);
-        if (chunk > 0) {
-          TMEM_LD32(tmem + lane_base + 2 * kTile + col, hi);
-          TMEM_LD32(tmem + lane_base + 3 * kTile + col, lo);
-        }
-        tmem_wait_ld();
-#pragma unroll
-        for (int t = 0; t < 32; ++t) {
-          const float a = __uint_as_float(acc[t]);
-          float h = 0.f, l = 0.f;
-          if (chunk > 0) {
-            h = __uint_as_float(hi[t]);
-            l = __uint_as_float(lo[t]);
-          }
-          // two-sum: h + a = s + e exactly
-          const float s = __fadd_rn(h, a);
-          const float bb = __fsub_rn(s, h);
-          const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(a, bb));
-          hi[t] = __float_as_uint(s);
-          lo[t] = __float_as_uint(__fadd_rn(l, e));
-        }
-        if (final_chunk) {
-          if (row < args.n) {
-#pragma unroll
-            for (int t = 0; t < 32; ++t) {
-              const int j = j0 + cg * 32 + t;
-              if (j < args.n && j <= row) {
-                double* hp = args.head + (int64_t)row * args.ldh + j;
-                const double tail = args.diag_exact && j == row
-                                        ? args.w_diag
-                                        : (double)__uint_as_float(hi[t]) + (double)__uint_as_float(lo[t]);
-                const double v = tail + *hp;
-                if (args.E) args.E[(int64_t)row * args.ldE + j] = (float)v;
-                else *hp = v;  // a K-window of a streamed build: carry the sum in FP64
-              }
-            }
-          }
-        } else {
-          TMEM_ST32(tmem + lane_base + 2 * kTile + col, hi);
-          TMEM_ST32(tmem + lane_base + 3 * kTile + col, lo);
-        }
-      }
-      tmem_wait_st();
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty[buf]);
-      ++chunk;
-      kb = kb_last + 1;
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 0) {
-    tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem)
-                 : "memory");
-  }
-}
-
-// ---- 256 x 256 tiles, FP32 accumulation ----------------------------------------------
+// ---- the tile kernel ------------------------------------------------------------------
 //
 // The whole of TMEM holds one 256 x 256 output tile: two M = 128, N = 256 accumulators
-// (rows i0 .. i0 + 127 and i0 + 128 .. i0 + 255).  Twice the tile edge of k_ek_tc halves
-// the operand bytes per MMA, which is what limits these stages; the price is that no TMEM
-// is left for a second accumulator or hi/lo pairs.
-//   SIX = false: three-product stages (32 columns of planes 0 and 1 for 256 rows and 256
-//     columns, 64 KB, 12 MMAs of 128 x 256 x 16) then one-product stages (64 columns of
-//     plane 0, 64 KB, 8 MMAs); three 64 KB stages in flight.  The summed weight of these
-//     K-blocks is small (each reduced group's weight times its product bound stays below
-//     1e-8): one FP32 accumulation over the launch.
-//   SIX = true: six-product stages (32 columns of planes 0-2, 96 KB, 24 MMAs); two stages.
-//     FP32 accumulation error grows with the terms added and their size (the tensor-core
-//     adds lose ~0.1 ulp on average, not centred), so after each accumulation chunk of
-//     the host's schedule the MMAs pause while the epilogue adds the accumulator, by an
-//     error-free two-sum, into the tile's running hi / lo floats: 512 KB per CTA of global
-//     scratch, each thread's entries laid out for whole-warp 512-byte accesses, small
-//     enough for the whole grid's to stay in L2.  The FP64 head is touched once per tile.
-// Off the diagonal the k-space terms oscillate in sign; the diagonal, where every term is
-// positive, takes the exact FP64 weight sum instead (range_weight).  Eight epilogue
-// warps: TMEM lane quarter warp % 4, column half (warp - 2) / 4.
+// (rows i0 .. i0 + 127 and i0 + 128 .. i0 + 255); against 128 x 128 tiles this halves the
+// operand bytes per MMA, which is what limits these stages.
+//   SIX = true (BF16, the six-product K-blocks): stages of 32 columns of planes 0-2 for the
+//     tile's 256 rows and 256 columns (96 KB, 24 MMAs of 128 x 256 x 16); two stages.
+//   SIX = false (FP16): three-product stages (32 columns of planes 0 and 1, 64 KB, 12 MMAs)
+//     then one-product stages (64 columns of plane 0, 64 KB, 8 MMAs); three stages.
+// The tensor cores' FP32 adds lose ~0.1 ulp each on average, not centred, so the
+// accumulator is drained after each accumulation chunk: the MMAs pause while the
+// epilogue adds it, by an error-free two-sum, into the tile's running hi / lo floats in
+// the SM's 512 KB scratch slot (each thread's entries laid out for whole-warp 512-byte
+// accesses; small enough for all SMs' slots to stay in L2).  The FP64 head is touched
+// once per tile.  Off the diagonal the k-space terms oscillate in sign; the diagonal,
+// where every term is positive, takes the exact FP64 weight sum (range_weight).  Eight
+// epilogue warps: TMEM lane quarter warp % 4, column half (warp - 2) / 4.
 constexpr int kStripTile = 256;
 constexpr int kStripThreads = 320;  // 10 warps: TMA, MMA, 8 epilogue
-constexpr uint32_t kIdescN256 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(256 >> 3) << 17) |
-                                ((uint32_t)(kTile >> 4) << 24);
 
 template <bool SIX>
 struct StripCfg {
   static constexpr int kStages = SIX ? 2 : 3;
   static constexpr int kStageBytes = (SIX ? 96 : 64) * 1024;
   static constexpr int kPlanes = SIX ? 3 : 2;   // planes of a narrow (32-column) stage
-  static constexpr int kProds = SIX ? 6 : 3;    // BF16 products of a narrow stage
+  static constexpr int kProds = SIX ? 6 : 3;    // products of a narrow stage
 };
-
-__device__ __forceinline__ void mma_bf16_id(uint32_t d_tmem, uint64_t a, uint64_t b,
-                                            uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
 
 struct StripArgs {
   int n, npad;
@@ -490,8 +197,9 @@ struct StripArgs {
   int kb_end;     // one past the last K-block
   int kb3_end;    // SIX = false: K-blocks before this take three products, the rest one
   int kb_col0;    // the operand planes start at this K-block
-  const uint32_t* chunk_end;  // SIX: bit per K-block, an accumulation chunk ends after it
-  float* scratch; // SIX: per SM 2 x 65,536 floats (the tile's running hi / lo sums)
+  const uint32_t* chunk_end;  // bit per K-block: an accumulation chunk ends after it
+  const int* kexp;            // per K-block: FP16 blocks hold 2^kexp a (0 for BF16 blocks)
+  float* scratch; // per SM 2 x 65,536 floats (the tile's running hi / lo sums)
   int scratch_slots;  // SM slots in scratch (%nsmid)
   double* head;   // [n][ldh] FP64 head + everything before kb_begin (lower triangle)
   int64_t ldh;
@@ -594,13 +302,22 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
                : max(0, min(args.kb_end, args.kb3_end) - args.kb_begin));
   const int kb1 = max(args.kb_begin, args.kb3_end);
   const int nst = nnarrow + (SIX ? 0 : max(0, args.kb_end - kb1));
-  // an accumulation chunk ends with stage t: the tile's last stage, or (SIX) the second
-  // half of a K-block whose chunk bit is set
+  // K-block of stage t, and whether stage t is its last
+  auto stage_block = [&](int t, bool& last_of_block) {
+    if (t < nnarrow) {
+      last_of_block = (t & 1) != 0;
+      return args.kb_begin + t / 2;
+    }
+    last_of_block = true;
+    return kb1 + (t - nnarrow);
+  };
+  // an accumulation chunk ends with stage t: the tile's last stage, or the last stage of
+  // a K-block whose chunk bit is set
   auto chunk_ends = [&](int t) {
     if (t + 1 == nst) return true;
-    if (!SIX || !(t & 1)) return false;
-    const int g = args.kb_begin + t / 2;
-    return ((args.chunk_end[g >> 5] >> (g & 31)) & 1u) != 0u;
+    bool last;
+    const int g = stage_block(t, last);
+    return last && ((args.chunk_end[g >> 5] >> (g & 31)) & 1u) != 0u;
   };
 
   if (threadIdx.x == 0) {
@@ -673,7 +390,8 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
       for (int tile = blockIdx.x; tile < args.tiles && ok; tile += gridDim.x) {
         const StripTile tg(tile, args.npad);
         // on a diagonal tile the first row half needs only the first 128 columns
-        const uint32_t id0 = tg.diag ? kIdesc : kIdescN256;
+        constexpr uint32_t kId256 = idesc_f16(SIX, 256), kId128 = idesc_f16(SIX, 128);
+        const uint32_t id0 = tg.diag ? kId128 : kId256;
         bool first = true;  // first stage of an accumulation chunk
         for (int t = 0; t < nst; ++t, ++g) {
           const int s = g % kStages;
@@ -694,7 +412,7 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
                   const int pa = (kPa >> (4 * p)) & 15, pb = (kPb >> (4 * p)) & 15;
                   const uint64_t da = smem_desc<32>(st + (2 * pa + r) * kNarrow + ks * 32);
                   const uint64_t db = smem_desc<32>(st + (2 * P + 2 * pb) * kNarrow + ks * 32);
-                  mma_bf16_id(tmem + (uint32_t)(r * 256), da, db, r == 0 ? id0 : kIdescN256,
+                  mma_f16(tmem + (uint32_t)(r * 256), da, db, r == 0 ? id0 : kId256,
                               (first && ks == 0 && p == 0) ? 0u : 1u);
                 }
           } else {
@@ -703,7 +421,7 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
               for (int r = 0; r < tg.rb; ++r) {
                 const uint64_t da = smem_desc<64>(st + r * kWide + ks * 32);
                 const uint64_t db = smem_desc<64>(st + 2 * kWide + ks * 32);
-                mma_bf16_id(tmem + (uint32_t)(r * 256), da, db, r == 0 ? id0 : kIdescN256,
+                mma_f16(tmem + (uint32_t)(r * 256), da, db, r == 0 ? id0 : kId256,
                             (first && ks == 0) ? 0u : 1u);
               }
           }
@@ -719,15 +437,16 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
     }
   } else {
     // ---- epilogue: warps 2-9, TMEM lane quarter q = warp % 4, column half h ---------
-    // A chunk before a tile's last goes, by an error-free two-sum, into the tile's running
-    // hi / lo floats in this CTA's scratch (each thread its own 8 x 32 entries, laid out so
-    // that a warp's accesses are contiguous); the last chunk adds hi + lo + acc to head.
+    // A chunk before a tile's last goes, times 2^-2kexp (exact), by an error-free two-sum
+    // into the tile's running hi / lo floats in the SM's scratch slot (each thread its
+    // own 8 x 32 entries, laid out so that a warp's accesses are contiguous); the last
+    // chunk adds hi + lo + acc to head.
     const int q = warp & 3, h = (warp - 2) >> 2, ew = warp - 2;
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
     float4* hi4 = nullptr;
     float4* lo4 = nullptr;
     bool ok = true;
-    if (SIX) {
+    {
       uint32_t smid;
       asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
       if ((int)smid < args.scratch_slots) {
@@ -747,6 +466,8 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
         int t1 = t0;
         while (!chunk_ends(t1)) ++t1;
         const bool final_chunk = t1 + 1 == nst;
+        bool unused;
+        const float scale = __int_as_float((127 - 2 * args.kexp[stage_block(t0, unused)]) << 23);
         ok = mbar_wait(&acc_full, chunk & 1, args.err, 14);
         if (!ok) break;
         tc_fence_after();
@@ -763,7 +484,7 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
             const int grp = (r * 4 + cl) * 8 * 32;  // float4 offset of this group
             if (final_chunk) {
               double tail[32];
-              if (SIX && ci > 0) {
+              if (ci > 0) {
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                   const float4 hv = hi4[grp + u * 32], lv = lo4[grp + u * 32];
@@ -773,10 +494,10 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
                   tail[4 * u + 3] = (double)hv.w + (double)lv.w;
                 }
 #pragma unroll
-                for (int t = 0; t < 32; ++t) tail[t] += (double)__uint_as_float(acc[t]);
+                for (int t = 0; t < 32; ++t) tail[t] += (double)(__uint_as_float(acc[t]) * scale);
               } else {
 #pragma unroll
-                for (int t = 0; t < 32; ++t) tail[t] = (double)__uint_as_float(acc[t]);
+                for (int t = 0; t < 32; ++t) tail[t] = (double)(__uint_as_float(acc[t]) * scale);
               }
               if (row < args.n) strip_final(args, tail, row, tg.j0 + cg * 32);
             } else {
@@ -795,7 +516,7 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
 #pragma unroll
               for (int t = 0; t < 32; ++t) {
                 // two-sum: hv + a = s + e exactly
-                const float a = __uint_as_float(acc[t]);
+                const float a = __uint_as_float(acc[t]) * scale;
                 const float s = __fadd_rn(hv[t], a);
                 const float bb = __fsub_rn(s, hv[t]);
                 const float e = __fadd_rn(__fsub_rn(hv[t], __fsub_rn(s, bb)), __fsub_rn(a, bb));
@@ -897,105 +618,66 @@ void launch_nsmid(int* d_out, cudaStream_t s) {
   note_launch();
 }
 
-// K-blocks [kb_begin, kb_end) of the lower triangle from BF16 planes holding the K-blocks
-// kb_col0 .. kb_col0 + plane_cols / 64; the result plus head goes to float E, or back into
-// head (FP64) when E is null.  Two launches, the first adding its K-range to head and the
-// second writing E: the six-product K-blocks, then the three- and one-product ones, both
-// on 256 x 256 tiles (k_ek_strip).  CPM_TC_STRIP=0 in the environment runs the whole range
-// on 128 x 128 tiles with TMEM two-sum drains instead (k_ek_tc).  `mid`, when given, is
-// recorded before the light launch.
+// K-blocks [kb_begin, kb_end) of the lower triangle from the 16-bit planes holding the
+// K-blocks kb_col0 .. kb_col0 + plane_cols / 64; the result plus head goes to float E, or
+// back into head (FP64) when E is null.  Two launches, the first adding its K-range to
+// head and the second writing E: the six-product (BF16) K-blocks, then the three- and
+// one-product (FP16) ones.  `mid`, when given, is recorded before the second.
 int launch_ek_tc(const void* p0, const void* p1, const void* p2, int npad, int64_t plane_cols,
                  int kb_col0, int n, int kb_begin, int kb_end, int kb6_end, int kb3_end,
-                 const uint32_t* chunk_end, double* head, int64_t ldh, float* E, int64_t ldE,
-                 int* err, const double* kw, float* scratch, int scratch_slots, cudaEvent_t mid,
-                 cudaStream_t s) {
-  const char* env = getenv("CPM_TC_BK");
-  const int bk = env && atoi(env) == 32 ? 32 : 64;
-  const char* env_strip = getenv("CPM_TC_STRIP");
-  const bool strip = !(env_strip && atoi(env_strip) == 0);
-  CUtensorMap m0, m1, m2, m0n, m1n, m2n;
-  if (!make_map(&m0, p0, npad, plane_cols, bk) || !make_map(&m1, p1, npad, plane_cols, bk) ||
-      !make_map(&m2, p2, npad, plane_cols, bk) || !make_map(&m0n, p0, npad, plane_cols, 32) ||
+                 const uint32_t* chunk_end, const int* kexp, double* head, int64_t ldh,
+                 float* E, int64_t ldE, int* err, const double* kw, float* scratch,
+                 int scratch_slots, cudaEvent_t mid, cudaStream_t s) {
+  if (!scratch || scratch_slots < 1 || (kb6_end & 1) || (kb_begin & 1)) return CPM_EINVAL;
+  CUtensorMap m0, m0n, m1n, m2n;
+  if (!make_map(&m0, p0, npad, plane_cols, 64) || !make_map(&m0n, p0, npad, plane_cols, 32) ||
       !make_map(&m1n, p1, npad, plane_cols, 32) || !make_map(&m2n, p2, npad, plane_cols, 32))
     return CPM_ECUDA;
-  const int smem = kRingBytes + 1024;
   const int smem6 = StripCfg<true>::kStages * StripCfg<true>::kStageBytes + 1024;
   const int smem31 = StripCfg<false>::kStages * StripCfg<false>::kStageBytes + 1024;
-  if (cudaFuncSetAttribute(k_ek_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(k_ek_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(k_ek_strip<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(k_ek_strip<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            smem6) != cudaSuccess ||
       cudaFuncSetAttribute(k_ek_strip<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            smem31) != cudaSuccess)
     return CPM_ECUDA;
-  // segments: kind 0 = k_ek_tc, 1 = six-product 256-tiles, 2 = light 256-tiles; the
-  // boundary is kept even so that each segment holds whole [cos | sin] block pairs
-  struct Seg {
-    int kind, b, e;
-  };
-  Seg seg[2];
-  int nseg = 0;
-  const int x6_end = strip ? std::min(kb_end, (kb6_end + 1) & ~1) : kb_end;
-  if (kb_begin < x6_end) seg[nseg++] = {strip ? 1 : 0, kb_begin, x6_end};
-  const int s_begin = std::max(kb_begin, x6_end);
-  const int first_light = nseg;
-  if (s_begin < kb_end) seg[nseg++] = {2, s_begin, kb_end};
-  for (int q = 0; q < nseg; ++q) {
-    float* Eq = q + 1 == nseg ? E : nullptr;
-    if (q == first_light && mid) cudaEventRecord(mid, s);
-    if (seg[q].kind == 0) {
-      TcArgs a;
-      a.n = n;
-      a.kb_begin = seg[q].b;
-      a.kb_end = seg[q].e;
-      a.kb6_end = kb6_end;
-      a.kb3_end = kb3_end;
-      a.kb_col0 = kb_col0;
-      a.chunk_end = chunk_end;
-      a.head = head;
-      a.ldh = ldh;
-      a.E = Eq;
-      a.ldE = ldE;
-      a.err = err;
-      a.diag_exact = range_weight(kw, seg[q].b, seg[q].e, &a.w_diag);
-      const int nt = (n + kTile - 1) / kTile;
-      const int tiles = nt * (nt + 1) / 2;
-      if (bk == 32) (k_ek_tc<32><<<tiles, kThreads, smem, s>>>(m0, m1, m2, a), note_launch());
-      else (k_ek_tc<64><<<tiles, kThreads, smem, s>>>(m0, m1, m2, a), note_launch());
-    } else {
-      StripArgs a;
-      a.n = n;
-      a.npad = npad;
-      a.scratch = scratch;
-      a.scratch_slots = scratch_slots;
-      a.kb_begin = seg[q].b;
-      a.kb_end = seg[q].e;
-      a.kb3_end = kb3_end;
-      a.kb_col0 = kb_col0;
-      a.chunk_end = chunk_end;
-      a.head = head;
-      a.ldh = ldh;
-      a.E = Eq;
-      a.ldE = ldE;
-      a.err = err;
-      a.diag_exact = range_weight(kw, seg[q].b, seg[q].e, &a.w_diag);
-      const int nt = (n + kStripTile - 1) / kStripTile;
-      a.tiles = nt * (nt + 1) / 2;
-      // one CTA per tile; the hardware hands each SM its next tile as it frees up
-      const int grid = a.tiles;
-      if (seg[q].kind == 1 && (!scratch || scratch_slots < 1)) return CPM_EINVAL;
-      if (seg[q].kind == 1)
-        (k_ek_strip<true><<<grid, kStripThreads, smem6, s>>>(m0, m0n, m1n, m2n, a),
-         note_launch());
-      else
-        (k_ek_strip<false><<<grid, kStripThreads, smem31, s>>>(m0, m0n, m1n, m2n, a),
-         note_launch());
-    }
+  // the six-product part [kb_begin, x6_end) and the rest [l_begin, kb_end); kb6_end is
+  // even, so each part holds whole [cos | sin] block pairs
+  const int x6_end = std::min(kb_end, kb6_end);
+  const int l_begin = std::max(kb_begin, x6_end);
+  const int nt = (n + kStripTile - 1) / kStripTile;
+  StripArgs a;
+  a.n = n;
+  a.npad = npad;
+  a.tiles = nt * (nt + 1) / 2;
+  a.kb3_end = kb3_end;
+  a.kb_col0 = kb_col0;
+  a.chunk_end = chunk_end;
+  a.kexp = kexp;
+  a.scratch = scratch;
+  a.scratch_slots = scratch_slots;
+  a.head = head;
+  a.ldh = ldh;
+  a.ldE = ldE;
+  a.err = err;
+  // one CTA per tile; the hardware hands each SM its next tile as it frees up
+  if (kb_begin < x6_end) {
+    a.kb_begin = kb_begin;
+    a.kb_end = x6_end;
+    a.E = l_begin < kb_end ? nullptr : E;
+    a.diag_exact = range_weight(kw, a.kb_begin, a.kb_end, &a.w_diag);
+    (k_ek_strip<true><<<a.tiles, kStripThreads, smem6, s>>>(m0, m0n, m1n, m2n, a),
+     note_launch());
   }
-  if (first_light == nseg && mid) cudaEventRecord(mid, s);
-  if (nseg == 0 && E)  // nothing of the tail in this window
+  if (mid) cudaEventRecord(mid, s);
+  if (l_begin < kb_end) {
+    a.kb_begin = l_begin;
+    a.kb_end = kb_end;
+    a.E = E;
+    a.diag_exact = range_weight(kw, a.kb_begin, a.kb_end, &a.w_diag);
+    (k_ek_strip<false><<<a.tiles, kStripThreads, smem31, s>>>(m0, m0n, m1n, m2n, a),
+     note_launch());
+  }
+  if (kb_begin >= kb_end && E)  // nothing of the tail in this window
     (k_head_to_float<<<dim3((n + 31) / 32, (n + 31) / 32), dim3(32, 8), 0, s>>>(head, ldh, E,
                                                                               ldE, n),
      note_launch());
