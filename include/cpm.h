@@ -124,9 +124,19 @@ int cpm_destroy(cpm_ctx* c);
  *  - the PCG-DC preconditioner (if selected) and d = d' / (1^T d'), E_n d' = 1.
  * n: electrode atoms (1 <= n).  xyz[n*3]: positions (A).  alpha[n]: Gaussian inverse
  * widths (1/A) of Eq. 4; INFINITY marks a point charge (no self-energy, Sec. II C).
- * Replaces any earlier build on the context.
+ * Replaces any earlier build on the context.  Device buffers of the earlier build are
+ * reused where large enough; the BF16X6 build's workspace (its 16-bit operand planes,
+ * up to 12 bytes per electrode atom and k-vector, the FP64 head matrix of 8 N^2 bytes,
+ * and a 512 KB scratch slot per SM) is kept for the next build until
+ * cpm_release_workspace or cpm_destroy.
  */
 int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha);
+
+/* Frees the context's kept workspace: the E build's (above) and the solve and potential
+ * workspaces, which later calls reserve again as needed.  The built E, P, d and the
+ * operand A stay.  Waits for the context's stream first.  No counterpart in the paper:
+ * device-memory management of this library. */
+int cpm_release_workspace(cpm_ctx* c);
 
 /*
  * b = chi - k_e * b^sol for `frames` electrolyte frames (Eq. 25), in the

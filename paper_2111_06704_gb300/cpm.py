@@ -87,7 +87,7 @@ EXPORTS = ["cpm_default_params", "cpm_create", "cpm_destroy", "cpm_build_E", "cp
            "cpm_mlp_adam", "cpm_guess_apply", "cpm_apply_E", "cpm_get_precond",
            "cpm_last_error", "cpm_batch_create", "cpm_batch_destroy", "cpm_batch_solve",
            "cpm_batch_neutralize", "cpm_batch_last_error", "cpm_get_E_rows",
-           "cpm_guess"]
+           "cpm_guess", "cpm_release_workspace"]
 
 _lib = None
 
@@ -113,6 +113,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.cpm_default_params.restype = None
     lib.cpm_create.argtypes = [P(vp), P(cpm_params)]
     lib.cpm_destroy.argtypes = [vp]
+    lib.cpm_release_workspace.argtypes = [vp]
     lib.cpm_build_E.argtypes = [vp, i, vp, vp]
     lib.cpm_potential.argtypes = [vp, i, i, vp, vp, vp, vp, vp]
     lib.cpm_solve.argtypes = [vp, i, vp, vp, i, d, i, vp, vp]
@@ -215,6 +216,10 @@ class Context:
         if getattr(self, "h", None):
             self.lib.cpm_destroy(self.h)
             self.h = None
+
+    def cpm_release_workspace(self):
+        """Frees the kept build, solve and potential workspaces (E, P, d and A stay)."""
+        self._check(self.lib.cpm_release_workspace(self.h))
 
     def __del__(self):
         try:

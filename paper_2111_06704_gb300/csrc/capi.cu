@@ -163,6 +163,13 @@ void kvector_table(const cpm_params& p, std::vector<int>& hkl, std::vector<doubl
   w.swap(w2);
 }
 
+void release_workspace(Ctx* c) {
+  Buf* ws[] = {&c->tc_planes[0], &c->tc_planes[1], &c->tc_planes[2], &c->tc_head, &c->tc_err,
+               &c->tc_hsplit, &c->tc_scratch, &c->ws_solve, &c->ws_in0, &c->ws_in1, &c->ws_in2,
+               &c->ws_out0, &c->ws_out1, &c->ws_pot, &c->ws_guess, &c->ws_feat};
+  for (Buf* b : ws) buf_free(c, b);
+}
+
 void free_build(Ctx* c) {
   Buf* all[] = {&c->xyz, &c->alpha, &c->sfix, &c->hkl, &c->sqw, &c->flush, &c->chunk_end,
                 &c->kexp,
@@ -171,6 +178,7 @@ void free_build(Ctx* c) {
                 &c->nbr_off, &c->nbr_idx, &c->prow, &c->d, &c->shell_off, &c->shell_members, &c->p_f32,
                 &c->turn};
   for (Buf* b : all) buf_free(c, b);
+  release_workspace(c);
   c->built = false;
   c->shells_ready = false;
 }
@@ -252,19 +260,25 @@ int cpm_destroy(cpm_ctx* c) {
   cudaEventDestroy(c->ev_tc[0]);
   cudaEventDestroy(c->ev_tc[1]);
   cudaEventDestroy(c->ev_tc[2]);
-  Buf* ws[] = {&c->ws_solve, &c->ws_in0, &c->ws_in1, &c->ws_in2, &c->ws_out0, &c->ws_out1,
-               &c->ws_pot, &c->ws_guess, &c->ws_feat};
-  for (Buf* b : ws) buf_free(c, b);
   delete c;
   return CPM_OK;
 }
 
 const char* cpm_last_error(const cpm_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
+int cpm_release_workspace(cpm_ctx* c) {
+  if (!c) return CPM_EINVAL;
+  if (int st = cuda_check(c, cudaStreamSynchronize(c->stream), "release sync")) return st;
+  release_workspace(c);
+  return CPM_OK;
+}
+
 int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
   if (!c) return CPM_EINVAL;
   if (n < 1 || !xyz || !alpha) return set_err(c, CPM_EINVAL, "cpm_build_E: n >= 1 and arrays required");
-  free_build(c);
+  // buffers of the previous build are reused where large enough (reserve), not freed
+  c->built = false;
+  c->shells_ready = false;
   cudaStream_t s = c->stream;
   const bool f64 = c->fp64();
   int st;
@@ -381,19 +395,20 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
   constexpr size_t kResidentOperandBytes = 32ull << 30;
   c->streamed = tc && (c->p.stream_operand == 1 || a_bytes > kResidentOperandBytes);
   const size_t e_bytes = (size_t)n * c->ldE * c->esz();
-  if ((st = buf_alloc(c, &c->xyz, (size_t)n * 3 * sizeof(double))) ||
-      (st = buf_alloc(c, &c->alpha, (size_t)n * sizeof(double))) ||
-      (st = buf_alloc(c, &c->sfix, (size_t)c->npad * 3 * sizeof(uint32_t))) ||
-      (st = buf_alloc(c, &c->hkl, hkl.size() * sizeof(int))) ||
-      (st = buf_alloc(c, &c->sqw, sqw.size() * sizeof(double))) ||
-      (st = buf_alloc(c, &c->flush, fmask.size() * sizeof(uint32_t))) ||
-      (st = buf_alloc(c, &c->chunk_end, cmask.size() * sizeof(uint32_t))) ||
-      (st = buf_alloc(c, &c->kexp, kexp.size() * sizeof(int))) ||
-      (st = buf_alloc(c, &c->Ahead, (size_t)c->npad * 2 * std::max(c->kh, 1) * sizeof(double))) ||
-      (!c->streamed && (st = buf_alloc(c, &c->A, a_bytes))) ||
-      (st = buf_alloc(c, &c->E, e_bytes)) ||
-      (st = buf_alloc(c, &c->diag, 2 * (size_t)n * sizeof(double))) ||
-      (st = buf_alloc(c, &c->d, (size_t)n * sizeof(double)))) {
+  if (c->streamed) buf_free(c, &c->A);
+  if ((st = buf_reserve(c, &c->xyz, (size_t)n * 3 * sizeof(double))) ||
+      (st = buf_reserve(c, &c->alpha, (size_t)n * sizeof(double))) ||
+      (st = buf_reserve(c, &c->sfix, (size_t)c->npad * 3 * sizeof(uint32_t))) ||
+      (st = buf_reserve(c, &c->hkl, hkl.size() * sizeof(int))) ||
+      (st = buf_reserve(c, &c->sqw, sqw.size() * sizeof(double))) ||
+      (st = buf_reserve(c, &c->flush, fmask.size() * sizeof(uint32_t))) ||
+      (st = buf_reserve(c, &c->chunk_end, cmask.size() * sizeof(uint32_t))) ||
+      (st = buf_reserve(c, &c->kexp, kexp.size() * sizeof(int))) ||
+      (st = buf_reserve(c, &c->Ahead, (size_t)c->npad * 2 * std::max(c->kh, 1) * sizeof(double))) ||
+      (!c->streamed && (st = buf_reserve(c, &c->A, a_bytes))) ||
+      (st = buf_reserve(c, &c->E, e_bytes)) ||
+      (st = buf_reserve(c, &c->diag, 2 * (size_t)n * sizeof(double))) ||
+      (st = buf_reserve(c, &c->d, (size_t)n * sizeof(double)))) {
     free_build(c);
     return st;
   }
@@ -420,15 +435,12 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
   cudaEventRecord(ev[0], s);
   launch_fixed_point_coords((const double*)c->xyz.ptr, n, c->npad, c->p.box,
                             (uint32_t*)c->sfix.ptr, s);
-  Buf planes[3], ehead, errbuf, hsplit, tcscratch;
-  int sms = 0;  // SM slots of the tensor-core scratch (%nsmid)
-  auto free_tc = [&]() {
-    buf_free(c, &tcscratch);
-    for (Buf& b : planes) buf_free(c, &b);
-    buf_free(c, &ehead);
-    buf_free(c, &errbuf);
-    buf_free(c, &hsplit);
-  };
+  // the tensor-core workspace stays with the context for the next build (released by
+  // cpm_release_workspace or cpm_destroy, and on a failed build)
+  Buf* planes = c->tc_planes;
+  Buf &ehead = c->tc_head, &errbuf = c->tc_err, &hsplit = c->tc_hsplit,
+      &tcscratch = c->tc_scratch;
+  auto fail_tc = [&]() { release_workspace(c); };
   const int head_cols = 16 * c->heavy_steps;
   // k-vectors whose BF16 planes are held at once: all of them, or in a streamed build a
   // window of ~12 GB of planes (12 bytes per row and k-vector)
@@ -440,19 +452,20 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
                                                                (12ll * c->npad) / 64 * 64));
   if (tc) {
     const size_t pbytes = (size_t)c->npad * 2 * kwin * 2;
-    if ((st = buf_alloc(c, &planes[0], pbytes)) || (st = buf_alloc(c, &planes[1], pbytes)) ||
-        (st = buf_alloc(c, &planes[2], pbytes)) ||
-        (st = buf_alloc(c, &ehead, (size_t)n * c->ldE * sizeof(double))) ||
-        (st = buf_alloc(c, &errbuf, sizeof(int))) ||
-        (launch_nsmid((int*)errbuf.ptr, s),
-         st = cuda_check(c, cudaMemcpyAsync(&sms, errbuf.ptr, sizeof(int), cudaMemcpyDeviceToHost, s),
-                         "nsmid")) ||
-        (st = cuda_check(c, cudaStreamSynchronize(s), "nsmid sync")) ||
-        (sms = std::max(1, std::min(sms, 4096)),
-         st = buf_alloc(c, &tcscratch, (size_t)sms * ek_strip_scratch_floats() * sizeof(float))) ||
-        (st = buf_alloc(c, &hsplit, 2 * (size_t)c->npad * std::max(head_cols, 16) * sizeof(float))) ||
+    if ((st = buf_reserve(c, &planes[0], pbytes)) || (st = buf_reserve(c, &planes[1], pbytes)) ||
+        (st = buf_reserve(c, &planes[2], pbytes)) ||
+        (st = buf_reserve(c, &ehead, (size_t)n * c->ldE * sizeof(double))) ||
+        (st = buf_reserve(c, &errbuf, sizeof(int))) ||
+        (c->nsmid == 0 &&
+         (launch_nsmid((int*)errbuf.ptr, s),
+          (st = cuda_check(c, cudaMemcpyAsync(&c->nsmid, errbuf.ptr, sizeof(int),
+                                              cudaMemcpyDeviceToHost, s), "nsmid")) ||
+              (st = cuda_check(c, cudaStreamSynchronize(s), "nsmid sync")) ||
+              (c->nsmid = std::max(1, std::min(c->nsmid, 4096)), false))) ||
+        (st = buf_reserve(c, &tcscratch, (size_t)c->nsmid * ek_strip_scratch_floats() * sizeof(float))) ||
+        (st = buf_reserve(c, &hsplit, 2 * (size_t)c->npad * std::max(head_cols, 16) * sizeof(float))) ||
         (st = cuda_check(c, cudaMemsetAsync(errbuf.ptr, 0, sizeof(int), s), "err flag"))) {
-      free_tc();
+      fail_tc();
       for (auto& e : ev) cudaEventDestroy(e);
       return fail(st);
     }
@@ -499,7 +512,7 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
                         c->kb3_end, (const uint32_t*)c->chunk_end.ptr, (const int*)c->kexp.ptr,
                         (double*)ehead.ptr,
                         c->ldE, last ? (float*)c->E.ptr : nullptr, c->ldE, (int*)errbuf.ptr,
-                        c->kw.data(), (float*)tcscratch.ptr, sms,
+                        c->kw.data(), (float*)tcscratch.ptr, c->nsmid,
                         c->streamed ? nullptr : c->ev_tc[2], s);
     }
     cudaEventRecord(c->ev_tc[1], s);
@@ -513,7 +526,7 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
     c->t_light_ms = 0;
     if (!st && !c->streamed) cudaEventElapsedTime(&c->t_light_ms, c->ev_tc[2], c->ev_tc[1]);
     cudaEventDestroy(ev_head);
-    free_tc();
+    if (st) fail_tc();
   } else {
     st = launch_ek_simt(f64, c->A.ptr, c->npad, c->mpad, (const double*)c->xyz.ptr,
                         (const double*)c->alpha.ptr, n, geo, c->E.ptr, c->ldE, c->heavy_steps,

@@ -117,6 +117,10 @@ struct Ctx {
   std::vector<Buf*> scratch;
   std::vector<double> kw;  // k-vector weights W_K of the sorted table, mpad entries (0 past m)
   Buf ws_solve, ws_in0, ws_in1, ws_in2, ws_out0, ws_out1, ws_pot, ws_guess, ws_feat;
+  // tensor-core build workspace, kept for the next build: 16-bit operand planes, the FP64
+  // head matrix, the error flag, the head's float pairs, the per-SM hi / lo scratch
+  Buf tc_planes[3], tc_head, tc_err, tc_hsplit, tc_scratch;
+  int nsmid = 0;  // SM slots of tc_scratch (%nsmid), queried once
 
   float t_kspace_ms = 0, t_phase_ms = 0, t_precond_ms = 0, t_dsolve_ms = 0, t_tc_ms = 0;
   float t_matvec_ms = 0;  // last cpm_apply_E: the matvec launches alone

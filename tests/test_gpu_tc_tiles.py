@@ -47,3 +47,28 @@ def test_tensor_core_tail_against_fp64(cells):
     assert np.sqrt((d[off] ** 2).mean()) < 1e-8
     assert abs(np.diag(d).mean()) < 1e-7
     assert np.array_equal(e, e.T)
+
+
+def test_rebuilds_reuse_or_release_the_workspace():
+    # one context building electrodes of different sizes in one box, with its workspace
+    # kept between builds or released, gives what a fresh context gives, bit for bit
+    el = wl.two_sheet_electrode(20, 20)
+    part = np.arange(0, el.n, 3)  # a ragged subset (1,067 atoms) in the same box
+
+    def fresh(idx):
+        ctx = cpm.Context(el.box)
+        ctx.cpm_build_E(el.xyz[idx], el.alpha[idx])
+        e = ctx.cpm_get_E(cpm.CPM_E_STORED)
+        ctx.close()
+        return e
+
+    whole = np.arange(el.n)
+    ref = {"whole": fresh(whole), "part": fresh(part)}
+    ctx = cpm.Context(el.box)
+    for name, idx, release in [("whole", whole, False), ("part", part, False),
+                               ("whole", whole, True), ("part", part, True)]:
+        ctx.cpm_build_E(el.xyz[idx], el.alpha[idx])
+        assert np.array_equal(ctx.cpm_get_E(cpm.CPM_E_STORED), ref[name])
+        if release:
+            ctx.cpm_release_workspace()
+    ctx.close()
