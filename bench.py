@@ -265,6 +265,7 @@ def run_ours(args, rank, world, local_rank):
         info["tc_ms"].append(inf["t_tc_ms"])
         info["head_cols"] = inf["head_cols"]
         info["tc_blocks"] = list(inf["tc_blocks"])
+        info["tc_blocks_fp8"] = inf["tc_blocks_fp8"]
         info["head_ms"].append(inf["t_head_ms"])
         info["light_ms"].append(inf["t_tc_light_ms"])
         info["iters"].append(int(it[0]))
@@ -362,12 +363,13 @@ def run_ours(args, rank, world, local_rank):
                 "peak": bf16_peak, "unit": "TFLOP/s",
                 "kernel": "k_ek_strip<true> + k_ek_strip<false> (tcgen05 k-space GEMM on "
                           "256 x 256 tiles: six BF16 products per heavy K-block, then three or "
-                          "one FP16 products of per-block scaled values; two-sum chunk drains "
-                          "into per-SM hi/lo scratch)",
+                          "one FP16 or one FP8 product of per-block scaled values; two-sum chunk "
+                          "drains into per-SM hi/lo scratch)",
                 "peak_source": f"{src} bf16_tflops (burst)",
                 "issued_tflops": tc_flops / (tc_ms * 1e-3) / 1e12,
                 "fp32_accurate_tflops": 2.0 * (n * (n + 1) / 2) * tail_cols / (tc_ms * 1e-3) / 1e12,
                 "k_blocks_6_3_1_products": [n6, n3, n1],
+                "k_blocks_fp8": info.get("tc_blocks_fp8"),
                 "tc_ms": tc_ms, "light_ms": statistics.mean(info["light_ms"]),
                 "head_ms": statistics.mean(info["head_ms"])}
     elif args.precision == "fp32":
@@ -388,7 +390,7 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32": "f32", "fp64": "f64", "bf16x6": "bf16x6+fp16x3 (f32-accurate)"}[args.precision], "data": "synthetic",
+        "dtype": {"fp32": "f32", "fp64": "f64", "bf16x6": "bf16x6+fp16x3+fp8 (f32-accurate)"}[args.precision], "data": "synthetic",
         "config": {"workload": f"two-sheet graphene N={n}, {args.ions} ions, one frame per "
                                f"step incl. full E/P/d build",
                    "electrode_atoms": n, "ions": args.ions, "kvectors": m,

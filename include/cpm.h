@@ -266,6 +266,8 @@ typedef struct cpm_info_t {
   double t_head_ms;   /* BF16X6 builds: device time of the FP64-accurate head kernel */
   double t_tc_light_ms; /* BF16X6 builds with a resident operand: the part of t_tc_ms spent
                            on the three- and one-product K-blocks */
+  int tc_blocks_fp8;    /* BF16X6 builds: of tc_blocks[2], the K-blocks taking their one
+                           product in FP8 (E4M3) instead of FP16 */
 } cpm_info_t;
 
 int cpm_get_info(cpm_ctx* c, cpm_info_t* out);

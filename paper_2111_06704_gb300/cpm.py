@@ -78,6 +78,7 @@ class cpm_info_t(ctypes.Structure):
         ("tc_blocks", ctypes.c_int * 3),
         ("t_head_ms", ctypes.c_double),
         ("t_tc_light_ms", ctypes.c_double),
+        ("tc_blocks_fp8", ctypes.c_int),
     ]
 
 

@@ -165,7 +165,8 @@ void kvector_table(const cpm_params& p, std::vector<int>& hkl, std::vector<doubl
 }
 
 void release_workspace(Ctx* c) {
-  Buf* ws[] = {&c->tc_planes[0], &c->tc_planes[1], &c->tc_planes[2], &c->tc_head, &c->tc_err,
+  Buf* ws[] = {&c->tc_planes[0], &c->tc_planes[1], &c->tc_planes[2], &c->tc_planes[3],
+               &c->tc_head, &c->tc_err,
                &c->tc_hsplit, &c->tc_scratch, &c->dc_cnt, &c->dc_pcol, &c->dc_status, &c->ws_solve, &c->ws_in0, &c->ws_in1, &c->ws_in2,
                &c->ws_out0, &c->ws_out1, &c->ws_pot, &c->ws_guess, &c->ws_feat};
   for (Buf* b : ws) buf_free(c, b);
@@ -357,32 +358,39 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
           bwm[b] = std::max(bwm[b], 64.0 * w[64 * (b / 2) + t]);
         }
     // Product count (weights decrease along the table): trailing blocks whose summed
-    // bound times the one-FP16-product error (2^-10 + 2^-23, the second for subnormal
-    // remainders) stays within 1e-8 take one product; the blocks before them up to
-    // another 1e-8 at the three-FP16-product error (5 x 2^-22) take three; the rest the
-    // six BF16 products (~2^-24).  Both ends even: whole [cos | sin] pairs per region,
-    // one more block with more products at most.
+    // bound times the one-FP8 (E4M3) product error (2 x 2^-4 + 2^-8 + 3e-5, the last for
+    // subnormals; bound 0.13) stays within 1e-8 take one FP8 product; the blocks before
+    // them up to another 1e-8 at the one-FP16-product error (2^-10 + 2^-23) one FP16
+    // product; the blocks before them up to another 1e-8 at the three-FP16-product error
+    // (5 x 2^-22) three; the rest the six BF16 products (~2^-24).  All ends even: whole
+    // [cos | sin] pairs per region, one more block with more products at most.
     const int kb0 = c->heavy_steps / 4;
     const double budget = 1e-8;
-    int kb3 = nkb;
+    int kb8 = nkb;
     double tw = 0.0;
+    while (kb8 > kb0 && (tw + bwm[kb8 - 1]) * 0.13 <= budget) tw += bwm[--kb8];
+    kb8 = std::min(nkb, (kb8 + 1) & ~1);
+    int kb3 = kb8;
+    tw = 0.0;
     while (kb3 > kb0 && (tw + bwm[kb3 - 1]) * (0x1p-10 + 0x1p-23) <= budget) tw += bwm[--kb3];
-    kb3 = std::min(nkb, (kb3 + 1) & ~1);
+    kb3 = std::min(kb8, (kb3 + 1) & ~1);
     int kb6 = kb3;
     tw = 0.0;
     while (kb6 > kb0 && (tw + bwm[kb6 - 1]) * 5 * 0x1p-22 <= budget) tw += bwm[--kb6];
     kb6 = std::min(kb3, (kb6 + 1) & ~1);
     c->kb6_end = kb6;
     c->kb3_end = kb3;
-    // FP16 blocks: x = 2^e a with 2^e sqrt(max W) in [1/2, 1), so |x| < 1
+    c->kb8_begin = kb8;
+    // FP16 blocks: x = 2^e a with 2^e sqrt(max W) in [1/2, 1), so |x| < 1; FP8 blocks
+    // 2^8 times that, [128, 256), inside E4M3's normal range (max 448)
     for (int b = kb6; b < nkb; ++b)
-      if (bwm[b] > 0.0) kexp[b] = -ilogb(sqrt(bwm[b] / 64.0)) - 1;
+      if (bwm[b] > 0.0) kexp[b] = -ilogb(sqrt(bwm[b] / 64.0)) - 1 + (b >= kb8 ? 8 : 0);
     // Accumulation chunks.  Six-product blocks: up to 5e-3 of weight or 32 blocks (the
     // FP32 accumulation error of a chunk stays near 6e-8 x 5e-3 x sqrt(768 terms) ~ 1e-8;
     // measured: E unchanged at the 512-atom cell against 5e-4 / 8; at 3,200 atoms 2e-2 / 32
-    // doubles the off-diagonal RMS error, 3.9e-9 -> 9.7e-9).  FP16 blocks: one scale per
-    // chunk (a chunk ends where the next block's scale differs), at most 512 blocks; their
-    // summed weight is below 1e-2.
+    // doubles the off-diagonal RMS error, 3.9e-9 -> 9.7e-9).  FP16 and FP8 blocks: one
+    // scale per chunk (a chunk ends where the next block's scale differs, always after a
+    // whole [cos | sin] pair), at most 512 blocks; their summed weight is below 1e-2.
     double cw = 0.0;
     int len = 0;
     for (int b = kb0; b < nkb; ++b) {
@@ -463,7 +471,7 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
   if (tc) {
     const size_t pbytes = (size_t)c->npad * 2 * kwin * 2;
     if ((st = buf_reserve(c, &planes[0], pbytes)) || (st = buf_reserve(c, &planes[1], pbytes)) ||
-        (st = buf_reserve(c, &planes[2], pbytes)) ||
+        (st = buf_reserve(c, &planes[2], pbytes)) || (st = buf_reserve(c, &planes[3], pbytes / 2)) ||
         (st = buf_reserve(c, &ehead, (size_t)n * c->ldE * sizeof(double))) ||
         (st = buf_reserve(c, &errbuf, sizeof(int))) ||
         (c->nsmid == 0 &&
@@ -482,12 +490,12 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
   }
   // A (and, for the tensor-core build, its BF16 planes where the schedule reads them);
   // a streamed build makes the planes window by window below
-  void* plane_ptrs[3] = {planes[0].ptr, planes[1].ptr, planes[2].ptr};
+  void* plane_ptrs[4] = {planes[0].ptr, planes[1].ptr, planes[2].ptr, planes[3].ptr};
   if (!c->streamed)
     launch_structure_operand(f64, (const double*)c->xyz.ptr, (const uint32_t*)c->sfix.ptr,
                              c->npad, n, (const int*)c->hkl.ptr, (const double*)c->sqw.ptr,
                              c->mpad, c->p.box, c->A.ptr, tc ? plane_ptrs : nullptr,
-                             c->heavy_steps / 4, c->kb6_end, c->kb3_end,
+                             c->heavy_steps / 4, c->kb6_end, c->kb3_end, c->kb8_begin,
                              (const int*)c->kexp.ptr, 0, c->mpad, s);
   if (c->kh > 0)
     launch_structure_operand_head((const double*)c->xyz.ptr, c->npad, n, (const int*)c->hkl.ptr,
@@ -515,11 +523,13 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
         launch_structure_operand(false, (const double*)c->xyz.ptr, (const uint32_t*)c->sfix.ptr,
                                  c->npad, n, (const int*)c->hkl.ptr, (const double*)c->sqw.ptr,
                                  c->mpad, c->p.box, nullptr, plane_ptrs, c->heavy_steps / 4,
-                                 c->kb6_end, c->kb3_end, (const int*)c->kexp.ptr, kbeg, kend, s);
-      st = launch_ek_tc(planes[0].ptr, planes[1].ptr, planes[2].ptr, c->npad,
+                                 c->kb6_end, c->kb3_end, c->kb8_begin, (const int*)c->kexp.ptr,
+                                 kbeg, kend, s);
+      st = launch_ek_tc(planes[0].ptr, planes[1].ptr, planes[2].ptr, planes[3].ptr, c->npad,
                         2 * (int64_t)(kend - kbeg), kbeg / 32, n,
                         std::max(c->heavy_steps / 4, kbeg / 32), kend / 32, c->kb6_end,
-                        c->kb3_end, (const uint32_t*)c->chunk_end.ptr, (const int*)c->kexp.ptr,
+                        c->kb3_end, c->kb8_begin, (const uint32_t*)c->chunk_end.ptr,
+                        (const int*)c->kexp.ptr,
                         (double*)ehead.ptr,
                         c->ldE, last ? (float*)c->E.ptr : nullptr, c->ldE, (int*)errbuf.ptr,
                         c->kw.data(), (float*)tcscratch.ptr, c->nsmid,
@@ -838,6 +848,7 @@ int cpm_get_info(cpm_ctx* c, cpm_info_t* out) {
   out->tc_blocks[0] = tc ? c->kb6_end - kb0 : 0;
   out->tc_blocks[1] = tc ? c->kb3_end - c->kb6_end : 0;
   out->tc_blocks[2] = tc ? kbn - c->kb3_end : 0;
+  out->tc_blocks_fp8 = tc ? kbn - c->kb8_begin : 0;
   out->t_head_ms = c->t_head_ms;
   out->t_tc_light_ms = c->t_light_ms;
   out->d_iters = c->d_iters;

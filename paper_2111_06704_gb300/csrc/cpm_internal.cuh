@@ -91,6 +91,7 @@ struct Ctx {
   bool streamed = false;  // A too large to keep: built in k-windows, potential direct
   int kb6_end = 0, kb3_end = 0;  // tensor-core K-blocks: six products before kb6_end,
                                  // three before kb3_end, one after
+  int kb8_begin = 0;             // K-blocks from here take one FP8 product
   Buf A;        // float/double [npad][2*mpad]
   Buf E;        // float/double [n][ldE]
   Buf diag;     // double [2n]: diag(E_n), then its reciprocal
@@ -118,9 +119,9 @@ struct Ctx {
   std::vector<Buf*> scratch;
   std::vector<double> kw;  // k-vector weights W_K of the sorted table, mpad entries (0 past m)
   Buf ws_solve, ws_in0, ws_in1, ws_in2, ws_out0, ws_out1, ws_pot, ws_guess, ws_feat;
-  // tensor-core build workspace, kept for the next build: 16-bit operand planes, the FP64
+  // tensor-core build workspace, kept for the next build: operand planes, the FP64
   // head matrix, the error flag, the head's float pairs, the per-SM hi / lo scratch
-  Buf tc_planes[3], tc_head, tc_err, tc_hsplit, tc_scratch;
+  Buf tc_planes[4], tc_head, tc_err, tc_hsplit, tc_scratch;  // planes 0-2: 16-bit, 3: FP8
   Buf dc_cnt, dc_pcol, dc_status;  // PCG-DC build workspace
   int nsmid = 0;  // SM slots of tc_scratch (%nsmid), queried once
 
@@ -154,7 +155,7 @@ void launch_fixed_point_coords(const double* xyz, int n, int npad, const double 
 void launch_structure_operand(bool fp64, const double* xyz, const uint32_t* sfix, int npad,
                               int n, const int* hkl, const double* sqw, int mpad,
                               const double L[3], void* A, void* const* planes, int kb0,
-                              int kb6, int kb3, const int* kexp, int kbeg, int kend,
+                              int kb6, int kb3, int kb8, const int* kexp, int kbeg, int kend,
                               cudaStream_t s);
 void launch_structure_operand_head(const double* xyz, int npad, int n, const int* hkl,
                                    const double* sqw, int kh, const double L[3], double* Ahead,
@@ -169,8 +170,9 @@ int launch_ek_head_f64(const double* Ahead, int kh, int ktot, int npad, float* h
                        double* Ehead, int64_t ldE, cudaStream_t s);
 
 // tc_syrk.cu
-int launch_ek_tc(const void* p0, const void* p1, const void* p2, int npad, int64_t plane_cols,
-                 int kb_col0, int n, int kb_begin, int kb_end, int kb6_end, int kb3_end,
+int launch_ek_tc(const void* p0, const void* p1, const void* p2, const void* p8, int npad,
+                 int64_t plane_cols, int kb_col0, int n, int kb_begin, int kb_end, int kb6_end,
+                 int kb3_end, int kb8_begin,
                  const uint32_t* chunk_end, const int* kexp, double* head, int64_t ldh,
                  float* E, int64_t ldE, int* err, const double* kw, float* scratch,
                  int scratch_slots, cudaEvent_t mid, cudaStream_t s);

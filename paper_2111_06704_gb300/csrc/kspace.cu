@@ -10,6 +10,7 @@
 // A[i] = [sqrt(W) cos(K.r_i) | sqrt(W) sin(K.r_i)]: a dense contraction over 2M terms.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <math.h>
 
 #include "cpm_internal.cuh"
@@ -51,21 +52,27 @@ __global__ void k_fixed_point_coords(const double* __restrict__ xyz, int n, int 
 // schedule of K-block b, 64 columns):
 //   kb0 <= b < kb6: BF16, a = a0 + a1 + a2, each plane the rounding of the remainder of
 //     the previous (six products);
-//   kb6 <= b: FP16 of the block's power-of-two scaled value x = 2^kexp[b] a (|x| < 1),
-//     x = h0 + h1 below kb3 (three products), h0 alone from kb3 on (one product).
+//   kb6 <= b < kb8: FP16 of the block's power-of-two scaled value x = 2^kexp[b] a
+//     (|x| < 1), x = h0 + h1 below kb3 (three products), h0 alone from kb3 on (one);
+//   kb8 <= b: FP8 E4M3 of x = 2^kexp[b] a (|x| < 256), one product, in its own byte plane.
 // FP16 keeps 11 bits a plane against BF16's 8, so two planes and three products hold
-// ~2^-21 of each product where BF16 needs six; its narrow exponent range is what the
-// per-block scale is for.
+// ~2^-21 of each product where BF16 needs six; the narrow exponent ranges of FP16 and
+// FP8 are what the per-block scale is for.
 struct PlaneOut {
   uint16_t* p[3];
+  uint8_t* p8;
   const int* kexp;  // per K-block
-  int kb0, kb6, kb3;
+  int kb0, kb6, kb3, kb8;
 };
 
 __device__ __forceinline__ void write_planes(const PlaneOut& po, size_t e, int b, float a) {
   if (b < po.kb0) return;
   if (b >= po.kb6) {
-    const float x = ldexpf(a, po.kexp[b]);  // exact: a power of two
+    const float x = a * __int_as_float((127 + po.kexp[b]) << 23);  // exact: a power of two
+    if (b >= po.kb8) {
+      po.p8[e] = (uint8_t)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+      return;
+    }
     const __half h0 = __float2half_rn(x);
     po.p[0][e] = __half_as_ushort(h0);
     if (b < po.kb3) po.p[1][e] = __half_as_ushort(__float2half_rn(x - __half2float(h0)));
@@ -535,7 +542,7 @@ void launch_structure_operand_head(const double* xyz, int npad, int n, const int
 void launch_structure_operand(bool fp64, const double* xyz, const uint32_t* sfix, int npad,
                               int n, const int* hkl, const double* sqw, int mpad,
                               const double L[3], void* A, void* const* planes, int kb0,
-                              int kb6, int kb3, const int* kexp, int kbeg, int kend,
+                              int kb6, int kb3, int kb8, const int* kexp, int kbeg, int kend,
                               cudaStream_t s) {
   dim3 grid((kend - kbeg + 127) / 128, npad < 1024 ? npad : 1024);
   PlaneOut po{};
@@ -545,6 +552,8 @@ void launch_structure_operand(bool fp64, const double* xyz, const uint32_t* sfix
                                                 L[2], (double*)A), note_launch());
   } else if (planes) {
     for (int t = 0; t < 3; ++t) po.p[t] = (uint16_t*)planes[t];
+    po.p8 = (uint8_t*)planes[3];
+    po.kb8 = kb8;
     po.kexp = kexp;
     po.kb0 = kb0;
     po.kb6 = kb6;

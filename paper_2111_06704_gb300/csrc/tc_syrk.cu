@@ -117,6 +117,20 @@ __host__ __device__ constexpr uint32_t idesc_f16(bool bf16, int n) {
          ((uint32_t)(kTile >> 4) << 24);
 }
 
+// Instruction descriptor, kind::f8f6f4: D = F32, A = B = E4M3 (format 0), both K-major,
+// M = 128, N = n.
+__host__ __device__ constexpr uint32_t idesc_f8(int n) {
+  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
 __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                         uint32_t acc) {
   asm volatile(
@@ -195,7 +209,8 @@ struct StripArgs {
   int tiles;      // lower-triangle 256 x 256 tiles
   int kb_begin;   // first K-block
   int kb_end;     // one past the last K-block
-  int kb3_end;    // SIX = false: K-blocks before this take three products, the rest one
+  int kb3_end;    // SIX = false: K-blocks before this take three products, the rest one,
+  int kb8_begin;  //   from this one (even) on in FP8
   int kb_col0;    // the operand planes start at this K-block
   const uint32_t* chunk_end;  // bit per K-block: an accumulation chunk ends after it
   const int* kexp;            // per K-block: FP16 blocks hold 2^kexp a (0 for BF16 blocks)
@@ -281,9 +296,10 @@ template <bool SIX>
 __global__ void __launch_bounds__(kStripThreads, 1)
 k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CUtensorMap map0n,
            const __grid_constant__ CUtensorMap map1n, const __grid_constant__ CUtensorMap map2n,
-           StripArgs args) {
+           const __grid_constant__ CUtensorMap map8, StripArgs args) {
   // map0w: plane 0 in 128 x 64 boxes (128-byte swizzle); map0n / map1n / map2n: planes
-  // 0-2 in 128 x 32 boxes (64-byte swizzle)
+  // 0-2 in 128 x 32 boxes (64-byte swizzle); map8: the FP8 plane in 128 x 128 boxes
+  // (128-byte swizzle)
   using Cfg = StripCfg<SIX>;
   constexpr int kStages = Cfg::kStages, kStageBytes = Cfg::kStageBytes;
   constexpr int P = Cfg::kPlanes;
@@ -295,21 +311,27 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
   constexpr int kNarrow = kTile * 32 * 2, kWide = kTile * 64 * 2;  // 8 KB and 16 KB tiles
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // narrow stages (two per K-block) then wide ones (one per one-product K-block); the
-  // same for every tile
+  // narrow stages (two per K-block), then wide FP16 ones (one per one-product K-block),
+  // then FP8 ones (one per [cos | sin] pair of one-product K-blocks); the same for every
+  // tile
   const int nnarrow =
       2 * (SIX ? args.kb_end - args.kb_begin
                : max(0, min(args.kb_end, args.kb3_end) - args.kb_begin));
   const int kb1 = max(args.kb_begin, args.kb3_end);
-  const int nst = nnarrow + (SIX ? 0 : max(0, args.kb_end - kb1));
-  // K-block of stage t, and whether stage t is its last
+  const int kb8 = SIX ? args.kb_end : max(args.kb_begin, args.kb8_begin);
+  const int nwide = SIX ? 0 : max(0, min(args.kb_end, kb8) - kb1);
+  const int t8 = nnarrow + nwide;  // first FP8 stage
+  const int nst = t8 + (SIX ? 0 : max(0, args.kb_end - kb8) / 2);
+  // K-block of stage t (an FP8 stage: the second of its pair), and whether stage t is its
+  // last
   auto stage_block = [&](int t, bool& last_of_block) {
     if (t < nnarrow) {
       last_of_block = (t & 1) != 0;
       return args.kb_begin + t / 2;
     }
     last_of_block = true;
-    return kb1 + (t - nnarrow);
+    if (t < t8) return kb1 + (t - nnarrow);
+    return kb8 + 2 * (t - t8) + 1;
   };
   // an accumulation chunk ends with stage t: the tile's last stage, or the last stage of
   // a K-block whose chunk bit is set
@@ -366,6 +388,15 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
                 tma_load_2d(st + (2 * P + 2 * p + c) * kNarrow, mp, &full_bar[s], x,
                             tg.j0 + c * kTile);
             }
+          } else if (t >= t8) {
+            // 128 FP8 columns (a [cos | sin] pair): A half r at r x 16 KB, B halves at
+            // 32 KB and 48 KB
+            const int x = (kb8 - args.kb_col0 + 2 * (t - t8)) * kBlockK;
+            mbar_expect_tx(&full_bar[s], (tg.rb + tg.cb) * kWide);
+            for (int r = 0; r < tg.rb; ++r)
+              tma_load_2d(st + r * kWide, &map8, &full_bar[s], x, tg.i0 + r * kTile);
+            for (int c = 0; c < tg.cb; ++c)
+              tma_load_2d(st + 2 * kWide + c * kWide, &map8, &full_bar[s], x, tg.j0 + c * kTile);
           } else {
             // 64 columns of plane 0: A half r at r x 16 KB, B halves at 32 KB and 48 KB
             const int x = (kb1 - args.kb_col0 + (t - nnarrow)) * kBlockK;
@@ -415,6 +446,17 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
                   mma_f16(tmem + (uint32_t)(r * 256), da, db, r == 0 ? id0 : kId256,
                               (first && ks == 0 && p == 0) ? 0u : 1u);
                 }
+          } else if (t >= t8) {
+            // 128-byte rows of 128 FP8 values: K = 32 (32 bytes) per MMA
+            constexpr uint32_t kF8_256 = idesc_f8(256), kF8_128 = idesc_f8(128);
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+              for (int r = 0; r < tg.rb; ++r) {
+                const uint64_t da = smem_desc<64>(st + r * kWide + ks * 32);
+                const uint64_t db = smem_desc<64>(st + 2 * kWide + ks * 32);
+                mma_f8(tmem + (uint32_t)(r * 256), da, db,
+                       (r == 0 && tg.diag) ? kF8_128 : kF8_256, (first && ks == 0) ? 0u : 1u);
+              }
           } else {
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks)
@@ -569,16 +611,20 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-bool make_map(CUtensorMap* m, const void* base, int rows, int64_t cols, int bk) {
+// 2-D map of a [rows][cols] plane of 16-bit values (bytes = false) in 128-row boxes of bk
+// columns (bk = 64: 128-byte swizzle, bk = 32: 64-byte), or of bytes (bytes = true) in
+// 128 x 128 boxes (128-byte swizzle).
+bool make_map(CUtensorMap* m, const void* base, int rows, int64_t cols, int bk,
+              bool bytes = false) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-  cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)kTile};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * (bytes ? 1 : 2)};
+  cuuint32_t box[2] = {(cuuint32_t)(bytes ? 128 : bk), (cuuint32_t)kTile};
   cuuint32_t estr[2] = {1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
-            estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+  return fn(m, bytes ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+            const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            bytes || bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -623,15 +669,18 @@ void launch_nsmid(int* d_out, cudaStream_t s) {
 // back into head (FP64) when E is null.  Two launches, the first adding its K-range to
 // head and the second writing E: the six-product (BF16) K-blocks, then the three- and
 // one-product (FP16) ones.  `mid`, when given, is recorded before the second.
-int launch_ek_tc(const void* p0, const void* p1, const void* p2, int npad, int64_t plane_cols,
-                 int kb_col0, int n, int kb_begin, int kb_end, int kb6_end, int kb3_end,
+int launch_ek_tc(const void* p0, const void* p1, const void* p2, const void* p8, int npad,
+                 int64_t plane_cols, int kb_col0, int n, int kb_begin, int kb_end, int kb6_end,
+                 int kb3_end, int kb8_begin,
                  const uint32_t* chunk_end, const int* kexp, double* head, int64_t ldh,
                  float* E, int64_t ldE, int* err, const double* kw, float* scratch,
                  int scratch_slots, cudaEvent_t mid, cudaStream_t s) {
-  if (!scratch || scratch_slots < 1 || (kb6_end & 1) || (kb_begin & 1)) return CPM_EINVAL;
-  CUtensorMap m0, m0n, m1n, m2n;
+  if (!scratch || scratch_slots < 1 || (kb6_end & 1) || (kb_begin & 1) || (kb8_begin & 1))
+    return CPM_EINVAL;
+  CUtensorMap m0, m0n, m1n, m2n, m8;
   if (!make_map(&m0, p0, npad, plane_cols, 64) || !make_map(&m0n, p0, npad, plane_cols, 32) ||
-      !make_map(&m1n, p1, npad, plane_cols, 32) || !make_map(&m2n, p2, npad, plane_cols, 32))
+      !make_map(&m1n, p1, npad, plane_cols, 32) || !make_map(&m2n, p2, npad, plane_cols, 32) ||
+      !make_map(&m8, p8, npad, plane_cols, 128, true))
     return CPM_ECUDA;
   const int smem6 = StripCfg<true>::kStages * StripCfg<true>::kStageBytes + 1024;
   const int smem31 = StripCfg<false>::kStages * StripCfg<false>::kStageBytes + 1024;
@@ -650,6 +699,7 @@ int launch_ek_tc(const void* p0, const void* p1, const void* p2, int npad, int64
   a.npad = npad;
   a.tiles = nt * (nt + 1) / 2;
   a.kb3_end = kb3_end;
+  a.kb8_begin = kb8_begin;
   a.kb_col0 = kb_col0;
   a.chunk_end = chunk_end;
   a.kexp = kexp;
@@ -665,7 +715,7 @@ int launch_ek_tc(const void* p0, const void* p1, const void* p2, int npad, int64
     a.kb_end = x6_end;
     a.E = l_begin < kb_end ? nullptr : E;
     a.diag_exact = range_weight(kw, a.kb_begin, a.kb_end, &a.w_diag);
-    (k_ek_strip<true><<<a.tiles, kStripThreads, smem6, s>>>(m0, m0n, m1n, m2n, a),
+    (k_ek_strip<true><<<a.tiles, kStripThreads, smem6, s>>>(m0, m0n, m1n, m2n, m8, a),
      note_launch());
   }
   if (mid) cudaEventRecord(mid, s);
@@ -674,7 +724,7 @@ int launch_ek_tc(const void* p0, const void* p1, const void* p2, int npad, int64
     a.kb_end = kb_end;
     a.E = E;
     a.diag_exact = range_weight(kw, a.kb_begin, a.kb_end, &a.w_diag);
-    (k_ek_strip<false><<<a.tiles, kStripThreads, smem31, s>>>(m0, m0n, m1n, m2n, a),
+    (k_ek_strip<false><<<a.tiles, kStripThreads, smem31, s>>>(m0, m0n, m1n, m2n, m8, a),
      note_launch());
   }
   if (kb_begin >= kb_end && E)  // nothing of the tail in this window
