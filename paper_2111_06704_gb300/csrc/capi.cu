@@ -288,9 +288,10 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
   c->npad = (int)round_up(n, 128);
   c->ldE = round_up(n, 128);
   c->vol = c->p.box[0] * c->p.box[1] * c->p.box[2];
-  std::vector<int> hkl;
-  std::vector<double> w;
-  kvector_table(c->p, hkl, w);
+  // the k-vector table depends on the box, g and eps only: made once per context
+  if (c->kv_w.empty()) kvector_table(c->p, c->kv_hkl, c->kv_w);
+  std::vector<int> hkl = c->kv_hkl;
+  const std::vector<double>& w = c->kv_w;
   c->m = (int)w.size();
   c->mpad = (int)round_up(std::max(c->m, 1), 64);
   hkl.resize(3 * (size_t)c->mpad, 0);

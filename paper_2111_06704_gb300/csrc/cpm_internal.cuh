@@ -118,6 +118,8 @@ struct Ctx {
   // scratch (grown on demand, never shrunk)
   std::vector<Buf*> scratch;
   std::vector<double> kw;  // k-vector weights W_K of the sorted table, mpad entries (0 past m)
+  std::vector<int> kv_hkl;    // the k-vector table (host), made on the first build
+  std::vector<double> kv_w;
   Buf ws_solve, ws_in0, ws_in1, ws_in2, ws_out0, ws_out1, ws_pot, ws_guess, ws_feat;
   // tensor-core build workspace, kept for the next build: operand planes, the FP64
   // head matrix, the error flag, the head's float pairs, the per-SM hi / lo scratch
