@@ -113,11 +113,13 @@ __global__ void k_dc_pairs(const double* __restrict__ xyz, int n, double lx, dou
 // (a pair of tau's neighbours closer than r_cut is an entry of the first one's pattern
 // row: each warp walks a neighbour's row, coalesced, and finds each entry's position in
 // tau's list, held in shared memory, by binary search) and kept as its packed upper
-// triangle.  A float copy is
-// factored P M = L U with partial pivoting (FP64 runs at 1/64 of the float rate here, and
-// the factorisation is m^3 / 3 multiply-adds), and the solution is refined against the
-// FP64 matrix: x += (LU)^-1 P (e_tau - M x), residuals in FP64, until the correction is
-// below FP64 rounding of x (each step gains the ~1e-5 that kappa(M) x 2^-24 leaves).
+// triangle.  A float copy is factored P M = L U with partial pivoting (FP64 runs at 1/64
+// of the float rate here, and the factorisation is m^3 / 3 multiply-adds), and the
+// solution is refined against the FP64 matrix: x += (LU)^-1 P (e_tau - M x), residuals in
+// FP64.  Each step shrinks the error by about kappa(M) 2^-24 (~1e-5 here), so the error
+// left after adding a correction d is about that times |d|: refinement stops once
+// |d| <= 1e-9 |x| (error ~1e-13 even at kappa(M) 2^-24 = 1e-4; typically after the
+// second correction).
 constexpr int kDcThreads = 128;
 constexpr int kDcMaxRefine = 6;
 
@@ -272,7 +274,7 @@ k_dc_local(const double* __restrict__ alpha, const int64_t* __restrict__ off,
         dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, sh));
         xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, sh));
       }
-      if (lane == 0 && dmax <= 1e-16 * xmax) s_done = 1;
+      if (lane == 0 && dmax <= 1e-9 * xmax) s_done = 1;
     }
     __syncthreads();
     if (s_done) break;
