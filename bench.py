@@ -358,14 +358,18 @@ def run_ours(args, rank, world, local_rank):
         tail_cols = 64 * (n6 + n3 + n1)
         tc_flops = 2.0 * (nt * (nt - 1) / 2 + 0.75 * nt) * 256 * 256 * prod_cols
         algo_flops = 2.0 * (n * (n + 1) / 2) * prod_cols
-        bf16_peak = peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"])
+        # the tail runs ~100 ms without a break inside each step: the sustained (power-
+        # capped) BF16 rate is its denominator; the burst one is reported beside it
+        bf16_peak = peaks.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"])
+        burst = peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"])
         roof = {"bound": "tensor", "achieved": algo_flops / (tc_ms * 1e-3) / 1e12,
                 "peak": bf16_peak, "unit": "TFLOP/s",
                 "kernel": "k_ek_strip<true> + k_ek_strip<false> (tcgen05 k-space GEMM on "
                           "256 x 256 tiles: six BF16 products per heavy K-block, then three or "
                           "one FP16 or one FP8 product of per-block scaled values; two-sum chunk "
                           "drains into per-SM hi/lo scratch)",
-                "peak_source": f"{src} bf16_tflops (burst)",
+                "peak_source": f"{src} bf16_tflops_sustained",
+                "frac_of_burst": algo_flops / (tc_ms * 1e-3) / 1e12 / burst,
                 "issued_tflops": tc_flops / (tc_ms * 1e-3) / 1e12,
                 "fp32_accurate_tflops": 2.0 * (n * (n + 1) / 2) * tail_cols / (tc_ms * 1e-3) / 1e12,
                 "k_blocks_6_3_1_products": [n6, n3, n1],
@@ -385,6 +389,11 @@ def run_ours(args, rank, world, local_rank):
                 "peak_source": "derived FP64 rate"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
+    if args.precision == "bf16x6" and n == 12800:
+        # DRAM read + write of the two tail launches of one build, from the one-pass ncu
+        # launch list of this workload (profiles/launches_bf16x6_N12800.md)
+        roof["traffic"] = 483.3e9
+        roof["traffic_unit"] = "bytes per build (both launches)"
     value = world * 1000.0 / ms
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
