@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--precision", choices=["bf16x6", "fp32", "fp64"], default="bf16x6")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["precision", "batch", "learned", "matvec", "scale"],
+    ap.add_argument("--workload", choices=["precision", "batch", "learned", "matvec", "scale",
+                                           "scale-learned"],
                     default="precision")
     ap.add_argument("--rhs", type=int, default=1,
                     help="directions per matvec (matvec workload), frames per step (scale)")
@@ -861,6 +862,120 @@ def run_learned(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_scale_learned(args, rank, world, local_rank):
+    """Scale point with the learned initial guess: the ~106,600-atom electrode, its 20,000
+    ions random-walked in 0.1 A steps; the guess network is trained on `--train-frames`
+    (at most 48) solver-generated frames and compared with the previous-step guess (Eq. 26)
+    on `--rhs` (16 unless given) held-out frames solved as one multi-right-hand-side batch,
+    all to 1e-6 relative residual.  Streamed build as in the scale workload."""
+    import torch
+
+    from paper_2111_06704_gb300 import cpm
+    from paper_2111_06704_gb300.guess import LearnedGuess
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    T, H = min(args.train_frames, 48), (args.rhs if args.rhs > 1 else 16)
+    t_gen = time.perf_counter()
+    work = wl.scale_walk(T + H + 1, step=0.1, seed=wl.seed_for(5, rank))
+    el, io = work.electrode, work.electrolyte
+    n, F = el.n, io.frames
+    tt = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    ctx = cpm.Context(el.box, g_ewald=0.15, rcut_real=24.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.cpm_build_E(tt(el.xyz), tt(el.alpha))
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    chi = tt(el.chi)
+    b = torch.empty((F, n), dtype=torch.float64, device=dev)
+    qs = torch.empty(F, dtype=torch.float64, device=dev)
+    qb = torch.zeros((F, n), dtype=torch.float64, device=dev)
+    for f0 in range(0, F, 16):
+        f1 = min(F, f0 + 16)
+        ctx.cpm_potential(tt(io.xyz[f0:f1]), tt(io.q[f0:f1]), chi, b[f0:f1], qs[f0:f1])
+    for f0 in range(0, T + 1, H):
+        f1 = min(T + 1, f0 + H)
+        ctx.cpm_solve(b[f0:f1], qb[f0:f1], tol=1e-9, maxit=5000)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t_gen
+
+    g = LearnedGuess(ctx, seed=rank)
+    t_train = time.perf_counter()
+    feat = g.features(b[1:T + 1], b[0:T], chi).reshape(-1, 32)
+    target = (qb[1:T + 1] - qb[0:T]).reshape(-1).to(torch.float32).contiguous()
+    k = min(feat.shape[0], 500 * 512)
+    g.set_normalisation(feat[:k].cpu().numpy(), target[:k].cpu().numpy())
+    losses = g.train(feat, target, epochs=args.epochs, batch=65536, lr=2e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t_train
+    del feat, target
+
+    test = slice(T + 1, T + H + 1)
+    bt = b[test].contiguous()
+    bp = b[T:T + H].contiguous()
+    qst = qs[test].contiguous()
+
+    # previous-step charges: frame T's, then each held-out frame's own converged solution
+    prev = torch.empty((H, n), dtype=torch.float64, device=dev)
+    prev[0] = qb[T]
+    ref = torch.zeros((H, n), dtype=torch.float64, device=dev)
+    ctx.cpm_solve(bt, ref, tol=1e-9, maxit=5000)
+    prev[1:] = ref[:-1]
+
+    def solve_prev():
+        q = prev.clone()
+        _, it, _ = ctx.cpm_solve(bt, q, use_guess=True, tol=TOL, maxit=5000)
+        ctx.cpm_neutralize(q, qst)
+        return it
+
+    def solve_learned():
+        q0 = g.guess_frames(bt, bp, chi, prev)
+        _, it, _ = ctx.cpm_solve(bt, q0, use_guess=True, tol=TOL, maxit=5000)
+        ctx.cpm_neutralize(q0, qst)
+        return it
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        it = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t1, it
+
+    for _ in range(max(1, args.warmup)):
+        solve_prev()
+        solve_learned()
+    with ClockSampler(local_rank) as clocks:
+        s_prev, it_prev = timed(solve_prev)
+        s_learn, it_learn = timed(solve_learned)
+        s_guess, _ = timed(lambda: g.guess_frames(bt, bp, chi, prev))
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": world * H / s_learn, "unit": "solves/s", "n_gpus": world,
+        "steps": 1, "warmup": args.warmup, "ms_per_step": 1e3 * s_learn,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x6+fp16x3+fp8 (f32-accurate); guess network bf16 weights, f32 accumulation",
+        "data": "synthetic",
+        "config": {"workload": f"scale point with the learned guess: N={n}, {io.n_ion} ions "
+                               f"random-walked 0.1 A/frame, {T} training frames, {H} held-out "
+                               f"frames solved as one batch (build once)",
+                   "electrode_atoms": n, "ions": io.n_ion, "rhs": H, "tol": TOL,
+                   "g_ewald": 0.15, "rcut_real": 24.0, "epochs": args.epochs},
+        "e_build_s": build_s,
+        "learned": {"mean_iters": float(np.mean(it_learn)), "max_iters": int(np.max(it_learn)),
+                    "solves_per_s": H / s_learn, "guess_ms": 1e3 * s_guess},
+        "previous_step": {"mean_iters": float(np.mean(it_prev)), "max_iters": int(np.max(it_prev)),
+                          "solves_per_s": H / s_prev},
+        "iteration_gain": float(np.mean(it_prev) - np.mean(it_learn)),
+        "train": {"seconds": train_s, "samples": T * n, "first_loss": float(losses[0]),
+                  "last_loss": float(losses[-1]), "steps": len(losses)},
+        "generate_seconds": gen_s,
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -880,6 +995,8 @@ def main():
         run_matvec(args, rank, world, local_rank)
     elif args.workload == "scale":
         run_scale(args, rank, world, local_rank)
+    elif args.workload == "scale-learned":
+        run_scale_learned(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
     if world > 1:

@@ -301,3 +301,23 @@ def scale_point(seed: int | None = None, n_ion: int = 20000, rhs: int = 1) -> Wo
         frames.append(f)
     return Workload(f"six stacked graphene sheets with pinholes N={el.n}, {len(qv)} ions",
                     el, Electrolyte(np.stack(frames), np.broadcast_to(qv, (rhs, len(qv))).copy()))
+
+
+def scale_walk(frames: int, step: float = 0.1, seed: int | None = None) -> Workload:
+    """The scale-point electrode and ions (frame 0 of scale_point) random-walked with
+    isotropic Gaussian steps, one frame per step, each ion reflected back into its own gap
+    (at least 2 A from both sheets); x and y wrap."""
+    base = scale_point(seed=seed, rhs=1)
+    el, ions0, q = base.electrode, base.electrolyte.xyz[0], base.electrolyte.q[0]
+    rng = np.random.default_rng((seed_for(5) if seed is None else seed) + 1)
+    gap = np.floor(ions0[:, 2] / 7.0).astype(int)
+    out = np.empty((frames,) + ions0.shape)
+    cur = ions0.copy()
+    for f in range(frames):
+        cur = cur + rng.normal(0.0, step, size=cur.shape)
+        cur[:, 0] %= el.box[0]
+        cur[:, 1] %= el.box[1]
+        cur[:, 2] = _reflect(cur[:, 2], 7.0 * gap + 2.0, 7.0 * (gap + 1) - 2.0)
+        out[f] = cur
+    return Workload(f"{base.name}, {frames} random-walk frames", el,
+                    Electrolyte(out, np.broadcast_to(q, (frames, q.shape[0])).copy()))
