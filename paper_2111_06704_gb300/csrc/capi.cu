@@ -490,14 +490,23 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
     }
   }
   // A (and, for the tensor-core build, its BF16 planes where the schedule reads them);
-  // a streamed build makes the planes window by window below
+  // a streamed build makes the planes window by window below.  The float operand's
+  // phases come from the 4,096-entry phasor table (made once per context)
+  if (!f64 && !c->turn.ptr) {
+    if ((st = buf_alloc(c, &c->turn, 4096 * 4 * sizeof(float)))) {
+      fail_tc();
+      for (auto& e : ev) cudaEventDestroy(e);
+      return fail(st);
+    }
+    launch_turn_table(c->turn.ptr, s);
+  }
   void* plane_ptrs[4] = {planes[0].ptr, planes[1].ptr, planes[2].ptr, planes[3].ptr};
   if (!c->streamed)
     launch_structure_operand(f64, (const double*)c->xyz.ptr, (const uint32_t*)c->sfix.ptr,
                              c->npad, n, (const int*)c->hkl.ptr, (const double*)c->sqw.ptr,
                              c->mpad, c->p.box, c->A.ptr, tc ? plane_ptrs : nullptr,
                              c->heavy_steps / 4, c->kb6_end, c->kb3_end, c->kb8_begin,
-                             (const int*)c->kexp.ptr, 0, c->mpad, s);
+                             (const int*)c->kexp.ptr, c->turn.ptr, 0, c->mpad, s);
   if (c->kh > 0)
     launch_structure_operand_head((const double*)c->xyz.ptr, c->npad, n, (const int*)c->hkl.ptr,
                                   (const double*)c->sqw.ptr, c->kh, c->p.box,
@@ -525,7 +534,7 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
                                  c->npad, n, (const int*)c->hkl.ptr, (const double*)c->sqw.ptr,
                                  c->mpad, c->p.box, nullptr, plane_ptrs, c->heavy_steps / 4,
                                  c->kb6_end, c->kb3_end, c->kb8_begin, (const int*)c->kexp.ptr,
-                                 kbeg, kend, s);
+                                 c->turn.ptr, kbeg, kend, s);
       st = launch_ek_tc(planes[0].ptr, planes[1].ptr, planes[2].ptr, planes[3].ptr, c->npad,
                         2 * (int64_t)(kend - kbeg), kbeg / 32, n,
                         std::max(c->heavy_steps / 4, kbeg / 32), kend / 32, c->kb6_end,

@@ -157,8 +157,8 @@ void launch_fixed_point_coords(const double* xyz, int n, int npad, const double 
 void launch_structure_operand(bool fp64, const double* xyz, const uint32_t* sfix, int npad,
                               int n, const int* hkl, const double* sqw, int mpad,
                               const double L[3], void* A, void* const* planes, int kb0,
-                              int kb6, int kb3, int kb8, const int* kexp, int kbeg, int kend,
-                              cudaStream_t s);
+                              int kb6, int kb3, int kb8, const int* kexp, const void* turn,
+                              int kbeg, int kend, cudaStream_t s);
 void launch_structure_operand_head(const double* xyz, int npad, int n, const int* hkl,
                                    const double* sqw, int kh, const double L[3], double* Ahead,
                                    cudaStream_t s);

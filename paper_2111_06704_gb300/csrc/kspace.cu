@@ -86,6 +86,21 @@ __device__ __forceinline__ void write_planes(const PlaneOut& po, size_t e, int b
   po.p[2][e] = __bfloat16_as_ushort(__float2bfloat16_rn(r1 - __bfloat162float(b1)));
 }
 
+// sin and cos of 2 pi x for a fixed-point phase x = ph 2^-32 from the 4,096-entry table T
+// of exp(2 pi i j / 4096) as float pairs (cos hi, cos lo, sin hi, sin lo; made in FP64)
+// and the remaining angle t = 2 pi (ph mod 2^20) 2^-32 < 1.6e-3 rad by angle addition:
+// cos = Tc - (t^2/2) Tc - t Ts and sin = Ts - (t^2/2) Ts + t Tc, the large term added last
+// (t^4/24 < 3e-13 and t^3/6 are below float rounding of the result).  About one float
+// ulp, as sincos_turns, in a third of the instructions.
+__device__ __forceinline__ void sincos_table(uint32_t ph, const float4* __restrict__ T,
+                                             float* s, float* c) {
+  const float4 t4 = __ldg(T + (ph >> 20));
+  const float t = (float)(ph & 0xFFFFFu) * 1.462918119976564e-09f;  // 2 pi 2^-32
+  const float h = -0.5f * t * t;
+  *c = t4.x + fmaf(h, t4.x, fmaf(-t, t4.z, t4.y));
+  *s = t4.z + fmaf(h, t4.z, fmaf(t, t4.x, t4.w));
+}
+
 // A (lda = 2 mpad) and, with PLANES, the BF16 planes for the k-vectors [kbeg, kend)
 // (multiples of 64), the planes laid out over that window only: row stride
 // 2 (kend - kbeg), column kcol - 2 kbeg.  A may be null (a streamed build keeps no A).
@@ -93,7 +108,8 @@ template <bool PLANES>
 __global__ void k_structure_operand_f32(const uint32_t* __restrict__ sfix, int npad, int n,
                                         const int* __restrict__ hkl,
                                         const double* __restrict__ sqw, int mpad, int kbeg,
-                                        int kend, float* __restrict__ A, PlaneOut po) {
+                                        int kend, const float4* __restrict__ turn,
+                                        float* __restrict__ A, PlaneOut po) {
   int k = kbeg + blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= kend) return;
   const uint32_t h = (uint32_t)hkl[3 * k], kk = (uint32_t)hkl[3 * k + 1],
@@ -108,7 +124,7 @@ __global__ void k_structure_operand_f32(const uint32_t* __restrict__ sfix, int n
     float c = 0.f, s = 0.f;
     if (i < n) {
       const uint32_t ph = h * sfix[3 * i] + kk * sfix[3 * i + 1] + l * sfix[3 * i + 2];
-      sincos_turns(ph, &s, &c);
+      sincos_table(ph, turn, &s, &c);
       c *= w;
       s *= w;
     }
@@ -542,8 +558,8 @@ void launch_structure_operand_head(const double* xyz, int npad, int n, const int
 void launch_structure_operand(bool fp64, const double* xyz, const uint32_t* sfix, int npad,
                               int n, const int* hkl, const double* sqw, int mpad,
                               const double L[3], void* A, void* const* planes, int kb0,
-                              int kb6, int kb3, int kb8, const int* kexp, int kbeg, int kend,
-                              cudaStream_t s) {
+                              int kb6, int kb3, int kb8, const int* kexp, const void* turn,
+                              int kbeg, int kend, cudaStream_t s) {
   dim3 grid((kend - kbeg + 127) / 128, npad < 1024 ? npad : 1024);
   PlaneOut po{};
   if (fp64) {
@@ -559,10 +575,12 @@ void launch_structure_operand(bool fp64, const double* xyz, const uint32_t* sfix
     po.kb6 = kb6;
     po.kb3 = kb3;
     (k_structure_operand_f32<true><<<grid, 128, 0, s>>>(sfix, npad, n, hkl, sqw, mpad, kbeg,
-                                                        kend, (float*)A, po), note_launch());
+                                                        kend, (const float4*)turn, (float*)A,
+                                                        po), note_launch());
   } else {
     (k_structure_operand_f32<false><<<grid, 128, 0, s>>>(sfix, npad, n, hkl, sqw, mpad, kbeg,
-                                                         kend, (float*)A, po), note_launch());
+                                                         kend, (const float4*)turn, (float*)A,
+                                                         po), note_launch());
   }
 }
 
