@@ -540,7 +540,7 @@ def run_scale(args, rank, world, local_rank):
         "metric": METRIC, "value": world * F * 1000.0 / ms, "unit": "solves/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16x6 (f32-accurate)", "data": "synthetic",
+        "dtype": "bf16x6+fp16x3+fp8 (f32-accurate)", "data": "synthetic",
         "config": {"workload": f"scale point: six stacked graphene sheets with pinholes, "
                                f"N={n}, {io.n_ion} ions, {F} frames per step (build once)",
                    "electrode_atoms": n, "ions": io.n_ion, "rhs": F, "tol": TOL,

@@ -688,7 +688,7 @@ int cpm_potential(cpm_ctx* c, int frames, int n_ion, const double* ion_xyz,
   }
   launch_bsol_kspace(f64, c->A.ptr, (const double*)c->Ahead.ptr, n, c->mpad, c->kh, v, vh,
                      frames, bk, (const uint32_t*)c->sfix.ptr, (const int*)c->hkl.ptr,
-                     (const double*)c->sqw.ptr, s);
+                     (const double*)c->sqw.ptr, c->turn.ptr, s);
   launch_bsol_real_and_finish((const double*)c->xyz.ptr, (const double*)c->alpha.ptr,
                               (const uint32_t*)c->sfix.ptr, n, dx, dq, sion, frames, n_ion,
                               geometry(c), dchi, bk, db, dqs, s);

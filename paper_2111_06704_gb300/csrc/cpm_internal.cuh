@@ -29,6 +29,21 @@ __device__ __forceinline__ void sincos_turns(uint32_t ph, float* s, float* c) {
   *s = fmaf(c0, t, s0);
 }
 
+// sin and cos of 2 pi x for a fixed-point phase x = ph 2^-32 from the 4,096-entry table T
+// of exp(2 pi i j / 4096) as float pairs (cos hi, cos lo, sin hi, sin lo; made in FP64)
+// and the remaining angle t = 2 pi (ph mod 2^20) 2^-32 < 1.6e-3 rad by angle addition:
+// cos = Tc - (t^2/2) Tc - t Ts and sin = Ts - (t^2/2) Ts + t Tc, the large term added last
+// (t^4/24 < 3e-13 and t^3/6 are below float rounding of the result).  About one float
+// ulp, as sincos_turns, in a third of the instructions.
+__device__ __forceinline__ void sincos_table(uint32_t ph, const float4* __restrict__ T,
+                                             float* s, float* c) {
+  const float4 t4 = __ldg(T + (ph >> 20));
+  const float t = (float)(ph & 0xFFFFFu) * 1.462918119976564e-09f;  // 2 pi 2^-32
+  const float h = -0.5f * t * t;
+  *c = t4.x + fmaf(h, t4.x, fmaf(-t, t4.z, t4.y));
+  *s = t4.z + fmaf(h, t4.z, fmaf(t, t4.x, t4.w));
+}
+
 // (h, l) += q x for a float pair (h, l) and q = qh + ql: the product qh x is split
 // exactly (two-product) and added by an error-free two-sum, so the pair carries the sum
 // to ~1e-14 relative however many terms are added.
@@ -197,7 +212,7 @@ void launch_ion_structure_factor(bool fp64, const double* ion_xyz, const uint32_
 void launch_bsol_kspace(bool fp64, const void* A, const double* Ahead, int n, int mpad, int kh,
                         const void* v, const double* vhead, int frames, double* bsol,
                         const uint32_t* sfix, const int* hkl, const double* sqw,
-                        cudaStream_t s);
+                        const void* turn, cudaStream_t s);
 void launch_bsol_real_and_finish(const double* xyz, const double* alpha, const uint32_t* sfix,
                                  int n, const double* ion_xyz, const double* ion_q,
                                  const uint32_t* sion, int frames, int n_ion,

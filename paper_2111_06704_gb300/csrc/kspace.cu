@@ -86,21 +86,6 @@ __device__ __forceinline__ void write_planes(const PlaneOut& po, size_t e, int b
   po.p[2][e] = __bfloat16_as_ushort(__float2bfloat16_rn(r1 - __bfloat162float(b1)));
 }
 
-// sin and cos of 2 pi x for a fixed-point phase x = ph 2^-32 from the 4,096-entry table T
-// of exp(2 pi i j / 4096) as float pairs (cos hi, cos lo, sin hi, sin lo; made in FP64)
-// and the remaining angle t = 2 pi (ph mod 2^20) 2^-32 < 1.6e-3 rad by angle addition:
-// cos = Tc - (t^2/2) Tc - t Ts and sin = Ts - (t^2/2) Ts + t Tc, the large term added last
-// (t^4/24 < 3e-13 and t^3/6 are below float rounding of the result).  About one float
-// ulp, as sincos_turns, in a third of the instructions.
-__device__ __forceinline__ void sincos_table(uint32_t ph, const float4* __restrict__ T,
-                                             float* s, float* c) {
-  const float4 t4 = __ldg(T + (ph >> 20));
-  const float t = (float)(ph & 0xFFFFFu) * 1.462918119976564e-09f;  // 2 pi 2^-32
-  const float h = -0.5f * t * t;
-  *c = t4.x + fmaf(h, t4.x, fmaf(-t, t4.z, t4.y));
-  *s = t4.z + fmaf(h, t4.z, fmaf(t, t4.x, t4.w));
-}
-
 // A (lda = 2 mpad) and, with PLANES, the BF16 planes for the k-vectors [kbeg, kend)
 // (multiples of 64), the planes laid out over that window only: row stride
 // 2 (kend - kbeg), column kcol - 2 kbeg.  A may be null (a streamed build keeps no A).

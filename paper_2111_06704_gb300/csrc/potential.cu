@@ -274,7 +274,8 @@ constexpr int kDirectChunk = 256;
 __global__ void __launch_bounds__(128)
 k_bsol_kspace_direct(const uint32_t* __restrict__ sfix, int n, const int* __restrict__ hkl,
                      const double* __restrict__ sqw, int mpad, int kh,
-                     const float* __restrict__ v, double* __restrict__ bsol) {
+                     const float4* __restrict__ turn, const float* __restrict__ v,
+                     double* __restrict__ bsol) {
   __shared__ uint32_t sh[kDirectChunk][3];
   __shared__ float sv[kDirectChunk][3];  // sqrt(W), v_cos, v_sin
   const int f = blockIdx.y;
@@ -304,7 +305,7 @@ k_bsol_kspace_direct(const uint32_t* __restrict__ sfix, int n, const int* __rest
     if (i >= n) continue;
     for (int t = 0; t < cnt; ++t) {
       float sn, cs;
-      sincos_turns(sh[t][0] * u0 + sh[t][1] * u1 + sh[t][2] * u2, &sn, &cs);
+      sincos_table(sh[t][0] * u0 + sh[t][1] * u1 + sh[t][2] * u2, turn, &sn, &cs);
       const float term = sv[t][0] * fmaf(sn, sv[t][2], cs * sv[t][1]);
       const float s2 = hi + term;
       const float bb = s2 - hi;
@@ -507,13 +508,14 @@ void launch_ion_structure_factor(bool fp64, const double* ion_xyz, const uint32_
 void launch_bsol_kspace(bool fp64, const void* A, const double* Ahead, int n, int mpad, int kh,
                         const void* v, const double* vhead, int frames, double* bsol,
                         const uint32_t* sfix, const int* hkl, const double* sqw,
-                        cudaStream_t s) {
+                        const void* turn, cudaStream_t s) {
   const int64_t lda = 2 * (int64_t)mpad;
   if (!A && !fp64) {
     for (int f0 = 0; f0 < frames; f0 += 65535) {
       const int nf = std::min(frames - f0, 65535);
       (k_bsol_kspace_direct<<<dim3((n + 127) / 128, nf), 128, 0, s>>>(
-           sfix, n, hkl, sqw, mpad, kh, (const float*)v + f0 * lda, bsol + (int64_t)f0 * n),
+           sfix, n, hkl, sqw, mpad, kh, (const float4*)turn, (const float*)v + f0 * lda,
+           bsol + (int64_t)f0 * n),
        note_launch());
     }
     for (int g0 = 0; kh > 0 && g0 < (frames + 3) / 4; g0 += 65535) {
