@@ -643,7 +643,7 @@ def run_batch(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16x6 (f32-accurate)", "data": "synthetic",
+        "dtype": "bf16x6+fp16x3+fp8 (f32-accurate)", "data": "synthetic",
         "config": {"workload": f"batching form: two-sheet graphene N={n}, {F} frames x "
                                f"{io.n_ion} ions per step incl. E/P/d build",
                    "frames": F, "ions": io.n_ion, "tol": TOL,
@@ -840,7 +840,7 @@ def run_learned(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": 1, "warmup": args.warmup, "ms_per_step": 1e3 * s_learn,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16x6 (f32-accurate); guess network bf16 weights, f32 accumulation",
+        "dtype": "bf16x6+fp16x3+fp8 (f32-accurate); guess network bf16 weights, f32 accumulation",
         "data": "synthetic",
         "config": {"workload": f"learned-guess form: two-sheet graphene N={n}, 200 ions "
                                f"random-walked 0.1 A/frame, {T} training frames, {H} held-out "
