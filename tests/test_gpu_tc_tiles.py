@@ -72,3 +72,15 @@ def test_rebuilds_reuse_or_release_the_workspace():
         if release:
             ctx.cpm_release_workspace()
     ctx.close()
+
+
+def test_tile_pairs_match_single_tiles(monkeypatch):
+    # the default runs tile pairs as two-CTA clusters that share the operand rows by
+    # multicast; one CTA per tile (CPM_TC_PAIRS=0) sums the same products in the same
+    # order, so E is the same bit for bit (a ragged size: an even row's pair ends in a
+    # CTA with no tile of its own)
+    el = wl.two_sheet_electrode(13, 11)
+    e_pairs, _ = build(el, cpm.CPM_PREC_BF16X6)
+    monkeypatch.setenv("CPM_TC_PAIRS", "0")
+    e_single, _ = build(el, cpm.CPM_PREC_BF16X6)
+    assert np.array_equal(e_pairs, e_single)
