@@ -39,6 +39,7 @@ def test_tensor_core_tail_against_fp64(cells):
     e, info = build(el, cpm.CPM_PREC_BF16X6)
     n6, n3, n1 = info["tc_blocks"]
     assert n6 > 0 and n3 > 0 and n1 > 0  # all three product counts take part
+    assert 0 < info["tc_blocks_fp8"] < n1  # one-product blocks in FP16 and in FP8
     assert n6 % 2 == 0 and (n6 + n3) % 2 == 0  # region ends hold whole [cos | sin] pairs
     scale = np.abs(e64).max()
     d = e - e64
