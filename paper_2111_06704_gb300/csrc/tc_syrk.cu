@@ -8,17 +8,20 @@
 //   six BF16 products a0 b0 + a0 b1 + a1 b0 + a0 b2 + a1 b1 + a2 b0 (a = a0 + a1 + a2,
 //     ~2^-24 of each product), for the heavier part;
 //   three FP16 products h0 g0 + h0 g1 + h1 g0 of the block's power-of-two scaled values
-//     (x = h0 + h1, within 5 x 2^-22), or one, h0 g0 (within 2^-10 + 2^-23),
+//     (x = h0 + h1, within 5 x 2^-22), or one, h0 g0 (within 2^-10 + 2^-23), or, for the
+//     lightest blocks, one E4M3 product (within 0.13),
 // such that each reduced group's summed weight times its bound stays below 1e-8 (E
-// entries are O(1)).  BF16 x BF16 and FP16 x FP16 products are exact in the FP32
-// accumulator.
+// entries are O(1)).  BF16 x BF16, FP16 x FP16 and E4M3 x E4M3 products are exact in the
+// FP32 accumulator.
 //
-// Tiles of 256 x 256 outputs of the lower triangle, one CTA each; warp roles: TMA
-// producer, single-thread MMA issuer, eight epilogue warps.  All 512 TMEM columns hold
-// two M = 128, N = 256 FP32 accumulators.  After each accumulation chunk of the host's
-// schedule the MMAs pause while the epilogue adds the accumulator (times the chunk's
-// scale) into the tile's running hi / lo floats by an error-free two-sum; the last chunk
-// adds hi + lo + the accumulator to the FP64 head and writes float E (or FP64 head).
+// Tiles of 256 x 256 outputs of the lower triangle, one CTA each; by default two tiles of
+// one tile row run as a two-CTA cluster that loads their shared operand rows once, by
+// multicast.  Warp roles: TMA producer, single-thread MMA issuer, eight epilogue warps.
+// All 512 TMEM columns hold two M = 128, N = 256 FP32 accumulators.  After each
+// accumulation chunk of the host's schedule the MMAs pause while the epilogue adds the
+// accumulator (times the chunk's scale) into the tile's running hi / lo floats by an
+// error-free two-sum; the last chunk adds hi + lo + the accumulator to the FP64 head and
+// writes float E (or FP64 head).
 //
 // Every wait is bounded: on timeout the kernel records an error code and leaves; the
 // host reports a CPM_ECUDA-class failure instead of hanging.
@@ -208,8 +211,9 @@ __device__ __forceinline__ void tri_tile(int t, int& I, int& J) {
 // operand bytes per MMA, which is what limits these stages.
 //   SIX = true (BF16, the six-product K-blocks): stages of 32 columns of planes 0-2 for the
 //     tile's 256 rows and 256 columns (96 KB, 24 MMAs of 128 x 256 x 16); two stages.
-//   SIX = false (FP16): three-product stages (32 columns of planes 0 and 1, 64 KB, 12 MMAs)
-//     then one-product stages (64 columns of plane 0, 64 KB, 8 MMAs); three stages.
+//   SIX = false (FP16 / FP8): three-product stages (32 columns of planes 0 and 1, 64 KB,
+//     12 MMAs), then one-product FP16 stages (64 columns of plane 0, 64 KB, 8 MMAs), then
+//     FP8 stages (the 128 columns of one [cos | sin] pair, 64 KB, 8 MMAs); three stages.
 // The tensor cores' FP32 adds lose ~0.1 ulp each on average, not centred, so the
 // accumulator is drained after each accumulation chunk: the MMAs pause while the
 // epilogue adds it, by an error-free two-sum, into the tile's running hi / lo floats in
