@@ -1,9 +1,10 @@
 """Pins of the FP64 oracle to values fixed by the paper and by mathematics (no GPU).
 
 Each test ties an oracle function to something other than itself: printed constants
-(Table 1, Supplementary Note on the Madelung constant, Fig. 1, Fig. 2), textbook
-constants (rock salt), an independent brute-force lattice sum (Eq. 17 with a finite
-neutralising width), the splitting-parameter independence of Eq. 19-20, and the
+(all rows of Table 1 with its width and screening columns, the Supplementary Note's
+Madelung constants, both kept with their citations under tests/golden/; Fig. 1, Fig. 2),
+textbook constants (rock salt), an independent brute-force lattice sum (Eq. 17 with a
+finite neutralising width), the splitting-parameter independence of Eq. 19-20, and the
 agreement of three independent routes to the neutral charges (Eq. 29 + 34, Eq. 33,
 Eq. 35).
 """
@@ -16,7 +17,7 @@ from oracle import ewald as ew
 from oracle import precond as pc
 from oracle import solve as sv
 from paper_2111_06704_gb300 import workloads as wl
-from tests import _cases
+from tests import _cases, _golden
 
 INF = np.inf
 S3 = math.sqrt(3.0)
@@ -29,19 +30,23 @@ def _point_matrix(xyz, box, g, rc, slab=False, eps=1e-16):
 
 # ---------------------------------------------------------------- Madelung constants
 
+# printed values, with their citations, in tests/golden/madelung_3d.txt
+MADELUNG = {r[0]: float(r[2]) for r in _golden.rows("madelung_3d.txt")}
+
+
 @pytest.mark.parametrize("edge", [1.0, 2.5])
 def test_simple_cubic_wigner_constant(edge):
     # Supplementary Note "Madelung constant in Ewald interaction matrix": the diagonal
-    # entry of E for one point charge in a cube of edge L is xi / L, xi = -2.837297479.
+    # entry of E for one point charge in a cube of edge L is xi / L.
     e = _point_matrix([[0.1 * edge, 0.2 * edge, 0.3 * edge]], (edge,) * 3, 3.0 / edge,
                       3.0 * edge)
-    assert e[0, 0] * edge == pytest.approx(-2.837297479, abs=2e-9)
+    assert e[0, 0] * edge == pytest.approx(MADELUNG["SC"], abs=2e-9)
 
 
 def test_bcc_wigner_constant():
-    # Same note: U^BCC = -3.63923345028097 for the two-site body-centred cubic cell.
+    # Same note: U^BCC for the two-site body-centred cubic cell.
     e = _point_matrix([[0, 0, 0], [0.5, 0.5, 0.5]], (1.0,) * 3, 3.0, 3.0)
-    assert e[0].sum() == pytest.approx(-3.63923345028097, rel=1e-9)
+    assert e[0].sum() == pytest.approx(MADELUNG["BCC"], rel=1e-9)
 
 
 def test_fcc_wigner_constant_recorded():
@@ -51,7 +56,7 @@ def test_fcc_wigner_constant_recorded():
     e = _point_matrix([[0, 0, 0], [0, 0.5, 0.5], [0.5, 0, 0.5], [0.5, 0.5, 0]], (1.0,) * 3,
                       3.0, 3.0)
     val = e[0].sum()
-    assert val == pytest.approx(-4.58536207398061, abs=6e-4)
+    assert val == pytest.approx(MADELUNG["FCC"], abs=6e-4)
     r_ws = (3.0 / (16.0 * math.pi)) ** (1.0 / 3.0)
     assert val * r_ws == pytest.approx(-1.7917472, abs=1e-7)
 
@@ -71,7 +76,7 @@ def test_fig1_three_charges_diagonal_is_xi():
     # entry of E is the SC Wigner constant xi (the self-interaction is position-free).
     e = _point_matrix([[0.5, 0.5, 0.49], [0.5, 0.5, 0.5], [0.5, 0.5, 0.51]], (1.0,) * 3, 3.0,
                       3.0)
-    assert np.allclose(np.diag(e), -2.837297479, atol=2e-9)
+    assert np.allclose(np.diag(e), MADELUNG["SC"], atol=2e-9)
     # off-diagonal entries approach the bare Coulomb law at short range (Eq. S7)
     assert e[0, 1] - e[0, 0] == pytest.approx(1.0 / 0.01, rel=1e-3)
 
@@ -87,41 +92,111 @@ def test_fig1_charge_matrix_inverse():
 
 # ------------------------------------------------------- 2D lattices (Table 1, Eq. 39)
 
-LATTICES = {
-    # name: (rectangular cell, basis, U^LATT of Table 1 at nearest-neighbour distance 1)
-    "SQ": ((1.0, 1.0), [(0, 0)], 3.90026492000196),
-    "HEX": ((1.0, S3), [(0, 0), (0.5, S3 / 2)], 4.21342263613691),
+CELLS = {
+    # name: (rectangular cell, basis) at nearest-neighbour distance 1
+    "SQ": ((1.0, 1.0), [(0, 0)]),
+    "HEX": ((1.0, S3), [(0, 0), (0.5, S3 / 2)]),
     "Kagome": ((2.0, 2 * S3), [(0, 0), (1, 0), (0.5, S3 / 2), (1, S3), (0, S3),
-                               (1.5, 1.5 * S3)], 3.51118553011409),
-    "GRA": ((S3, 3.0), [(0, 0), (0, 1), (S3 / 2, 1.5), (S3 / 2, 2.5)], 3.32302166466011),
+                               (1.5, 1.5 * S3)]),
+    "GRA": ((S3, 3.0), [(0, 0), (0, 1), (S3 / 2, 1.5), (S3 / 2, 2.5)]),
 }
+# Table 1's rows, as printed (tests/golden/table1_2d_lattices.txt)
+TABLE1 = _golden.rows("table1_2d_lattices.txt")
+TABLE1_IDS = [f"{r[0]}@{r[1]}" for r in TABLE1]
 
 
-@pytest.mark.parametrize("name", sorted(LATTICES))
-def test_table1_lattice_constants(name):
+def _density(name):
+    """Sites per unit area at nearest-neighbour distance 1."""
+    (ax, ay), basis = CELLS[name]
+    return len(basis) / (ax * ay)
+
+
+def _r1nn(row):
+    """The row's nearest-neighbour distance: 1, or the one at which the lattice has
+    graphene's density at its 1.42 A bond length (the table's second block)."""
+    if float(row[1]) == 1.0:
+        return 1.0
+    return 1.42 * math.sqrt(_density(row[0]) / _density("GRA"))
+
+
+def _sheet(name, r1):
+    """A flat periodic sheet of about 6 x 6 (x r1) in a box 40 r1 tall."""
+    (ax, ay), basis = CELLS[name]
+    nx, ny = max(1, round(6 / ax)), max(1, round(6 / ay))
+    pts = [((ix * ax + bx) * r1, (iy * ay + by) * r1, 0.0) for ix in range(nx)
+           for iy in range(ny) for bx, by in basis]
+    return np.array(pts), (nx * ax * r1, ny * ay * r1, 40.0 * r1)
+
+
+def _u_tol(row):
+    """How closely U^LATT of a row is reproduced: the rows at distance 1 and graphene's
+    row to their printed digits; the other rows of the density-matched block only to
+    within 5e-10 relative (their printed digits drift from U(1) / R_1nn there)."""
+    u = float(row[3])
+    return 1e-12 if (float(row[1]) == 1.0 or row[0] == "GRA") else 5e-10 * u
+
+
+def _last_digit(text):
+    """One unit of the last printed decimal of `text`."""
+    return 10.0 ** -len(text.split(".")[1])
+
+
+@pytest.mark.parametrize("row", TABLE1, ids=TABLE1_IDS)
+def test_table1_lattice_constants(row):
     # One flat sheet of equal point charges in a tall periodic box with the slab
     # correction of Eq. 39: the Lz^2/6 term cancels the 3D background's sheet-to-sheet
-    # potential exactly, so the row sum of E is the 2D Wigner potential -U^LATT / r_1nn
-    # (Table 1; Sec. III C gives U^GRA / r_1NN = -3.32302166466011).
-    (ax, ay), basis, u = LATTICES[name]
-    nx, ny = max(1, round(6 / ax)), max(1, round(6 / ay))
-    pts = [(ix * ax + bx, iy * ay + by, 0.0) for ix in range(nx) for iy in range(ny)
-           for bx, by in basis]
-    box = (nx * ax, ny * ay, 40.0)
-    e = _point_matrix(pts, box, 1.2, 5.0, slab=True)
-    assert np.allclose(e.sum(axis=1), -u, atol=1e-12)
+    # potential exactly, so every row sum of E is the 2D Wigner potential -U^LATT
+    # (Sec. III C: U^GRA / r_1NN = -3.32302166466011 at r_1NN = 1).
+    name, u = row[0], float(row[3])
+    r1 = _r1nn(row)
+    # the derived distance and density agree with the printed ones (Table 1 prints the
+    # square lattice's 1.61845 as 1.619)
+    assert abs(r1 - float(row[1])) <= 1e-3
+    assert abs(_density(name) / r1**2 - float(row[2])) <= _last_digit(row[2])
+    pts, box = _sheet(name, r1)
+    e = _point_matrix(pts, box, 1.2 / r1, 5.0 * r1, slab=True)
+    assert np.allclose(e.sum(axis=1), -u, rtol=0, atol=_u_tol(row))
+
+
+@pytest.mark.parametrize("row", TABLE1, ids=TABLE1_IDS)
+def test_table1_gaussian_width_columns(row):
+    # Table 1's width columns: alpha0 = sqrt(pi/2) U^LATT makes a charge's Gaussian
+    # self-energy sqrt(2/pi) alpha0 (Eq. 6) cancel the lattice potential, and the
+    # nearest neighbours screen one another by erfc(alpha_ii0 R_1nn) with the cross width
+    # alpha_ii0 of two equal Gaussians (Sec. II A).  With alpha = alpha0 on every atom,
+    # a row sum of E is then minus the neighbours' screening alone.
+    from scipy.special import erfc
+    name, u = row[0], float(row[3])
+    r1 = _r1nn(row)
+    a0 = math.sqrt(math.pi / 2) * u
+    aii = ew.mix_alpha(a0, a0)
+    # printed to a few decimals; Table 1 rounds graphene's 2.93295 1/A to 2.934
+    assert abs(a0 - float(row[4])) <= 1.5 * _last_digit(row[4])
+    assert abs(aii - float(row[5])) <= 1.5 * _last_digit(row[5])
+    # the screening column is printed to 7 decimals, the Kagome row truncated
+    assert abs(erfc(aii * r1) - float(row[6])) <= 1e-7
+    pts, box = _sheet(name, r1)
+    e = ew.interaction_matrix(pts, np.full(len(pts), a0), box, 1.2 / r1, 5.0 * r1, 1e-16,
+                              True)
+    # brute force over the infinite sheet: every other site within 5 R_1nn of a site
+    (ax, ay), basis = CELLS[name]
+    cells = [(ix * ax + bx, iy * ay + by) for ix in range(-8, 9) for iy in range(-8, 9)
+             for bx, by in basis]
+    for i in range(len(basis)):
+        d = np.hypot(*(np.array(cells) - np.array(basis[i])).T) * r1
+        d = d[(d > 1e-9) & (d < 5.0 * r1)]
+        screen = np.sum(erfc(aii * d) / d)
+        assert screen > 0
+        assert e[i].sum() == pytest.approx(-screen, abs=1e-11 + _u_tol(row))
 
 
 def test_table1_graphene_at_bond_length():
-    # Table 1 lists U^GRA = 2.34015610187332 at r_1nn = 1.42 A; Sec. III C gives the
-    # matching width alpha0 = sqrt(pi/2) U^GRA = 2.93295072600296 1/A.
-    (ax, ay), basis, _ = LATTICES["GRA"]
-    s = 1.42
-    pts = [(ix * ax * s + bx * s, iy * ay * s + by * s, 0.0) for ix in range(3)
-           for iy in range(2) for bx, by in basis]
-    box = (3 * ax * s, 2 * ay * s, 50.0)
-    e = _point_matrix(pts, box, 1.0, 6.0, slab=True)
-    assert e[0].sum() == pytest.approx(-2.34015610187332, abs=1e-12)
+    # Sec. III C: graphene at r_1nn = 1.42 A has the matching width
+    # alpha0 = sqrt(pi/2) U^GRA = 2.93295072600296 1/A.
+    row = next(r for r in TABLE1 if r[0] == "GRA" and r[1] == "1.420")
+    pts, box = _sheet("GRA", 1.42)
+    e = _point_matrix(pts, box, 1.2 / 1.42, 5.0 * 1.42, slab=True)
+    assert e[0].sum() == pytest.approx(-float(row[3]), abs=1e-12)
     assert math.sqrt(math.pi / 2) * -e[0].sum() == pytest.approx(2.93295072600296, abs=1e-11)
 
 
