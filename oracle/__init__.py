@@ -18,7 +18,8 @@ Dynamics Simulation" (arXiv 2111.06704), cited by section and equation:
   silent on it) in FP64 with hand-written backpropagation.
 
 Parity status: every function is pinned by ``tests/test_oracle_pins.py`` (Madelung
-constants, 2D lattice constants of Table 1, a brute-force real-space lattice sum of
-Eq. 17, splitting-parameter independence, three routes to the neutral charges, the
-Fig. 2 neighbour count) except where a function's docstring says "parity unpinned".
+constants, the 2D lattice constants and Gaussian widths of Table 1, brute-force
+real-space lattice sums of Eq. 17 for E and for b^sol, splitting-parameter independence,
+three routes to the neutral charges, the Fig. 2 neighbour count) except where a
+function's docstring says "parity unpinned".
 """

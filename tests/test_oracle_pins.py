@@ -4,7 +4,8 @@ Each test ties an oracle function to something other than itself: printed consta
 (all rows of Table 1 with its width and screening columns, the Supplementary Note's
 Madelung constants, both kept with their citations under tests/golden/; Fig. 1, Fig. 2),
 textbook constants (rock salt), an independent brute-force lattice sum (Eq. 17 with a
-finite neutralising width), the splitting-parameter independence of Eq. 19-20, and the
+finite neutralising width) for E and for the electrolyte potential b^sol of Eq. 25, the
+splitting-parameter independence of Eq. 19-20, and the
 agreement of three independent routes to the neutral charges (Eq. 29 + 34, Eq. 33,
 Eq. 35).
 """
@@ -202,27 +203,29 @@ def test_table1_graphene_at_bond_length():
 
 # ------------------------------------------- brute force and splitting independence
 
-def _eq17_brute_force(xyz, alpha, box, lam, rmax):
+def _eq17_brute_force(xyz, alpha, box, lam, rmax, xyz_b=None, alpha_b=None):
     """Eq. 17 with a finite neutralising width lambda: a direct real-space lattice sum
     of [erf(alpha_ij r) - erf(lambda r)] / r minus pi / (V lambda^2).  Exact up to
-    exp(-K_min^2 / 4 lambda^2) because lambda's own reciprocal sum is dropped."""
+    exp(-K_min^2 / 4 lambda^2) because lambda's own reciprocal sum is dropped.  With a
+    second set (xyz_b, alpha_b; inf for a point charge) the block between the two sets."""
     from scipy.special import erf
     xyz = np.asarray(xyz)
+    same = xyz_b is None
+    xb, ab = (xyz, alpha) if same else (np.asarray(xyz_b), alpha_b)
     L = np.asarray(box)
-    n = len(xyz)
     nr = [int(math.ceil(rmax / l)) for l in L]
     grid = np.array(np.meshgrid(*[np.arange(-m, m + 1) for m in nr], indexing="ij"))
     shifts = grid.reshape(3, -1).T * L
-    out = np.zeros((n, n))
-    for i in range(n):
-        for j in range(n):
-            aij = ew.mix_alpha(alpha[i], alpha[j])
-            d = xyz[i] - xyz[j] + shifts
+    out = np.zeros((len(xyz), len(xb)))
+    for i in range(len(xyz)):
+        for j in range(len(xb)):
+            aij = ew.mix_alpha(alpha[i], ab[j])
+            d = xyz[i] - xb[j] + shifts
             r = np.sqrt((d * d).sum(axis=1))
             keep = (r < rmax) & (r > 0)
             rr = r[keep]
             s = np.sum((erf(aij * rr) - erf(lam * rr)) / rr)
-            if i == j:
+            if same and i == j:
                 s += 2.0 * (aij - lam) / math.sqrt(math.pi)  # r -> 0 limit of the n = 0 term
             out[i, j] = s
     return out - math.pi / (np.prod(L) * lam * lam)
@@ -236,6 +239,36 @@ def test_eq17_brute_force_lattice_sum():
     ref = _eq17_brute_force(xyz, alpha, box, lam=0.09, rmax=75.0)
     e = ew.interaction_matrix(xyz, alpha, box, 0.9, 6.6, 1e-16, slab=False)
     assert np.allclose(e, ref, atol=1e-11, rtol=0)
+
+
+def test_electrolyte_potential_brute_force():
+    # Eq. 25: b^sol_i = sum_I q_I e_iI with the point-Gaussian width alpha_iI = alpha_i,
+    # against the Eq. 17 lattice sum of Gaussian electrode atoms and point ions (a net
+    # ionic charge, so the background term counts too)
+    rng = np.random.default_rng(12)
+    box = (5.0, 5.5, 6.0)
+    xyz = rng.uniform(0, 1, (3, 3)) * np.array(box)
+    alpha = rng.uniform(1.5, 2.5, 3)
+    ion_xyz = rng.uniform(0, 1, (4, 3)) * np.array(box)
+    ion_q = np.array([1.0, -1.0, 1.0, 1.0])
+    ref = _eq17_brute_force(xyz, alpha, box, 0.09, 75.0, ion_xyz, np.full(4, INF)) @ ion_q
+    bsol = ew.electrolyte_potential(xyz, alpha, ion_xyz, ion_q, box, 0.9, 6.6, 1e-16,
+                                    slab=False)
+    assert np.allclose(bsol, ref, atol=1e-11, rtol=0)
+
+
+def test_electrolyte_potential_is_a_block_of_e():
+    # with the slab correction too: e_iI is the electrode-ion block of E over the union
+    # of electrode atoms and point ions (Eq. 22 for i != j, Eq. 39), whose slab term the
+    # Table 1 sheets pin
+    work = _cases.tiny_two_sheet(q_sol=2)
+    el, io = work.electrode, work.electrolyte
+    both = np.vstack([el.xyz, io.xyz[0]])
+    alpha = np.concatenate([el.alpha, np.full(len(io.q[0]), INF)])
+    e = ew.interaction_matrix(both, alpha, el.box, 0.3, 12.0, 1e-8, True)
+    bsol = ew.electrolyte_potential(el.xyz, el.alpha, io.xyz[0], io.q[0], el.box, 0.3, 12.0)
+    ref = e[:el.n, el.n:] @ io.q[0]
+    assert np.abs(bsol - ref).max() < 1e-12 * np.abs(ref).max()
 
 
 def test_splitting_parameter_independence():
