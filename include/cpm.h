@@ -61,8 +61,10 @@ extern "C" {
 #define CPM_PREC_FP64 0    /* FP64 phases, FP64 structure-factor GEMM, FP64 E and matvec */
 #define CPM_PREC_FP32 1    /* exact fixed-point phases, FP32 SIMT GEMM with K-chunks
                               summed in FP64, FP32 E, FP32 matvec with FP64 reductions */
-#define CPM_PREC_BF16X6 2  /* as FP32, but the GEMM runs on tcgen05 tensor cores with a
-                              three-way BF16 split of each operand (6 products) */
+#define CPM_PREC_BF16X6 2  /* as FP32, but the GEMM runs on tcgen05 tensor cores: six
+                              products of a three-way BF16 split of each operand for
+                              the heavy k-vectors, three or one FP16 or one FP8 product
+                              of scaled operands for the light ones (cpm_plan_kspace) */
 
 /* ---- preconditioners (Sec. III B 2) ----------------------------------------------- */
 #define CPM_PRECOND_NONE 0    /* conventional CG */
@@ -137,6 +139,40 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha);
  * operand A stay.  Waits for the context's stream first.  No counterpart in the paper:
  * device-memory management of this library. */
 int cpm_release_workspace(cpm_ctx* c);
+
+/*
+ * The host plan of the k-space sum of cpm_build_E for the parameters p: host arithmetic
+ * only, no context, build or GPU.
+ *  - The k-vector table of Eq. 13 / Eq. 20 (as above) in the build's order, decreasing
+ *    weight W_K (ties keep the h, k, l loop order).
+ *  - The head: the leading operand columns (cos and sin halves of 64 k-vectors per 128
+ *    columns) that the build sums in float-float (BF16X6) or FP64 (FP32) arithmetic.
+ *  - For BF16X6, the tail after the head in K-blocks of 64 operand columns (block b:
+ *    the cos (b even) or sin (b odd) half of k-vectors 64 (b / 2) ..): each block's
+ *    product format, its power-of-two operand scale 2^kexp and the blocks that end an
+ *    accumulation chunk.  Each format's region is the longest run of trailing blocks
+ *    whose summed bound 64 max W_K times the format's error per product stays within
+ *    1e-8 (E4M3: 0.13, one FP16 product: 2^-10 + 2^-23, three: 5 x 2^-22), region ends
+ *    rounded up to even blocks; six BF16 products before them.
+ * out: sizes and region bounds.  hkl[3 m] (h, k, l per k-vector), w[m] (W_K, 1/A),
+ * kexp[kb_end] and chunk_end[kb_end] (1 where a chunk ends): host arrays, filled when not
+ * NULL (call once with NULL arrays for the sizes).  CPM_EINVAL for a NULL p or out or
+ * parameters cpm_create rejects.
+ */
+typedef struct cpm_kspace_plan {
+  int m;          /* k-vectors in the table */
+  int m_pad;      /* m rounded up to 64 (the operand has 2 m_pad columns) */
+  int head_cols;  /* leading operand columns summed in float-float / FP64 */
+  int kb_begin;   /* first K-block of the tail: head_cols / 64 */
+  int kb6_end;    /* six BF16 products in [kb_begin, kb6_end) */
+  int kb3_end;    /* three FP16 products in [kb6_end, kb3_end) */
+  int kb8_begin;  /* one FP16 product in [kb3_end, kb8_begin), one E4M3 product after */
+  int kb_end;     /* 2 m_pad / 64 */
+  int chunks;     /* accumulation chunks of the tail */
+} cpm_kspace_plan;
+
+int cpm_plan_kspace(const cpm_params* p, cpm_kspace_plan* out, int* hkl, double* w,
+                    int* kexp, uint8_t* chunk_end);
 
 /*
  * b = chi - k_e * b^sol for `frames` electrolyte frames (Eq. 25), in the

@@ -82,13 +82,27 @@ class cpm_info_t(ctypes.Structure):
     ]
 
 
+class cpm_kspace_plan(ctypes.Structure):
+    _fields_ = [
+        ("m", ctypes.c_int),
+        ("m_pad", ctypes.c_int),
+        ("head_cols", ctypes.c_int),
+        ("kb_begin", ctypes.c_int),
+        ("kb6_end", ctypes.c_int),
+        ("kb3_end", ctypes.c_int),
+        ("kb8_begin", ctypes.c_int),
+        ("kb_end", ctypes.c_int),
+        ("chunks", ctypes.c_int),
+    ]
+
+
 EXPORTS = ["cpm_default_params", "cpm_create", "cpm_destroy", "cpm_build_E", "cpm_potential",
            "cpm_solve", "cpm_solve_static", "cpm_neutralize", "cpm_get_E", "cpm_get_info",
            "cpm_get_d", "cpm_guess_features", "cpm_mlp_forward", "cpm_mlp_grad",
            "cpm_mlp_adam", "cpm_guess_apply", "cpm_apply_E", "cpm_get_precond",
            "cpm_last_error", "cpm_batch_create", "cpm_batch_destroy", "cpm_batch_solve",
            "cpm_batch_neutralize", "cpm_batch_last_error", "cpm_get_E_rows",
-           "cpm_guess", "cpm_release_workspace"]
+           "cpm_guess", "cpm_release_workspace", "cpm_plan_kspace"]
 
 _lib = None
 
@@ -138,6 +152,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.cpm_guess_apply.argtypes = [vp, i64, vp, ctypes.c_float, vp, vp]
     lib.cpm_guess.argtypes = [vp, vp, vp, i, i, vp, vp, vp, ctypes.c_float, vp, vp]
     lib.cpm_apply_E.argtypes = [vp, i, vp, vp]
+    lib.cpm_plan_kspace.argtypes = [P(cpm_params), P(cpm_kspace_plan), vp, vp, vp, vp]
     lib.cpm_last_error.argtypes = [vp]
     lib.cpm_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -176,6 +191,31 @@ def default_params(box, **kw) -> cpm_params:
             raise KeyError(k)
         setattr(p, k, v)
     return p
+
+
+def cpm_plan_kspace(box, **params) -> dict:
+    """The host plan of the k-space sum for these parameters (no GPU needed): the plan's
+    sizes and region bounds, and the arrays hkl [m, 3], w [m], kexp [kb_end] and
+    chunk_end [kb_end] (bool)."""
+    lib = load()
+    p = default_params(box, **params)
+    plan = cpm_kspace_plan()
+    st = lib.cpm_plan_kspace(ctypes.byref(p), ctypes.byref(plan), None, None, None, None)
+    if st != CPM_OK:
+        raise CpmError(st, "cpm_plan_kspace: invalid parameters")
+    hkl = np.zeros((plan.m, 3), dtype=np.int32)
+    w = np.zeros(plan.m, dtype=np.float64)
+    kexp = np.zeros(plan.kb_end, dtype=np.int32)
+    chunk_end = np.zeros(plan.kb_end, dtype=np.uint8)
+    vp = ctypes.c_void_p
+    st = lib.cpm_plan_kspace(ctypes.byref(p), ctypes.byref(plan), hkl.ctypes.data_as(vp),
+                             w.ctypes.data_as(vp), kexp.ctypes.data_as(vp),
+                             chunk_end.ctypes.data_as(vp))
+    if st != CPM_OK:
+        raise CpmError(st, "cpm_plan_kspace failed")
+    out = {name: getattr(plan, name) for name, _ in cpm_kspace_plan._fields_}
+    out.update(hkl=hkl, w=w, kexp=kexp, chunk_end=chunk_end.astype(bool))
+    return out
 
 
 class Context:

@@ -164,6 +164,136 @@ void kvector_table(const cpm_params& p, std::vector<int>& hkl, std::vector<doubl
   w.swap(w2);
 }
 
+// Host plan of the k-space sum, from the sorted k-vector weights w (mpad = their count
+// rounded up to 64) and the precision alone: the head of leading k-steps summed in float-float or
+// FP64, the flush mask of the SIMT builds, and the tensor-core tail's product regions,
+// per-block scales and accumulation chunks.
+struct KPlan {
+  int heavy_steps = 0;  // leading 16-column k-steps of the head
+  int kh = 0;           // k-vectors of the b^sol contraction kept in FP64
+  int kb0 = 0, kb6 = 0, kb3 = 0, kb8 = 0, nkb = 0;  // tensor-core K-block regions
+  std::vector<uint32_t> fmask;  // SIMT builds: k-steps after which float partials flush
+  std::vector<uint32_t> cmask;  // tensor cores: K-blocks that end an accumulation chunk
+  std::vector<int> kexp;        // tensor cores: per-K-block power-of-two scale
+};
+
+void plan_kspace(const std::vector<double>& w, int mpad, int precision, KPlan& pl) {
+  const int m = (int)w.size();
+  const bool f64 = precision == CPM_PREC_FP64;
+  // Accumulation schedule of the float k-space GEMM.  k-step s covers 16 operand
+  // columns: block s / 8 holds 64 k-vectors as [cos | sin], so its steps 0-3 and 4-7
+  // carry the same weights.  Leading blocks whose steps carry more than 2e-3 of weight
+  // are summed exactly in FP64; later float partials are flushed into FP64 once a chunk
+  // has gathered about 1e-3 of weight or 32 steps.
+  const int nk = 2 * mpad / 16;
+  std::vector<uint32_t>& fmask = pl.fmask;
+  fmask.assign((nk + 31) / 32, 0u);
+  {
+    std::vector<double> ws(nk, 0.0);
+    for (int st = 0; st < nk; ++st) {
+      const int k0 = 64 * (st / 8) + 16 * (st % 4);
+      for (int t = 0; t < 16; ++t)
+        if (k0 + t < m) ws[st] += w[k0 + t];
+    }
+    int heavy = 0;
+    while (heavy < nk && ws[heavy] > 2e-3) ++heavy;
+    heavy = std::min(std::min(nk, 128), (heavy + 7) / 8 * 8);  // at most 1024 k-vectors
+    pl.heavy_steps = heavy;
+    if (precision == CPM_PREC_BF16X6) {
+      // the tensor-core build sums its six-product blocks in chunks of up to 5e-3 of
+      // weight; only the steps heavier than that stay in the float-float head (16 of 56
+      // steps at 12,800 atoms: the head kernel 30.7 -> 11.0 ms, E's off-diagonal RMS
+      // error against FP64 4.9e-9 -> 6.2e-9 at 3,200 atoms)
+      int h5 = 0;
+      while (h5 < nk && ws[h5] > 5e-3) ++h5;
+      pl.heavy_steps = std::min(heavy, (h5 + 7) / 8 * 8);
+    }
+    // head of the b^sol contraction kept in FP64: the heavy blocks, at least 256 and at
+    // most 1024 k-vectors
+    pl.kh = f64 ? 0 : std::min(mpad, std::max(256, std::min(1024, heavy / 8 * 64)));
+    double cw = 0.0;
+    int len = 0;
+    for (int st = heavy; st < nk; ++st) {
+      cw += ws[st];
+      ++len;
+      if (cw >= 1e-3 || len >= 32 || st == nk - 1) {
+        fmask[st >> 5] |= 1u << (st & 31);
+        cw = 0.0;
+        len = 0;
+      }
+    }
+  }
+
+  // Tensor-core build: product schedule, per-block FP16 scales and accumulation chunks of
+  // the 64-column K-blocks after the head (K-block b holds the cos or sin columns of
+  // k-vectors 64 (b / 2) ..; a pair shares its weights).
+  const int nkb = 2 * mpad / 64;
+  std::vector<uint32_t>& cmask = pl.cmask;
+  std::vector<int>& kexp = pl.kexp;
+  cmask.assign((nkb + 31) / 32, 0u);
+  kexp.assign(nkb, 0);
+  pl.nkb = nkb;
+  {
+    // bwm[b]: 64 x the block's largest weight, which bounds the block's |a_i a_j| sums
+    std::vector<double> bw(nkb, 0.0), bwm(nkb, 0.0);
+    for (int b = 0; b < nkb; ++b)
+      for (int t = 0; t < 64; ++t)
+        if (64 * (b / 2) + t < m) {
+          bw[b] += w[64 * (b / 2) + t];
+          bwm[b] = std::max(bwm[b], 64.0 * w[64 * (b / 2) + t]);
+        }
+    // Product count (weights decrease along the table): trailing blocks whose summed
+    // bound times the one-FP8 (E4M3) product error (2 x 2^-4 + 2^-8 + 3e-5, the last for
+    // subnormals; bound 0.13) stays within 1e-8 take one FP8 product; the blocks before
+    // them up to another 1e-8 at the one-FP16-product error (2^-10 + 2^-23) one FP16
+    // product; the blocks before them up to another 1e-8 at the three-FP16-product error
+    // (5 x 2^-22) three; the rest the six BF16 products (~2^-24).  All ends even: whole
+    // [cos | sin] pairs per region, one more block with more products at most.
+    const int kb0 = pl.heavy_steps / 4;
+    const double budget = 1e-8;
+    int kb8 = nkb;
+    double tw = 0.0;
+    while (kb8 > kb0 && (tw + bwm[kb8 - 1]) * 0.13 <= budget) tw += bwm[--kb8];
+    kb8 = std::min(nkb, (kb8 + 1) & ~1);
+    int kb3 = kb8;
+    tw = 0.0;
+    while (kb3 > kb0 && (tw + bwm[kb3 - 1]) * (0x1p-10 + 0x1p-23) <= budget) tw += bwm[--kb3];
+    kb3 = std::min(kb8, (kb3 + 1) & ~1);
+    int kb6 = kb3;
+    tw = 0.0;
+    while (kb6 > kb0 && (tw + bwm[kb6 - 1]) * 5 * 0x1p-22 <= budget) tw += bwm[--kb6];
+    kb6 = std::min(kb3, (kb6 + 1) & ~1);
+    pl.kb0 = kb0;
+    pl.kb6 = kb6;
+    pl.kb3 = kb3;
+    pl.kb8 = kb8;
+    // FP16 blocks: x = 2^e a with 2^e sqrt(max W) in [1/2, 1), so |x| < 1; FP8 blocks
+    // 2^8 times that, [128, 256), inside E4M3's normal range (max 448)
+    for (int b = kb6; b < nkb; ++b)
+      if (bwm[b] > 0.0) kexp[b] = -ilogb(sqrt(bwm[b] / 64.0)) - 1 + (b >= kb8 ? 8 : 0);
+    // Accumulation chunks.  Six-product blocks: up to 5e-3 of weight or 32 blocks (the
+    // FP32 accumulation error of a chunk stays near 6e-8 x 5e-3 x sqrt(768 terms) ~ 1e-8;
+    // measured: E unchanged at the 512-atom cell against 5e-4 / 8; at 3,200 atoms 2e-2 / 32
+    // doubles the off-diagonal RMS error, 3.9e-9 -> 9.7e-9).  FP16 and FP8 blocks: one
+    // scale per chunk (a chunk ends where the next block's scale differs, always after a
+    // whole [cos | sin] pair), at most 512 blocks; their summed weight is below 1e-2.
+    double cw = 0.0;
+    int len = 0;
+    for (int b = kb0; b < nkb; ++b) {
+      cw += bw[b];
+      ++len;
+      const bool end = b == nkb - 1 || b + 1 == kb6 ||
+                       (b < kb6 ? (cw >= 5e-3 || len >= 32)
+                                : (kexp[b + 1] != kexp[b] || len >= 512));
+      if (end) {
+        cmask[b >> 5] |= 1u << (b & 31);
+        cw = 0.0;
+        len = 0;
+      }
+    }
+  }
+}
+
 void release_workspace(Ctx* c) {
   Buf* ws[] = {&c->tc_planes[0], &c->tc_planes[1], &c->tc_planes[2], &c->tc_planes[3],
                &c->tc_head, &c->tc_err,
@@ -227,18 +357,23 @@ void cpm_default_params(cpm_params* p) {
   p->p_gap = 1;
 }
 
+static bool params_valid(const cpm_params* p) {
+  if (!(p->box[0] > 0 && p->box[1] > 0 && p->box[2] > 0) || !(p->g_ewald > 0) ||
+      !(p->rcut_real > 0) || !(p->kspace_eps > 0 && p->kspace_eps < 1))
+    return false;
+  if (p->precision != CPM_PREC_FP64 && p->precision != CPM_PREC_FP32 &&
+      p->precision != CPM_PREC_BF16X6)
+    return false;
+  if (p->precond < CPM_PRECOND_NONE || p->precond > CPM_PRECOND_DC) return false;
+  if (p->stream_operand < 0 || p->stream_operand > 1 || p->k_window < 0) return false;
+  if ((p->alloc == nullptr) != (p->free == nullptr)) return false;
+  return true;
+}
+
 int cpm_create(cpm_ctx** out, const cpm_params* p) {
   if (!out || !p) return CPM_EINVAL;
   *out = nullptr;
-  if (!(p->box[0] > 0 && p->box[1] > 0 && p->box[2] > 0) || !(p->g_ewald > 0) ||
-      !(p->rcut_real > 0) || !(p->kspace_eps > 0 && p->kspace_eps < 1))
-    return CPM_EINVAL;
-  if (p->precision != CPM_PREC_FP64 && p->precision != CPM_PREC_FP32 &&
-      p->precision != CPM_PREC_BF16X6)
-    return CPM_EINVAL;
-  if (p->precond < CPM_PRECOND_NONE || p->precond > CPM_PRECOND_DC) return CPM_EINVAL;
-  if (p->stream_operand < 0 || p->stream_operand > 1 || p->k_window < 0) return CPM_EINVAL;
-  if ((p->alloc == nullptr) != (p->free == nullptr)) return CPM_EINVAL;
+  if (!params_valid(p)) return CPM_EINVAL;
   cpm_ctx* c = new (std::nothrow) cpm_ctx();
   if (!c) return CPM_ENOMEM;
   c->p = *p;
@@ -267,6 +402,34 @@ int cpm_destroy(cpm_ctx* c) {
 }
 
 const char* cpm_last_error(const cpm_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int cpm_plan_kspace(const cpm_params* p, cpm_kspace_plan* out, int* hkl, double* w,
+                    int* kexp, uint8_t* chunk_end) {
+  if (!p || !out || !params_valid(p)) return CPM_EINVAL;
+  std::vector<int> h;
+  std::vector<double> wt;
+  cpm::kvector_table(*p, h, wt);
+  const int m = (int)wt.size();
+  const int mpad = (int)cpm::round_up(std::max(m, 1), 64);
+  cpm::KPlan pl;
+  cpm::plan_kspace(wt, mpad, p->precision, pl);
+  out->m = m;
+  out->m_pad = mpad;
+  out->head_cols = 16 * pl.heavy_steps;
+  out->kb_begin = pl.kb0;
+  out->kb6_end = pl.kb6;
+  out->kb3_end = pl.kb3;
+  out->kb8_begin = pl.kb8;
+  out->kb_end = pl.nkb;
+  out->chunks = 0;
+  for (int b = 0; b < pl.nkb; ++b) out->chunks += (pl.cmask[b >> 5] >> (b & 31)) & 1u;
+  if (hkl) std::copy(h.begin(), h.end(), hkl);
+  if (w) std::copy(wt.begin(), wt.end(), w);
+  if (kexp) std::copy(pl.kexp.begin(), pl.kexp.end(), kexp);
+  if (chunk_end)
+    for (int b = 0; b < pl.nkb; ++b) chunk_end[b] = (uint8_t)((pl.cmask[b >> 5] >> (b & 31)) & 1u);
+  return CPM_OK;
+}
 
 int cpm_release_workspace(cpm_ctx* c) {
   if (!c) return CPM_EINVAL;
@@ -299,114 +462,17 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
   for (int k = 0; k < c->m; ++k) sqw[k] = sqrt(w[k]);
   c->kw.assign(c->mpad, 0.0);
   std::copy(w.begin(), w.end(), c->kw.begin());
-  // Accumulation schedule of the float k-space GEMM.  k-step s covers 16 operand
-  // columns: block s / 8 holds 64 k-vectors as [cos | sin], so its steps 0-3 and 4-7
-  // carry the same weights.  Leading blocks whose steps carry more than 2e-3 of weight
-  // are summed exactly in FP64; later float partials are flushed into FP64 once a chunk
-  // has gathered about 1e-3 of weight or 32 steps.
-  const int nk = 2 * c->mpad / 16;
-  std::vector<uint32_t> fmask((nk + 31) / 32, 0u);
-  {
-    std::vector<double> ws(nk, 0.0);
-    for (int st = 0; st < nk; ++st) {
-      const int k0 = 64 * (st / 8) + 16 * (st % 4);
-      for (int t = 0; t < 16; ++t)
-        if (k0 + t < c->m) ws[st] += w[k0 + t];
-    }
-    int heavy = 0;
-    while (heavy < nk && ws[heavy] > 2e-3) ++heavy;
-    heavy = std::min(std::min(nk, 128), (heavy + 7) / 8 * 8);  // at most 1024 k-vectors
-    c->heavy_steps = heavy;
-    if (c->p.precision == CPM_PREC_BF16X6) {
-      // the tensor-core build sums its six-product blocks in chunks of up to 5e-3 of
-      // weight; only the steps heavier than that stay in the float-float head (16 of 56
-      // steps at 12,800 atoms: the head kernel 30.7 -> 11.0 ms, E's off-diagonal RMS
-      // error against FP64 4.9e-9 -> 6.2e-9 at 3,200 atoms)
-      int h5 = 0;
-      while (h5 < nk && ws[h5] > 5e-3) ++h5;
-      c->heavy_steps = std::min(heavy, (h5 + 7) / 8 * 8);
-    }
-    // head of the b^sol contraction kept in FP64: the heavy blocks, at least 256 and at
-    // most 1024 k-vectors
-    c->kh = f64 ? 0 : std::min(c->mpad, std::max(256, std::min(1024, heavy / 8 * 64)));
-    double cw = 0.0;
-    int len = 0;
-    for (int st = heavy; st < nk; ++st) {
-      cw += ws[st];
-      ++len;
-      if (cw >= 1e-3 || len >= 32 || st == nk - 1) {
-        fmask[st >> 5] |= 1u << (st & 31);
-        cw = 0.0;
-        len = 0;
-      }
-    }
-  }
-
-  // Tensor-core build: product schedule, per-block FP16 scales and accumulation chunks of
-  // the 64-column K-blocks after the head (K-block b holds the cos or sin columns of
-  // k-vectors 64 (b / 2) ..; a pair shares its weights).
+  KPlan pl;
+  plan_kspace(w, c->mpad, c->p.precision, pl);
+  c->heavy_steps = pl.heavy_steps;
+  c->kh = pl.kh;
+  c->kb6_end = pl.kb6;
+  c->kb3_end = pl.kb3;
+  c->kb8_begin = pl.kb8;
   const bool tc = c->p.precision == CPM_PREC_BF16X6;
-  const int nkb = 2 * c->mpad / 64;
-  std::vector<uint32_t> cmask((nkb + 31) / 32, 0u);
-  std::vector<int> kexp(nkb, 0);
-  {
-    // bwm[b]: 64 x the block's largest weight, which bounds the block's |a_i a_j| sums
-    std::vector<double> bw(nkb, 0.0), bwm(nkb, 0.0);
-    for (int b = 0; b < nkb; ++b)
-      for (int t = 0; t < 64; ++t)
-        if (64 * (b / 2) + t < c->m) {
-          bw[b] += w[64 * (b / 2) + t];
-          bwm[b] = std::max(bwm[b], 64.0 * w[64 * (b / 2) + t]);
-        }
-    // Product count (weights decrease along the table): trailing blocks whose summed
-    // bound times the one-FP8 (E4M3) product error (2 x 2^-4 + 2^-8 + 3e-5, the last for
-    // subnormals; bound 0.13) stays within 1e-8 take one FP8 product; the blocks before
-    // them up to another 1e-8 at the one-FP16-product error (2^-10 + 2^-23) one FP16
-    // product; the blocks before them up to another 1e-8 at the three-FP16-product error
-    // (5 x 2^-22) three; the rest the six BF16 products (~2^-24).  All ends even: whole
-    // [cos | sin] pairs per region, one more block with more products at most.
-    const int kb0 = c->heavy_steps / 4;
-    const double budget = 1e-8;
-    int kb8 = nkb;
-    double tw = 0.0;
-    while (kb8 > kb0 && (tw + bwm[kb8 - 1]) * 0.13 <= budget) tw += bwm[--kb8];
-    kb8 = std::min(nkb, (kb8 + 1) & ~1);
-    int kb3 = kb8;
-    tw = 0.0;
-    while (kb3 > kb0 && (tw + bwm[kb3 - 1]) * (0x1p-10 + 0x1p-23) <= budget) tw += bwm[--kb3];
-    kb3 = std::min(kb8, (kb3 + 1) & ~1);
-    int kb6 = kb3;
-    tw = 0.0;
-    while (kb6 > kb0 && (tw + bwm[kb6 - 1]) * 5 * 0x1p-22 <= budget) tw += bwm[--kb6];
-    kb6 = std::min(kb3, (kb6 + 1) & ~1);
-    c->kb6_end = kb6;
-    c->kb3_end = kb3;
-    c->kb8_begin = kb8;
-    // FP16 blocks: x = 2^e a with 2^e sqrt(max W) in [1/2, 1), so |x| < 1; FP8 blocks
-    // 2^8 times that, [128, 256), inside E4M3's normal range (max 448)
-    for (int b = kb6; b < nkb; ++b)
-      if (bwm[b] > 0.0) kexp[b] = -ilogb(sqrt(bwm[b] / 64.0)) - 1 + (b >= kb8 ? 8 : 0);
-    // Accumulation chunks.  Six-product blocks: up to 5e-3 of weight or 32 blocks (the
-    // FP32 accumulation error of a chunk stays near 6e-8 x 5e-3 x sqrt(768 terms) ~ 1e-8;
-    // measured: E unchanged at the 512-atom cell against 5e-4 / 8; at 3,200 atoms 2e-2 / 32
-    // doubles the off-diagonal RMS error, 3.9e-9 -> 9.7e-9).  FP16 and FP8 blocks: one
-    // scale per chunk (a chunk ends where the next block's scale differs, always after a
-    // whole [cos | sin] pair), at most 512 blocks; their summed weight is below 1e-2.
-    double cw = 0.0;
-    int len = 0;
-    for (int b = kb0; b < nkb; ++b) {
-      cw += bw[b];
-      ++len;
-      const bool end = b == nkb - 1 || b + 1 == kb6 ||
-                       (b < kb6 ? (cw >= 5e-3 || len >= 32)
-                                : (kexp[b + 1] != kexp[b] || len >= 512));
-      if (end) {
-        cmask[b >> 5] |= 1u << (b & 31);
-        cw = 0.0;
-        len = 0;
-      }
-    }
-  }
+  const std::vector<uint32_t>& fmask = pl.fmask;
+  const std::vector<uint32_t>& cmask = pl.cmask;
+  const std::vector<int>& kexp = pl.kexp;
 
   const size_t a_bytes = (size_t)c->npad * 2 * c->mpad * c->esz();
   // A larger than this is not kept: the tensor-core build streams it in k-windows and the
