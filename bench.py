@@ -156,19 +156,6 @@ def make_workload(cells: int, n_ion: int, rank: int):
     return el, ions[None], q[None]
 
 
-def kspace_count(box, g=wl.G_EWALD, eps=wl.KSPACE_EPS):
-    """Number of half-space k-vectors (same rule as the library's table)."""
-    import math
-    kc = 2 * g * math.sqrt(math.log(1 / eps))
-    lx, ly, lz = box
-    hm, km, lm = (int(math.floor(kc * L / (2 * math.pi))) for L in (lx, ly, lz))
-    h, k, l = np.meshgrid(np.arange(0, hm + 1), np.arange(-km, km + 1), np.arange(-lm, lm + 1),
-                          indexing="ij")
-    half = (h > 0) | ((h == 0) & (k > 0)) | ((h == 0) & (k == 0) & (l > 0))
-    k2 = (2 * math.pi * h / lx) ** 2 + (2 * math.pi * k / ly) ** 2 + (2 * math.pi * l / lz) ** 2
-    return int(np.count_nonzero(half & (k2 <= kc * kc)))
-
-
 # ------------------------------------------------------------------- the oracle on CPU
 
 def oracle_sample(el, ions, q, n_rows=1, lu_n=2048):
@@ -211,7 +198,6 @@ def run_reference(args, rank, world):
     times = []
     desc = ""
     for _ in range(args.steps):
-        t0 = time.perf_counter()
         est, desc = oracle_sample(el, ions, q)
         times.append(est)
     sec = statistics.mean(times)
@@ -339,7 +325,7 @@ def run_ours(args, rank, world, local_rank):
     if rank != 0:
         return
     peaks, src = measured_peaks()
-    m = kspace_count(el.box)
+    m = cpm.cpm_plan_kspace(el.box)["m"]  # k-vectors of the build's table
     kspace_ms = statistics.mean(info["kspace_ms"])
     # algorithmic FLOPs of the k-space GEMM: lower triangle incl. diagonal, 2M columns
     flops = 2.0 * (n * (n + 1) / 2) * (2 * m)
