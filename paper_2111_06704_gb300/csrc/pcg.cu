@@ -383,7 +383,8 @@ k_update(int n, int64_t ldv, int nrhs, const ColState* __restrict__ st,
 }
 
 // z = P r (+ p_gap * sum r on the complement of the pattern) for PCG-DC, one thread per
-// row; partial dots [r^T z_new, r^T z_old] into slots 0, 1.
+// row; partial dots [r^T z_new, r^T z_old] into slots 0, 1.  rsum_part may be the dots
+// buffer itself: the kernel only reads its slot 3 and only writes slots 0 and 1.
 __global__ void __launch_bounds__(kThreads)
 k_dc_apply(int n, int64_t ldv, int nrhs, const ColState* __restrict__ st,
            const int64_t* __restrict__ off, const int* __restrict__ idx,

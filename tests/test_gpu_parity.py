@@ -12,7 +12,6 @@ solve to 1e-9.
 import numpy as np
 import pytest
 
-from oracle import ewald as ew
 from oracle import precond as pc
 from paper_2111_06704_gb300 import cpm
 from paper_2111_06704_gb300 import workloads as wl

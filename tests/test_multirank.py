@@ -3,8 +3,6 @@ the job time is the slowest rank's, and only rank 0 reports (no GPU)."""
 import os
 import socket
 
-import numpy as np
-import pytest
 import torch.distributed as dist
 import torch.multiprocessing as mp
 
