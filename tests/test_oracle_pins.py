@@ -5,7 +5,8 @@ Each test ties an oracle function to something other than itself: printed consta
 Madelung constants, both kept with their citations under tests/golden/; Fig. 1, Fig. 2),
 textbook constants (rock salt), an independent brute-force lattice sum (Eq. 17 with a
 finite neutralising width) for E and for the electrolyte potential b^sol of Eq. 25, the
-splitting-parameter independence of Eq. 19-20, and the
+closed-form charge of a two-sheet graphene capacitor (parallel plates plus Table 1's
+lattice potential), the splitting-parameter independence of Eq. 19-20, and the
 agreement of three independent routes to the neutral charges (Eq. 29 + 34, Eq. 33,
 Eq. 35).
 """
@@ -199,6 +200,47 @@ def test_table1_graphene_at_bond_length():
     e = _point_matrix(pts, box, 1.2 / 1.42, 5.0 * 1.42, slab=True)
     assert e[0].sum() == pytest.approx(-float(row[3]), abs=1e-12)
     assert math.sqrt(math.pi / 2) * -e[0].sum() == pytest.approx(2.93295072600296, abs=1e-11)
+
+
+# ------------------------------------------------ two-sheet capacitor (closed form)
+
+@pytest.mark.parametrize("alpha", ["alpha0", 1.979, 1.2])
+@pytest.mark.parametrize("ewald", ["tight", "default"])
+def test_two_sheet_capacitor_closed_form(alpha, ewald):
+    # Two ideal graphene sheets d = 30 A apart at chi = -0.5 / +0.5 V, no ions, slab
+    # correction (Eq. 39), neutral charges from the two-step method (Eq. 35).  By symmetry
+    # every atom of a sheet carries the same charge, -q or +q.  Each sheet is a uniform
+    # density sigma = q / A_atom plus its Wigner lattice part, so the potential difference
+    # is the parallel-plate 4 pi sigma d plus, on each sheet, q times the Gaussian
+    # self-energy sqrt(2/pi) alpha (Eq. 6) minus the lattice potential U^GRA (Table 1)
+    # minus the neighbours' screening erfc(alpha_ii r) / r (Sec. II A):
+    #   q (4 pi d / A_atom + 2 W) = delta chi / k_e,  W = sqrt(2/pi) alpha - U^GRA - S.
+    # The lattice parts of one sheet reach the other as exp(-|G| d) ~ 1e-38.
+    from scipy.special import erfc
+    bond, d = 1.42, 30.0
+    u = float(next(r for r in TABLE1 if r[0] == "GRA" and r[1] == "1.420")[3])
+    if alpha == "alpha0":
+        alpha = math.sqrt(math.pi / 2) * u  # Table 1's matching width, W ~ -7e-5
+    a, b = wl.ideal_graphene_cell(bond)
+    lo = wl.graphene_sheet(4, 3, 0.0, a, b)
+    hi = wl.graphene_sheet(4, 3, d, a, b)
+    xyz = np.vstack([lo, hi])
+    box = (4 * a, 3 * b, 90.0)
+    g, rc, eps = (0.3, 18.0, 1e-14) if ewald == "tight" else (0.3, 12.0, 1e-8)
+    e = ew.interaction_matrix(xyz, np.full(len(xyz), alpha), box, g, rc, eps, True)
+    chi = np.r_[np.full(len(lo), -0.5), np.full(len(hi), 0.5)]
+    q = sv.two_step(e, chi / ew.KE, 0.0)
+    # the closed form: S over the infinite sheet by brute force
+    cell = wl.graphene_sheet(1, 1, 0.0, a, b)[:, :2]
+    sites = np.array([(ix * a + x, iy * b + y) for ix in range(-12, 13)
+                      for iy in range(-12, 13) for x, y in cell])
+    r = np.hypot(*(sites - cell[0]).T)
+    r = r[(r > 1e-9) & (r < 30.0)]
+    w = math.sqrt(2 / math.pi) * alpha - u - np.sum(erfc(ew.mix_alpha(alpha, alpha) * r) / r)
+    q0 = (1.0 / ew.KE) / (4 * math.pi * d / (a * b / 4) + 2 * w)
+    ref = np.r_[np.full(len(lo), -q0), np.full(len(hi), q0)]
+    tol = 1e-11 if ewald == "tight" else 1e-8
+    assert np.abs(q - ref).max() < tol * q0
 
 
 # ------------------------------------------- brute force and splitting independence
