@@ -20,7 +20,7 @@ Dynamics Simulation" (arXiv 2111.06704), cited by section and equation:
 Parity status: every function is pinned by ``tests/test_oracle_pins.py`` (Madelung
 constants, the 2D lattice constants and Gaussian widths of Table 1, brute-force
 real-space lattice sums of Eq. 17 for E and for b^sol, the closed-form charges of a
-two-sheet capacitor, splitting-parameter independence,
-three routes to the neutral charges, the Fig. 2 neighbour count) except where a
-function's docstring says "parity unpinned".
+two-sheet capacitor, splitting-parameter independence, three routes to the neutral
+charges, the Fig. 2 neighbour count) except where a function's docstring says "parity
+unpinned".
 """
