@@ -57,3 +57,30 @@ def test_create_rejects_missing_box():
     p = cpm.default_params((0.0, 10.0, 30.0))
     h = ctypes.c_void_p()
     assert lib.cpm_create(ctypes.byref(h), ctypes.byref(p)) == cpm.CPM_EINVAL
+
+
+def _null_args(fn):
+    """NULL for every pointer argument, zero for every number (per the binding's argtypes)."""
+    out = []
+    for t in fn.argtypes:
+        if t in (ctypes.c_int, ctypes.c_int64):
+            out.append(0)
+        elif t in (ctypes.c_double, ctypes.c_float):
+            out.append(0.0)
+        else:
+            out.append(None)
+    return out
+
+
+def test_every_call_rejects_a_null_handle():
+    # a NULL context, batch or output handle is a bad argument (CPM_EINVAL): each call
+    # checks it before any CUDA work, so this runs without a GPU
+    lib = cpm.load()
+    skip = {"cpm_default_params", "cpm_last_error", "cpm_batch_last_error"}
+    for name in cpm.EXPORTS:
+        if name in skip:
+            continue
+        fn = getattr(lib, name)
+        assert fn(*_null_args(fn)) == cpm.CPM_EINVAL, name
+    assert lib.cpm_last_error(None) == b"null context"
+    assert lib.cpm_batch_last_error(None) == b"null batch"
