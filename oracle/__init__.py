@@ -16,6 +16,9 @@ Dynamics Simulation" (arXiv 2111.06704), cited by section and equation:
 * ``precond`` -- the PCG-DC preconditioner (Eq. 36) and p_gap (Eq. 37).
 * ``mlp``     -- the per-atom initial-guess network (project-defined; the paper is
   silent on it) in FP64 with hand-written backpropagation.
+* ``gcd``     -- fixed total charge per electrode (galvanostatic charge-discharge,
+  Eq. S14-S24): capacitance coefficients and the two-step GCD charges; pinned by
+  ``tests/test_oracle_gcd.py``.
 
 Parity status: every function is pinned by ``tests/test_oracle_pins.py`` (Madelung
 constants, the 2D lattice constants and Gaussian widths of Table 1, brute-force
