@@ -147,3 +147,14 @@ def test_plan_rejects_what_create_rejects():
     assert lib.cpm_plan_kspace(ctypes.byref(p), None, None, None, None, None) == cpm.CPM_EINVAL
     assert lib.cpm_plan_kspace(None, ctypes.byref(out), None, None, None, None) == cpm.CPM_EINVAL
     assert math.isfinite(cpm.cpm_plan_kspace((10.0, 10.0, 30.0))["w"][0])
+
+
+@pytest.mark.parametrize("box,g,m", [
+    ((8 * wl.CELL_A, 8 * wl.CELL_B, 90.0), 0.3, 8_645),          # the 512-atom cell
+    ((40 * wl.CELL_A, 40 * wl.CELL_B, 90.0), 0.3, 217_619),      # the 12,800-atom cell
+    ((90 * wl.CELL_A, 52 * wl.CELL_B, 105.0), 0.3, 742_575),     # the scale point
+    ((90 * wl.CELL_A, 52 * wl.CELL_B, 105.0), 0.15, 92_837),     # ... at its g = 0.15
+])
+def test_table_sizes_of_the_workloads(box, g, m):
+    # the k-vector counts of the workloads, counted independently of this library
+    assert _plan(box, g_ewald=g)["m"] == m
