@@ -198,6 +198,25 @@ def test_tiny_cell_with_images_and_net_charge(prec, q_sol):
     ctx.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "bf16x6"])
+def test_one_atom_electrode(prec):
+    # The degenerate electrode: one atom, so d = 1 (Eq. S8) and Eq. 35 gives it the whole
+    # compensating charge, q = -Q^sol, whatever b is; E is its self-interaction alone.
+    work = _cases.tiny_two_sheet(q_sol=3, n_ion=9)
+    el, io = work.electrode, work.electrolyte
+    one = wl.Workload("one atom", wl.Electrode(el.xyz[:1], el.alpha[:1], el.chi[:1], el.box),
+                      io)
+    oc = _cases.oracle_case(one)
+    ctx = make_ctx(one, prec, rcut_dc=3.0)
+    assert rel_max(ctx.cpm_get_E(cpm.CPM_E_PAPER), oc.e_paper) < E_TOL[prec]
+    assert np.allclose(ctx.cpm_get_d(), 1.0, rtol=0, atol=1e-12)
+    q, _, _, b, qsol = cpm.charges(ctx, io.xyz, io.q, el.chi[:1], tol=1e-10)
+    assert rel_max(b, oc.b_neutral_volts) < B_TOL[prec]
+    assert qsol[0] == 3 and q.shape == (1, 1)
+    assert q[0, 0] == pytest.approx(-3.0, abs=1e-12) and oc.q[0, 0] == pytest.approx(-3.0)
+    ctx.close()
+
+
 def test_no_ions_and_many_frames():
     work = _cases.tiny_two_sheet()
     el = work.electrode
