@@ -224,6 +224,43 @@ int cpm_solve_static(cpm_ctx* c, int nrhs, const double* b, double* q_inout, int
  */
 int cpm_neutralize(cpm_ctx* c, int nrhs, double* q_inout, const double* qsol);
 
+/* ---- fixed total charge per electrode (GCD) -------------------------------------- */
+#define CPM_GCD_MAX_ELECTRODES 16
+
+/*
+ * Galvanostatic charge-discharge constraint (Supplementary Note, Eq. S14-S24): the
+ * electrode atoms form m electrodes, each holding a given total charge Q_a^0 while its
+ * atoms share one potential shift Delta mu_a.  An alternative second step to
+ * cpm_neutralize; the first step stays cpm_solve.
+ *
+ * cpm_gcd_setup: labels[n] (host or device) assigns atom i to electrode labels[i] in
+ * 0 .. m-1, 1 <= m <= CPM_GCD_MAX_ELECTRODES, no electrode empty.  Solves
+ * E a^h = b^h (b^h one on electrode h, Eq. S22-S23) for the m electrodes by the
+ * context's PCG to the relative residual tol within maxit iterations, forms the
+ * capacitance coefficients C_ab = sum over the atoms of electrode a of a^b_i (Eq. S24),
+ * and inverts C.  Kept until the next cpm_build_E, which drops it.  c_out[m*m] (host or
+ * device, optional) receives C in e/V, row a, column b.  These are the coefficients of
+ * the stored neutral-equivalent E_n.  What charges of zero net sum see of them is the
+ * paper's, e.g. the joint capacitance (C_aa C_bb - C_ab^2) / sum_ab C_ab of Eq. S21;
+ * C_E itself is not.  iters_out[m], relres_out[m]: optional host arrays.
+ * CPM_EINVAL for bad labels or arguments, CPM_ENOCONV if a solve misses tol,
+ * CPM_EBREAKDOWN if C is singular to working precision.
+ *
+ * cpm_gcd_charges: q_inout[nrhs*n] holds q^b = E^-1 b from cpm_solve on entry and the
+ * GCD charges on exit, q = q^b + A C^-1 (Q^0 - B^T q^b) (Eq. S16-S20), with
+ * A = (a^1 .. a^m) and B the indicator columns.  q0[nrhs*m] (host or device): Q_a^0 per
+ * frame (e).  E_n stands in for E only for charges of the right net sum, so each frame's
+ * totals must balance its electrolyte charge: |sum_a q0[f*m + a] + qsol[f]| at most 1e-9
+ * of max(1, sum_a |q0[f*m + a]| + |qsol[f]|) (qsol from cpm_potential; NULL = 0), else
+ * CPM_EINVAL.  dmu_out[nrhs*m] (optional, host or device) receives Delta mu_a in volts,
+ * up to one constant per frame that the form of E shifts; differences between
+ * electrodes are the paper's.  CPM_EINVAL before cpm_gcd_setup.
+ */
+int cpm_gcd_setup(cpm_ctx* c, int m, const int* labels, double tol, int maxit, double* c_out,
+                  int* iters_out, double* relres_out);
+int cpm_gcd_charges(cpm_ctx* c, int nrhs, double* q_inout, const double* q0,
+                    const double* qsol, double* dmu_out);
+
 /* ---- learned initial guess ------------------------------------------------------------
  * The paper has no learned component; the warm start it describes is the previous MD
  * step's charges (Eq. 26).  These calls add a small per-atom network that predicts the

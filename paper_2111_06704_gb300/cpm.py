@@ -32,6 +32,8 @@ CPM_PRECOND_DC = 2
 CPM_E_STORED = 0
 CPM_E_PAPER = 1
 
+CPM_GCD_MAX_ELECTRODES = 16
+
 KE = 14.399645478  # V A / e
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -102,7 +104,8 @@ EXPORTS = ["cpm_default_params", "cpm_create", "cpm_destroy", "cpm_build_E", "cp
            "cpm_mlp_adam", "cpm_guess_apply", "cpm_apply_E", "cpm_get_precond",
            "cpm_last_error", "cpm_batch_create", "cpm_batch_destroy", "cpm_batch_solve",
            "cpm_batch_neutralize", "cpm_batch_last_error", "cpm_get_E_rows",
-           "cpm_guess", "cpm_release_workspace", "cpm_plan_kspace"]
+           "cpm_guess", "cpm_release_workspace", "cpm_plan_kspace", "cpm_gcd_setup",
+           "cpm_gcd_charges"]
 
 _lib = None
 
@@ -153,6 +156,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.cpm_guess.argtypes = [vp, vp, vp, i, i, vp, vp, vp, ctypes.c_float, vp, vp]
     lib.cpm_apply_E.argtypes = [vp, i, vp, vp]
     lib.cpm_plan_kspace.argtypes = [P(cpm_params), P(cpm_kspace_plan), vp, vp, vp, vp]
+    lib.cpm_gcd_setup.argtypes = [vp, i, vp, d, i, vp, vp, vp]
+    lib.cpm_gcd_charges.argtypes = [vp, i, vp, vp, vp, vp]
     lib.cpm_last_error.argtypes = [vp]
     lib.cpm_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -246,6 +251,7 @@ class Context:
         self._check(self.lib.cpm_create(ctypes.byref(h), ctypes.byref(self.params)), None)
         self.h = h
         self.n = 0
+        self.gcd_m = 0
 
     def _check(self, st, h=-1):
         if st != CPM_OK:
@@ -275,6 +281,7 @@ class Context:
         pa, ka = _ptr(alpha)
         self._check(self.lib.cpm_build_E(self.h, n, px, pa))
         self.n = n
+        self.gcd_m = 0  # a rebuild drops the electrodes' solves
 
     def cpm_potential(self, ion_xyz, ion_q, chi, b_out=None, qsol_out=None):
         frames, n_ion = int(ion_q.shape[0]), int(ion_q.shape[1])
@@ -333,6 +340,44 @@ class Context:
         if isinstance(q, np.ndarray) and kq is not q:
             q[...] = kq
         return q
+
+    # -- fixed charge per electrode (GCD, Eq. S14-S24) ------------------------------
+    def cpm_gcd_setup(self, labels, m=None, tol=1e-10, maxit=2000):
+        """Splits the electrode into electrodes by labels [n] (0 .. m-1) and prepares
+        their capacitance coefficients.  Returns (C [m, m] in e/V of the stored form,
+        iterations [m], relative residuals [m])."""
+        if hasattr(labels, "is_cuda") and labels.is_cuda:
+            lab, plab = labels, ctypes.c_void_p(labels.data_ptr())
+            if m is None:
+                m = int(labels.max().item()) + 1
+        else:
+            lab = np.ascontiguousarray(labels, dtype=np.int32)
+            plab = lab.ctypes.data_as(ctypes.c_void_p)
+            if m is None:
+                m = int(lab.max()) + 1
+        c = np.zeros((m, m))
+        iters = np.zeros(m, dtype=np.int32)
+        rel = np.zeros(m)
+        self._check(self.lib.cpm_gcd_setup(self.h, int(m), plab, float(tol), int(maxit),
+                                           c.ctypes.data_as(ctypes.c_void_p),
+                                           iters.ctypes.data_as(ctypes.c_void_p),
+                                           rel.ctypes.data_as(ctypes.c_void_p)))
+        self.gcd_m = m
+        return c, iters, rel
+
+    def cpm_gcd_charges(self, q, q0, qsol=None):
+        """q holds q^b [nrhs, n] (cpm_solve); on return the charges with the totals
+        q0 [nrhs, m] on the electrodes.  Returns (q, Delta mu [nrhs, m] in V)."""
+        nrhs = int(q.shape[0]) if q.ndim == 2 else 1
+        pq, kq = _ptr(q)
+        p0, k0 = _ptr(q0)
+        ps, ks = _ptr(qsol)
+        dmu = np.zeros((nrhs, self.gcd_m))
+        self._check(self.lib.cpm_gcd_charges(self.h, nrhs, pq, p0, ps,
+                                             dmu.ctypes.data_as(ctypes.c_void_p)))
+        if isinstance(q, np.ndarray) and kq is not q:
+            q[...] = kq
+        return q, dmu
 
     # -- inspection -----------------------------------------------------------------
     def cpm_get_E(self, form=CPM_E_STORED):

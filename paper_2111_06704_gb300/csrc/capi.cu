@@ -107,6 +107,18 @@ int stage_out(Ctx* c, Buf* tmp, void* dst, size_t bytes, void** out) {
   return CPM_OK;
 }
 
+// Copies `count` elements of `src` (host or device) to the host vector `dst`.
+template <typename T>
+int to_host(Ctx* c, std::vector<T>& dst, const T* src, size_t count) {
+  dst.resize(count);
+  if (!is_device_ptr(src)) {
+    std::copy(src, src + count, dst.begin());
+    return CPM_OK;
+  }
+  return cuda_check(c, cudaMemcpy(dst.data(), src, count * sizeof(T), cudaMemcpyDeviceToHost),
+                    "copy to host");
+}
+
 int copy_out(Ctx* c, void* dst, const void* dev, size_t bytes) {
   if (dst == dev) return CPM_OK;
   return cuda_check(c, cudaMemcpyAsync(dst, dev, bytes, cudaMemcpyDeviceToHost, c->stream),
@@ -308,7 +320,8 @@ void free_build(Ctx* c) {
                 &c->Ahead, &c->A,
                 &c->E, &c->diag,
                 &c->nbr_off, &c->nbr_idx, &c->prow, &c->d, &c->shell_off, &c->shell_members, &c->p_f32,
-                &c->turn};
+                &c->turn, &c->gcd_labels, &c->gcd_a, &c->gcd_c, &c->gcd_cinv, &c->gcd_status,
+                &c->gcd_work};
   for (Buf* b : all) buf_free(c, b);
   release_workspace(c);
   c->built = false;
@@ -444,6 +457,7 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
   // buffers of the previous build are reused where large enough (reserve), not freed
   c->built = false;
   c->shells_ready = false;
+  c->gcd_m = 0;  // the electrodes' solves belong to the previous E
   cudaStream_t s = c->stream;
   const bool f64 = c->fp64();
   int st;
@@ -827,6 +841,131 @@ int cpm_neutralize(cpm_ctx* c, int nrhs, double* q_inout, const double* qsol) {
   if ((st = cuda_check(c, cudaGetLastError(), "neutralize"))) return st;
   if (!q_dev && (st = copy_out(c, q_inout, dq, bytes))) return st;
   return cuda_check(c, cudaStreamSynchronize(c->stream), "neutralize sync");
+}
+
+int cpm_gcd_setup(cpm_ctx* c, int m, const int* labels, double tol, int maxit, double* c_out,
+                  int* iters_out, double* relres_out) {
+  if (!c) return CPM_EINVAL;
+  if (!c->built) return set_err(c, CPM_ENOTBUILT, "cpm_gcd_setup before cpm_build_E");
+  if (m < 1 || m > CPM_GCD_MAX_ELECTRODES || !labels || !(tol > 0) || maxit < 1)
+    return set_err(c, CPM_EINVAL, "cpm_gcd_setup: bad arguments");
+  c->gcd_m = 0;
+  const int n = c->n;
+  cudaStream_t s = c->stream;
+  int st;
+  if ((st = cuda_check(c, cudaStreamSynchronize(s), "gcd sync"))) return st;
+  // labels: every one in range and no electrode empty (checked on the host)
+  std::vector<int> lab;
+  if ((st = to_host(c, lab, labels, (size_t)n))) return st;
+  std::vector<int> count(m, 0);
+  for (int i = 0; i < n; ++i) {
+    if (lab[i] < 0 || lab[i] >= m) return set_err(c, CPM_EINVAL, "cpm_gcd_setup: label out of range");
+    ++count[lab[i]];
+  }
+  for (int a = 0; a < m; ++a)
+    if (count[a] == 0) return set_err(c, CPM_EINVAL, "cpm_gcd_setup: an electrode has no atoms");
+  const size_t vec_bytes = (size_t)m * n * sizeof(double);
+  if ((st = buf_reserve(c, &c->gcd_labels, (size_t)n * sizeof(int))) ||
+      (st = buf_reserve(c, &c->gcd_a, vec_bytes)) ||
+      (st = buf_reserve(c, &c->ws_in2, vec_bytes)) ||
+      (st = buf_reserve(c, &c->gcd_c, (size_t)m * m * sizeof(double))) ||
+      (st = buf_reserve(c, &c->gcd_cinv, (size_t)m * m * sizeof(double))) ||
+      (st = buf_reserve(c, &c->gcd_status, sizeof(int))))
+    return st;
+  int* dlab = (int*)c->gcd_labels.ptr;
+  double* rhs = (double*)c->ws_in2.ptr;
+  if ((st = cuda_check(c, cudaMemcpyAsync(dlab, lab.data(), (size_t)n * sizeof(int),
+                                          cudaMemcpyHostToDevice, s), "gcd labels")))
+    return st;
+  // Eq. S22-S23: a^h = E^-1 b^h for every electrode, one PCG over m right-hand sides
+  launch_gcd_indicators(dlab, n, m, rhs, s);
+  if ((st = cuda_check(c, cudaGetLastError(), "gcd indicators"))) return st;
+  std::vector<int> it(m);
+  std::vector<double> rr(m);
+  SolveArgs a{m, rhs, 1.0, (double*)c->gcd_a.ptr, false, tol, maxit, it.data(), rr.data()};
+  const int solve_st = pcg_solve(c, a);
+  if (iters_out) memcpy(iters_out, it.data(), m * sizeof(int));
+  if (relres_out) memcpy(relres_out, rr.data(), m * sizeof(double));
+  if (solve_st == CPM_ENOCONV)
+    return set_err(c, CPM_ENOCONV, "cpm_gcd_setup: an electrode's solve missed tol");
+  if (solve_st != CPM_OK) return solve_st;
+  // Eq. S24: C_ab = sum over electrode a of a^b, then C^-1
+  launch_gcd_sums((const double*)c->gcd_a.ptr, n, m, dlab, m, (double*)c->gcd_c.ptr, s);
+  launch_gcd_invert((const double*)c->gcd_c.ptr, m, (double*)c->gcd_cinv.ptr,
+                    (int*)c->gcd_status.ptr, s);
+  if ((st = cuda_check(c, cudaGetLastError(), "gcd capacitance"))) return st;
+  int singular = 0;
+  std::vector<double> ct((size_t)m * m);
+  if ((st = cuda_check(c, cudaMemcpyAsync(&singular, c->gcd_status.ptr, sizeof(int),
+                                          cudaMemcpyDeviceToHost, s), "gcd status")) ||
+      (st = cuda_check(c, cudaMemcpyAsync(ct.data(), c->gcd_c.ptr, ct.size() * sizeof(double),
+                                          cudaMemcpyDeviceToHost, s), "gcd C")) ||
+      (st = cuda_check(c, cudaStreamSynchronize(s), "gcd sync")))
+    return st;
+  if (singular) return set_err(c, CPM_EBREAKDOWN, "cpm_gcd_setup: C is singular");
+  if (c_out) {
+    std::vector<double> cv((size_t)m * m);
+    for (int r = 0; r < m; ++r)
+      for (int q = 0; q < m; ++q) cv[(size_t)r * m + q] = ct[(size_t)q * m + r] / kKe;  // e/V
+    if ((st = cuda_check(c, cudaMemcpy(c_out, cv.data(), cv.size() * sizeof(double),
+                                       cudaMemcpyDefault), "gcd C out")))
+      return st;
+  }
+  c->gcd_m = m;
+  return CPM_OK;
+}
+
+int cpm_gcd_charges(cpm_ctx* c, int nrhs, double* q_inout, const double* q0,
+                    const double* qsol, double* dmu_out) {
+  if (!c) return CPM_EINVAL;
+  if (!c->built) return set_err(c, CPM_ENOTBUILT, "cpm_gcd_charges before cpm_build_E");
+  if (c->gcd_m < 1) return set_err(c, CPM_EINVAL, "cpm_gcd_charges before cpm_gcd_setup");
+  if (nrhs < 1 || !q_inout || !q0) return set_err(c, CPM_EINVAL, "cpm_gcd_charges: bad arguments");
+  const int n = c->n, m = c->gcd_m;
+  cudaStream_t s = c->stream;
+  int st;
+  if ((st = cuda_check(c, cudaStreamSynchronize(s), "gcd sync"))) return st;
+  // the totals must balance the electrolyte: E_n stands in for E only then
+  std::vector<double> hq0, hqs(nrhs, 0.0);
+  if ((st = to_host(c, hq0, q0, (size_t)nrhs * m))) return st;
+  if (qsol && (st = to_host(c, hqs, qsol, (size_t)nrhs))) return st;
+  for (int f = 0; f < nrhs; ++f) {
+    double tot = hqs[f], mag = fabs(hqs[f]);
+    for (int a = 0; a < m; ++a) {
+      tot += hq0[(size_t)f * m + a];
+      mag += fabs(hq0[(size_t)f * m + a]);
+    }
+    if (!(fabs(tot) <= 1e-9 * std::max(1.0, mag)))
+      return set_err(c, CPM_EINVAL, "cpm_gcd_charges: electrode totals do not balance Q^sol");
+  }
+  const size_t bytes = (size_t)nrhs * n * sizeof(double);
+  const size_t mbytes = (size_t)nrhs * m * sizeof(double);
+  double* dq = nullptr;
+  const double* dq0 = nullptr;
+  double* ddmu = nullptr;
+  const bool q_dev = is_device_ptr(q_inout);
+  if (q_dev) {
+    dq = q_inout;
+  } else {
+    if ((st = buf_reserve(c, &c->ws_out0, bytes))) return st;
+    dq = (double*)c->ws_out0.ptr;
+    if ((st = cuda_check(c, cudaMemcpyAsync(dq, q_inout, bytes, cudaMemcpyHostToDevice, s),
+                         "q in")))
+      return st;
+  }
+  if ((st = stage_in(c, &c->ws_in1, q0, mbytes, (const void**)&dq0))) return st;
+  if (dmu_out && (st = stage_out(c, &c->ws_out1, dmu_out, mbytes, (void**)&ddmu))) return st;
+  if ((st = buf_reserve(c, &c->gcd_work, 2 * mbytes))) return st;
+  double* sums = (double*)c->gcd_work.ptr;
+  double* dmu = sums + (size_t)nrhs * m;
+  const int* dlab = (const int*)c->gcd_labels.ptr;
+  launch_gcd_sums(dq, n, nrhs, dlab, m, sums, s);  // B^T q^b
+  launch_gcd_shifts((const double*)c->gcd_cinv.ptr, dq0, sums, nrhs, m, dmu, ddmu, s);
+  launch_gcd_apply(dq, (const double*)c->gcd_a.ptr, dmu, n, nrhs, m, s);
+  if ((st = cuda_check(c, cudaGetLastError(), "gcd charges"))) return st;
+  if (!q_dev && (st = copy_out(c, q_inout, dq, bytes))) return st;
+  if (dmu_out && (st = copy_out(c, dmu_out, ddmu, mbytes))) return st;
+  return cuda_check(c, cudaStreamSynchronize(s), "gcd charges sync");
 }
 
 int cpm_get_E(cpm_ctx* c, int form, double* out, int64_t ld) {

@@ -130,6 +130,15 @@ struct Ctx {
   double c_ele = 0;
   int d_iters = 0;
 
+  // fixed charge per electrode (GCD), made by cpm_gcd_setup, dropped by a rebuild
+  int gcd_m = 0;       // electrodes; 0: not set up
+  Buf gcd_labels;      // int32 [n]
+  Buf gcd_a;           // double [m][n]: a^h = E_n^-1 b^h
+  Buf gcd_c;           // double [m][m]: C_ab at [b * m + a]
+  Buf gcd_cinv;        // double [m][m]: C^-1, row-major
+  Buf gcd_status;      // int: singular C
+  Buf gcd_work;        // double: per-frame sums and shifts
+
   // scratch (grown on demand, never shrunk)
   std::vector<Buf*> scratch;
   std::vector<double> kw;  // k-vector weights W_K of the sorted table, mpad entries (0 past m)
@@ -261,5 +270,15 @@ int build_dc_preconditioner(Ctx* c);
 int copy_precond(Ctx* c, int64_t* off, int* idx, double* val);
 int apply_p_gap(Ctx* c);
 int device_sum(Ctx* c, const double* v, int64_t len, double* out);
+
+// ---- fixed charge per electrode, GCD (gcd.cu) -------------------------------------
+void launch_gcd_indicators(const int* labels, int n, int m, double* bh, cudaStream_t s);
+void launch_gcd_sums(const double* x, int n, int nvec, const int* labels, int m, double* out,
+                     cudaStream_t s);
+void launch_gcd_invert(const double* ct, int m, double* cinv, int* status, cudaStream_t s);
+void launch_gcd_shifts(const double* cinv, const double* q0, const double* sums, int nrhs,
+                       int m, double* dmu, double* dmu_volts, cudaStream_t s);
+void launch_gcd_apply(double* q, const double* amat, const double* dmu, int n, int nrhs, int m,
+                      cudaStream_t s);
 
 }  // namespace cpm
