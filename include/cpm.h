@@ -261,6 +261,30 @@ int cpm_gcd_setup(cpm_ctx* c, int m, const int* labels, double tol, int maxit, d
 int cpm_gcd_charges(cpm_ctx* c, int nrhs, double* q_inout, const double* q0,
                     const double* qsol, double* dmu_out);
 
+/* ---- the matrix path for a small fixed electrode ---------------------------------- */
+#define CPM_SMATRIX_MAX_ATOMS 8192
+
+/*
+ * The paper's matrix alternative to the iterative solve (Eq. 33 with Eq. 35): S =
+ * E^-1 (I - 1 d^T), formed once per geometry, after which a frame's neutral charges are
+ * one dense product, q = S b - Q^sol d, with no iteration.
+ *
+ * cpm_smatrix_build: forms S from the n columns E^-1 e_j, which the context's PCG solves
+ * to the relative residual tol within maxit iterations (n right-hand sides at once).
+ * S takes 8 n^2 bytes and is kept until the next cpm_build_E, which drops it.
+ * n <= CPM_SMATRIX_MAX_ATOMS.  max_iters_out (optional): the most iterations a column
+ * took.  CPM_EINVAL for n above the limit or bad arguments, CPM_ENOCONV if a column
+ * misses tol.
+ *
+ * cpm_smatrix_charges: b[frames*n] in volts (as cpm_potential returns it), qsol[frames]
+ * (NULL = 0), q_out[frames*n]: the neutral charges (e), as cpm_solve followed by
+ * cpm_neutralize give them to the solve's tolerance.  All host or device.  CPM_EINVAL
+ * before cpm_smatrix_build.
+ */
+int cpm_smatrix_build(cpm_ctx* c, double tol, int maxit, int* max_iters_out);
+int cpm_smatrix_charges(cpm_ctx* c, int frames, const double* b, const double* qsol,
+                        double* q_out);
+
 /* ---- learned initial guess ------------------------------------------------------------
  * The paper has no learned component; the warm start it describes is the previous MD
  * step's charges (Eq. 26).  These calls add a small per-atom network that predicts the

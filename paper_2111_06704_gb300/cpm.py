@@ -33,6 +33,7 @@ CPM_E_STORED = 0
 CPM_E_PAPER = 1
 
 CPM_GCD_MAX_ELECTRODES = 16
+CPM_SMATRIX_MAX_ATOMS = 8192
 
 KE = 14.399645478  # V A / e
 
@@ -105,7 +106,7 @@ EXPORTS = ["cpm_default_params", "cpm_create", "cpm_destroy", "cpm_build_E", "cp
            "cpm_last_error", "cpm_batch_create", "cpm_batch_destroy", "cpm_batch_solve",
            "cpm_batch_neutralize", "cpm_batch_last_error", "cpm_get_E_rows",
            "cpm_guess", "cpm_release_workspace", "cpm_plan_kspace", "cpm_gcd_setup",
-           "cpm_gcd_charges"]
+           "cpm_gcd_charges", "cpm_smatrix_build", "cpm_smatrix_charges"]
 
 _lib = None
 
@@ -158,6 +159,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.cpm_plan_kspace.argtypes = [P(cpm_params), P(cpm_kspace_plan), vp, vp, vp, vp]
     lib.cpm_gcd_setup.argtypes = [vp, i, vp, d, i, vp, vp, vp]
     lib.cpm_gcd_charges.argtypes = [vp, i, vp, vp, vp, vp]
+    lib.cpm_smatrix_build.argtypes = [vp, d, i, vp]
+    lib.cpm_smatrix_charges.argtypes = [vp, i, vp, vp, vp]
     lib.cpm_last_error.argtypes = [vp]
     lib.cpm_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -378,6 +381,26 @@ class Context:
         if isinstance(q, np.ndarray) and kq is not q:
             q[...] = kq
         return q, dmu
+
+    # -- the matrix path (Eq. 33 with Eq. 35) ----------------------------------------
+    def cpm_smatrix_build(self, tol=1e-12, maxit=2000):
+        """Forms S = E^-1 (I - 1 d^T) once; returns the most PCG iterations a column took."""
+        it = ctypes.c_int(0)
+        self._check(self.lib.cpm_smatrix_build(self.h, float(tol), int(maxit), ctypes.byref(it)))
+        return it.value
+
+    def cpm_smatrix_charges(self, b, qsol=None, q_out=None):
+        """Neutral charges q = S b - Q^sol d for b [frames, n] in volts."""
+        frames = int(b.shape[0]) if b.ndim == 2 else 1
+        if q_out is None:
+            q_out = np.empty((frames, self.n))
+        pb, kb = _ptr(b)
+        ps, ks = _ptr(qsol)
+        pq, kq = _ptr(q_out)
+        self._check(self.lib.cpm_smatrix_charges(self.h, frames, pb, ps, pq))
+        if isinstance(q_out, np.ndarray) and kq is not q_out:
+            q_out[...] = kq
+        return q_out
 
     # -- inspection -----------------------------------------------------------------
     def cpm_get_E(self, form=CPM_E_STORED):

@@ -321,7 +321,7 @@ void free_build(Ctx* c) {
                 &c->E, &c->diag,
                 &c->nbr_off, &c->nbr_idx, &c->prow, &c->d, &c->shell_off, &c->shell_members, &c->p_f32,
                 &c->turn, &c->gcd_labels, &c->gcd_a, &c->gcd_c, &c->gcd_cinv, &c->gcd_status,
-                &c->gcd_work};
+                &c->gcd_work, &c->smat};
   for (Buf* b : all) buf_free(c, b);
   release_workspace(c);
   c->built = false;
@@ -457,7 +457,8 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
   // buffers of the previous build are reused where large enough (reserve), not freed
   c->built = false;
   c->shells_ready = false;
-  c->gcd_m = 0;  // the electrodes' solves belong to the previous E
+  c->gcd_m = 0;  // the electrodes' solves and S belong to the previous E
+  c->smat_ready = false;
   cudaStream_t s = c->stream;
   const bool f64 = c->fp64();
   int st;
@@ -966,6 +967,66 @@ int cpm_gcd_charges(cpm_ctx* c, int nrhs, double* q_inout, const double* q0,
   if (!q_dev && (st = copy_out(c, q_inout, dq, bytes))) return st;
   if (dmu_out && (st = copy_out(c, dmu_out, ddmu, mbytes))) return st;
   return cuda_check(c, cudaStreamSynchronize(s), "gcd charges sync");
+}
+
+int cpm_smatrix_build(cpm_ctx* c, double tol, int maxit, int* max_iters_out) {
+  if (!c) return CPM_EINVAL;
+  if (!c->built) return set_err(c, CPM_ENOTBUILT, "cpm_smatrix_build before cpm_build_E");
+  if (!(tol > 0) || maxit < 1) return set_err(c, CPM_EINVAL, "cpm_smatrix_build: bad arguments");
+  const int n = c->n;
+  if (n > CPM_SMATRIX_MAX_ATOMS)
+    return set_err(c, CPM_EINVAL, "cpm_smatrix_build: n above CPM_SMATRIX_MAX_ATOMS");
+  c->smat_ready = false;
+  cudaStream_t s = c->stream;
+  int st;
+  const size_t bytes = (size_t)n * n * sizeof(double);
+  if ((st = buf_reserve(c, &c->smat, bytes)) || (st = buf_reserve(c, &c->ws_in2, bytes)))
+    return st;
+  double* ident = (double*)c->ws_in2.ptr;
+  double* x = (double*)c->smat.ptr;
+  launch_identity(ident, n, s);
+  if ((st = cuda_check(c, cudaGetLastError(), "identity"))) return st;
+  // the columns E^-1 e_j: n right-hand sides of one PCG (b already in e/A: scale 1)
+  std::vector<int> it(n);
+  std::vector<double> rr(n);
+  SolveArgs a{n, ident, 1.0, x, false, tol, maxit, it.data(), rr.data()};
+  const int solve_st = pcg_solve(c, a);
+  if (max_iters_out) *max_iters_out = *std::max_element(it.begin(), it.end());
+  if (solve_st == CPM_ENOCONV)
+    return set_err(c, CPM_ENOCONV, "cpm_smatrix_build: a column missed tol");
+  if (solve_st != CPM_OK) return solve_st;
+  launch_smatrix_form(x, (const double*)c->d.ptr, c->c_ele, n, s);
+  if ((st = cuda_check(c, cudaGetLastError(), "smatrix form")) ||
+      (st = cuda_check(c, cudaStreamSynchronize(s), "smatrix sync")))
+    return st;
+  c->smat_ready = true;
+  return CPM_OK;
+}
+
+int cpm_smatrix_charges(cpm_ctx* c, int frames, const double* b, const double* qsol,
+                        double* q_out) {
+  if (!c) return CPM_EINVAL;
+  if (!c->built) return set_err(c, CPM_ENOTBUILT, "cpm_smatrix_charges before cpm_build_E");
+  if (!c->smat_ready)
+    return set_err(c, CPM_EINVAL, "cpm_smatrix_charges before cpm_smatrix_build");
+  if (frames < 1 || frames > smatrix_max_frames() || !b || !q_out)
+    return set_err(c, CPM_EINVAL, "cpm_smatrix_charges: bad arguments");
+  const int n = c->n;
+  cudaStream_t s = c->stream;
+  const size_t bytes = (size_t)frames * n * sizeof(double);
+  int st;
+  const double* db = nullptr;
+  const double* dqs = nullptr;
+  double* dq = nullptr;
+  if ((st = stage_in(c, &c->ws_in0, b, bytes, (const void**)&db))) return st;
+  if (qsol && (st = stage_in(c, &c->ws_in1, qsol, frames * sizeof(double), (const void**)&dqs)))
+    return st;
+  if ((st = stage_out(c, &c->ws_out0, q_out, bytes, (void**)&dq))) return st;
+  launch_smatrix_apply((const double*)c->smat.ptr, db, dqs, (const double*)c->d.ptr, n, frames,
+                       1.0 / kKe, dq, s);
+  if ((st = cuda_check(c, cudaGetLastError(), "smatrix apply"))) return st;
+  if ((st = copy_out(c, q_out, dq, bytes))) return st;
+  return cuda_check(c, cudaStreamSynchronize(s), "smatrix sync");
 }
 
 int cpm_get_E(cpm_ctx* c, int form, double* out, int64_t ld) {

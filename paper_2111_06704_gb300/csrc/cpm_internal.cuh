@@ -139,6 +139,10 @@ struct Ctx {
   Buf gcd_status;      // int: singular C
   Buf gcd_work;        // double: per-frame sums and shifts
 
+  // the matrix path: S = E_n^-1 (I - 1 d^T), column-major (S_ij at [j * n + i])
+  bool smat_ready = false;
+  Buf smat;            // double [n][n]
+
   // scratch (grown on demand, never shrunk)
   std::vector<Buf*> scratch;
   std::vector<double> kw;  // k-vector weights W_K of the sorted table, mpad entries (0 past m)
@@ -280,5 +284,12 @@ void launch_gcd_shifts(const double* cinv, const double* q0, const double* sums,
                        int m, double* dmu, double* dmu_volts, cudaStream_t s);
 void launch_gcd_apply(double* q, const double* amat, const double* dmu, int n, int nrhs, int m,
                       cudaStream_t s);
+
+// ---- the matrix path (smatrix.cu) --------------------------------------------------
+int smatrix_max_frames();
+void launch_identity(double* x, int n, cudaStream_t s);
+void launch_smatrix_form(double* x, const double* d, double c_ele, int n, cudaStream_t s);
+void launch_smatrix_apply(const double* S, const double* b, const double* qsol, const double* d,
+                          int n, int frames, double bscale, double* q, cudaStream_t s);
 
 }  // namespace cpm
