@@ -1,4 +1,5 @@
-"""The PCG-DC preconditioner, built atom by atom (test infrastructure only).
+"""The PCG-DC preconditioner, built atom by atom, and the sparsified-inverse
+preconditioners PCG-Normal and PCG-Full it is compared with (test infrastructure only).
 
 Sec. III B 2, steps 1)-3) and Eq. 36-37.  Readings where the text leaves room:
 * neighbours of tau are the atoms j with r_tau_j <= r_cut (inclusive), tau included;
@@ -80,3 +81,17 @@ def fill_gap(p, nb, gap: float):
     for t, idx in enumerate(nb):
         out[idx, t] = p[idx, t]
     return out
+
+
+def sparsified_inverse(e, xyz, box, rcut: float, strict: bool = True):
+    """PCG-Normal / PCG-Full (Sec. III B 2, Fig. 2a-c, Fig. 6a): P keeps the entries of
+    E^-1 for the pairs within rcut and is zero elsewhere.  PCG-Normal: r_ij < r_cut
+    (strict, as printed).  PCG-Full: every pair of the neighbour list, read as the
+    real-space cutoff (pass it with strict=False).  r_ij is the minimum-image distance, so
+    a pair counts once whatever its images.  Returns (P, pattern lists)."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    einv = np.linalg.inv(np.asarray(e, dtype=np.float64))
+    d = _min_image(xyz[:, None, :] - xyz[None, :, :], box)
+    r = np.sqrt(np.einsum("ijk,ijk->ij", d, d))
+    mask = r < rcut if strict else r <= rcut
+    return np.where(mask, einv, 0.0), [np.nonzero(mask[:, t])[0] for t in range(len(xyz))]
