@@ -95,7 +95,8 @@ def test_joint_capacitance_of_a_two_sheet_capacitor(prec):
     r = r[(r > 1e-9) & (r < 30.0)]
     w = math.sqrt(2 / math.pi) * alpha - u - np.sum(erfc(ew.mix_alpha(alpha, alpha) * r) / r)
     ref = len(lo) / (4 * math.pi * d / (a * b / 4) + 2 * w) / ew.KE
-    assert gcd.joint_capacitance(c) == pytest.approx(ref, rel=1e-6)
+    # the Ewald settings alone leave ~6e-9 (the oracle at the same settings)
+    assert gcd.joint_capacitance(c) == pytest.approx(ref, rel=1e-8 if prec == "fp64" else 2e-6)
     ctx.close()
 
 
