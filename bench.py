@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--heldout-frames", type=int, default=2000)
     ap.add_argument("--epochs", type=int, default=3)
     ap.add_argument("--frames", type=int, default=256, help="frames per batch (batch workload)")
+    ap.add_argument("--matrix-path", action="store_true",
+                    help="batch workload: also time the matrix path (S formed once, q = S b)")
     ap.add_argument("--baseline-frames", type=int, default=16,
                     help="frames timed for the per-frame FP64 baseline (batch workload)")
     return ap.parse_args()
@@ -597,6 +599,17 @@ def run_batch(args, rank, world, local_rank):
         solve_ms = timed(lambda: (ctx.cpm_solve(b, q, tol=TOL, maxit=2000),
                                   ctx.cpm_neutralize(q, qs)), 3)
         pot_ms = timed(lambda: ctx.cpm_potential(ion_xyz, ion_q, chi, b, qs), 3)
+        matrix = None
+        if args.matrix_path:
+            # the matrix path on the same E: S formed once, then one product per batch
+            build_ms = timed(lambda: ctx.cpm_smatrix_build(tol=1e-10, maxit=2000), 1)
+            qm = torch.empty((F, n), dtype=torch.float64, device=dev)
+            mat_ms = timed(lambda: ctx.cpm_smatrix_charges(b, qs, qm), 3)
+            matrix = {"s_build_ms": build_ms,
+                      "charges": {"value": F * 1000.0 / mat_ms, "unit": "solves/s",
+                                  "what": "cpm_smatrix_charges alone (b given)"},
+                      "with_b": {"value": F * 1000.0 / (mat_ms + pot_ms), "unit": "solves/s"},
+                      "max_rel_diff_vs_pcg": float((qm - q).abs().max() / q.abs().max())}
 
         # plain per-frame FP64 Jacobi PCG on the same GPU, zero and previous-step guesses
         base.cpm_build_E(xyz, alpha)
@@ -650,6 +663,8 @@ def run_batch(args, rank, world, local_rank):
     }
     if ragged is not None:
         line["ragged"] = ragged
+    if matrix is not None:
+        line["matrix_path"] = matrix
     print(json.dumps(line), flush=True)
 
 
