@@ -19,6 +19,10 @@ Dynamics Simulation" (arXiv 2111.06704), cited by section and equation:
 * ``gcd``     -- fixed total charge per electrode (galvanostatic charge-discharge,
   Eq. S14-S24): capacitance coefficients and the two-step GCD charges; pinned by
   ``tests/test_oracle_gcd.py``.
+* ``forces``  -- forces on the ions from the electrode's Gaussian charges (Eq. S25 inside
+  the Ewald form of Eq. 22 / 25); pinned by ``tests/test_oracle_forces.py``.
+* ``precond.sparsified_inverse`` -- the PCG-Normal / PCG-Full preconditioners (Fig. 6a);
+  pinned by ``tests/test_oracle_pcg_variants.py``.
 
 Parity status: every function is pinned by ``tests/test_oracle_pins.py`` (Madelung
 constants, the 2D lattice constants and Gaussian widths of Table 1, brute-force
