@@ -68,7 +68,8 @@ def test_one_electrode_is_the_neutralisation():
     qb, _, _ = ctx.cpm_solve(b, tol=1e-12)
     q1 = ctx.cpm_neutralize(qb.copy(), qsol)
     q2, _ = ctx.cpm_gcd_charges(qb.copy(), -qsol[:, None], qsol)
-    assert np.abs(q1 - q2).max() < 1e-10 * np.abs(q1).max()
+    # the build solves E d' = 1 to 1e-10, so d carries ~kappa x 1e-10 relative error
+    assert np.abs(q1 - q2).max() < 1e-7 * np.abs(q1).max()
     ctx.close()
 
 
