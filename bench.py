@@ -42,7 +42,9 @@ FP32_LANES_PER_SM = 128
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 10 for the default workload, whose 140 ms "
+                         "steps then span enough clock samples; 3 otherwise)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cells", type=int, default=40, help="cells per sheet edge (40: 12,800 atoms)")
@@ -65,7 +67,10 @@ def parse():
                     help="batch workload: also time the matrix path (S formed once, q = S b)")
     ap.add_argument("--baseline-frames", type=int, default=16,
                     help="frames timed for the per-frame FP64 baseline (batch workload)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 10 if args.impl == "ours" and args.workload == "precision" else 3
+    return args
 
 
 def measured_peaks():
