@@ -321,7 +321,7 @@ void free_build(Ctx* c) {
                 &c->E, &c->diag,
                 &c->nbr_off, &c->nbr_idx, &c->prow, &c->d, &c->shell_off, &c->shell_members, &c->p_f32,
                 &c->turn, &c->gcd_labels, &c->gcd_a, &c->gcd_c, &c->gcd_cinv, &c->gcd_status,
-                &c->gcd_work, &c->smat};
+                &c->gcd_scratch, &c->smat};
   for (Buf* b : all) buf_free(c, b);
   release_workspace(c);
   c->built = false;
@@ -956,8 +956,8 @@ int cpm_gcd_charges(cpm_ctx* c, int nrhs, double* q_inout, const double* q0,
   }
   if ((st = stage_in(c, &c->ws_in1, q0, mbytes, (const void**)&dq0))) return st;
   if (dmu_out && (st = stage_out(c, &c->ws_out1, dmu_out, mbytes, (void**)&ddmu))) return st;
-  if ((st = buf_reserve(c, &c->gcd_work, 2 * mbytes))) return st;
-  double* sums = (double*)c->gcd_work.ptr;
+  if ((st = buf_reserve(c, &c->gcd_scratch, 2 * mbytes))) return st;
+  double* sums = (double*)c->gcd_scratch.ptr;
   double* dmu = sums + (size_t)nrhs * m;
   const int* dlab = (const int*)c->gcd_labels.ptr;
   launch_gcd_sums(dq, n, nrhs, dlab, m, sums, s);  // B^T q^b

@@ -137,7 +137,7 @@ struct Ctx {
   Buf gcd_c;           // double [m][m]: C_ab at [b * m + a]
   Buf gcd_cinv;        // double [m][m]: C^-1, row-major
   Buf gcd_status;      // int: singular C
-  Buf gcd_work;        // double: per-frame sums and shifts
+  Buf gcd_scratch;        // double: per-frame sums and shifts
 
   // the matrix path: S = E_n^-1 (I - 1 d^T), column-major (S_ij at [j * n + i])
   bool smat_ready = false;
