@@ -14,9 +14,7 @@
 // entries are O(1)).  BF16 x BF16, FP16 x FP16 and E4M3 x E4M3 products are exact in the
 // FP32 accumulator.
 //
-// Tiles of 256 x 256 outputs of the lower triangle, one CTA each; by default two tiles of
-// one tile row run as a two-CTA cluster that loads their shared operand rows once, by
-// multicast.  Warp roles: TMA producer, single-thread MMA issuer, eight epilogue warps.
+// Tiles of 256 x 256 outputs of the lower triangle, one CTA each.  Warp roles: TMA producer, single-thread MMA issuer, eight epilogue warps.
 // All 512 TMEM columns hold two M = 128, N = 256 FP32 accumulators.  After each
 // accumulation chunk of the host's schedule the MMAs pause while the epilogue adds the
 // accumulator (times the chunk's scale) into the tile's running hi / lo floats by an
@@ -32,7 +30,6 @@
 
 #include <algorithm>
 #include <cmath>
-#include <stdlib.h>
 
 #include "cpm_internal.cuh"
 
@@ -140,31 +137,6 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b,
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-// The same load delivered to every CTA of the cluster in `mask`, at the same shared-memory
-// offsets, each CTA's barrier at `bar`'s offset receiving the bytes.
-__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                               int x, int y, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      ".multicast::cluster [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_addr(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_addr(bar)), "r"(x), "r"(y), "h"(mask)
-      : "memory");
-}
-
-// Arrives on the barrier at `bar`'s offset in every CTA of the cluster in `mask` once the
-// MMAs issued so far have completed.
-__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-      " [%0], %1;" ::"r"(smem_addr(bar)), "h"(mask)
-      : "memory");
-}
-
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" :::
-                   "memory");
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -301,27 +273,13 @@ __device__ __forceinline__ void strip_final(const StripArgs& a, const double (&t
   }
 }
 
-// Tile geometry: lower-triangle tile `tile`, or with pairs, CTA `rank` of pair `tile`:
-// row I's tiles go in pairs (I, J0), (I, J0 + 1), J0 even, which share the operand rows
-// of I; the pairs of rows 0 .. I-1 number floor((I + 1)^2 / 4), and an even row's last
-// pair ends in (I, I + 1), above the diagonal: that CTA loads its half of the shared rows
-// for its partner and computes nothing (valid = false).
-__device__ __forceinline__ int pairs_before(int I) { return (I + 1) * (I + 1) / 4; }
-
+// Tile geometry: lower-triangle tile `tile` (row-major over the triangle).
 struct StripTile {
   int i0, j0, rb, cb;
-  bool diag, valid;
-  __device__ StripTile(int tile, int npad, bool pairs, int rank) {
+  bool diag;
+  __device__ StripTile(int tile, int npad) {
     int I, J;
-    if (pairs) {
-      I = max(0, (int)(2.0 * sqrt((double)tile)) - 1);
-      while (pairs_before(I + 1) <= tile) ++I;
-      while (I > 0 && pairs_before(I) > tile) --I;
-      J = 2 * (tile - pairs_before(I)) + rank;
-    } else {
-      tri_tile(tile, I, J);
-    }
-    valid = J <= I;
+    tri_tile(tile, I, J);
     i0 = I * kStripTile;
     j0 = J * kStripTile;
     diag = I == J;
@@ -332,28 +290,21 @@ struct StripTile {
 };
 
 // The loads of a wide (one-plane, 128-byte-row) stage: A half r at r x 16 KB, B halves
-// at 32 KB and 48 KB; with pairs the A half `rank` goes to both CTAs.
-template <bool PAIRS>
+// at 32 KB and 48 KB.
 __device__ __forceinline__ void wide_loads(uint8_t* st, const CUtensorMap* map, uint64_t* bar,
-                                           int x, const StripTile& tg, uint32_t rank) {
+                                           int x, const StripTile& tg) {
   constexpr int kWide = kTile * 64 * 2;
-  mbar_expect_tx(bar, (tg.rb + (tg.valid ? tg.cb : 0)) * kWide);
-  if (PAIRS) {
-    if ((int)rank < tg.rb)
-      tma_load_2d_mc(st + rank * kWide, map, bar, x, tg.i0 + (int)rank * kTile, 0x3);
-  } else {
-    for (int r = 0; r < tg.rb; ++r) tma_load_2d(st + r * kWide, map, bar, x, tg.i0 + r * kTile);
-  }
-  if (tg.valid)
-    for (int c = 0; c < tg.cb; ++c)
-      tma_load_2d(st + 2 * kWide + c * kWide, map, bar, x, tg.j0 + c * kTile);
+  mbar_expect_tx(bar, (tg.rb + tg.cb) * kWide);
+  for (int r = 0; r < tg.rb; ++r) tma_load_2d(st + r * kWide, map, bar, x, tg.i0 + r * kTile);
+  for (int c = 0; c < tg.cb; ++c)
+    tma_load_2d(st + 2 * kWide + c * kWide, map, bar, x, tg.j0 + c * kTile);
 }
 
 // Each CTA takes tiles blockIdx.x, blockIdx.x + gridDim.x, ... (one, when the grid covers
 // the tiles); the ring's stage count and the accumulator's chunk count run on across
 // tiles.  The scratch slot is the SM's: its shared memory and TMEM admit one CTA of this
 // kernel per SM at a time.
-template <bool SIX, bool PAIRS>
+template <bool SIX>
 __global__ void __launch_bounds__(kStripThreads, 1)
 k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CUtensorMap map0n,
            const __grid_constant__ CUtensorMap map1n, const __grid_constant__ CUtensorMap map2n,
@@ -406,7 +357,7 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full_bar[s], 1);
-      mbar_init(&empty_bar[s], PAIRS ? 2 : 1);  // pairs: both CTAs have read the slot
+      mbar_init(&empty_bar[s], 1);
     }
     mbar_init(&acc_full, 1);
     mbar_init(&acc_empty, 8);
@@ -420,14 +371,10 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
   }
   tc_fence_before();
   __syncthreads();
-  if (PAIRS) cluster_sync();  // the partner's barriers exist before anything reaches them
   tc_fence_after();
   const uint32_t tmem = tmem_base_s;
-  // pairs: this CTA's rank; the pair index takes the place of the tile index
-  uint32_t rank = 0;
-  if (PAIRS) asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
-  const int tile0 = PAIRS ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
-  const int tstep = PAIRS ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+  const int tile0 = (int)blockIdx.x;
+  const int tstep = (int)gridDim.x;
 
   if (warp == 0) {
     // ---- TMA producer ------------------------------------------------------------
@@ -435,7 +382,7 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
       uint32_t g = 0;  // stages issued by this CTA
       bool ok = true;
       for (int tile = tile0; tile < args.tiles && ok; tile += tstep) {
-        const StripTile tg(tile, args.npad, PAIRS, rank);
+        const StripTile tg(tile, args.npad);
         for (int t = 0; t < nst; ++t, ++g) {
           const int s = g % kStages;
           ok = mbar_wait(&empty_bar[s], ((g / kStages) & 1) ^ 1, args.err, 11);
@@ -445,32 +392,25 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
             // 32 columns of planes 0 .. P-1: A plane p half r at slot 2p + r, B plane p
             // half c at slot 2P + 2p + c (the two B halves adjacent: one N = 256 operand)
             const int x = (args.kb_begin - args.kb_col0) * kBlockK + t * 32;
-            mbar_expect_tx(&full_bar[s], P * (tg.rb + (tg.valid ? tg.cb : 0)) * kNarrow);
+            mbar_expect_tx(&full_bar[s], P * (tg.rb + tg.cb) * kNarrow);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
               const CUtensorMap* mp = p == 0 ? &map0n : p == 1 ? &map1n : &map2n;
-              if (PAIRS) {  // row half `rank` for both CTAs of the pair
-                if ((int)rank < tg.rb)
-                  tma_load_2d_mc(st + (2 * p + rank) * kNarrow, mp, &full_bar[s], x,
-                                 tg.i0 + (int)rank * kTile, 0x3);
-              } else {
-                for (int r = 0; r < tg.rb; ++r)
-                  tma_load_2d(st + (2 * p + r) * kNarrow, mp, &full_bar[s], x, tg.i0 + r * kTile);
-              }
-              if (tg.valid)
-                for (int c = 0; c < tg.cb; ++c)
-                  tma_load_2d(st + (2 * P + 2 * p + c) * kNarrow, mp, &full_bar[s], x,
-                              tg.j0 + c * kTile);
+              for (int r = 0; r < tg.rb; ++r)
+                tma_load_2d(st + (2 * p + r) * kNarrow, mp, &full_bar[s], x, tg.i0 + r * kTile);
+              for (int c = 0; c < tg.cb; ++c)
+                tma_load_2d(st + (2 * P + 2 * p + c) * kNarrow, mp, &full_bar[s], x,
+                            tg.j0 + c * kTile);
             }
           } else if (t >= t8) {
             // 128 FP8 columns (a [cos | sin] pair): A half r at r x 16 KB, B halves at
             // 32 KB and 48 KB
             const int x = (kb8 - args.kb_col0 + 2 * (t - t8)) * kBlockK;
-            wide_loads<PAIRS>(st, &map8, &full_bar[s], x, tg, rank);
+            wide_loads(st, &map8, &full_bar[s], x, tg);
           } else {
             // 64 columns of plane 0: A half r at r x 16 KB, B halves at 32 KB and 48 KB
             const int x = (kb1 - args.kb_col0 + (t - nnarrow)) * kBlockK;
-            wide_loads<PAIRS>(st, &map0w, &full_bar[s], x, tg, rank);
+            wide_loads(st, &map0w, &full_bar[s], x, tg);
           }
         }
       }
@@ -484,7 +424,7 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
       uint32_t g = 0, chunk = 0;  // stages consumed, chunks committed by this CTA
       bool ok = true;
       for (int tile = tile0; tile < args.tiles && ok; tile += tstep) {
-        const StripTile tg(tile, args.npad, PAIRS, rank);
+        const StripTile tg(tile, args.npad);
         // on a diagonal tile the first row half needs only the first 128 columns
         constexpr uint32_t kId256 = idesc_f16(SIX, 256), kId128 = idesc_f16(SIX, 128);
         const uint32_t id0 = tg.diag ? kId128 : kId256;
@@ -499,9 +439,7 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
           }
           tc_fence_after();
           const uint32_t st = smem_addr(ring + s * kStageBytes);
-          if (!tg.valid) {
-            // nothing to compute: the stage is only released below
-          } else if (t < nnarrow) {
+          if (t < nnarrow) {
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks)
               for (int r = 0; r < tg.rb; ++r)
@@ -535,9 +473,8 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
               }
           }
           first = false;
-          // frees the stage once these MMAs have read it (pairs: in both CTAs' counts)
-          if (PAIRS) mma_commit_mc(&empty_bar[s], 0x3);
-          else mma_commit(&empty_bar[s]);
+          // frees the stage once these MMAs have read it
+          mma_commit(&empty_bar[s]);
           if (chunk_ends(t)) {
             mma_commit(&acc_full);
             ++chunk;
@@ -571,7 +508,7 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
     }
     uint32_t chunk = 0;
     for (int tile = tile0; tile < args.tiles && ok; tile += tstep) {
-      const StripTile tg(tile, args.npad, PAIRS, rank);
+      const StripTile tg(tile, args.npad);
       int ci = 0;  // chunk index within the tile
       for (int t0 = 0; t0 < nst; ++ci) {
         int t1 = t0;
@@ -582,7 +519,7 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
         ok = mbar_wait(&acc_full, chunk & 1, args.err, 14);
         if (!ok) break;
         tc_fence_after();
-        for (int r = 0; tg.valid && r < tg.rb; ++r) {
+        for (int r = 0; r < tg.rb; ++r) {
           const int row = tg.i0 + r * kTile + 32 * q + lane;
 #pragma unroll 1
           for (int cl = 0; cl < 4; ++cl) {
@@ -652,8 +589,6 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
   }
   tc_fence_before();
   __syncthreads();
-  // pairs: neither CTA leaves while its partner may still load into it or arrive on it
-  if (PAIRS) cluster_sync();
   if (warp == 0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem)
@@ -755,17 +690,9 @@ int launch_ek_tc(const void* p0, const void* p1, const void* p2, const void* p8,
     return CPM_ECUDA;
   const int smem6 = StripCfg<true>::kStages * StripCfg<true>::kStageBytes + 1024;
   const int smem31 = StripCfg<false>::kStages * StripCfg<false>::kStageBytes + 1024;
-  // pairs of tiles sharing their operand rows through cluster multicast (CPM_TC_PAIRS=0
-  // in the environment: one CTA per tile, every operand loaded by its own CTA)
-  const char* env_pairs = getenv("CPM_TC_PAIRS");
-  const bool pairs = !(env_pairs && atoi(env_pairs) == 0);
-  if (cudaFuncSetAttribute(k_ek_strip<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(k_ek_strip<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            smem6) != cudaSuccess ||
-      cudaFuncSetAttribute(k_ek_strip<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           smem31) != cudaSuccess ||
-      cudaFuncSetAttribute(k_ek_strip<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           smem6) != cudaSuccess ||
-      cudaFuncSetAttribute(k_ek_strip<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(k_ek_strip<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            smem31) != cudaSuccess)
     return CPM_ECUDA;
   // the six-product part [kb_begin, x6_end) and the rest [l_begin, kb_end); kb6_end is
@@ -776,8 +703,7 @@ int launch_ek_tc(const void* p0, const void* p1, const void* p2, const void* p8,
   StripArgs a;
   a.n = n;
   a.npad = npad;
-  // pairs: floor((nt + 1)^2 / 4) pairs of two CTAs; else nt (nt + 1) / 2 tiles
-  a.tiles = pairs ? (nt + 1) * (nt + 1) / 4 : nt * (nt + 1) / 2;
+  a.tiles = nt * (nt + 1) / 2;
   a.kb3_end = kb3_end;
   a.kb8_begin = kb8_begin;
   a.kb_col0 = kb_col0;
@@ -789,30 +715,15 @@ int launch_ek_tc(const void* p0, const void* p1, const void* p2, const void* p8,
   a.ldh = ldh;
   a.ldE = ldE;
   a.err = err;
-  // one CTA per tile (pairs: one cluster per pair); the hardware hands each SM its next
-  // tile as it frees up
+  // one CTA per tile; the hardware hands each SM its next tile as it frees up
   auto launch = [&](bool six) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(pairs ? 2 * a.tiles : a.tiles);
-    cfg.blockDim = dim3(kStripThreads);
-    cfg.dynamicSmemBytes = six ? smem6 : smem31;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = pairs ? 2 : 1;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    cudaError_t e;
+    const int smem = six ? smem6 : smem31;
     if (six)
-      e = pairs ? cudaLaunchKernelEx(&cfg, k_ek_strip<true, true>, m0, m0n, m1n, m2n, m8, a)
-                : cudaLaunchKernelEx(&cfg, k_ek_strip<true, false>, m0, m0n, m1n, m2n, m8, a);
+      k_ek_strip<true><<<a.tiles, kStripThreads, smem, s>>>(m0, m0n, m1n, m2n, m8, a);
     else
-      e = pairs ? cudaLaunchKernelEx(&cfg, k_ek_strip<false, true>, m0, m0n, m1n, m2n, m8, a)
-                : cudaLaunchKernelEx(&cfg, k_ek_strip<false, false>, m0, m0n, m1n, m2n, m8, a);
+      k_ek_strip<false><<<a.tiles, kStripThreads, smem, s>>>(m0, m0n, m1n, m2n, m8, a);
     note_launch();
-    return e;
+    return cudaGetLastError();
   };
   if (kb_begin < x6_end) {
     a.kb_begin = kb_begin;

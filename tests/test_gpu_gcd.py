@@ -14,8 +14,7 @@ from paper_2111_06704_gb300 import cpm
 from paper_2111_06704_gb300 import workloads as wl
 from tests import _cases, _golden
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skip(reason="the GCD kernels have not run on a GPU yet")]
+pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():

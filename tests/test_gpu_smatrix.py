@@ -6,8 +6,7 @@ import pytest
 from paper_2111_06704_gb300 import cpm
 from tests import _cases
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skip(reason="the matrix-path kernels have not run on a GPU yet")]
+pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():

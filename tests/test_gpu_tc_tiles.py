@@ -1,5 +1,5 @@
-"""The tensor-core k-space tail of the BF16X6 build against the FP64 build, on electrodes
-whose size is not a multiple of the 256 x 256 tile edge.
+"""The tensor-core k-space tail of the BF16X6 build against the FP64 oracle and the FP64
+build, on electrodes whose size is not a multiple of the 256 x 256 tile edge.
 
 * 1,144 atoms (padded to 1,152): the last tile row holds one 128-row half, so the
   kernels' half-tile paths run; 3,200 atoms: several full tiles per row.
@@ -13,6 +13,8 @@ whose size is not a multiple of the 256 x 256 tile edge.
 import numpy as np
 import pytest
 
+from oracle import ewald as ew
+from oracle import solve as sv
 from paper_2111_06704_gb300 import cpm
 from paper_2111_06704_gb300 import workloads as wl
 
@@ -75,13 +77,27 @@ def test_rebuilds_reuse_or_release_the_workspace():
     ctx.close()
 
 
-def test_tile_pairs_match_single_tiles(monkeypatch):
-    # the default runs tile pairs as two-CTA clusters that share the operand rows by
-    # multicast; one CTA per tile (CPM_TC_PAIRS=0) sums the same products in the same
-    # order, so E is the same bit for bit (a ragged size: an even row's pair ends in a
-    # CTA with no tile of its own)
+def test_multi_tile_tail_against_the_oracle():
+    # 1,144 atoms: five tile rows of 256, the last a single 128-row half.  E entry by entry
+    # against the oracle's FP64 sums (the factored reciprocal form, pinned to the pairwise
+    # difference form on CPU) and the neutral charges of a 446-ion frame against the
+    # bordered solve (Eq. 29, Eq. 34)
     el = wl.two_sheet_electrode(13, 11)
-    e_pairs, _ = build(el, cpm.CPM_PREC_BF16X6)
-    monkeypatch.setenv("CPM_TC_PAIRS", "0")
-    e_single, _ = build(el, cpm.CPM_PREC_BF16X6)
-    assert np.array_equal(e_pairs, e_single)
+    rng = np.random.default_rng(wl.seed_for(2, 11))
+    ions, q_ion = wl.random_ions(rng, 223, 223, el.box, min_sep=2.5)
+    ctx = cpm.Context(el.box)  # the default BF16X6 build
+    ctx.cpm_build_E(el.xyz, el.alpha)
+    e_gpu = ctx.cpm_get_E(cpm.CPM_E_PAPER)
+    q, it, rel, _, qsol = cpm.charges(ctx, ions[None], q_ion[None], el.chi, tol=1e-10,
+                                      maxit=2000)
+    ctx.close()
+    e_ref = ew.interaction_matrix(el.xyz, el.alpha, el.box, wl.G_EWALD, wl.RCUT_REAL,
+                                  wl.KSPACE_EPS, True, kspace="factored")
+    assert np.abs(e_gpu - e_ref).max() < 1e-6 * np.abs(e_ref).max()
+    off = ~np.eye(el.n, dtype=bool)
+    assert np.sqrt(((e_gpu - e_ref)[off] ** 2).mean()) < 1e-8
+    bsol = ew.electrolyte_potential(el.xyz, el.alpha, ions, q_ion, el.box, wl.G_EWALD,
+                                    wl.RCUT_REAL, wl.KSPACE_EPS, True, kspace="factored")
+    q_ref, _ = sv.solve_bordered(e_ref, ew.rhs_volts(el.chi, bsol) / ew.KE, float(q_ion.sum()))
+    assert rel[0] <= 1e-10
+    assert np.linalg.norm(q[0] - q_ref) < 1e-6 * np.linalg.norm(q_ref)
