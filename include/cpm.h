@@ -28,7 +28,8 @@
  * conjugate gradient cannot handle.  cpm_potential returns b in the same form.
  *
  * Pointers: every array argument may be a host pointer or a CUDA device pointer of the
- * context's device (detected with cudaPointerGetAttributes).  The caller owns them; the
+ * context's device (detected with cudaPointerGetAttributes; device memory of another
+ * device is rejected with CPM_EINVAL).  The caller owns them; the
  * library never keeps them past the call.  Host arrays are staged through device
  * buffers inside the call.  Layouts are row-major and contiguous.
  *
@@ -133,6 +134,24 @@ int cpm_destroy(cpm_ctx* c);
  * cpm_release_workspace or cpm_destroy.
  */
 int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha);
+
+/*
+ * cpm_build_E_copy: builds dst from the built E of src instead of from the geometry.  No
+ * counterpart in the paper: it serves the plain FP64 PCG baseline on electrodes where an
+ * FP64 k-space build is out of reach (at 106,568 atoms the FP64 E takes 91 GB and its
+ * FP64 GEMM some 4e15 FLOP at the FP64 rate).  dst gets src's stored E_n in dst's
+ * storage precision (float to FP64 is an exact widening; equal precisions copy), src's
+ * diagonal, d and C^ele, and, when dst selects PCG-DC, src's PCG-DC preconditioner (src
+ * must have one with the same g_dc, rcut_dc and p_gap).  Jacobi and no preconditioner
+ * need nothing more.  Both contexts on one device, with the same box, g, r_c, eps and
+ * slab setting, else CPM_EINVAL; an FP64 src cannot be narrowed (CPM_EINVAL).  dst then
+ * serves cpm_solve, cpm_solve_static, cpm_neutralize, cpm_apply_E, cpm_get_E(_rows),
+ * cpm_get_d, cpm_get_precond, the GCD and matrix-path calls; it has no k-space tables, so
+ * cpm_potential and the learned-guess feature calls return CPM_EINVAL (compute b on src).
+ * Replaces dst's earlier build; src is left as it was (its stream is synchronised first).
+ * dst holds its own copies: src may be rebuilt or destroyed afterwards.
+ */
+int cpm_build_E_copy(cpm_ctx* dst, cpm_ctx* src);
 
 /* Frees the context's kept workspace: the E build's (above) and the solve and potential
  * workspaces, which later calls reserve again as needed.  The built E, P, d and the
@@ -365,6 +384,9 @@ typedef struct cpm_info_t {
                            on the three- and one-product K-blocks */
   int tc_blocks_fp8;    /* BF16X6 builds: of tc_blocks[2], the K-blocks taking their one
                            product in FP8 (E4M3) instead of FP16 */
+  double t_tc_loop_ms;  /* BF16X6 builds: the whole k-window loop of the tail; a streamed
+                           build makes each window's operand planes inside it, so there
+                           t_tc_ms (the tensor-core launches alone) is the smaller */
 } cpm_info_t;
 
 int cpm_get_info(cpm_ctx* c, cpm_info_t* out);

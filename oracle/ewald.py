@@ -89,7 +89,8 @@ def real_space_pairs(ra, rb, alpha_ab, box, g: float, rc: float, same_set: bool)
                        for k in range(-nr[2], nr[2] + 1)], dtype=np.float64) * L
     alpha_ab = np.broadcast_to(np.asarray(alpha_ab, dtype=np.float64), (na, nb))
     rows = max(1, 2_000_000 // max(1, nb))
-    for a0 in range(0, na, rows):
+
+    def block(a0):
         d = ra[a0:a0 + rows, None, :] - rb[None, :, :]  # [c, nb, 3]
         aab = alpha_ab[a0:a0 + rows]
         for s in shifts:
@@ -103,6 +104,10 @@ def real_space_pairs(ra, rb, alpha_ab, box, g: float, rc: float, same_set: bool)
                 continue
             rm = r[mask]
             out[a0:a0 + rows][mask] += _erfc_over_r(g * rm, rm) - _erfc_over_r(aab[mask] * rm, rm)
+
+    # row blocks are independent; numpy releases the GIL, so they run on all host cores
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as pool:
+        list(pool.map(block, range(0, na, rows)))
     return out
 
 
@@ -131,8 +136,48 @@ def kspace_pairs(ra, rb, box, g: float, eps: float = 1e-8):
     return out
 
 
+def kspace_matrix_factored(xyz, box, g: float, eps: float = 1e-8, chunk: int = 2048):
+    """Reciprocal part of Eq. 22-23 for every pair through the angle-addition identity
+    cos(K.(r_i - r_j)) = cos(K.r_i) cos(K.r_j) + sin(K.r_i) sin(K.r_j):
+    sum_K W_K cos(K.r_ij) = (C W C^T + S W S^T)_ij with C_iK = cos(K.r_i), S_iK = sin(K.r_i).
+    The sum over K is a library matrix product (FP64 BLAS), taken over chunks of the
+    k-vector table so memory stays bounded.  Equal to ``kspace_pairs`` up to rounding; it
+    serves electrodes where the pairwise difference form is too slow."""
+    _, kvec, w = kvectors(box, g, eps)
+    xyz = np.asarray(xyz, dtype=np.float64)
+    n = xyz.shape[0]
+    out = np.zeros((n, n))
+    for k0 in range(0, kvec.shape[0], chunk):
+        ph = xyz @ kvec[k0:k0 + chunk].T                  # K . r_i, [n, c]
+        sw = np.sqrt(w[k0:k0 + chunk])
+        c = np.cos(ph) * sw
+        out += c @ c.T
+        c = np.sin(ph) * sw
+        out += c @ c.T
+    return out
+
+
+def kspace_potential_factored(xyz, ion_xyz, ion_q, box, g: float, eps: float = 1e-8,
+                              chunk: int = 2048):
+    """sum_I q_I sum_K W_K cos(K.(r_i - r_I)) for every electrode atom i, through the same
+    identity: sum_K W_K [cos(K.r_i) Re S(K) + sin(K.r_i) Im S(K)] with the structure factor
+    S(K) = sum_I q_I exp(i K.r_I).  Equal to ``kspace_pairs(...) @ ion_q`` up to rounding."""
+    _, kvec, w = kvectors(box, g, eps)
+    xyz = np.asarray(xyz, dtype=np.float64)
+    ion_xyz = np.asarray(ion_xyz, dtype=np.float64)
+    ion_q = np.asarray(ion_q, dtype=np.float64)
+    out = np.zeros(xyz.shape[0])
+    for k0 in range(0, kvec.shape[0], chunk):
+        kc = kvec[k0:k0 + chunk]
+        phi = ion_xyz @ kc.T                               # K . r_I, [n_ion, c]
+        re, im = np.cos(phi).T @ ion_q, np.sin(phi).T @ ion_q
+        ph = xyz @ kc.T
+        out += np.cos(ph) @ (w[k0:k0 + chunk] * re) + np.sin(ph) @ (w[k0:k0 + chunk] * im)
+    return out
+
+
 def interaction_matrix(xyz, alpha, box, g: float, rc: float, eps: float = 1e-8,
-                       slab: bool = True):
+                       slab: bool = True, kspace: str = "difference"):
     """The Gaussian Ewald interaction matrix E of Eq. 22, entry by entry.
 
     e_ij = [real space, Eq. 22 first case, summed over images within rc]
@@ -143,7 +188,9 @@ def interaction_matrix(xyz, alpha, box, g: float, rc: float, eps: float = 1e-8,
 
     The reciprocal prefactor is 4 pi / V as in Eq. 16 (Eq. 23 prints a second 4 pi that
     phi-hat already carries).  The diagonal Gaussian self-energy is Eq. 6,
-    sqrt(2/pi) alpha_i; a point charge (alpha = inf) has none (end of Sec. II C)."""
+    sqrt(2/pi) alpha_i; a point charge (alpha = inf) has none (end of Sec. II C).
+    ``kspace`` = "factored" sums the reciprocal part by ``kspace_matrix_factored`` (the
+    FP64 BLAS form for large electrodes) instead of the pairwise difference form."""
     xyz = np.asarray(xyz, dtype=np.float64)
     alpha = np.asarray(alpha, dtype=np.float64)
     n = xyz.shape[0]
@@ -151,7 +198,10 @@ def interaction_matrix(xyz, alpha, box, g: float, rc: float, eps: float = 1e-8,
     vol = lx * ly * lz
     a_ij = mix_alpha(alpha[:, None], alpha[None, :])
     e = real_space_pairs(xyz, xyz, a_ij, box, g, rc, same_set=True)
-    e += kspace_pairs(xyz, xyz, box, g, eps)
+    if kspace == "factored":
+        e += kspace_matrix_factored(xyz, box, g, eps)
+    else:
+        e += kspace_pairs(xyz, xyz, box, g, eps)
     e -= math.pi / (vol * g * g)
     self_e = np.where(np.isinf(alpha), 0.0, math.sqrt(2.0 / math.pi) * np.where(np.isinf(alpha), 0.0, alpha))
     e[np.arange(n), np.arange(n)] += -2.0 * g / SQRT_PI + self_e
@@ -162,12 +212,14 @@ def interaction_matrix(xyz, alpha, box, g: float, rc: float, eps: float = 1e-8,
 
 
 def electrolyte_potential(xyz, alpha, ion_xyz, ion_q, box, g: float, rc: float,
-                          eps: float = 1e-8, slab: bool = True):
+                          eps: float = 1e-8, slab: bool = True, kspace: str = "difference"):
     """b^sol_i = sum_I q_I e_iI(alpha_i) (Eq. 25) for point-charge ions.
 
     e_iI uses the point-Gaussian coefficient alpha_iI = alpha_i (Sec. II A, after Eq. 5)
     in the same Ewald form as Eq. 22 (off-diagonal case), plus -pi/(V g^2) and, with
-    ``slab``, the Eq. 39 correction.  Returns b^sol in e/A, shape [N]."""
+    ``slab``, the Eq. 39 correction.  ``kspace`` = "factored" sums the reciprocal part
+    through the ions' structure factors (``kspace_potential_factored``).  Returns b^sol
+    in e/A, shape [N]."""
     xyz = np.asarray(xyz, dtype=np.float64)
     alpha = np.asarray(alpha, dtype=np.float64)
     ion_xyz = np.asarray(ion_xyz, dtype=np.float64)
@@ -176,12 +228,16 @@ def electrolyte_potential(xyz, alpha, ion_xyz, ion_q, box, g: float, rc: float,
     vol = lx * ly * lz
     a_iI = np.broadcast_to(alpha[:, None], (xyz.shape[0], ion_xyz.shape[0]))
     e = real_space_pairs(xyz, ion_xyz, a_iI, box, g, rc, same_set=False)
-    e += kspace_pairs(xyz, ion_xyz, box, g, eps)
+    if kspace != "factored":
+        e += kspace_pairs(xyz, ion_xyz, box, g, eps)
     e -= math.pi / (vol * g * g)
     if slab:
         z, zi = xyz[:, 2], ion_xyz[:, 2]
         e += -(2.0 * math.pi / vol) * ((z[:, None] - zi[None, :]) ** 2 + lz * lz / 6.0)
-    return e @ ion_q
+    out = e @ ion_q
+    if kspace == "factored":
+        out += kspace_potential_factored(xyz, ion_xyz, ion_q, box, g, eps)
+    return out
 
 
 def rhs_volts(chi, bsol):

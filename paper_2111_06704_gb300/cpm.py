@@ -82,6 +82,7 @@ class cpm_info_t(ctypes.Structure):
         ("t_head_ms", ctypes.c_double),
         ("t_tc_light_ms", ctypes.c_double),
         ("tc_blocks_fp8", ctypes.c_int),
+        ("t_tc_loop_ms", ctypes.c_double),
     ]
 
 
@@ -106,7 +107,8 @@ EXPORTS = ["cpm_default_params", "cpm_create", "cpm_destroy", "cpm_build_E", "cp
            "cpm_last_error", "cpm_batch_create", "cpm_batch_destroy", "cpm_batch_solve",
            "cpm_batch_neutralize", "cpm_batch_last_error", "cpm_get_E_rows",
            "cpm_guess", "cpm_release_workspace", "cpm_plan_kspace", "cpm_gcd_setup",
-           "cpm_gcd_charges", "cpm_smatrix_build", "cpm_smatrix_charges"]
+           "cpm_gcd_charges", "cpm_smatrix_build", "cpm_smatrix_charges",
+           "cpm_build_E_copy"]
 
 _lib = None
 
@@ -134,6 +136,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.cpm_destroy.argtypes = [vp]
     lib.cpm_release_workspace.argtypes = [vp]
     lib.cpm_build_E.argtypes = [vp, i, vp, vp]
+    lib.cpm_build_E_copy.argtypes = [vp, vp]
     lib.cpm_potential.argtypes = [vp, i, i, vp, vp, vp, vp, vp]
     lib.cpm_solve.argtypes = [vp, i, vp, vp, i, d, i, vp, vp]
     lib.cpm_solve_static.argtypes = [vp, i, vp, vp, i, d, i, vp, vp]
@@ -285,6 +288,14 @@ class Context:
         self._check(self.lib.cpm_build_E(self.h, n, px, pa))
         self.n = n
         self.gcd_m = 0  # a rebuild drops the electrodes' solves
+
+    def cpm_build_E_copy(self, src: "Context"):
+        """This context takes src's built E (in this context's storage precision), d and
+        diagonal, and its PCG-DC preconditioner when this context selects PCG-DC: the
+        solve-side build, with no k-space tables (no cpm_potential here)."""
+        self._check(self.lib.cpm_build_E_copy(self.h, src.h))
+        self.n = src.n
+        self.gcd_m = 0
 
     def cpm_potential(self, ion_xyz, ion_q, chi, b_out=None, qsol_out=None):
         frames, n_ion = int(ion_q.shape[0]), int(ion_q.shape[1])

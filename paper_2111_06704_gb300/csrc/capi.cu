@@ -69,22 +69,35 @@ int buf_reserve(Ctx* c, Buf* b, size_t bytes) {
   return buf_alloc(c, b, bytes);
 }
 
-namespace {
-
-bool is_device_ptr(const void* p) {
-  if (!p) return false;
+int pointer_where(const Ctx* c, const void* p) {
+  if (!p) return 0;
   cudaPointerAttributes at;
   cudaError_t e = cudaPointerGetAttributes(&at, p);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return 0;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return 1;
+  if (at.type == cudaMemoryTypeDevice) return at.device == c->device ? 1 : -1;
+  return 0;
 }
+
+int on_device(Ctx* c, const void* p, bool* dev) {
+  const int w = pointer_where(c, p);
+  if (w < 0)
+    return set_err(c, CPM_EINVAL, "an array lives in the memory of another CUDA device than "
+                                  "the context's");
+  *dev = w > 0;
+  return CPM_OK;
+}
+
+namespace {
 
 // Returns a device pointer holding `bytes` of `src` (src itself if it is on the device).
 int stage_in(Ctx* c, Buf* tmp, const void* src, size_t bytes, const void** out) {
-  if (is_device_ptr(src)) {
+  bool dev = false;
+  if (int st = on_device(c, src, &dev)) return st;
+  if (dev) {
     *out = src;
     return CPM_OK;
   }
@@ -98,7 +111,9 @@ int stage_in(Ctx* c, Buf* tmp, const void* src, size_t bytes, const void** out) 
 
 // Device destination for `dst` (dst itself when on the device); copy_out finishes it.
 int stage_out(Ctx* c, Buf* tmp, void* dst, size_t bytes, void** out) {
-  if (is_device_ptr(dst)) {
+  bool dev = false;
+  if (int st = on_device(c, dst, &dev)) return st;
+  if (dev) {
     *out = dst;
     return CPM_OK;
   }
@@ -111,7 +126,9 @@ int stage_out(Ctx* c, Buf* tmp, void* dst, size_t bytes, void** out) {
 template <typename T>
 int to_host(Ctx* c, std::vector<T>& dst, const T* src, size_t count) {
   dst.resize(count);
-  if (!is_device_ptr(src)) {
+  bool dev = false;
+  if (int st = on_device(c, src, &dev)) return st;
+  if (!dev) {
     std::copy(src, src + count, dst.begin());
     return CPM_OK;
   }
@@ -325,7 +342,10 @@ void free_build(Ctx* c) {
   for (Buf* b : all) buf_free(c, b);
   release_workspace(c);
   c->built = false;
+  c->solve_only = false;
   c->shells_ready = false;
+  c->gcd_m = 0;
+  c->smat_ready = false;
 }
 
 __global__ void k_inverse_tail(double* diag, int n) {
@@ -337,6 +357,13 @@ __global__ void k_fill(double* v, int64_t len, double x) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
        i += (int64_t)gridDim.x * blockDim.x)
     v[i] = x;
+}
+
+// dst [n][ld] (double) = src [n][ld] (float): exact widening of the stored matrix.
+__global__ void k_widen(const float* __restrict__ src, double* __restrict__ dst, int64_t len) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (double)src[i];
 }
 
 __global__ void k_scale(double* v, int64_t len, double s) {
@@ -451,8 +478,86 @@ int cpm_release_workspace(cpm_ctx* c) {
   return CPM_OK;
 }
 
+int cpm_build_E_copy(cpm_ctx* dst, cpm_ctx* src) {
+  if (!dst || !src) return CPM_EINVAL;
+  if (dst == src) return set_err(dst, CPM_EINVAL, "cpm_build_E_copy: dst and src are the same");
+  if (!src->built) return set_err(dst, CPM_ENOTBUILT, "cpm_build_E_copy: src is not built");
+  const cpm_params &pd = dst->p, &ps = src->p;
+  if (dst->device != src->device || pd.box[0] != ps.box[0] || pd.box[1] != ps.box[1] ||
+      pd.box[2] != ps.box[2] || pd.g_ewald != ps.g_ewald || pd.rcut_real != ps.rcut_real ||
+      pd.kspace_eps != ps.kspace_eps || pd.slab != ps.slab)
+    return set_err(dst, CPM_EINVAL, "cpm_build_E_copy: device, box or Ewald parameters differ");
+  const bool copy_dc = pd.precond == CPM_PRECOND_DC;
+  if (copy_dc && (ps.precond != CPM_PRECOND_DC || pd.g_dc != ps.g_dc ||
+                  pd.rcut_dc != ps.rcut_dc || pd.p_gap != ps.p_gap))
+    return set_err(dst, CPM_EINVAL, "cpm_build_E_copy: PCG-DC is copied from a src with the "
+                                    "same g_dc, rcut_dc and p_gap");
+  if (!dst->fp64() && src->fp64())
+    return set_err(dst, CPM_EINVAL, "cpm_build_E_copy: FP64 E cannot be narrowed");
+  int st;
+  if ((st = cuda_check(src, cudaStreamSynchronize(src->stream), "copy src sync"))) return st;
+  free_build(dst);
+  const int n = src->n;
+  cudaStream_t s = dst->stream;
+  dst->n = n;
+  dst->npad = src->npad;
+  dst->ldE = src->ldE;
+  dst->vol = src->vol;
+  dst->m = src->m;
+  dst->mpad = src->mpad;
+  dst->c_ele = src->c_ele;
+  dst->d_iters = src->d_iters;
+  const int64_t len = (int64_t)n * src->ldE;
+  const size_t nb = (size_t)n * sizeof(double);
+  if ((st = buf_alloc(dst, &dst->xyz, 3 * nb)) || (st = buf_alloc(dst, &dst->alpha, nb)) ||
+      (st = buf_alloc(dst, &dst->E, (size_t)len * dst->esz())) ||
+      (st = buf_alloc(dst, &dst->diag, 2 * nb)) || (st = buf_alloc(dst, &dst->d, nb))) {
+    free_build(dst);
+    return st;
+  }
+  const cudaMemcpyKind d2d = cudaMemcpyDeviceToDevice;
+  st = cuda_check(dst, cudaMemcpyAsync(dst->xyz.ptr, src->xyz.ptr, 3 * nb, d2d, s), "xyz");
+  if (!st) st = cuda_check(dst, cudaMemcpyAsync(dst->alpha.ptr, src->alpha.ptr, nb, d2d, s), "alpha");
+  if (!st) st = cuda_check(dst, cudaMemcpyAsync(dst->diag.ptr, src->diag.ptr, 2 * nb, d2d, s), "diag");
+  if (!st) st = cuda_check(dst, cudaMemcpyAsync(dst->d.ptr, src->d.ptr, nb, d2d, s), "d");
+  if (!st) {
+    if (dst->esz() == src->esz())
+      st = cuda_check(dst, cudaMemcpyAsync(dst->E.ptr, src->E.ptr, (size_t)len * dst->esz(), d2d,
+                                           s), "E");
+    else
+      (k_widen<<<4 * 152, 256, 0, s>>>((const float*)src->E.ptr, (double*)dst->E.ptr, len),
+       note_launch());
+  }
+  if (!st && copy_dc) {
+    dst->nnz = src->nnz;
+    dst->pgap = src->pgap;
+    const size_t ob = (size_t)(n + 1) * sizeof(int64_t);
+    if ((st = buf_alloc(dst, &dst->nbr_off, ob)) ||
+        (st = buf_alloc(dst, &dst->nbr_idx, (size_t)src->nnz * sizeof(int))) ||
+        (st = buf_alloc(dst, &dst->prow, (size_t)src->nnz * sizeof(double)))) {
+      free_build(dst);
+      return st;
+    }
+    st = cuda_check(dst, cudaMemcpyAsync(dst->nbr_off.ptr, src->nbr_off.ptr, ob, d2d, s), "P");
+    if (!st) st = cuda_check(dst, cudaMemcpyAsync(dst->nbr_idx.ptr, src->nbr_idx.ptr,
+                                                  (size_t)src->nnz * sizeof(int), d2d, s), "P");
+    if (!st) st = cuda_check(dst, cudaMemcpyAsync(dst->prow.ptr, src->prow.ptr,
+                                                  (size_t)src->nnz * sizeof(double), d2d, s), "P");
+  }
+  if (!st) st = cuda_check(dst, cudaGetLastError(), "copy build");
+  if (!st) st = cuda_check(dst, cudaStreamSynchronize(s), "copy build sync");
+  if (st) {
+    free_build(dst);
+    return st;
+  }
+  dst->solve_only = true;
+  dst->built = true;
+  return CPM_OK;
+}
+
 int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
   if (!c) return CPM_EINVAL;
+  c->solve_only = false;
   if (n < 1 || !xyz || !alpha) return set_err(c, CPM_EINVAL, "cpm_build_E: n >= 1 and arrays required");
   // buffers of the previous build are reused where large enough (reserve), not freed
   c->built = false;
@@ -606,16 +711,23 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
                             (double*)ehead.ptr, c->ldE, s);
     cudaEventRecord(c->ev_tc[0], s);
     // the tail, one k-window at a time: every window but the last carries the sum in the
-    // FP64 head matrix, the last writes float E
+    // FP64 head matrix, the last writes float E.  A streamed build times the tensor-core
+    // launches of every window apart from the operand planes made between them.
+    std::vector<cudaEvent_t> wev;
     for (int kbeg = 0; kbeg < c->mpad && !st; kbeg += kwin) {
       const int kend = std::min(c->mpad, kbeg + kwin);
       const bool last = kend == c->mpad;
-      if (c->streamed)
+      if (c->streamed) {
         launch_structure_operand(false, (const double*)c->xyz.ptr, (const uint32_t*)c->sfix.ptr,
                                  c->npad, n, (const int*)c->hkl.ptr, (const double*)c->sqw.ptr,
                                  c->mpad, c->p.box, nullptr, plane_ptrs, c->heavy_steps / 4,
                                  c->kb6_end, c->kb3_end, c->kb8_begin, (const int*)c->kexp.ptr,
                                  c->turn.ptr, kbeg, kend, s);
+        wev.resize(wev.size() + 2);
+        cudaEventCreate(&wev[wev.size() - 2]);
+        cudaEventCreate(&wev[wev.size() - 1]);
+        cudaEventRecord(wev[wev.size() - 2], s);
+      }
       st = launch_ek_tc(planes[0].ptr, planes[1].ptr, planes[2].ptr, planes[3].ptr, c->npad,
                         2 * (int64_t)(kend - kbeg), kbeg / 32, n,
                         std::max(c->heavy_steps / 4, kbeg / 32), kend / 32, c->kb6_end,
@@ -625,6 +737,7 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
                         c->ldE, last ? (float*)c->E.ptr : nullptr, c->ldE, (int*)errbuf.ptr,
                         c->kw.data(), (float*)tcscratch.ptr, c->nsmid,
                         c->streamed ? nullptr : c->ev_tc[2], s);
+      if (c->streamed) cudaEventRecord(wev.back(), s);
     }
     cudaEventRecord(c->ev_tc[1], s);
     int herr = 0;
@@ -633,6 +746,16 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
     if (!st) st = cuda_check(c, cudaStreamSynchronize(s), "tc sync");
     if (!st && herr) st = set_err(c, CPM_ECUDA, "tensor-core k-space kernel: a pipeline wait timed out");
     if (!st) cudaEventElapsedTime(&c->t_tc_ms, c->ev_tc[0], c->ev_tc[1]);
+    c->t_tc_loop_ms = c->t_tc_ms;
+    if (!st && c->streamed) {  // the tensor-core launches alone
+      c->t_tc_ms = 0;
+      for (size_t w = 0; w + 1 < wev.size(); w += 2) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, wev[w], wev[w + 1]);
+        c->t_tc_ms += ms;
+      }
+    }
+    for (auto& e : wev) cudaEventDestroy(e);
     if (!st) cudaEventElapsedTime(&c->t_head_ms, ev_head, c->ev_tc[0]);
     c->t_light_ms = 0;
     if (!st && !c->streamed) cudaEventElapsedTime(&c->t_light_ms, c->ev_tc[2], c->ev_tc[1]);
@@ -718,6 +841,9 @@ int cpm_potential(cpm_ctx* c, int frames, int n_ion, const double* ion_xyz,
                   const double* ion_q, const double* chi, double* b_out, double* qsol_out) {
   if (!c) return CPM_EINVAL;
   if (!c->built) return set_err(c, CPM_ENOTBUILT, "cpm_potential before cpm_build_E");
+  if (c->solve_only)
+    return set_err(c, CPM_EINVAL, "cpm_potential: a context built by cpm_build_E_copy has no "
+                                  "k-space tables; compute b on the source context");
   if (frames < 1 || n_ion < 0 || !chi || !b_out || (n_ion > 0 && (!ion_xyz || !ion_q)))
     return set_err(c, CPM_EINVAL, "cpm_potential: bad arguments");
   const int n = c->n;
@@ -794,7 +920,8 @@ int cpm_solve(cpm_ctx* c, int nrhs, const double* b, double* q_inout, int use_gu
   double* dq = nullptr;
   int st;
   if ((st = stage_in(c, &c->ws_in0, b, bytes, (const void**)&db))) return st;
-  const bool q_dev = is_device_ptr(q_inout);
+  bool q_dev = false;
+  if ((st = on_device(c, q_inout, &q_dev))) return st;
   if (q_dev) {
     dq = q_inout;
   } else {
@@ -826,7 +953,8 @@ int cpm_neutralize(cpm_ctx* c, int nrhs, double* q_inout, const double* qsol) {
   int st;
   double* dq = nullptr;
   const double* dqs = nullptr;
-  const bool q_dev = is_device_ptr(q_inout);
+  bool q_dev = false;
+  if ((st = on_device(c, q_inout, &q_dev))) return st;
   if (q_dev) {
     dq = q_inout;
   } else {
@@ -944,7 +1072,8 @@ int cpm_gcd_charges(cpm_ctx* c, int nrhs, double* q_inout, const double* q0,
   double* dq = nullptr;
   const double* dq0 = nullptr;
   double* ddmu = nullptr;
-  const bool q_dev = is_device_ptr(q_inout);
+  bool q_dev = false;
+  if ((st = on_device(c, q_inout, &q_dev))) return st;
   if (q_dev) {
     dq = q_inout;
   } else {
@@ -1127,6 +1256,7 @@ int cpm_get_info(cpm_ctx* c, cpm_info_t* out) {
   out->tc_blocks_fp8 = tc ? kbn - c->kb8_begin : 0;
   out->t_head_ms = c->t_head_ms;
   out->t_tc_light_ms = c->t_light_ms;
+  out->t_tc_loop_ms = c->t_tc_loop_ms;
   out->d_iters = c->d_iters;
   out->launches = launch_count();
   return CPM_OK;

@@ -84,6 +84,8 @@ struct Ctx {
   std::string err;
 
   bool built = false;
+  bool solve_only = false;  // built by cpm_build_E_copy: E, P, d without the geometry's
+                            // k-space tables (no potential, no guess features)
   int n = 0;        // electrode atoms
   int npad = 0;     // rows of A (multiple of 128), zero beyond n
   int m = 0;        // k-vectors
@@ -159,6 +161,7 @@ struct Ctx {
   float t_matvec_ms = 0;  // last cpm_apply_E: the matvec launches alone
   float t_head_ms = 0;    // FP64-accurate head of the tensor-core build
   float t_light_ms = 0;   // tensor-core tail: the three- and one-product K-blocks
+  float t_tc_loop_ms = 0; // the tail's window loop (streamed builds: operand planes too)
   cudaEvent_t ev_tc[3] = {nullptr, nullptr, nullptr};
 
   bool fp64() const { return p.precision == CPM_PREC_FP64; }
@@ -175,6 +178,12 @@ void buf_free(Ctx* c, Buf* b);
 int buf_reserve(Ctx* c, Buf* b, size_t bytes);  // grow-only
 int set_err(Ctx* c, int code, const std::string& msg);
 int cuda_check(Ctx* c, cudaError_t e, const char* what);
+// Where the array at p lives: 1 in device memory of the context's device (or managed
+// memory), 0 in host memory (or p is null), -1 in device memory of another device.
+int pointer_where(const Ctx* c, const void* p);
+// *dev = whether p is device memory the context's kernels may use; CPM_EINVAL (with a
+// message) when it is device memory of another device.
+int on_device(Ctx* c, const void* p, bool* dev);
 
 // ---- kernels (launchers) -----------------------------------------------------------
 // kspace.cu

@@ -426,15 +426,8 @@ __global__ void k_guess_apply(int64_t len, const float* __restrict__ y, float sc
     q0[k] = q_prev[k] + (double)scale * (double)y[k];
 }
 
-bool on_device(const void* p) {
-  if (!p) return false;
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
+// Device memory of the context's device (or managed memory): what these kernels may use.
+bool dev_ok(const Ctx* c, const void* p) { return pointer_where(c, p) == 1; }
 
 constexpr size_t kGradSmem =
     sizeof(float) * (kP + kB * (kF + 1) + 5 * kB * kLd + kB);
@@ -452,9 +445,11 @@ int features_async(cpm_ctx* c, int frames, const double* b, const double* b_prev
                    const double* chi, float* feat) {
   if (!c) return CPM_EINVAL;
   if (!c->built) return set_err(c, CPM_ENOTBUILT, "cpm_guess_features before cpm_build_E");
+  if (c->solve_only)
+    return set_err(c, CPM_EINVAL, "cpm_guess_features: a context built by cpm_build_E_copy");
   if (c->p.precond != CPM_PRECOND_DC || !c->nbr_off.ptr)
     return set_err(c, CPM_EINVAL, "cpm_guess_features needs the PCG-DC neighbour lists");
-  if (frames < 1 || !on_device(b) || !on_device(b_prev) || !on_device(chi) || !on_device(feat))
+  if (frames < 1 || !dev_ok(c, b) || !dev_ok(c, b_prev) || !dev_ok(c, chi) || !dev_ok(c, feat))
     return set_err(c, CPM_EINVAL, "cpm_guess_features: frames >= 1 and device arrays");
   int st = CPM_OK;
   const int n = c->n;
@@ -540,8 +535,8 @@ int cpm_guess(cpm_ctx* c, const float* params, const float* norm, int bf16, int 
               const double* q_prev, double* q0) {
   if (!c) return CPM_EINVAL;
   if (!c->built) return set_err(c, CPM_ENOTBUILT, "cpm_guess before cpm_build_E");
-  if (frames < 1 || !on_device(params) || !on_device(norm) || !on_device(q_prev) ||
-      !on_device(q0))
+  if (frames < 1 || !dev_ok(c, params) || !dev_ok(c, norm) || !dev_ok(c, q_prev) ||
+      !dev_ok(c, q0))
     return set_err(c, CPM_EINVAL, "cpm_guess: frames >= 1 and device arrays");
   const int64_t samples = (int64_t)frames * c->n;
   int st = buf_reserve(c, &c->ws_feat, samples * kF * sizeof(float));
@@ -566,8 +561,8 @@ int cpm_guess(cpm_ctx* c, const float* params, const float* norm, int bf16, int 
 int cpm_mlp_forward(cpm_ctx* c, const float* params, const float* norm, int bf16,
                     int64_t samples, const float* feat, float* out) {
   if (!c) return CPM_EINVAL;
-  if (samples < 1 || !on_device(params) || !on_device(norm) || !on_device(feat) ||
-      !on_device(out))
+  if (samples < 1 || !dev_ok(c, params) || !dev_ok(c, norm) || !dev_ok(c, feat) ||
+      !dev_ok(c, out))
     return set_err(c, CPM_EINVAL, "cpm_mlp_forward: samples >= 1 and device arrays");
   int st = cuda_check(c, cudaFuncSetAttribute(k_mlp_forward,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -588,8 +583,8 @@ int cpm_mlp_grad(cpm_ctx* c, const float* params, const float* norm, int bf16,
                  int64_t samples, const float* feat, const float* target, float* grad,
                  double* loss) {
   if (!c) return CPM_EINVAL;
-  if (samples < 1 || !on_device(params) || !on_device(norm) || !on_device(feat) ||
-      !on_device(target) || !on_device(grad) || !on_device(loss))
+  if (samples < 1 || !dev_ok(c, params) || !dev_ok(c, norm) || !dev_ok(c, feat) ||
+      !dev_ok(c, target) || !dev_ok(c, grad) || !dev_ok(c, loss))
     return set_err(c, CPM_EINVAL, "cpm_mlp_grad: samples >= 1 and device arrays");
   int st = cuda_check(c, cudaMemsetAsync(grad, 0, kP * sizeof(float), c->stream), "grad zero");
   if (!st) st = cuda_check(c, cudaMemsetAsync(loss, 0, sizeof(double), c->stream), "loss zero");
@@ -607,7 +602,7 @@ int cpm_mlp_grad(cpm_ctx* c, const float* params, const float* norm, int bf16,
 int cpm_mlp_adam(cpm_ctx* c, float* params, float* m, float* v, const float* grad, int step,
                  float lr) {
   if (!c) return CPM_EINVAL;
-  if (step < 1 || !on_device(params) || !on_device(m) || !on_device(v) || !on_device(grad))
+  if (step < 1 || !dev_ok(c, params) || !dev_ok(c, m) || !dev_ok(c, v) || !dev_ok(c, grad))
     return set_err(c, CPM_EINVAL, "cpm_mlp_adam: step >= 1 and device arrays");
   const float c1 = 1.0f / (1.0f - powf(0.9f, (float)step));
   const float c2 = 1.0f / (1.0f - powf(0.999f, (float)step));
@@ -618,7 +613,7 @@ int cpm_mlp_adam(cpm_ctx* c, float* params, float* m, float* v, const float* gra
 int cpm_guess_apply(cpm_ctx* c, int64_t len, const float* y, float scale, const double* q_prev,
                     double* q0) {
   if (!c) return CPM_EINVAL;
-  if (len < 1 || !on_device(y) || !on_device(q_prev) || !on_device(q0))
+  if (len < 1 || !dev_ok(c, y) || !dev_ok(c, q_prev) || !dev_ok(c, q0))
     return set_err(c, CPM_EINVAL, "cpm_guess_apply: len >= 1 and device arrays");
   (k_guess_apply<<<256, 256, 0, c->stream>>>(len, y, scale, q_prev, q0), note_launch());
   int st = cuda_check(c, cudaGetLastError(), "guess apply");

@@ -30,16 +30,6 @@ constexpr int kMaxDevices = 64;
 void* g_scratch_addr[kMaxDevices] = {};
 std::mutex g_scratch_mutex;
 
-bool is_device_pointer(const void* p) {
-  if (!p) return false;
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
-
 // Device address of the scratch array on `device` (looked up once, that device current).
 int scratch_address(Ctx* c, void** out) {
   if (c->device < 0 || c->device >= kMaxDevices)
@@ -75,9 +65,10 @@ extern "C" int cpm_solve_static(cpm_ctx* c, int nrhs, const double* b, double* q
   if (!c->built) return set_err(c, CPM_ENOTBUILT, "cpm_solve_static before cpm_build_E");
   if (nrhs < 1 || !(tol > 0) || maxit < 1)
     return set_err(c, CPM_EINVAL, "cpm_solve_static: bad arguments");
-  if (!is_device_pointer(b) || !is_device_pointer(q_inout))
+  if (pointer_where(c, b) != 1 || pointer_where(c, q_inout) != 1)
     return set_err(c, CPM_EINVAL,
-                   "cpm_solve_static: b and q must be device pointers (staging would allocate)");
+                   "cpm_solve_static: b and q must be device pointers of the context's device "
+                   "(staging would allocate)");
   void* ws = nullptr;
   if (int st = scratch_address(c, &ws)) return st;
   SolveArgs a{nrhs, b, 1.0 / kKe, q_inout, use_guess != 0, tol, maxit, iters_out, relres_out};

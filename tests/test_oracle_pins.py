@@ -339,6 +339,20 @@ def test_kspace_truncation_reading():
     assert len(w) == 8645 and np.all(hkl[:, 0] >= 0)
 
 
+def test_factored_reciprocal_sums_equal_the_pairwise_form():
+    # the angle-addition (C W C^T + S W S^T) form that serves large electrodes against the
+    # difference form of Eq. 23, for E and for the electrolyte potential of Eq. 25
+    work = _cases.tiny_two_sheet(nx=4, ny=4, n_ion=37, q_sol=3)
+    el, io = work.electrode, work.electrolyte
+    a = ew.kspace_pairs(el.xyz, el.xyz, el.box, 0.3, 1e-8)
+    b = ew.kspace_matrix_factored(el.xyz, el.box, 0.3, 1e-8, chunk=300)
+    assert np.abs(a - b).max() <= 1e-13 * np.abs(a).max()
+    p1 = ew.electrolyte_potential(el.xyz, el.alpha, io.xyz[0], io.q[0], el.box, 0.3, 12.0)
+    p2 = ew.electrolyte_potential(el.xyz, el.alpha, io.xyz[0], io.q[0], el.box, 0.3, 12.0,
+                                  kspace="factored")
+    assert np.abs(p1 - p2).max() <= 1e-13 * np.abs(p1).max()
+
+
 def test_matrix_symmetry():
     work = _cases.tiny_two_sheet()
     el = work.electrode
@@ -367,6 +381,10 @@ def test_three_routes_agree(q_sol):
     if q_sol == 0:
         q3 = sv.s_matrix(e) @ b
         assert np.abs(q1 - q3).max() < 1e-10 * scale
+    # the second step alone, given q^b = E^-1 b and d (Eq. 35, S8-S9)
+    d, _, _ = sv.neutralizing_vector(e)
+    q4 = sv.neutralize(np.linalg.solve(e, b), d, qs)
+    assert np.abs(q1 - q4).max() < 1e-10 * scale
 
 
 @pytest.mark.parametrize("q_sol", [0, 2])

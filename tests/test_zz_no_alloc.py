@@ -56,6 +56,36 @@ def test_static_solve_matches_cpm_solve_twice():
     ctx.close()
 
 
+def test_static_solve_allocates_nothing_on_a_fresh_context():
+    # every allocation of this context goes through torch's caching allocator, whose
+    # cumulative count of allocation requests must not move across the no-allocation
+    # solve, even though no cpm_solve has reserved a workspace on this context before
+    work = _cases.tiny_two_sheet()
+    el, io = work.electrode, work.electrolyte
+    ctx = cpm.Context(el.box, torch_allocator=True, rcut_dc=3.0)
+    ctx.cpm_build_E(el.xyz, el.alpha)
+    b = torch.empty((2, el.n), dtype=torch.float64, device="cuda")
+    qs = torch.empty(2, dtype=torch.float64, device="cuda")
+    ctx.cpm_potential(_dev(np.concatenate([io.xyz, io.xyz])),
+                      _dev(np.concatenate([io.q, io.q])), _dev(el.chi), b, qs)
+    q = torch.zeros((2, el.n), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    count0 = torch.cuda.memory_stats()["allocation.all.allocated"]
+    used0 = torch.cuda.memory_allocated()
+    for _ in range(2):
+        q.zero_()
+        it, rel = ctx.cpm_solve_static(b, q, tol=1e-10)
+        assert np.all(rel <= 1e-10)
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_stats()["allocation.all.allocated"] == count0
+    assert torch.cuda.memory_allocated() == used0
+    # the same charges as the allocating solve on this context
+    q_ref = torch.zeros_like(q)
+    ctx.cpm_solve(b, q_ref, tol=1e-10)
+    assert _rel(q, q_ref) < TOL
+    ctx.close()
+
+
 def test_static_solve_rejects_what_it_cannot_serve():
     work = _cases.tiny_two_sheet()
     el = work.electrode
