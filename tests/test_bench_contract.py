@@ -14,7 +14,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def test_reference_arm_prints_one_contract_line():
     out = subprocess.run(
         [sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
-         "--cells", "6", "--ions", "100"],
+         "--workload", "precision", "--cells", "6", "--ions", "100"],
         cwd=ROOT, capture_output=True, text=True, timeout=300, check=True)
     lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1
@@ -28,3 +28,5 @@ def test_reference_arm_prints_one_contract_line():
     assert "N=288" in cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "solves/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+    # the step is the bounded sample: its wall time, not the extrapolated solve time
+    assert d["ms_per_step"] < 300e3 and d["value"] * d["ms_per_step"] / 1e3 <= 1.0
