@@ -7,6 +7,9 @@ host, sum q = -Q^sol, sum d = 1).
 Tolerances as in the small-cell parity tests: E and b entries to 1e-6 of the largest
 entry; the residual to the solve tolerance.
 """
+import hashlib
+import os
+
 import numpy as np
 import pytest
 
@@ -21,6 +24,11 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 ROWS = [0, 4321, 12799]  # first atom, a middle one, the last one (upper sheet)
+
+# the oracle's answers for this cell and frame, written by
+# tests/golden/make_two_sheet_n12800.py (oracle/ alone: FP64 sums, bordered solve)
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                      "two_sheet_n12800.npz")
 
 
 @pytest.fixture(scope="module")
@@ -84,3 +92,31 @@ def test_solution_properties(full):
     assert abs(q.sum() + qsol.sum()) < 1e-12 * np.abs(q).sum()
     d = ctx.cpm_get_d()
     assert d.sum() == pytest.approx(1.0, abs=1e-12)
+
+
+def test_charges_against_the_oracle(full):
+    # the whole q vector of the 12,800-atom cell against the oracle's bordered solve, in
+    # the default BF16X6 build: converged (tol 1e-10) within the 1e-6 parity bar, and in
+    # the bench's configuration (tol 1e-6) within what that residual allows
+    gold = np.load(GOLDEN)
+    work, ctx, *_ = full
+    el = work.electrode
+    digest = hashlib.sha256(np.ascontiguousarray(el.xyz).tobytes() +
+                            np.ascontiguousarray(el.alpha).tobytes()).hexdigest()
+    assert str(gold["electrode_sha256"]) == digest
+    b, qsol = ctx.cpm_potential(gold["ion_xyz"][None], gold["ion_q"][None], el.chi)
+    assert np.abs(b[0] - gold["b_neutral"]).max() < 1e-6 * np.abs(gold["b_neutral"]).max()
+    assert qsol[0] == pytest.approx(float(gold["q_sol"]), abs=1e-12)
+    qb, _, rel = ctx.cpm_solve(b, tol=1e-6, maxit=2000)
+    q6 = ctx.cpm_neutralize(qb, qsol)[0]
+    err6 = np.linalg.norm(q6 - gold["q"]) / np.linalg.norm(gold["q"])
+    qb, _, rel = ctx.cpm_solve(b, tol=1e-10, maxit=4000)
+    assert rel[0] <= 1e-10
+    q = ctx.cpm_neutralize(qb, qsol)[0]
+    err = np.linalg.norm(q - gold["q"]) / np.linalg.norm(gold["q"])
+    d = ctx.cpm_get_d()
+    err_d = np.linalg.norm(d - gold["d"]) / np.linalg.norm(gold["d"])
+    print(f"q error: {err:.3e} converged, {err6:.3e} at tol 1e-6; d error {err_d:.3e}")
+    assert err < 1e-6
+    assert err_d < 1e-6
+    assert err6 < 1e-5
