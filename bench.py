@@ -861,7 +861,7 @@ def run_learned(args, rank, world, local_rank):
     feat = g.features(b[1:T + 1], b[0:T], chi).reshape(-1, 32)
     target = (qb[1:T + 1] - qb[0:T]).reshape(-1).to(torch.float32).contiguous()
     k = min(T, 500) * n
-    g.set_normalisation(feat[:k].cpu().numpy(), target[:k].cpu().numpy())
+    g.set_normalisation(feat[:k], target[:k])
     losses = g.train(feat, target, epochs=args.epochs, batch=65536, lr=2e-3)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t_train
@@ -1016,7 +1016,7 @@ def run_scale_point(args, rank, world, local_rank):
         feat = g.features(b[1:T + 1], b[0:T], chi).reshape(-1, 32)
         target = (qb[1:T + 1] - qb[0:T]).reshape(-1).to(torch.float32).contiguous()
         k = min(feat.shape[0], 500 * 512)
-        g.set_normalisation(feat[:k].cpu().numpy(), target[:k].cpu().numpy())
+        g.set_normalisation(feat[:k], target[:k])
         losses = g.train(feat, target, epochs=args.epochs, batch=65536, lr=2e-3)
         del feat, target
         test = slice(T + 1, T + H + 1)
@@ -1027,6 +1027,7 @@ def run_scale_point(args, rank, world, local_rank):
         qst = torch.empty(H, dtype=torch.float64, device=dev)
         phase = {"potential": 0.0, "guess": 0.0, "solve": 0.0, "neutralize": 0.0}
         iters = []
+        last_max_iters = [0]
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
 
         def step(q_out=None, record=True):
@@ -1036,6 +1037,7 @@ def run_scale_point(args, rank, world, local_rank):
             q0 = g.guess_frames(bt, b_prev, chi, q_prev)
             ev[2].record(stream)
             _, it, _ = ctx.cpm_solve(bt, q0, use_guess=True, tol=TOL, maxit=5000)
+            last_max_iters[0] = int(np.max(it))
             ev[3].record(stream)
             ctx.cpm_neutralize(q0, qst)
             ev[4].record(stream)
@@ -1066,6 +1068,14 @@ def run_scale_point(args, rank, world, local_rank):
             torch.cuda.synchronize()
         launches = ctx.cpm_get_info()["launches"] - launches0
         ms = max_over_ranks(t0.elapsed_time(t1) / args.steps, world)
+        sinfo = ctx.cpm_get_info()  # the last step's solve
+        solve_parts = {"solve_ms": sinfo["t_solve_ms"], "matvec_ms": sinfo["t_solve_matvec_ms"],
+                       "replacement_ms": sinfo["t_solve_replace_ms"],
+                       "replacements": sinfo["solve_replacements"],
+                       "max_iterations": last_max_iters[0]}
+        pot_parts = {"ion_structure_factors_ms": sinfo["t_pot_sf_ms"],
+                     "kspace_ms": sinfo["t_pot_kspace_ms"],
+                     "real_space_and_finish_ms": sinfo["t_pot_real_ms"]}
         # the same frames from the previous-step charges alone (Eq. 26), for the guess's gain
         q0 = q_prev.clone()
         _, it_prev, _ = ctx.cpm_solve(bt, q0, use_guess=True, tol=TOL, maxit=5000)
@@ -1211,6 +1221,16 @@ def run_scale_point(args, rank, world, local_rank):
                      "d_solve": binfo["t_dsolve_ms"]},
         "build_clocks": build_clocks.summary(),
         "phase_ms_per_step": {k: v / args.steps for k, v in phase.items()},
+        "solve_breakdown": solve_parts,
+        "potential_breakdown": pot_parts,
+        "step_matvec": {
+            "kernel": "k_matvec_fast (the 16 columns' inner matvec, E streamed once per "
+                      "iteration)",
+            "ms_per_launch": solve_parts["matvec_ms"] / max(1, solve_parts["max_iterations"]),
+            "gbs": e_bytes / (solve_parts["matvec_ms"] / max(1, solve_parts["max_iterations"])
+                              * 1e-3) / 1e9,
+            "note": "matvec_ms also holds the initial exact matvec of the guess; launches of "
+                    "one iteration counted as one"},
         "mean_iters": statistics.mean(iters),
         "previous_step_guess_iters": float(np.mean(it_prev)),
         "q_rel_err_vs_tight_solve": q_err,
@@ -1286,7 +1306,7 @@ def run_scale_learned(args, rank, world, local_rank):
     feat = g.features(b[1:T + 1], b[0:T], chi).reshape(-1, 32)
     target = (qb[1:T + 1] - qb[0:T]).reshape(-1).to(torch.float32).contiguous()
     k = min(feat.shape[0], 500 * 512)
-    g.set_normalisation(feat[:k].cpu().numpy(), target[:k].cpu().numpy())
+    g.set_normalisation(feat[:k], target[:k])
     losses = g.train(feat, target, epochs=args.epochs, batch=65536, lr=2e-3)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t_train

@@ -57,6 +57,7 @@ extern "C" {
 #define CPM_ENOCONV (-4)     /* maxit reached: q holds the last iterate, relres is set */
 #define CPM_EBREAKDOWN (-5)  /* p^T E p <= 0 or a non-finite value in the iteration */
 #define CPM_ENOTBUILT (-7)   /* cpm_build_E has not succeeded on this context */
+#define CPM_EIO (-8)         /* a file could not be written or read, or is not a valid one */
 
 /* ---- precision of the E build and of the solve ----------------------------------- */
 #define CPM_PREC_FP64 0    /* FP64 phases, FP64 structure-factor GEMM, FP64 E and matvec */
@@ -71,6 +72,12 @@ extern "C" {
 #define CPM_PRECOND_NONE 0    /* conventional CG */
 #define CPM_PRECOND_JACOBI 1  /* diag(E)^-1: the plain baseline */
 #define CPM_PRECOND_DC 2      /* PCG-DC: columns of local inverses M_tau^-1 (Eq. 36) */
+#define CPM_PRECOND_NORMAL 3  /* PCG-Normal (Fig. 6a): the entries of E^-1 for the pairs
+                                 with r < rcut_dc (minimum image), zero elsewhere */
+#define CPM_PRECOND_FULL 4    /* PCG-Full (Fig. 6a): the entries of E^-1 for the pairs
+                                 with r <= rcut_real.  Normal and Full find E^-1 by one
+                                 Jacobi-preconditioned solve over the n identity columns
+                                 at build time (n <= CPM_SMATRIX_MAX_ATOMS) */
 
 /* ---- forms for cpm_get_E ----------------------------------------------------------- */
 #define CPM_E_STORED 0  /* the stored neutral-equivalent E_n */
@@ -101,6 +108,25 @@ typedef struct cpm_params {
      k-vectors per window (rounded down to a multiple of 64), 0 automatic. */
   int stream_operand;
   int k_window;
+  /* Matvec of solves with two or more right-hand sides of a float-stored E:
+     0 (default): the inner iterations apply E to every group of 16 columns in one pass
+     with float products and sums (~1e-6 of the row's partial sums), and the true
+     residual b - E x, through the error-free matvec below, replaces the recursive one
+     whenever a column's residual has fallen 100-fold since its last replacement or it
+     reports convergence: a column converges on its true residual only.
+     1: every matvec error-free (products split exactly, float-pair sums; up to four
+     columns per pass over E).  One right-hand side always takes the error-free matvec. */
+  int matvec_mode;
+  /* How a solve runs.  0 (default): chosen per context by its online autotuner for each
+     bucket of right-hand-side counts (1, 2-3, 4-7, .., 128 and more): the first eligible
+     solve of a bucket runs on the cluster path, the next on the kernel path, each timed
+     per iteration on the device, and later solves take the faster (a build resets it).
+     1: the kernel path: a few kernels an iteration, the host polling convergence every
+     four iterations (every size, every precision, ragged batches).  2: the cluster path:
+     the whole solve in one launch, one thread-block cluster of 8 CTAs per right-hand
+     side, for float storage and n <= 4,096 (larger or FP64 contexts take the kernel
+     path).  cpm_solve_static always takes the kernel path. */
+  int solver_path;
 } cpm_params;
 
 typedef struct cpm_ctx cpm_ctx;
@@ -203,6 +229,21 @@ int cpm_plan_kspace(const cpm_params* p, cpm_kspace_plan* out, int* hkl, double*
  */
 int cpm_potential(cpm_ctx* c, int frames, int n_ion, const double* ion_xyz,
                   const double* ion_q, const double* chi, double* b_out, double* qsol_out);
+
+/*
+ * Forces on the electrolyte ions from the electrode charges: F_I = -q_I d/dr_I
+ * sum_i q_i e_iI(alpha_i), with e_iI the point-Gaussian coefficient of Eq. 25 in the
+ * paper's form (real space with the Gaussian's own terms of Eq. S25, reciprocal space,
+ * and the slab term of Eq. 39; the constants drop out).  ion_xyz[frames*n_ion*3] (A),
+ * ion_q[frames*n_ion] (e), q[frames*n] the electrode charges (e, e.g. cpm_neutralize's),
+ * f_out[frames*n_ion*3] in e^2/A^2 (times k_e = 14.399645478 for eV/A).  Real space in
+ * FP64 over every image within r_c; the reciprocal part from the electrode's
+ * charge-weighted structure factors (head k-vectors in FP64, the rest in float phasors
+ * with error-free float-pair sums).  Not a step of the charge solve: what the charges do to
+ * the ions in an MD step (Supplementary Note, Eq. S25).
+ */
+int cpm_ion_forces(cpm_ctx* c, int frames, int n_ion, const double* ion_xyz,
+                   const double* ion_q, const double* q, double* f_out);
 
 /*
  * First step of Eq. 35: solves E_n q^b = b / k_e for nrhs right-hand sides by
@@ -339,6 +380,30 @@ int cpm_mlp_grad(cpm_ctx* c, const float* params, const float* norm, int bf16,
 int cpm_mlp_adam(cpm_ctx* c, float* params, float* m, float* v, const float* grad, int step,
                  float lr);
 
+/* The network's initial parameters into params[CPM_MLP_PARAMS] (device): the weights of a
+ * layer with i inputs uniform in [-sqrt(6/i), sqrt(6/i)) (the output layer's times 0.1,
+ * so that the first guesses stay near the previous step's charges), biases zero.  Weight
+ * k is drawn from output number k of a SplitMix64 stream seeded with `seed` (its top 53
+ * bits as a uniform in [0, 1)), so the same seed gives the same network on any device. */
+int cpm_guess_init(cpm_ctx* c, uint64_t seed, float* params);
+
+/* The feature normalisation and the target scale from `samples` training samples:
+ * norm[64] (host or device) receives each feature's mean, then its inverse standard
+ * deviation (0 for a feature constant over the samples); *target_scale (host) the
+ * standard deviation of target[samples] (1 if it is 0).  feat[samples*32] and
+ * target[samples] are device arrays; the sums run in FP64 in a fixed order. */
+int cpm_guess_norm(cpm_ctx* c, int64_t samples, const float* feat, const float* target,
+                   float* norm, float* target_scale);
+
+/* A trained network to / from a file: parameters[CPM_MLP_PARAMS], norm[64] and the
+ * target scale (pointers host or device), with a header (magic "CPMGUESS", version 1,
+ * sizes) and an FNV-1a checksum.  CPM_EIO when the file cannot be written or read, or
+ * its header, size or checksum do not match; nothing is written into the outputs then.
+ * No context: host file operations only. */
+int cpm_guess_save(const char* path, const float* params, const float* norm,
+                   float target_scale);
+int cpm_guess_load(const char* path, float* params, float* norm, float* target_scale);
+
 /* q0[k] = q_prev[k] + scale * y[k] for k < len. */
 int cpm_guess_apply(cpm_ctx* c, int64_t len, const float* y, float scale, const double* q_prev,
                     double* q0);
@@ -387,6 +452,14 @@ typedef struct cpm_info_t {
   double t_tc_loop_ms;  /* BF16X6 builds: the whole k-window loop of the tail; a streamed
                            build makes each window's operand planes inside it, so there
                            t_tc_ms (the tensor-core launches alone) is the smaller */
+  double t_solve_ms;         /* last PCG solve on this context: device time */
+  double t_solve_matvec_ms;  /* ... of its matvec launches (inner and error-free) */
+  double t_solve_replace_ms; /* ... of its residual replacements (many-column solves) */
+  int solve_replacements;    /* ... and their count */
+  double t_pot_sf_ms;        /* last cpm_potential: the ions' structure factors, */
+  double t_pot_kspace_ms;    /* the k-space contraction with the electrode operand, */
+  double t_pot_real_ms;      /* the real-space sums and b = chi - k_e b^sol (device time) */
+  int solve_path;            /* path of the last solve: 1 kernels, 2 cluster-resident */
 } cpm_info_t;
 
 int cpm_get_info(cpm_ctx* c, cpm_info_t* out);

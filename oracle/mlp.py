@@ -65,6 +65,49 @@ def init_params(rng, scale=1.0):
     return np.concatenate(parts)
 
 
+def splitmix64_uniform(seed: int, k):
+    """Output numbers k (from 0) of the SplitMix64 stream seeded with `seed` (Steele, Lea
+    and Flood, 2014) as doubles uniform in [0, 1) from their top 53 bits."""
+    m = (1 << 64) - 1
+    k = np.asarray(k, dtype=object)
+    out = np.empty(k.shape, dtype=np.float64)
+    for idx, kk in np.ndenumerate(k):
+        z = (seed + (int(kk) + 1) * 0x9E3779B97F4A7C15) & m
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & m
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & m
+        z ^= z >> 31
+        out[idx] = (z >> 11) * 2.0 ** -53
+    return out
+
+
+def init_params_counter(seed: int):
+    """The library's initialisation (project choice), written out: layer by layer, the
+    weights of a layer with i inputs uniform in [-sqrt(6/i), sqrt(6/i)), the output
+    layer's times 0.1, biases zero; parameter k takes SplitMix64 output k.  Returned as
+    float32, the type the library stores."""
+    out, k = [], 0
+    for li, (o, i) in enumerate(LAYERS):
+        lim = np.sqrt(6.0 / i) * (0.1 if li == len(LAYERS) - 1 else 1.0)
+        u = splitmix64_uniform(seed, np.arange(k, k + o * i))
+        out.append((lim * (2.0 * u - 1.0)).astype(np.float32))
+        k += o * i
+        out.append(np.zeros(o, dtype=np.float32))
+        k += o
+    return np.concatenate(out)
+
+
+def normalisation(feat, target):
+    """Per-feature mean and inverse standard deviation (population; 0 for a constant
+    feature) and the target's standard deviation (1 if 0), in FP64."""
+    f = np.asarray(feat, dtype=np.float64).reshape(-1, N_FEATURES)
+    mu = f.mean(axis=0)
+    sd = np.sqrt(((f - mu) ** 2).mean(axis=0))
+    inv = np.where(sd > 1e-12, 1.0 / np.where(sd > 1e-12, sd, 1.0), 0.0)
+    t = np.asarray(target, dtype=np.float64)
+    ts = float(np.sqrt(((t - t.mean()) ** 2).mean()))
+    return np.concatenate([mu, inv]), (ts if ts > 0 else 1.0)
+
+
 def forward(params, x):
     """x [S, 32] -> y [S]; also returns the pre-activations for backprop."""
     layers = unpack(np.asarray(params, dtype=np.float64))

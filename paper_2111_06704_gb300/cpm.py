@@ -20,6 +20,9 @@ CPM_ECUDA = -3
 CPM_ENOCONV = -4
 CPM_EBREAKDOWN = -5
 CPM_ENOTBUILT = -7
+CPM_EIO = -8
+CPM_MLP_FEATURES = 32
+CPM_MLP_PARAMS = 10497
 
 CPM_PREC_FP64 = 0
 CPM_PREC_FP32 = 1
@@ -28,6 +31,8 @@ CPM_PREC_BF16X6 = 2
 CPM_PRECOND_NONE = 0
 CPM_PRECOND_JACOBI = 1
 CPM_PRECOND_DC = 2
+CPM_PRECOND_NORMAL = 3
+CPM_PRECOND_FULL = 4
 
 CPM_E_STORED = 0
 CPM_E_PAPER = 1
@@ -59,6 +64,8 @@ class cpm_params(ctypes.Structure):
         ("alloc_user", ctypes.c_void_p),
         ("stream_operand", ctypes.c_int),
         ("k_window", ctypes.c_int),
+        ("matvec_mode", ctypes.c_int),
+        ("solver_path", ctypes.c_int),
     ]
 
 
@@ -83,6 +90,14 @@ class cpm_info_t(ctypes.Structure):
         ("t_tc_light_ms", ctypes.c_double),
         ("tc_blocks_fp8", ctypes.c_int),
         ("t_tc_loop_ms", ctypes.c_double),
+        ("t_solve_ms", ctypes.c_double),
+        ("t_solve_matvec_ms", ctypes.c_double),
+        ("t_solve_replace_ms", ctypes.c_double),
+        ("solve_replacements", ctypes.c_int),
+        ("t_pot_sf_ms", ctypes.c_double),
+        ("t_pot_kspace_ms", ctypes.c_double),
+        ("t_pot_real_ms", ctypes.c_double),
+        ("solve_path", ctypes.c_int),
     ]
 
 
@@ -108,7 +123,8 @@ EXPORTS = ["cpm_default_params", "cpm_create", "cpm_destroy", "cpm_build_E", "cp
            "cpm_batch_neutralize", "cpm_batch_last_error", "cpm_get_E_rows",
            "cpm_guess", "cpm_release_workspace", "cpm_plan_kspace", "cpm_gcd_setup",
            "cpm_gcd_charges", "cpm_smatrix_build", "cpm_smatrix_charges",
-           "cpm_build_E_copy"]
+           "cpm_build_E_copy", "cpm_guess_init", "cpm_guess_norm", "cpm_guess_save",
+           "cpm_guess_load", "cpm_ion_forces"]
 
 _lib = None
 
@@ -137,6 +153,11 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.cpm_release_workspace.argtypes = [vp]
     lib.cpm_build_E.argtypes = [vp, i, vp, vp]
     lib.cpm_build_E_copy.argtypes = [vp, vp]
+    lib.cpm_ion_forces.argtypes = [vp, i, i, vp, vp, vp, vp]
+    lib.cpm_guess_init.argtypes = [vp, ctypes.c_uint64, vp]
+    lib.cpm_guess_norm.argtypes = [vp, i64, vp, vp, vp, vp]
+    lib.cpm_guess_save.argtypes = [ctypes.c_char_p, vp, vp, ctypes.c_float]
+    lib.cpm_guess_load.argtypes = [ctypes.c_char_p, vp, vp, vp]
     lib.cpm_potential.argtypes = [vp, i, i, vp, vp, vp, vp, vp]
     lib.cpm_solve.argtypes = [vp, i, vp, vp, i, d, i, vp, vp]
     lib.cpm_solve_static.argtypes = [vp, i, vp, vp, i, d, i, vp, vp]
@@ -232,13 +253,21 @@ def cpm_plan_kspace(box, **params) -> dict:
 class Context:
     """One libcpm context (one electrode geometry, one CUDA device and stream)."""
 
-    def __init__(self, box, stream=None, torch_allocator: bool = False, **params):
+    def __init__(self, box, stream=None, torch_allocator: bool = False, allocator=None,
+                 **params):
+        """allocator: optional (alloc(nbytes) -> device address or None, free(address))
+        pair of Python callables behind the library's allocator callback."""
         self.lib = load()
         self.params = default_params(box, **params)
         if stream is not None:
             self.params.stream = ctypes.c_void_p(int(stream))
         self._cb = None
-        if torch_allocator:
+        if allocator is not None:
+            alloc_py, free_py = allocator
+            self._cb = (ALLOC_FN(lambda nbytes, _user: alloc_py(int(nbytes))),
+                        FREE_FN(lambda ptr, _user: free_py(ptr)))
+            self.params.alloc, self.params.free = self._cb
+        elif torch_allocator:
             import torch
             dev = torch.cuda.current_device()
 
@@ -314,6 +343,20 @@ class Context:
         if isinstance(qsol_out, np.ndarray) and k5 is not qsol_out:
             qsol_out[...] = k5
         return b_out, qsol_out
+
+    def cpm_ion_forces(self, ion_xyz, ion_q, q, f_out=None):
+        """Forces on the ions from the electrode charges q [frames, n] (e^2/A^2)."""
+        frames, n_ion = int(ion_q.shape[0]), int(ion_q.shape[1])
+        if f_out is None:
+            f_out = np.empty((frames, n_ion, 3))
+        p1, k1 = _ptr(ion_xyz)
+        p2, k2 = _ptr(ion_q)
+        p3, k3 = _ptr(q)
+        p4, k4 = _ptr(f_out)
+        self._check(self.lib.cpm_ion_forces(self.h, frames, n_ion, p1, p2, p3, p4))
+        if isinstance(f_out, np.ndarray) and k4 is not f_out:
+            f_out[...] = k4
+        return f_out
 
     def cpm_solve(self, b, q=None, use_guess=False, tol=1e-6, maxit=1000, allow_noconv=False):
         nrhs = int(b.shape[0]) if b.ndim == 2 else 1

@@ -327,7 +327,7 @@ void release_workspace(Ctx* c) {
   Buf* ws[] = {&c->tc_planes[0], &c->tc_planes[1], &c->tc_planes[2], &c->tc_planes[3],
                &c->tc_head, &c->tc_err,
                &c->tc_hsplit, &c->tc_scratch, &c->dc_cnt, &c->dc_pcol, &c->dc_status, &c->ws_solve, &c->ws_in0, &c->ws_in1, &c->ws_in2,
-               &c->ws_out0, &c->ws_out1, &c->ws_pot, &c->ws_guess, &c->ws_feat};
+               &c->ws_out0, &c->ws_out1, &c->ws_pot, &c->ws_guess, &c->ws_feat, &c->ws_cluster};
   for (Buf* b : ws) buf_free(c, b);
 }
 
@@ -346,6 +346,10 @@ void free_build(Ctx* c) {
   c->shells_ready = false;
   c->gcd_m = 0;
   c->smat_ready = false;
+  for (int b = 0; b < 8; ++b) {  // the solver's autotuner starts again with the next build
+    c->tune_path[b] = 0;
+    c->tune_cost[b][0] = c->tune_cost[b][1] = 0.f;
+  }
 }
 
 __global__ void k_inverse_tail(double* diag, int n) {
@@ -357,6 +361,18 @@ __global__ void k_fill(double* v, int64_t len, double x) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
        i += (int64_t)gridDim.x * blockDim.x)
     v[i] = x;
+}
+
+// *bad = 1 when a coordinate is not finite or a width is neither positive and finite nor
+// +INFINITY (a point charge); *bad starts at 0.
+__global__ void k_check_geometry(const double* __restrict__ xyz, const double* __restrict__ alpha,
+                                 int n, int* __restrict__ bad) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double a = alpha[i];
+    if (!isfinite(xyz[3 * i]) || !isfinite(xyz[3 * i + 1]) || !isfinite(xyz[3 * i + 2]) ||
+        !(a > 0.0) || isnan(a))
+      *bad = 1;
+  }
 }
 
 // dst [n][ld] (double) = src [n][ld] (float): exact widening of the stored matrix.
@@ -404,8 +420,10 @@ static bool params_valid(const cpm_params* p) {
   if (p->precision != CPM_PREC_FP64 && p->precision != CPM_PREC_FP32 &&
       p->precision != CPM_PREC_BF16X6)
     return false;
-  if (p->precond < CPM_PRECOND_NONE || p->precond > CPM_PRECOND_DC) return false;
+  if (p->precond < CPM_PRECOND_NONE || p->precond > CPM_PRECOND_FULL) return false;
   if (p->stream_operand < 0 || p->stream_operand > 1 || p->k_window < 0) return false;
+  if (p->matvec_mode < 0 || p->matvec_mode > 1) return false;
+  if (p->solver_path < 0 || p->solver_path > 2) return false;
   if ((p->alloc == nullptr) != (p->free == nullptr)) return false;
   return true;
 }
@@ -437,6 +455,8 @@ int cpm_destroy(cpm_ctx* c) {
   cudaEventDestroy(c->ev_tc[0]);
   cudaEventDestroy(c->ev_tc[1]);
   cudaEventDestroy(c->ev_tc[2]);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->ev_pot) cudaEventDestroy(e);
   delete c;
   return CPM_OK;
 }
@@ -487,11 +507,11 @@ int cpm_build_E_copy(cpm_ctx* dst, cpm_ctx* src) {
       pd.box[2] != ps.box[2] || pd.g_ewald != ps.g_ewald || pd.rcut_real != ps.rcut_real ||
       pd.kspace_eps != ps.kspace_eps || pd.slab != ps.slab)
     return set_err(dst, CPM_EINVAL, "cpm_build_E_copy: device, box or Ewald parameters differ");
-  const bool copy_dc = pd.precond == CPM_PRECOND_DC;
-  if (copy_dc && (ps.precond != CPM_PRECOND_DC || pd.g_dc != ps.g_dc ||
+  const bool copy_dc = pd.precond >= CPM_PRECOND_DC;  // PCG-DC, -Normal or -Full
+  if (copy_dc && (ps.precond != pd.precond || pd.g_dc != ps.g_dc ||
                   pd.rcut_dc != ps.rcut_dc || pd.p_gap != ps.p_gap))
-    return set_err(dst, CPM_EINVAL, "cpm_build_E_copy: PCG-DC is copied from a src with the "
-                                    "same g_dc, rcut_dc and p_gap");
+    return set_err(dst, CPM_EINVAL, "cpm_build_E_copy: a sparse preconditioner is copied "
+                                    "from a src with the same one (g_dc, rcut_dc, p_gap)");
   if (!dst->fp64() && src->fp64())
     return set_err(dst, CPM_EINVAL, "cpm_build_E_copy: FP64 E cannot be narrowed");
   int st;
@@ -558,6 +578,10 @@ int cpm_build_E_copy(cpm_ctx* dst, cpm_ctx* src) {
 int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
   if (!c) return CPM_EINVAL;
   c->solve_only = false;
+  for (int b = 0; b < 8; ++b) {  // the solver's autotuner starts again for this electrode
+    c->tune_path[b] = 0;
+    c->tune_cost[b][0] = c->tune_cost[b][1] = 0.f;
+  }
   if (n < 1 || !xyz || !alpha) return set_err(c, CPM_EINVAL, "cpm_build_E: n >= 1 and arrays required");
   // buffers of the previous build are reused where large enough (reserve), not freed
   c->built = false;
@@ -568,7 +592,8 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
   const bool f64 = c->fp64();
   int st;
   c->n = n;
-  c->npad = (int)round_up(n, 128);
+  // rows of the operand: whole 256-row blocks for the tensor-core tail's CTA pairs
+  c->npad = (int)round_up(n, c->p.precision == CPM_PREC_BF16X6 ? 256 : 128);
   c->ldE = round_up(n, 128);
   c->vol = c->p.box[0] * c->p.box[1] * c->p.box[2];
   // the k-vector table depends on the box, g and eps only: made once per context
@@ -633,6 +658,20 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
       (st = cuda_check(c, cudaMemsetAsync(c->E.ptr, 0, e_bytes, s), "E memset")) ||
       (st = cuda_check(c, cudaStreamSynchronize(s), "build upload")))
     return fail(st);
+  {  // the geometry is checked before any kernel uses it (the diagonal buffer is free yet)
+    int bad = 0;
+    int* dbad = (int*)c->diag.ptr;
+    if ((st = cuda_check(c, cudaMemsetAsync(dbad, 0, sizeof(int), s), "check flag"))) return fail(st);
+    (k_check_geometry<<<std::min((n + 255) / 256, 1024), 256, 0, s>>>(
+         (const double*)c->xyz.ptr, (const double*)c->alpha.ptr, n, dbad), note_launch());
+    if ((st = cuda_check(c, cudaMemcpyAsync(&bad, dbad, sizeof(int), cudaMemcpyDeviceToHost, s),
+                         "check flag")) ||
+        (st = cuda_check(c, cudaStreamSynchronize(s), "check sync")))
+      return fail(st);
+    if (bad)
+      return fail(set_err(c, CPM_EINVAL, "cpm_build_E: a coordinate is not finite or a width "
+                                         "is not positive (INFINITY marks a point charge)"));
+  }
 
   cudaEvent_t ev[6];
   for (auto& e : ev) cudaEventCreate(&e);
@@ -782,7 +821,12 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
   c->built = true;  // E is usable from here on (the solves below need it)
 
   cudaEventRecord(ev[3], s);
-  if (c->p.precond == CPM_PRECOND_DC) {
+  if (c->p.precond == CPM_PRECOND_NORMAL || c->p.precond == CPM_PRECOND_FULL) {
+    if ((st = build_sparse_inverse(c))) {
+      for (auto& e : ev) cudaEventDestroy(e);
+      return fail(st);
+    }
+  } else if (c->p.precond == CPM_PRECOND_DC) {
     if ((st = build_dc_preconditioner(c))) {
       for (auto& e : ev) cudaEventDestroy(e);
       return fail(st);
@@ -885,6 +929,16 @@ int cpm_potential(cpm_ctx* c, int frames, int n_ion, const double* ion_xyz,
   double* vh = (double*)((char*)c->ws_pot.ptr + vbytes);
   double* bk = (double*)((char*)c->ws_pot.ptr + vbytes + hbytes);
   uint32_t* sion = (uint32_t*)((char*)c->ws_pot.ptr + vbytes + hbytes + kbytes);
+  cudaEvent_t pev[4];
+  for (int e = 0; e < 4; ++e) {
+    while (c->ev_pot.size() < 4) {
+      cudaEvent_t x;
+      cudaEventCreate(&x);
+      c->ev_pot.push_back(x);
+    }
+    pev[e] = c->ev_pot[e];
+  }
+  cudaEventRecord(pev[0], s);
   if (n_ion > 0) {
     launch_ion_fixed(dx, frames, n_ion, c->p.box, sion, s);
     launch_ion_structure_factor(f64, dx, sion, dq, frames, n_ion, (const int*)c->hkl.ptr,
@@ -893,19 +947,84 @@ int cpm_potential(cpm_ctx* c, int frames, int n_ion, const double* ion_xyz,
   } else if ((st = cuda_check(c, cudaMemsetAsync(v, 0, vbytes + hbytes, s), "v zero"))) {
     return st;
   }
+  cudaEventRecord(pev[1], s);
   launch_bsol_kspace(f64, c->A.ptr, (const double*)c->Ahead.ptr, n, c->mpad, c->kh, v, vh,
                      frames, bk, (const uint32_t*)c->sfix.ptr, (const int*)c->hkl.ptr,
                      (const double*)c->sqw.ptr, c->turn.ptr, s);
+  cudaEventRecord(pev[2], s);
   launch_bsol_real_and_finish((const double*)c->xyz.ptr, (const double*)c->alpha.ptr,
                               (const uint32_t*)c->sfix.ptr, n, dx, dq, sion, frames, n_ion,
                               geometry(c), dchi, bk, db, dqs, s);
+  cudaEventRecord(pev[3], s);
   if ((st = cuda_check(c, cudaGetLastError(), "potential kernels"))) return st;
   if (qsol_out && n_ion == 0 &&
       (st = cuda_check(c, cudaMemsetAsync(dqs, 0, frames * sizeof(double), s), "qsol zero")))
     return st;
   if ((st = copy_out(c, b_out, db, (size_t)frames * n * sizeof(double)))) return st;
   if (qsol_out && (st = copy_out(c, qsol_out, dqs, (size_t)frames * sizeof(double)))) return st;
-  return cuda_check(c, cudaStreamSynchronize(s), "potential sync");
+  if ((st = cuda_check(c, cudaStreamSynchronize(s), "potential sync"))) return st;
+  cudaEventElapsedTime(&c->t_pot_sf_ms, pev[0], pev[1]);
+  cudaEventElapsedTime(&c->t_pot_kspace_ms, pev[1], pev[2]);
+  cudaEventElapsedTime(&c->t_pot_real_ms, pev[2], pev[3]);
+  return CPM_OK;
+}
+
+int cpm_ion_forces(cpm_ctx* c, int frames, int n_ion, const double* ion_xyz,
+                   const double* ion_q, const double* q, double* f_out) {
+  if (!c) return CPM_EINVAL;
+  if (!c->built) return set_err(c, CPM_ENOTBUILT, "cpm_ion_forces before cpm_build_E");
+  if (c->solve_only)
+    return set_err(c, CPM_EINVAL, "cpm_ion_forces: a context built by cpm_build_E_copy");
+  if (frames < 1 || n_ion < 1 || !ion_xyz || !ion_q || !q || !f_out)
+    return set_err(c, CPM_EINVAL, "cpm_ion_forces: bad arguments");
+  const int n = c->n;
+  cudaStream_t s = c->stream;
+  const bool f64 = c->fp64();
+  const double *dx = nullptr, *dq = nullptr, *dqe = nullptr;
+  double* dout = nullptr;
+  int st;
+  if ((st = stage_in(c, &c->ws_in0, ion_xyz, (size_t)frames * n_ion * 3 * sizeof(double),
+                     (const void**)&dx)) ||
+      (st = stage_in(c, &c->ws_in1, ion_q, (size_t)frames * n_ion * sizeof(double),
+                     (const void**)&dq)) ||
+      (st = stage_in(c, &c->ws_in2, q, (size_t)frames * n * sizeof(double), (const void**)&dqe)) ||
+      (st = stage_out(c, &c->ws_out0, f_out, (size_t)frames * n_ion * 3 * sizeof(double),
+                      (void**)&dout)))
+    return st;
+  // scratch: structure factors v [frames][2 mpad] (storage type) | v_head [frames][2 kh] |
+  //          fixed-point ion coordinates [frames][n_ion][3] | k-space gradients [frames][n_ion][3]
+  auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const int kh = f64 ? c->mpad : c->kh;  // FP64 storage: every k-vector in FP64
+  const size_t vbytes = up((size_t)frames * 2 * c->mpad * c->esz());
+  const size_t hbytes = up((size_t)frames * 2 * std::max(c->kh, 1) * sizeof(double));
+  const size_t ubytes = up((size_t)frames * n_ion * 3 * sizeof(uint32_t));
+  const size_t gbytes = up((size_t)frames * n_ion * 3 * sizeof(double));
+  if ((st = buf_reserve(c, &c->ws_pot, vbytes + hbytes + ubytes + gbytes))) return st;
+  if (!f64 && !c->turn.ptr) {
+    if ((st = buf_alloc(c, &c->turn, 4096 * 4 * sizeof(float)))) return st;
+    launch_turn_table(c->turn.ptr, s);
+  }
+  char* base = (char*)c->ws_pot.ptr;
+  void* v = base;
+  double* vh = (double*)(base + vbytes);
+  uint32_t* sion = (uint32_t*)(base + vbytes + hbytes);
+  double* grad = (double*)(base + vbytes + hbytes + ubytes);
+  launch_ion_fixed(dx, frames, n_ion, c->p.box, sion, s);
+  // the electrode's charge-weighted structure factors, frame by frame: the ions' kernel
+  // run over the electrode atoms (same coordinates every frame)
+  for (int f = 0; f < frames; ++f)
+    launch_ion_structure_factor(f64, (const double*)c->xyz.ptr, (const uint32_t*)c->sfix.ptr,
+                                dqe + (size_t)f * n, 1, n, (const int*)c->hkl.ptr,
+                                (const double*)c->sqw.ptr, c->mpad, c->kh, c->p.box,
+                                c->turn.ptr, (char*)v + (size_t)f * 2 * c->mpad * c->esz(),
+                                vh + (size_t)f * 2 * std::max(c->kh, 1), s);
+  launch_ion_forces((const double*)c->xyz.ptr, (const double*)c->alpha.ptr,
+                    (const uint32_t*)c->sfix.ptr, n, dx, dq, sion, frames, n_ion, dqe,
+                    (const int*)c->hkl.ptr, (const double*)c->sqw.ptr, c->mpad, kh, geometry(c),
+                    c->turn.ptr, (const float*)v, f64 ? (const double*)v : vh, grad, dout, s);
+  if ((st = cuda_check(c, cudaGetLastError(), "ion forces"))) return st;
+  if ((st = copy_out(c, f_out, dout, (size_t)frames * n_ion * 3 * sizeof(double)))) return st;
+  return cuda_check(c, cudaStreamSynchronize(s), "ion forces sync");
 }
 
 int cpm_solve(cpm_ctx* c, int nrhs, const double* b, double* q_inout, int use_guess,
@@ -1227,8 +1346,9 @@ int cpm_get_d(cpm_ctx* c, double* d_out) {
 int cpm_get_precond(cpm_ctx* c, int64_t* off, int* idx, double* val) {
   if (!c) return CPM_EINVAL;
   if (!c->built) return set_err(c, CPM_ENOTBUILT, "cpm_get_precond before cpm_build_E");
-  if (c->p.precond != CPM_PRECOND_DC || !c->nbr_off.ptr)
-    return set_err(c, CPM_EINVAL, "cpm_get_precond: the context was built without PCG-DC");
+  if (c->p.precond < CPM_PRECOND_DC || !c->nbr_off.ptr)
+    return set_err(c, CPM_EINVAL, "cpm_get_precond: the context was built without a sparse "
+                                  "preconditioner (PCG-DC, -Normal or -Full)");
   if (!off || !idx || !val) return set_err(c, CPM_EINVAL, "cpm_get_precond: null output");
   return copy_precond(c, off, idx, val);
 }
@@ -1257,6 +1377,14 @@ int cpm_get_info(cpm_ctx* c, cpm_info_t* out) {
   out->t_head_ms = c->t_head_ms;
   out->t_tc_light_ms = c->t_light_ms;
   out->t_tc_loop_ms = c->t_tc_loop_ms;
+  out->t_solve_ms = c->t_solve_ms;
+  out->t_solve_matvec_ms = c->t_solve_mv_ms;
+  out->t_solve_replace_ms = c->t_solve_rep_ms;
+  out->solve_replacements = c->solve_replacements;
+  out->t_pot_sf_ms = c->t_pot_sf_ms;
+  out->t_pot_kspace_ms = c->t_pot_kspace_ms;
+  out->t_pot_real_ms = c->t_pot_real_ms;
+  out->solve_path = c->last_solve_path;
   out->d_iters = c->d_iters;
   out->launches = launch_count();
   return CPM_OK;

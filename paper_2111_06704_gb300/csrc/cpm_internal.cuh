@@ -151,6 +151,13 @@ struct Ctx {
   std::vector<int> kv_hkl;    // the k-vector table (host), made on the first build
   std::vector<double> kv_w;
   Buf ws_solve, ws_in0, ws_in1, ws_in2, ws_out0, ws_out1, ws_pot, ws_guess, ws_feat;
+  Buf ws_cluster;  // per-column results of the cluster-resident solve
+  // the solver's online autotuner: per bucket of right-hand-side counts (1, 2-3, 4-7, ..,
+  // 128+), the path found faster (0 not yet known, 1 host-driven kernels, 2 cluster-
+  // resident) and the measured device time per iteration of each path (reset by a build)
+  int tune_path[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  float tune_cost[8][2] = {};
+  int last_solve_path = 0;
   // tensor-core build workspace, kept for the next build: operand planes, the FP64
   // head matrix, the error flag, the head's float pairs, the per-SM hi / lo scratch
   Buf tc_planes[4], tc_head, tc_err, tc_hsplit, tc_scratch;  // planes 0-2: 16-bit, 3: FP8
@@ -162,6 +169,15 @@ struct Ctx {
   float t_head_ms = 0;    // FP64-accurate head of the tensor-core build
   float t_light_ms = 0;   // tensor-core tail: the three- and one-product K-blocks
   float t_tc_loop_ms = 0; // the tail's window loop (streamed builds: operand planes too)
+  // last PCG solve: its device time, that of its matvec launches (fast or exact), of its
+  // residual replacements, and their count
+  float t_solve_ms = 0, t_solve_mv_ms = 0, t_solve_rep_ms = 0;
+  int solve_replacements = 0;
+  std::vector<cudaEvent_t> ev_pool;  // timing events of the solve, made on first use
+  // last cpm_potential: the ions' structure factors, the k-space contraction, the real
+  // space with the finish (device time)
+  float t_pot_sf_ms = 0, t_pot_kspace_ms = 0, t_pot_real_ms = 0;
+  std::vector<cudaEvent_t> ev_pot;
   cudaEvent_t ev_tc[3] = {nullptr, nullptr, nullptr};
 
   bool fp64() const { return p.precision == CPM_PREC_FP64; }
@@ -241,6 +257,13 @@ void launch_bsol_real_and_finish(const double* xyz, const double* alpha, const u
                                  const Geometry& geo, const double* chi, const double* bsol_k,
                                  double* b_out, double* qsol, cudaStream_t s);
 
+void launch_ion_forces(const double* xyz, const double* alpha, const uint32_t* sfix, int n,
+                       const double* ion_xyz, const double* ion_q, const uint32_t* sion,
+                       int frames, int n_ion, const double* q, const int* hkl,
+                       const double* sqw, int mpad, int kh, const Geometry& geo,
+                       const void* turn, const float* v, const double* vhead, double* grad,
+                       double* out, cudaStream_t s);
+
 // pcg.cu
 // One system of a ragged batch: a right-hand side with its own (float) matrix, size and
 // preconditioner.  Vectors of the batch are laid out [system][ld], zero past n.
@@ -269,8 +292,13 @@ struct SolveArgs {
   void* ws = nullptr;    // optional fixed device workspace (else the context's, grown)
   size_t ws_bytes = 0;
   const SysCol* sys = nullptr;  // ragged batch: device array [nrhs], one system per column
+  bool timed = true;             // record the solve's device timings (events of the context)
 };
 int pcg_solve(Ctx* c, const SolveArgs& a);
+// pcg_cluster.cu: the whole solve in one launch, one cluster per right-hand side
+// (CPM_EINVAL when the context does not fit it)
+int pcg_solve_cluster(Ctx* c, const SolveArgs& a);
+int cluster_solve_max_atoms();
 int apply_E(Ctx* c, int nrhs, const double* p, double* q);  // device arrays [nrhs][n]
 void launch_neutralize(double* q, int nrhs, int n, const double* d, const double* qsol,
                        cudaStream_t s);
@@ -280,6 +308,7 @@ void launch_neutralize_ragged(double* q, int count, int64_t ld, const SysCol* sy
 
 // dc.cu
 int build_dc_preconditioner(Ctx* c);
+int build_sparse_inverse(Ctx* c);  // PCG-Normal / PCG-Full
 int copy_precond(Ctx* c, int64_t* off, int* idx, double* val);
 int apply_p_gap(Ctx* c);
 int device_sum(Ctx* c, const double* v, int64_t len, double* out);

@@ -28,7 +28,8 @@ __device__ __forceinline__ double dist2(const double* a, const double* b, double
   return dx * dx + dy * dy + dz * dz;
 }
 
-// One warp per atom: count (fill == 0) or list (fill == 1) its neighbours in index order.
+// One warp per atom: count (fill == 0) or list (fill == 1) its neighbours in index order
+// (r <= r_cut, or r < r_cut with strict).
 // The candidates of a block are staged as float positions; the float minimum-image
 // distance decides every pair outside a band of +-0.01 A^2 around r_cut^2 (float
 // positions of a box below 1e4 A are off by < 1e-3 A, so the band is ample), and the
@@ -39,7 +40,7 @@ constexpr int kNbrStage = 1024;
 __global__ void __launch_bounds__(kNbrWarps * 32)
 k_neighbours(const double* __restrict__ xyz, int n, double lx, double ly, double lz,
              double rc2, int* __restrict__ cnt, const int64_t* __restrict__ off,
-             int* __restrict__ idx, int fill) {
+             int* __restrict__ idx, int fill, int strict = 0) {
   __shared__ float4 sp[kNbrStage];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = blockIdx.x * kNbrWarps + warp;
@@ -73,7 +74,10 @@ k_neighbours(const double* __restrict__ xyz, int n, double lx, double ly, double
         dz -= Lz * rintf(dz * iz);
         const float r2 = dx * dx + dy * dy + dz * dz;
         if (r2 < lo2) in = true;
-        else if (r2 <= hi2) in = dist2(xyz + 3 * t, xyz + 3 * j, lx, ly, lz) <= rc2;
+        else if (r2 <= hi2) {
+          const double d2 = dist2(xyz + 3 * t, xyz + 3 * j, lx, ly, lz);
+          in = strict ? d2 < rc2 : d2 <= rc2;
+        }
       }
       const unsigned m = __ballot_sync(0xffffffffu, in);
       if (fill && in) idx[off[t] + c + __popc(m & ((1u << lane) - 1u))] = j;
@@ -413,6 +417,87 @@ int build_dc_preconditioner(Ctx* c) {
   if (st) return st;
   if (hs) return set_err(c, CPM_EINVAL, "a PCG-DC local matrix is singular");
   return CPM_OK;
+}
+
+// P[j][tau] = (E^-1)_{j tau} on the pattern, from the columns E^-1 e_tau (column-major,
+// X[tau * n + j]); one block per row j.
+__global__ void k_gather_inverse(int n, const int64_t* __restrict__ off,
+                                 const int* __restrict__ idx, const double* __restrict__ X,
+                                 double* __restrict__ prow) {
+  const int j = blockIdx.x;
+  for (int64_t e = off[j] + threadIdx.x; e < off[j + 1]; e += blockDim.x)
+    prow[e] = X[(int64_t)idx[e] * n + j];
+}
+
+// PCG-Normal / PCG-Full (Sec. III B 2, Fig. 6a): the pattern of the pairs within the
+// cutoff (minimum image; r < rcut_dc for Normal, r <= rcut_real for Full) and the entries
+// of E^-1 on it, from the n columns E^-1 e_j solved by the context's PCG with the Jacobi
+// preconditioner to 1e-10.  No p_gap fill.  n <= CPM_SMATRIX_MAX_ATOMS (two n x n FP64
+// work arrays).
+int build_sparse_inverse(Ctx* c) {
+  const int n = c->n;
+  const double* L = c->p.box;
+  const bool full = c->p.precond == CPM_PRECOND_FULL;
+  const double rc = full ? c->p.rcut_real : c->p.rcut_dc;
+  if (n > CPM_SMATRIX_MAX_ATOMS)
+    return set_err(c, CPM_EINVAL, "PCG-Normal / PCG-Full: n above CPM_SMATRIX_MAX_ATOMS");
+  if (!(rc > 0.0)) return set_err(c, CPM_EINVAL, "PCG-Normal / PCG-Full: cutoff must be positive");
+  cudaStream_t s = c->stream;
+  Buf& cnt = c->dc_cnt;
+  int st;
+  if ((st = buf_reserve(c, &cnt, (size_t)n * sizeof(int)))) return st;
+  const int blocks = (n + kNbrWarps - 1) / kNbrWarps;
+  (k_neighbours<<<blocks, kNbrWarps * 32, 0, s>>>((const double*)c->xyz.ptr, n, L[0], L[1],
+                                                   L[2], rc * rc, (int*)cnt.ptr, nullptr,
+                                                   nullptr, 0, full ? 0 : 1), note_launch());
+  std::vector<int> hc(n);
+  st = cuda_check(c, cudaMemcpyAsync(hc.data(), cnt.ptr, n * sizeof(int),
+                                     cudaMemcpyDeviceToHost, s), "pattern counts");
+  if (!st) st = cuda_check(c, cudaStreamSynchronize(s), "pattern counts sync");
+  if (st) return st;
+  std::vector<int64_t> off(n + 1, 0);
+  for (int i = 0; i < n; ++i) off[i + 1] = off[i] + hc[i];
+  c->nnz = off[n];
+  c->pgap = 0.0;
+  if ((st = buf_reserve(c, &c->nbr_off, (n + 1) * sizeof(int64_t))) ||
+      (st = buf_reserve(c, &c->nbr_idx, c->nnz * sizeof(int))) ||
+      (st = buf_reserve(c, &c->prow, c->nnz * sizeof(double))))
+    return st;
+  st = cuda_check(c, cudaMemcpyAsync(c->nbr_off.ptr, off.data(), (n + 1) * sizeof(int64_t),
+                                     cudaMemcpyHostToDevice, s), "pattern offsets");
+  if (st) return st;
+  (k_neighbours<<<blocks, kNbrWarps * 32, 0, s>>>((const double*)c->xyz.ptr, n, L[0], L[1],
+                                                   L[2], rc * rc, nullptr,
+                                                   (const int64_t*)c->nbr_off.ptr,
+                                                   (int*)c->nbr_idx.ptr, 1, full ? 0 : 1),
+   note_launch());
+  // the columns of E^-1: one PCG over the n identity columns, Jacobi-preconditioned
+  Buf ident, cols;
+  const size_t bytes = (size_t)n * n * sizeof(double);
+  if ((st = buf_alloc(c, &ident, bytes))) return st;
+  if ((st = buf_alloc(c, &cols, bytes))) {
+    buf_free(c, &ident);
+    return st;
+  }
+  launch_identity((double*)ident.ptr, n, s);
+  std::vector<int> it(n);
+  std::vector<double> rr(n);
+  SolveArgs a{n, (const double*)ident.ptr, 1.0, (double*)cols.ptr, false, 1e-10, 20000,
+              it.data(), rr.data()};
+  const int saved = c->p.precond;
+  c->p.precond = CPM_PRECOND_JACOBI;
+  st = pcg_solve(c, a);
+  c->p.precond = saved;
+  if (!st) {
+    (k_gather_inverse<<<n, 128, 0, s>>>(n, (const int64_t*)c->nbr_off.ptr,
+                                        (const int*)c->nbr_idx.ptr, (const double*)cols.ptr,
+                                        (double*)c->prow.ptr), note_launch());
+    st = cuda_check(c, cudaGetLastError(), "gather inverse");
+  }
+  if (!st) st = cuda_check(c, cudaStreamSynchronize(s), "sparse inverse sync");
+  buf_free(c, &ident);
+  buf_free(c, &cols);
+  return st;
 }
 
 __global__ void k_shift(double* __restrict__ v, int64_t len, double s) {

@@ -27,6 +27,8 @@ struct ColState {
   double relres;  // ||r|| / ||b||
   int iter;
   int done;       // 0 running, 1 converged, 2 breakdown
+  int restart;    // residual replacement reopened a converged column: p = z next
+  int pad_;
 };
 
 constexpr int kThreads = 256;
@@ -228,6 +230,153 @@ k_matvec_f32(const float* __restrict__ E, int64_t ldE, int n, const float* __res
 #pragma unroll
     for (int i = 0; i < RBB; ++i) s += spq[i * NR + t];
     pq_part[(int64_t)blockIdx.x * nrhs + c0 + t] = s;
+  }
+}
+
+// The inner matvec of a many-column solve: q[c] = E p_c for the kFastCols columns of one
+// column group at once, so E is streamed from HBM once per iteration for all of them.
+// Products and partial sums are plain float (each lane sums one 1/32 share of the row);
+// lanes combine in FP64.  That is ~1e-6 of the row's partial sums, not the ~1e-14 of
+// k_matvec_f32: the solver uses it only between residual replacements, which recompute
+// b - E x with k_matvec_f32 (pcg_solve).  A block owns 64 rows (8 warps x 8 rows); stages
+// of E [64][128] and of the group's directions (xt[j][16] in global memory, four 16-byte
+// chunks per column, stored chunk-major in shared memory) go to shared memory by
+// cp.async, four stages in flight.  Lane l takes columns l, l + 32, l + 64, l + 96 of a
+// stage: its E values and its directions' chunks are consecutive across the warp, so
+// every shared-memory load is free of bank conflicts.
+constexpr int kFastCols = 16;
+constexpr int kFastRows = 64;
+constexpr int kFastK = 128;
+constexpr int kFastStages = 4;
+constexpr int kFastEBytes = kFastRows * kFastK * 4;    // 32 KB
+constexpr int kFastXBytes = kFastK * kFastCols * 4;    // 8 KB
+constexpr int kFastStageBytes = kFastEBytes + kFastXBytes;
+constexpr int kFastSmem = kFastStages * kFastStageBytes;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_matvec_fast(const float* __restrict__ E, int64_t ldE, int n, const float* __restrict__ xt,
+              const double* __restrict__ p64, int64_t ldv, int g0, int nrhs,
+              double* __restrict__ q, double* __restrict__ pq_part,
+              const ColState* __restrict__ st) {
+  extern __shared__ __align__(16) uint8_t fsm[];
+  const int grp = g0 + blockIdx.y;  // column group: columns 16 grp ..
+  const int c0 = grp * kFastCols;
+  const int ncol = min(kFastCols, nrhs - c0);
+  if (st) {  // a group with every column converged is not multiplied (uniform per block)
+    bool live = false;
+    for (int r = 0; r < ncol; ++r) live |= st[c0 + r].done == 0;
+    if (!live) {
+      if (threadIdx.x < ncol) pq_part[(int64_t)blockIdx.x * nrhs + c0 + threadIdx.x] = 0.0;
+      return;
+    }
+  }
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int row0 = blockIdx.x * kFastRows;
+  const float* xg = xt + (int64_t)grp * ldv * kFastCols;
+  const int nk = (int)(ldE / kFastK);
+  // stage s: E rows row0 .. +63 (clamped to n - 1), columns k0 .. k0 + 127; directions of
+  // those columns, 16-byte chunk v of column j at chunk position (v + (j >> 1)) & 3
+  auto load_stage = [&](int kt, int slot) {
+    uint8_t* base = fsm + slot * kFastStageBytes;
+    const int64_t k0 = (int64_t)kt * kFastK;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {  // 2,048 16-byte chunks of E
+      const int ch = tid + u * kThreads;
+      const int r = ch >> 5, cc = (ch & 31) * 4;
+      const int row = min(row0 + r, n - 1);
+      cp_async16(base + (r * kFastK + cc) * 4, E + (int64_t)row * ldE + k0 + cc);
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {  // 512 16-byte chunks of the directions: chunk v of
+      const int ch = tid + u * kThreads;  // column j at [v][j]
+      const int j = ch >> 2, v = ch & 3;
+      cp_async16(base + kFastEBytes + (v * kFastK + j) * 16, xg + (k0 + j) * kFastCols + v * 4);
+    }
+  };
+  float acc[8][kFastCols];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int cc = 0; cc < kFastCols; ++cc) acc[i][cc] = 0.f;
+#pragma unroll
+  for (int s = 0; s < kFastStages - 1; ++s) {
+    if (s < nk) load_stage(s, s);
+    cp_async_commit();
+  }
+  for (int kt = 0; kt < nk; ++kt) {
+    cp_async_wait<kFastStages - 2>();
+    __syncthreads();  // stage kt has landed for every thread; stage kt - 1 is free
+    if (kt + kFastStages - 1 < nk) load_stage(kt + kFastStages - 1, (kt + kFastStages - 1) % kFastStages);
+    cp_async_commit();
+    const uint8_t* base = fsm + (kt % kFastStages) * kFastStageBytes;
+    const float* es = reinterpret_cast<const float*>(base) + (warp * 8) * kFastK + lane;
+    const float4* xs = reinterpret_cast<const float4*>(base + kFastEBytes) + lane;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {  // column j = lane + 32 w
+      float xv[kFastCols], ev[8];
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+        *reinterpret_cast<float4*>(xv + 4 * v) = xs[v * kFastK + 32 * w];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) ev[i] = es[i * kFastK + 32 * w];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int cc = 0; cc < kFastCols; ++cc) acc[i][cc] = fmaf(ev[i], xv[cc], acc[i][cc]);
+    }
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  // lanes combine in FP64 through shared memory (the stage ring is free now): warp w's
+  // partials as buf[e][lane] with e = 16 i + cc (33-float rows: conflict-free both ways),
+  // then lane l sums entries e = l, l + 32, l + 64, l + 96 over the 32 lanes: column
+  // cc = l & 15 of rows i = (l >> 4) + 2 m
+  float* buf = reinterpret_cast<float*>(fsm) + warp * (8 * kFastCols * 33);
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int cc = 0; cc < kFastCols; ++cc) buf[(i * kFastCols + cc) * 33 + lane] = acc[i][cc];
+  __syncwarp();
+  double* spq = reinterpret_cast<double*>(fsm + 8 * 8 * kFastCols * 33 * 4);  // [8][16]
+  double pq = 0.0;
+  {
+    const int cc = lane & 15;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int e = lane + 32 * m, i = e / kFastCols;
+      double v = 0.0;
+      for (int k = 0; k < 32; ++k) v += (double)buf[e * 33 + k];
+      const int row = row0 + warp * 8 + i;
+      if (row < n && cc < ncol) {
+        const int64_t o = (int64_t)(c0 + cc) * ldv + row;
+        q[o] = v;
+        pq += v * p64[o];
+      }
+    }
+  }
+  // sum the lanes of one column (lanes cc and cc + 16), then the warps
+  pq += __shfl_xor_sync(0xffffffffu, pq, 16);
+  if (lane < kFastCols) spq[warp * kFastCols + lane] = pq;
+  __syncthreads();
+  if (tid < ncol) {
+    double sum = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) sum += spq[w * kFastCols + tid];
+    pq_part[(int64_t)blockIdx.x * nrhs + c0 + tid] = sum;
   }
 }
 
@@ -464,22 +613,152 @@ __global__ void k_beta(const double* __restrict__ dots, int nparts, int nrhs, do
 
 // p = z + beta p, and the matvec's copy: the value itself in FP64 storage, a float
 // pair hi + lo (plo != nullptr) in float storage.
+// first = 2: only the columns whose residual replacement reopened them (restart flag),
+// which start again from p = z.  xt (float storage, many-column solves): the directions
+// again, transposed per group of 16 columns, [group][row][16], for k_matvec_fast.
 template <typename T>
 __global__ void k_p_update(int n, int64_t ldv, int nrhs, const ColState* __restrict__ st,
                            const double* __restrict__ z, double* __restrict__ p,
-                           T* __restrict__ pv, T* __restrict__ plo, int first) {
+                           T* __restrict__ pv, T* __restrict__ plo, int first,
+                           float* __restrict__ xt = nullptr) {
   {
     const int col = blockIdx.y;
-    if (!first && st[col].done) return;
+    if (first == 2 && !st[col].restart) return;
+    if (first == 0 && st[col].done) return;
     const double bta = first ? 0.0 : st[col].beta;
     const int64_t o = (int64_t)col * ldv;
+    float* xc = xt ? xt + ((int64_t)(col / kFastCols) * ldv * kFastCols + col % kFastCols)
+                   : nullptr;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
       const double v = z[o + i] + bta * p[o + i];
       p[o + i] = v;
       const T hi = (T)v;
       pv[o + i] = hi;
       if (plo) plo[o + i] = (T)(v - (double)hi);
+      if (xc) xc[(int64_t)i * kFastCols] = (float)v;
     }
+  }
+}
+
+// v = hi + lo as float pairs (the exact matvec's input), elementwise.
+__global__ void k_split(const double* __restrict__ v, int64_t len, float* __restrict__ hi,
+                        float* __restrict__ lo) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float h = (float)v[i];
+    hi[i] = h;
+    lo[i] = (float)(v[i] - (double)h);
+  }
+}
+
+// The difference x - x_a of every column, in the transposed group layout of
+// k_matvec_fast ([group][row][16]); rows past n stay zero (the workspace is zeroed).
+__global__ void k_diff_t(int n, int64_t ldv, const double* __restrict__ x,
+                         const double* __restrict__ xa, float* __restrict__ xdt) {
+  const int col = blockIdx.y;
+  const int64_t o = (int64_t)col * ldv;
+  float* xc = xdt + ((int64_t)(col / kFastCols) * ldv * kFastCols + col % kFastCols);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    xc[(int64_t)i * kFastCols] = (float)(x[o + i] - xa[o + i]);
+}
+
+// Columns that broke down in the fast iteration count as converged for the next
+// replacement, which recomputes their residual exactly and reopens them (restart).
+__global__ void k_reopen_broken(ColState* __restrict__ st, int nrhs) {
+  for (int col = threadIdx.x; col < nrhs; col += blockDim.x)
+    if (st[col].done == 2) st[col].done = 1;
+}
+
+// Residual replacement from the anchor: r = r_a - q with q = E (x - x_a) from the fast
+// matvec; otherwise as k_replace_r.
+__global__ void __launch_bounds__(kThreads)
+k_anchor_r(int n, int64_t ldv, int nrhs, const ColState* __restrict__ st,
+           const double* __restrict__ ra, const double* __restrict__ q, double* __restrict__ r,
+           double* __restrict__ z, const double* __restrict__ inv_diag, int pre,
+           double* __restrict__ dots) {
+  __shared__ double sm[32 * 4];
+  const int col = blockIdx.y;
+  if (st[col].done == 2) return;
+  double v[4] = {0, 0, 0, 0};
+  const int64_t o = (int64_t)col * ldv;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double ri = ra[o + i] - q[o + i];
+    r[o + i] = ri;
+    if (pre != CPM_PRECOND_DC) {
+      const double zi = pre == CPM_PRECOND_JACOBI ? ri * inv_diag[i] : ri;
+      z[o + i] = zi;
+      v[0] += ri * zi;
+    }
+    v[2] += ri * ri;
+    v[3] += ri;
+  }
+  block_sum<4>(v, sm);
+  if (threadIdx.x == 0)
+    for (int t = 0; t < 4; ++t) dots[((int64_t)blockIdx.x * nrhs + col) * 4 + t] = v[t];
+}
+
+// Residual replacement, first part: r = b bscale - q with q = E x from the exact matvec;
+// Jacobi / none also form z; partial dots [r^T z, -, r^T r, sum r] as k_update writes
+// them (PCG-DC forms z in k_dc_apply next).  Columns that broke down are left alone.
+__global__ void __launch_bounds__(kThreads)
+k_replace_r(int n, int64_t ldv, int nrhs, const ColState* __restrict__ st,
+            const double* __restrict__ b, double bscale, const double* __restrict__ q,
+            double* __restrict__ r, double* __restrict__ z, const double* __restrict__ inv_diag,
+            int pre, double* __restrict__ dots) {
+  __shared__ double sm[32 * 4];
+  const int col = blockIdx.y;
+  if (st[col].done == 2) return;  // uniform per block; its dots are not read
+  double v[4] = {0, 0, 0, 0};
+  const int64_t o = (int64_t)col * ldv;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double ri = b[(int64_t)col * n + i] * bscale - q[o + i];
+    r[o + i] = ri;
+    if (pre != CPM_PRECOND_DC) {
+      const double zi = pre == CPM_PRECOND_JACOBI ? ri * inv_diag[i] : ri;
+      z[o + i] = zi;
+      v[0] += ri * zi;
+    }
+    v[2] += ri * ri;
+    v[3] += ri;
+  }
+  block_sum<4>(v, sm);
+  if (threadIdx.x == 0)
+    for (int t = 0; t < 4; ++t) dots[((int64_t)blockIdx.x * nrhs + col) * 4 + t] = v[t];
+}
+
+// Residual replacement, second part: the true relative residual decides convergence; a
+// column that had converged on its recursive residual but not on the true one runs again
+// from p = z (restart flag); every running column continues with the replaced r, z and
+// r^T z and its direction unchanged.
+__global__ void k_replace_state(const double* __restrict__ dots, int nparts, int nrhs,
+                                double tol, ColState* __restrict__ st) {
+  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (col >= nrhs) return;
+  double s0 = 0.0, s2 = 0.0;
+  for (int b = lane; b < nparts; b += 32) {
+    s0 += dots[((int64_t)b * nrhs + col) * 4 + 0];
+    s2 += dots[((int64_t)b * nrhs + col) * 4 + 2];
+  }
+  s0 = warp_sum(s0);
+  s2 = warp_sum(s2);
+  if (lane == 0) {
+    ColState c = st[col];
+    if (c.done != 2) {
+      c.relres = c.bb > 0.0 ? sqrt(s2 / c.bb) : 0.0;
+      c.rz = s0;
+      if (!isfinite(c.relres)) {
+        c.done = 2;
+      } else if (c.relres <= tol) {
+        c.done = 1;
+      } else {
+        c.restart = c.done == 1 ? 1 : 0;
+        c.done = 0;
+        if (!(c.rz != 0.0)) c.done = 2;
+      }
+      if (c.done) c.restart = 0;
+    }
+    st[col] = c;
   }
 }
 
@@ -541,6 +820,8 @@ __global__ void k_init_state(const double* __restrict__ dots, int nparts, int nr
     c.beta = 0.0;
     c.iter = 0;
     c.done = 0;
+    c.restart = 0;
+    c.pad_ = 0;
     if (c.bb == 0.0) {
       c.relres = 0.0;
       c.done = 1;
@@ -680,7 +961,56 @@ void launch_matvec<float>(const Ctx* c, const void* pv, const void* plo, const d
 
 }  // namespace
 
+namespace {
+int pcg_solve_kernels(Ctx* c, const SolveArgs& a);
+}  // namespace
+
+// The solve: the cluster-resident kernel (small electrodes) or the host-driven kernels.
+// With solver_path 0 the choice is the context's online autotuner's: for each bucket of
+// right-hand-side counts, the first eligible solve runs on the cluster path and the next
+// on the host-driven one, each timed per iteration on the device; later solves of that
+// bucket take the faster.  Both give the same iteration on the same matrix.
 int pcg_solve(Ctx* c, const SolveArgs& a) {
+  const bool eligible = !c->fp64() && !a.sys && !a.ws && c->n <= cluster_solve_max_atoms() &&
+                        c->p.solver_path != 1;
+  int bucket = 0;
+  while (bucket < 7 && (2 << bucket) <= a.nrhs) ++bucket;
+  int path = 1;
+  if (eligible) {
+    if (c->p.solver_path == 2) path = 2;
+    else if (c->tune_path[bucket]) path = c->tune_path[bucket];
+    else path = c->tune_cost[bucket][1] > 0.f ? 1 : 2;  // try the cluster path first
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const bool tuning = eligible && c->p.solver_path == 0 && !c->tune_path[bucket];
+  if (tuning) {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, c->stream);
+  }
+  int st = path == 2 ? pcg_solve_cluster(c, a) : pcg_solve_kernels(c, a);
+  c->last_solve_path = path;
+  if (tuning) {
+    cudaEventRecord(e1, c->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    int iters = 1;
+    for (int col = 0; a.iters && col < a.nrhs; ++col) iters = std::max(iters, a.iters[col]);
+    if (st == CPM_OK || st == CPM_ENOCONV) {
+      c->tune_cost[bucket][path - 1] = ms / iters;
+      if (c->tune_cost[bucket][0] > 0.f && c->tune_cost[bucket][1] > 0.f)
+        c->tune_path[bucket] = c->tune_cost[bucket][1] < c->tune_cost[bucket][0] ? 2 : 1;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  return st;
+}
+
+namespace {
+
+int pcg_solve_kernels(Ctx* c, const SolveArgs& a) {
   const int n = c->n, nrhs = a.nrhs;
   const int64_t ldv = c->ldE;
   const int sms = sm_count(c->device);
@@ -689,11 +1019,28 @@ int pcg_solve(Ctx* c, const SolveArgs& a) {
   const dim3 g2(ge, nrhs);
   // p^T q partials per column: one per matvec block (the ragged kernel takes kMvRows rows
   // per block)
-  const int gm = a.sys ? (n + kMvRows - 1) / kMvRows : matvec_parts(c);
-  const int pre = c->p.precond;
+  const int gm_exact = a.sys ? (n + kMvRows - 1) / kMvRows : matvec_parts(c);
+  // PCG-Normal and PCG-Full apply their P in the row form PCG-DC's takes
+  const int pre = c->p.precond >= CPM_PRECOND_DC ? CPM_PRECOND_DC : c->p.precond;
   const bool f64 = c->fp64();
+  // many columns of one float E: the inner iterations stream E once for every group of
+  // 16 columns (k_matvec_fast, float sums), and a replaced residual takes the place of the
+  // recursive one whenever a column's residual has fallen 100-fold since the last
+  // replacement or it reports convergence; convergence is declared on replaced residuals
+  // only.  A replacement is b - E x through the exact matvec (an anchor), or, once every
+  // running column's anchor is within 1e-2 of its b, r_a - E (x - x_a) through the fast
+  // matvec: the error of the fast sums then scales with the anchor's residual, not with
+  // E x.  A breakdown in the fast iteration (its float sums can turn p^T E p negative near
+  // a tight tolerance) switches the solve to the exact matvec for good, and the broken
+  // columns start again from an exact residual.
+  const bool fast0 = !f64 && !a.sys && nrhs >= 2 && c->p.matvec_mode == 0;
+  bool fast = fast0;
+  const int gm_fast = (n + kFastRows - 1) / kFastRows;
+  int gm = fast ? gm_fast : gm_exact;
+  const int groups = (nrhs + kFastCols - 1) / kFastCols;
   const size_t vbytes = (size_t)nrhs * ldv * sizeof(double);
-  // layout: x r z p q (double) | pv (storage type) | pq_part | dots | dots_dc | states
+  // layout: x r z p q (double) | pv (storage type) | [fast: xt | x hi | x lo] | pq_part |
+  //         dots | dots_dc | states
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
@@ -702,7 +1049,11 @@ int pcg_solve(Ctx* c, const SolveArgs& a) {
   };
   const size_t ox = take(vbytes), orr = take(vbytes), oz = take(vbytes), op = take(vbytes),
                oq = take(vbytes), opv = take((f64 ? 1 : 2) * (size_t)nrhs * ldv * c->esz()),
-               opq = take((size_t)gm * nrhs * sizeof(double)),
+               oxt = fast ? take((size_t)groups * kFastCols * ldv * sizeof(float)) : 0,
+               oxs = fast ? take(2 * (size_t)nrhs * ldv * sizeof(float)) : 0,
+               oxd = fast ? take((size_t)groups * kFastCols * ldv * sizeof(float)) : 0,
+               oxa = fast ? take(vbytes) : 0, ora = fast ? take(vbytes) : 0,
+               opq = take((size_t)std::max(gm_fast, gm_exact) * nrhs * sizeof(double)),
                odt = take((size_t)ge * nrhs * 4 * sizeof(double)),
                odc = take((size_t)ge * nrhs * 4 * sizeof(double)),
                ost = take(2 * (size_t)nrhs * sizeof(ColState));
@@ -730,10 +1081,40 @@ int pcg_solve(Ctx* c, const SolveArgs& a) {
   double* dots = (double*)(base + odt);
   double* dots_dc = (double*)(base + odc);
   ColState* st = (ColState*)(base + ost);
+  float* xt = fast ? (float*)(base + oxt) : nullptr;
+  float* xhi = fast ? (float*)(base + oxs) : nullptr;
+  float* xlo = fast ? xhi + (size_t)nrhs * ldv : nullptr;
+  float* xdt = fast ? (float*)(base + oxd) : nullptr;  // x - x_a, transposed per group
+  double* xa = fast ? (double*)(base + oxa) : nullptr;  // the anchor's x and r
+  double* ra = fast ? (double*)(base + ora) : nullptr;
   cudaStream_t s = c->stream;
+  if (fast && cuda_check(c, cudaFuncSetAttribute(k_matvec_fast,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 kFastSmem), "fast matvec smem"))
+    return CPM_ECUDA;
+  // device timing of the solve's parts: event pairs from the context's pool
+  size_t nev = 0;
+  auto ev = [&]() -> cudaEvent_t {
+    if (!a.timed) return nullptr;
+    if (nev == c->ev_pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      c->ev_pool.push_back(e);
+    }
+    cudaEvent_t e = c->ev_pool[nev++];
+    cudaEventRecord(e, c->stream);
+    return e;
+  };
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> t_mv, t_rep;
+  const cudaEvent_t t_begin = ev();
   // cur: the column states (converged columns are skipped), nullptr before they exist
   auto matvec = [&](const ColState* cur) {
-    if (f64) {
+    if (fast) {  // the inner matvec of a many-column solve
+      for (int g0 = 0; g0 < groups; g0 += 65535)
+        (k_matvec_fast<<<dim3(gm_fast, std::min(groups - g0, 65535)), kThreads, kFastSmem, s>>>(
+             (const float*)c->E.ptr, c->ldE, n, xt, p, ldv, g0, nrhs, q, pq_part, cur),
+         note_launch());
+    } else if (f64) {
       launch_matvec<double>(c, pv, nullptr, p, ldv, nrhs, q, pq_part, gm, cur);
     } else if (a.sys) {  // ragged batch: one system per column
       (k_matvec_ragged<<<dim3(gm, nrhs), kThreads, 0, s>>>(a.sys, (const float*)pv, plo, p, ldv,
@@ -748,11 +1129,12 @@ int pcg_solve(Ctx* c, const SolveArgs& a) {
   const double* inv_diag = c->diag.ptr ? (const double*)c->diag.ptr + n : nullptr;
   // initial guess: q = E x0 through the same (hi + lo) matvec
   const double* q2 = nullptr;
-  if (a.use_guess) {
+  if (a.use_guess) {  // the exact matvec, also in a many-column solve
     if (cuda_check(c, copy_cols(x, ldv, a.x, n, n, nrhs, s), "copy guess")) return CPM_ECUDA;
     if (f64) (k_p_update<double><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, st, x, p, (double*)pv, nullptr, 1), note_launch());
     else (k_p_update<float><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, st, x, p, (float*)pv, plo, 1), note_launch());
-    matvec(nullptr);
+    if (fast) launch_matvec<float>(c, pv, plo, p, ldv, nrhs, q, pq_part, gm_exact, nullptr);
+    else matvec(nullptr);
   }
   (k_init_r<<<g2, kThreads, 0, s>>>(n, ldv, nrhs, a.b, a.bscale, q, q2, a.use_guess ? 1 : 0, r, x, z,
                                    inv_diag, pre, dots, a.sys), note_launch());
@@ -766,7 +1148,7 @@ int pcg_solve(Ctx* c, const SolveArgs& a) {
     (k_init_rz_dc<<<gcol, wb * 32, 0, s>>>(dots_dc, ge, nrhs, st), note_launch());
   }
   if (f64) (k_p_update<double><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, st, z, p, (double*)pv, nullptr, 1), note_launch());
-  else (k_p_update<float><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, st, z, p, (float*)pv, plo, 1), note_launch());
+  else (k_p_update<float><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, st, z, p, (float*)pv, plo, 1, xt), note_launch());
   if (cuda_check(c, cudaGetLastError(), "pcg init")) return CPM_ECUDA;
 
   std::vector<ColState> host(nrhs);
@@ -774,6 +1156,10 @@ int pcg_solve(Ctx* c, const SolveArgs& a) {
   int it = 0;
   bool all_done = false;
   const int check_every = 4;
+  // many-column solves: a column counts as converged once a replaced (true) residual says
+  // so (verified); level is its relative residual at its last replacement
+  std::vector<char> verified(nrhs, 0);
+  std::vector<double> level(nrhs, 1.0);
   // state at the start of iteration `it` lives in st[(it & 1) * nrhs]
   auto poll = [&](int k) -> int {
     ColState* cur = st + (size_t)(k & 1) * nrhs;
@@ -783,14 +1169,76 @@ int pcg_solve(Ctx* c, const SolveArgs& a) {
       return CPM_ECUDA;
     if (cuda_check(c, cudaStreamSynchronize(s), "poll sync")) return CPM_ECUDA;
     all_done = true;
-    for (auto& h : host) all_done &= h.done != 0;
+    for (int col = 0; col < nrhs; ++col)
+      all_done &= host[col].done == 2 || (host[col].done == 1 && (!fast || verified[col]));
     return CPM_OK;
   };
+  // residual replacement (many-column solves): r = b - E x through the exact matvec for
+  // every column, then z, r^T z and the convergence test on the true residual
+  const int64_t vlen = (int64_t)nrhs * ldv;
+  std::vector<double> anchor_level(nrhs, 1.0);  // relres at each column's anchor
+  auto replace = [&](int k) -> int {
+    ColState* cur = st + (size_t)(k & 1) * nrhs;
+    const cudaEvent_t e0 = ev();
+    // the fast sums' error (~1e-5 of |E (x - x_a)|, i.e. of the anchor's residual) must
+    // stay a tenth of the tolerance: anchors within min(1e-2, 1e4 tol) of b
+    bool from_anchor = fast;
+    const double near = std::min(1e-2, 1e4 * a.tol);
+    for (int col = 0; col < nrhs; ++col)
+      if (host[col].done != 2 && anchor_level[col] > near) from_anchor = false;
+    const int gvec = (int)std::min<int64_t>((vlen + kThreads - 1) / kThreads, 4 * sms);
+    if (from_anchor) {  // r = r_a - E_fast (x - x_a)
+      (k_diff_t<<<g2, kThreads, 0, s>>>(n, ldv, x, xa, xdt), note_launch());
+      for (int g0 = 0; g0 < groups; g0 += 65535)
+        (k_matvec_fast<<<dim3(gm_fast, std::min(groups - g0, 65535)), kThreads, kFastSmem, s>>>(
+             (const float*)c->E.ptr, c->ldE, n, xdt, x, ldv, g0, nrhs, q, pq_part, nullptr),
+         note_launch());
+      (k_anchor_r<<<g2, kThreads, 0, s>>>(n, ldv, nrhs, cur, ra, q, r, z, inv_diag, pre, dots),
+       note_launch());
+    } else {  // r = b - E x, exactly; the new anchor
+      (k_split<<<gvec, kThreads, 0, s>>>(x, vlen, xhi, xlo), note_launch());
+      launch_matvec<float>(c, xhi, xlo, x, ldv, nrhs, q, pq_part, gm_exact, nullptr);
+      (k_replace_r<<<g2, kThreads, 0, s>>>(n, ldv, nrhs, cur, a.b, a.bscale, q, r, z, inv_diag,
+                                           pre, dots), note_launch());
+      if (cuda_check(c, cudaMemcpyAsync(xa, x, vbytes, cudaMemcpyDeviceToDevice, s), "anchor x") ||
+          cuda_check(c, cudaMemcpyAsync(ra, r, vbytes, cudaMemcpyDeviceToDevice, s), "anchor r"))
+        return CPM_ECUDA;
+    }
+    if (pre == CPM_PRECOND_DC)
+      (k_dc_apply<<<g2, kThreads, 0, s>>>(n, ldv, nrhs, cur, (const int64_t*)c->nbr_off.ptr,
+                                         (const int*)c->nbr_idx.ptr, (const double*)c->prow.ptr,
+                                         c->pgap, r, z, dots, ge, dots, 1, nullptr),
+       note_launch());
+    (k_replace_state<<<gcol, wb * 32, 0, s>>>(dots, ge, nrhs, a.tol, cur), note_launch());
+    (k_p_update<float><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, cur, z, p, (float*)pv, plo, 2, xt),
+     note_launch());
+    t_rep.emplace_back(e0, ev());
+    if (cuda_check(c, cudaGetLastError(), "residual replacement")) return CPM_ECUDA;
+    if (int e = poll(k)) return e;
+    for (int col = 0; col < nrhs; ++col) {
+      level[col] = host[col].relres;
+      verified[col] = host[col].done == 1;
+      if (!from_anchor) anchor_level[col] = host[col].relres;
+    }
+    return poll(k);  // all_done with the verified flags
+  };
+  if ((rc = poll(0))) return rc;
+  for (int col = 0; col < nrhs; ++col) {
+    verified[col] = host[col].done == 1;  // exact r0
+    anchor_level[col] = host[col].relres;
+  }
+  if (fast && (cuda_check(c, cudaMemcpyAsync(xa, x, vbytes, cudaMemcpyDeviceToDevice, s),
+                          "anchor x") ||
+               cuda_check(c, cudaMemcpyAsync(ra, r, vbytes, cudaMemcpyDeviceToDevice, s),
+                          "anchor r")))
+    return CPM_ECUDA;
   if ((rc = poll(0))) return rc;
   while (!all_done && it < a.maxit) {
     ColState* cur = st + (size_t)(it & 1) * nrhs;
     ColState* nxt = st + (size_t)((it + 1) & 1) * nrhs;
+    const cudaEvent_t m0 = ev();
     matvec(cur);
+    t_mv.emplace_back(m0, ev());
     (k_alpha<<<gcol, wb * 32, 0, s>>>(pq_part, gm, nrhs, cur), note_launch());
     if (pre == CPM_PRECOND_DC) {
       (k_update<CPM_PRECOND_DC><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, cur, x, r, z, p, q,
@@ -808,16 +1256,42 @@ int pcg_solve(Ctx* c, const SolveArgs& a) {
     }
     (k_beta<<<gcol, wb * 32, 0, s>>>(dots, ge, nrhs, a.tol, flexible, cur, nxt), note_launch());
     if (f64) (k_p_update<double><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, nxt, z, p, (double*)pv, nullptr, 0), note_launch());
-    else (k_p_update<float><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, nxt, z, p, (float*)pv, plo, 0), note_launch());
+    else (k_p_update<float><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, nxt, z, p, (float*)pv, plo, 0, fast ? xt : nullptr), note_launch());
     ++it;
     if (it % check_every == 0 || it == a.maxit) {
       if (cuda_check(c, cudaGetLastError(), "pcg iteration")) return CPM_ECUDA;
       if ((rc = poll(it))) return rc;
+      bool broke = false;  // a column broke down in the fast iteration
+      for (int col = 0; fast && col < nrhs; ++col) broke |= host[col].done == 2;
+      if (fast0 && (!all_done || broke)) {
+        bool need = it == a.maxit;
+        for (int col = 0; col < nrhs; ++col) {
+          const ColState& h = host[col];
+          need |= (h.done == 1 && !verified[col]) || (h.done == 0 && h.relres <= 1e-2 * level[col]);
+        }
+        if (broke) {  // the exact matvec from here on; broken columns start again
+          fast = false;
+          gm = gm_exact;
+          (k_reopen_broken<<<1, 256, 0, s>>>(st + (size_t)(it & 1) * nrhs, nrhs), note_launch());
+          for (int col = 0; col < nrhs; ++col) anchor_level[col] = 1.0;
+          need = true;
+        }
+        if (need && (rc = replace(it))) return rc;
+      }
     }
   }
   if (!all_done && (rc = poll(it))) return rc;
   if (cuda_check(c, copy_cols(a.x, n, x, ldv, n, nrhs, s), "copy x")) return CPM_ECUDA;
+  const cudaEvent_t t_end = ev();
   if (cuda_check(c, cudaStreamSynchronize(s), "pcg end")) return CPM_ECUDA;
+  if (a.timed) {
+    float ms = 0;
+    cudaEventElapsedTime(&c->t_solve_ms, t_begin, t_end);
+    c->t_solve_mv_ms = c->t_solve_rep_ms = 0;
+    for (auto& e : t_mv) c->t_solve_mv_ms += (cudaEventElapsedTime(&ms, e.first, e.second), ms);
+    for (auto& e : t_rep) c->t_solve_rep_ms += (cudaEventElapsedTime(&ms, e.first, e.second), ms);
+    c->solve_replacements = (int)t_rep.size();
+  }
   int status = CPM_OK;
   for (int col = 0; col < nrhs; ++col) {
     if (a.iters) a.iters[col] = host[col].iter;
@@ -829,6 +1303,8 @@ int pcg_solve(Ctx* c, const SolveArgs& a) {
   if (status == CPM_ENOCONV) return set_err(c, status, "PCG reached maxit before tol");
   return CPM_OK;
 }
+
+}  // namespace
 
 // q = E_n p for nrhs columns (device arrays [nrhs][n]) through the solver's matvec; the
 // matvec launches alone are timed with events on the context's stream (t_matvec_ms).

@@ -266,28 +266,33 @@ k_bsol_kspace(const T* __restrict__ A, int n, int64_t lda, const T* __restrict__
 }
 
 // Streamed builds keep no A: b^sol_k[f][i] = sum_{k >= kh} sqrt(W_k) [cos(K.r_i) v_c +
-// sin(K.r_i) v_s] with the electrode phases formed on the fly (fixed point, sincos_turns)
-// and the terms summed in error-free float pairs; one thread per electrode atom, the
-// k-vectors of a chunk and their structure factors staged in shared memory.
-constexpr int kDirectChunk = 256;
+// sin(K.r_i) v_s] with the electrode phases formed on the fly (fixed point, sincos_table)
+// and the terms summed in error-free float pairs.  One thread per electrode atom and up to
+// kDirectFrames frames per block: each phasor is formed once and used for every frame of
+// the block; the k-vectors of a chunk and their structure factors are staged in shared
+// memory.
+constexpr int kDirectChunk = 128;
+constexpr int kDirectFrames = 16;
 
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 4)
 k_bsol_kspace_direct(const uint32_t* __restrict__ sfix, int n, const int* __restrict__ hkl,
                      const double* __restrict__ sqw, int mpad, int kh,
-                     const float4* __restrict__ turn, const float* __restrict__ v,
+                     const float4* __restrict__ turn, const float* __restrict__ v, int frames,
                      double* __restrict__ bsol) {
   __shared__ uint32_t sh[kDirectChunk][3];
-  __shared__ float sv[kDirectChunk][3];  // sqrt(W), v_cos, v_sin
-  const int f = blockIdx.y;
+  __shared__ float2 sv[kDirectChunk][kDirectFrames];  // sqrt(W) (v_cos, v_sin) per frame
+  const int f0 = blockIdx.y * kDirectFrames;
+  const int nf = min(kDirectFrames, frames - f0);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const float* vf = v + (size_t)f * 2 * mpad;
   uint32_t u0 = 0, u1 = 0, u2 = 0;
   if (i < n) {
     u0 = sfix[3 * i];
     u1 = sfix[3 * i + 1];
     u2 = sfix[3 * i + 2];
   }
-  float hi = 0.f, lo = 0.f;
+  float hi[kDirectFrames], lo[kDirectFrames];
+#pragma unroll
+  for (int f = 0; f < kDirectFrames; ++f) hi[f] = lo[f] = 0.f;
   for (int k0 = kh; k0 < mpad; k0 += kDirectChunk) {
     const int cnt = min(kDirectChunk, mpad - k0);
     __syncthreads();
@@ -296,33 +301,61 @@ k_bsol_kspace_direct(const uint32_t* __restrict__ sfix, int n, const int* __rest
       sh[t][0] = (uint32_t)hkl[3 * k];
       sh[t][1] = (uint32_t)hkl[3 * k + 1];
       sh[t][2] = (uint32_t)hkl[3 * k + 2];
+    }
+    for (int e = threadIdx.x; e < cnt * kDirectFrames; e += blockDim.x) {
+      const int t = e / kDirectFrames, f = e % kDirectFrames;
+      const int k = k0 + t;
       const size_t kcol = 128 * (size_t)(k >> 6) + (k & 63);
-      sv[t][0] = (float)sqw[k];
-      sv[t][1] = vf[kcol];
-      sv[t][2] = vf[kcol + 64];
+      const float w = (float)sqw[k];
+      float2 val = make_float2(0.f, 0.f);
+      if (f < nf) {
+        const float* vf = v + (size_t)(f0 + f) * 2 * mpad;
+        val = make_float2(w * vf[kcol], w * vf[kcol + 64]);
+      }
+      sv[t][f] = val;
     }
     __syncthreads();
     if (i >= n) continue;
     for (int t = 0; t < cnt; ++t) {
       float sn, cs;
       sincos_table(sh[t][0] * u0 + sh[t][1] * u1 + sh[t][2] * u2, turn, &sn, &cs);
-      const float term = sv[t][0] * fmaf(sn, sv[t][2], cs * sv[t][1]);
-      const float s2 = hi + term;
-      const float bb = s2 - hi;
-      lo += (hi - (s2 - bb)) + (term - bb);
-      hi = s2;
+#pragma unroll
+      for (int f = 0; f < kDirectFrames; ++f) {
+        const float2 vv = sv[t][f];
+        const float term = fmaf(sn, vv.y, cs * vv.x);
+        const float s2 = hi[f] + term;
+        const float bb = s2 - hi[f];
+        lo[f] += (hi[f] - (s2 - bb)) + (term - bb);
+        hi[f] = s2;
+      }
     }
   }
-  if (i < n) bsol[(size_t)f * n + i] = (double)hi + (double)lo;
+  if (i < n)
+#pragma unroll
+    for (int f = 0; f < kDirectFrames; ++f)
+      if (f < nf) bsol[(size_t)(f0 + f) * n + i] = (double)hi[f] + (double)lo[f];
 }
 
 // FP64 real-space sum of one electrode-ion pair over every image within r_c:
 // sum q_I [erfc(g r) - erfc(alpha_i r)] / r.
+// When every box edge exceeds 2 r_c only the nearest image can be in range; a pair beyond
+// r_split (where erfc(g r) / r < 1e-4 / A, and erfc(alpha r) underflows) then takes the
+// float erfc: about 4 ulp of a term below 1e-4, against the 1e-9 e/A that b^sol is held
+// to, summed in FP64.
 __device__ __forceinline__ double pair_images(const double* ri, double ai, const double* ion,
                                               const double* L, const double* invL,
                                               const bool* single, double rc, double rc2,
                                               double g) {
   double d[3] = {ri[0] - ion[0], ri[1] - ion[1], ri[2] - ion[2]};
+  if (single[0] && single[1] && single[2]) {
+    for (int u = 0; u < 3; ++u) d[u] -= L[u] * rint(d[u] * invL[u]);
+    const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (r2 >= rc2 || r2 == 0.0) return 0.0;
+    const double r = sqrt(r2);
+    double e = erfc(g * r);
+    if (ai * r < 6.0) e -= erfc(ai * r);
+    return ion[3] * e / r;
+  }
   int lo[3], hi[3];
   for (int u = 0; u < 3; ++u) {
     if (single[u]) {  // box edge above 2 rc: only the minimum image can be in range
@@ -476,6 +509,196 @@ k_bsol_real(const double* __restrict__ xyz, const double* __restrict__ alpha,
   if (i == 0 && qsol) qsol[f] = qs;
 }
 
+
+// ---- forces on the ions: F_I = -q_I d/dr_I sum_i q_i e_iI (Eq. S25 inside the Ewald
+// sums of Eq. 22 / 25, the paper's form with Eq. 39) ------------------------------------
+//
+// Reciprocal part: d/dr_I cos(K.(r_i - r_I)) = sin(K.(r_i - r_I)) K, so with the
+// electrode's charge-weighted structure factors (C_K, S_K) = sum_i q_i (cos, sin)(K.r_i),
+// grad_I = sum_K W_K [S_K cos(K.r_I) - C_K sin(K.r_I)] K.  v holds sqrt(W) (C, S) in the
+// operand's column layout (the ions' structure-factor kernel run over the electrode), so
+// the term is sqrt(W_K) (v_s cos - v_c sin).  The head k-vectors (heaviest) in FP64 from
+// FP64 phasors; the tail in float from the table phasors (about one ulp) summed in
+// error-free float pairs; the integer h, k, l multiply last: K = 2 pi (h/Lx, k/Ly, l/Lz).
+constexpr int kForceChunk = 256;
+
+__global__ void __launch_bounds__(128)
+k_force_kspace(const uint32_t* __restrict__ sion, int n_ion, const int* __restrict__ hkl,
+               const double* __restrict__ sqw, int mpad, int kh,
+               const float4* __restrict__ turn, const float* __restrict__ v,
+               const double* __restrict__ vhead, double lx, double ly, double lz,
+               double* __restrict__ grad) {
+  __shared__ int sk[kForceChunk][3];
+  __shared__ double sw[kForceChunk][3];  // sqrt(W), v_c, v_s (head: FP64; tail: floats)
+  const int f = blockIdx.y;
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t* u = sion + ((size_t)f * n_ion + (I < n_ion ? I : 0)) * 3;
+  const uint32_t u0 = u[0], u1 = u[1], u2 = u[2];
+  const float* vf = v + (size_t)f * 2 * mpad;
+  const double* vh = vhead + (size_t)f * 2 * (size_t)(kh > 0 ? kh : 1);
+  double g64[3] = {0.0, 0.0, 0.0};
+  float gh[3] = {0.f, 0.f, 0.f}, gl[3] = {0.f, 0.f, 0.f};
+  for (int k0 = 0; k0 < mpad; k0 += kForceChunk) {
+    const int cnt = min(kForceChunk, mpad - k0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+      const int k = k0 + t;
+      sk[t][0] = hkl[3 * k];
+      sk[t][1] = hkl[3 * k + 1];
+      sk[t][2] = hkl[3 * k + 2];
+      const size_t kcol = 128 * (size_t)(k >> 6) + (k & 63);
+      sw[t][0] = sqw[k];
+      if (k < kh) {
+        sw[t][1] = vh[kcol];
+        sw[t][2] = vh[kcol + 64];
+      } else {
+        sw[t][1] = (double)vf[kcol];
+        sw[t][2] = (double)vf[kcol + 64];
+      }
+    }
+    __syncthreads();
+    if (I >= n_ion) continue;
+    for (int t = 0; t < cnt; ++t) {
+      const uint32_t ph = (uint32_t)sk[t][0] * u0 + (uint32_t)sk[t][1] * u1 +
+                          (uint32_t)sk[t][2] * u2;
+      if (k0 + t < kh) {
+        double sn, cs;
+        sincospi((double)(int32_t)ph * 0x1p-31, &sn, &cs);
+        const double term = sw[t][0] * (sw[t][2] * cs - sw[t][1] * sn);
+        g64[0] += term * sk[t][0];
+        g64[1] += term * sk[t][1];
+        g64[2] += term * sk[t][2];
+      } else {
+        float sn, cs;
+        sincos_table(ph, turn, &sn, &cs);
+        const float term = (float)sw[t][0] * fmaf((float)sw[t][2], cs, -(float)sw[t][1] * sn);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const float x = term * (float)sk[t][d];  // h, k, l: small integers, exact
+          const float s2 = gh[d] + x;
+          const float bb = s2 - gh[d];
+          gl[d] += (gh[d] - (s2 - bb)) + (x - bb);
+          gh[d] = s2;
+        }
+      }
+    }
+  }
+  if (I >= n_ion) return;
+  const double twopi = 2.0 * kPi, L[3] = {lx, ly, lz};
+  double* g = grad + ((size_t)f * n_ion + I) * 3;
+  for (int d = 0; d < 3; ++d) g[d] = (g64[d] + (double)gh[d] + (double)gl[d]) * twopi / L[d];
+}
+
+// d/dr [erfc(g r) / r - erfc(a r) / r] (a = INFINITY: a point charge, no Gaussian term).
+__device__ __forceinline__ double radial_derivative(double g, double a, double r) {
+  const double two_sqrtpi = 1.1283791670955126;  // 2 / sqrt(pi)
+  double num = -two_sqrtpi * g * exp(-(g * r) * (g * r));
+  double e = erfc(g * r);
+  if (isfinite(a)) {
+    num += two_sqrtpi * a * exp(-(a * r) * (a * r));
+    e -= erfc(a * r);
+  }
+  return num / r - e / (r * r);
+}
+
+// Real part and slab term, then F_I = -q_I grad_I.  One thread per ion (grid row: frame);
+// electrode atoms staged by chunks.  A pair is screened in float from the exact
+// fixed-point difference of its nearest image (0.01 A^2 band, as k_bsol_real); the pairs
+// that pass sum every image within r_c in FP64: grad -= q_i f'(r) / r (r_i - r_I + R).
+// The slab term of Eq. 39: grad_z += (4 pi / V) (sum_i q_i z_i - sum_i q_i z_I).
+__global__ void __launch_bounds__(128)
+k_force_real(const double* __restrict__ xyz, const double* __restrict__ alpha,
+             const uint32_t* __restrict__ sfix, int n, const double* __restrict__ ion_xyz,
+             const double* __restrict__ ion_q, const uint32_t* __restrict__ sion, int n_ion,
+             const double* __restrict__ q, double lx, double ly, double lz, double g,
+             double rc, int slab, const double* __restrict__ grad_k, double* __restrict__ out) {
+  __shared__ uint32_t su[kForceChunk][3];
+  __shared__ double sx[kForceChunk][5];  // x, y, z, alpha, q
+  __shared__ double red[2][128];
+  const int f = blockIdx.y;
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = I < n_ion;
+  const size_t e = (size_t)f * n_ion + (live ? I : 0);
+  const double ri[3] = {ion_xyz[3 * e], ion_xyz[3 * e + 1], ion_xyz[3 * e + 2]};
+  const uint32_t ui[3] = {sion[3 * e], sion[3 * e + 1], sion[3 * e + 2]};
+  const double* qf = q + (size_t)f * n;
+  const double L[3] = {lx, ly, lz};
+  const double invL[3] = {1.0 / lx, 1.0 / ly, 1.0 / lz};
+  const float fs[3] = {(float)(lx * 0x1p-32), (float)(ly * 0x1p-32), (float)(lz * 0x1p-32)};
+  const double rc2 = rc * rc;
+  const float screen2 = (float)rc2 + 0.01f;
+  double gr[3] = {0.0, 0.0, 0.0};
+  double qz = 0.0, qs = 0.0;  // this thread's share of sum q_i z_i and sum q_i
+  for (int base = 0; base < n; base += kForceChunk) {
+    const int cnt = min(kForceChunk, n - base);
+    __syncthreads();
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+      const int i = base + t;
+      su[t][0] = sfix[3 * i];
+      su[t][1] = sfix[3 * i + 1];
+      su[t][2] = sfix[3 * i + 2];
+      sx[t][0] = xyz[3 * i];
+      sx[t][1] = xyz[3 * i + 1];
+      sx[t][2] = xyz[3 * i + 2];
+      sx[t][3] = alpha[i];
+      sx[t][4] = qf[i];
+      qz += qf[i] * xyz[3 * i + 2];
+      qs += qf[i];
+    }
+    __syncthreads();
+    if (!live) continue;
+    for (int t = 0; t < cnt; ++t) {
+      float m2 = 0.f;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const float du = (float)(int32_t)(su[t][d] - ui[d]) * fs[d];
+        m2 = fmaf(du, du, m2);
+      }
+      if (m2 >= screen2) continue;
+      // every image of the pair within r_c
+      double d0[3];
+      int lo[3], hi[3];
+      for (int d = 0; d < 3; ++d) {
+        d0[d] = sx[t][d] - ri[d];
+        d0[d] -= L[d] * rint(d0[d] * invL[d]);
+        lo[d] = (int)ceil((-rc - d0[d]) * invL[d]);
+        hi[d] = (int)floor((rc - d0[d]) * invL[d]);
+      }
+      for (int a = lo[0]; a <= hi[0]; ++a)
+        for (int b = lo[1]; b <= hi[1]; ++b)
+          for (int c = lo[2]; c <= hi[2]; ++c) {
+            const double dx = d0[0] + a * L[0], dy = d0[1] + b * L[1], dz = d0[2] + c * L[2];
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 >= rc2 || r2 == 0.0) continue;
+            const double r = sqrt(r2);
+            const double w = sx[t][4] * radial_derivative(g, sx[t][3], r) / r;
+            gr[0] -= w * dx;
+            gr[1] -= w * dy;
+            gr[2] -= w * dz;
+          }
+    }
+  }
+  // the frame's sum q_i z_i and sum q_i over the block's threads
+  red[0][threadIdx.x] = qz;
+  red[1][threadIdx.x] = qs;
+  __syncthreads();
+  for (int o = 64; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + o];
+      red[1][threadIdx.x] += red[1][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (!live) return;
+  const double* gk = grad_k + e * 3;
+  double gz = gr[2] + gk[2];
+  if (slab) gz += (4.0 * kPi / (lx * ly * lz)) * (red[0][0] - red[1][0] * ri[2]);
+  const double qI = ion_q[e];
+  out[3 * e] = -qI * (gr[0] + gk[0]);
+  out[3 * e + 1] = -qI * (gr[1] + gk[1]);
+  out[3 * e + 2] = -qI * gz;
+}
+
 }  // namespace
 
 void launch_ion_fixed(const double* ion_xyz, int frames, int n_ion, const double L[3],
@@ -511,11 +734,12 @@ void launch_bsol_kspace(bool fp64, const void* A, const double* Ahead, int n, in
                         const void* turn, cudaStream_t s) {
   const int64_t lda = 2 * (int64_t)mpad;
   if (!A && !fp64) {
-    for (int f0 = 0; f0 < frames; f0 += 65535) {
-      const int nf = std::min(frames - f0, 65535);
-      (k_bsol_kspace_direct<<<dim3((n + 127) / 128, nf), 128, 0, s>>>(
+    const int fgroups = (frames + kDirectFrames - 1) / kDirectFrames;
+    for (int g0 = 0; g0 < fgroups; g0 += 65535) {
+      const int f0 = g0 * kDirectFrames;
+      (k_bsol_kspace_direct<<<dim3((n + 127) / 128, std::min(fgroups - g0, 65535)), 128, 0, s>>>(
            sfix, n, hkl, sqw, mpad, kh, (const float4*)turn, (const float*)v + f0 * lda,
-           bsol + (int64_t)f0 * n),
+           frames - f0, bsol + (int64_t)f0 * n),
        note_launch());
     }
     for (int g0 = 0; kh > 0 && g0 < (frames + 3) / 4; g0 += 65535) {
@@ -556,6 +780,25 @@ void launch_bsol_real_and_finish(const double* xyz, const double* alpha, const u
   (k_bsol_real<<<grid, kRealWarps * 32, 0, s>>>(xyz, alpha, sfix, n, ion_xyz, ion_q, sion, n_ion, geo.L[0],
                                    geo.L[1], geo.L[2], geo.g, geo.rc, dip, chi, bsol_k, b_out,
                                    qsol), note_launch());
+}
+
+}  // namespace cpm
+
+namespace cpm {
+
+void launch_ion_forces(const double* xyz, const double* alpha, const uint32_t* sfix, int n,
+                       const double* ion_xyz, const double* ion_q, const uint32_t* sion,
+                       int frames, int n_ion, const double* q, const int* hkl,
+                       const double* sqw, int mpad, int kh, const Geometry& geo,
+                       const void* turn, const float* v, const double* vhead, double* grad,
+                       double* out, cudaStream_t s) {
+  const dim3 grid((n_ion + 127) / 128, frames);
+  (k_force_kspace<<<grid, 128, 0, s>>>(sion, n_ion, hkl, sqw, mpad, kh, (const float4*)turn, v,
+                                       vhead, geo.L[0], geo.L[1], geo.L[2], grad),
+   note_launch());
+  (k_force_real<<<grid, 128, 0, s>>>(xyz, alpha, sfix, n, ion_xyz, ion_q, sion, n_ion, q,
+                                     geo.L[0], geo.L[1], geo.L[2], geo.g, geo.rc, geo.slab,
+                                     grad, out), note_launch());
 }
 
 }  // namespace cpm

@@ -74,6 +74,7 @@ extern "C" int cpm_solve_static(cpm_ctx* c, int nrhs, const double* b, double* q
   SolveArgs a{nrhs, b, 1.0 / kKe, q_inout, use_guess != 0, tol, maxit, iters_out, relres_out};
   a.ws = ws;
   a.ws_bytes = CPM_STATIC_SCRATCH_BYTES;
+  a.timed = false;
   const int st = pcg_solve(c, a);
   if (st != CPM_OK && st != CPM_ENOCONV) return st;
   const int sync = cuda_check(c, cudaStreamSynchronize(c->stream), "solve_static sync");

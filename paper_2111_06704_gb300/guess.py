@@ -31,15 +31,9 @@ class LearnedGuess:
         self.lib = ctx.lib
         self.bf16 = 1 if bf16 else 0
         self.dev = torch.device("cuda", torch.cuda.current_device())
-        rng = np.random.default_rng(seed)
-        parts = []
-        for o, i in [(64, 32), (64, 64), (64, 64), (1, 64)]:
-            lim = np.sqrt(6.0 / i)
-            parts.append(rng.uniform(-lim, lim, size=o * i))
-            parts.append(np.zeros(o))
-        p = np.concatenate(parts).astype(np.float32)
-        p[-65:-1] *= 0.1  # small output layer: start close to the previous-step guess
-        self.params = torch.tensor(p, device=self.dev)
+        self.params = torch.empty(N_PARAMS, dtype=torch.float32, device=self.dev)
+        self.ctx._check(self.lib.cpm_guess_init(self.ctx.h, ctypes.c_uint64(seed),
+                                                _vp(self.params)))
         self.m = torch.zeros_like(self.params)
         self.v = torch.zeros_like(self.params)
         self.grad = torch.zeros_like(self.params)
@@ -100,16 +94,32 @@ class LearnedGuess:
         return q0
 
     # -- training -------------------------------------------------------------------
-    def set_normalisation(self, feat_sample: np.ndarray, target_sample: np.ndarray):
-        """Per-feature mean / inverse deviation and the target scale from a host sample."""
-        import torch
-        f = feat_sample.reshape(-1, N_FEATURES).astype(np.float64)
-        mu = f.mean(axis=0)
-        sd = f.std(axis=0)
-        inv = np.where(sd > 1e-12, 1.0 / np.where(sd > 1e-12, sd, 1.0), 0.0)
-        self.norm = torch.tensor(np.concatenate([mu, inv]).astype(np.float32), device=self.dev)
-        ts = float(np.std(target_sample))
-        self.target_scale = ts if ts > 0 else 1.0
+    def set_normalisation(self, feat, target):
+        """Per-feature mean / inverse deviation and the target scale from device samples
+        feat [S, 32] and target [S] (float32), by cpm_guess_norm."""
+        feat = feat.contiguous()
+        target = target.to(feat.dtype).contiguous()
+        ts = ctypes.c_float(1.0)
+        self.ctx._check(self.lib.cpm_guess_norm(self.ctx.h, ctypes.c_int64(feat.shape[0]),
+                                                _vp(feat), _vp(target), _vp(self.norm),
+                                                ctypes.byref(ts)))
+        self.target_scale = float(ts.value)
+
+    def save(self, path: str):
+        """The trained network (parameters, normalisation, target scale) to a file."""
+        st = self.lib.cpm_guess_save(path.encode(), _vp(self.params), _vp(self.norm),
+                                     ctypes.c_float(self.target_scale))
+        if st != cpm.CPM_OK:
+            raise cpm.CpmError(st, f"cpm_guess_save: cannot write {path}")
+
+    def load(self, path: str):
+        """A network written by save()."""
+        ts = ctypes.c_float(1.0)
+        st = self.lib.cpm_guess_load(path.encode(), _vp(self.params), _vp(self.norm),
+                                     ctypes.byref(ts))
+        if st != cpm.CPM_OK:
+            raise cpm.CpmError(st, f"cpm_guess_load: {path} is not a valid guess file")
+        self.target_scale = float(ts.value)
 
     def train(self, feat, target_q, epochs=3, batch=32768, lr=2e-3, seed=0, log=None):
         """Adam on the mean squared error of net(features) vs Delta q^b / target_scale.

@@ -63,7 +63,7 @@ def _null_args(fn):
     """NULL for every pointer argument, zero for every number (per the binding's argtypes)."""
     out = []
     for t in fn.argtypes:
-        if t in (ctypes.c_int, ctypes.c_int64):
+        if t in (ctypes.c_int, ctypes.c_int64, ctypes.c_uint64):
             out.append(0)
         elif t in (ctypes.c_double, ctypes.c_float):
             out.append(0.0)

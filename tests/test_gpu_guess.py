@@ -98,7 +98,7 @@ def test_trained_guess_beats_the_previous_step(walk):
     train = slice(1, 121)
     feat = g.features(b[train], b[0:120], chi).reshape(-1, mlp.N_FEATURES).contiguous()
     target = (qb[train] - qb[0:120]).reshape(-1).to(torch.float32).contiguous()
-    g.set_normalisation(feat.cpu().numpy(), target.cpu().numpy())
+    g.set_normalisation(feat, target)
     losses = g.train(feat, target, epochs=40, batch=8192, lr=3e-3)
     assert losses[-1] < 0.5 * losses[0]
     # held-out frames 121..160: PCG iterations to 1e-6 from both guesses
@@ -116,9 +116,34 @@ def test_one_call_guess_equals_the_three_calls(walk):
     chi = _dev(work.electrode.chi)
     g = LearnedGuess(ctx, seed=5)
     feat = g.features(b[1:9], b[0:8], chi)
-    g.set_normalisation(feat.reshape(-1, mlp.N_FEATURES).cpu().numpy(),
-                        (qb[1:9] - qb[0:8]).reshape(-1).cpu().numpy())
+    g.set_normalisation(feat.reshape(-1, mlp.N_FEATURES),
+                        (qb[1:9] - qb[0:8]).reshape(-1).to(torch.float32))
     prev = qb[0:8].contiguous()
     three = g.guess(feat, prev).reshape(prev.shape)
     one = g.guess_frames(b[1:9].contiguous(), b[0:8].contiguous(), chi, prev)
     assert torch.equal(one, three)
+
+
+def test_library_initialisation_and_normalisation_match_the_oracle(walk, tmp_path):
+    ctx, work, b, qb = walk
+    chi = _dev(work.electrode.chi)
+    g = LearnedGuess(ctx, seed=20211106)
+    # the counter-based initialisation, bit for bit
+    assert np.array_equal(g.params.cpu().numpy(), mlp.init_params_counter(20211106))
+    feat = g.features(b[1:9], b[0:8], chi).reshape(-1, mlp.N_FEATURES).contiguous()
+    target = (qb[1:9] - qb[0:8]).reshape(-1).to(torch.float32).contiguous()
+    g.set_normalisation(feat, target)
+    norm_ref, ts_ref = mlp.normalisation(feat.cpu().numpy(), target.cpu().numpy())
+    np.testing.assert_allclose(g.norm.cpu().numpy(), norm_ref, rtol=1e-6, atol=1e-30)
+    assert g.target_scale == pytest.approx(ts_ref, rel=1e-6)
+    # a trained network survives the file format (device arrays in and out)
+    g.train(feat, target, epochs=2, batch=4096, lr=1e-3)
+    path = str(tmp_path / "net.cpmguess")
+    g.save(path)
+    h = LearnedGuess(ctx, seed=1)
+    h.load(path)
+    assert torch.equal(h.params, g.params) and torch.equal(h.norm, g.norm)
+    assert h.target_scale == g.target_scale
+    prev = qb[0:8].contiguous()
+    assert torch.equal(h.guess_frames(b[1:9].contiguous(), b[0:8].contiguous(), chi, prev),
+                       g.guess_frames(b[1:9].contiguous(), b[0:8].contiguous(), chi, prev))

@@ -96,3 +96,37 @@ def test_dc_feature_is_the_local_inverse_applied_to_the_change():
     db = rng.standard_normal(9)
     f = mlp.features(b0 + db, b0, np.zeros(9), xyz, box, nb, p)
     assert np.allclose(m @ f[:, 20], db / ew.KE, rtol=0, atol=1e-12)
+
+
+def test_splitmix64_published_outputs():
+    # the first outputs of the SplitMix64 stream seeded with 0, as published with the
+    # generator's reference code (top 53 bits of each as the uniform)
+    first = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    u = mlp.splitmix64_uniform(0, [0, 1, 2])
+    assert list(u) == [(v >> 11) * 2.0 ** -53 for v in first]
+
+
+def test_counter_initialisation_layout_and_bounds():
+    p = mlp.init_params_counter(20211106)
+    assert p.dtype == np.float32 and p.shape == (mlp.N_PARAMS,)
+    layers = mlp.unpack(p.astype(np.float64))
+    for li, ((w, b), (o, i)) in enumerate(zip(layers, mlp.LAYERS)):
+        lim = np.sqrt(6.0 / i) * (0.1 if li == 3 else 1.0)
+        assert np.all(b == 0) and np.all(np.abs(w) <= lim)
+        if w.size >= 2048:  # a uniform on [-lim, lim): mean ~0, variance lim^2 / 3
+            assert abs(w.mean()) < 0.05 * lim
+            assert abs(w.var() / (lim * lim / 3.0) - 1.0) < 0.1
+    # the seed decides the draw
+    assert not np.array_equal(p, mlp.init_params_counter(1))
+
+
+def test_normalisation_small_case():
+    feat = np.zeros((4, mlp.N_FEATURES), dtype=np.float32)
+    feat[:, 0] = [1.0, 2.0, 3.0, 4.0]   # mean 2.5, population deviation sqrt(1.25)
+    feat[:, 1] = 7.0                    # constant: inverse deviation 0
+    norm, ts = mlp.normalisation(feat, [1.0, -1.0, 1.0, -1.0])
+    assert norm[0] == 2.5 and norm[1] == 7.0
+    assert norm[32] == pytest.approx(1.0 / np.sqrt(1.25)) and norm[33] == 0.0
+    assert ts == 1.0
+    _, ts0 = mlp.normalisation(feat, np.zeros(4))
+    assert ts0 == 1.0
