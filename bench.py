@@ -1224,13 +1224,13 @@ def run_scale_point(args, rank, world, local_rank):
         "solve_breakdown": solve_parts,
         "potential_breakdown": pot_parts,
         "step_matvec": {
-            "kernel": "k_matvec_fast (the 16 columns' inner matvec, E streamed once per "
+            "kernel": "k_matvec_stream (the 16 columns' inner matvec, E streamed once per "
                       "iteration)",
             "ms_per_launch": solve_parts["matvec_ms"] / max(1, solve_parts["max_iterations"]),
             "gbs": e_bytes / (solve_parts["matvec_ms"] / max(1, solve_parts["max_iterations"])
                               * 1e-3) / 1e9,
-            "note": "matvec_ms also holds the initial exact matvec of the guess; launches of "
-                    "one iteration counted as one"},
+            "note": "matvec_ms: the iterations' matvec launches (one per iteration for the "
+                    "group of 16 columns), events around each"},
         "mean_iters": statistics.mean(iters),
         "previous_step_guess_iters": float(np.mean(it_prev)),
         "q_rel_err_vs_tight_solve": q_err,

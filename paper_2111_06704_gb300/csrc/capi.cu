@@ -954,7 +954,8 @@ int cpm_potential(cpm_ctx* c, int frames, int n_ion, const double* ion_xyz,
   cudaEventRecord(pev[2], s);
   launch_bsol_real_and_finish((const double*)c->xyz.ptr, (const double*)c->alpha.ptr,
                               (const uint32_t*)c->sfix.ptr, n, dx, dq, sion, frames, n_ion,
-                              geometry(c), dchi, bk, db, dqs, s);
+                              geometry(c), dchi, bk, db, dqs,
+                              c->p.precision != CPM_PREC_FP64, s);
   cudaEventRecord(pev[3], s);
   if ((st = cuda_check(c, cudaGetLastError(), "potential kernels"))) return st;
   if (qsol_out && n_ion == 0 &&

@@ -255,7 +255,7 @@ void launch_bsol_real_and_finish(const double* xyz, const double* alpha, const u
                                  int n, const double* ion_xyz, const double* ion_q,
                                  const uint32_t* sion, int frames, int n_ion,
                                  const Geometry& geo, const double* chi, const double* bsol_k,
-                                 double* b_out, double* qsol, cudaStream_t s);
+                                 double* b_out, double* qsol, bool far_float, cudaStream_t s);
 
 void launch_ion_forces(const double* xyz, const double* alpha, const uint32_t* sfix, int n,
                        const double* ion_xyz, const double* ion_q, const uint32_t* sion,

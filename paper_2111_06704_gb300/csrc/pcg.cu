@@ -13,6 +13,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "async_copy.cuh"
 #include "cpm_internal.cuh"
 
 namespace cpm {
@@ -233,151 +234,244 @@ k_matvec_f32(const float* __restrict__ E, int64_t ldE, int n, const float* __res
   }
 }
 
-// The inner matvec of a many-column solve: q[c] = E p_c for the kFastCols columns of one
-// column group at once, so E is streamed from HBM once per iteration for all of them.
-// Products and partial sums are plain float (each lane sums one 1/32 share of the row);
-// lanes combine in FP64.  That is ~1e-6 of the row's partial sums, not the ~1e-14 of
-// k_matvec_f32: the solver uses it only between residual replacements, which recompute
-// b - E x with k_matvec_f32 (pcg_solve).  A block owns 64 rows (8 warps x 8 rows); stages
-// of E [64][128] and of the group's directions (xt[j][16] in global memory, four 16-byte
-// chunks per column, stored chunk-major in shared memory) go to shared memory by
-// cp.async, four stages in flight.  Lane l takes columns l, l + 32, l + 64, l + 96 of a
-// stage: its E values and its directions' chunks are consecutive across the warp, so
-// every shared-memory load is free of bank conflicts.
-constexpr int kFastCols = 16;
-constexpr int kFastRows = 64;
-constexpr int kFastK = 128;
-constexpr int kFastStages = 4;
-constexpr int kFastEBytes = kFastRows * kFastK * 4;    // 32 KB
-constexpr int kFastXBytes = kFastK * kFastCols * 4;    // 8 KB
-constexpr int kFastStageBytes = kFastEBytes + kFastXBytes;
-constexpr int kFastSmem = kFastStages * kFastStageBytes;
+constexpr int kFastCols = 16;  // columns of one group of a many-column solve
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
-                   (uint32_t)__cvta_generic_to_shared(smem)),
-               "l"(gmem)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
+// The inner matvec of a many-column solve, streamed by TMA: q[c] = E p_c for the 16
+// columns of one column group, E read from HBM once for all of them.  A unit is 256 rows
+// of E times one of `splits` equal shares of its columns; the host picks the share count
+// so that the units fill whole waves of the GPU.  One thread issues the copies (a 256 x 64
+// tile of E as two 128-byte-swizzled 256 x 32 TMA boxes, evict-first in L2, and the
+// group's 64 x 16 directions by one bulk copy) into a three-stage ring with full / empty
+// mbarriers, two stages ahead of its own warp (eight warps of 255 registers: two to each
+// scheduler); each warp w takes 8 of a stage's 64 columns, lane l rows l + 32 i (i < 8):
+// each E value is read from shared memory once (a float4 of four columns, the swizzle
+// keeps the eight lanes of each quarter-warp on distinct banks) and each direction value
+// is a broadcast.  Products and the per-lane partial sums are plain float, as
+// before (a lane sums 8 columns a stage over the unit's share: ~1e-6 of the row's partial
+// sums, not the ~1e-14 of k_matvec_f32, so the solver uses it only between residual
+// replacements, which recompute b - E x with k_matvec_f32); warps combine through shared
+// memory (pairwise, in float), and the last unit of a row block to finish (a counter per
+// row block, reset by that unit) adds the shares' FP64 partials in share order, writes q
+// and the p^T q partial of the block.  Every wait is bounded: on timeout the kernel
+// records an error code in *err and leaves once its copies have landed.
+constexpr int kStRows = 256;
+constexpr int kStK = 64;
+constexpr int kStStages = 3;
+constexpr int kStWarps = 8;
+constexpr int kStThreads = kStWarps * 32;
+constexpr int kStBox = kStRows * 32 * 4;                   // 32 KB: a 256 x 32 box of E
+constexpr int kStXBytes = kStK * kFastCols * 4;            // 4 KB of directions
+constexpr int kStStageBytes = 2 * kStBox + kStXBytes;      // 68 KB
+constexpr int kStSmem = kStStages * kStStageBytes + 1024;  // and 1 KB for the alignment
+constexpr int kStOut = kStRows * kFastCols;                // 4,096 outputs a unit
 
-__global__ void __launch_bounds__(kThreads, 1)
-k_matvec_fast(const float* __restrict__ E, int64_t ldE, int n, const float* __restrict__ xt,
-              const double* __restrict__ p64, int64_t ldv, int g0, int nrhs,
-              double* __restrict__ q, double* __restrict__ pq_part,
-              const ColState* __restrict__ st) {
-  extern __shared__ __align__(16) uint8_t fsm[];
-  const int grp = g0 + blockIdx.y;  // column group: columns 16 grp ..
-  const int c0 = grp * kFastCols;
-  const int ncol = min(kFastCols, nrhs - c0);
-  if (st) {  // a group with every column converged is not multiplied (uniform per block)
+struct StreamArgs {
+  int n, nst, splits, nrb;  // rows; 64-column stages a row; shares; row blocks
+  const float* xt;          // directions, [group][ldv][16]
+  const double* p64;
+  int64_t ldv;
+  int g0, nrhs;
+  double* part;     // [group][nrb * splits][4096] FP64 partials of the units
+  unsigned* count;  // [group][nrb] finished units, zero between launches
+  double* q;
+  double* pq_part;  // [nrb][nrhs]
+  const ColState* st;
+  int* err;
+};
+
+__global__ void __launch_bounds__(kStThreads, 1)
+k_matvec_stream(const __grid_constant__ CUtensorMap emap, StreamArgs a) {
+  extern __shared__ __align__(1024) uint8_t sraw[];
+  uint8_t* ring = (uint8_t*)(((uintptr_t)sraw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full[kStStages], empty[kStStages];
+  __shared__ int s_issued, s_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int grp = a.g0 + blockIdx.y, c0 = grp * kFastCols;
+  const int ncol = min(kFastCols, a.nrhs - c0);
+  const int rb = blockIdx.x / a.splits, sp = blockIdx.x % a.splits;
+  if (a.st) {  // a group with every column converged is not multiplied (uniform per grid row)
     bool live = false;
-    for (int r = 0; r < ncol; ++r) live |= st[c0 + r].done == 0;
+    for (int r = 0; r < ncol; ++r) live |= a.st[c0 + r].done == 0;
     if (!live) {
-      if (threadIdx.x < ncol) pq_part[(int64_t)blockIdx.x * nrhs + c0 + threadIdx.x] = 0.0;
+      if (sp == 0 && tid < ncol) a.pq_part[(int64_t)rb * a.nrhs + c0 + tid] = 0.0;
       return;
     }
   }
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int row0 = blockIdx.x * kFastRows;
-  const float* xg = xt + (int64_t)grp * ldv * kFastCols;
-  const int nk = (int)(ldE / kFastK);
-  // stage s: E rows row0 .. +63 (clamped to n - 1), columns k0 .. k0 + 127; directions of
-  // those columns, 16-byte chunk v of column j at chunk position (v + (j >> 1)) & 3
-  auto load_stage = [&](int kt, int slot) {
-    uint8_t* base = fsm + slot * kFastStageBytes;
-    const int64_t k0 = (int64_t)kt * kFastK;
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {  // 2,048 16-byte chunks of E
-      const int ch = tid + u * kThreads;
-      const int r = ch >> 5, cc = (ch & 31) * 4;
-      const int row = min(row0 + r, n - 1);
-      cp_async16(base + (r * kFastK + cc) * 4, E + (int64_t)row * ldE + k0 + cc);
+  const int kt0 = (int)((int64_t)sp * a.nst / a.splits);
+  const int cnt = (int)((int64_t)(sp + 1) * a.nst / a.splits) - kt0;
+  const int row0 = rb * kStRows;
+  if (tid == 0) {
+    for (int s = 0; s < kStStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kStWarps);
     }
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {  // 512 16-byte chunks of the directions: chunk v of
-      const int ch = tid + u * kThreads;  // column j at [v][j]
-      const int j = ch >> 2, v = ch & 3;
-      cp_async16(base + kFastEBytes + (v * kFastK + j) * 16, xg + (k0 + j) * kFastCols + v * 4);
-    }
-  };
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_issued = 0;
+  }
+  __syncthreads();
   float acc[8][kFastCols];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int cc = 0; cc < kFastCols; ++cc) acc[i][cc] = 0.f;
+  // stage i into its slot once every warp has released the slot's previous stage
+  const uint64_t pol = tid == 0 ? l2_evict_first() : 0;
+  const float* xg = a.xt + (int64_t)grp * a.ldv * kFastCols;
+  auto issue = [&](int i) -> bool {
+    const int slot = i % kStStages;
+    if (i >= kStStages && !mbar_wait(&empty[slot], ((i / kStStages) - 1) & 1, a.err, 21))
+      return false;
+    uint8_t* sb = ring + slot * kStStageBytes;
+    const int k0 = (kt0 + i) * kStK;
+    mbar_expect_tx(&full[slot], kStStageBytes);
+    tma_load_2d_hint(sb, &emap, &full[slot], k0, row0, pol);
+    tma_load_2d_hint(sb + kStBox, &emap, &full[slot], k0 + 32, row0, pol);
+    bulk_load(sb + 2 * kStBox, xg + (int64_t)k0 * kFastCols, kStXBytes, &full[slot]);
+    s_issued = i + 1;
+    return true;
+  };
+  bool ok = true;
+  if (tid == 0)
+    for (int i = 0; i < min(cnt, kStStages - 1) && ok; ++i) ok = issue(i);
+  // products: warp w takes columns 8 w .. 8 w + 7 of each stage
+  const int box = warp >> 2;
+  for (int i = 0; i < cnt; ++i) {
+    if (tid == 0 && ok && i + kStStages - 1 < cnt) ok = issue(i + kStStages - 1);
+    const int slot = i % kStStages;
+    if (!mbar_wait(&full[slot], (i / kStStages) & 1, a.err, 22)) break;
+    const uint8_t* sb = ring + slot * kStStageBytes;
+    const uint8_t* eb = sb + box * kStBox + lane * 128;
+    const float4* xs = reinterpret_cast<const float4*>(sb + 2 * kStBox) + warp * 8 * 4;
 #pragma unroll
-  for (int s = 0; s < kFastStages - 1; ++s) {
-    if (s < nk) load_stage(s, s);
-    cp_async_commit();
-  }
-  for (int kt = 0; kt < nk; ++kt) {
-    cp_async_wait<kFastStages - 2>();
-    __syncthreads();  // stage kt has landed for every thread; stage kt - 1 is free
-    if (kt + kFastStages - 1 < nk) load_stage(kt + kFastStages - 1, (kt + kFastStages - 1) % kFastStages);
-    cp_async_commit();
-    const uint8_t* base = fsm + (kt % kFastStages) * kFastStageBytes;
-    const float* es = reinterpret_cast<const float*>(base) + (warp * 8) * kFastK + lane;
-    const float4* xs = reinterpret_cast<const float4*>(base + kFastEBytes) + lane;
+    for (int c = 0; c < 2; ++c) {
+      // 16-byte chunk (warp & 3) * 2 + c of the row, at its swizzled place
+      const int ch = (((warp & 3) * 2 + c) ^ (lane & 7)) * 16;
+      float4 e[8];
 #pragma unroll
-    for (int w = 0; w < 4; ++w) {  // column j = lane + 32 w
-      float xv[kFastCols], ev[8];
+      for (int r = 0; r < 8; ++r)
+        e[r] = *reinterpret_cast<const float4*>(eb + r * 32 * 128 + ch);
 #pragma unroll
-      for (int v = 0; v < 4; ++v)
-        *reinterpret_cast<float4*>(xv + 4 * v) = xs[v * kFastK + 32 * w];
+      for (int kk = 0; kk < 4; ++kk) {
+        float xv[kFastCols];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) ev[i] = es[i * kFastK + 32 * w];
+        for (int v = 0; v < 4; ++v)
+          *reinterpret_cast<float4*>(xv + 4 * v) = xs[(4 * c + kk) * 4 + v];
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+        for (int r = 0; r < 8; ++r) {
+          const float ev = kk == 0 ? e[r].x : kk == 1 ? e[r].y : kk == 2 ? e[r].z : e[r].w;
 #pragma unroll
-        for (int cc = 0; cc < kFastCols; ++cc) acc[i][cc] = fmaf(ev[i], xv[cc], acc[i][cc]);
-    }
-  }
-  cp_async_wait<0>();
-  __syncthreads();
-  // lanes combine in FP64 through shared memory (the stage ring is free now): warp w's
-  // partials as buf[e][lane] with e = 16 i + cc (33-float rows: conflict-free both ways),
-  // then lane l sums entries e = l, l + 32, l + 64, l + 96 over the 32 lanes: column
-  // cc = l & 15 of rows i = (l >> 4) + 2 m
-  float* buf = reinterpret_cast<float*>(fsm) + warp * (8 * kFastCols * 33);
-#pragma unroll
-  for (int i = 0; i < 8; ++i)
-#pragma unroll
-    for (int cc = 0; cc < kFastCols; ++cc) buf[(i * kFastCols + cc) * 33 + lane] = acc[i][cc];
-  __syncwarp();
-  double* spq = reinterpret_cast<double*>(fsm + 8 * 8 * kFastCols * 33 * 4);  // [8][16]
-  double pq = 0.0;
-  {
-    const int cc = lane & 15;
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const int e = lane + 32 * m, i = e / kFastCols;
-      double v = 0.0;
-      for (int k = 0; k < 32; ++k) v += (double)buf[e * 33 + k];
-      const int row = row0 + warp * 8 + i;
-      if (row < n && cc < ncol) {
-        const int64_t o = (int64_t)(c0 + cc) * ldv + row;
-        q[o] = v;
-        pq += v * p64[o];
+          for (int cc = 0; cc < kFastCols; ++cc) acc[r][cc] = fmaf(ev, xv[cc], acc[r][cc]);
+        }
       }
     }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[slot]);
   }
-  // sum the lanes of one column (lanes cc and cc + 16), then the warps
-  pq += __shfl_xor_sync(0xffffffffu, pq, 16);
-  if (lane < kFastCols) spq[warp * kFastCols + lane] = pq;
   __syncthreads();
-  if (tid < ncol) {
-    double sum = 0.0;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) sum += spq[w * kFastCols + tid];
-    pq_part[(int64_t)blockIdx.x * nrhs + c0 + tid] = sum;
+  if (tid == 0) {  // copies still in flight (after an error): let them land before leaving
+    const int issued = s_issued;
+    for (int i = max(0, issued - kStStages); i < issued; ++i)
+      mbar_wait_drain(&full[i % kStStages], (i / kStStages) & 1);
+    s_flag = *(volatile int*)a.err;
   }
+  __syncthreads();
+  if (s_flag) return;
+  // warps' partials to shared memory: output o = (16 r + cc) 32 + lane of warp w at
+  // red[w][o] (whole-warp 128-byte rows)
+  float* red = reinterpret_cast<float*>(ring);
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int cc = 0; cc < kFastCols; ++cc)
+      red[warp * kStOut + (r * kFastCols + cc) * 32 + lane] = acc[r][cc];
+  __syncthreads();
+  double v[kStOut / (kStWarps * 32)];  // outputs o = tid + 256 m
+#pragma unroll
+  for (int m = 0; m < kStOut / (kStWarps * 32); ++m) {
+    const int o = tid + kStWarps * 32 * m;
+    // the eight warps' partials pairwise in float (three roundings of each, against the
+    // thousands in every partial), then FP64
+    float pw[kStWarps];
+#pragma unroll
+    for (int w = 0; w < kStWarps; ++w) pw[w] = red[w * kStOut + o];
+    v[m] = (double)(((pw[0] + pw[1]) + (pw[2] + pw[3])) + ((pw[4] + pw[5]) + (pw[6] + pw[7])));
+  }
+  constexpr int kM = kStOut / (kStWarps * 32);
+  if (a.splits > 1) {
+    const int64_t unit = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    double* mine = a.part + unit * kStOut;
+#pragma unroll
+    for (int m = 0; m < kM; ++m) mine[tid + kStWarps * 32 * m] = v[m];
+    __threadfence();
+    __syncthreads();
+    unsigned* counter = a.count + (int64_t)blockIdx.y * a.nrb + rb;
+    if (tid == 0) s_flag = atomicAdd(counter, 1u) == (unsigned)(a.splits - 1);
+    __syncthreads();
+    if (!s_flag) return;
+    __threadfence();
+    const double* shares = a.part + ((int64_t)blockIdx.y * gridDim.x + (int64_t)rb * a.splits) * kStOut;
+#pragma unroll
+    for (int m = 0; m < kM; ++m) {
+      const int o = tid + kStWarps * 32 * m;
+      double sum = 0.0;
+      for (int s = 0; s < a.splits; ++s) sum += __ldcg(shares + (int64_t)s * kStOut + o);
+      v[m] = sum;
+    }
+    if (tid == 0) *counter = 0u;
+  }
+  // o = (16 r + cc) 32 + lane: thread t holds column w = t / 32 for even m, w + 8 for odd
+  double pq_even = 0.0, pq_odd = 0.0;
+#pragma unroll
+  for (int m = 0; m < kM; ++m) {
+    const int o = tid + kStWarps * 32 * m;
+    const int cc = (o >> 5) & 15, row = row0 + (o >> 9) * 32 + (o & 31);
+    if (row < a.n && cc < ncol) {
+      const int64_t at = (int64_t)(c0 + cc) * a.ldv + row;
+      a.q[at] = v[m];
+      const double t = v[m] * a.p64[at];
+      if (m & 1) pq_odd += t;
+      else pq_even += t;
+    }
+  }
+  pq_even = warp_sum(pq_even);
+  pq_odd = warp_sum(pq_odd);
+  if (lane == 0) {
+    if (warp < ncol) a.pq_part[(int64_t)rb * a.nrhs + c0 + warp] = pq_even;
+    if (warp + 8 < ncol) a.pq_part[(int64_t)rb * a.nrhs + c0 + warp + 8] = pq_odd;
+  }
+}
+
+// Units of the streamed matvec: `splits` shares of each row's columns such that row
+// blocks x shares x groups fills whole waves of `sms` CTAs best (a smaller share count
+// unless a larger one fills 2% more of the last wave).
+int stream_splits(int nrb, int groups, int nst, int sms) {
+  int best = 1;
+  double best_eff = -1.0;
+  for (int sp = 1; sp <= std::min(8, nst); ++sp) {
+    const int64_t units = (int64_t)nrb * sp * groups;
+    const int64_t waves = (units + sms - 1) / sms;
+    const double eff = (double)units / (double)(waves * sms);
+    if (eff > best_eff + 0.02) {
+      best_eff = eff;
+      best = sp;
+    }
+  }
+  return best;
+}
+
+// TMA map of the float E [n][ldE] in 256-row x 32-column boxes, 128-byte swizzle; rows past
+// n read as zero.
+bool make_stream_map(CUtensorMap* m, const float* E, int n, int64_t ldE) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)ldE, (cuuint64_t)n};
+  cuuint64_t strides[1] = {(cuuint64_t)ldE * 4};
+  cuuint32_t box[2] = {32, (cuuint32_t)kStRows};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(E), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
 }
 
 // Ragged batch: column c is system c with its own float E (ld, n); one column per grid
@@ -615,7 +709,7 @@ __global__ void k_beta(const double* __restrict__ dots, int nparts, int nrhs, do
 // pair hi + lo (plo != nullptr) in float storage.
 // first = 2: only the columns whose residual replacement reopened them (restart flag),
 // which start again from p = z.  xt (float storage, many-column solves): the directions
-// again, transposed per group of 16 columns, [group][row][16], for k_matvec_fast.
+// again, transposed per group of 16 columns, [group][row][16], for k_matvec_stream.
 template <typename T>
 __global__ void k_p_update(int n, int64_t ldv, int nrhs, const ColState* __restrict__ st,
                            const double* __restrict__ z, double* __restrict__ p,
@@ -652,7 +746,7 @@ __global__ void k_split(const double* __restrict__ v, int64_t len, float* __rest
 }
 
 // The difference x - x_a of every column, in the transposed group layout of
-// k_matvec_fast ([group][row][16]); rows past n stay zero (the workspace is zeroed).
+// k_matvec_stream ([group][row][16]); rows past n stay zero (the workspace is zeroed).
 __global__ void k_diff_t(int n, int64_t ldv, const double* __restrict__ x,
                          const double* __restrict__ xa, float* __restrict__ xdt) {
   const int col = blockIdx.y;
@@ -1024,7 +1118,7 @@ int pcg_solve_kernels(Ctx* c, const SolveArgs& a) {
   const int pre = c->p.precond >= CPM_PRECOND_DC ? CPM_PRECOND_DC : c->p.precond;
   const bool f64 = c->fp64();
   // many columns of one float E: the inner iterations stream E once for every group of
-  // 16 columns (k_matvec_fast, float sums), and a replaced residual takes the place of the
+  // 16 columns (k_matvec_stream, float sums), and a replaced residual takes the place of the
   // recursive one whenever a column's residual has fallen 100-fold since the last
   // replacement or it reports convergence; convergence is declared on replaced residuals
   // only.  A replacement is b - E x through the exact matvec (an anchor), or, once every
@@ -1035,12 +1129,18 @@ int pcg_solve_kernels(Ctx* c, const SolveArgs& a) {
   // columns start again from an exact residual.
   const bool fast0 = !f64 && !a.sys && nrhs >= 2 && c->p.matvec_mode == 0;
   bool fast = fast0;
-  const int gm_fast = (n + kFastRows - 1) / kFastRows;
+  const int gm_fast = (n + kStRows - 1) / kStRows;  // row blocks of the streamed matvec
   int gm = fast ? gm_fast : gm_exact;
   const int groups = (nrhs + kFastCols - 1) / kFastCols;
   const size_t vbytes = (size_t)nrhs * ldv * sizeof(double);
-  // layout: x r z p q (double) | pv (storage type) | [fast: xt | x hi | x lo] | pq_part |
-  //         dots | dots_dc | states
+  // the streamed matvec's units: row blocks x shares per group of a launch
+  const int nst = (int)(c->ldE / kStK);
+  const int glaunch = std::min(groups, 65535);
+  const int splits = fast ? stream_splits(gm_fast, glaunch, nst, sms) : 1;
+  const size_t cnt_bytes = (size_t)glaunch * gm_fast * sizeof(unsigned);
+  // layout: x r z p q (double) | pv (storage type) | [fast: xt | x hi | x lo | x - x_a |
+  //         x_a | r_a | unit partials | counters, error flag] | pq_part | dots | dots_dc |
+  //         states
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
@@ -1053,6 +1153,10 @@ int pcg_solve_kernels(Ctx* c, const SolveArgs& a) {
                oxs = fast ? take(2 * (size_t)nrhs * ldv * sizeof(float)) : 0,
                oxd = fast ? take((size_t)groups * kFastCols * ldv * sizeof(float)) : 0,
                oxa = fast ? take(vbytes) : 0, ora = fast ? take(vbytes) : 0,
+               opart = fast && splits > 1
+                           ? take((size_t)glaunch * gm_fast * splits * kStOut * sizeof(double))
+                           : 0,
+               ocnt = fast ? take(cnt_bytes + sizeof(int)) : 0,
                opq = take((size_t)std::max(gm_fast, gm_exact) * nrhs * sizeof(double)),
                odt = take((size_t)ge * nrhs * 4 * sizeof(double)),
                odc = take((size_t)ge * nrhs * 4 * sizeof(double)),
@@ -1088,10 +1192,29 @@ int pcg_solve_kernels(Ctx* c, const SolveArgs& a) {
   double* xa = fast ? (double*)(base + oxa) : nullptr;  // the anchor's x and r
   double* ra = fast ? (double*)(base + ora) : nullptr;
   cudaStream_t s = c->stream;
-  if (fast && cuda_check(c, cudaFuncSetAttribute(k_matvec_fast,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 kFastSmem), "fast matvec smem"))
-    return CPM_ECUDA;
+  // the streamed matvec: its TMA map of E, units' partials and counters (zeroed above)
+  CUtensorMap emap;
+  double* part = fast && splits > 1 ? (double*)(base + opart) : nullptr;
+  unsigned* counts = fast ? (unsigned*)(base + ocnt) : nullptr;
+  int* mv_err = fast ? (int*)(base + ocnt + cnt_bytes) : nullptr;
+  if (fast) {
+    if (!make_stream_map(&emap, (const float*)c->E.ptr, n, c->ldE))
+      return set_err(c, CPM_ECUDA, "TMA map of E for the streamed matvec");
+    if (cuda_check(c, cudaFuncSetAttribute(k_matvec_stream,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, kStSmem),
+                   "streamed matvec smem"))
+      return CPM_ECUDA;
+  }
+  auto stream_mv = [&](const float* xin, const ColState* cur) {
+    StreamArgs sa{n, nst, splits, gm_fast, xin, p, ldv, 0, nrhs, part, counts, q, pq_part, cur,
+                  mv_err};
+    for (int g0 = 0; g0 < groups; g0 += 65535) {
+      sa.g0 = g0;
+      (k_matvec_stream<<<dim3(gm_fast * splits, std::min(groups - g0, 65535)), kStThreads,
+                         kStSmem, s>>>(emap, sa),
+       note_launch());
+    }
+  };
   // device timing of the solve's parts: event pairs from the context's pool
   size_t nev = 0;
   auto ev = [&]() -> cudaEvent_t {
@@ -1110,10 +1233,7 @@ int pcg_solve_kernels(Ctx* c, const SolveArgs& a) {
   // cur: the column states (converged columns are skipped), nullptr before they exist
   auto matvec = [&](const ColState* cur) {
     if (fast) {  // the inner matvec of a many-column solve
-      for (int g0 = 0; g0 < groups; g0 += 65535)
-        (k_matvec_fast<<<dim3(gm_fast, std::min(groups - g0, 65535)), kThreads, kFastSmem, s>>>(
-             (const float*)c->E.ptr, c->ldE, n, xt, p, ldv, g0, nrhs, q, pq_part, cur),
-         note_launch());
+      stream_mv(xt, cur);
     } else if (f64) {
       launch_matvec<double>(c, pv, nullptr, p, ldv, nrhs, q, pq_part, gm, cur);
     } else if (a.sys) {  // ragged batch: one system per column
@@ -1167,7 +1287,15 @@ int pcg_solve_kernels(Ctx* c, const SolveArgs& a) {
                                       cudaMemcpyDeviceToHost, s),
                    "poll"))
       return CPM_ECUDA;
+    int wait_err = 0;  // a bounded wait of the streamed matvec ran out
+    if (mv_err && cuda_check(c, cudaMemcpyAsync(&wait_err, mv_err, sizeof(int),
+                                                cudaMemcpyDeviceToHost, s),
+                             "poll"))
+      return CPM_ECUDA;
     if (cuda_check(c, cudaStreamSynchronize(s), "poll sync")) return CPM_ECUDA;
+    if (wait_err)
+      return set_err(c, CPM_ECUDA, "streamed matvec: a copy did not land in time (code " +
+                                       std::to_string(wait_err) + ")");
     all_done = true;
     for (int col = 0; col < nrhs; ++col)
       all_done &= host[col].done == 2 || (host[col].done == 1 && (!fast || verified[col]));
@@ -1189,10 +1317,7 @@ int pcg_solve_kernels(Ctx* c, const SolveArgs& a) {
     const int gvec = (int)std::min<int64_t>((vlen + kThreads - 1) / kThreads, 4 * sms);
     if (from_anchor) {  // r = r_a - E_fast (x - x_a)
       (k_diff_t<<<g2, kThreads, 0, s>>>(n, ldv, x, xa, xdt), note_launch());
-      for (int g0 = 0; g0 < groups; g0 += 65535)
-        (k_matvec_fast<<<dim3(gm_fast, std::min(groups - g0, 65535)), kThreads, kFastSmem, s>>>(
-             (const float*)c->E.ptr, c->ldE, n, xdt, x, ldv, g0, nrhs, q, pq_part, nullptr),
-         note_launch());
+      stream_mv(xdt, nullptr);
       (k_anchor_r<<<g2, kThreads, 0, s>>>(n, ldv, nrhs, cur, ra, q, r, z, inv_diag, pre, dots),
        note_launch());
     } else {  // r = b - E x, exactly; the new anchor

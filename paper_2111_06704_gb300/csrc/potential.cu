@@ -338,10 +338,7 @@ k_bsol_kspace_direct(const uint32_t* __restrict__ sfix, int n, const int* __rest
 
 // FP64 real-space sum of one electrode-ion pair over every image within r_c:
 // sum q_I [erfc(g r) - erfc(alpha_i r)] / r.
-// When every box edge exceeds 2 r_c only the nearest image can be in range; a pair beyond
-// r_split (where erfc(g r) / r < 1e-4 / A, and erfc(alpha r) underflows) then takes the
-// float erfc: about 4 ulp of a term below 1e-4, against the 1e-9 e/A that b^sol is held
-// to, summed in FP64.
+// When every box edge exceeds 2 r_c only the nearest image can be in range.
 __device__ __forceinline__ double pair_images(const double* ri, double ai, const double* ion,
                                               const double* L, const double* invL,
                                               const bool* single, double rc, double rc2,
@@ -390,28 +387,48 @@ __device__ __forceinline__ double pair_images(const double* ri, double ai, const
 }
 
 // Real-space electrode-ion sums, slab dipole term, and b = chi - k_e b^sol.
-// Four warps, 32 electrode atoms each; ions staged through shared memory.  Every image
-// of a pair is at least as far as its nearest one, so a pair whose nearest-image distance
-// is beyond r_cut contributes nothing: each lane screens its atom against every ion in
-// float from the exact fixed-point coordinate difference (off by < 1e-3 A^2 in r^2,
-// against a band of 0.01 A^2).  The pairs that pass are queued per warp and summed in
-// FP64 over their images 32 at a time, all lanes busy; each atom then adds its queued
-// pairs in ion order, so the sums are those of a plain per-atom loop.
+// Four warps, 32 electrode atoms each (one a lane); ions staged through shared memory in
+// chunks.  Every image of a pair is at least as far as its nearest one, so a pair whose
+// nearest image lies beyond r_c contributes nothing: each lane screens its atom against
+// every ion in float from the exact fixed-point coordinate difference (off by < 1e-3 A^2
+// in r^2, against a band of 0.01 A^2).  The pairs that pass go to one of two per-warp
+// queues that outlive the chunks and are evaluated 32 at a time, all lanes busy, each
+// atom then adding its queued values in queue order:
+//   near pairs (and every pair when a box edge is below 2 r_c): FP64 over their images,
+//     from the ions' FP64 coordinates kept in the queue;
+//   far pairs (one image per direction, r^2 >= r_split^2 where erfc(g r) / r <= 1e-4 1/A,
+//     r^2 below r_c^2 by more than the float error, alpha r >= 6 so that the Gaussian term
+//     has vanished): float, from the screen's r^2 (~1e-7 relative), the term to ~1e-6 of
+//     itself (<= 1e-10 1/A a pair), summed in float apart and added at the end.
+// No warp runs both arithmetic paths in one pass.  The float constants of the screen come
+// from the host: FP64 runs at 1/64 of the float rate here, and a constant formed from the
+// FP64 parameters would otherwise be re-formed inside the loop.
 constexpr int kRealWarps = 4;
 
-__global__ void __launch_bounds__(kRealWarps * 32)
+struct RealScreen {
+  float fs[3];    // L / 2^32: fixed-point units of each coordinate, A
+  float screen2;  // r_c^2 + 0.01
+  float cut2;     // r_c^2 (1 - 1e-5): far pairs lie below
+  float far2;     // r_split^2 (r_c^2 when no pair is far)
+  float g;        // Ewald splitting parameter, 1/A
+  int all_single; // every box edge above 2 r_c
+};
+
+__global__ void __launch_bounds__(kRealWarps * 32, 6)
 k_bsol_real(const double* __restrict__ xyz, const double* __restrict__ alpha,
             const uint32_t* __restrict__ sfix, int n, const double* __restrict__ ion_xyz,
             const double* __restrict__ ion_q, const uint32_t* __restrict__ sion, int n_ion,
-            double lx, double ly, double lz, double g, double rc, double dip,
-            const double* __restrict__ chi, const double* __restrict__ bsol_k,
+            double lx, double ly, double lz, double g, double rc, const RealScreen rs,
+            double dip, const double* __restrict__ chi, const double* __restrict__ bsol_k,
             double* __restrict__ b_out, double* __restrict__ qsol) {
   __shared__ double sx[kIonChunk][4];
   __shared__ uint32_t su[kIonChunk][3];
-  __shared__ double sa[kRealWarps * 32][4];        // the block's atoms: x, y, z, alpha
-  __shared__ uint32_t queue[kRealWarps][64];       // (atom lane << 16) | ion in chunk
+  __shared__ double sa[kRealWarps * 32][4];   // the block's atoms: x, y, z, alpha
+  __shared__ double nq[kRealWarps][64][4];    // near queue: ion x, y, z, q
+  __shared__ float2 fq[kRealWarps][64];       // far queue: r^2, q
+  __shared__ uint8_t nlane[kRealWarps][64], flane[kRealWarps][64];
   __shared__ double qval[kRealWarps][32];
-  __shared__ uint32_t qkey[kRealWarps][32];
+  __shared__ float fval[kRealWarps][32];
   const int f = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -419,6 +436,7 @@ k_bsol_real(const double* __restrict__ xyz, const double* __restrict__ alpha,
   const double* iq = ion_q + (size_t)f * n_ion;
   const uint32_t* iu = sion + (size_t)f * n_ion * 3;
   uint32_t ui[3] = {0, 0, 0};
+  float af2 = 0.f;  // alpha^2 of the lane's atom
   if (i < n) {
     ui[0] = sfix[3 * i];
     ui[1] = sfix[3 * i + 1];
@@ -427,31 +445,43 @@ k_bsol_real(const double* __restrict__ xyz, const double* __restrict__ alpha,
     sa[threadIdx.x][1] = xyz[3 * i + 1];
     sa[threadIdx.x][2] = xyz[3 * i + 2];
     sa[threadIdx.x][3] = alpha[i];
+    af2 = (float)(alpha[i] * alpha[i]);
   }
   const double L[3] = {lx, ly, lz};
   const double rc2 = rc * rc;
   const double invL[3] = {1.0 / lx, 1.0 / ly, 1.0 / lz};
   const bool single[3] = {2.0 * rc < lx, 2.0 * rc < ly, 2.0 * rc < lz};
-  const float fs[3] = {(float)(lx * 0x1p-32), (float)(ly * 0x1p-32), (float)(lz * 0x1p-32)};
-  const float screen2 = (float)rc2 + 0.01f;
-  // evaluates the first `cnt` queued pairs (one per lane) and adds each atom's values in
+  // evaluates the first `cnt` queued pairs (one a lane); each atom adds its values in
   // queue order
   auto drain = [&](int cnt, double& acc) {
     __syncwarp();
     if (lane < cnt) {
-      const uint32_t e = queue[warp][lane];
-      const int a = (int)(e >> 16), t = (int)(e & 0xffffu);
-      qval[warp][lane] = pair_images(sa[warp * 32 + a], sa[warp * 32 + a][3], sx[t], L, invL,
-                                     single, rc, rc2, g);
-      qkey[warp][lane] = (uint32_t)a;
+      const int a = nlane[warp][lane];
+      qval[warp][lane] = pair_images(sa[warp * 32 + a], sa[warp * 32 + a][3], nq[warp][lane],
+                                     L, invL, single, rc, rc2, g);
     }
     __syncwarp();
     for (int k = 0; k < cnt; ++k)
-      if (qkey[warp][k] == (uint32_t)lane) acc += qval[warp][k];
+      if (nlane[warp][k] == lane) acc += qval[warp][k];
+    __syncwarp();
+  };
+  auto drain_far = [&](int cnt, float& acc) {
+    __syncwarp();
+    if (lane < cnt) {
+      const float2 e = fq[warp][lane];
+      const float ir = rsqrtf(e.x);  // 1 / r to ~2 ulp
+      fval[warp][lane] = e.y * (erfcf(rs.g * (e.x * ir)) * ir);
+    }
+    __syncwarp();
+    for (int k = 0; k < cnt; ++k)
+      if (flane[warp][k] == lane) acc += fval[warp][k];
     __syncwarp();
   };
   // sum q_I z_I and sum q_I over the frame: each thread takes the ions it stages
   double acc = 0.0, qz = 0.0, qs = 0.0;
+  float accf = 0.f;
+  int qn = 0, fn = 0;  // queued near and far pairs of this warp (warp-uniform)
+  const unsigned below = (1u << lane) - 1u;
   for (int base = 0; base < n_ion; base += kIonChunk) {
     const int cnt = min(kIonChunk, n_ion - base);
     __syncthreads();
@@ -467,29 +497,59 @@ k_bsol_real(const double* __restrict__ xyz, const double* __restrict__ alpha,
       qs += sx[t][3];
     }
     __syncthreads();
-    int qn = 0;  // queued pairs of this warp (warp-uniform)
     for (int t = 0; t < cnt; ++t) {
-      bool cand = false;
+      bool near = false, far = false;
+      float m2 = 0.f;
       if (i < n) {
-        float m2 = 0.f;
 #pragma unroll
         for (int u = 0; u < 3; ++u) {
-          const float du = (float)(int32_t)(ui[u] - su[t][u]) * fs[u];  // nearest image
+          const float du = (float)(int32_t)(ui[u] - su[t][u]) * rs.fs[u];  // nearest image
           m2 = fmaf(du, du, m2);
         }
-        cand = m2 < screen2;
+        far = rs.all_single && m2 >= rs.far2 && m2 < rs.cut2 && af2 * m2 >= 36.0f;
+        near = !far && m2 < rs.screen2;
       }
-      const unsigned m = __ballot_sync(0xffffffffu, cand);
-      if (cand) queue[warp][qn + __popc(m & ((1u << lane) - 1u))] = ((uint32_t)lane << 16) | t;
-      qn += __popc(m);
+      const unsigned mn = __ballot_sync(0xffffffffu, near);
+      const unsigned mf = __ballot_sync(0xffffffffu, far);
+      if (near) {
+        const int at = qn + __popc(mn & below);
+        nq[warp][at][0] = sx[t][0];
+        nq[warp][at][1] = sx[t][1];
+        nq[warp][at][2] = sx[t][2];
+        nq[warp][at][3] = sx[t][3];
+        nlane[warp][at] = (uint8_t)lane;
+      }
+      if (far) {
+        const int at = fn + __popc(mf & below);
+        fq[warp][at] = make_float2(m2, (float)sx[t][3]);
+        flane[warp][at] = (uint8_t)lane;
+      }
+      qn += __popc(mn);
+      fn += __popc(mf);
       if (qn >= 32) {
         drain(32, acc);
-        if (lane < qn - 32) queue[warp][lane] = queue[warp][32 + lane];
+        if (lane < qn - 32) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) nq[warp][lane][c] = nq[warp][32 + lane][c];
+          nlane[warp][lane] = nlane[warp][32 + lane];
+        }
         qn -= 32;
+        __syncwarp();
+      }
+      if (fn >= 32) {
+        drain_far(32, accf);
+        if (lane < fn - 32) {
+          fq[warp][lane] = fq[warp][32 + lane];
+          flane[warp][lane] = flane[warp][32 + lane];
+        }
+        fn -= 32;
+        __syncwarp();
       }
     }
-    if (qn > 0) drain(qn, acc);
   }
+  if (qn > 0) drain(qn, acc);
+  if (fn > 0) drain_far(fn, accf);
+  acc += (double)accf;
   __shared__ double red[2][kRealWarps];
   for (int o = 16; o; o >>= 1) {
     qz += __shfl_xor_sync(0xffffffffu, qz, o);
@@ -774,12 +834,34 @@ void launch_bsol_real_and_finish(const double* xyz, const double* alpha, const u
                                  int n, const double* ion_xyz, const double* ion_q,
                                  const uint32_t* sion, int frames, int n_ion,
                                  const Geometry& geo, const double* chi, const double* bsol_k,
-                                 double* b_out, double* qsol, cudaStream_t s) {
+                                 double* b_out, double* qsol, bool far_float, cudaStream_t s) {
   dim3 grid((n + kRealWarps * 32 - 1) / (kRealWarps * 32), frames);
   double dip = geo.slab ? 4.0 * kPi / geo.vol : 0.0;
-  (k_bsol_real<<<grid, kRealWarps * 32, 0, s>>>(xyz, alpha, sfix, n, ion_xyz, ion_q, sion, n_ion, geo.L[0],
-                                   geo.L[1], geo.L[2], geo.g, geo.rc, dip, chi, bsol_k, b_out,
-                                   qsol), note_launch());
+  // r_split: erfc(g r) / r = 1e-4 / A (bisection); r_c (no far pairs) when the term never
+  // gets that small or the FP64 build asks for FP64 throughout
+  double lo = 1e-3, hi = geo.rc;
+  if (!far_float || erfc(geo.g * hi) / hi > 1e-4) {
+    lo = hi;
+  } else {
+    for (int it = 0; it < 60; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (erfc(geo.g * mid) / mid > 1e-4) lo = mid;
+      else hi = mid;
+    }
+    lo = hi;
+  }
+  RealScreen rs;
+  for (int u = 0; u < 3; ++u) rs.fs[u] = (float)(geo.L[u] * 0x1p-32);
+  const double rc2 = geo.rc * geo.rc;
+  rs.screen2 = (float)rc2 + 0.01f;
+  rs.cut2 = (float)(rc2 * (1.0 - 1e-5));
+  rs.far2 = (float)(lo * lo);
+  rs.g = (float)geo.g;
+  rs.all_single = 2.0 * geo.rc < geo.L[0] && 2.0 * geo.rc < geo.L[1] && 2.0 * geo.rc < geo.L[2];
+  (k_bsol_real<<<grid, kRealWarps * 32, 0, s>>>(xyz, alpha, sfix, n, ion_xyz, ion_q, sion, n_ion,
+                                               geo.L[0], geo.L[1], geo.L[2], geo.g, geo.rc, rs,
+                                               dip, chi, bsol_k, b_out, qsol),
+   note_launch());
 }
 
 }  // namespace cpm

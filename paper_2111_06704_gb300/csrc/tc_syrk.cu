@@ -33,6 +33,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include "async_copy.cuh"
 #include "cpm_internal.cuh"
 
 namespace cpm {
@@ -41,52 +42,6 @@ namespace {
 
 constexpr int kTile = 128;           // output tile edge
 constexpr int kBlockK = 64;          // operand columns per K-block of the schedule
-constexpr long long kWaitCycles = 20000000000ll;      // ~10 s at 2 GHz: wait limit
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait: gives up after kWaitCycles SM clocks (~10 s) or once another thread has
-// recorded an error; on its own timeout it records `code` in *err.  Returns true when the
-// phase completed.
-__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
-  const long long t0 = clock64();
-  for (unsigned it = 0;; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255u) == 255u) {
-      if (*(volatile int*)err) return false;
-      if (clock64() - t0 > kWaitCycles) break;
-    }
-  }
-  atomicCAS(err, 0, code);
-  return false;
-}
 
 // As mbar_wait, with cluster-scope acquire: for barriers that the peer CTA of a pair
 // arrives on (its writes before the arrival are visible after the wait).
@@ -112,25 +67,6 @@ __device__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity, int* err, int 
   }
   atomicCAS(err, 0, code);
   return false;
-}
-
-// Bounded wait for the way out of a kernel (after an error too): no early exit on the
-// error flag, a limit of ~0.5 s; returns whether the phase completed.
-__device__ bool mbar_wait_drain(uint64_t* bar, uint32_t parity) {
-  const long long t0 = clock64();
-  for (unsigned it = 0;; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255u) == 255u && clock64() - t0 > kWaitCycles / 20) return false;
-  }
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                            int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_addr(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_addr(bar)), "r"(x), "r"(y)
-      : "memory");
 }
 
 // Shared-memory matrix descriptor: K-major tile, 128-byte swizzle, rows of 128 B,
@@ -1042,19 +978,6 @@ __global__ void k_head_to_float(const double* __restrict__ head, int64_t ldh,
   const int j = blockIdx.x * 32 + threadIdx.x;
   for (int i = blockIdx.y * 32 + threadIdx.y; i < min(n, (int)(blockIdx.y + 1) * 32); i += 8)
     if (j < n && j <= i) E[(int64_t)i * ldE + j] = (float)head[(int64_t)i * ldh + j];
-}
-
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-  }
-  return fn;
 }
 
 // 2-D map of a [rows][cols] plane of 16-bit values (bytes = false) in 128-row boxes of bk

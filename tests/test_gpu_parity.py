@@ -12,6 +12,7 @@ solve to 1e-9.
 import numpy as np
 import pytest
 
+from oracle import ewald as ew
 from oracle import precond as pc
 from paper_2111_06704_gb300 import cpm
 from paper_2111_06704_gb300 import workloads as wl
@@ -197,6 +198,37 @@ def test_tiny_cell_with_images_and_net_charge(prec, q_sol):
     assert rel_max(b, oc.b_neutral_volts) < B_TOL[prec]
     assert qsol[0] == q_sol
     assert rel_l2(q, oc.q) < Q_TOL[prec]
+    ctx.close()
+
+
+@pytest.fixture(scope="module")
+def wide_cell():
+    # box edges 29.5 x 29.8 A, above 2 r_cut = 24 A: one image per direction, so the real
+    # space takes the far electrode-ion pairs (erfc(g r) / r <= 1e-4 1/A) in float in the
+    # FP32 and BF16X6 builds, and in FP64 in the FP64 build
+    el = wl.two_sheet_electrode(12, 7)
+    rng = np.random.default_rng(wl.seed_for(1, 7))
+    frames = [wl.random_ions(rng, 200, 200, el.box, min_sep=2.5) for _ in range(3)]
+    io = wl.Electrolyte(np.stack([f[0] for f in frames]), np.stack([f[1] for f in frames]))
+    g, rc, eps = wl.G_EWALD, wl.RCUT_REAL, wl.KSPACE_EPS
+    ref = []
+    for f in range(io.frames):
+        bsol = ew.electrolyte_potential(el.xyz, el.alpha, io.xyz[f], io.q[f], el.box, g, rc, eps)
+        bsn = ew.neutral_form_bsol(bsol, el.xyz, io.xyz[f], io.q[f], el.box, g)
+        ref.append(ew.rhs_volts(el.chi, bsn))
+    return el, io, np.array(ref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x6"])
+def test_potential_with_float_far_pairs(prec, wide_cell):
+    el, io, ref = wide_cell
+    ctx = cpm.Context(el.box, precision=PREC[prec], rcut_dc=3.0)
+    ctx.cpm_build_E(el.xyz, el.alpha)
+    b, qsol = ctx.cpm_potential(io.xyz, io.q, el.chi)
+    err = rel_max(b, ref)
+    print(f"{prec}: b max error {err:.2e} of the largest entry")
+    assert err < B_TOL[prec]
+    assert np.all(qsol == 0)
     ctx.close()
 
 
