@@ -33,6 +33,11 @@ if ROOT not in sys.path:
 from paper_2111_06704_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "charge solves/s at 1e-6 rel. residual & E-build s, vs plain FP64 PCG same GPU"
+# DRAM bytes (read + write) per element of E of one k_matvec_stream launch, from the ncu
+# capture of that kernel on a 25,600-atom case (16 columns),
+# scaled to a full launch by N^2; None until a capture of the current kernel exists.
+STREAM_TRAFFIC_PER_ELEMENT = None
+STREAM_TRAFFIC_NOTE = "no capture of the current kernel yet"
 TOL = 1e-6
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 SMS = 152
@@ -1178,6 +1183,23 @@ def run_scale_point(args, rank, world, local_rank):
     sustained = peaks.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"])
     burst = peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"])
     achieved = method_flops / (tc_ms * 1e-3) / 1e12
+    # the step's dominant kernel: the streamed 16-column matvec of the PCG iterations
+    mv_launch_ms = solve_parts["matvec_ms"] / max(1, solve_parts["max_iterations"])
+    mv_bytes = 4.0 * n * n + H * n * 4.0 + H * n * 8.0
+    mv_achieved = mv_bytes / (mv_launch_ms * 1e-3) / 1e9
+    step_roof = {"bound": "hbm", "achieved": mv_achieved, "peak": hbm, "unit": "GB/s",
+                 "frac": mv_achieved / hbm,
+                 "traffic": STREAM_TRAFFIC_PER_ELEMENT * n * n
+                 if STREAM_TRAFFIC_PER_ELEMENT else None,
+                 "kernel": "k_matvec_stream (16-column float matvec of the PCG iterations, E "
+                           "streamed by TMA once per iteration)",
+                 "timed_region": "the timed steps: CUDA events around each iteration's matvec "
+                                 "launch on the solve stream (last step's solve)",
+                 "work": "algorithmic bytes per launch: N^2 x 4 (E) + 16 N x 4 (float "
+                         "directions) + 16 N x 8 (FP64 products)",
+                 "ms_per_launch": mv_launch_ms, "bytes_per_launch": mv_bytes,
+                 "peak_source": f"{src} hbm_gbs (of measured)",
+                 "traffic_source": STREAM_TRAFFIC_NOTE}
     roof = {"bound": "tensor", "achieved": achieved, "peak": sustained, "unit": "TFLOP/s",
             "frac": achieved / sustained, "traffic": None,
             "kernel": "k_ek_strip (tcgen05 k-space tail of the E build, all k-windows)",
@@ -1234,7 +1256,8 @@ def run_scale_point(args, rank, world, local_rank):
         "mean_iters": statistics.mean(iters),
         "previous_step_guess_iters": float(np.mean(it_prev)),
         "q_rel_err_vs_tight_solve": q_err,
-        "roofline": roof,
+        "roofline": step_roof,
+        "build_roofline": roof,
         "matvec_roofline": {"bound": "hbm", "kernel": "k_matvec_f32 (PCG matvec, E streamed "
                             "once per pass of up to four columns)",
                             "achieved": mv_gbs[1], "peak": hbm, "unit": "GB/s",

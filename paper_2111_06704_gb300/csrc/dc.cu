@@ -33,21 +33,28 @@ __device__ __forceinline__ double dist2(const double* a, const double* b, double
 // The candidates of a block are staged as float positions; the float minimum-image
 // distance decides every pair outside a band of +-0.01 A^2 around r_cut^2 (float
 // positions of a box below 1e4 A are off by < 1e-3 A, so the band is ample), and the
-// pairs inside it are decided by the FP64 distance, as the definition asks.
+// pairs inside it are decided by the FP64 distance, as the definition asks.  The float
+// constants come from the host (a constant formed from the FP64 parameters could be
+// re-formed inside the loop, at 1/64 of the float rate).
 constexpr int kNbrWarps = 8;
 constexpr int kNbrStage = 1024;
 
+struct NbrFloat {
+  float L[3], inv[3];  // box edges and their reciprocals
+  float lo2, hi2;      // r_cut^2 -+ 0.01: the band decided in FP64
+};
+
 __global__ void __launch_bounds__(kNbrWarps * 32)
 k_neighbours(const double* __restrict__ xyz, int n, double lx, double ly, double lz,
-             double rc2, int* __restrict__ cnt, const int64_t* __restrict__ off,
-             int* __restrict__ idx, int fill, int strict = 0) {
+             double rc2, const NbrFloat nf, int* __restrict__ cnt,
+             const int64_t* __restrict__ off, int* __restrict__ idx, int fill, int strict) {
   __shared__ float4 sp[kNbrStage];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = blockIdx.x * kNbrWarps + warp;
   const bool live = t < n;
-  const float Lx = (float)lx, Ly = (float)ly, Lz = (float)lz;
-  const float ix = (float)(1.0 / lx), iy = (float)(1.0 / ly), iz = (float)(1.0 / lz);
-  const float lo2 = (float)rc2 - 0.01f, hi2 = (float)rc2 + 0.01f;
+  const float Lx = nf.L[0], Ly = nf.L[1], Lz = nf.L[2];
+  const float ix = nf.inv[0], iy = nf.inv[1], iz = nf.inv[2];
+  const float lo2 = nf.lo2, hi2 = nf.hi2;
   float tx = 0.f, ty = 0.f, tz = 0.f;
   if (live) {
     tx = (float)xyz[3 * t];
@@ -85,6 +92,21 @@ k_neighbours(const double* __restrict__ xyz, int n, double lx, double ly, double
     }
   }
   if (!fill && live && lane == 0) cnt[t] = c;
+}
+
+void launch_neighbours(const double* xyz, int n, const double* L, double rc2, int* cnt,
+                       const int64_t* off, int* idx, int fill, int strict, cudaStream_t s) {
+  NbrFloat nf;
+  for (int u = 0; u < 3; ++u) {
+    nf.L[u] = (float)L[u];
+    nf.inv[u] = (float)(1.0 / L[u]);
+  }
+  nf.lo2 = (float)rc2 - 0.01f;
+  nf.hi2 = (float)rc2 + 0.01f;
+  const int blocks = (n + kNbrWarps - 1) / kNbrWarps;
+  (k_neighbours<<<blocks, kNbrWarps * 32, 0, s>>>(xyz, n, L[0], L[1], L[2], rc2, nf, cnt, off,
+                                                   idx, fill, strict),
+   note_launch());
 }
 
 // The off-diagonal value of Eq. 36 for every pattern entry (j, j'): (erfc(g r) -
@@ -358,10 +380,8 @@ int build_dc_preconditioner(Ctx* c) {
   // workspace kept by the context (buf_reserve): the counts, the local solutions, a flag
   Buf &cnt = c->dc_cnt, &pcol = c->dc_pcol, &status = c->dc_status;
   if (int rc2 = buf_reserve(c, &cnt, (size_t)n * sizeof(int))) return rc2;
-  const int blocks = (n + kNbrWarps - 1) / kNbrWarps;
-  (k_neighbours<<<blocks, kNbrWarps * 32, 0, s>>>((const double*)c->xyz.ptr, n, L[0], L[1],
-                                                   L[2], rc * rc, (int*)cnt.ptr, nullptr,
-                                                   nullptr, 0), note_launch());
+  launch_neighbours((const double*)c->xyz.ptr, n, L, rc * rc, (int*)cnt.ptr, nullptr, nullptr,
+                    0, 0, s);
   std::vector<int> hc(n);
   int st = cuda_check(c, cudaMemcpyAsync(hc.data(), cnt.ptr, n * sizeof(int),
                                          cudaMemcpyDeviceToHost, s), "dc counts");
@@ -385,10 +405,8 @@ int build_dc_preconditioner(Ctx* c) {
                                      cudaMemcpyHostToDevice, s), "dc offsets");
   if (!st) st = cuda_check(c, cudaMemsetAsync(status.ptr, 0, sizeof(int), s), "dc status");
   if (!st) {
-    (k_neighbours<<<blocks, kNbrWarps * 32, 0, s>>>((const double*)c->xyz.ptr, n, L[0], L[1],
-                                                   L[2], rc * rc, nullptr,
-                                                   (const int64_t*)c->nbr_off.ptr,
-                                                   (int*)c->nbr_idx.ptr, 1), note_launch());
+    launch_neighbours((const double*)c->xyz.ptr, n, L, rc * rc, nullptr,
+                      (const int64_t*)c->nbr_off.ptr, (int*)c->nbr_idx.ptr, 1, 0, s);
     const size_t smem = dc_local_smem(mx);
     st = cuda_check(c, cudaFuncSetAttribute(k_dc_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)smem), "dc smem");
@@ -446,10 +464,8 @@ int build_sparse_inverse(Ctx* c) {
   Buf& cnt = c->dc_cnt;
   int st;
   if ((st = buf_reserve(c, &cnt, (size_t)n * sizeof(int)))) return st;
-  const int blocks = (n + kNbrWarps - 1) / kNbrWarps;
-  (k_neighbours<<<blocks, kNbrWarps * 32, 0, s>>>((const double*)c->xyz.ptr, n, L[0], L[1],
-                                                   L[2], rc * rc, (int*)cnt.ptr, nullptr,
-                                                   nullptr, 0, full ? 0 : 1), note_launch());
+  launch_neighbours((const double*)c->xyz.ptr, n, L, rc * rc, (int*)cnt.ptr, nullptr, nullptr,
+                    0, full ? 0 : 1, s);
   std::vector<int> hc(n);
   st = cuda_check(c, cudaMemcpyAsync(hc.data(), cnt.ptr, n * sizeof(int),
                                      cudaMemcpyDeviceToHost, s), "pattern counts");
@@ -466,11 +482,8 @@ int build_sparse_inverse(Ctx* c) {
   st = cuda_check(c, cudaMemcpyAsync(c->nbr_off.ptr, off.data(), (n + 1) * sizeof(int64_t),
                                      cudaMemcpyHostToDevice, s), "pattern offsets");
   if (st) return st;
-  (k_neighbours<<<blocks, kNbrWarps * 32, 0, s>>>((const double*)c->xyz.ptr, n, L[0], L[1],
-                                                   L[2], rc * rc, nullptr,
-                                                   (const int64_t*)c->nbr_off.ptr,
-                                                   (int*)c->nbr_idx.ptr, 1, full ? 0 : 1),
-   note_launch());
+  launch_neighbours((const double*)c->xyz.ptr, n, L, rc * rc, nullptr,
+                    (const int64_t*)c->nbr_off.ptr, (int*)c->nbr_idx.ptr, 1, full ? 0 : 1, s);
   // the columns of E^-1: one PCG over the n identity columns, Jacobi-preconditioned
   Buf ident, cols;
   const size_t bytes = (size_t)n * n * sizeof(double);

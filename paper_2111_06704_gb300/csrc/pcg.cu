@@ -1247,15 +1247,17 @@ int pcg_solve_kernels(Ctx* c, const SolveArgs& a) {
   if (cuda_check(c, cudaMemsetAsync(base, 0, ost, s), "memset")) return CPM_ECUDA;
 
   const double* inv_diag = c->diag.ptr ? (const double*)c->diag.ptr + n : nullptr;
-  // initial guess: q = E x0 through the same (hi + lo) matvec
+  // initial guess: q = E x0 through the solve's matvec (a many-column solve: the streamed
+  // float one; its r0 is no anchor, and the first replacement recomputes b - E x exactly)
   const double* q2 = nullptr;
-  if (a.use_guess) {  // the exact matvec, also in a many-column solve
+  if (a.use_guess) {
     if (cuda_check(c, copy_cols(x, ldv, a.x, n, n, nrhs, s), "copy guess")) return CPM_ECUDA;
     if (f64) (k_p_update<double><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, st, x, p, (double*)pv, nullptr, 1), note_launch());
-    else (k_p_update<float><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, st, x, p, (float*)pv, plo, 1), note_launch());
-    if (fast) launch_matvec<float>(c, pv, plo, p, ldv, nrhs, q, pq_part, gm_exact, nullptr);
+    else (k_p_update<float><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, st, x, p, (float*)pv, plo, 1, xt), note_launch());
+    if (fast) stream_mv(xt, nullptr);
     else matvec(nullptr);
   }
+  const bool exact_r0 = !(fast && a.use_guess);
   (k_init_r<<<g2, kThreads, 0, s>>>(n, ldv, nrhs, a.b, a.bscale, q, q2, a.use_guess ? 1 : 0, r, x, z,
                                    inv_diag, pre, dots, a.sys), note_launch());
   const int wb = 8;  // warps per block for the per-column reductions
@@ -1348,9 +1350,9 @@ int pcg_solve_kernels(Ctx* c, const SolveArgs& a) {
     return poll(k);  // all_done with the verified flags
   };
   if ((rc = poll(0))) return rc;
-  for (int col = 0; col < nrhs; ++col) {
-    verified[col] = host[col].done == 1;  // exact r0
-    anchor_level[col] = host[col].relres;
+  for (int col = 0; col < nrhs; ++col) {  // an exact r0 is the first anchor
+    verified[col] = exact_r0 && host[col].done == 1;
+    anchor_level[col] = exact_r0 ? host[col].relres : 1.0;
   }
   if (fast && (cuda_check(c, cudaMemcpyAsync(xa, x, vbytes, cudaMemcpyDeviceToDevice, s),
                           "anchor x") ||

@@ -95,8 +95,8 @@ __device__ __forceinline__ void phasor_ff(uint32_t ph, const float4* __restrict_
 // in the column layout of the electrode operand, c(k) = 128 (k / 64) + k % 64, from the
 // exact fixed-point phases.  Sums over the ions run in error-free float pairs (S_K is a
 // sum of O(n_ion) unit phasors whose float partial sums would lose bits; FP64 runs at
-// 1/64 of the float rate here).  The tail k-vectors take float sin/cos (sincos_turns,
-// about one ulp); the head (k < kh, the heaviest weights) takes float-pair phasors and
+// 1/64 of the float rate here).  The tail k-vectors take float sin/cos from the phasor
+// table (sincos_table, about one ulp); the head (k < kh, the heaviest weights) takes float-pair phasors and
 // goes out in FP64 to vhead for the FP64 head contraction.
 __global__ void __launch_bounds__(kSfThreads)
 k_ion_sf_f32(const uint32_t* __restrict__ sion, const double* __restrict__ ion_q, int n_ion,
@@ -144,7 +144,7 @@ k_ion_sf_f32(const uint32_t* __restrict__ sion, const double* __restrict__ ion_q
       for (int t = 0; t < cnt; ++t) {
         const uint32_t ph = h * sf[t][0] + kk * sf[t][1] + l * sf[t][2];
         float s, c;
-        sincos_turns(ph, &s, &c);
+        sincos_table(ph, turn, &s, &c);
         pair_fma(reh, rel, sqh[t], sql[t], c);
         pair_fma(imh, iml, sqh[t], sql[t], s);
       }
@@ -414,6 +414,18 @@ struct RealScreen {
   int all_single; // every box edge above 2 r_c
 };
 
+RealScreen real_screen(const Geometry& geo, double rsplit2) {
+  RealScreen rs;
+  for (int u = 0; u < 3; ++u) rs.fs[u] = (float)(geo.L[u] * 0x1p-32);
+  const double rc2 = geo.rc * geo.rc;
+  rs.screen2 = (float)rc2 + 0.01f;
+  rs.cut2 = (float)(rc2 * (1.0 - 1e-5));
+  rs.far2 = (float)rsplit2;
+  rs.g = (float)geo.g;
+  rs.all_single = 2.0 * geo.rc < geo.L[0] && 2.0 * geo.rc < geo.L[1] && 2.0 * geo.rc < geo.L[2];
+  return rs;
+}
+
 __global__ void __launch_bounds__(kRealWarps * 32, 6)
 k_bsol_real(const double* __restrict__ xyz, const double* __restrict__ alpha,
             const uint32_t* __restrict__ sfix, int n, const double* __restrict__ ion_xyz,
@@ -589,7 +601,8 @@ k_force_kspace(const uint32_t* __restrict__ sion, int n_ion, const int* __restri
                const double* __restrict__ vhead, double lx, double ly, double lz,
                double* __restrict__ grad) {
   __shared__ int sk[kForceChunk][3];
-  __shared__ double sw[kForceChunk][3];  // sqrt(W), v_c, v_s (head: FP64; tail: floats)
+  __shared__ double sw[kForceChunk][3];  // head: sqrt(W), v_c, v_s in FP64
+  __shared__ float swf[kForceChunk][3];  // tail: the same as floats (converted once here)
   const int f = blockIdx.y;
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t* u = sion + ((size_t)f * n_ion + (I < n_ion ? I : 0)) * 3;
@@ -612,8 +625,9 @@ k_force_kspace(const uint32_t* __restrict__ sion, int n_ion, const int* __restri
         sw[t][1] = vh[kcol];
         sw[t][2] = vh[kcol + 64];
       } else {
-        sw[t][1] = (double)vf[kcol];
-        sw[t][2] = (double)vf[kcol + 64];
+        swf[t][0] = (float)sqw[k];
+        swf[t][1] = vf[kcol];
+        swf[t][2] = vf[kcol + 64];
       }
     }
     __syncthreads();
@@ -631,7 +645,7 @@ k_force_kspace(const uint32_t* __restrict__ sion, int n_ion, const int* __restri
       } else {
         float sn, cs;
         sincos_table(ph, turn, &sn, &cs);
-        const float term = (float)sw[t][0] * fmaf((float)sw[t][2], cs, -(float)sw[t][1] * sn);
+        const float term = swf[t][0] * fmaf(swf[t][2], cs, -swf[t][1] * sn);
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
           const float x = term * (float)sk[t][d];  // h, k, l: small integers, exact
@@ -671,7 +685,8 @@ k_force_real(const double* __restrict__ xyz, const double* __restrict__ alpha,
              const uint32_t* __restrict__ sfix, int n, const double* __restrict__ ion_xyz,
              const double* __restrict__ ion_q, const uint32_t* __restrict__ sion, int n_ion,
              const double* __restrict__ q, double lx, double ly, double lz, double g,
-             double rc, int slab, const double* __restrict__ grad_k, double* __restrict__ out) {
+             double rc, const RealScreen rs, int slab, const double* __restrict__ grad_k,
+             double* __restrict__ out) {
   __shared__ uint32_t su[kForceChunk][3];
   __shared__ double sx[kForceChunk][5];  // x, y, z, alpha, q
   __shared__ double red[2][128];
@@ -684,9 +699,7 @@ k_force_real(const double* __restrict__ xyz, const double* __restrict__ alpha,
   const double* qf = q + (size_t)f * n;
   const double L[3] = {lx, ly, lz};
   const double invL[3] = {1.0 / lx, 1.0 / ly, 1.0 / lz};
-  const float fs[3] = {(float)(lx * 0x1p-32), (float)(ly * 0x1p-32), (float)(lz * 0x1p-32)};
   const double rc2 = rc * rc;
-  const float screen2 = (float)rc2 + 0.01f;
   double gr[3] = {0.0, 0.0, 0.0};
   double qz = 0.0, qs = 0.0;  // this thread's share of sum q_i z_i and sum q_i
   for (int base = 0; base < n; base += kForceChunk) {
@@ -711,10 +724,10 @@ k_force_real(const double* __restrict__ xyz, const double* __restrict__ alpha,
       float m2 = 0.f;
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        const float du = (float)(int32_t)(su[t][d] - ui[d]) * fs[d];
+        const float du = (float)(int32_t)(su[t][d] - ui[d]) * rs.fs[d];
         m2 = fmaf(du, du, m2);
       }
-      if (m2 >= screen2) continue;
+      if (m2 >= rs.screen2) continue;
       // every image of the pair within r_c
       double d0[3];
       int lo[3], hi[3];
@@ -850,14 +863,7 @@ void launch_bsol_real_and_finish(const double* xyz, const double* alpha, const u
     }
     lo = hi;
   }
-  RealScreen rs;
-  for (int u = 0; u < 3; ++u) rs.fs[u] = (float)(geo.L[u] * 0x1p-32);
-  const double rc2 = geo.rc * geo.rc;
-  rs.screen2 = (float)rc2 + 0.01f;
-  rs.cut2 = (float)(rc2 * (1.0 - 1e-5));
-  rs.far2 = (float)(lo * lo);
-  rs.g = (float)geo.g;
-  rs.all_single = 2.0 * geo.rc < geo.L[0] && 2.0 * geo.rc < geo.L[1] && 2.0 * geo.rc < geo.L[2];
+  const RealScreen rs = real_screen(geo, lo * lo);
   (k_bsol_real<<<grid, kRealWarps * 32, 0, s>>>(xyz, alpha, sfix, n, ion_xyz, ion_q, sion, n_ion,
                                                geo.L[0], geo.L[1], geo.L[2], geo.g, geo.rc, rs,
                                                dip, chi, bsol_k, b_out, qsol),
@@ -879,8 +885,9 @@ void launch_ion_forces(const double* xyz, const double* alpha, const uint32_t* s
                                        vhead, geo.L[0], geo.L[1], geo.L[2], grad),
    note_launch());
   (k_force_real<<<grid, 128, 0, s>>>(xyz, alpha, sfix, n, ion_xyz, ion_q, sion, n_ion, q,
-                                     geo.L[0], geo.L[1], geo.L[2], geo.g, geo.rc, geo.slab,
-                                     grad, out), note_launch());
+                                     geo.L[0], geo.L[1], geo.L[2], geo.g, geo.rc,
+                                     real_screen(geo, geo.rc * geo.rc), geo.slab, grad, out),
+   note_launch());
 }
 
 }  // namespace cpm
