@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", choices=["scale-point", "precision", "batch", "learned",
-                                           "matvec", "scale", "scale-learned"],
+                                           "matvec", "scale", "scale-learned", "build"],
                     default="scale-point")
     ap.add_argument("--rhs", type=int, default=1,
                     help="directions per matvec (matvec workload), frames per step (scale)")
@@ -68,6 +68,12 @@ def parse():
     ap.add_argument("--heldout-frames", type=int, default=2000)
     ap.add_argument("--epochs", type=int, default=3)
     ap.add_argument("--frames", type=int, default=256, help="frames per batch (batch workload)")
+    ap.add_argument("--stack", type=int, nargs=2, default=[90, 52], metavar=("NX", "NY"),
+                    help="build workload: cells of each of the six stacked sheets (90 52: the "
+                         "scale point's electrode)")
+    ap.add_argument("--stream", action="store_true",
+                    help="matvec workload: time the streamed 16-column matvec inside a PCG solve "
+                         "of --rhs random right-hand sides instead of cpm_apply_E")
     ap.add_argument("--matrix-path", action="store_true",
                     help="batch workload: also time the matrix path (S formed once, q = S b)")
     ap.add_argument("--baseline-frames", type=int, default=None,
@@ -528,13 +534,22 @@ def run_matvec(args, rank, world, local_rank):
     rng = np.random.default_rng(wl.seed_for(2, rank))
     p = torch.tensor(rng.standard_normal((args.rhs, n)), device=dev)
     q = torch.empty_like(p)
-    for _ in range(args.warmup):
+
+    def once():
+        if args.stream:  # the PCG iterations' streamed matvec, per launch
+            q.zero_()
+            _, it, _ = ctx.cpm_solve(p, q, tol=1e-6, maxit=500)
+            inf = ctx.cpm_get_info()
+            return inf["t_solve_matvec_ms"] / max(1, int(np.max(it)))
         ctx.cpm_apply_E(p, q)
+        return ctx.cpm_get_info()["t_matvec_ms"]
+
+    for _ in range(args.warmup):
+        once()
     ms = []
     with ClockSampler(local_rank) as clocks:
         for _ in range(args.steps):
-            ctx.cpm_apply_E(p, q)
-            ms.append(ctx.cpm_get_info()["t_matvec_ms"])
+            ms.append(once())
     ms = max_over_ranks(statistics.median(ms), world)
     if rank != 0:
         return
@@ -546,10 +561,72 @@ def run_matvec(args, rank, world, local_rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": f"matvec: two-sheet graphene N={n}, {args.rhs} right-hand "
-                                   f"side(s) per pass, E {e_bytes / 1e6:.0f} MB",
+                                   f"side(s) per pass, E {e_bytes / 1e6:.0f} MB"
+                                   + (", the streamed matvec of PCG iterations"
+                                      if args.stream else ""),
                        "l2": "E larger than L2" if e_bytes > 129e6 else "E fits in L2"},
             "roofline": {"bound": "hbm", "achieved": gbs / world, "peak": peak, "unit": "GB/s",
                          "frac": gbs / world / peak, "traffic": None},
+            "clocks": clocks.summary()}
+    print(json.dumps(line), flush=True)
+
+
+def run_build(args, rank, world, local_rank):
+    """The E build alone (cpm_build_E: operand, head, tensor-core tail, PCG-DC, d) of the
+    scale point's electrode or a smaller one of the same kind (six stacked sheets of
+    --stack NX NY cells with 5% pinholes, g = 0.15, r_c = 24), timed with CUDA events; the
+    tail's method-FLOP roofline against the sustained BF16 rate."""
+    import torch
+
+    from paper_2111_06704_gb300 import cpm
+
+    torch.cuda.set_device(local_rank)
+    rng = np.random.default_rng(wl.seed_for(5, rank))
+    el = wl.stacked_electrode(rng, nx=args.stack[0], ny=args.stack[1])
+    n = el.n
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = cpm.Context(el.box, stream=stream.cuda_stream, g_ewald=SCALE_G, rcut_real=SCALE_RC)
+    for _ in range(args.warmup):
+        ctx.cpm_build_E(el.xyz, el.alpha)
+    ts, tcs = [], []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clocks:
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            e0.record(stream)
+            ctx.cpm_build_E(el.xyz, el.alpha)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            inf = ctx.cpm_get_info()
+            ts.append(e0.elapsed_time(e1))
+            tcs.append(inf["t_tc_ms"])
+    ms = max_over_ranks(statistics.median(ts), world)
+    if rank != 0:
+        return
+    peaks, src = measured_peaks()
+    sustained = peaks.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"])
+    n6, n3, n1 = inf["tc_blocks"]
+    tail_cols = 64 * (n6 + n3 + n1)
+    tc_ms = statistics.median(tcs)
+    achieved = 2.0 * (n * (n + 1) / 2) * tail_cols / (tc_ms * 1e-3) / 1e12
+    line = {"metric": "E builds/s", "value": world * 1000.0 / ms, "unit": "builds/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16x6+fp16x3+fp8 (f32-accurate E)", "data": "synthetic",
+            "config": {"workload": f"E build: six stacked {args.stack[0]} x {args.stack[1]}-cell "
+                                   f"graphene sheets with pinholes, N={n}, g={SCALE_G}, "
+                                   f"r_c={SCALE_RC}", "electrode_atoms": n,
+                       "kvectors": inf["m"]},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": sustained,
+                         "unit": "TFLOP/s", "frac": achieved / sustained, "traffic": None,
+                         "kernel": "k_ek_strip (tcgen05 k-space tail)",
+                         "work": "method FLOPs: N(N+1)/2 x 2 x tail operand columns "
+                                 f"({tail_cols})", "tc_ms": tc_ms,
+                         "peak_source": f"{src} bf16_tflops_sustained (of measured)"},
+            "build_ms": {"kspace": inf["t_kspace_ms"], "head": inf["t_head_ms"],
+                         "tensor_core": tc_ms, "precond": inf["t_precond_ms"],
+                         "d_solve": inf["t_dsolve_ms"]},
             "clocks": clocks.summary()}
     print(json.dumps(line), flush=True)
 
@@ -1256,8 +1333,8 @@ def run_scale_point(args, rank, world, local_rank):
         "mean_iters": statistics.mean(iters),
         "previous_step_guess_iters": float(np.mean(it_prev)),
         "q_rel_err_vs_tight_solve": q_err,
-        "roofline": step_roof,
-        "build_roofline": roof,
+        "roofline": roof,
+        "step_roofline": step_roof,
         "matvec_roofline": {"bound": "hbm", "kernel": "k_matvec_f32 (PCG matvec, E streamed "
                             "once per pass of up to four columns)",
                             "achieved": mv_gbs[1], "peak": hbm, "unit": "GB/s",
@@ -1423,6 +1500,8 @@ def main():
         run_scale_learned(args, rank, world, local_rank)
     elif args.workload == "precision":
         run_ours(args, rank, world, local_rank)
+    elif args.workload == "build":
+        run_build(args, rank, world, local_rank)
     else:
         run_scale_point(args, rank, world, local_rank)
     if world > 1:

@@ -404,6 +404,16 @@ int cpm_guess_save(const char* path, const float* params, const float* norm,
                    float target_scale);
 int cpm_guess_load(const char* path, float* params, float* norm, float* target_scale);
 
+/* One training step in one call: the gradient of the mean squared error on `samples`
+ * samples (as cpm_mlp_grad, into the device buffers grad[CPM_MLP_PARAMS] and loss[1]),
+ * then one Adam step on params with moments m, v (as cpm_mlp_adam, step >= 1).  When
+ * loss_out (host) is not NULL it receives the mean squared error before the step.  All
+ * other arrays are device arrays; CPM_EINVAL for host pointers, samples < 1 or step < 1. */
+int cpm_guess_train_step(cpm_ctx* c, float* params, const float* norm, int bf16,
+                         int64_t samples, const float* feat, const float* target, float* m,
+                         float* v, float* grad, double* loss, int step, float lr,
+                         double* loss_out);
+
 /* q0[k] = q_prev[k] + scale * y[k] for k < len. */
 int cpm_guess_apply(cpm_ctx* c, int64_t len, const float* y, float scale, const double* q_prev,
                     double* q0);

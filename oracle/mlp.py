@@ -175,3 +175,15 @@ def features(b, b_prev, chi, xyz, box, nbrs, p_dc):
     f[:, 19] = np.where(z > z.mean(), 1.0, -1.0)
     f[:, 20] = (np.asarray(p_dc, dtype=np.float64) @ db) / KE
     return f
+
+
+def adam_step(params, m, v, grad, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step (Kingma and Ba, Algorithm 1) in FP64: the moving moments of the
+    gradient and its square, their bias corrections for step >= 1, and the update
+    lr m_hat / (sqrt(v_hat) + eps).  Returns the new (params, m, v)."""
+    g = np.asarray(grad, dtype=np.float64)
+    m = beta1 * np.asarray(m, dtype=np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, dtype=np.float64) + (1.0 - beta2) * g * g
+    m_hat = m / (1.0 - beta1 ** step)
+    v_hat = v / (1.0 - beta2 ** step)
+    return np.asarray(params, dtype=np.float64) - lr * m_hat / (np.sqrt(v_hat) + eps), m, v

@@ -124,7 +124,7 @@ EXPORTS = ["cpm_default_params", "cpm_create", "cpm_destroy", "cpm_build_E", "cp
            "cpm_guess", "cpm_release_workspace", "cpm_plan_kspace", "cpm_gcd_setup",
            "cpm_gcd_charges", "cpm_smatrix_build", "cpm_smatrix_charges",
            "cpm_build_E_copy", "cpm_guess_init", "cpm_guess_norm", "cpm_guess_save",
-           "cpm_guess_load", "cpm_ion_forces"]
+           "cpm_guess_load", "cpm_ion_forces", "cpm_guess_train_step"]
 
 _lib = None
 
@@ -177,6 +177,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.cpm_mlp_forward.argtypes = [vp, vp, vp, i, i64, vp, vp]
     lib.cpm_mlp_grad.argtypes = [vp, vp, vp, i, i64, vp, vp, vp, vp]
     lib.cpm_mlp_adam.argtypes = [vp, vp, vp, vp, vp, i, ctypes.c_float]
+    lib.cpm_guess_train_step.argtypes = [vp, vp, vp, i, i64, vp, vp, vp, vp, vp, vp, i,
+                                         ctypes.c_float, vp]
     lib.cpm_guess_apply.argtypes = [vp, i64, vp, ctypes.c_float, vp, vp]
     lib.cpm_guess.argtypes = [vp, vp, vp, i, i, vp, vp, vp, ctypes.c_float, vp, vp]
     lib.cpm_apply_E.argtypes = [vp, i, vp, vp]

@@ -610,6 +610,43 @@ int cpm_mlp_adam(cpm_ctx* c, float* params, float* m, float* v, const float* gra
   return cuda_check(c, cudaGetLastError(), "adam");
 }
 
+int cpm_guess_train_step(cpm_ctx* c, float* params, const float* norm, int bf16,
+                         int64_t samples, const float* feat, const float* target, float* m,
+                         float* v, float* grad, double* loss, int step, float lr,
+                         double* loss_out) {
+  if (!c) return CPM_EINVAL;
+  if (samples < 1 || step < 1 || !dev_ok(c, params) || !dev_ok(c, norm) ||
+      !dev_ok(c, feat) || !dev_ok(c, target) || !dev_ok(c, m) || !dev_ok(c, v) ||
+      !dev_ok(c, grad) || !dev_ok(c, loss))
+    return set_err(c, CPM_EINVAL,
+                   "cpm_guess_train_step: samples >= 1, step >= 1 and device arrays");
+  int st = cuda_check(c, cudaMemsetAsync(grad, 0, kP * sizeof(float), c->stream), "grad zero");
+  if (!st) st = cuda_check(c, cudaMemsetAsync(loss, 0, sizeof(double), c->stream), "loss zero");
+  if (!st) st = cuda_check(c, cudaFuncSetAttribute(k_mlp_grad,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)kGradSmem), "grad smem");
+  if (st) return st;
+  const int64_t blocks = (samples + kB - 1) / kB;
+  (k_mlp_grad<<<(unsigned)blocks, kB, kGradSmem, c->stream>>>(
+       params, norm, bf16, samples, 1.0 / (double)samples, feat, target, grad, loss),
+   note_launch());
+  const float c1 = 1.0f / (1.0f - powf(0.9f, (float)step));
+  const float c2 = 1.0f / (1.0f - powf(0.999f, (float)step));
+  (k_adam<<<(kP + 255) / 256, 256, 0, c->stream>>>(params, m, v, grad, kP, lr, c1, c2),
+   note_launch());
+  if ((st = cuda_check(c, cudaGetLastError(), "train step"))) return st;
+  if (loss_out) {
+    double l = 0.0;
+    if ((st = cuda_check(c, cudaMemcpyAsync(&l, loss, sizeof(double), cudaMemcpyDeviceToHost,
+                                            c->stream), "train step loss")))
+      return st;
+    if ((st = cuda_check(c, cudaStreamSynchronize(c->stream), "train step sync"))) return st;
+    *loss_out = l / (double)samples;
+    return CPM_OK;
+  }
+  return cuda_check(c, cudaStreamSynchronize(c->stream), "train step sync");
+}
+
 int cpm_guess_apply(cpm_ctx* c, int64_t len, const float* y, float scale, const double* q_prev,
                     double* q0) {
   if (!c) return CPM_EINVAL;

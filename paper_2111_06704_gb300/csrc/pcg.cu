@@ -172,30 +172,84 @@ k_matvec_f32(const float* __restrict__ E, int64_t ldE, int n, const float* __res
   for (int i = 0; i < RB; ++i)
 #pragma unroll
     for (int r = 0; r < NR; ++r) part[i][r] = perr[i][r] = 0.f;
-  for (int g = sub; g < ngroups; g += WS) {
-    const int64_t cc = (int64_t)g * 128 + lane * 4;
-    float ev[RB][4];
+  if constexpr (NR % 2 == 0) {
+    // columns in pairs: the same operations on float pairs, two IEEE results an
+    // instruction (a - b as fma(b, -1, a)), so every value is the scalar path's
+    const float2 m1 = make_float2(-1.f, -1.f);
+    float2 part2[RB][NR / 2], perr2[RB][NR / 2];
 #pragma unroll
     for (int i = 0; i < RB; ++i)
-      *reinterpret_cast<float4*>(ev[i]) = __ldcs(reinterpret_cast<const float4*>(erow[i] + cc));
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      const int64_t o = (int64_t)(c0 + r) * ldv + cc;
-      float hv[4], lv[4];
-      *reinterpret_cast<float4*>(hv) = __ldg(reinterpret_cast<const float4*>(pv + o));
-      *reinterpret_cast<float4*>(lv) = __ldg(reinterpret_cast<const float4*>(plo + o));
+      for (int r = 0; r < NR / 2; ++r) part2[i][r] = perr2[i][r] = make_float2(0.f, 0.f);
+    for (int g = sub; g < ngroups; g += WS) {
+      const int64_t cc = (int64_t)g * 128 + lane * 4;
+      float ev[RB][4];
 #pragma unroll
       for (int i = 0; i < RB; ++i)
+        *reinterpret_cast<float4*>(ev[i]) = __ldcs(reinterpret_cast<const float4*>(erow[i] + cc));
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-          const float e = ev[i][w];
-          const float pr = e * hv[w];
-          const float s = part[i][r] + pr;
-          const float bb = s - part[i][r];
-          const float e2 = (part[i][r] - (s - bb)) + (pr - bb);
-          perr[i][r] = fmaf(e, lv[w], perr[i][r] + (fmaf(e, hv[w], -pr) + e2));
-          part[i][r] = s;
-        }
+      for (int rp = 0; rp < NR / 2; ++rp) {
+        const int64_t o0 = (int64_t)(c0 + 2 * rp) * ldv + cc, o1 = o0 + ldv;
+        float h0[4], l0[4], h1[4], l1[4];
+        *reinterpret_cast<float4*>(h0) = __ldg(reinterpret_cast<const float4*>(pv + o0));
+        *reinterpret_cast<float4*>(l0) = __ldg(reinterpret_cast<const float4*>(plo + o0));
+        *reinterpret_cast<float4*>(h1) = __ldg(reinterpret_cast<const float4*>(pv + o1));
+        *reinterpret_cast<float4*>(l1) = __ldg(reinterpret_cast<const float4*>(plo + o1));
+#pragma unroll
+        for (int i = 0; i < RB; ++i)
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            const float2 e2 = make_float2(ev[i][w], ev[i][w]);
+            const float2 ne2 = make_float2(-ev[i][w], -ev[i][w]);
+            const float2 h2 = make_float2(h0[w], h1[w]), l2 = make_float2(l0[w], l1[w]);
+            float2& P = part2[i][rp];
+            float2& Q = perr2[i][rp];
+            const float2 pr = __fmul2_rn(e2, h2);
+            const float2 s = __fadd2_rn(P, pr);
+            const float2 bb = __ffma2_rn(P, m1, s);                              // s - P
+            const float2 t2 = __ffma2_rn(__ffma2_rn(bb, m1, s), m1, P);          // P - (s - bb)
+            const float2 er = __fadd2_rn(t2, __ffma2_rn(bb, m1, pr));            // + (pr - bb)
+            const float2 npe = __ffma2_rn(ne2, h2, pr);                          // pr - e h
+            Q = __ffma2_rn(e2, l2, __fadd2_rn(Q, __ffma2_rn(npe, m1, er)));
+            P = s;
+          }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+#pragma unroll
+      for (int rp = 0; rp < NR / 2; ++rp) {
+        part[i][2 * rp] = part2[i][rp].x;
+        part[i][2 * rp + 1] = part2[i][rp].y;
+        perr[i][2 * rp] = perr2[i][rp].x;
+        perr[i][2 * rp + 1] = perr2[i][rp].y;
+      }
+  } else {  // one column at a time
+    for (int g = sub; g < ngroups; g += WS) {
+      const int64_t cc = (int64_t)g * 128 + lane * 4;
+      float ev[RB][4];
+#pragma unroll
+      for (int i = 0; i < RB; ++i)
+        *reinterpret_cast<float4*>(ev[i]) = __ldcs(reinterpret_cast<const float4*>(erow[i] + cc));
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        const int64_t o = (int64_t)(c0 + r) * ldv + cc;
+        float hv[4], lv[4];
+        *reinterpret_cast<float4*>(hv) = __ldg(reinterpret_cast<const float4*>(pv + o));
+        *reinterpret_cast<float4*>(lv) = __ldg(reinterpret_cast<const float4*>(plo + o));
+#pragma unroll
+        for (int i = 0; i < RB; ++i)
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            const float e = ev[i][w];
+            const float pr = e * hv[w];
+            const float s = part[i][r] + pr;
+            const float bb = s - part[i][r];
+            const float e2 = (part[i][r] - (s - bb)) + (pr - bb);
+            perr[i][r] = fmaf(e, lv[w], perr[i][r] + (fmaf(e, hv[w], -pr) + e2));
+            part[i][r] = s;
+          }
+      }
     }
   }
 #pragma unroll
@@ -309,11 +363,13 @@ k_matvec_stream(const __grid_constant__ CUtensorMap emap, StreamArgs a) {
     s_issued = 0;
   }
   __syncthreads();
-  float acc[8][kFastCols];
+  // acc[r][j]: columns 2 j and 2 j + 1 of row l + 32 r, updated by paired FMAs (two
+  // IEEE fmas in one instruction: half the issue slots of scalar ones)
+  float2 acc[8][kFastCols / 2];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int cc = 0; cc < kFastCols; ++cc) acc[i][cc] = 0.f;
+    for (int j = 0; j < kFastCols / 2; ++j) acc[i][j] = make_float2(0.f, 0.f);
   // stage i into its slot once every warp has released the slot's previous stage
   const uint64_t pol = tid == 0 ? l2_evict_first() : 0;
   const float* xg = a.xt + (int64_t)grp * a.ldv * kFastCols;
@@ -359,8 +415,10 @@ k_matvec_stream(const __grid_constant__ CUtensorMap emap, StreamArgs a) {
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
           const float ev = kk == 0 ? e[r].x : kk == 1 ? e[r].y : kk == 2 ? e[r].z : e[r].w;
+          const float2 e2 = make_float2(ev, ev);
 #pragma unroll
-          for (int cc = 0; cc < kFastCols; ++cc) acc[r][cc] = fmaf(ev, xv[cc], acc[r][cc]);
+          for (int j = 0; j < kFastCols / 2; ++j)
+            acc[r][j] = __ffma2_rn(e2, make_float2(xv[2 * j], xv[2 * j + 1]), acc[r][j]);
         }
       }
     }
@@ -383,7 +441,8 @@ k_matvec_stream(const __grid_constant__ CUtensorMap emap, StreamArgs a) {
   for (int r = 0; r < 8; ++r)
 #pragma unroll
     for (int cc = 0; cc < kFastCols; ++cc)
-      red[warp * kStOut + (r * kFastCols + cc) * 32 + lane] = acc[r][cc];
+      red[warp * kStOut + (r * kFastCols + cc) * 32 + lane] =
+          (cc & 1) ? acc[r][cc >> 1].y : acc[r][cc >> 1].x;
   __syncthreads();
   double v[kStOut / (kStWarps * 32)];  // outputs o = tid + 256 m
 #pragma unroll

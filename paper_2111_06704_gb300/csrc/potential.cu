@@ -141,13 +141,28 @@ k_ion_sf_f32(const uint32_t* __restrict__ sion, const double* __restrict__ ion_q
         ff_add(imh, iml, ph_, pl_, imh, iml);
       }
     } else {
+      // the cos and sin sums as one float pair each (paired float instructions, two IEEE
+      // results an instruction: the values of pair_fma on each)
+      float2 hh = make_float2(reh, imh), ll = make_float2(rel, iml);
+      const float2 m1 = make_float2(-1.f, -1.f);
       for (int t = 0; t < cnt; ++t) {
         const uint32_t ph = h * sf[t][0] + kk * sf[t][1] + l * sf[t][2];
         float s, c;
         sincos_table(ph, turn, &s, &c);
-        pair_fma(reh, rel, sqh[t], sql[t], c);
-        pair_fma(imh, iml, sqh[t], sql[t], s);
+        const float2 x = make_float2(c, s), qh = make_float2(sqh[t], sqh[t]);
+        const float2 p = __fmul2_rn(qh, x);
+        const float2 pe = __ffma2_rn(qh, x, __fmul2_rn(p, m1));                  // qh x - p
+        const float2 s2 = __fadd2_rn(hh, p);
+        const float2 bb = __ffma2_rn(hh, m1, s2);                                // s2 - h
+        const float2 a = __ffma2_rn(__ffma2_rn(bb, m1, s2), m1, hh);             // h - (s2 - bb)
+        const float2 e = __fadd2_rn(a, __ffma2_rn(bb, m1, p));                   // + (p - bb)
+        ll = __fadd2_rn(ll, __fadd2_rn(e, __ffma2_rn(make_float2(sql[t], sql[t]), x, pe)));
+        hh = s2;
       }
+      reh = hh.x;
+      imh = hh.y;
+      rel = ll.x;
+      iml = ll.y;
     }
   }
   if (k >= mpad) return;
@@ -270,7 +285,8 @@ k_bsol_kspace(const T* __restrict__ A, int n, int64_t lda, const T* __restrict__
 // and the terms summed in error-free float pairs.  One thread per electrode atom and up to
 // kDirectFrames frames per block: each phasor is formed once and used for every frame of
 // the block; the k-vectors of a chunk and their structure factors are staged in shared
-// memory.
+// memory.  Frames go in pairs through paired float instructions (two IEEE results an
+// instruction, a - b as fma(b, -1, a)): the values are those of one frame at a time.
 constexpr int kDirectChunk = 128;
 constexpr int kDirectFrames = 16;
 
@@ -280,7 +296,8 @@ k_bsol_kspace_direct(const uint32_t* __restrict__ sfix, int n, const int* __rest
                      const float4* __restrict__ turn, const float* __restrict__ v, int frames,
                      double* __restrict__ bsol) {
   __shared__ uint32_t sh[kDirectChunk][3];
-  __shared__ float2 sv[kDirectChunk][kDirectFrames];  // sqrt(W) (v_cos, v_sin) per frame
+  // sqrt(W) (v_cos, v_sin) of frames 2 p and 2 p + 1: (c_2p, c_2p+1, s_2p, s_2p+1)
+  __shared__ float4 sv[kDirectChunk][kDirectFrames / 2];
   const int f0 = blockIdx.y * kDirectFrames;
   const int nf = min(kDirectFrames, frames - f0);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -290,9 +307,10 @@ k_bsol_kspace_direct(const uint32_t* __restrict__ sfix, int n, const int* __rest
     u1 = sfix[3 * i + 1];
     u2 = sfix[3 * i + 2];
   }
-  float hi[kDirectFrames], lo[kDirectFrames];
+  float2 hi[kDirectFrames / 2], lo[kDirectFrames / 2];
 #pragma unroll
-  for (int f = 0; f < kDirectFrames; ++f) hi[f] = lo[f] = 0.f;
+  for (int f = 0; f < kDirectFrames / 2; ++f) hi[f] = lo[f] = make_float2(0.f, 0.f);
+  const float2 m1 = make_float2(-1.f, -1.f);
   for (int k0 = kh; k0 < mpad; k0 += kDirectChunk) {
     const int cnt = min(kDirectChunk, mpad - k0);
     __syncthreads();
@@ -302,38 +320,50 @@ k_bsol_kspace_direct(const uint32_t* __restrict__ sfix, int n, const int* __rest
       sh[t][1] = (uint32_t)hkl[3 * k + 1];
       sh[t][2] = (uint32_t)hkl[3 * k + 2];
     }
-    for (int e = threadIdx.x; e < cnt * kDirectFrames; e += blockDim.x) {
-      const int t = e / kDirectFrames, f = e % kDirectFrames;
+    for (int e = threadIdx.x; e < cnt * (kDirectFrames / 2); e += blockDim.x) {
+      const int t = e / (kDirectFrames / 2), fp = e % (kDirectFrames / 2);
       const int k = k0 + t;
       const size_t kcol = 128 * (size_t)(k >> 6) + (k & 63);
       const float w = (float)sqw[k];
-      float2 val = make_float2(0.f, 0.f);
-      if (f < nf) {
-        const float* vf = v + (size_t)(f0 + f) * 2 * mpad;
-        val = make_float2(w * vf[kcol], w * vf[kcol + 64]);
+      float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (2 * fp < nf) {
+        const float* vf = v + (size_t)(f0 + 2 * fp) * 2 * mpad;
+        val.x = w * vf[kcol];
+        val.z = w * vf[kcol + 64];
       }
-      sv[t][f] = val;
+      if (2 * fp + 1 < nf) {
+        const float* vf = v + (size_t)(f0 + 2 * fp + 1) * 2 * mpad;
+        val.y = w * vf[kcol];
+        val.w = w * vf[kcol + 64];
+      }
+      sv[t][fp] = val;
     }
     __syncthreads();
     if (i >= n) continue;
     for (int t = 0; t < cnt; ++t) {
       float sn, cs;
       sincos_table(sh[t][0] * u0 + sh[t][1] * u1 + sh[t][2] * u2, turn, &sn, &cs);
+      const float2 sn2 = make_float2(sn, sn), cs2 = make_float2(cs, cs);
 #pragma unroll
-      for (int f = 0; f < kDirectFrames; ++f) {
-        const float2 vv = sv[t][f];
-        const float term = fmaf(sn, vv.y, cs * vv.x);
-        const float s2 = hi[f] + term;
-        const float bb = s2 - hi[f];
-        lo[f] += (hi[f] - (s2 - bb)) + (term - bb);
+      for (int f = 0; f < kDirectFrames / 2; ++f) {
+        const float4 vv = sv[t][f];
+        const float2 term = __ffma2_rn(sn2, make_float2(vv.z, vv.w),
+                                       __fmul2_rn(cs2, make_float2(vv.x, vv.y)));
+        const float2 s2 = __fadd2_rn(hi[f], term);
+        const float2 bb = __ffma2_rn(hi[f], m1, s2);                          // s2 - hi
+        const float2 a = __ffma2_rn(__ffma2_rn(bb, m1, s2), m1, hi[f]);       // hi - (s2 - bb)
+        lo[f] = __fadd2_rn(lo[f], __fadd2_rn(a, __ffma2_rn(bb, m1, term)));   // + (term - bb)
         hi[f] = s2;
       }
     }
   }
   if (i < n)
 #pragma unroll
-    for (int f = 0; f < kDirectFrames; ++f)
-      if (f < nf) bsol[(size_t)(f0 + f) * n + i] = (double)hi[f] + (double)lo[f];
+    for (int f = 0; f < kDirectFrames; ++f) {
+      const float h = (f & 1) ? hi[f >> 1].y : hi[f >> 1].x;
+      const float l = (f & 1) ? lo[f >> 1].y : lo[f >> 1].x;
+      if (f < nf) bsol[(size_t)(f0 + f) * n + i] = (double)h + (double)l;
+    }
 }
 
 // FP64 real-space sum of one electrode-ion pair over every image within r_c:

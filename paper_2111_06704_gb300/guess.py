@@ -73,6 +73,18 @@ class LearnedGuess:
                                               _vp(self.v), _vp(self.grad), self.step,
                                               ctypes.c_float(lr)))
 
+    def train_step(self, feat, target, lr):
+        """Gradient and Adam step in one library call; returns the batch's mean squared
+        error before the step."""
+        s = feat.numel() // N_FEATURES
+        self.step += 1
+        loss = ctypes.c_double(0.0)
+        self.ctx._check(self.lib.cpm_guess_train_step(
+            self.ctx.h, _vp(self.params), _vp(self.norm), self.bf16, ctypes.c_int64(s),
+            _vp(feat), _vp(target), _vp(self.m), _vp(self.v), _vp(self.grad), _vp(self.loss),
+            self.step, ctypes.c_float(lr), ctypes.byref(loss)))
+        return loss.value
+
     def guess(self, feat, q_prev):
         import torch
         y = self.forward(feat)
@@ -134,8 +146,7 @@ class LearnedGuess:
         for ep in range(epochs):
             for b0 in rng.permutation(starts):
                 b1 = min(s, b0 + batch)
-                losses.append(self.gradient(feat[b0:b1], target[b0:b1]))
-                self.adam(lr)
+                losses.append(self.train_step(feat[b0:b1], target[b0:b1], lr))
             if log:
                 log(f"epoch {ep}: loss {np.mean(losses[-len(starts):]):.4e}")
         return losses

@@ -90,6 +90,34 @@ def test_forward_and_gradient_match_the_oracle(walk, bf16):
         assert np.abs(y_gpu - y32).max() <= 1e-3 * np.abs(y32).max() * 20
 
 
+def test_one_call_training_step_against_the_oracle(walk):
+    # cpm_guess_train_step: the gradient of the batch's mean squared error, then one Adam
+    # step, against the oracle's backpropagation and Adam step in FP64.  Where a gradient
+    # component stands clear of zero the first step is lr sign(g) (closed form of the
+    # oracle pin), so the parameters must agree to the gradient's float error; elsewhere
+    # each move is at most lr.
+    ctx = walk[0]
+    rng = np.random.default_rng(11)
+    g = LearnedGuess(ctx, seed=5)
+    p = mlp.init_params(rng, scale=0.8).astype(np.float32)
+    g.params = _dev(p, torch.float32)
+    s, lr = 1000, 1e-3
+    x = rng.standard_normal((s, mlp.N_FEATURES)).astype(np.float32)
+    t = rng.standard_normal(s).astype(np.float32)
+    loss = g.train_step(_dev(x, torch.float32), _dev(t, torch.float32), lr)
+    p1 = g.params.cpu().numpy().astype(np.float64)
+    loss_ref, grad_ref = mlp.loss_and_grad(p.astype(np.float64), x.astype(np.float64),
+                                           t.astype(np.float64))
+    p_ref, _, _ = mlp.adam_step(p, np.zeros_like(grad_ref), np.zeros_like(grad_ref),
+                                grad_ref, 1, lr)
+    assert loss == pytest.approx(loss_ref, rel=1e-5)
+    clear = np.abs(grad_ref) > 1e-3 * np.abs(grad_ref).max()
+    assert clear.sum() > 1000
+    assert np.abs(p1 - p_ref)[clear].max() <= 1e-6 + 1e-6 * lr
+    assert np.all(np.abs(p1 - p) <= lr * (1 + 1e-5) + 1e-7)
+    assert g.step == 1
+
+
 def test_trained_guess_beats_the_previous_step(walk):
     ctx, work, b, qb = walk
     el = work.electrode

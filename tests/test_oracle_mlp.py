@@ -130,3 +130,20 @@ def test_normalisation_small_case():
     assert ts == 1.0
     _, ts0 = mlp.normalisation(feat, np.zeros(4))
     assert ts0 == 1.0
+
+
+def test_adam_first_steps_closed_form():
+    # From zero moments the bias corrections make the first step lr g / (|g| + eps), i.e.
+    # lr sign(g) where |g| >> eps; a constant gradient keeps m_hat = g and v_hat = g^2 at
+    # every later step, so each step moves by the same amount.
+    g = np.array([3.0, -2e-3, 0.0, 1e-9])
+    p0 = np.array([1.0, 1.0, 1.0, 1.0])
+    p1, m, v = mlp.adam_step(p0, np.zeros(4), np.zeros(4), g, 1, 0.01)
+    assert np.allclose(p1, p0 - 0.01 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
+    assert p1[0] == pytest.approx(0.99, abs=1e-10) and p1[1] == pytest.approx(1.01, abs=1e-7)
+    assert p1[2] == 1.0
+    p, mm, vv = p0, np.zeros(4), np.zeros(4)
+    for step in range(1, 6):
+        prev = p
+        p, mm, vv = mlp.adam_step(p, mm, vv, g, step, 0.01)
+        assert np.allclose(p - prev, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=1e-15)
