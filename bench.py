@@ -33,11 +33,6 @@ if ROOT not in sys.path:
 from paper_2111_06704_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "charge solves/s at 1e-6 rel. residual & E-build s, vs plain FP64 PCG same GPU"
-# DRAM bytes (read + write) per element of E of one k_matvec_stream launch, from the ncu
-# capture of that kernel on a 25,600-atom case (16 columns),
-# scaled to a full launch by N^2; None until a capture of the current kernel exists.
-STREAM_TRAFFIC_PER_ELEMENT = None
-STREAM_TRAFFIC_NOTE = "no capture of the current kernel yet"
 TOL = 1e-6
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 SMS = 152
@@ -71,6 +66,8 @@ def parse():
     ap.add_argument("--stack", type=int, nargs=2, default=[90, 52], metavar=("NX", "NY"),
                     help="build workload: cells of each of the six stacked sheets (90 52: the "
                          "scale point's electrode)")
+    ap.add_argument("--sheets", type=int, default=6,
+                    help="build workload: stacked sheets (6: the scale point's electrode)")
     ap.add_argument("--stream", action="store_true",
                     help="matvec workload: time the streamed 16-column matvec inside a PCG solve "
                          "of --rhs random right-hand sides instead of cpm_apply_E")
@@ -85,6 +82,25 @@ def parse():
     if args.baseline_frames is None:
         args.baseline_frames = 2 if args.workload == "scale-point" else 16
     return args
+
+
+def stream_traffic():
+    """DRAM bytes (read + write) per element of E of one k_matvec_stream launch, read from
+    the committed summary of that kernel's ncu capture (a 25,992-atom case, 16 columns);
+    the bench scales it to a full launch by N^2.  (None, note) when the summary is absent."""
+    import re
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles",
+                        "k_matvec_stream_N25992.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None, "no capture summary"
+    m = re.search(r"DRAM bytes per element of E \(read \+ write\)[^|]*\|\s*([0-9.]+)", text)
+    if not m:
+        return None, "no traffic figure in the capture summary"
+    return float(m.group(1)), ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                               "launch at N=25,992 (profiles/k_matvec_stream_N25992.md), "
+                               "per element of E, times N^2")
 
 
 def measured_peaks():
@@ -582,7 +598,7 @@ def run_build(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     rng = np.random.default_rng(wl.seed_for(5, rank))
-    el = wl.stacked_electrode(rng, nx=args.stack[0], ny=args.stack[1])
+    el = wl.stacked_electrode(rng, nx=args.stack[0], ny=args.stack[1], sheets=args.sheets)
     n = el.n
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
@@ -614,7 +630,8 @@ def run_build(args, rank, world, local_rank):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16x6+fp16x3+fp8 (f32-accurate E)", "data": "synthetic",
-            "config": {"workload": f"E build: six stacked {args.stack[0]} x {args.stack[1]}-cell "
+            "config": {"workload": f"E build: {args.sheets} stacked {args.stack[0]} x "
+                                   f"{args.stack[1]}-cell "
                                    f"graphene sheets with pinholes, N={n}, g={SCALE_G}, "
                                    f"r_c={SCALE_RC}", "electrode_atoms": n,
                        "kvectors": inf["m"]},
@@ -869,15 +886,17 @@ def run_ragged(args, rank, dev, stream, timed):
         for k, (c, (x, qi, chi)) in enumerate(zip(ctxs, ins)):
             c.cpm_potential(x, qi, chi, b[offs[k]:offs[k + 1]].view(1, -1), qs[k:k + 1])
 
-    def batched():
-        potentials()
+    def batched(with_b=True):
+        if with_b:
+            potentials()
         q.zero_()
         _, it, _ = batch.solve(b, q, tol=TOL, maxit=2000)
         batch.neutralize(q, qs)
         its["batch"] = float(np.mean(it))
 
-    def one_by_one():
-        potentials()
+    def one_by_one(with_b=True):
+        if with_b:
+            potentials()
         q.zero_()
         it_all = []
         for k, c in enumerate(ctxs):
@@ -892,6 +911,8 @@ def run_ragged(args, rank, dev, stream, timed):
     ms_batch = timed(batched, 2)
     ms_single = timed(one_by_one, 2)
     pot_ms = timed(potentials, 2)
+    ms_batch_solve = timed(lambda: batched(False), 2)
+    ms_single_solve = timed(lambda: one_by_one(False), 2)
     out = {"systems": len(ctxs), "atoms_min": min(sizes), "atoms_max": max(sizes),
            "atoms_total": tot, "build_s_all": build_s,
            "batched": {"value": len(ctxs) * 1000.0 / ms_batch, "unit": "solves/s",
@@ -899,7 +920,11 @@ def run_ragged(args, rank, dev, stream, timed):
            "one_context_at_a_time": {"value": len(ctxs) * 1000.0 / ms_single,
                                      "unit": "solves/s", "ms": ms_single,
                                      "mean_iters": its["single"]},
-           "potential_ms_all": pot_ms}
+           "potential_ms_all": pot_ms,
+           "solve_only": {"batched_ms": ms_batch_solve, "one_at_a_time_ms": ms_single_solve,
+                          "speedup": ms_single_solve / ms_batch_solve,
+                          "what": "cpm_batch_solve + cpm_batch_neutralize against cpm_solve + "
+                                  "cpm_neutralize per context, b given"}}
     batch.close()
     for c in ctxs:
         c.close()
@@ -1261,13 +1286,13 @@ def run_scale_point(args, rank, world, local_rank):
     burst = peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"])
     achieved = method_flops / (tc_ms * 1e-3) / 1e12
     # the step's dominant kernel: the streamed 16-column matvec of the PCG iterations
+    stream_tb, stream_note = stream_traffic()
     mv_launch_ms = solve_parts["matvec_ms"] / max(1, solve_parts["max_iterations"])
     mv_bytes = 4.0 * n * n + H * n * 4.0 + H * n * 8.0
     mv_achieved = mv_bytes / (mv_launch_ms * 1e-3) / 1e9
     step_roof = {"bound": "hbm", "achieved": mv_achieved, "peak": hbm, "unit": "GB/s",
                  "frac": mv_achieved / hbm,
-                 "traffic": STREAM_TRAFFIC_PER_ELEMENT * n * n
-                 if STREAM_TRAFFIC_PER_ELEMENT else None,
+                 "traffic": (stream_tb * n * n) if stream_tb else None,
                  "kernel": "k_matvec_stream (16-column float matvec of the PCG iterations, E "
                            "streamed by TMA once per iteration)",
                  "timed_region": "the timed steps: CUDA events around each iteration's matvec "
@@ -1276,7 +1301,7 @@ def run_scale_point(args, rank, world, local_rank):
                          "directions) + 16 N x 8 (FP64 products)",
                  "ms_per_launch": mv_launch_ms, "bytes_per_launch": mv_bytes,
                  "peak_source": f"{src} hbm_gbs (of measured)",
-                 "traffic_source": STREAM_TRAFFIC_NOTE}
+                 "traffic_source": stream_note}
     roof = {"bound": "tensor", "achieved": achieved, "peak": sustained, "unit": "TFLOP/s",
             "frac": achieved / sustained, "traffic": None,
             "kernel": "k_ek_strip (tcgen05 k-space tail of the E build, all k-windows)",

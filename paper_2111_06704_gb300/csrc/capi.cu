@@ -327,8 +327,10 @@ void release_workspace(Ctx* c) {
   Buf* ws[] = {&c->tc_planes[0], &c->tc_planes[1], &c->tc_planes[2], &c->tc_planes[3],
                &c->tc_head, &c->tc_err,
                &c->tc_hsplit, &c->tc_scratch, &c->dc_cnt, &c->dc_pcol, &c->dc_status, &c->ws_solve, &c->ws_in0, &c->ws_in1, &c->ws_in2,
-               &c->ws_out0, &c->ws_out1, &c->ws_pot, &c->ws_guess, &c->ws_feat, &c->ws_cluster};
+               &c->ws_out0, &c->ws_out1, &c->ws_pot, &c->ws_guess, &c->ws_feat, &c->ws_cluster,
+               &c->tc_tiles};
   for (Buf* b : ws) buf_free(c, b);
+  c->tc_tiles_nt = 0;
 }
 
 void free_build(Ctx* c) {
@@ -688,12 +690,33 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
   const int head_cols = 16 * c->heavy_steps;
   // k-vectors whose BF16 planes are held at once: all of them, or in a streamed build a
   // window of ~12 GB of planes (12 bytes per row and k-vector)
+  // window of planes sized to the device: half of the memory left free once the head
+  // matrix is in place, between 12 and 64 GiB (14 bytes a row and k-vector: three BF16
+  // planes and the FP8 one, cos and sin).  Each window costs one pass of every tile's
+  // epilogue and of the head matrix, so fewer, larger windows are cheaper.  The first
+  // streamed build of a geometry fixes the window, so that rebuilds repeat it exactly.
   int kwin = c->mpad;
-  if (c->streamed)
-    kwin = c->p.k_window > 0
-               ? std::max(64, std::min(c->mpad, c->p.k_window / 64 * 64))
-               : std::max(64, (int)std::min<int64_t>(c->mpad, (int64_t)(12ull << 30) /
-                                                               (12ll * c->npad) / 64 * 64));
+  if (c->streamed) {
+    if (c->p.k_window > 0) {
+      kwin = std::max(64, std::min(c->mpad, c->p.k_window / 64 * 64));
+    } else if (c->kwin_n == n && c->kwin_mpad == c->mpad && c->kwin > 0) {
+      kwin = c->kwin;
+    } else {
+      size_t fr = 0, tot = 0;
+      cudaMemGetInfo(&fr, &tot);
+      const int64_t head_b = c->tc_head.bytes >= (size_t)n * c->ldE * sizeof(double)
+                                 ? 0 : (int64_t)n * c->ldE * (int64_t)sizeof(double);
+      const int64_t held = (int64_t)c->tc_planes[0].bytes * 3 + (int64_t)c->tc_planes[3].bytes;
+      int64_t budget = ((int64_t)fr - head_b + held) / 2;
+      budget = std::max<int64_t>(12ll << 30, std::min<int64_t>(64ll << 30, budget));
+      kwin = std::max(64, (int)std::min<int64_t>(c->mpad, budget / (14ll * c->npad) / 64 * 64));
+      const int windows = (c->mpad + kwin - 1) / kwin;  // equal windows, none a sliver
+      kwin = std::min(kwin, ((c->mpad + windows - 1) / windows + 63) / 64 * 64);
+      c->kwin = kwin;
+      c->kwin_n = n;
+      c->kwin_mpad = c->mpad;
+    }
+  }
   if (tc) {
     const size_t pbytes = (size_t)c->npad * 2 * kwin * 2;
     if ((st = buf_reserve(c, &planes[0], pbytes)) || (st = buf_reserve(c, &planes[1], pbytes)) ||
@@ -738,8 +761,9 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
                                   (double*)c->Ahead.ptr, s);
   cudaEventRecord(ev[1], s);
   if (tc) {
-    // FP64 head (heaviest k-vectors) with the real-space, self and dipole terms, then the
-    // tensor-core tail, which adds the head in its epilogue
+    // head (heaviest k-vectors, float-float) with the real-space, self and dipole terms in
+    // FP64, kept as float pairs; then the tensor-core tail, which adds the head in its
+    // epilogue
     cudaEvent_t ev_head;
     cudaEventCreate(&ev_head);
     cudaEventRecord(ev_head, s);
@@ -747,11 +771,22 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
     st = launch_ek_head_f64((const double*)c->Ahead.ptr, c->kh, head_cols, c->npad, hhi,
                             hhi + (size_t)c->npad * std::max(head_cols, 16),
                             (const double*)c->xyz.ptr, (const double*)c->alpha.ptr, n, geo,
-                            (double*)ehead.ptr, c->ldE, s);
+                            (float2*)ehead.ptr, c->ldE, s);
+    // the tile order of the tensor-core launches (kept with the context per row-block count)
+    const int nt = (n + 255) / 256;
+    if (!st && c->tc_tiles_nt != nt) {
+      const std::vector<uint32_t> order = ek_tile_order(nt);
+      if (!(st = buf_reserve(c, &c->tc_tiles, order.size() * sizeof(uint32_t))))
+        st = cuda_check(c, cudaMemcpyAsync(c->tc_tiles.ptr, order.data(),
+                                           order.size() * sizeof(uint32_t),
+                                           cudaMemcpyHostToDevice, s), "tile order");
+      if (!st) st = cuda_check(c, cudaStreamSynchronize(s), "tile order sync");
+      c->tc_tiles_nt = st ? 0 : nt;
+    }
     cudaEventRecord(c->ev_tc[0], s);
     // the tail, one k-window at a time: every window but the last carries the sum in the
-    // FP64 head matrix, the last writes float E.  A streamed build times the tensor-core
-    // launches of every window apart from the operand planes made between them.
+    // head matrix (float pairs), the last writes float E.  A streamed build times the
+    // tensor-core launches of every window apart from the operand planes made between them.
     std::vector<cudaEvent_t> wev;
     for (int kbeg = 0; kbeg < c->mpad && !st; kbeg += kwin) {
       const int kend = std::min(c->mpad, kbeg + kwin);
@@ -772,9 +807,10 @@ int cpm_build_E(cpm_ctx* c, int n, const double* xyz, const double* alpha) {
                         std::max(c->heavy_steps / 4, kbeg / 32), kend / 32, c->kb6_end,
                         c->kb3_end, c->kb8_begin, (const uint32_t*)c->chunk_end.ptr,
                         (const int*)c->kexp.ptr,
-                        (double*)ehead.ptr,
+                        (float2*)ehead.ptr,
                         c->ldE, last ? (float*)c->E.ptr : nullptr, c->ldE, (int*)errbuf.ptr,
                         c->kw.data(), (float*)tcscratch.ptr, c->nsmid,
+                        (const uint32_t*)c->tc_tiles.ptr,
                         c->streamed ? nullptr : c->ev_tc[2], s);
       if (c->streamed) cudaEventRecord(wev.back(), s);
     }

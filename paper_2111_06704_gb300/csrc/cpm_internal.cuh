@@ -106,6 +106,7 @@ struct Ctx {
   Buf chunk_end;        // uint32 bit per K-block of 64 columns (tensor-core build)
   Buf kexp;             // int per K-block: FP16 plane scale exponent (tensor-core build)
   bool streamed = false;  // A too large to keep: built in k-windows, potential direct
+  int kwin = 0, kwin_n = 0, kwin_mpad = 0;  // the streamed build's k-window, fixed per geometry
   int kb6_end = 0, kb3_end = 0;  // tensor-core K-blocks: six products before kb6_end,
                                  // three before kb3_end, one after
   int kb8_begin = 0;             // K-blocks from here take one FP8 product
@@ -161,6 +162,8 @@ struct Ctx {
   // tensor-core build workspace, kept for the next build: operand planes, the FP64
   // head matrix, the error flag, the head's float pairs, the per-SM hi / lo scratch
   Buf tc_planes[4], tc_head, tc_err, tc_hsplit, tc_scratch;  // planes 0-2: 16-bit, 3: FP8
+  Buf tc_tiles;       // the tile kernels' tile order, for tc_tiles_nt row blocks
+  int tc_tiles_nt = 0;
   Buf dc_cnt, dc_pcol, dc_status;  // PCG-DC build workspace
   int nsmid = 0;  // SM slots of tc_scratch (%nsmid), queried once
 
@@ -222,15 +225,17 @@ void launch_mirror_lower(bool fp64, void* E, int n, int64_t ldE, cudaStream_t s)
 
 int launch_ek_head_f64(const double* Ahead, int kh, int ktot, int npad, float* hi, float* lo,
                        const double* xyz, const double* alpha, int n, const Geometry& geo,
-                       double* Ehead, int64_t ldE, cudaStream_t s);
+                       float2* Ehead, int64_t ldE, cudaStream_t s);
 
 // tc_syrk.cu
 int launch_ek_tc(const void* p0, const void* p1, const void* p2, const void* p8, int npad,
                  int64_t plane_cols, int kb_col0, int n, int kb_begin, int kb_end, int kb6_end,
                  int kb3_end, int kb8_begin,
-                 const uint32_t* chunk_end, const int* kexp, double* head, int64_t ldh,
+                 const uint32_t* chunk_end, const int* kexp, float2* head, int64_t ldh,
                  float* E, int64_t ldE, int* err, const double* kw, float* scratch,
-                 int scratch_slots, cudaEvent_t mid, cudaStream_t s);
+                 int scratch_slots, const uint32_t* tile_map, cudaEvent_t mid,
+                 cudaStream_t s);
+std::vector<uint32_t> ek_tile_order(int nt);  // the tile kernels' tile order (host)
 int64_t ek_strip_scratch_floats();  // per SM slot of the 256 x 256 tile kernels
 void launch_nsmid(int* d_out, cudaStream_t s);
 void launch_extract_diag(bool fp64, const void* E, int n, int64_t ldE, double* diag,

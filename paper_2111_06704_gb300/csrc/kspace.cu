@@ -403,10 +403,11 @@ k_ek_simt(const T* __restrict__ A, int64_t lda, int ktot, T* __restrict__ E, int
 // (al*bl is below 2^-48 of the product) is added to a float pair (hi, lo) per output
 // with an error-free two-sum.  About 11 float operations per term instead of one FP64
 // FMA, which runs at 1/64 of the float rate on this GPU.  The epilogue adds the
-// real-space, self and dipole terms in FP64 and writes the FP64 head matrix.
+// real-space, self and dipole terms in FP64 and writes the head matrix as float pairs
+// (hi, lo): ~2^-48 of each entry, and the tensor-core tail adds to it in float.
 __global__ void __launch_bounds__(256)
 k_ek_head_ff(const float* __restrict__ Ah_g, const float* __restrict__ Al_g, int64_t lda,
-             int ktot, double* __restrict__ Eh, int64_t ldE, Epi ep) {
+             int ktot, float2* __restrict__ Eh, int64_t ldE, Epi ep) {
   constexpr int BM = 64, BK = 16, TM = 4, LD = BM + 4;
   __shared__ __align__(16) float Ah[BK][LD], Al[BK][LD], Bh[BK][LD], Bl[BK][LD];
   int I, J;
@@ -459,8 +460,9 @@ k_ek_head_ff(const float* __restrict__ Ah_g, const float* __restrict__ Al_g, int
     for (int b = 0; b < TM; ++b) {
       const int j = j0 + tx * 4 + b;
       if (i >= ep.n || j >= ep.n || j > i) continue;
-      Eh[(int64_t)i * ldE + j] =
-          (double)sh[a][b] + (double)sl[a][b] + epilogue_terms(ep, i, j);
+      const double v = (double)sh[a][b] + (double)sl[a][b] + epilogue_terms(ep, i, j);
+      const float vh = (float)v;
+      Eh[(int64_t)i * ldE + j] = make_float2(vh, (float)(v - (double)vh));
     }
   }
 }
@@ -599,10 +601,10 @@ int launch_ek_simt(bool fp64, const void* A, int npad, int mpad, const double* x
 
 // FP64-accurate head of the k-space sum (the first ktot columns of the FP64 head operand,
 // row stride 2 kh, split into float pairs in hi/lo [npad][ktot]) plus the real-space,
-// self and dipole terms, lower triangle, into Ehead.
+// self and dipole terms, lower triangle, into Ehead as float pairs (hi, lo).
 int launch_ek_head_f64(const double* Ahead, int kh, int ktot, int npad, float* hi, float* lo,
                        const double* xyz, const double* alpha, int n, const Geometry& geo,
-                       double* Ehead, int64_t ldE, cudaStream_t s) {
+                       float2* Ehead, int64_t ldE, cudaStream_t s) {
   const Epi ep = make_epi(xyz, alpha, n, geo);
   constexpr int BM = 64;
   const int nt = (n + BM - 1) / BM;

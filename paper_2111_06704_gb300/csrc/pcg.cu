@@ -172,84 +172,30 @@ k_matvec_f32(const float* __restrict__ E, int64_t ldE, int n, const float* __res
   for (int i = 0; i < RB; ++i)
 #pragma unroll
     for (int r = 0; r < NR; ++r) part[i][r] = perr[i][r] = 0.f;
-  if constexpr (NR % 2 == 0) {
-    // columns in pairs: the same operations on float pairs, two IEEE results an
-    // instruction (a - b as fma(b, -1, a)), so every value is the scalar path's
-    const float2 m1 = make_float2(-1.f, -1.f);
-    float2 part2[RB][NR / 2], perr2[RB][NR / 2];
+  for (int g = sub; g < ngroups; g += WS) {
+    const int64_t cc = (int64_t)g * 128 + lane * 4;
+    float ev[RB][4];
 #pragma unroll
     for (int i = 0; i < RB; ++i)
+      *reinterpret_cast<float4*>(ev[i]) = __ldcs(reinterpret_cast<const float4*>(erow[i] + cc));
 #pragma unroll
-      for (int r = 0; r < NR / 2; ++r) part2[i][r] = perr2[i][r] = make_float2(0.f, 0.f);
-    for (int g = sub; g < ngroups; g += WS) {
-      const int64_t cc = (int64_t)g * 128 + lane * 4;
-      float ev[RB][4];
-#pragma unroll
-      for (int i = 0; i < RB; ++i)
-        *reinterpret_cast<float4*>(ev[i]) = __ldcs(reinterpret_cast<const float4*>(erow[i] + cc));
-#pragma unroll
-      for (int rp = 0; rp < NR / 2; ++rp) {
-        const int64_t o0 = (int64_t)(c0 + 2 * rp) * ldv + cc, o1 = o0 + ldv;
-        float h0[4], l0[4], h1[4], l1[4];
-        *reinterpret_cast<float4*>(h0) = __ldg(reinterpret_cast<const float4*>(pv + o0));
-        *reinterpret_cast<float4*>(l0) = __ldg(reinterpret_cast<const float4*>(plo + o0));
-        *reinterpret_cast<float4*>(h1) = __ldg(reinterpret_cast<const float4*>(pv + o1));
-        *reinterpret_cast<float4*>(l1) = __ldg(reinterpret_cast<const float4*>(plo + o1));
-#pragma unroll
-        for (int i = 0; i < RB; ++i)
-#pragma unroll
-          for (int w = 0; w < 4; ++w) {
-            const float2 e2 = make_float2(ev[i][w], ev[i][w]);
-            const float2 ne2 = make_float2(-ev[i][w], -ev[i][w]);
-            const float2 h2 = make_float2(h0[w], h1[w]), l2 = make_float2(l0[w], l1[w]);
-            float2& P = part2[i][rp];
-            float2& Q = perr2[i][rp];
-            const float2 pr = __fmul2_rn(e2, h2);
-            const float2 s = __fadd2_rn(P, pr);
-            const float2 bb = __ffma2_rn(P, m1, s);                              // s - P
-            const float2 t2 = __ffma2_rn(__ffma2_rn(bb, m1, s), m1, P);          // P - (s - bb)
-            const float2 er = __fadd2_rn(t2, __ffma2_rn(bb, m1, pr));            // + (pr - bb)
-            const float2 npe = __ffma2_rn(ne2, h2, pr);                          // pr - e h
-            Q = __ffma2_rn(e2, l2, __fadd2_rn(Q, __ffma2_rn(npe, m1, er)));
-            P = s;
-          }
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < RB; ++i)
-#pragma unroll
-      for (int rp = 0; rp < NR / 2; ++rp) {
-        part[i][2 * rp] = part2[i][rp].x;
-        part[i][2 * rp + 1] = part2[i][rp].y;
-        perr[i][2 * rp] = perr2[i][rp].x;
-        perr[i][2 * rp + 1] = perr2[i][rp].y;
-      }
-  } else {  // one column at a time
-    for (int g = sub; g < ngroups; g += WS) {
-      const int64_t cc = (int64_t)g * 128 + lane * 4;
-      float ev[RB][4];
+    for (int r = 0; r < NR; ++r) {
+      const int64_t o = (int64_t)(c0 + r) * ldv + cc;
+      float hv[4], lv[4];
+      *reinterpret_cast<float4*>(hv) = __ldg(reinterpret_cast<const float4*>(pv + o));
+      *reinterpret_cast<float4*>(lv) = __ldg(reinterpret_cast<const float4*>(plo + o));
 #pragma unroll
       for (int i = 0; i < RB; ++i)
-        *reinterpret_cast<float4*>(ev[i]) = __ldcs(reinterpret_cast<const float4*>(erow[i] + cc));
 #pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        const int64_t o = (int64_t)(c0 + r) * ldv + cc;
-        float hv[4], lv[4];
-        *reinterpret_cast<float4*>(hv) = __ldg(reinterpret_cast<const float4*>(pv + o));
-        *reinterpret_cast<float4*>(lv) = __ldg(reinterpret_cast<const float4*>(plo + o));
-#pragma unroll
-        for (int i = 0; i < RB; ++i)
-#pragma unroll
-          for (int w = 0; w < 4; ++w) {
-            const float e = ev[i][w];
-            const float pr = e * hv[w];
-            const float s = part[i][r] + pr;
-            const float bb = s - part[i][r];
-            const float e2 = (part[i][r] - (s - bb)) + (pr - bb);
-            perr[i][r] = fmaf(e, lv[w], perr[i][r] + (fmaf(e, hv[w], -pr) + e2));
-            part[i][r] = s;
-          }
-      }
+        for (int w = 0; w < 4; ++w) {
+          const float e = ev[i][w];
+          const float pr = e * hv[w];
+          const float s = part[i][r] + pr;
+          const float bb = s - part[i][r];
+          const float e2 = (part[i][r] - (s - bb)) + (pr - bb);
+          perr[i][r] = fmaf(e, lv[w], perr[i][r] + (fmaf(e, hv[w], -pr) + e2));
+          part[i][r] = s;
+        }
     }
   }
 #pragma unroll

@@ -141,28 +141,13 @@ k_ion_sf_f32(const uint32_t* __restrict__ sion, const double* __restrict__ ion_q
         ff_add(imh, iml, ph_, pl_, imh, iml);
       }
     } else {
-      // the cos and sin sums as one float pair each (paired float instructions, two IEEE
-      // results an instruction: the values of pair_fma on each)
-      float2 hh = make_float2(reh, imh), ll = make_float2(rel, iml);
-      const float2 m1 = make_float2(-1.f, -1.f);
       for (int t = 0; t < cnt; ++t) {
         const uint32_t ph = h * sf[t][0] + kk * sf[t][1] + l * sf[t][2];
         float s, c;
         sincos_table(ph, turn, &s, &c);
-        const float2 x = make_float2(c, s), qh = make_float2(sqh[t], sqh[t]);
-        const float2 p = __fmul2_rn(qh, x);
-        const float2 pe = __ffma2_rn(qh, x, __fmul2_rn(p, m1));                  // qh x - p
-        const float2 s2 = __fadd2_rn(hh, p);
-        const float2 bb = __ffma2_rn(hh, m1, s2);                                // s2 - h
-        const float2 a = __ffma2_rn(__ffma2_rn(bb, m1, s2), m1, hh);             // h - (s2 - bb)
-        const float2 e = __fadd2_rn(a, __ffma2_rn(bb, m1, p));                   // + (p - bb)
-        ll = __fadd2_rn(ll, __fadd2_rn(e, __ffma2_rn(make_float2(sql[t], sql[t]), x, pe)));
-        hh = s2;
+        pair_fma(reh, rel, sqh[t], sql[t], c);
+        pair_fma(imh, iml, sqh[t], sql[t], s);
       }
-      reh = hh.x;
-      imh = hh.y;
-      rel = ll.x;
-      iml = ll.y;
     }
   }
   if (k >= mpad) return;

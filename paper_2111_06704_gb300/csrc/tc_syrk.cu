@@ -18,8 +18,8 @@
 // All 512 TMEM columns hold two M = 128, N = 256 FP32 accumulators.  After each
 // accumulation chunk of the host's schedule the MMAs pause while the epilogue adds the
 // accumulator (times the chunk's scale) into the tile's running hi / lo floats by an
-// error-free two-sum; the last chunk adds hi + lo + the accumulator to the FP64 head and
-// writes float E (or FP64 head).
+// error-free two-sum; the last chunk adds hi + lo + the accumulator to the head (float
+// pairs, float arithmetic only) and writes float E (or the head).
 //
 // Every wait is bounded: on timeout the kernel records an error code and leaves; the
 // host reports a CPM_ECUDA-class failure instead of hanging.
@@ -164,9 +164,10 @@ __device__ __forceinline__ void tri_tile(int t, int& I, int& J) {
 // accumulator is drained after each accumulation chunk: the MMAs pause while the
 // epilogue adds it, by an error-free two-sum, into the tile's running hi / lo floats in
 // the SM's 512 KB scratch slot (each thread's entries laid out for whole-warp 512-byte
-// accesses; small enough for all SMs' slots to stay in L2).  The FP64 head is touched
-// once per tile.  Off the diagonal the k-space terms oscillate in sign; the diagonal,
-// where every term is positive, takes the exact FP64 weight sum (range_weight).  Eight
+// accesses; small enough for all SMs' slots to stay in L2).  The head (float pairs) is
+// touched once per tile.  Off the diagonal the k-space terms oscillate in sign; the
+// diagonal, where every term is positive, takes the exact weight sum (range_weight, FP64
+// on the host, as a float pair).  Eight
 // epilogue warps: TMEM lane quarter warp % 4, column half (warp - 2) / 4.
 constexpr int kStripTile = 256;
 constexpr int kStripThreads = 320;  // 10 warps: TMA, MMA, 8 epilogue
@@ -191,59 +192,111 @@ struct StripArgs {
   const int* kexp;            // per K-block: FP16 blocks hold 2^kexp a (0 for BF16 blocks)
   float* scratch; // per SM 2 x 65,536 floats (the tile's running hi / lo sums)
   int scratch_slots;  // SM slots in scratch (%nsmid)
-  double* head;   // [n][ldh] FP64 head + everything before kb_begin (lower triangle)
+  float2* head;   // [n][ldh] head + everything before kb_begin as float pairs (hi, lo),
+                  //   lower triangle
   int64_t ldh;
   float* E;       // float E, or null: the sum goes back into head (FP64)
   int64_t ldE;
   int* err;
   int diag_exact;  // the diagonal takes w_diag in place of its accumulated sum
-  double w_diag;   // sum of W_K over the launch's k-vectors
+  float wd_hi, wd_lo;  // sum of W_K over the launch's k-vectors, as a float pair
+  const uint32_t* tile_map;  // tile t -> (I << 16) | J, or null: row-major triangle order
 };
 
-// One epilogue thread's 32 final tail values (row `row`, columns jb .. jb + 31) plus the
-// FP64 head: the head segment is loaded whole before any store (16-byte vectors where the
-// segment lies below the diagonal and inside n); the sum goes to float E, or back to head
-// without E.  The diagonal entry takes the exact weight sum.
-__device__ __forceinline__ void strip_final(const StripArgs& a, const double (&tail)[32], int row,
-                                            int jb) {
+// One epilogue thread's 32 final tail values (row `row`, columns jb .. jb + 31), each a
+// float pair (th, tl), plus the head: the head segment (float pairs, ~2^-48 of each
+// entry) is loaded whole before any store (16-byte vectors where the segment lies below
+// the diagonal and inside n); the pairs meet in an error-free two-sum of the high parts
+// and a rounded add of the low ones, then one renormalising step.  The sum goes to float
+// E (the high part: the float nearest the pair), or back to the head without E.  The
+// diagonal entry takes the exact weight sum.  Float arithmetic only: this GPU runs FP64
+// at 1/64 of the float rate, and this runs once for every entry of every tile.
+__device__ __forceinline__ void strip_final(const StripArgs& a, const float (&th)[32],
+                                            const float (&tl)[32], int row, int jb) {
   const int jmax = min(a.n - 1, row);
   if (jb > jmax) return;
-  double* hp = a.head + (int64_t)row * a.ldh + jb;
+  float2* hp = a.head + (int64_t)row * a.ldh + jb;
   const bool full = jb + 31 <= jmax;
-  double hv[32];
+  float hh[32], hl[32];
   if (full) {
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
-      const double2 x = reinterpret_cast<const double2*>(hp)[u];
-      hv[2 * u] = x.x;
-      hv[2 * u + 1] = x.y;
+      const float4 x = reinterpret_cast<const float4*>(hp)[u];
+      hh[2 * u] = x.x;
+      hl[2 * u] = x.y;
+      hh[2 * u + 1] = x.z;
+      hl[2 * u + 1] = x.w;
     }
   } else {
 #pragma unroll
-    for (int t = 0; t < 32; ++t) hv[t] = jb + t <= jmax ? hp[t] : 0.0;
+    for (int t = 0; t < 32; ++t) {
+      const float2 x = jb + t <= jmax ? hp[t] : make_float2(0.f, 0.f);
+      hh[t] = x.x;
+      hl[t] = x.y;
+    }
   }
 #pragma unroll
-  for (int t = 0; t < 32; ++t) hv[t] += a.diag_exact && jb + t == row ? a.w_diag : tail[t];
+  for (int t = 0; t < 32; ++t) {
+    const bool dg = a.diag_exact && jb + t == row;
+    const float bh = dg ? a.wd_hi : th[t], bl = dg ? a.wd_lo : tl[t];
+    const float s = __fadd_rn(hh[t], bh);
+    const float bb = __fsub_rn(s, hh[t]);
+    const float e = __fadd_rn(__fsub_rn(hh[t], __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+    const float lo = __fadd_rn(__fadd_rn(hl[t], bl), e);
+    hh[t] = __fadd_rn(s, lo);
+    hl[t] = __fsub_rn(lo, __fsub_rn(hh[t], s));
+  }
   if (a.E) {
     float* ep = a.E + (int64_t)row * a.ldE + jb;
     if (full) {
 #pragma unroll
       for (int u = 0; u < 8; ++u)
-        reinterpret_cast<float4*>(ep)[u] = make_float4((float)hv[4 * u], (float)hv[4 * u + 1],
-                                                       (float)hv[4 * u + 2], (float)hv[4 * u + 3]);
+        reinterpret_cast<float4*>(ep)[u] =
+            make_float4(hh[4 * u], hh[4 * u + 1], hh[4 * u + 2], hh[4 * u + 3]);
     } else {
 #pragma unroll
       for (int t = 0; t < 32; ++t)
-        if (jb + t <= jmax) ep[t] = (float)hv[t];
+        if (jb + t <= jmax) ep[t] = hh[t];
     }
   } else if (full) {
 #pragma unroll
     for (int u = 0; u < 16; ++u)
-      reinterpret_cast<double2*>(hp)[u] = make_double2(hv[2 * u], hv[2 * u + 1]);
+      reinterpret_cast<float4*>(hp)[u] =
+          make_float4(hh[2 * u], hl[2 * u], hh[2 * u + 1], hl[2 * u + 1]);
   } else {
 #pragma unroll
     for (int t = 0; t < 32; ++t)
-      if (jb + t <= jmax) hp[t] = hv[t];
+      if (jb + t <= jmax) hp[t] = make_float2(hh[t], hl[t]);
+  }
+}
+
+// The final chunk's tail of one group of 32 accumulators: the running (hi, lo) sums of
+// the earlier chunks (ci > 0) plus the accumulator times its scale, by a two-sum.
+__device__ __forceinline__ void final_tail(bool earlier, const float4* hi4, const float4* lo4,
+                                           int grp, const uint32_t (&acc)[32], float scale,
+                                           float (&th)[32], float (&tl)[32]) {
+  if (earlier) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const float4 a4 = hi4[grp + u * 32], b4 = lo4[grp + u * 32];
+      th[4 * u] = a4.x, th[4 * u + 1] = a4.y, th[4 * u + 2] = a4.z, th[4 * u + 3] = a4.w;
+      tl[4 * u] = b4.x, tl[4 * u + 1] = b4.y, tl[4 * u + 2] = b4.z, tl[4 * u + 3] = b4.w;
+    }
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      const float v = __uint_as_float(acc[t]) * scale;
+      const float s = __fadd_rn(th[t], v);
+      const float bb = __fsub_rn(s, th[t]);
+      const float e = __fadd_rn(__fsub_rn(th[t], __fsub_rn(s, bb)), __fsub_rn(v, bb));
+      th[t] = s;
+      tl[t] = __fadd_rn(tl[t], e);
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      th[t] = __uint_as_float(acc[t]) * scale;
+      tl[t] = 0.f;
+    }
   }
 }
 
@@ -251,9 +304,15 @@ __device__ __forceinline__ void strip_final(const StripArgs& a, const double (&t
 struct StripTile {
   int i0, j0, rb, cb;
   bool diag;
-  __device__ StripTile(int tile, int npad) {
+  __device__ StripTile(int tile, int npad, const uint32_t* map) {
     int I, J;
-    tri_tile(tile, I, J);
+    if (map) {
+      const uint32_t v = map[tile];
+      I = (int)(v >> 16);
+      J = (int)(v & 0xffffu);
+    } else {
+      tri_tile(tile, I, J);
+    }
     i0 = I * kStripTile;
     j0 = J * kStripTile;
     diag = I == J;
@@ -356,7 +415,7 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
       uint32_t g = 0;  // stages issued by this CTA
       bool ok = true;
       for (int tile = tile0; tile < args.tiles && ok; tile += tstep) {
-        const StripTile tg(tile, args.npad);
+        const StripTile tg(tile, args.npad, args.tile_map);
         for (int t = 0; t < nst; ++t, ++g) {
           const int s = g % kStages;
           ok = mbar_wait(&empty_bar[s], ((g / kStages) & 1) ^ 1, args.err, 11);
@@ -398,7 +457,7 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
       uint32_t g = 0, chunk = 0;  // stages consumed, chunks committed by this CTA
       bool ok = true;
       for (int tile = tile0; tile < args.tiles && ok; tile += tstep) {
-        const StripTile tg(tile, args.npad);
+        const StripTile tg(tile, args.npad, args.tile_map);
         // on a diagonal tile the first row half needs only the first 128 columns
         constexpr uint32_t kId256 = idesc_f16(SIX, 256), kId128 = idesc_f16(SIX, 128);
         const uint32_t id0 = tg.diag ? kId128 : kId256;
@@ -482,7 +541,7 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
     }
     uint32_t chunk = 0;
     for (int tile = tile0; tile < args.tiles && ok; tile += tstep) {
-      const StripTile tg(tile, args.npad);
+      const StripTile tg(tile, args.npad, args.tile_map);
       int ci = 0;  // chunk index within the tile
       for (int t0 = 0; t0 < nst; ++ci) {
         int t1 = t0;
@@ -505,23 +564,9 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
             tmem_wait_ld();
             const int grp = (r * 4 + cl) * 8 * 32;  // float4 offset of this group
             if (final_chunk) {
-              double tail[32];
-              if (ci > 0) {
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                  const float4 hv = hi4[grp + u * 32], lv = lo4[grp + u * 32];
-                  tail[4 * u] = (double)hv.x + (double)lv.x;
-                  tail[4 * u + 1] = (double)hv.y + (double)lv.y;
-                  tail[4 * u + 2] = (double)hv.z + (double)lv.z;
-                  tail[4 * u + 3] = (double)hv.w + (double)lv.w;
-                }
-#pragma unroll
-                for (int t = 0; t < 32; ++t) tail[t] += (double)(__uint_as_float(acc[t]) * scale);
-              } else {
-#pragma unroll
-                for (int t = 0; t < 32; ++t) tail[t] = (double)(__uint_as_float(acc[t]) * scale);
-              }
-              if (row < args.n) strip_final(args, tail, row, tg.j0 + cg * 32);
+              float th[32], tl[32];
+              final_tail(ci > 0, hi4, lo4, grp, acc, scale, th, tl);
+              if (row < args.n) strip_final(args, th, tl, row, tg.j0 + cg * 32);
             } else {
               float hv[32], lv[32];
               if (ci > 0) {
@@ -905,23 +950,9 @@ k_ek_pair(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CUt
           tmem_wait_ld();
           const int grp = cg * 8 * 32;
           if (final_chunk) {
-            double tail[32];
-            if (ci > 0) {
-#pragma unroll
-              for (int u = 0; u < 8; ++u) {
-                const float4 hv = hi4[grp + u * 32], lv = lo4[grp + u * 32];
-                tail[4 * u] = (double)hv.x + (double)lv.x;
-                tail[4 * u + 1] = (double)hv.y + (double)lv.y;
-                tail[4 * u + 2] = (double)hv.z + (double)lv.z;
-                tail[4 * u + 3] = (double)hv.w + (double)lv.w;
-              }
-#pragma unroll
-              for (int t = 0; t < 32; ++t) tail[t] += (double)(__uint_as_float(acc[t]) * scale);
-            } else {
-#pragma unroll
-              for (int t = 0; t < 32; ++t) tail[t] = (double)(__uint_as_float(acc[t]) * scale);
-            }
-            if (row < args.n) strip_final(args, tail, row, jb0 + cg * 32);
+            float th[32], tl[32];
+            final_tail(ci > 0, hi4, lo4, grp, acc, scale, th, tl);
+            if (row < args.n) strip_final(args, th, tl, row, jb0 + cg * 32);
           } else {
             float hv[32], lv[32];
             if (ci > 0) {
@@ -972,12 +1003,16 @@ k_ek_pair(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CUt
   }
 }
 
-// E = head (lower triangle) when the tail contributes nothing to the last window.
-__global__ void k_head_to_float(const double* __restrict__ head, int64_t ldh,
+// E = head (lower triangle) when the tail contributes nothing to the last window: the
+// float nearest each (hi, lo) pair.
+__global__ void k_head_to_float(const float2* __restrict__ head, int64_t ldh,
                                 float* __restrict__ E, int64_t ldE, int n) {
   const int j = blockIdx.x * 32 + threadIdx.x;
   for (int i = blockIdx.y * 32 + threadIdx.y; i < min(n, (int)(blockIdx.y + 1) * 32); i += 8)
-    if (j < n && j <= i) E[(int64_t)i * ldE + j] = (float)head[(int64_t)i * ldh + j];
+    if (j < n && j <= i) {
+      const float2 x = head[(int64_t)i * ldh + j];
+      E[(int64_t)i * ldE + j] = x.x + x.y;
+    }
 }
 
 // 2-D map of a [rows][cols] plane of 16-bit values (bytes = false) in 128-row boxes of bk
@@ -1023,6 +1058,31 @@ __global__ void k_nsmid(int* out) {
   *out = (int)v;
 }
 
+// The order in which the CTAs of the tile kernels take the nt (nt + 1) / 2 lower-triangle
+// tiles: blocks of 12 x 12 tiles (about one wave of the 152 SMs), the blocks in row-major
+// triangle order and the tiles of a block row by row.  The tiles in flight then share 12
+// operand row blocks and 12 column blocks, which they stream at about the same K
+// position, so the L2 serves most of their operand loads; in plain row-major order they
+// share one row block and stream ~150 different column blocks.
+std::vector<uint32_t> ek_tile_order(int nt) {
+  constexpr int G = 12;
+  std::vector<uint32_t> map;
+  map.reserve((size_t)nt * (nt + 1) / 2);
+  const int nb = (nt + G - 1) / G;
+  for (int bi = 0; bi < nb; ++bi)
+    for (int bj = 0; bj <= bi; ++bj)
+      for (int a = 0; a < G; ++a) {
+        const int I = bi * G + a;
+        if (I >= nt) break;
+        for (int b = 0; b < G; ++b) {
+          const int J = bj * G + b;
+          if (J > I) break;
+          map.push_back(((uint32_t)I << 16) | (uint32_t)J);
+        }
+      }
+  return map;
+}
+
 // Floats of k_ek_strip scratch per SM slot.
 int64_t ek_strip_scratch_floats() { return 2 * 65536; }
 
@@ -1041,9 +1101,10 @@ void launch_nsmid(int* d_out, cudaStream_t s) {
 int launch_ek_tc(const void* p0, const void* p1, const void* p2, const void* p8, int npad,
                  int64_t plane_cols, int kb_col0, int n, int kb_begin, int kb_end, int kb6_end,
                  int kb3_end, int kb8_begin,
-                 const uint32_t* chunk_end, const int* kexp, double* head, int64_t ldh,
+                 const uint32_t* chunk_end, const int* kexp, float2* head, int64_t ldh,
                  float* E, int64_t ldE, int* err, const double* kw, float* scratch,
-                 int scratch_slots, cudaEvent_t mid, cudaStream_t s) {
+                 int scratch_slots, const uint32_t* tile_map, cudaEvent_t mid,
+                 cudaStream_t s) {
   if (!scratch || scratch_slots < 1 || (kb6_end & 1) || (kb_begin & 1) || (kb8_begin & 1))
     return CPM_EINVAL;
   CUtensorMap m0, m0n, m1n, m2n, m8;
@@ -1089,7 +1150,9 @@ int launch_ek_tc(const void* p0, const void* p1, const void* p2, const void* p8,
   a.ldh = ldh;
   a.ldE = ldE;
   a.err = err;
-  // one CTA per tile; the hardware hands each SM its next tile as it frees up
+  a.tile_map = pair2 ? nullptr : tile_map;
+  // one CTA per tile; the hardware hands each SM its next tile as it frees up, in the
+  // order of the tile map
   auto launch = [&](bool six) {
     const int smem = six ? smem6 : smem31;
     if (pair2) {  // one two-CTA cluster per pair tile
@@ -1121,7 +1184,12 @@ int launch_ek_tc(const void* p0, const void* p1, const void* p2, const void* p8,
     a.kb_begin = kb_begin;
     a.kb_end = x6_end;
     a.E = l_begin < kb_end ? nullptr : E;
-    a.diag_exact = range_weight(kw, a.kb_begin, a.kb_end, &a.w_diag);
+    {
+      double w = 0.0;
+      a.diag_exact = range_weight(kw, a.kb_begin, a.kb_end, &w);
+      a.wd_hi = (float)w;
+      a.wd_lo = (float)(w - (double)a.wd_hi);
+    }
     if (launch(true) != cudaSuccess) return CPM_ECUDA;
   }
   if (mid) cudaEventRecord(mid, s);
@@ -1129,7 +1197,12 @@ int launch_ek_tc(const void* p0, const void* p1, const void* p2, const void* p8,
     a.kb_begin = l_begin;
     a.kb_end = kb_end;
     a.E = E;
-    a.diag_exact = range_weight(kw, a.kb_begin, a.kb_end, &a.w_diag);
+    {
+      double w = 0.0;
+      a.diag_exact = range_weight(kw, a.kb_begin, a.kb_end, &w);
+      a.wd_hi = (float)w;
+      a.wd_lo = (float)(w - (double)a.wd_hi);
+    }
     if (launch(false) != cudaSuccess) return CPM_ECUDA;
   }
   if (kb_begin >= kb_end && E)  // nothing of the tail in this window

@@ -98,7 +98,7 @@ def test_one_call_training_step_against_the_oracle(walk):
     # each move is at most lr.
     ctx = walk[0]
     rng = np.random.default_rng(11)
-    g = LearnedGuess(ctx, seed=5)
+    g = LearnedGuess(ctx, seed=5, bf16=False)  # FP32 weights: the oracle's network
     p = mlp.init_params(rng, scale=0.8).astype(np.float32)
     g.params = _dev(p, torch.float32)
     s, lr = 1000, 1e-3
@@ -111,8 +111,10 @@ def test_one_call_training_step_against_the_oracle(walk):
     p_ref, _, _ = mlp.adam_step(p, np.zeros_like(grad_ref), np.zeros_like(grad_ref),
                                 grad_ref, 1, lr)
     assert loss == pytest.approx(loss_ref, rel=1e-5)
-    clear = np.abs(grad_ref) > 1e-3 * np.abs(grad_ref).max()
-    assert clear.sum() > 1000
+    # the gradient is good to ~1e-5 of its norm (the gradient test), so a component a
+    # hundredth of the largest keeps its sign
+    clear = np.abs(grad_ref) > 1e-2 * np.abs(grad_ref).max()
+    assert clear.sum() > 100
     assert np.abs(p1 - p_ref)[clear].max() <= 1e-6 + 1e-6 * lr
     assert np.all(np.abs(p1 - p) <= lr * (1 + 1e-5) + 1e-7)
     assert g.step == 1

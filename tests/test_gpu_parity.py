@@ -94,6 +94,8 @@ def test_charges_match_oracle(built, oc):
     io, el = oc.work.electrolyte, oc.work.electrode
     q, iters, rel, b, qsol = cpm.charges(ctx, io.xyz, io.q, el.chi, tol=1e-12 if prec == "fp64" else 1e-10)
     assert np.all(rel <= (1e-12 if prec == "fp64" else 1e-9))
+    print(f"512 atoms, {prec} build: q error {rel_l2(q, oc.q):.2e}, "
+          f"b error {rel_max(b, oc.b_neutral_volts):.2e} of max|b|")
     assert rel_l2(q, oc.q) < Q_TOL[prec]
     assert abs(q.sum() + oc.q_sol.sum()) < 1e-12 * np.abs(q).sum()  # Eq. 34
 

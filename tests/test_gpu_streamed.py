@@ -46,7 +46,9 @@ def test_windowed_build_matches_oracle_and_resident(small_cell_oracle):
     assert rel_max(b_s, oc.b_neutral_volts) < 1e-6
     assert rel_max(b_s, b_r) < 1e-8
     q, it, rel, _, _ = cpm.charges(stream, io.xyz, io.q, el.chi, tol=1e-10)
-    assert np.linalg.norm(q - oc.q) / np.linalg.norm(oc.q) < 1e-6
+    err = np.linalg.norm(q - oc.q) / np.linalg.norm(oc.q)
+    print(f"streamed build, 512 atoms: q error {err:.2e}")
+    assert err < 1e-6
     stream.close()
     res.close()
 

@@ -100,4 +100,7 @@ def test_multi_tile_tail_against_the_oracle():
                                     wl.RCUT_REAL, wl.KSPACE_EPS, True, kspace="factored")
     q_ref, _ = sv.solve_bordered(e_ref, ew.rhs_volts(el.chi, bsol) / ew.KE, float(q_ion.sum()))
     assert rel[0] <= 1e-10
-    assert np.linalg.norm(q[0] - q_ref) < 1e-6 * np.linalg.norm(q_ref)
+    err = np.linalg.norm(q[0] - q_ref) / np.linalg.norm(q_ref)
+    print(f"1,144 atoms: E max error {np.abs(e_gpu - e_ref).max() / np.abs(e_ref).max():.2e} "
+          f"of max|E|, q error {err:.2e}")
+    assert err < 1e-6
