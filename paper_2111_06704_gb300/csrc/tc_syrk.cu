@@ -270,15 +270,36 @@ __device__ __forceinline__ void strip_final(const StripArgs& a, const float (&th
   }
 }
 
+// The running sums of the tiles in the SMs' scratch slots (78 MB for 152 SMs) are read
+// and written with an evict-last L2 policy, so that the operand streams, which pass
+// through L2 once per tile, do not push them out to DRAM between drains.
+__device__ __forceinline__ uint64_t l2_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ float4 ld_keep(const float4* p, uint64_t pol) {
+  float4 v;
+  asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_keep(float4* p, float4 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p),
+               "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol)
+               : "memory");
+}
+
 // The final chunk's tail of one group of 32 accumulators: the running (hi, lo) sums of
 // the earlier chunks (ci > 0) plus the accumulator times its scale, by a two-sum.
 __device__ __forceinline__ void final_tail(bool earlier, const float4* hi4, const float4* lo4,
                                            int grp, const uint32_t (&acc)[32], float scale,
-                                           float (&th)[32], float (&tl)[32]) {
+                                           uint64_t keep, float (&th)[32], float (&tl)[32]) {
   if (earlier) {
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const float4 a4 = hi4[grp + u * 32], b4 = lo4[grp + u * 32];
+      const float4 a4 = ld_keep(hi4 + grp + u * 32, keep), b4 = ld_keep(lo4 + grp + u * 32, keep);
       th[4 * u] = a4.x, th[4 * u + 1] = a4.y, th[4 * u + 2] = a4.z, th[4 * u + 3] = a4.w;
       tl[4 * u] = b4.x, tl[4 * u + 1] = b4.y, tl[4 * u + 2] = b4.z, tl[4 * u + 3] = b4.w;
     }
@@ -524,6 +545,7 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
     // chunk adds hi + lo + acc to head.
     const int q = warp & 3, h = (warp - 2) >> 2, ew = warp - 2;
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+    const uint64_t keep = l2_evict_last();  // the scratch slot's L2 policy
     float4* hi4 = nullptr;
     float4* lo4 = nullptr;
     bool ok = true;
@@ -565,14 +587,15 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
             const int grp = (r * 4 + cl) * 8 * 32;  // float4 offset of this group
             if (final_chunk) {
               float th[32], tl[32];
-              final_tail(ci > 0, hi4, lo4, grp, acc, scale, th, tl);
+              final_tail(ci > 0, hi4, lo4, grp, acc, scale, keep, th, tl);
               if (row < args.n) strip_final(args, th, tl, row, tg.j0 + cg * 32);
             } else {
               float hv[32], lv[32];
               if (ci > 0) {
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                  const float4 a4 = hi4[grp + u * 32], b4 = lo4[grp + u * 32];
+                  const float4 a4 = ld_keep(hi4 + grp + u * 32, keep);
+                  const float4 b4 = ld_keep(lo4 + grp + u * 32, keep);
                   hv[4 * u] = a4.x, hv[4 * u + 1] = a4.y, hv[4 * u + 2] = a4.z, hv[4 * u + 3] = a4.w;
                   lv[4 * u] = b4.x, lv[4 * u + 1] = b4.y, lv[4 * u + 2] = b4.z, lv[4 * u + 3] = b4.w;
                 }
@@ -592,8 +615,10 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
               }
 #pragma unroll
               for (int u = 0; u < 8; ++u) {
-                hi4[grp + u * 32] = make_float4(hv[4 * u], hv[4 * u + 1], hv[4 * u + 2], hv[4 * u + 3]);
-                lo4[grp + u * 32] = make_float4(lv[4 * u], lv[4 * u + 1], lv[4 * u + 2], lv[4 * u + 3]);
+                st_keep(hi4 + grp + u * 32,
+                        make_float4(hv[4 * u], hv[4 * u + 1], hv[4 * u + 2], hv[4 * u + 3]), keep);
+                st_keep(lo4 + grp + u * 32,
+                        make_float4(lv[4 * u], lv[4 * u + 1], lv[4 * u + 2], lv[4 * u + 3]), keep);
               }
             }
           }
@@ -909,6 +934,7 @@ k_ek_pair(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CUt
     const int q = warp & 3, h = (warp - 2) >> 2, ew = warp - 2;
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
     const uint32_t acce_leader = peer_addr(&acc_empty, 0);
+    const uint64_t keep = l2_evict_last();  // the scratch slot's L2 policy
     float4* hi4 = nullptr;
     float4* lo4 = nullptr;
     bool ok = true;
@@ -951,14 +977,15 @@ k_ek_pair(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CUt
           const int grp = cg * 8 * 32;
           if (final_chunk) {
             float th[32], tl[32];
-            final_tail(ci > 0, hi4, lo4, grp, acc, scale, th, tl);
+            final_tail(ci > 0, hi4, lo4, grp, acc, scale, keep, th, tl);
             if (row < args.n) strip_final(args, th, tl, row, jb0 + cg * 32);
           } else {
             float hv[32], lv[32];
             if (ci > 0) {
 #pragma unroll
               for (int u = 0; u < 8; ++u) {
-                const float4 a4 = hi4[grp + u * 32], b4 = lo4[grp + u * 32];
+                const float4 a4 = ld_keep(hi4 + grp + u * 32, keep);
+                const float4 b4 = ld_keep(lo4 + grp + u * 32, keep);
                 hv[4 * u] = a4.x, hv[4 * u + 1] = a4.y, hv[4 * u + 2] = a4.z, hv[4 * u + 3] = a4.w;
                 lv[4 * u] = b4.x, lv[4 * u + 1] = b4.y, lv[4 * u + 2] = b4.z, lv[4 * u + 3] = b4.w;
               }
@@ -977,8 +1004,10 @@ k_ek_pair(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CUt
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-              hi4[grp + u * 32] = make_float4(hv[4 * u], hv[4 * u + 1], hv[4 * u + 2], hv[4 * u + 3]);
-              lo4[grp + u * 32] = make_float4(lv[4 * u], lv[4 * u + 1], lv[4 * u + 2], lv[4 * u + 3]);
+              st_keep(hi4 + grp + u * 32,
+                      make_float4(hv[4 * u], hv[4 * u + 1], hv[4 * u + 2], hv[4 * u + 3]), keep);
+              st_keep(lo4 + grp + u * 32,
+                      make_float4(lv[4 * u], lv[4 * u + 1], lv[4 * u + 2], lv[4 * u + 3]), keep);
             }
           }
         }
