@@ -104,6 +104,25 @@ def stream_traffic():
                                "per element of E, times N^2")
 
 
+def tail_traffic():
+    """DRAM bytes (read + write) per tile and tail K-block of the tensor-core tail, read from
+    the committed summary of its ncu capture (a reduced scale-point electrode); the bench
+    scales it by tiles x K-blocks.  (None, note) when the summary is absent."""
+    import re
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles",
+                        "k_ek_strip_stacked_N8869.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None, "no capture summary"
+    m = re.search(r"\|\s*DRAM bytes per tile and K-block\s*\|\s*([0-9,]+)", text)
+    if not m:
+        return None, "no traffic figure in the capture summary"
+    return float(m.group(1).replace(",", "")), (
+        "ncu dram__bytes_read.sum + dram__bytes_write.sum of both tile launches at N=8,869 "
+        "(profiles/k_ek_strip_stacked_N8869.md), per tile and K-block, times tiles x K-blocks")
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -1235,6 +1254,7 @@ def run_scale_point(args, rank, world, local_rank):
         solve_parts = {"solve_ms": sinfo["t_solve_ms"], "matvec_ms": sinfo["t_solve_matvec_ms"],
                        "replacement_ms": sinfo["t_solve_replace_ms"],
                        "replacements": sinfo["solve_replacements"],
+                       "dc_apply_ms": sinfo["t_solve_dc_ms"],
                        "max_iterations": last_max_iters[0]}
         pot_parts = {"ion_structure_factors_ms": sinfo["t_pot_sf_ms"],
                      "kspace_ms": sinfo["t_pot_kspace_ms"],
@@ -1358,8 +1378,13 @@ def run_scale_point(args, rank, world, local_rank):
                  "ms_per_launch": mv_launch_ms, "bytes_per_launch": mv_bytes,
                  "peak_source": f"{src} hbm_gbs (of measured)",
                  "traffic_source": stream_note}
+    tail_tb, tail_note = tail_traffic()
+    nt_tiles = (n + 255) // 256
     roof = {"bound": "tensor", "achieved": achieved, "peak": sustained, "unit": "TFLOP/s",
-            "frac": achieved / sustained, "traffic": None,
+            "frac": achieved / sustained,
+            "traffic": (tail_tb * nt_tiles * (nt_tiles + 1) // 2 * (n6 + n3 + n1))
+            if tail_tb else None,
+            "traffic_source": tail_note,
             "kernel": "k_ek_strip (tcgen05 k-space tail of the E build, all k-windows)",
             "timed_region": "the timed cpm_build_E (CUDA events around each window's "
                             "tensor-core launches, on the build stream)",
@@ -1369,9 +1394,7 @@ def run_scale_point(args, rank, world, local_rank):
             "frac_of_burst": achieved / burst,
             "issued_tflops": issued_flops / (tc_ms * 1e-3) / 1e12,
             "k_blocks_6_3_1_products": [n6, n3, n1], "k_blocks_fp8": binfo["tc_blocks_fp8"],
-            "tc_ms": tc_ms, "tc_loop_ms": binfo["t_tc_loop_ms"], "head_ms": binfo["t_head_ms"],
-            "traffic_note": "not captured at this size (ncu counters stay on small cases); "
-                            "see the small-case capture of the same kernel in profiles/"}
+            "tc_ms": tc_ms, "tc_loop_ms": binfo["t_tc_loop_ms"], "head_ms": binfo["t_head_ms"]}
     mv_gbs = {r: e_bytes / (t * 1e-3) / 1e9 for r, t in mv.items()}
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,

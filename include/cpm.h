@@ -470,6 +470,8 @@ typedef struct cpm_info_t {
   double t_pot_kspace_ms;    /* the k-space contraction with the electrode operand, */
   double t_pot_real_ms;      /* the real-space sums and b = chi - k_e b^sol (device time) */
   int solve_path;            /* path of the last solve: 1 kernels, 2 cluster-resident */
+  double t_solve_dc_ms;      /* last PCG-DC solve on the kernel path: device time of its
+                                preconditioner applies (z = P r) */
 } cpm_info_t;
 
 int cpm_get_info(cpm_ctx* c, cpm_info_t* out);

@@ -98,6 +98,7 @@ class cpm_info_t(ctypes.Structure):
         ("t_pot_kspace_ms", ctypes.c_double),
         ("t_pot_real_ms", ctypes.c_double),
         ("solve_path", ctypes.c_int),
+        ("t_solve_dc_ms", ctypes.c_double),
     ]
 
 

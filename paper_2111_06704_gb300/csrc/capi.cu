@@ -1418,6 +1418,7 @@ int cpm_get_info(cpm_ctx* c, cpm_info_t* out) {
   out->t_solve_matvec_ms = c->t_solve_mv_ms;
   out->t_solve_replace_ms = c->t_solve_rep_ms;
   out->solve_replacements = c->solve_replacements;
+  out->t_solve_dc_ms = c->t_solve_dc_ms;
   out->t_pot_sf_ms = c->t_pot_sf_ms;
   out->t_pot_kspace_ms = c->t_pot_kspace_ms;
   out->t_pot_real_ms = c->t_pot_real_ms;

@@ -174,7 +174,7 @@ struct Ctx {
   float t_tc_loop_ms = 0; // the tail's window loop (streamed builds: operand planes too)
   // last PCG solve: its device time, that of its matvec launches (fast or exact), of its
   // residual replacements, and their count
-  float t_solve_ms = 0, t_solve_mv_ms = 0, t_solve_rep_ms = 0;
+  float t_solve_ms = 0, t_solve_mv_ms = 0, t_solve_rep_ms = 0, t_solve_dc_ms = 0;
   int solve_replacements = 0;
   std::vector<cudaEvent_t> ev_pool;  // timing events of the solve, made on first use
   // last cpm_potential: the ions' structure factors, the k-space contraction, the real

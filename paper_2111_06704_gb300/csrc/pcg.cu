@@ -758,7 +758,120 @@ __global__ void k_diff_t(int n, int64_t ldv, const double* __restrict__ x,
   const int64_t o = (int64_t)col * ldv;
   float* xc = xdt + ((int64_t)(col / kFastCols) * ldv * kFastCols + col % kFastCols);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    xc[(int64_t)i * kFastCols] = (float)(x[o + i] - xa[o + i]);
+    xc[(int64_t)i * kFastCols] = (float)(xa ? x[o + i] - xa[o + i] : x[o + i]);
+}
+
+// PCG-DC apply of the many-column solves of a float E: z = P r (+ p_gap sum r) for the
+// 16 columns of a group in one pass over P (the per-column kernel above reads P once for
+// every column: at r_cut = 8 A, some 200 entries a row, that is HBM-bound).  rt holds r
+// as floats in the streamed matvec's layout ([group][row][16]).  A warp takes a row at a
+// time, 32 entries per step: one coalesced load of their column indices and values, then
+// four independent 16-byte gathers a lane (lane l: entries 8 k + l / 4, k < 4, columns
+// 4 (l % 4) .. + 3, the index and value passed by shuffles), the eight slots summed by
+// shuffles at the row's end.  The sums are float: P r is the preconditioner's output
+// only (the flexible Polak-Ribiere step tolerates its rounding, ~1e-7 of z) and
+// convergence is decided on replaced residuals.  A block works through a contiguous run
+// of rows, so that neighbouring rows' gathers meet in L1.  The grid's x extent is the
+// dots' part count, as in k_dc_apply; partial dots [r^T z_new, r^T z_old] into slots 0,
+// 1 of every column of the group; rsum_part may be the dots buffer itself (only slot 3
+// is read).
+constexpr int kDcThreads = 512;
+
+__global__ void __launch_bounds__(kDcThreads)
+k_dc_apply_t(int n, int64_t ldv, int nrhs, const ColState* __restrict__ st,
+             const int64_t* __restrict__ off, const int* __restrict__ idx,
+             const double* __restrict__ prow, double pgap, const float* __restrict__ rt,
+             const double* __restrict__ r, double* __restrict__ z,
+             const double* __restrict__ rsum_part, int nparts, double* __restrict__ dots,
+             int first) {
+  constexpr int kWarps = kDcThreads / 32;
+  __shared__ double s_gsum[kFastCols];
+  __shared__ int s_active[kFastCols];
+  __shared__ double s_red[kWarps][kFastCols][2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = blockIdx.y, c0 = grp * kFastCols;
+  for (int cc = warp; cc < kFastCols; cc += kWarps) {  // p_gap sums and active flags
+    const int col = c0 + cc;
+    double sr = 0.0;
+    if (col < nrhs && pgap != 0.0)
+      for (int b = lane; b < nparts; b += 32) sr += rsum_part[((int64_t)b * nrhs + col) * 4 + 3];
+    sr = warp_sum(sr);
+    if (lane == 0) {
+      s_gsum[cc] = pgap * sr;
+      s_active[cc] = col < nrhs && (first || st[col].done == 0);
+    }
+  }
+  __syncthreads();
+  const int slot = lane >> 2, cq = 4 * (lane & 3);
+  // after the shuffles every lane holds its four columns' sums; lane l < 16 finishes
+  // column c = 4 (l % 4) + l / 4, component l / 4 of its float4
+  const int cf = cq + slot, comp = slot;
+  const bool fin = lane < 16 && c0 + cf < nrhs;
+  const bool act = fin && s_active[cf];
+  const double gsum = fin ? s_gsum[cf] : 0.0;
+  const int64_t oz = (int64_t)(c0 + cf) * ldv;
+  const float* rg = rt + (int64_t)grp * ldv * kFastCols + cq;
+  const int per = (n + gridDim.x - 1) / gridDim.x;
+  const int j0 = blockIdx.x * per, j1 = min(n, j0 + per);
+  double v0 = 0.0, v1 = 0.0;
+  for (int j = j0 + warp; j < j1; j += kWarps) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int64_t e1 = off[j + 1];
+    for (int64_t e0 = off[j]; e0 < e1; e0 += 32) {
+      const int left = (int)min((int64_t)32, e1 - e0);  // entries in this step
+      int id = 0;
+      float pe = 0.f;
+      if (lane < left) {
+        id = __ldg(idx + e0 + lane);
+        pe = (float)__ldg(prow + e0 + lane);
+      }
+      float4 rv[4];
+      float pk[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int src = 8 * k + slot;
+        const int ik = __shfl_sync(0xffffffffu, id, src);
+        pk[k] = __shfl_sync(0xffffffffu, pe, src);
+        rv[k] = src < left ? __ldg(reinterpret_cast<const float4*>(rg + (int64_t)ik * kFastCols))
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        acc.x = fmaf(pk[k], rv[k].x, acc.x);
+        acc.y = fmaf(pk[k], rv[k].y, acc.y);
+        acc.z = fmaf(pk[k], rv[k].z, acc.z);
+        acc.w = fmaf(pk[k], rv[k].w, acc.w);
+      }
+    }
+#pragma unroll
+    for (int o = 4; o < 32; o <<= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+      acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
+      acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
+    }
+    if (fin) {
+      const float a = comp == 0 ? acc.x : comp == 1 ? acc.y : comp == 2 ? acc.z : acc.w;
+      const double zn = gsum + (double)a;
+      const double rj = r[oz + j];
+      const double zo = z[oz + j];
+      if (act) z[oz + j] = zn;
+      v0 += rj * zn;
+      v1 += rj * zo;
+    }
+  }
+  if (lane < 16) {
+    s_red[warp][cf][0] = v0;
+    s_red[warp][cf][1] = v1;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * kFastCols) {
+    const int cc = threadIdx.x >> 1, t = threadIdx.x & 1;
+    double sv = 0.0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) sv += s_red[w][cc][t];
+    if (c0 + cc < nrhs) dots[((int64_t)blockIdx.x * nrhs + c0 + cc) * 4 + t] = sv;
+  }
 }
 
 // Columns that broke down in the fast iteration count as converged for the next
@@ -1233,9 +1346,28 @@ int pcg_solve_kernels(Ctx* c, const SolveArgs& a) {
     cudaEventRecord(e, c->stream);
     return e;
   };
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> t_mv, t_rep;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> t_mv, t_rep, t_dc;
   const cudaEvent_t t_begin = ev();
   // cur: the column states (converged columns are skipped), nullptr before they exist
+  // z = P r for PCG-DC: the many-column float path in one pass over P for each group of
+  // 16 columns (r first transposed to floats into the x - x_a buffer, free at this point),
+  // every other solve per column
+  auto dc_apply = [&](const ColState* cur, double* dots_out, int first) {
+    const cudaEvent_t d0 = ev();
+    if (fast) {
+      (k_diff_t<<<g2, kThreads, 0, s>>>(n, ldv, r, nullptr, xdt), note_launch());
+      (k_dc_apply_t<<<dim3(ge, groups), kDcThreads, 0, s>>>(
+           n, ldv, nrhs, cur, (const int64_t*)c->nbr_off.ptr, (const int*)c->nbr_idx.ptr,
+           (const double*)c->prow.ptr, c->pgap, xdt, r, z, dots, ge, dots_out, first),
+       note_launch());
+    } else {
+      (k_dc_apply<<<g2, kThreads, 0, s>>>(n, ldv, nrhs, cur, (const int64_t*)c->nbr_off.ptr,
+                                         (const int*)c->nbr_idx.ptr, (const double*)c->prow.ptr,
+                                         c->pgap, r, z, dots, ge, dots_out, first, a.sys),
+       note_launch());
+    }
+    t_dc.emplace_back(d0, ev());
+  };
   auto matvec = [&](const ColState* cur) {
     if (fast) {  // the inner matvec of a many-column solve
       stream_mv(xt, cur);
@@ -1269,9 +1401,7 @@ int pcg_solve_kernels(Ctx* c, const SolveArgs& a) {
   const int gcol = (nrhs + wb - 1) / wb;
   (k_init_state<<<gcol, wb * 32, 0, s>>>(dots, ge, nrhs, a.tol, pre, st), note_launch());
   if (pre == CPM_PRECOND_DC) {
-    (k_dc_apply<<<g2, kThreads, 0, s>>>(n, ldv, nrhs, st, (const int64_t*)c->nbr_off.ptr,
-                                       (const int*)c->nbr_idx.ptr, (const double*)c->prow.ptr,
-                                       c->pgap, r, z, dots, ge, dots_dc, 1, a.sys), note_launch());
+    dc_apply(st, dots_dc, 1);
     (k_init_rz_dc<<<gcol, wb * 32, 0, s>>>(dots_dc, ge, nrhs, st), note_launch());
   }
   if (f64) (k_p_update<double><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, st, z, p, (double*)pv, nullptr, 1), note_launch());
@@ -1336,11 +1466,7 @@ int pcg_solve_kernels(Ctx* c, const SolveArgs& a) {
           cuda_check(c, cudaMemcpyAsync(ra, r, vbytes, cudaMemcpyDeviceToDevice, s), "anchor r"))
         return CPM_ECUDA;
     }
-    if (pre == CPM_PRECOND_DC)
-      (k_dc_apply<<<g2, kThreads, 0, s>>>(n, ldv, nrhs, cur, (const int64_t*)c->nbr_off.ptr,
-                                         (const int*)c->nbr_idx.ptr, (const double*)c->prow.ptr,
-                                         c->pgap, r, z, dots, ge, dots, 1, nullptr),
-       note_launch());
+    if (pre == CPM_PRECOND_DC) dc_apply(cur, dots, 1);
     (k_replace_state<<<gcol, wb * 32, 0, s>>>(dots, ge, nrhs, a.tol, cur), note_launch());
     (k_p_update<float><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, cur, z, p, (float*)pv, plo, 2, xt),
      note_launch());
@@ -1375,10 +1501,7 @@ int pcg_solve_kernels(Ctx* c, const SolveArgs& a) {
     if (pre == CPM_PRECOND_DC) {
       (k_update<CPM_PRECOND_DC><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, cur, x, r, z, p, q,
                                                        inv_diag, dots, a.sys), note_launch());
-      (k_dc_apply<<<g2, kThreads, 0, s>>>(n, ldv, nrhs, cur, (const int64_t*)c->nbr_off.ptr,
-                                         (const int*)c->nbr_idx.ptr,
-                                         (const double*)c->prow.ptr, c->pgap, r, z, dots, ge,
-                                         dots, 0, a.sys), note_launch());
+      dc_apply(cur, dots, 0);
     } else if (pre == CPM_PRECOND_JACOBI) {
       (k_update<CPM_PRECOND_JACOBI><<<g2, kThreads, 0, s>>>(n, ldv, nrhs, cur, x, r, z, p, q,
                                                            inv_diag, dots, a.sys), note_launch());
@@ -1419,9 +1542,10 @@ int pcg_solve_kernels(Ctx* c, const SolveArgs& a) {
   if (a.timed) {
     float ms = 0;
     cudaEventElapsedTime(&c->t_solve_ms, t_begin, t_end);
-    c->t_solve_mv_ms = c->t_solve_rep_ms = 0;
+    c->t_solve_mv_ms = c->t_solve_rep_ms = c->t_solve_dc_ms = 0;
     for (auto& e : t_mv) c->t_solve_mv_ms += (cudaEventElapsedTime(&ms, e.first, e.second), ms);
     for (auto& e : t_rep) c->t_solve_rep_ms += (cudaEventElapsedTime(&ms, e.first, e.second), ms);
+    for (auto& e : t_dc) c->t_solve_dc_ms += (cudaEventElapsedTime(&ms, e.first, e.second), ms);
     c->solve_replacements = (int)t_rep.size();
   }
   int status = CPM_OK;

@@ -91,14 +91,26 @@ __device__ __forceinline__ void phasor_ff(uint32_t ph, const float4* __restrict_
   ff_add(ah, al, bh, bl, sh, sl);
 }
 
+// (h, l) += x by an error-free two-sum of the high part.
+__device__ __forceinline__ void pair_add1(float& h, float& l, float x) {
+  const float s = h + x;
+  const float bb = s - h;
+  l += (h - (s - bb)) + (x - bb);
+  h = s;
+}
+
+constexpr int kSfBlock = 8;  // ions a float block sum of the tail k-vectors holds
+
 // v[f][c(k)] = sqrt(W_k) sum_I q_I cos(theta_Ik), v[f][c(k) + 64] = sqrt(W_k) sum_I q_I sin,
 // in the column layout of the electrode operand, c(k) = 128 (k / 64) + k % 64, from the
 // exact fixed-point phases.  Sums over the ions run in error-free float pairs (S_K is a
 // sum of O(n_ion) unit phasors whose float partial sums would lose bits; FP64 runs at
-// 1/64 of the float rate here).  The tail k-vectors take float sin/cos from the phasor
-// table (sincos_table, about one ulp); the head (k < kh, the heaviest weights) takes float-pair phasors and
-// goes out in FP64 to vhead for the FP64 head contraction.
-__global__ void __launch_bounds__(kSfThreads)
+// 1/64 of the float rate here); the tail's terms go in float blocks of kSfBlock ions, each
+// block's sum into the pair (a few ulp of a block, not of the whole sum).  The tail
+// k-vectors take float sin/cos from the phasor table (sincos_table, about one ulp); the
+// head (k < kh, the heaviest weights) takes float-pair phasors and goes out in FP64 to
+// vhead for the FP64 head contraction.
+__global__ void __launch_bounds__(kSfThreads, 8)
 k_ion_sf_f32(const uint32_t* __restrict__ sion, const double* __restrict__ ion_q, int n_ion,
              const int* __restrict__ hkl, const double* __restrict__ sqw, int mpad, int kh,
              const float4* __restrict__ turn, float* __restrict__ vout,
@@ -117,6 +129,7 @@ k_ion_sf_f32(const uint32_t* __restrict__ sion, const double* __restrict__ ion_q
   }
   const bool head = k < kh;  // whole blocks take one branch unless they straddle kh
   float reh = 0.f, rel = 0.f, imh = 0.f, iml = 0.f;
+  float rlo = 0.f, ilo = 0.f;  // tail: the charges' low parts times the phasors
   for (int base = 0; base < n_ion; base += kIonChunk) {
     const int cnt = min(kIonChunk, n_ion - base);
     __syncthreads();
@@ -141,17 +154,36 @@ k_ion_sf_f32(const uint32_t* __restrict__ sion, const double* __restrict__ ion_q
         ff_add(imh, iml, ph_, pl_, imh, iml);
       }
     } else {
-      for (int t = 0; t < cnt; ++t) {
+      // blocks of kSfBlock ions summed in float, then added to the pairs by a two-sum;
+      // the charges' low parts (zero for charges that are floats) summed in float apart
+      int t = 0;
+      for (; t + kSfBlock <= cnt; t += kSfBlock) {
+        float br = 0.f, bi = 0.f;
+#pragma unroll
+        for (int u = 0; u < kSfBlock; ++u) {
+          const uint32_t ph = h * sf[t + u][0] + kk * sf[t + u][1] + l * sf[t + u][2];
+          float sn, cs;
+          sincos_table(ph, turn, &sn, &cs);
+          br = fmaf(sqh[t + u], cs, br);
+          bi = fmaf(sqh[t + u], sn, bi);
+          rlo = fmaf(sql[t + u], cs, rlo);
+          ilo = fmaf(sql[t + u], sn, ilo);
+        }
+        pair_add1(reh, rel, br);
+        pair_add1(imh, iml, bi);
+      }
+      for (; t < cnt; ++t) {
         const uint32_t ph = h * sf[t][0] + kk * sf[t][1] + l * sf[t][2];
-        float s, c;
-        sincos_table(ph, turn, &s, &c);
-        pair_fma(reh, rel, sqh[t], sql[t], c);
-        pair_fma(imh, iml, sqh[t], sql[t], s);
+        float sn, cs;
+        sincos_table(ph, turn, &sn, &cs);
+        pair_fma(reh, rel, sqh[t], sql[t], cs);
+        pair_fma(imh, iml, sqh[t], sql[t], sn);
       }
     }
   }
   if (k >= mpad) return;
-  const double re = (double)reh + (double)rel, im = (double)imh + (double)iml;
+  const double re = (double)reh + (double)rel + (double)rlo,
+               im = (double)imh + (double)iml + (double)ilo;
   const double w = sqw[k];
   const size_t kcol = 128 * (size_t)(k >> 6) + (k & 63);  // operand column layout
   float* v = vout + (size_t)f * 2 * mpad;
@@ -266,14 +298,17 @@ k_bsol_kspace(const T* __restrict__ A, int n, int64_t lda, const T* __restrict__
 }
 
 // Streamed builds keep no A: b^sol_k[f][i] = sum_{k >= kh} sqrt(W_k) [cos(K.r_i) v_c +
-// sin(K.r_i) v_s] with the electrode phases formed on the fly (fixed point, sincos_table)
-// and the terms summed in error-free float pairs.  One thread per electrode atom and up to
+// sin(K.r_i) v_s] with the electrode phases formed on the fly (fixed point, sincos_table);
+// the terms of kDirectBlock consecutive k-vectors are summed in float, and each block's
+// sum goes into an error-free float pair (a two-sum), so the rounding of the plain sums
+// grows with the block, not with the ~10^5 k-vectors.  One thread per electrode atom and up to
 // kDirectFrames frames per block: each phasor is formed once and used for every frame of
 // the block; the k-vectors of a chunk and their structure factors are staged in shared
 // memory.  Frames go in pairs through paired float instructions (two IEEE results an
 // instruction, a - b as fma(b, -1, a)): the values are those of one frame at a time.
 constexpr int kDirectChunk = 128;
 constexpr int kDirectFrames = 16;
+constexpr int kDirectBlock = 8;  // divides every chunk: head and table ends are multiples of 16
 
 __global__ void __launch_bounds__(128, 4)
 k_bsol_kspace_direct(const uint32_t* __restrict__ sfix, int n, const int* __restrict__ hkl,
@@ -325,15 +360,26 @@ k_bsol_kspace_direct(const uint32_t* __restrict__ sfix, int n, const int* __rest
     }
     __syncthreads();
     if (i >= n) continue;
-    for (int t = 0; t < cnt; ++t) {
-      float sn, cs;
-      sincos_table(sh[t][0] * u0 + sh[t][1] * u1 + sh[t][2] * u2, turn, &sn, &cs);
-      const float2 sn2 = make_float2(sn, sn), cs2 = make_float2(cs, cs);
+    for (int tb = 0; tb < cnt; tb += kDirectBlock) {
+      float2 blk[kDirectFrames / 2];
+#pragma unroll
+      for (int f = 0; f < kDirectFrames / 2; ++f) blk[f] = make_float2(0.f, 0.f);
+#pragma unroll 2
+      for (int tt = 0; tt < kDirectBlock; ++tt) {
+        const int t = tb + tt;
+        float sn, cs;
+        sincos_table(sh[t][0] * u0 + sh[t][1] * u1 + sh[t][2] * u2, turn, &sn, &cs);
+        const float2 sn2 = make_float2(sn, sn), cs2 = make_float2(cs, cs);
+#pragma unroll
+        for (int f = 0; f < kDirectFrames / 2; ++f) {
+          const float4 vv = sv[t][f];
+          blk[f] = __ffma2_rn(sn2, make_float2(vv.z, vv.w),
+                              __ffma2_rn(cs2, make_float2(vv.x, vv.y), blk[f]));
+        }
+      }
 #pragma unroll
       for (int f = 0; f < kDirectFrames / 2; ++f) {
-        const float4 vv = sv[t][f];
-        const float2 term = __ffma2_rn(sn2, make_float2(vv.z, vv.w),
-                                       __fmul2_rn(cs2, make_float2(vv.x, vv.y)));
+        const float2 term = blk[f];
         const float2 s2 = __fadd2_rn(hi[f], term);
         const float2 bb = __ffma2_rn(hi[f], m1, s2);                          // s2 - hi
         const float2 a = __ffma2_rn(__ffma2_rn(bb, m1, s2), m1, hi[f]);       // hi - (s2 - bb)
@@ -403,22 +449,27 @@ __device__ __forceinline__ double pair_images(const double* ri, double ai, const
 
 // Real-space electrode-ion sums, slab dipole term, and b = chi - k_e b^sol.
 // Four warps, 32 electrode atoms each (one a lane); ions staged through shared memory in
-// chunks.  Every image of a pair is at least as far as its nearest one, so a pair whose
-// nearest image lies beyond r_c contributes nothing: each lane screens its atom against
-// every ion in float from the exact fixed-point coordinate difference (off by < 1e-3 A^2
-// in r^2, against a band of 0.01 A^2).  The pairs that pass go to one of two per-warp
-// queues that outlive the chunks and are evaluated 32 at a time, all lanes busy, each
-// atom then adding its queued values in queue order:
-//   near pairs (and every pair when a box edge is below 2 r_c): FP64 over their images,
-//     from the ions' FP64 coordinates kept in the queue;
-//   far pairs (one image per direction, r^2 >= r_split^2 where erfc(g r) / r <= 1e-4 1/A,
-//     r^2 below r_c^2 by more than the float error, alpha r >= 6 so that the Gaussian term
-//     has vanished): float, from the screen's r^2 (~1e-7 relative), the term to ~1e-6 of
-//     itself (<= 1e-10 1/A a pair), summed in float apart and added at the end.
-// No warp runs both arithmetic paths in one pass.  The float constants of the screen come
-// from the host: FP64 runs at 1/64 of the float rate here, and a constant formed from the
-// FP64 parameters would otherwise be re-formed inside the loop.
+// chunks.  Each lane screens its atom against every ion and every image of it that can
+// lie within r_c: the nearest image from the exact fixed-point coordinate difference,
+// plus the host's list of whole-box shifts (just the zero shift when every box edge
+// exceeds 2 r_c), in float (off by < 1e-3 A^2 in r^2, against a band of 0.01 A^2).  The
+// images that pass go to one of two per-warp queues that outlive the chunks and are
+// evaluated 32 at a time, all lanes busy, each atom then adding its queued values in
+// queue order:
+//   near images: FP64, from the FP64 coordinates kept in the queue, the image fixed by
+//     the fixed-point nearest one and the shift (so the screen and the sum agree on it);
+//   far images (r^2 >= r_split^2 where erfc(g r) / r <= 1e-4 1/A, r^2 below r_c^2 by more
+//     than the float error, alpha r >= 6 so that the Gaussian term has vanished): float,
+//     from the screen's r^2 (~1e-7 relative; the term to ~1e-6 of itself, <= 1e-10 1/A),
+//     summed in float apart and added at the end.
+// No warp runs both arithmetic paths in one pass.  A box so small that more than
+// kMaxShifts shifts would be needed takes every image of a screened pair in FP64 instead.
+// The float constants of the screen come from the host: FP64 runs at 1/64 of the float
+// rate here, and a constant formed from the FP64 parameters would otherwise be re-formed
+// inside the loop.
 constexpr int kRealWarps = 4;
+
+constexpr int kMaxShifts = 64;
 
 struct RealScreen {
   float fs[3];    // L / 2^32: fixed-point units of each coordinate, A
@@ -427,6 +478,9 @@ struct RealScreen {
   float far2;     // r_split^2 (r_c^2 when no pair is far)
   float g;        // Ewald splitting parameter, 1/A
   int all_single; // every box edge above 2 r_c
+  int nshift;     // whole-box shifts screened (0: every image of a pair in FP64)
+  float shift[kMaxShifts][3];       // k L, A
+  signed char kshift[kMaxShifts][3];  // k
 };
 
 RealScreen real_screen(const Geometry& geo, double rsplit2) {
@@ -438,9 +492,33 @@ RealScreen real_screen(const Geometry& geo, double rsplit2) {
   rs.far2 = (float)rsplit2;
   rs.g = (float)geo.g;
   rs.all_single = 2.0 * geo.rc < geo.L[0] && 2.0 * geo.rc < geo.L[1] && 2.0 * geo.rc < geo.L[2];
+  // shifts k with |k| <= floor((r_c + L / 2) / L) per direction (only k = 0 where
+  // L > 2 r_c): every image within r_c of an atom, given the nearest one
+  int m[3], total = 1;
+  for (int u = 0; u < 3; ++u) {
+    m[u] = 2.0 * geo.rc < geo.L[u] ? 0 : (int)floor((geo.rc + 0.5 * geo.L[u]) / geo.L[u]);
+    total *= 2 * m[u] + 1;
+  }
+  rs.nshift = total <= kMaxShifts ? total : 0;
+  int k = 0;
+  for (int a = -m[0]; rs.nshift && a <= m[0]; ++a)
+    for (int b = -m[1]; b <= m[1]; ++b)
+      for (int c = -m[2]; c <= m[2]; ++c, ++k) {
+        const int ks[3] = {a, b, c};
+        for (int u = 0; u < 3; ++u) {
+          rs.shift[k][u] = (float)(ks[u] * geo.L[u]);
+          rs.kshift[k][u] = (signed char)ks[u];
+        }
+      }
   return rs;
 }
 
+// Screen modes: every box edge above 2 r_c (the nearest image only, near and far queues),
+// a list of whole-box shifts (each shifted image screened, near and far queues), or every
+// image of a screened pair in FP64 (boxes needing more than kMaxShifts shifts).
+enum RealMode { kSingleImage = 0, kShiftList = 1, kAllImages = 2 };
+
+template <int kMode>
 __global__ void __launch_bounds__(kRealWarps * 32, 6)
 k_bsol_real(const double* __restrict__ xyz, const double* __restrict__ alpha,
             const uint32_t* __restrict__ sfix, int n, const double* __restrict__ ion_xyz,
@@ -449,9 +527,12 @@ k_bsol_real(const double* __restrict__ xyz, const double* __restrict__ alpha,
             double dip, const double* __restrict__ chi, const double* __restrict__ bsol_k,
             double* __restrict__ b_out, double* __restrict__ qsol) {
   __shared__ double sx[kIonChunk][4];
-  __shared__ uint32_t su[kIonChunk][3];
+  __shared__ uint4 su[kIonChunk];  // fixed-point x, y, z (and a pad: one 16-byte load)
   __shared__ double sa[kRealWarps * 32][4];   // the block's atoms: x, y, z, alpha
-  __shared__ double nq[kRealWarps][64][4];    // near queue: ion x, y, z, q
+  __shared__ double nq[kRealWarps][64][4];    // near queue: ion x, y, z, q,
+  constexpr int kShiftWarps = kMode == kShiftList ? kRealWarps : 1;
+  __shared__ int32_t ndl[kShiftWarps][64][3];  //   the fixed-point difference, the shift
+  __shared__ uint8_t nsh[kShiftWarps][64];
   __shared__ float2 fq[kRealWarps][64];       // far queue: r^2, q
   __shared__ uint8_t nlane[kRealWarps][64], flane[kRealWarps][64];
   __shared__ double qval[kRealWarps][32];
@@ -478,14 +559,39 @@ k_bsol_real(const double* __restrict__ xyz, const double* __restrict__ alpha,
   const double rc2 = rc * rc;
   const double invL[3] = {1.0 / lx, 1.0 / ly, 1.0 / lz};
   const bool single[3] = {2.0 * rc < lx, 2.0 * rc < ly, 2.0 * rc < lz};
-  // evaluates the first `cnt` queued pairs (one a lane); each atom adds its values in
+  // evaluates the first `cnt` queued images (one a lane); each atom adds its values in
   // queue order
   auto drain = [&](int cnt, double& acc) {
     __syncwarp();
     if (lane < cnt) {
       const int a = nlane[warp][lane];
-      qval[warp][lane] = pair_images(sa[warp * 32 + a], sa[warp * 32 + a][3], nq[warp][lane],
-                                     L, invL, single, rc, rc2, g);
+      const double* at = sa[warp * 32 + a];
+      const double* ion = nq[warp][lane];
+      if constexpr (kMode == kShiftList) {
+        // the image: the fixed-point nearest one (whole boxes k from the FP64 difference)
+        // plus the queued shift (with every edge above 2 r_c the shift is zero, and the
+        // nearest image by rint below is the same but where it lies beyond r_c)
+        const int si = nsh[warp][lane];
+        double r2 = 0.0;
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          const double dd = at[u] - ion[u];
+          const double dfx = (double)ndl[warp][lane][u] * (L[u] * 0x1p-32);
+          const double k = rint((dd - dfx) * invL[u]) - (double)rs.kshift[si][u];
+          const double du = dd - k * L[u];
+          r2 += du * du;
+        }
+        double v = 0.0;
+        if (r2 < rc2 && r2 > 0.0) {
+          const double r = sqrt(r2);
+          double e = erfc(g * r);
+          if (at[3] * r < 6.0) e -= erfc(at[3] * r);
+          v = ion[3] * e / r;
+        }
+        qval[warp][lane] = v;
+      } else {
+        qval[warp][lane] = pair_images(at, at[3], ion, L, invL, single, rc, rc2, g);
+      }
     }
     __syncwarp();
     for (int k = 0; k < cnt; ++k)
@@ -517,60 +623,88 @@ k_bsol_real(const double* __restrict__ xyz, const double* __restrict__ alpha,
       sx[t][1] = ix[3 * (base + t) + 1];
       sx[t][2] = ix[3 * (base + t) + 2];
       sx[t][3] = iq[base + t];
-      su[t][0] = iu[3 * (base + t)];
-      su[t][1] = iu[3 * (base + t) + 1];
-      su[t][2] = iu[3 * (base + t) + 2];
+      su[t] = make_uint4(iu[3 * (base + t)], iu[3 * (base + t) + 1], iu[3 * (base + t) + 2], 0u);
       qz += sx[t][3] * sx[t][2];
       qs += sx[t][3];
     }
     __syncthreads();
+    const int ns = kMode == kShiftList ? rs.nshift : 1;
     for (int t = 0; t < cnt; ++t) {
-      bool near = false, far = false;
-      float m2 = 0.f;
+      int32_t dl[3] = {0, 0, 0};
+      float dn[3] = {0.f, 0.f, 0.f};  // the nearest image
       if (i < n) {
+        const uint4 ut = su[t];
+        dl[0] = (int32_t)(ui[0] - ut.x);
+        dl[1] = (int32_t)(ui[1] - ut.y);
+        dl[2] = (int32_t)(ui[2] - ut.z);
 #pragma unroll
-        for (int u = 0; u < 3; ++u) {
-          const float du = (float)(int32_t)(ui[u] - su[t][u]) * rs.fs[u];  // nearest image
-          m2 = fmaf(du, du, m2);
-        }
-        far = rs.all_single && m2 >= rs.far2 && m2 < rs.cut2 && af2 * m2 >= 36.0f;
-        near = !far && m2 < rs.screen2;
+        for (int u = 0; u < 3; ++u) dn[u] = (float)dl[u] * rs.fs[u];
       }
-      const unsigned mn = __ballot_sync(0xffffffffu, near);
-      const unsigned mf = __ballot_sync(0xffffffffu, far);
-      if (near) {
-        const int at = qn + __popc(mn & below);
-        nq[warp][at][0] = sx[t][0];
-        nq[warp][at][1] = sx[t][1];
-        nq[warp][at][2] = sx[t][2];
-        nq[warp][at][3] = sx[t][3];
-        nlane[warp][at] = (uint8_t)lane;
-      }
-      if (far) {
-        const int at = fn + __popc(mf & below);
-        fq[warp][at] = make_float2(m2, (float)sx[t][3]);
-        flane[warp][at] = (uint8_t)lane;
-      }
-      qn += __popc(mn);
-      fn += __popc(mf);
-      if (qn >= 32) {
-        drain(32, acc);
-        if (lane < qn - 32) {
+      for (int si = 0; si < ns; ++si) {
+        bool near = false, far = false;
+        float m2 = 0.f;
+        if (i < n) {
+          if constexpr (kMode == kShiftList) {
 #pragma unroll
-          for (int c = 0; c < 4; ++c) nq[warp][lane][c] = nq[warp][32 + lane][c];
-          nlane[warp][lane] = nlane[warp][32 + lane];
+            for (int u = 0; u < 3; ++u) {
+              const float du = dn[u] + rs.shift[si][u];
+              m2 = fmaf(du, du, m2);
+            }
+          } else {
+            m2 = fmaf(dn[0], dn[0], fmaf(dn[1], dn[1], dn[2] * dn[2]));
+          }
+          if constexpr (kMode != kAllImages)
+            far = m2 >= rs.far2 && m2 < rs.cut2 && af2 * m2 >= 36.0f;
+          near = !far && m2 < rs.screen2;
         }
-        qn -= 32;
-        __syncwarp();
-      }
-      if (fn >= 32) {
-        drain_far(32, accf);
-        if (lane < fn - 32) {
-          fq[warp][lane] = fq[warp][32 + lane];
-          flane[warp][lane] = flane[warp][32 + lane];
+        const unsigned mn = __ballot_sync(0xffffffffu, near);
+        const unsigned mf = __ballot_sync(0xffffffffu, far);
+        if ((mn | mf) == 0u) continue;  // no lane's image passed (most steps)
+        if (near) {
+          const int at = qn + __popc(mn & below);
+          nq[warp][at][0] = sx[t][0];
+          nq[warp][at][1] = sx[t][1];
+          nq[warp][at][2] = sx[t][2];
+          nq[warp][at][3] = sx[t][3];
+          if constexpr (kMode == kShiftList) {
+            ndl[warp][at][0] = dl[0];
+            ndl[warp][at][1] = dl[1];
+            ndl[warp][at][2] = dl[2];
+            nsh[warp][at] = (uint8_t)si;
+          }
+          nlane[warp][at] = (uint8_t)lane;
         }
-        fn -= 32;
-        __syncwarp();
+        if (far) {
+          const int at = fn + __popc(mf & below);
+          fq[warp][at] = make_float2(m2, (float)sx[t][3]);
+          flane[warp][at] = (uint8_t)lane;
+        }
+        qn += __popc(mn);
+        fn += __popc(mf);
+        if (qn >= 32) {
+          drain(32, acc);
+          if (lane < qn - 32) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) nq[warp][lane][c] = nq[warp][32 + lane][c];
+            if constexpr (kMode == kShiftList) {
+#pragma unroll
+              for (int c = 0; c < 3; ++c) ndl[warp][lane][c] = ndl[warp][32 + lane][c];
+              nsh[warp][lane] = nsh[warp][32 + lane];
+            }
+            nlane[warp][lane] = nlane[warp][32 + lane];
+          }
+          qn -= 32;
+          __syncwarp();
+        }
+        if (fn >= 32) {
+          drain_far(32, accf);
+          if (lane < fn - 32) {
+            fq[warp][lane] = fq[warp][32 + lane];
+            flane[warp][lane] = flane[warp][32 + lane];
+          }
+          fn -= 32;
+          __syncwarp();
+        }
       }
     }
   }
@@ -879,9 +1013,12 @@ void launch_bsol_real_and_finish(const double* xyz, const double* alpha, const u
     lo = hi;
   }
   const RealScreen rs = real_screen(geo, lo * lo);
-  (k_bsol_real<<<grid, kRealWarps * 32, 0, s>>>(xyz, alpha, sfix, n, ion_xyz, ion_q, sion, n_ion,
-                                               geo.L[0], geo.L[1], geo.L[2], geo.g, geo.rc, rs,
-                                               dip, chi, bsol_k, b_out, qsol),
+  auto kernel = rs.all_single ? k_bsol_real<kSingleImage>
+                : rs.nshift   ? k_bsol_real<kShiftList>
+                              : k_bsol_real<kAllImages>;
+  (kernel<<<grid, kRealWarps * 32, 0, s>>>(xyz, alpha, sfix, n, ion_xyz, ion_q, sion, n_ion,
+                                          geo.L[0], geo.L[1], geo.L[2], geo.g, geo.rc, rs, dip,
+                                          chi, bsol_k, b_out, qsol),
    note_launch());
 }
 

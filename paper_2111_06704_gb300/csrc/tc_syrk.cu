@@ -30,8 +30,6 @@
 
 #include <algorithm>
 #include <cmath>
-#include <stdlib.h>
-#include <string.h>
 
 #include "async_copy.cuh"
 #include "cpm_internal.cuh"
@@ -42,32 +40,6 @@ namespace {
 
 constexpr int kTile = 128;           // output tile edge
 constexpr int kBlockK = 64;          // operand columns per K-block of the schedule
-
-// As mbar_wait, with cluster-scope acquire: for barriers that the peer CTA of a pair
-// arrives on (its writes before the arrival are visible after the wait).
-__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity, int* err, int code) {
-  const long long t0 = clock64();
-  for (unsigned it = 0;; ++it) {
-    if (mbar_try_wait_cluster(bar, parity)) return true;
-    if ((it & 255u) == 255u) {
-      if (*(volatile int*)err) return false;
-      if (clock64() - t0 > kWaitCycles) break;
-    }
-  }
-  atomicCAS(err, 0, code);
-  return false;
-}
 
 // Shared-memory matrix descriptor: K-major tile, 128-byte swizzle, rows of 128 B,
 // 8-row groups 1024 B apart (SBO), version 1, layout type 2 (SWIZZLE_128B).
@@ -640,398 +612,6 @@ k_ek_strip(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CU
   }
 }
 
-// ---- the CTA-pair kernel (tcgen05 cta_group::2) ------------------------------------
-//
-// A two-CTA cluster computes tile row block I (256 rows) against column blocks J0 and
-// J0 + 1 (J0 even; J0 alone where J0 + 1 > I) with M = 256, N = 256 MMAs: the A operand's
-// 256 rows are split between the CTAs (rank r holds rows i0 + 128 r ..), and so is each
-// block's B operand; the MMA hardware reads the peer's halves from the peer's shared
-// memory at the same offsets.  Each CTA's TMEM holds its 128 rows of both blocks (columns
-// 0-255: J0, 256-511: J0 + 1).  Against one CTA per 256 x 256 tile, an SM loads 384 rows
-// instead of 512 per K column for the same 65,536 outputs: a quarter less operand traffic
-// per MMA, and more of the K range in flight in the same shared memory.
-//
-// Each CTA loads its own halves by TMA onto its own full barrier; the peer's (otherwise
-// idle) MMA warp relays each completed stage to the leader's full barrier (two arrivals:
-// the leader's own expect-tx arrival and the relay).  The leader's single MMA thread issues
-// every MMA and commits their completion to the stage's empty barrier of both CTAs, and
-// a chunk's end to both CTAs' accumulator barriers; the epilogue warps of both CTAs report
-// a drained accumulator to the leader's acc_empty (16 arrivals).  Chunks, scales, drains
-// into the per-SM hi / lo scratch and the final write are those of k_ek_strip, per CTA
-// over its 128 rows.  Every wait is bounded.
-constexpr int kPairThreads = 320;  // 10 warps: TMA, MMA (leader) / relay (peer), 8 epilogue
-
-template <bool SIX>
-struct PairCfg {
-  static constexpr int kPlanes = SIX ? 3 : 2;   // planes of a narrow (32-column) stage
-  static constexpr int kProds = SIX ? 6 : 3;    // products of a narrow stage
-  static constexpr int kStageBytes = (SIX ? 72 : 48) * 1024;
-  static constexpr int kStages = SIX ? 3 : 4;
-};
-
-// Pair tile `pair`: row block I, first column block J0 = 2 (pair - P(I)) with
-// P(I) = floor((I + 1)^2 / 4) pairs in rows 0 .. I-1; nb = 2 column blocks unless
-// J0 + 1 > I.
-struct PairTile {
-  int I, J0, i0, j0, nb;
-  __device__ explicit PairTile(int pair) {
-    I = max(0, (int)(2.0 * sqrt((double)pair)) - 1);
-    while ((I + 2) * (I + 2) / 4 <= pair) ++I;
-    while (I > 0 && (I + 1) * (I + 1) / 4 > pair) --I;
-    J0 = 2 * (pair - (I + 1) * (I + 1) / 4);
-    i0 = I * kStripTile;
-    j0 = J0 * kStripTile;
-    nb = J0 + 1 <= I ? 2 : 1;
-  }
-};
-
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-
-// Shared::cluster address of the object at the same offset as `p` in CTA `rank`.
-__device__ __forceinline__ uint32_t peer_addr(const void* p, uint32_t rank) {
-  uint32_t a;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(smem_addr(p)), "r"(rank));
-  return a;
-}
-
-__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
-               : "memory");
-}
-
-__device__ __forceinline__ void pair_cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" :::
-                   "memory");
-}
-
-__device__ __forceinline__ void mma2_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void mma2_f8(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                        uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-// Arrives on the barrier at shared::cluster address `bar` (this CTA's or the peer's) once
-// the MMAs issued so far by this thread have completed.
-__device__ __forceinline__ void mma2_commit(uint32_t bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-      : "memory");
-}
-
-// Instruction descriptors with M = 256 (cta_group::2).
-__host__ __device__ constexpr uint32_t idesc2_f16(bool bf16, int n) {
-  return (1u << 4) | (bf16 ? (1u << 7) | (1u << 10) : 0u) | ((uint32_t)(n >> 3) << 17) |
-         ((uint32_t)(256 >> 4) << 24);
-}
-__host__ __device__ constexpr uint32_t idesc2_f8(int n) {
-  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(256 >> 4) << 24);
-}
-
-template <bool SIX>
-__global__ void __launch_bounds__(kPairThreads, 1)
-k_ek_pair(const __grid_constant__ CUtensorMap map0w, const __grid_constant__ CUtensorMap map0n,
-          const __grid_constant__ CUtensorMap map1n, const __grid_constant__ CUtensorMap map2n,
-          const __grid_constant__ CUtensorMap map8, StripArgs args) {
-  using Cfg = PairCfg<SIX>;
-  constexpr int kStages = Cfg::kStages, kStageBytes = Cfg::kStageBytes;
-  constexpr int P = Cfg::kPlanes;
-  constexpr int kNarrow = kTile * 32 * 2, kWide = kTile * 64 * 2;  // 8 KB and 16 KB halves
-  extern __shared__ __align__(1024) uint8_t smem_raw[];
-  uint8_t* ring = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages];
-  __shared__ __align__(8) uint64_t acc_full, acc_empty, mma_done;
-  __shared__ uint32_t tmem_base_s;
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t rank = cluster_rank();
-  const bool leader = rank == 0;
-  // the stage sequence of one tile (the same for every tile and in both CTAs)
-  const int nnarrow =
-      2 * (SIX ? args.kb_end - args.kb_begin
-               : max(0, min(args.kb_end, args.kb3_end) - args.kb_begin));
-  const int kb1 = max(args.kb_begin, args.kb3_end);
-  const int kb8 = SIX ? args.kb_end : max(args.kb_begin, args.kb8_begin);
-  const int nwide = SIX ? 0 : max(0, min(args.kb_end, kb8) - kb1);
-  const int t8 = nnarrow + nwide;
-  const int nst = t8 + (SIX ? 0 : max(0, args.kb_end - kb8) / 2);
-  auto stage_block = [&](int t, bool& last_of_block) {
-    if (t < nnarrow) {
-      last_of_block = (t & 1) != 0;
-      return args.kb_begin + t / 2;
-    }
-    last_of_block = true;
-    if (t < t8) return kb1 + (t - nnarrow);
-    return kb8 + 2 * (t - t8) + 1;
-  };
-  auto chunk_ends = [&](int t) {
-    if (t + 1 == nst) return true;
-    bool last;
-    const int g = stage_block(t, last);
-    return last && ((args.chunk_end[g >> 5] >> (g & 31)) & 1u) != 0u;
-  };
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(&full_bar[s], leader ? 2 : 1);  // leader: its own arrival + the relay
-      mbar_init(&empty_bar[s], 1);
-    }
-    mbar_init(&acc_full, 1);
-    mbar_init(&acc_empty, 16);  // eight epilogue warps of each CTA (leader's barrier)
-    mbar_init(&mma_done, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
-                     smem_addr(&tmem_base_s))
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
-  }
-  tc_fence_before();
-  __syncthreads();
-  pair_cluster_sync();  // both CTAs' barriers exist before anything reaches them
-  tc_fence_after();
-  const uint32_t tmem = tmem_base_s;
-  const int pair0 = (int)(blockIdx.x >> 1), pstep = (int)(gridDim.x >> 1);
-
-  if (warp == 0) {
-    // ---- TMA producer (both CTAs): this CTA's halves onto its own full barrier ------
-    if (lane == 0) {
-      uint32_t g = 0;
-      bool ok = true;
-      for (int pr = pair0; pr < args.tiles && ok; pr += pstep) {
-        const PairTile tg(pr);
-        const int ra = tg.i0 + (int)rank * kTile;  // this CTA's A rows
-        for (int t = 0; t < nst; ++t, ++g) {
-          const int s = g % kStages;
-          ok = mbar_wait(&empty_bar[s], ((g / kStages) & 1) ^ 1, args.err, 21);
-          if (!ok) break;
-          uint8_t* st = ring + s * kStageBytes;
-          if (t < nnarrow) {
-            // A plane p at slot p, B plane p block h at slot P + 2 p + h (8 KB each)
-            const int x = (args.kb_begin - args.kb_col0) * kBlockK + t * 32;
-            mbar_expect_tx(&full_bar[s], P * (1 + tg.nb) * kNarrow);
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-              const CUtensorMap* mp = p == 0 ? &map0n : p == 1 ? &map1n : &map2n;
-              tma_load_2d(st + p * kNarrow, mp, &full_bar[s], x, ra);
-              for (int h = 0; h < tg.nb; ++h)
-                tma_load_2d(st + (P + 2 * p + h) * kNarrow, mp, &full_bar[s], x,
-                            tg.j0 + h * kStripTile + (int)rank * kTile);
-            }
-          } else {
-            // one plane, 128-byte rows: A at 0, B block h at (1 + h) x 16 KB
-            const CUtensorMap* mp = t >= t8 ? &map8 : &map0w;
-            const int x = t >= t8 ? (kb8 - args.kb_col0 + 2 * (t - t8)) * kBlockK
-                                  : (kb1 - args.kb_col0 + (t - nnarrow)) * kBlockK;
-            mbar_expect_tx(&full_bar[s], (1 + tg.nb) * kWide);
-            tma_load_2d(st, mp, &full_bar[s], x, ra);
-            for (int h = 0; h < tg.nb; ++h)
-              tma_load_2d(st + (1 + h) * kWide, mp, &full_bar[s], x,
-                          tg.j0 + h * kStripTile + (int)rank * kTile);
-          }
-        }
-      }
-      // on the way out (normal or not), the copies of the last stages issued have landed
-      // (their phases completed) before the CTA may leave; a short bound on the error path
-      for (uint32_t u = g > (uint32_t)kStages ? g - kStages : 0; u < g; ++u)
-        if (!mbar_wait_drain(&full_bar[u % kStages], (u / kStages) & 1)) break;
-    }
-  } else if (warp == 1) {
-    if (lane == 0 && !leader) {
-      // ---- relay (peer): each stage of this CTA landed -> the leader's full barrier --
-      const uint32_t remote0 = peer_addr(&full_bar[0], 0);
-      uint32_t g = 0;
-      bool ok = true;
-      for (int pr = pair0; pr < args.tiles && ok; pr += pstep)
-        for (int t = 0; t < nst; ++t, ++g) {
-          const int s = g % kStages;
-          ok = mbar_wait(&full_bar[s], (g / kStages) & 1, args.err, 22);
-          if (!ok) break;
-          mbar_arrive_remote(remote0 + (uint32_t)s * 8u);
-        }
-    } else if (lane == 0) {
-      // ---- MMA issuer (leader) --------------------------------------------------------
-      constexpr uint32_t kPa = 0x210100u, kPb = 0x012010u;
-      constexpr uint32_t kId = idesc2_f16(SIX, 256), kId8 = idesc2_f8(256);
-      uint32_t empty_mine[kStages], empty_peer[kStages];
-      for (int s = 0; s < kStages; ++s) {
-        empty_mine[s] = smem_addr(&empty_bar[s]);
-        empty_peer[s] = peer_addr(&empty_bar[s], 1);
-      }
-      const uint32_t accf_mine = smem_addr(&acc_full), accf_peer = peer_addr(&acc_full, 1);
-      uint32_t g = 0, chunk = 0;
-      bool ok = true, issued = false;
-      for (int pr = pair0; pr < args.tiles && ok; pr += pstep) {
-        const PairTile tg(pr);
-        bool first = true;
-        for (int t = 0; t < nst; ++t, ++g) {
-          const int s = g % kStages;
-          ok = mbar_wait_cluster(&full_bar[s], (g / kStages) & 1, args.err, 23);
-          if (!ok) break;
-          if (first && chunk > 0) {  // both CTAs' epilogues have read the previous chunk
-            ok = mbar_wait_cluster(&acc_empty, (chunk - 1) & 1, args.err, 24);
-            if (!ok) break;
-          }
-          tc_fence_after();
-          const uint32_t st = smem_addr(ring + s * kStageBytes);
-          if (t < nnarrow) {
-#pragma unroll
-            for (int ks = 0; ks < 2; ++ks)
-              for (int h = 0; h < tg.nb; ++h)
-#pragma unroll
-                for (int p = 0; p < Cfg::kProds; ++p) {
-                  const int pa = (kPa >> (4 * p)) & 15, pb = (kPb >> (4 * p)) & 15;
-                  const uint64_t da = smem_desc<32>(st + pa * kNarrow + ks * 32);
-                  const uint64_t db = smem_desc<32>(st + (P + 2 * pb + h) * kNarrow + ks * 32);
-                  mma2_f16(tmem + (uint32_t)(h * 256), da, db, kId,
-                           (first && ks == 0 && p == 0) ? 0u : 1u);
-                }
-          } else {
-            const bool f8 = t >= t8;
-#pragma unroll
-            for (int ks = 0; ks < 4; ++ks)
-              for (int h = 0; h < tg.nb; ++h) {
-                const uint64_t da = smem_desc<64>(st + ks * 32);
-                const uint64_t db = smem_desc<64>(st + (1 + h) * kWide + ks * 32);
-                if (f8) mma2_f8(tmem + (uint32_t)(h * 256), da, db, kId8, (first && ks == 0) ? 0u : 1u);
-                else mma2_f16(tmem + (uint32_t)(h * 256), da, db, kId, (first && ks == 0) ? 0u : 1u);
-              }
-          }
-          issued = true;
-          first = false;
-          mma2_commit(empty_mine[s]);
-          mma2_commit(empty_peer[s]);
-          if (chunk_ends(t)) {
-            mma2_commit(accf_mine);
-            mma2_commit(accf_peer);
-            ++chunk;
-            first = true;
-          }
-        }
-      }
-      // every MMA issued has completed before the TMEM is given back
-      if (issued) {
-        mma2_commit(smem_addr(&mma_done));
-        if (!mbar_wait_drain(&mma_done, 0)) atomicCAS(args.err, 0, 27);
-      }
-    }
-  } else {
-    // ---- epilogue: warps 2-9 of both CTAs; lane quarter q = warp % 4, block h ---------
-    const int q = warp & 3, h = (warp - 2) >> 2, ew = warp - 2;
-    const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-    const uint32_t acce_leader = peer_addr(&acc_empty, 0);
-    const uint64_t keep = l2_evict_last();  // the scratch slot's L2 policy
-    float4* hi4 = nullptr;
-    float4* lo4 = nullptr;
-    bool ok = true;
-    {
-      uint32_t smid;
-      asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
-      if ((int)smid < args.scratch_slots) {
-        hi4 = reinterpret_cast<float4*>(args.scratch + (size_t)smid * 2 * 65536) +
-              (size_t)ew * 8 * 8 * 32 + lane;
-        lo4 = hi4 + 65536 / 4;
-      } else {
-        atomicCAS(args.err, 0, 25);
-        ok = false;
-      }
-    }
-    uint32_t chunk = 0;
-    for (int pr = pair0; pr < args.tiles && ok; pr += pstep) {
-      const PairTile tg(pr);
-      const bool mine = h < tg.nb;  // this warp's block exists in this pair
-      const int jb0 = tg.j0 + h * kStripTile;
-      const bool diag_top = tg.J0 + h == tg.I && rank == 0;  // rows 0-127 of the diagonal block
-      const int row = tg.i0 + (int)rank * kTile + 32 * q + lane;
-      int ci = 0;
-      for (int t0 = 0; t0 < nst; ++ci) {
-        int t1 = t0;
-        while (!chunk_ends(t1)) ++t1;
-        const bool final_chunk = t1 + 1 == nst;
-        bool unused;
-        const float scale = __int_as_float((127 - 2 * args.kexp[stage_block(t0, unused)]) << 23);
-        ok = mbar_wait(&acc_full, chunk & 1, args.err, 26);
-        if (!ok) break;
-        tc_fence_after();
-#pragma unroll 1
-        for (int cg = 0; mine && cg < 8; ++cg) {
-          if (diag_top && cg >= 4) break;          // above the diagonal
-          if (jb0 + cg * 32 >= args.n) break;
-          uint32_t acc[32];
-          TMEM_LD32(tmem + lane_base + (uint32_t)(h * 256 + cg * 32), acc);
-          tmem_wait_ld();
-          const int grp = cg * 8 * 32;
-          if (final_chunk) {
-            float th[32], tl[32];
-            final_tail(ci > 0, hi4, lo4, grp, acc, scale, keep, th, tl);
-            if (row < args.n) strip_final(args, th, tl, row, jb0 + cg * 32);
-          } else {
-            float hv[32], lv[32];
-            if (ci > 0) {
-#pragma unroll
-              for (int u = 0; u < 8; ++u) {
-                const float4 a4 = ld_keep(hi4 + grp + u * 32, keep);
-                const float4 b4 = ld_keep(lo4 + grp + u * 32, keep);
-                hv[4 * u] = a4.x, hv[4 * u + 1] = a4.y, hv[4 * u + 2] = a4.z, hv[4 * u + 3] = a4.w;
-                lv[4 * u] = b4.x, lv[4 * u + 1] = b4.y, lv[4 * u + 2] = b4.z, lv[4 * u + 3] = b4.w;
-              }
-            } else {
-#pragma unroll
-              for (int t = 0; t < 32; ++t) hv[t] = lv[t] = 0.f;
-            }
-#pragma unroll
-            for (int t = 0; t < 32; ++t) {
-              const float a = __uint_as_float(acc[t]) * scale;
-              const float s2 = __fadd_rn(hv[t], a);
-              const float bb = __fsub_rn(s2, hv[t]);
-              const float e = __fadd_rn(__fsub_rn(hv[t], __fsub_rn(s2, bb)), __fsub_rn(a, bb));
-              hv[t] = s2;
-              lv[t] = __fadd_rn(lv[t], e);
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              st_keep(hi4 + grp + u * 32,
-                      make_float4(hv[4 * u], hv[4 * u + 1], hv[4 * u + 2], hv[4 * u + 3]), keep);
-              st_keep(lo4 + grp + u * 32,
-                      make_float4(lv[4 * u], lv[4 * u + 1], lv[4 * u + 2], lv[4 * u + 3]), keep);
-            }
-          }
-        }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) {
-          if (leader) mbar_arrive(&acc_empty);
-          else mbar_arrive_remote(acce_leader);
-        }
-        ++chunk;
-        t0 = t1 + 1;
-      }
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  pair_cluster_sync();  // neither CTA leaves while the other may still reach into it
-  if (warp == 0) {
-    tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, 512;" ::"r"(tmem)
-                 : "memory");
-  }
-}
-
 // E = head (lower triangle) when the tail contributes nothing to the last window: the
 // float nearest each (hi, lo) pair.
 __global__ void k_head_to_float(const float2* __restrict__ head, int64_t ldh,
@@ -1141,22 +721,12 @@ int launch_ek_tc(const void* p0, const void* p1, const void* p2, const void* p8,
       !make_map(&m1n, p1, npad, plane_cols, 32) || !make_map(&m2n, p2, npad, plane_cols, 32) ||
       !make_map(&m8, p8, npad, plane_cols, 128, true))
     return CPM_ECUDA;
-  // one CTA per 256 x 256 tile; CPM_TC_TILE=pair in the environment runs the CTA-pair
-  // kernel (cta_group::2) on 256 x 512 pair tiles where the rows fill whole 256-row blocks
-  const char* env_tile = getenv("CPM_TC_TILE");
-  const bool pair2 = npad % kStripTile == 0 && env_tile && strcmp(env_tile, "pair") == 0;
-  const int smem6 = pair2 ? PairCfg<true>::kStages * PairCfg<true>::kStageBytes + 1024
-                          : StripCfg<true>::kStages * StripCfg<true>::kStageBytes + 1024;
-  const int smem31 = pair2 ? PairCfg<false>::kStages * PairCfg<false>::kStageBytes + 1024
-                           : StripCfg<false>::kStages * StripCfg<false>::kStageBytes + 1024;
-  if (pair2 ? (cudaFuncSetAttribute(k_ek_pair<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    smem6) != cudaSuccess ||
-               cudaFuncSetAttribute(k_ek_pair<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    smem31) != cudaSuccess)
-            : (cudaFuncSetAttribute(k_ek_strip<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    smem6) != cudaSuccess ||
-               cudaFuncSetAttribute(k_ek_strip<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    smem31) != cudaSuccess))
+  const int smem6 = StripCfg<true>::kStages * StripCfg<true>::kStageBytes + 1024;
+  const int smem31 = StripCfg<false>::kStages * StripCfg<false>::kStageBytes + 1024;
+  if (cudaFuncSetAttribute(k_ek_strip<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           smem6) != cudaSuccess ||
+      cudaFuncSetAttribute(k_ek_strip<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           smem31) != cudaSuccess)
     return CPM_ECUDA;
   // the six-product part [kb_begin, x6_end) and the rest [l_begin, kb_end); kb6_end is
   // even, so each part holds whole [cos | sin] block pairs
@@ -1166,8 +736,7 @@ int launch_ek_tc(const void* p0, const void* p1, const void* p2, const void* p8,
   StripArgs a;
   a.n = n;
   a.npad = npad;
-  // single tiles: nt (nt + 1) / 2; pairs: floor((nt + 1)^2 / 4)
-  a.tiles = pair2 ? (nt + 1) * (nt + 1) / 4 : nt * (nt + 1) / 2;
+  a.tiles = nt * (nt + 1) / 2;
   a.kb3_end = kb3_end;
   a.kb8_begin = kb8_begin;
   a.kb_col0 = kb_col0;
@@ -1179,29 +748,11 @@ int launch_ek_tc(const void* p0, const void* p1, const void* p2, const void* p8,
   a.ldh = ldh;
   a.ldE = ldE;
   a.err = err;
-  a.tile_map = pair2 ? nullptr : tile_map;
+  a.tile_map = tile_map;
   // one CTA per tile; the hardware hands each SM its next tile as it frees up, in the
   // order of the tile map
   auto launch = [&](bool six) {
     const int smem = six ? smem6 : smem31;
-    if (pair2) {  // one two-CTA cluster per pair tile
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(2 * a.tiles);
-      cfg.blockDim = dim3(kPairThreads);
-      cfg.dynamicSmemBytes = smem;
-      cfg.stream = s;
-      cudaLaunchAttribute at[1];
-      at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = 2;
-      at[0].val.clusterDim.y = 1;
-      at[0].val.clusterDim.z = 1;
-      cfg.attrs = at;
-      cfg.numAttrs = 1;
-      const cudaError_t e = six ? cudaLaunchKernelEx(&cfg, k_ek_pair<true>, m0, m0n, m1n, m2n, m8, a)
-                                : cudaLaunchKernelEx(&cfg, k_ek_pair<false>, m0, m0n, m1n, m2n, m8, a);
-      note_launch();
-      return e;
-    }
     if (six)
       k_ek_strip<true><<<a.tiles, kStripThreads, smem, s>>>(m0, m0n, m1n, m2n, m8, a);
     else
