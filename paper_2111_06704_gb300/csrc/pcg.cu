@@ -763,34 +763,37 @@ __global__ void k_diff_t(int n, int64_t ldv, const double* __restrict__ x,
 
 // PCG-DC apply of the many-column solves of a float E: z = P r (+ p_gap sum r) for the
 // 16 columns of a group in one pass over P (the per-column kernel above reads P once for
-// every column: at r_cut = 8 A, some 200 entries a row, that is HBM-bound).  rt holds r
-// as floats in the streamed matvec's layout ([group][row][16]).  A warp takes a row at a
-// time, 32 entries per step: one coalesced load of their column indices and values, then
-// four independent 16-byte gathers a lane (lane l: entries 8 k + l / 4, k < 4, columns
-// 4 (l % 4) .. + 3, the index and value passed by shuffles), the eight slots summed by
-// shuffles at the row's end.  The sums are float: P r is the preconditioner's output
-// only (the flexible Polak-Ribiere step tolerates its rounding, ~1e-7 of z) and
-// convergence is decided on replaced residuals.  A block works through a contiguous run
-// of rows, so that neighbouring rows' gathers meet in L1.  The grid's x extent is the
-// dots' part count, as in k_dc_apply; partial dots [r^T z_new, r^T z_old] into slots 0,
-// 1 of every column of the group; rsum_part may be the dots buffer itself (only slot 3
-// is read).
-constexpr int kDcThreads = 512;
+// every column).  rt holds r as floats in the streamed matvec's layout ([group][row][16]).
+// A warp takes kDcRowsPerWarp consecutive rows, one at a time: it loads up to 128 of the
+// row's entries at once (four coalesced loads of column indices and values a lane), then
+// issues 16 independent 16-byte gathers a lane (lane l: entries 8 k + l / 4, columns
+// 4 (l % 4) .. + 3, the index and value passed by shuffles) and sums the eight slots by
+// shuffles at the row's end; the row's r and z are loaded before the gathers.  A row thus
+// waits on three memory round trips, not one for every 32 entries, and the grid (64 rows
+// a block, thousands of blocks) keeps every SM full.  The sums are float: P r is the
+// preconditioner's output only (the flexible Polak-Ribiere step tolerates its rounding,
+// ~1e-7 of z) and convergence is decided on replaced residuals.  Each block writes its
+// partial dots [r^T z_new, r^T z_old] to dpart; k_dc_dots adds them in block order into
+// the solver's dots (part 0; the other parts zero).  rsum_part may be the dots buffer
+// itself (only slot 3 is read).
+constexpr int kDcWarps = 8;
+constexpr int kDcRowsPerWarp = 8;
+constexpr int kDcRowsPerBlock = kDcWarps * kDcRowsPerWarp;
+constexpr int kDcChunk = 128;  // entries loaded at once
 
-__global__ void __launch_bounds__(kDcThreads)
+__global__ void __launch_bounds__(kDcWarps * 32, 3)
 k_dc_apply_t(int n, int64_t ldv, int nrhs, const ColState* __restrict__ st,
              const int64_t* __restrict__ off, const int* __restrict__ idx,
              const double* __restrict__ prow, double pgap, const float* __restrict__ rt,
              const double* __restrict__ r, double* __restrict__ z,
-             const double* __restrict__ rsum_part, int nparts, double* __restrict__ dots,
+             const double* __restrict__ rsum_part, int nparts, double* __restrict__ dpart,
              int first) {
-  constexpr int kWarps = kDcThreads / 32;
   __shared__ double s_gsum[kFastCols];
   __shared__ int s_active[kFastCols];
-  __shared__ double s_red[kWarps][kFastCols][2];
+  __shared__ double s_red[kDcWarps][kFastCols][2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = blockIdx.y, c0 = grp * kFastCols;
-  for (int cc = warp; cc < kFastCols; cc += kWarps) {  // p_gap sums and active flags
+  for (int cc = warp; cc < kFastCols; cc += kDcWarps) {  // p_gap sums and active flags
     const int col = c0 + cc;
     double sr = 0.0;
     if (col < nrhs && pgap != 0.0)
@@ -811,36 +814,38 @@ k_dc_apply_t(int n, int64_t ldv, int nrhs, const ColState* __restrict__ st,
   const double gsum = fin ? s_gsum[cf] : 0.0;
   const int64_t oz = (int64_t)(c0 + cf) * ldv;
   const float* rg = rt + (int64_t)grp * ldv * kFastCols + cq;
-  const int per = (n + gridDim.x - 1) / gridDim.x;
-  const int j0 = blockIdx.x * per, j1 = min(n, j0 + per);
+  const int jw = blockIdx.x * kDcRowsPerBlock + warp * kDcRowsPerWarp;
   double v0 = 0.0, v1 = 0.0;
-  for (int j = j0 + warp; j < j1; j += kWarps) {
+  for (int j = jw; j < min(n, jw + kDcRowsPerWarp); ++j) {
+    double rj = 0.0, zo = 0.0;
+    if (fin) {  // issued ahead of the gathers
+      rj = r[oz + j];
+      zo = z[oz + j];
+    }
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     const int64_t e1 = off[j + 1];
-    for (int64_t e0 = off[j]; e0 < e1; e0 += 32) {
-      const int left = (int)min((int64_t)32, e1 - e0);  // entries in this step
-      int id = 0;
-      float pe = 0.f;
-      if (lane < left) {
-        id = __ldg(idx + e0 + lane);
-        pe = (float)__ldg(prow + e0 + lane);
-      }
-      float4 rv[4];
-      float pk[4];
+    for (int64_t eb = off[j]; eb < e1; eb += kDcChunk) {
+      const int left = (int)min((int64_t)kDcChunk, e1 - eb);  // entries in this chunk
+      int id[kDcChunk / 32];
+      float pe[kDcChunk / 32];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int src = 8 * k + slot;
-        const int ik = __shfl_sync(0xffffffffu, id, src);
-        pk[k] = __shfl_sync(0xffffffffu, pe, src);
-        rv[k] = src < left ? __ldg(reinterpret_cast<const float4*>(rg + (int64_t)ik * kFastCols))
-                           : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int m = 0; m < kDcChunk / 32; ++m) {
+        const int t = 32 * m + lane;
+        id[m] = t < left ? __ldg(idx + eb + t) : 0;
+        pe[m] = t < left ? (float)__ldg(prow + eb + t) : 0.f;
       }
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        acc.x = fmaf(pk[k], rv[k].x, acc.x);
-        acc.y = fmaf(pk[k], rv[k].y, acc.y);
-        acc.z = fmaf(pk[k], rv[k].z, acc.z);
-        acc.w = fmaf(pk[k], rv[k].w, acc.w);
+      for (int k = 0; k < kDcChunk / 8; ++k) {
+        const int src = 8 * k + slot;  // entry of this chunk: load m = k / 4, lane 8 (k % 4) + slot
+        const int ik = __shfl_sync(0xffffffffu, id[k >> 2], 8 * (k & 3) + slot);
+        const float pk = __shfl_sync(0xffffffffu, pe[k >> 2], 8 * (k & 3) + slot);
+        if (src < left) {
+          const float4 rv = __ldg(reinterpret_cast<const float4*>(rg + (int64_t)ik * kFastCols));
+          acc.x = fmaf(pk, rv.x, acc.x);
+          acc.y = fmaf(pk, rv.y, acc.y);
+          acc.z = fmaf(pk, rv.z, acc.z);
+          acc.w = fmaf(pk, rv.w, acc.w);
+        }
       }
     }
 #pragma unroll
@@ -853,8 +858,6 @@ k_dc_apply_t(int n, int64_t ldv, int nrhs, const ColState* __restrict__ st,
     if (fin) {
       const float a = comp == 0 ? acc.x : comp == 1 ? acc.y : comp == 2 ? acc.z : acc.w;
       const double zn = gsum + (double)a;
-      const double rj = r[oz + j];
-      const double zo = z[oz + j];
       if (act) z[oz + j] = zn;
       v0 += rj * zn;
       v1 += rj * zo;
@@ -869,8 +872,28 @@ k_dc_apply_t(int n, int64_t ldv, int nrhs, const ColState* __restrict__ st,
     const int cc = threadIdx.x >> 1, t = threadIdx.x & 1;
     double sv = 0.0;
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) sv += s_red[w][cc][t];
-    if (c0 + cc < nrhs) dots[((int64_t)blockIdx.x * nrhs + c0 + cc) * 4 + t] = sv;
+    for (int w = 0; w < kDcWarps; ++w) sv += s_red[w][cc][t];
+    if (c0 + cc < nrhs) dpart[((int64_t)blockIdx.x * nrhs + c0 + cc) * 2 + t] = sv;
+  }
+}
+
+// The blocks' partial dots of k_dc_apply_t, added in block order: part 0 of slots 0 and 1
+// of every column takes the sums, parts 1 .. nparts - 1 zero (the readers add all parts).
+__global__ void k_dc_dots(const double* __restrict__ dpart, int nblk, int nrhs,
+                          double* __restrict__ dots, int nparts) {
+  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (col >= nrhs) return;
+  double s0 = 0.0, s1 = 0.0;
+  for (int b = lane; b < nblk; b += 32) {
+    s0 += dpart[((int64_t)b * nrhs + col) * 2];
+    s1 += dpart[((int64_t)b * nrhs + col) * 2 + 1];
+  }
+  s0 = warp_sum(s0);
+  s1 = warp_sum(s1);
+  for (int b = lane; b < nparts; b += 32) {
+    dots[((int64_t)b * nrhs + col) * 4] = b == 0 ? s0 : 0.0;
+    dots[((int64_t)b * nrhs + col) * 4 + 1] = b == 0 ? s1 : 0.0;
   }
 }
 
@@ -1256,6 +1279,7 @@ int pcg_solve_kernels(Ctx* c, const SolveArgs& a) {
   const int glaunch = std::min(groups, 65535);
   const int splits = fast ? stream_splits(gm_fast, glaunch, nst, sms) : 1;
   const size_t cnt_bytes = (size_t)glaunch * gm_fast * sizeof(unsigned);
+  const int nblk_dc = (n + kDcRowsPerBlock - 1) / kDcRowsPerBlock;  // blocks of the DC apply
   // layout: x r z p q (double) | pv (storage type) | [fast: xt | x hi | x lo | x - x_a |
   //         x_a | r_a | unit partials | counters, error flag] | pq_part | dots | dots_dc |
   //         states
@@ -1275,6 +1299,7 @@ int pcg_solve_kernels(Ctx* c, const SolveArgs& a) {
                            ? take((size_t)glaunch * gm_fast * splits * kStOut * sizeof(double))
                            : 0,
                ocnt = fast ? take(cnt_bytes + sizeof(int)) : 0,
+               odp = fast ? take((size_t)nblk_dc * nrhs * 2 * sizeof(double)) : 0,
                opq = take((size_t)std::max(gm_fast, gm_exact) * nrhs * sizeof(double)),
                odt = take((size_t)ge * nrhs * 4 * sizeof(double)),
                odc = take((size_t)ge * nrhs * 4 * sizeof(double)),
@@ -1309,6 +1334,7 @@ int pcg_solve_kernels(Ctx* c, const SolveArgs& a) {
   float* xdt = fast ? (float*)(base + oxd) : nullptr;  // x - x_a, transposed per group
   double* xa = fast ? (double*)(base + oxa) : nullptr;  // the anchor's x and r
   double* ra = fast ? (double*)(base + ora) : nullptr;
+  double* dpart = fast ? (double*)(base + odp) : nullptr;  // the DC apply's block dots
   cudaStream_t s = c->stream;
   // the streamed matvec: its TMA map of E, units' partials and counters (zeroed above)
   CUtensorMap emap;
@@ -1356,9 +1382,11 @@ int pcg_solve_kernels(Ctx* c, const SolveArgs& a) {
     const cudaEvent_t d0 = ev();
     if (fast) {
       (k_diff_t<<<g2, kThreads, 0, s>>>(n, ldv, r, nullptr, xdt), note_launch());
-      (k_dc_apply_t<<<dim3(ge, groups), kDcThreads, 0, s>>>(
+      (k_dc_apply_t<<<dim3(nblk_dc, groups), kDcWarps * 32, 0, s>>>(
            n, ldv, nrhs, cur, (const int64_t*)c->nbr_off.ptr, (const int*)c->nbr_idx.ptr,
-           (const double*)c->prow.ptr, c->pgap, xdt, r, z, dots, ge, dots_out, first),
+           (const double*)c->prow.ptr, c->pgap, xdt, r, z, dots, ge, dpart, first),
+       note_launch());
+      (k_dc_dots<<<(nrhs + 7) / 8, 256, 0, s>>>(dpart, nblk_dc, nrhs, dots_out, ge),
        note_launch());
     } else {
       (k_dc_apply<<<g2, kThreads, 0, s>>>(n, ldv, nrhs, cur, (const int64_t*)c->nbr_off.ptr,
