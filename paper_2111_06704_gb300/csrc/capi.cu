@@ -950,13 +950,20 @@ int cpm_potential(cpm_ctx* c, int frames, int n_ion, const double* ion_xyz,
                                   (void**)&dqs)))
     return st;
   // scratch: v [frames][2 mpad] (storage type) | v_head [frames][2 kh] | b^sol_k [frames][n]
-  //          | fixed-point ion coordinates [frames][n_ion][3]
+  //          | fixed-point ion coordinates [frames][n_ion][3] | the direct sum's k-range
+  //          shares [nsplit][frames][n] (a streamed build split into more than one)
   auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
   const size_t vbytes = up((size_t)frames * 2 * c->mpad * c->esz());
   const size_t hbytes = up((size_t)frames * 2 * std::max(c->kh, 1) * sizeof(double));
   const size_t kbytes = up((size_t)frames * n * sizeof(double));
   const size_t ubytes = up((size_t)frames * std::max(n_ion, 1) * 3 * sizeof(uint32_t));
-  if ((st = buf_reserve(c, &c->ws_pot, vbytes + hbytes + kbytes + ubytes))) return st;
+  int dev_sms = 1;
+  cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device);
+  const int nsplit = !c->A.ptr && !f64
+                         ? bsol_direct_splits(n, frames, c->mpad, c->kh, std::max(dev_sms, 1))
+                         : 1;
+  const size_t sbytes = nsplit > 1 ? (size_t)nsplit * kbytes : 0;
+  if ((st = buf_reserve(c, &c->ws_pot, vbytes + hbytes + kbytes + ubytes + sbytes))) return st;
   if (!f64 && !c->turn.ptr) {
     if ((st = buf_alloc(c, &c->turn, 4096 * 4 * sizeof(float)))) return st;
     launch_turn_table(c->turn.ptr, s);
@@ -965,6 +972,8 @@ int cpm_potential(cpm_ctx* c, int frames, int n_ion, const double* ion_xyz,
   double* vh = (double*)((char*)c->ws_pot.ptr + vbytes);
   double* bk = (double*)((char*)c->ws_pot.ptr + vbytes + hbytes);
   uint32_t* sion = (uint32_t*)((char*)c->ws_pot.ptr + vbytes + hbytes + kbytes);
+  double* spart =
+      nsplit > 1 ? (double*)((char*)c->ws_pot.ptr + vbytes + hbytes + kbytes + ubytes) : nullptr;
   cudaEvent_t pev[4];
   for (int e = 0; e < 4; ++e) {
     while (c->ev_pot.size() < 4) {
@@ -986,7 +995,7 @@ int cpm_potential(cpm_ctx* c, int frames, int n_ion, const double* ion_xyz,
   cudaEventRecord(pev[1], s);
   launch_bsol_kspace(f64, c->A.ptr, (const double*)c->Ahead.ptr, n, c->mpad, c->kh, v, vh,
                      frames, bk, (const uint32_t*)c->sfix.ptr, (const int*)c->hkl.ptr,
-                     (const double*)c->sqw.ptr, c->turn.ptr, s);
+                     (const double*)c->sqw.ptr, c->turn.ptr, nsplit, spart, s);
   cudaEventRecord(pev[2], s);
   launch_bsol_real_and_finish((const double*)c->xyz.ptr, (const double*)c->alpha.ptr,
                               (const uint32_t*)c->sfix.ptr, n, dx, dq, sion, frames, n_ion,

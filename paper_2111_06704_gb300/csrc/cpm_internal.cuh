@@ -34,14 +34,18 @@ __device__ __forceinline__ void sincos_turns(uint32_t ph, float* s, float* c) {
 // and the remaining angle t = 2 pi (ph mod 2^20) 2^-32 < 1.6e-3 rad by angle addition:
 // cos = Tc - (t^2/2) Tc - t Ts and sin = Ts - (t^2/2) Ts + t Tc, the large term added last
 // (t^4/24 < 3e-13 and t^3/6 are below float rounding of the result).  About one float
-// ulp, as sincos_turns, in a third of the instructions.
-__device__ __forceinline__ void sincos_table(uint32_t ph, const float4* __restrict__ T,
-                                             float* s, float* c) {
-  const float4 t4 = __ldg(T + (ph >> 20));
+// ulp, as sincos_turns, in a third of the instructions.  sincos_entry takes the table
+// entry t4 = T[ph >> 20] already loaded (from global or shared memory).
+__device__ __forceinline__ void sincos_entry(float4 t4, uint32_t ph, float* s, float* c) {
   const float t = (float)(ph & 0xFFFFFu) * 1.462918119976564e-09f;  // 2 pi 2^-32
   const float h = -0.5f * t * t;
   *c = t4.x + fmaf(h, t4.x, fmaf(-t, t4.z, t4.y));
   *s = t4.z + fmaf(h, t4.z, fmaf(t, t4.x, t4.w));
+}
+
+__device__ __forceinline__ void sincos_table(uint32_t ph, const float4* __restrict__ T,
+                                             float* s, float* c) {
+  sincos_entry(__ldg(T + (ph >> 20)), ph, s, c);
 }
 
 // (h, l) += q x for a float pair (h, l) and q = qh + ql: the product qh x is split
@@ -255,7 +259,10 @@ void launch_ion_structure_factor(bool fp64, const double* ion_xyz, const uint32_
 void launch_bsol_kspace(bool fp64, const void* A, const double* Ahead, int n, int mpad, int kh,
                         const void* v, const double* vhead, int frames, double* bsol,
                         const uint32_t* sfix, const int* hkl, const double* sqw,
-                        const void* turn, cudaStream_t s);
+                        const void* turn, int nsplit, double* split_part, cudaStream_t s);
+// shares of the k range of a streamed build's direct k-space sum (split_part then holds
+// nsplit x frames x n doubles)
+int bsol_direct_splits(int n, int frames, int mpad, int kh, int sms);
 void launch_bsol_real_and_finish(const double* xyz, const double* alpha, const uint32_t* sfix,
                                  int n, const double* ion_xyz, const double* ion_q,
                                  const uint32_t* sion, int frames, int n_ion,

@@ -314,13 +314,19 @@ __global__ void __launch_bounds__(128, 4)
 k_bsol_kspace_direct(const uint32_t* __restrict__ sfix, int n, const int* __restrict__ hkl,
                      const double* __restrict__ sqw, int mpad, int kh,
                      const float4* __restrict__ turn, const float* __restrict__ v, int frames,
-                     double* __restrict__ bsol) {
+                     double* __restrict__ bsol, int nsplit, int64_t split_stride) {
   __shared__ uint32_t sh[kDirectChunk][3];
   // sqrt(W) (v_cos, v_sin) of frames 2 p and 2 p + 1: (c_2p, c_2p+1, s_2p, s_2p+1)
   __shared__ float4 sv[kDirectChunk][kDirectFrames / 2];
   const int f0 = blockIdx.y * kDirectFrames;
   const int nf = min(kDirectFrames, frames - f0);
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // block = atom block + nblk x share: share sp takes chunks [c0, c1) of the k range
+  const int nblk = gridDim.x / nsplit, sp = blockIdx.x / nblk;
+  const int i = (blockIdx.x - sp * nblk) * blockDim.x + threadIdx.x;
+  const int nch = (mpad - kh + kDirectChunk - 1) / kDirectChunk;
+  const int kbeg = kh + (int)((int64_t)sp * nch / nsplit) * kDirectChunk;
+  const int kend = min(mpad, kh + (int)((int64_t)(sp + 1) * nch / nsplit) * kDirectChunk);
+  double* out = bsol + sp * split_stride;
   uint32_t u0 = 0, u1 = 0, u2 = 0;
   if (i < n) {
     u0 = sfix[3 * i];
@@ -331,8 +337,8 @@ k_bsol_kspace_direct(const uint32_t* __restrict__ sfix, int n, const int* __rest
 #pragma unroll
   for (int f = 0; f < kDirectFrames / 2; ++f) hi[f] = lo[f] = make_float2(0.f, 0.f);
   const float2 m1 = make_float2(-1.f, -1.f);
-  for (int k0 = kh; k0 < mpad; k0 += kDirectChunk) {
-    const int cnt = min(kDirectChunk, mpad - k0);
+  for (int k0 = kbeg; k0 < kend; k0 += kDirectChunk) {
+    const int cnt = min(kDirectChunk, kend - k0);
     __syncthreads();
     for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
       const int k = k0 + t;
@@ -393,7 +399,7 @@ k_bsol_kspace_direct(const uint32_t* __restrict__ sfix, int n, const int* __rest
     for (int f = 0; f < kDirectFrames; ++f) {
       const float h = (f & 1) ? hi[f >> 1].y : hi[f >> 1].x;
       const float l = (f & 1) ? lo[f >> 1].y : lo[f >> 1].x;
-      if (f < nf) bsol[(size_t)(f0 + f) * n + i] = (double)h + (double)l;
+      if (f < nf) out[(size_t)(f0 + f) * n + i] = (double)h + (double)l;
     }
 }
 
@@ -938,13 +944,51 @@ void launch_ion_structure_factor(bool fp64, const double* ion_xyz, const uint32_
                                  const double* ion_q, int frames, int n_ion, const int* hkl,
                                  const double* sqw, int mpad, int kh, const double L[3],
                                  const void* turn, void* v, double* vhead, cudaStream_t s) {
-  dim3 grid((mpad + kSfThreads - 1) / kSfThreads, frames);
-  if (fp64)
+  if (fp64) {
+    dim3 grid((mpad + kSfThreads - 1) / kSfThreads, frames);
     (k_ion_sf_f64<<<grid, kSfThreads, 0, s>>>(ion_xyz, ion_q, n_ion, hkl, sqw, mpad, L[0], L[1],
                                               L[2], (double*)v), note_launch());
-  else
+  } else {
+    dim3 grid((mpad + kSfThreads - 1) / kSfThreads, frames);
     (k_ion_sf_f32<<<grid, kSfThreads, 0, s>>>(sion, ion_q, n_ion, hkl, sqw, mpad, kh,
-                                              (const float4*)turn, (float*)v, vhead), note_launch());
+                                              (const float4*)turn, (float*)v, vhead),
+     note_launch());
+  }
+}
+
+namespace {
+
+// The k-range shares of the direct sum, summed in share order into b^sol_k.
+__global__ void k_sum_splits(const double* __restrict__ part, int nsplit, int64_t stride,
+                             int64_t count, double* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double v = part[e];
+    for (int sp = 1; sp < nsplit; ++sp) v += part[sp * stride + e];
+    out[e] = v;
+  }
+}
+
+}  // namespace
+
+// Shares of the k range for the direct sum: the atom blocks of kDirectFrames-frame groups
+// (four resident an SM) times the shares fill whole waves of `sms` SMs best (a larger
+// count only where it fills 2% more of the last wave).
+int bsol_direct_splits(int n, int frames, int mpad, int kh, int sms) {
+  const int64_t blocks = (int64_t)((n + 127) / 128) * ((frames + kDirectFrames - 1) / kDirectFrames);
+  const int nch = (mpad - kh + kDirectChunk - 1) / kDirectChunk;
+  const int64_t cap = 4 * (int64_t)sms;
+  int best = 1;
+  double best_eff = -1.0;
+  for (int sp = 1; sp <= std::min(4, std::max(1, nch)); ++sp) {
+    const int64_t units = blocks * sp, waves = (units + cap - 1) / cap;
+    const double eff = (double)units / (double)(waves * cap);
+    if (eff > best_eff + 0.02) {
+      best_eff = eff;
+      best = sp;
+    }
+  }
+  return best;
 }
 
 // b^sol_k = A v: in float storage the head k-vectors (the heaviest weights) are
@@ -953,17 +997,25 @@ void launch_ion_structure_factor(bool fp64, const double* ion_xyz, const uint32_
 void launch_bsol_kspace(bool fp64, const void* A, const double* Ahead, int n, int mpad, int kh,
                         const void* v, const double* vhead, int frames, double* bsol,
                         const uint32_t* sfix, const int* hkl, const double* sqw,
-                        const void* turn, cudaStream_t s) {
+                        const void* turn, int nsplit, double* split_part, cudaStream_t s) {
   const int64_t lda = 2 * (int64_t)mpad;
   if (!A && !fp64) {
     const int fgroups = (frames + kDirectFrames - 1) / kDirectFrames;
+    const int sp = split_part ? nsplit : 1;
+    const int64_t stride = (int64_t)frames * n;  // between shares
+    double* dst = sp > 1 ? split_part : bsol;
     for (int g0 = 0; g0 < fgroups; g0 += 65535) {
       const int f0 = g0 * kDirectFrames;
-      (k_bsol_kspace_direct<<<dim3((n + 127) / 128, std::min(fgroups - g0, 65535)), 128, 0, s>>>(
-           sfix, n, hkl, sqw, mpad, kh, (const float4*)turn, (const float*)v + f0 * lda,
-           frames - f0, bsol + (int64_t)f0 * n),
+      (k_bsol_kspace_direct<<<dim3(sp * ((n + 127) / 128), std::min(fgroups - g0, 65535)), 128,
+                              0, s>>>(sfix, n, hkl, sqw, mpad, kh, (const float4*)turn,
+                                      (const float*)v + f0 * lda, frames - f0,
+                                      dst + (int64_t)f0 * n, sp, stride),
        note_launch());
     }
+    if (sp > 1)
+      (k_sum_splits<<<(int)std::min<int64_t>((stride + 255) / 256, 8192), 256, 0, s>>>(
+           split_part, sp, stride, stride, bsol),
+       note_launch());
     for (int g0 = 0; kh > 0 && g0 < (frames + 3) / 4; g0 += 65535) {
       const int f0 = 4 * g0;
       const dim3 grid((n * 32 + 255) / 256, std::min((frames - f0 + 3) / 4, 65535));
