@@ -647,7 +647,6 @@ k_bsol_real(const double* __restrict__ xyz, const double* __restrict__ alpha,
         for (int u = 0; u < 3; ++u) dn[u] = (float)dl[u] * rs.fs[u];
       }
       for (int si = 0; si < ns; ++si) {
-        bool near = false, far = false;
         float m2 = 0.f;
         if (i < n) {
           if constexpr (kMode == kShiftList) {
@@ -659,13 +658,16 @@ k_bsol_real(const double* __restrict__ xyz, const double* __restrict__ alpha,
           } else {
             m2 = fmaf(dn[0], dn[0], fmaf(dn[1], dn[1], dn[2] * dn[2]));
           }
-          if constexpr (kMode != kAllImages)
-            far = m2 >= rs.far2 && m2 < rs.cut2 && af2 * m2 >= 36.0f;
-          near = !far && m2 < rs.screen2;
         }
+        // no lane's image within the screen (most steps): one vote, nothing queued
+        const bool inr = i < n && m2 < rs.screen2;
+        if (!__any_sync(0xffffffffu, inr)) continue;
+        bool far = false;
+        if constexpr (kMode != kAllImages)
+          far = inr && m2 >= rs.far2 && m2 < rs.cut2 && af2 * m2 >= 36.0f;
+        const bool near = inr && !far;
         const unsigned mn = __ballot_sync(0xffffffffu, near);
         const unsigned mf = __ballot_sync(0xffffffffu, far);
-        if ((mn | mf) == 0u) continue;  // no lane's image passed (most steps)
         if (near) {
           const int at = qn + __popc(mn & below);
           nq[warp][at][0] = sx[t][0];
