@@ -634,85 +634,117 @@ k_bsol_real(const double* __restrict__ xyz, const double* __restrict__ alpha,
       qs += sx[t][3];
     }
     __syncthreads();
-    const int ns = kMode == kShiftList ? rs.nshift : 1;
-    for (int t = 0; t < cnt; ++t) {
-      int32_t dl[3] = {0, 0, 0};
-      float dn[3] = {0.f, 0.f, 0.f};  // the nearest image
-      if (i < n) {
-        const uint4 ut = su[t];
-        dl[0] = (int32_t)(ui[0] - ut.x);
-        dl[1] = (int32_t)(ui[1] - ut.y);
-        dl[2] = (int32_t)(ui[2] - ut.z);
-#pragma unroll
-        for (int u = 0; u < 3; ++u) dn[u] = (float)dl[u] * rs.fs[u];
+    // one image of ion t (whole-box shift si) at r^2 = m2: classified, queued, and the
+    // queues drained when full (no lane's image within the screen: nothing, one vote)
+    auto place = [&](int t, int si, float m2, const int32_t (&dl)[3]) {
+      const bool inr = i < n && m2 < rs.screen2;
+      if (!__any_sync(0xffffffffu, inr)) return;
+      bool far = false;
+      if constexpr (kMode != kAllImages)
+        far = inr && m2 >= rs.far2 && m2 < rs.cut2 && af2 * m2 >= 36.0f;
+      const bool near = inr && !far;
+      const unsigned mn = __ballot_sync(0xffffffffu, near);
+      const unsigned mf = __ballot_sync(0xffffffffu, far);
+      if (near) {
+        const int at = qn + __popc(mn & below);
+        nq[warp][at][0] = sx[t][0];
+        nq[warp][at][1] = sx[t][1];
+        nq[warp][at][2] = sx[t][2];
+        nq[warp][at][3] = sx[t][3];
+        if constexpr (kMode == kShiftList) {
+          ndl[warp][at][0] = dl[0];
+          ndl[warp][at][1] = dl[1];
+          ndl[warp][at][2] = dl[2];
+          nsh[warp][at] = (uint8_t)si;
+        }
+        nlane[warp][at] = (uint8_t)lane;
       }
-      for (int si = 0; si < ns; ++si) {
+      if (far) {
+        const int at = fn + __popc(mf & below);
+        fq[warp][at] = make_float2(m2, (float)sx[t][3]);
+        flane[warp][at] = (uint8_t)lane;
+      }
+      qn += __popc(mn);
+      fn += __popc(mf);
+      if (qn >= 32) {
+        drain(32, acc);
+        if (lane < qn - 32) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) nq[warp][lane][c] = nq[warp][32 + lane][c];
+          if constexpr (kMode == kShiftList) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ndl[warp][lane][c] = ndl[warp][32 + lane][c];
+            nsh[warp][lane] = nsh[warp][32 + lane];
+          }
+          nlane[warp][lane] = nlane[warp][32 + lane];
+        }
+        qn -= 32;
+        __syncwarp();
+      }
+      if (fn >= 32) {
+        drain_far(32, accf);
+        if (lane < fn - 32) {
+          fq[warp][lane] = fq[warp][32 + lane];
+          flane[warp][lane] = flane[warp][32 + lane];
+        }
+        fn -= 32;
+        __syncwarp();
+      }
+    };
+    // the nearest image's fixed-point difference (dl) and float components (dn)
+    auto nearest = [&](int t, int32_t (&dl)[3], float (&dn)[3]) {
+      const uint4 ut = su[t];
+      dl[0] = (int32_t)(ui[0] - ut.x);
+      dl[1] = (int32_t)(ui[1] - ut.y);
+      dl[2] = (int32_t)(ui[2] - ut.z);
+#pragma unroll
+      for (int u = 0; u < 3; ++u) dn[u] = (float)dl[u] * rs.fs[u];
+    };
+    if constexpr (kMode == kShiftList) {
+      for (int t = 0; t < cnt; ++t) {
+        int32_t dl[3] = {0, 0, 0};
+        float dn[3] = {0.f, 0.f, 0.f};
+        if (i < n) nearest(t, dl, dn);
+        for (int si = 0; si < rs.nshift; ++si) {
+          float m2 = 0.f;
+#pragma unroll
+          for (int u = 0; u < 3; ++u) {
+            const float du = dn[u] + rs.shift[si][u];
+            m2 = fmaf(du, du, m2);
+          }
+          place(t, si, m2, dl);
+        }
+      }
+    } else {
+      // two ions a step: their r^2 in paired instructions (each the scalar fma chain's
+      // value), one vote over both, then each placed in ion order
+      const int32_t dz[3] = {0, 0, 0};
+      int t = 0;
+      for (; t + 1 < cnt; t += 2) {
+        float2 m2 = make_float2(0.f, 0.f);
+        if (i < n) {
+          int32_t da[3], db[3];
+          float fa[3], fb[3];
+          nearest(t, da, fa);
+          nearest(t + 1, db, fb);
+          const float2 d0 = make_float2(fa[0], fb[0]), d1 = make_float2(fa[1], fb[1]),
+                       d2 = make_float2(fa[2], fb[2]);
+          m2 = __ffma2_rn(d0, d0, __ffma2_rn(d1, d1, __fmul2_rn(d2, d2)));
+        }
+        const bool any = i < n && fminf(m2.x, m2.y) < rs.screen2;
+        if (!__any_sync(0xffffffffu, any)) continue;
+        place(t, 0, m2.x, dz);
+        place(t + 1, 0, m2.y, dz);
+      }
+      if (t < cnt) {
         float m2 = 0.f;
         if (i < n) {
-          if constexpr (kMode == kShiftList) {
-#pragma unroll
-            for (int u = 0; u < 3; ++u) {
-              const float du = dn[u] + rs.shift[si][u];
-              m2 = fmaf(du, du, m2);
-            }
-          } else {
-            m2 = fmaf(dn[0], dn[0], fmaf(dn[1], dn[1], dn[2] * dn[2]));
-          }
+          int32_t dl[3];
+          float dn[3];
+          nearest(t, dl, dn);
+          m2 = fmaf(dn[0], dn[0], fmaf(dn[1], dn[1], dn[2] * dn[2]));
         }
-        // no lane's image within the screen (most steps): one vote, nothing queued
-        const bool inr = i < n && m2 < rs.screen2;
-        if (!__any_sync(0xffffffffu, inr)) continue;
-        bool far = false;
-        if constexpr (kMode != kAllImages)
-          far = inr && m2 >= rs.far2 && m2 < rs.cut2 && af2 * m2 >= 36.0f;
-        const bool near = inr && !far;
-        const unsigned mn = __ballot_sync(0xffffffffu, near);
-        const unsigned mf = __ballot_sync(0xffffffffu, far);
-        if (near) {
-          const int at = qn + __popc(mn & below);
-          nq[warp][at][0] = sx[t][0];
-          nq[warp][at][1] = sx[t][1];
-          nq[warp][at][2] = sx[t][2];
-          nq[warp][at][3] = sx[t][3];
-          if constexpr (kMode == kShiftList) {
-            ndl[warp][at][0] = dl[0];
-            ndl[warp][at][1] = dl[1];
-            ndl[warp][at][2] = dl[2];
-            nsh[warp][at] = (uint8_t)si;
-          }
-          nlane[warp][at] = (uint8_t)lane;
-        }
-        if (far) {
-          const int at = fn + __popc(mf & below);
-          fq[warp][at] = make_float2(m2, (float)sx[t][3]);
-          flane[warp][at] = (uint8_t)lane;
-        }
-        qn += __popc(mn);
-        fn += __popc(mf);
-        if (qn >= 32) {
-          drain(32, acc);
-          if (lane < qn - 32) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) nq[warp][lane][c] = nq[warp][32 + lane][c];
-            if constexpr (kMode == kShiftList) {
-#pragma unroll
-              for (int c = 0; c < 3; ++c) ndl[warp][lane][c] = ndl[warp][32 + lane][c];
-              nsh[warp][lane] = nsh[warp][32 + lane];
-            }
-            nlane[warp][lane] = nlane[warp][32 + lane];
-          }
-          qn -= 32;
-          __syncwarp();
-        }
-        if (fn >= 32) {
-          drain_far(32, accf);
-          if (lane < fn - 32) {
-            fq[warp][lane] = fq[warp][32 + lane];
-            flane[warp][lane] = flane[warp][32 + lane];
-          }
-          fn -= 32;
-          __syncwarp();
-        }
+        place(t, 0, m2, dz);
       }
     }
   }
