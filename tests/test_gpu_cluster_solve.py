@@ -67,7 +67,11 @@ def test_cluster_path_many_frames_with_a_guess(small_cell_oracle):
     assert np.all(r2 <= 1e-9)
     for f in range(9):
         assert rel_l2(q2[f], q1[f]) < 1e-7
-    assert np.all(np.abs(it1.astype(int) - it2.astype(int)) <= 1)
+    # the kernel path's inner iterations sum in float (the streamed matvec and the
+    # many-column PCG-DC apply) between exact residual replacements, the cluster path's
+    # are error-free throughout: near a 1e-9 tolerance a replacement that reopens a column
+    # costs it an iteration or two
+    assert np.all(np.abs(it1.astype(int) - it2.astype(int)) <= 2)
 
 
 @pytest.mark.parametrize("cells", [(3, 2), (11, 9)])  # 48 and 792 atoms: ragged row slices
