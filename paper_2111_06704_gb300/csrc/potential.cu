@@ -101,6 +101,21 @@ __device__ __forceinline__ void pair_add1(float& h, float& l, float x) {
 
 constexpr int kSfBlock = 8;  // ions a float block sum of the tail k-vectors holds
 
+// sin and cos of 2 pi ph 2^-32 from a 64-entry table of exp(2 pi i j / 64) (float cos and
+// sin, in shared memory: 512 bytes, few bank conflicts for random entries) and the
+// remaining angle t = 2 pi (ph mod 2^26) 2^-32 < 0.099 rad by angle addition, with
+// cos t = 1 - t^2/2 + t^4/24 and sin t = t - t^3/6 + t^5/120 (the next terms, t^6/720 and
+// t^7/5040, lie below float rounding).  At most 1.5 float ulp of 1 (0.5 on average).
+__device__ __forceinline__ void sincos_t64(uint32_t ph, const float2* T, float* s, float* c) {
+  const float2 e = T[ph >> 26];
+  const float t = (float)(ph & 0x3FFFFFFu) * 1.462918119976564e-09f;  // 2 pi 2^-32
+  const float t2 = t * t;
+  const float ct = fmaf(t2, fmaf(t2, 1.0f / 24.0f, -0.5f), 1.0f);
+  const float st = t * fmaf(t2, fmaf(t2, 1.0f / 120.0f, -1.0f / 6.0f), 1.0f);
+  *c = fmaf(e.x, ct, -(e.y * st));
+  *s = fmaf(e.y, ct, e.x * st);
+}
+
 // v[f][c(k)] = sqrt(W_k) sum_I q_I cos(theta_Ik), v[f][c(k) + 64] = sqrt(W_k) sum_I q_I sin,
 // in the column layout of the electrode operand, c(k) = 128 (k / 64) + k % 64, from the
 // exact fixed-point phases.  Sums over the ions run in error-free float pairs (S_K is a
@@ -117,10 +132,15 @@ k_ion_sf_f32(const uint32_t* __restrict__ sion, const double* __restrict__ ion_q
              double* __restrict__ vhead) {
   __shared__ uint32_t sf[kIonChunk][3];
   __shared__ float sqh[kIonChunk], sql[kIonChunk];
+  __shared__ float2 t64[64];  // exp(2 pi i j / 64): entries 64 j of the 4,096-entry table
   const int f = blockIdx.y;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t* fx = sion + (size_t)f * n_ion * 3;
   const double* q = ion_q + (size_t)f * n_ion;
+  for (int j = threadIdx.x; j < 64; j += blockDim.x) {
+    const float4 e = __ldg(turn + 64 * j);
+    t64[j] = make_float2(e.x, e.z);
+  }
   uint32_t h = 0, kk = 0, l = 0;
   if (k < mpad) {
     h = (uint32_t)hkl[3 * k];
@@ -163,7 +183,7 @@ k_ion_sf_f32(const uint32_t* __restrict__ sion, const double* __restrict__ ion_q
         for (int u = 0; u < kSfBlock; ++u) {
           const uint32_t ph = h * sf[t + u][0] + kk * sf[t + u][1] + l * sf[t + u][2];
           float sn, cs;
-          sincos_table(ph, turn, &sn, &cs);
+          sincos_t64(ph, t64, &sn, &cs);
           br = fmaf(sqh[t + u], cs, br);
           bi = fmaf(sqh[t + u], sn, bi);
           rlo = fmaf(sql[t + u], cs, rlo);
@@ -175,7 +195,7 @@ k_ion_sf_f32(const uint32_t* __restrict__ sion, const double* __restrict__ ion_q
       for (; t < cnt; ++t) {
         const uint32_t ph = h * sf[t][0] + kk * sf[t][1] + l * sf[t][2];
         float sn, cs;
-        sincos_table(ph, turn, &sn, &cs);
+        sincos_t64(ph, t64, &sn, &cs);
         pair_fma(reh, rel, sqh[t], sql[t], cs);
         pair_fma(imh, iml, sqh[t], sql[t], sn);
       }
